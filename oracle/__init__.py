@@ -1,0 +1,117 @@
+"""CPU oracle for the GPU system-call workloads (TEST INFRASTRUCTURE ONLY).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline /
+reference leg may import this package.  It shares no code with the CUDA path:
+``oracle.c`` is a plain sequential C program that issues the same Linux calls
+(pread, pwrite, ...) on the same seeded inputs and computes every result by its
+plain definition in exact integer arithmetic.  Each function cites the passage
+of Vesely et al., "GPU System Calls" (arXiv 1705.06965) that it follows.
+
+Pins (tests/test_oracle.py): brute force on tiny inputs, the published
+splitmix64 and FNV vectors, a hand-counted golden file, generator-recorded
+ground truth, chunk-size invariance and closed forms.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so beside it (gcc; OpenMP only for the
+    files-to-cores wordcount baseline)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", _SO, src])
+    return _SO
+
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        L.oracle_splitmix64_at.restype = ctypes.c_uint64
+        L.oracle_splitmix64_at.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        L.oracle_c1_histogram.restype = ctypes.c_int64
+        L.oracle_c1_histogram.argtypes = [ctypes.c_char_p, ctypes.c_uint64, ctypes.c_void_p]
+        L.oracle_c2_pwrite.restype = ctypes.c_int64
+        L.oracle_c2_pwrite.argtypes = [ctypes.c_char_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
+        L.oracle_c3_wordcount.restype = ctypes.c_int64
+        L.oracle_c3_wordcount.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]
+        L.oracle_c3_wordcount_omp.restype = ctypes.c_int64
+        L.oracle_c3_wordcount_omp.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int]
+        _lib = L
+    return _lib
+
+
+def _check(r: int, what: str) -> int:
+    if r < 0:
+        raise OSError(-r, f"oracle {what}: {os.strerror(-r)}")
+    return r
+
+
+def splitmix64_at(seed: int, i: int) -> int:
+    """(i+1)-th output of splitmix64 started at state `seed` (Steele et al. 2014)."""
+    return int(_L().oracle_splitmix64_at(seed & ((1 << 64) - 1), i))
+
+
+def c1_histogram(path: str, chunk: int = 4096) -> np.ndarray:
+    """C1 (Sec. 6, Fig. 5 pread microbenchmark): 256-bin uint32 histogram of the
+    file's bytes, read with pread in `chunk`-byte pieces."""
+    h = np.zeros(256, np.uint32)
+    _check(_L().oracle_c1_histogram(path.encode(), chunk, h.ctypes.data), "c1_histogram")
+    return h
+
+
+def c2_pwrite(path: str, n_threads: int, group: int = 1, seed: int = 0x5EED0002) -> int:
+    """C2 (Sec. 4.1 / Sec. 5 pwrite at a granularity): write thread gid's 64-byte
+    splitmix64 pattern at offset gid*64, one pwrite per `group` work-items.
+    Returns the number of pwrite calls issued."""
+    return _check(_L().oracle_c2_pwrite(path.encode(), n_threads, group, seed), "c2_pwrite")
+
+
+def _paths_array(paths):
+    arr = (ctypes.c_char_p * len(paths))(*[p.encode() for p in paths])
+    return arr
+
+
+def _queries_array(queries):
+    q = np.zeros((len(queries), 16), np.uint8)
+    ln = np.zeros(len(queries), np.uint8)
+    for i, s in enumerate(queries):
+        if not 0 < len(s) <= 16:
+            raise ValueError("queries must be 1..16 bytes")
+        q[i, :len(s)] = np.frombuffer(s, np.uint8)
+        ln[i] = len(s)
+    return q, ln
+
+
+def c3_wordcount(paths, queries, chunk: int = 1 << 20, per_file: bool = False, threads: int = 0):
+    """C3 (Sec. 7.1 wordcount): whole-token occurrences of each query word over the
+    files (tokens split on ' ' and '\\n').  threads > 0 runs the paper's OpenMP
+    files-to-cores CPU version instead of the sequential one."""
+    pa = _paths_array(paths)
+    q, ln = _queries_array(queries)
+    counts = np.zeros(len(queries), np.uint64)
+    if threads > 0:
+        if per_file:
+            raise ValueError("per_file needs the sequential oracle")
+        tot = _check(_L().oracle_c3_wordcount_omp(pa, len(paths), q.ctypes.data, ln.ctypes.data, len(queries),
+                                                  chunk, counts.ctypes.data, threads), "c3_wordcount_omp")
+        return counts, tot
+    pf = np.zeros((len(paths), len(queries)), np.uint64) if per_file else None
+    tot = _check(_L().oracle_c3_wordcount(pa, len(paths), q.ctypes.data, ln.ctypes.data, len(queries), chunk,
+                                          counts.ctypes.data, pf.ctypes.data if per_file else None),
+                 "c3_wordcount")
+    return (counts, tot, pf) if per_file else (counts, tot)

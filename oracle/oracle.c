@@ -1,0 +1,230 @@
+/*
+ * CPU oracle for the GPU system-call workloads.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline/reference leg may load this library.  It shares no
+ * code, header, table or constant generator with the CUDA path: it is a plain,
+ * sequential program that issues the same Linux system calls (pread, pwrite,
+ * ...) on the same seeded inputs and computes every result by its plain
+ * definition, in exact integer arithmetic.
+ *
+ * Paper: Vesely et al., "GPU System Calls" (GENESYS), arXiv 1705.06965.
+ */
+#define _GNU_SOURCE
+#include <errno.h>
+#include <fcntl.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <unistd.h>
+
+/* ------------------------------------------------------------------ common */
+
+/* pread that keeps calling until `len` bytes or end of file (a short read is
+ * legal for pread(2); the caller retries at the advanced offset). */
+static int64_t pread_full(int fd, uint8_t *buf, uint64_t len, uint64_t off) {
+  uint64_t got = 0;
+  while (got < len) {
+    ssize_t r = pread(fd, buf + got, len - got, (off_t)(off + got));
+    if (r < 0) {
+      if (errno == EINTR) continue;
+      return -errno;
+    }
+    if (r == 0) break;                       /* end of file */
+    got += (uint64_t)r;
+  }
+  return (int64_t)got;
+}
+
+static int64_t pwrite_full(int fd, const uint8_t *buf, uint64_t len, uint64_t off) {
+  uint64_t put = 0;
+  while (put < len) {
+    ssize_t r = pwrite(fd, buf + put, len - put, (off_t)(off + put));
+    if (r < 0) {
+      if (errno == EINTR) continue;
+      return -errno;
+    }
+    put += (uint64_t)r;
+  }
+  return (int64_t)put;
+}
+
+/* splitmix64 (Steele, Lea & Flood, OOPSLA 2014), written out from its
+ * published definition: state advances by the golden gamma, the output is the
+ * state passed through two xor-shift-multiply rounds and a final xor-shift.
+ * oracle_splitmix64_at(seed, i) is the (i+1)-th output of a generator whose
+ * state starts at `seed`. */
+uint64_t oracle_splitmix64_at(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+/* ---------------------------------------------------------------------- C1
+ * The pread microbenchmark of Sec. 6 (Fig. 5): a file on tmpfs is read with
+ * pread in fixed-size chunks; here every byte read is counted into a 256-bin
+ * histogram.  The sum over bins is order-free, so the assignment of chunks to
+ * work-groups on the GPU cannot change the result.
+ *
+ * hist[b] = number of bytes of the file whose value is b, read chunk by chunk
+ * at offsets 0, chunk, 2*chunk, ...  Returns the number of bytes read or -errno. */
+int64_t oracle_c1_histogram(const char *path, uint64_t chunk, uint32_t *hist) {
+  if (chunk == 0) return -EINVAL;
+  int fd = open(path, O_RDONLY);
+  if (fd < 0) return -errno;
+  uint8_t *buf = (uint8_t *)malloc(chunk);
+  if (!buf) { close(fd); return -ENOMEM; }
+  for (int b = 0; b < 256; ++b) hist[b] = 0;
+  uint64_t off = 0;
+  int64_t ret = 0;
+  for (;;) {
+    int64_t r = pread_full(fd, buf, chunk, off);
+    if (r < 0) { ret = r; break; }
+    for (int64_t i = 0; i < r; ++i) hist[buf[i]] += 1;
+    off += (uint64_t)r;
+    if ((uint64_t)r < chunk) { ret = (int64_t)off; break; }
+  }
+  free(buf);
+  close(fd);
+  return ret;
+}
+
+/* ---------------------------------------------------------------------- C2
+ * The pwrite microbenchmark (Sec. 4.1 "Invocation granularity", Sec. 6): each
+ * of n_threads work-items owns the 64 bytes at file offset gid*64, filled with
+ * the eight 64-bit little-endian words splitmix64_at(seed, gid*8 + k), k=0..7.
+ * pwrite takes an absolute offset, so the file content does not depend on the
+ * order or grouping of the calls (Sec. 4.1).  The oracle issues the calls the
+ * way a group of `group` work-items does when one designated work-item calls
+ * on behalf of the group (Sec. 5): one pwrite of the group's contiguous
+ * group*64 bytes, in group order; group = 1 is the work-item grain.
+ * The file is created/truncated first.  Returns the number of pwrite calls. */
+int64_t oracle_c2_pwrite(const char *path, uint64_t n_threads, uint64_t group, uint64_t seed) {
+  if (group == 0) return -EINVAL;
+  int fd = open(path, O_CREAT | O_TRUNC | O_WRONLY, 0644);
+  if (fd < 0) return -errno;
+  uint8_t *buf = (uint8_t *)malloc(group * 64);
+  if (!buf) { close(fd); return -ENOMEM; }
+  int64_t calls = 0;
+  for (uint64_t g0 = 0; g0 < n_threads; g0 += group) {
+    uint64_t members = n_threads - g0 < group ? n_threads - g0 : group;
+    for (uint64_t t = 0; t < members; ++t)
+      for (uint64_t k = 0; k < 8; ++k) {
+        uint64_t w = oracle_splitmix64_at(seed, (g0 + t) * 8 + k);
+        for (int j = 0; j < 8; ++j) buf[t * 64 + k * 8 + j] = (uint8_t)(w >> (8 * j));
+      }
+    int64_t r = pwrite_full(fd, buf, members * 64, g0 * 64);
+    if (r < 0) { calls = r; break; }
+    ++calls;
+  }
+  free(buf);
+  close(fd);
+  return calls;
+}
+
+/* ---------------------------------------------------------------------- C3
+ * Wordcount (Sec. 7.1): count the occurrences of query words in a list of
+ * files.  Reading: a token is a maximal run of bytes that are neither ' ' nor
+ * '\n'; an occurrence is a token equal, byte for byte and as a whole, to a
+ * query.  Each file is read sequentially with pread in `chunk`-byte pieces;
+ * a token cut by a chunk boundary is carried over to the next piece.
+ *
+ * counts[q] += occurrences of query q (queries16[q*16 .. +qlen[q]]) over all
+ * files; if per_file is non-NULL, per_file[f*nq + q] gets the file's own count.
+ * Returns total bytes read or -errno. */
+static int is_sep(uint8_t c) { return c == ' ' || c == '\n'; }
+
+#define TOKMAX 16
+
+static void match_token(const uint8_t *tok, uint64_t len, const uint8_t *queries16,
+                        const uint8_t *qlen, int nq, uint64_t *counts) {
+  if (len == 0 || len > TOKMAX) return;       /* queries are at most 16 bytes */
+  for (int q = 0; q < nq; ++q)
+    if (qlen[q] == len && memcmp(queries16 + 16 * q, tok, len) == 0) { counts[q] += 1; return; }
+}
+
+static int64_t wordcount_file(const char *path, const uint8_t *queries16, const uint8_t *qlen, int nq,
+                              uint64_t chunk, uint8_t *buf, uint64_t *counts) {
+  int fd = open(path, O_RDONLY);
+  if (fd < 0) return -errno;
+  uint8_t tok[TOKMAX];
+  uint64_t tlen = 0;                          /* may exceed TOKMAX: then the token cannot match */
+  uint64_t off = 0;
+  for (;;) {
+    int64_t r = pread_full(fd, buf, chunk, off);
+    if (r < 0) { close(fd); return r; }
+    for (int64_t i = 0; i < r; ++i) {
+      uint8_t c = buf[i];
+      if (is_sep(c)) {
+        match_token(tok, tlen, queries16, qlen, nq, counts);
+        tlen = 0;
+      } else {
+        if (tlen < TOKMAX) tok[tlen] = c;
+        ++tlen;
+      }
+    }
+    off += (uint64_t)r;
+    if ((uint64_t)r < chunk) break;
+  }
+  match_token(tok, tlen, queries16, qlen, nq, counts);   /* a token that ends at end of file */
+  close(fd);
+  return (int64_t)off;
+}
+
+int64_t oracle_c3_wordcount(const char **paths, int n_files, const uint8_t *queries16, const uint8_t *qlen,
+                            int nq, uint64_t chunk, uint64_t *counts, uint64_t *per_file) {
+  if (chunk == 0) return -EINVAL;
+  uint8_t *buf = (uint8_t *)malloc(chunk);
+  uint64_t *fc = (uint64_t *)calloc((size_t)nq, sizeof(uint64_t));
+  if (!buf || !fc) { free(buf); free(fc); return -ENOMEM; }
+  for (int q = 0; q < nq; ++q) counts[q] = 0;
+  int64_t total = 0;
+  for (int f = 0; f < n_files; ++f) {
+    for (int q = 0; q < nq; ++q) fc[q] = 0;
+    int64_t r = wordcount_file(paths[f], queries16, qlen, nq, chunk, buf, fc);
+    if (r < 0) { total = r; break; }
+    total += r;
+    for (int q = 0; q < nq; ++q) {
+      counts[q] += fc[q];
+      if (per_file) per_file[(size_t)f * nq + q] = fc[q];
+    }
+  }
+  free(buf);
+  free(fc);
+  return total;
+}
+
+/* The paper's CPU comparison for wordcount (Sec. 7.1): the same count with
+ * OpenMP, files assigned to cores.  Same result as oracle_c3_wordcount. */
+int64_t oracle_c3_wordcount_omp(const char **paths, int n_files, const uint8_t *queries16, const uint8_t *qlen,
+                                int nq, uint64_t chunk, uint64_t *counts, int n_threads) {
+  if (chunk == 0) return -EINVAL;
+  for (int q = 0; q < nq; ++q) counts[q] = 0;
+  int64_t total = 0;
+  int err = 0;
+  if (n_threads < 1) n_threads = 1;
+#pragma omp parallel num_threads(n_threads)
+  {
+    uint8_t *buf = (uint8_t *)malloc(chunk);
+    uint64_t *fc = (uint64_t *)calloc((size_t)nq, sizeof(uint64_t));
+    uint64_t *mine = (uint64_t *)calloc((size_t)nq, sizeof(uint64_t));
+    int64_t my_total = 0;
+#pragma omp for schedule(dynamic, 1)
+    for (int f = 0; f < n_files; ++f) {
+      if (!buf || !fc || !mine) { err = -ENOMEM; continue; }
+      for (int q = 0; q < nq; ++q) fc[q] = 0;
+      int64_t r = wordcount_file(paths[f], queries16, qlen, nq, chunk, buf, fc);
+      if (r < 0) { err = (int)r; continue; }
+      my_total += r;
+      for (int q = 0; q < nq; ++q) mine[q] += fc[q];
+    }
+#pragma omp critical
+    {
+      total += my_total;
+      if (mine) for (int q = 0; q < nq; ++q) counts[q] += mine[q];
+    }
+    free(buf); free(fc); free(mine);
+  }
+  return err ? err : total;
+}

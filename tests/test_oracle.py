@@ -1,0 +1,199 @@
+"""Pins of the CPU oracle against facts fixed outside it (no GPU needed).
+
+Each pin is chosen so that a plausible mistake in the oracle - a dropped final
+chunk or token, an off-by-one offset, a wrong byte order, a transposed
+operand - fails at least one of them.
+"""
+import collections
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_lines(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [ln.rstrip("\n") for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+# ------------------------------------------------------------------ splitmix64
+
+def test_splitmix64_published_vector():
+    # Published outputs of the splitmix64 reference implementation, state 0.
+    for ln in _golden_lines("splitmix64_seed0.txt"):
+        i, hx = ln.split()
+        assert oracle.splitmix64_at(0, int(i)) == int(hx, 16)
+        assert workloads.splitmix64_at(0, int(i)) == int(hx, 16)
+
+
+# ------------------------------------------------------------------------- C1
+
+def _write(path, data: bytes):
+    with open(path, "wb") as f:
+        f.write(data)
+    return path
+
+
+def test_c1_golden_abracadabra(tmp_path):
+    lines = _golden_lines("c1_abracadabra.txt")
+    content = lines[0].split(" ", 1)[1].encode()
+    want = np.zeros(256, np.uint32)
+    for ln in lines[1:]:
+        b, c = ln.split()
+        want[int(b)] = int(c)
+    p = _write(tmp_path / "a.bin", content)
+    for chunk in (1, 2, 3, 4096):
+        assert np.array_equal(oracle.c1_histogram(str(p), chunk), want)
+
+
+@pytest.mark.parametrize("size", [0, 1, 63, 64, 4095, 4096, 4097, 3 * 4096 + 17])
+def test_c1_brute_force_and_chunk_invariance(tmp_path, size):
+    rng = np.random.default_rng(size + 1)
+    data = rng.integers(0, 256, size, dtype=np.uint8).tobytes()
+    p = _write(tmp_path / "r.bin", data)
+    brute = np.zeros(256, np.uint32)
+    for b in data:                      # counting loop, one byte at a time
+        brute[b] += 1
+    for chunk in (1, 7, 4096, 1 << 20):
+        h = oracle.c1_histogram(str(p), chunk)
+        assert np.array_equal(h, brute), chunk
+        assert int(h.sum()) == size
+
+
+def test_c1_full_size_invariants():
+    p = workloads.c1_file()
+    h = oracle.c1_histogram(p, 4096)
+    n = 4 << 20
+    assert int(h.sum(dtype=np.uint64)) == n
+    # splitmix64 bytes are close to uniform: every bin within 6 sigma of n/256
+    mu, sd = n / 256, (n * (1 / 256) * (255 / 256)) ** 0.5
+    assert np.all(np.abs(h.astype(np.float64) - mu) < 6 * sd)
+    # the file's first 8 bytes are the first stream word, little-endian
+    with open(p, "rb") as f:
+        head = f.read(8)
+    assert int.from_bytes(head, "little") == oracle.splitmix64_at(workloads.SEED_C1, 0)
+
+
+def test_c1_missing_file_is_an_error(tmp_path):
+    with pytest.raises(OSError):
+        oracle.c1_histogram(str(tmp_path / "nope.bin"))
+
+
+# ------------------------------------------------------------------------- C2
+
+@pytest.mark.parametrize("n", [1, 31, 1024, 1000, 4096 + 5])
+def test_c2_file_equals_stream_for_every_grouping(tmp_path, n):
+    want = workloads.stream_bytes(workloads.SEED_C2, n * 64)
+    for group in (1, 32, 64, 256, 1024, n):
+        p = str(tmp_path / f"c2_{group}.bin")
+        calls = oracle.c2_pwrite(p, n, group)
+        assert calls == -(-n // group)
+        with open(p, "rb") as f:
+            got = f.read()
+        assert len(got) == n * 64
+        assert got == want, group
+
+
+def test_c2_seed0_head_is_published_vector(tmp_path):
+    p = str(tmp_path / "c2s0.bin")
+    oracle.c2_pwrite(p, 1, 1, seed=0)
+    with open(p, "rb") as f:
+        head = f.read(24)
+    words = [int.from_bytes(head[8 * k:8 * k + 8], "little") for k in range(3)]
+    assert words == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+# ------------------------------------------------------------------------- C3
+
+def _brute_wordcount(data: bytes, queries):
+    toks = [t for t in re.split(rb"[ \n]", data) if t]
+    c = collections.Counter(toks)
+    return np.array([c[q] for q in queries], np.uint64)
+
+
+def test_c3_golden_tiny(tmp_path):
+    lines = _golden_lines("c3_tiny.txt")
+    content = "\n".join(ln[len("content "):] for ln in lines if ln.startswith("content "))
+    content = content.replace("\\n", "\n").encode()
+    counts = [ln.split()[1:] for ln in lines if ln.startswith("count ")]
+    queries = [q.encode() for q, _ in counts]
+    want = np.array([int(c) for _, c in counts], np.uint64)
+    p = _write(tmp_path / "t.txt", content)
+    for chunk in (1, 2, 3, 5, 4096):
+        got, tot = oracle.c3_wordcount([str(p)], queries, chunk=chunk)
+        assert tot == len(content)
+        assert np.array_equal(got, want), chunk
+
+
+EDGE_FILES = [
+    b"",
+    b" ",
+    b"\n\n  \n",
+    b"cat",
+    b"cat ",
+    b" cat",
+    b"cat\ncat cat\n\ncat",
+    b"catcat cat cat1 ca t",
+    b"abcdefghijklmnopqrstuvwxyz cat abcdefghijklmnop cat",   # tokens longer than 16
+    b"abcdefghijklmnop",                                    # a 16-byte query token at EOF
+]
+
+
+def test_c3_edge_cases_brute_force(tmp_path):
+    queries = [b"cat", b"ca", b"t", b"abcdefghijklmnop", b"dog"]
+    for i, data in enumerate(EDGE_FILES):
+        p = _write(tmp_path / f"e{i}.txt", data)
+        want = _brute_wordcount(data, queries)
+        for chunk in (1, 2, 3, 16, 4096):
+            got, _ = oracle.c3_wordcount([str(p)], queries, chunk=chunk)
+            assert np.array_equal(got, want), (data, chunk)
+
+
+def test_c3_random_brute_force_multi_file(tmp_path):
+    rng = np.random.default_rng(7)
+    alphabet = np.frombuffer(b"ab \n", np.uint8)
+    paths, datas = [], []
+    for i in range(6):
+        data = alphabet[rng.integers(0, 4, int(rng.integers(0, 3000)))].tobytes()
+        paths.append(str(_write(tmp_path / f"m{i}.txt", data)))
+        datas.append(data)
+    queries = [b"a", b"b", b"ab", b"ba", b"aab", b"abab", b"bbbb"]
+    want = sum(_brute_wordcount(d, queries) for d in datas)
+    for chunk in (1, 5, 64, 1 << 20):
+        got, tot = oracle.c3_wordcount(paths, queries, chunk=chunk)
+        assert tot == sum(len(d) for d in datas)
+        assert np.array_equal(got, want)
+    omp, _ = oracle.c3_wordcount(paths, queries, chunk=64, threads=3)
+    assert np.array_equal(omp, want)
+
+
+def test_c3_matches_generator_ground_truth():
+    # The generator records, as it writes each file, how many emitted tokens
+    # equal each query; the oracle must find exactly those occurrences.
+    c = workloads.corpus(workloads.C3_SMALL)
+    got, tot, pf = c3 = oracle.c3_wordcount(c.paths, c.queries, chunk=4096, per_file=True)
+    assert tot == c.total_bytes
+    assert np.array_equal(pf, c.truth)
+    assert np.array_equal(got, c.truth_total())
+    # present words are found, absent words (the last four queries) only ever
+    # as a truncated final token
+    assert got[:60].sum() > 0
+    # the query list holds distinct strings
+    assert len(set(c.queries)) == len(c.queries)
+    del c3
+
+
+def test_c3_files_are_well_formed():
+    c = workloads.corpus(workloads.C3_SMALL)
+    for p, sz in zip(c.paths[:8], c.sizes[:8]):
+        data = open(p, "rb").read()
+        assert len(data) == int(sz)
+        assert re.fullmatch(rb"[a-z \n]*", data)
+        assert not data.startswith((b" ", b"\n"))
+        assert b"  " not in data and b"\n\n" not in data and b" \n" not in data and b"\n " not in data

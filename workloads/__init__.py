@@ -1,0 +1,177 @@
+"""Seeded synthetic inputs for the GPU system-call workloads.
+
+This module only makes inputs (files, query lists, request traces) and records
+what it emitted.  It holds none of the method's arithmetic, and both the CUDA
+path and the CPU oracle read what it writes.  Randomness is splitmix64
+(Steele, Lea & Flood 2014) used counter-based, implemented in ``gen.c``.
+
+Workloads (sizes of the full configurations; tests use scaled-down ones):
+
+* C1 - one file of 4 MiB of splitmix64 stream bytes (seed 0x5EED0001), read with
+  pread in 4 KiB chunks (the paper's pread microbenchmark, Sec. 6 / Fig. 5).
+* C2 - no input file: each thread writes 64 bytes of the seed-0x5EED0002 stream
+  at offset gid*64 (the pwrite microbenchmark of Sec. 4.1 / Sec. 6).
+* C3 - a corpus of lowercase words (Zipf(1.1) over a 50k vocabulary, lognormal
+  file sizes) with 64 query words (wordcount, Sec. 7.1).
+"""
+from __future__ import annotations
+
+import ctypes
+import hashlib
+import json
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "libgen.so")
+
+SEED_C1 = 0x5EED0001
+SEED_C2 = 0x5EED0002
+SEED_C3 = 0x5EED0003
+SEED_C4 = 0x5EED0004
+SEED_C5 = 0x5EED0005
+
+GAMMA = 0x9E3779B97F4A7C15
+MASK64 = (1 << 64) - 1
+
+
+def build(force: bool = False) -> str:
+    """Compile gen.c into libgen.so beside it (gcc, OpenMP)."""
+    src = os.path.join(_HERE, "gen.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", _SO, src, "-lm"])
+    return _SO
+
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        _lib.gen_splitmix64_at.restype = ctypes.c_uint64
+        _lib.gen_splitmix64_at.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        _lib.gen_stream_bytes.restype = None
+        _lib.gen_stream_bytes.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64]
+        _lib.gen_stream_file.restype = ctypes.c_int
+        _lib.gen_stream_file.argtypes = [ctypes.c_char_p, ctypes.c_uint64, ctypes.c_uint64]
+        _lib.gen_corpus.restype = ctypes.c_int
+        _lib.gen_corpus.argtypes = [
+            ctypes.c_char_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+            ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        _lib.gen_vocab_word.restype = ctypes.c_int
+        _lib.gen_vocab_word.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_char_p]
+    return _lib
+
+
+def splitmix64_at(seed: int, i: int) -> int:
+    """i-th (0-based) output of a splitmix64 generator started at state `seed`."""
+    return int(_L().gen_splitmix64_at(seed & MASK64, i & MASK64))
+
+
+def stream_bytes(seed: int, nbytes: int, byte0: int = 0) -> bytes:
+    """Bytes [byte0, byte0+nbytes) of the little-endian stream of `seed`."""
+    buf = ctypes.create_string_buffer(max(nbytes, 1))
+    _L().gen_stream_bytes(seed & MASK64, byte0, buf, nbytes)
+    return buf.raw[:nbytes]
+
+
+def scratch_dir(name: str) -> str:
+    """A directory on tmpfs (the paper's pread microbenchmark reads tmpfs files)."""
+    base = os.environ.get("GENESYS_DATA_DIR", "/dev/shm" if os.path.isdir("/dev/shm") else "/tmp")
+    d = os.path.join(base, f"genesys_{os.getuid()}_{name}")
+    os.makedirs(d, exist_ok=True)
+    return d
+
+
+def c1_file(path: str | None = None, nbytes: int = 4 << 20, seed: int = SEED_C1) -> str:
+    """The C1 input: `nbytes` of the splitmix64 stream of `seed`."""
+    if path is None:
+        path = os.path.join(scratch_dir("c1"), f"c1_{seed:x}_{nbytes}.bin")
+    if not (os.path.exists(path) and os.path.getsize(path) == nbytes):
+        rc = _L().gen_stream_file(path.encode(), seed & MASK64, nbytes)
+        if rc:
+            raise OSError(-rc, f"gen_stream_file({path})")
+    return path
+
+
+@dataclass
+class Corpus:
+    dir: str
+    paths: list
+    sizes: np.ndarray            # uint64 [n_files]
+    queries: list                # list[bytes]
+    truth: np.ndarray            # uint64 [n_files, n_queries]: emitted tokens equal to each query
+    tokens: np.ndarray           # uint64 [n_files]
+    params: dict = field(default_factory=dict)
+
+    @property
+    def total_bytes(self) -> int:
+        return int(self.sizes.sum())
+
+    def truth_total(self) -> np.ndarray:
+        return self.truth.sum(axis=0, dtype=np.uint64)
+
+    def queries_packed(self) -> tuple[np.ndarray, np.ndarray]:
+        """Queries as a [nq, 16] uint8 array (NUL padded) and a [nq] length array."""
+        q = np.zeros((len(self.queries), 16), np.uint8)
+        ln = np.zeros(len(self.queries), np.uint8)
+        for i, s in enumerate(self.queries):
+            q[i, :len(s)] = np.frombuffer(s, np.uint8)
+            ln[i] = len(s)
+        return q, ln
+
+
+C3_FULL = dict(n_files=2000, median_bytes=256 * 1024, sigma=2.0, cap_bytes=64 << 20,
+               vocab_n=50000, zipf_s=1.1, n_present=60, n_absent=4, seed=SEED_C3)
+C3_SMALL = dict(n_files=48, median_bytes=24 * 1024, sigma=1.0, cap_bytes=512 << 10,
+                vocab_n=2000, zipf_s=1.1, n_present=60, n_absent=4, seed=SEED_C3)
+
+
+def corpus(params: dict | None = None, name: str | None = None, n_threads: int | None = None) -> Corpus:
+    """Generate (or reuse, keyed by the parameters) a word corpus on tmpfs."""
+    p = dict(C3_FULL if params is None else params)
+    key = "_".join(f"{k}{p[k]}" for k in sorted(p))
+    tag = name or "c3_" + hashlib.sha1(key.encode()).hexdigest()[:12]
+    d = scratch_dir(tag)
+    man = os.path.join(d, "manifest.json")
+    if os.path.exists(man):
+        with open(man) as f:
+            m = json.load(f)
+        if m.get("params") == p and all(os.path.exists(x) for x in m["paths"]):
+            return Corpus(d, m["paths"], np.array(m["sizes"], np.uint64),
+                          [bytes.fromhex(q) for q in m["queries"]],
+                          np.array(m["truth"], np.uint64).reshape(len(m["paths"]), -1),
+                          np.array(m["tokens"], np.uint64), p)
+    n, nq = p["n_files"], p["n_present"] + p["n_absent"]
+    sizes = np.zeros(n, np.uint64)
+    qbuf = np.zeros(nq * 16, np.uint8)
+    qlen = np.zeros(nq, np.uint8)
+    truth = np.zeros(n * nq, np.uint64)
+    tokens = np.zeros(n, np.uint64)
+    nt = n_threads or max(1, min(32, os.cpu_count() or 1))
+    rc = _L().gen_corpus(d.encode(), n, float(p["median_bytes"]), float(p["sigma"]), int(p["cap_bytes"]),
+                         int(p["vocab_n"]), float(p["zipf_s"]), int(p["n_present"]), int(p["n_absent"]),
+                         int(p["seed"]) & MASK64, nt, sizes.ctypes.data, qbuf.ctypes.data, qlen.ctypes.data,
+                         truth.ctypes.data, tokens.ctypes.data)
+    if rc:
+        raise OSError(-rc, "gen_corpus")
+    paths = [os.path.join(d, f"f{i:05d}.txt") for i in range(n)]
+    queries = [bytes(qbuf[16 * i:16 * i + int(qlen[i])]) for i in range(nq)]
+    with open(man, "w") as f:
+        json.dump({"params": p, "paths": paths, "sizes": sizes.tolist(), "queries": [q.hex() for q in queries],
+                   "truth": truth.tolist(), "tokens": tokens.tolist()}, f)
+    return Corpus(d, paths, sizes, queries, truth.reshape(n, nq), tokens, p)
+
+
+def vocab_word(seed: int, vocab_n: int, idx: int) -> bytes:
+    buf = ctypes.create_string_buffer(16)
+    n = _L().gen_vocab_word(seed & MASK64, vocab_n, idx, buf)
+    if n < 0:
+        raise OSError(-n, "gen_vocab_word")
+    return buf.raw[:n]
