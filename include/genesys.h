@@ -1,0 +1,214 @@
+/*
+ * genesys.h - C ABI of the B300 GPU system-call runtime.
+ *
+ * What it implements: the GENESYS mechanism of Vesely et al., "GPU System
+ * Calls" (arXiv 1705.06965): GPU code invokes Linux system calls with
+ * function-like semantics at a chosen invocation granularity, ordering and
+ * blocking mode (Sec. 4.1); requests travel through a syscall area of 64-byte
+ * slots in system memory visible to both processors (Sec. 5, Fig. 3, Fig. 4);
+ * CPU-side workers carry out the calls, optionally coalescing several requests
+ * into one unit of work (Sec. 4.2, Sec. 5), and write the results back; a
+ * host function waits until every GPU call has completed (Sec. 8.3).
+ *
+ * Conventions for every function below:
+ *   - return 0 (or a documented non-negative value) on success and a negative
+ *     GENESYS_E* code on failure; nothing aborts the process;
+ *     genesys_last_error() describes the last failure of the calling thread;
+ *   - pointers are plain host or device addresses; "device pointer" means
+ *     memory the GPU can address (cudaMalloc'd memory, or the host-mapped
+ *     staging arena, whose addresses are valid on both sides);
+ *   - a `stream` argument is a cudaStream_t passed as void* (NULL = the
+ *     legacy default stream);
+ *   - the context owns the syscall area, the doorbell rings, the staging arena
+ *     and the service threads; the caller owns file descriptors, sockets and
+ *     the device buffers it passes in.
+ */
+#ifndef GENESYS_H
+#define GENESYS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "genesys_layout.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ error codes */
+#define GENESYS_OK          0
+#define GENESYS_EINVAL    (-22)   /* bad argument or illegal flag combination        */
+#define GENESYS_ENOMEM    (-12)   /* allocation failed, or staging arena exhausted  */
+#define GENESYS_ETIMEDOUT (-110)  /* a bounded wait gave up                          */
+#define GENESYS_ENODEV    (-19)   /* no usable CUDA device                           */
+#define GENESYS_EDEVICE   (-1001) /* the GPU reported failed or timed-out calls     */
+#define GENESYS_ECUDA     (-1000) /* a CUDA runtime call failed                      */
+
+/* ------------------------------------------------------------ configuration */
+#define GENESYS_INIT_HOST_ONLY   0x1u /* no GPU: host memory only; requests come from
+                                         genesys_emulate_call (protocol tests)        */
+#define GENESYS_INIT_NO_THREADS  0x2u /* spawn no service threads: the caller drives
+                                         them with genesys_service                    */
+#define GENESYS_INIT_ANY_SYSCALL 0x4u /* pass any system call number to the kernel
+                                         (default: the supported set only)            */
+
+typedef struct genesys_config {
+  uint32_t n_slots;            /* syscall-area slots; 0 = one per resident GPU thread
+                                  (SMs x 2048), the paper's one-slot-per-active-
+                                  work-item sizing (Sec. 5)                            */
+  uint32_t n_service_threads;  /* CPU service threads, one doorbell ring each (>= 1)   */
+  const int32_t *service_cpus; /* CPU to pin each service thread to, or NULL           */
+  uint64_t staging_bytes;      /* pinned host-mapped staging arena                      */
+  uint64_t coalesce_window_ns; /* Sec. 4.2: how long a service thread waits after the
+                                  first request of a batch for more to arrive (0 = take
+                                  what is ready)                                       */
+  uint32_t coalesce_max;       /* Sec. 4.2: most requests processed as one batch (>= 1) */
+  uint32_t merge;              /* 1: a batch's pread/pwrite requests that are
+                                  contiguous in the file are merged into one Linux call
+                                  (pread/pwrite or preadv/pwritev)                    */
+  uint64_t device_deadline_ns; /* every device-side wait gives up after this long      */
+  uint32_t lat_samples;        /* capacity of the per-call latency sample buffer       */
+  uint32_t flags;              /* GENESYS_INIT_*                                       */
+  uint64_t idle_spin_ns;       /* a service thread busy-polls this long after its last
+                                  request before it starts napping                     */
+} genesys_config;
+
+typedef struct genesys_stats {
+  uint64_t requests;           /* GPU requests retired by the service threads          */
+  uint64_t os_calls;           /* Linux calls made for them (fewer when merged)        */
+  uint64_t failed;             /* requests whose result was negative                   */
+  uint64_t nonblocking_failed; /* of those, requests nobody waited for (Sec. 4.1)      */
+  uint64_t bytes;              /* bytes moved by read/write-like calls                 */
+  uint64_t batches;            /* batches processed (Sec. 4.2 coalescing units)        */
+  uint64_t busy_ns;            /* service-thread time spent processing batches         */
+  uint64_t by_op[8];           /* requests per op: pread, pwrite, sendto, recvfrom,
+                                  mmap, munmap, internal ops, other                    */
+} genesys_stats;
+
+typedef struct genesys_ctx genesys_ctx;
+
+/* Fill *cfg with defaults: slots = SMs x 2048 (or 65536 without a GPU), 4
+ * service threads, 256 MiB staging, no coalescing window, coalesce_max 64,
+ * merge on, 2 s device deadline, 1 M latency samples. */
+int genesys_config_default(genesys_config *cfg);
+
+/* Create a context on CUDA device `device`: allocates the syscall area, the
+ * completion words and the doorbell rings in pinned host-mapped memory, the
+ * device-side slot state in device memory, the staging arena, and starts the
+ * service threads.  *out receives the context.  Sec. 5. */
+int genesys_init(const genesys_config *cfg, int device, genesys_ctx **out);
+
+/* Stop the service threads (after draining for up to 1 s) and free everything
+ * the context owns.  Idempotent for a NULL context. */
+int genesys_shutdown(genesys_ctx *ctx);
+
+/* The device view of the context (plain struct, pass it to kernels by value;
+ * genesys_device.cuh reads it). */
+int genesys_device_view(genesys_ctx *ctx, genesys_dev *out);
+
+/* ------------------------------------------------------------ launching */
+#define GENESYS_LAUNCH_GRAN_MASK   0x3u   /* GENESYS_GRAN_* the kernel uses            */
+#define GENESYS_LAUNCH_RELAXED     0x10u  /* the kernel's calls use relaxed ordering   */
+#define GENESYS_LAUNCH_NONBLOCKING 0x20u  /* the kernel's calls are non-blocking       */
+#define GENESYS_LAUNCH_COOPERATIVE 0x100u /* force a cooperative launch                */
+#define GENESYS_LAUNCH_SYNC        0x200u /* wait for the kernel, then drain its calls */
+
+/* Launch a kernel that makes GPU system calls.  `kernel` is the kernel's host
+ * stub (a __global__ function pointer from a library linked against the shared
+ * CUDA runtime); grid/block are 3 sizes each; args as for cudaLaunchKernel.
+ * `flags` declares the granularity/ordering/blocking the kernel uses so that
+ * the legality rules of Sec. 4.1 are checked before launch:
+ *   - work-item grain with relaxed ordering -> GENESYS_EINVAL (always strong);
+ *   - kernel grain with strong ordering -> cooperative launch; a grid larger
+ *     than the resident set -> GENESYS_EINVAL (this is the deadlock of Sec. 4.1).
+ * The per-launch kernel-grain state is reset on `stream` before the kernel. */
+int genesys_launch(genesys_ctx *ctx, const void *kernel, const uint32_t grid[3], const uint32_t block[3],
+                   size_t smem_bytes, void **args, uint32_t flags, void *stream);
+
+/* With GENESYS_INIT_NO_THREADS: process ready requests on the calling thread
+ * for up to timeout_ns; returns the number of requests processed.  With
+ * service threads: waits up to timeout_ns for all published requests to be
+ * processed; returns 0 or GENESYS_ETIMEDOUT. */
+int genesys_service(genesys_ctx *ctx, uint64_t timeout_ns);
+
+/* Sec. 8.3: wait until every request published so far (non-blocking ones
+ * included) has completed.  Call it after the kernels that made the calls
+ * have finished (e.g. after a stream synchronize).  0 or GENESYS_ETIMEDOUT. */
+int genesys_drain(genesys_ctx *ctx, uint64_t timeout_ns);
+
+int genesys_stats_get(genesys_ctx *ctx, genesys_stats *out);
+int genesys_stats_reset(genesys_ctx *ctx);
+
+/* Copy the device status words (GENESYS_ST_*) into out; clear them if `clear`. */
+int genesys_status(genesys_ctx *ctx, int32_t out[GENESYS_ST_WORDS], int clear);
+
+/* Copy up to `cap` per-call latency samples (ns, caller-side invocation
+ * latency) into out (host memory); *n_out = samples recorded (may exceed
+ * cap); clears the buffer if `clear`. */
+int genesys_latency(genesys_ctx *ctx, uint64_t *out, uint32_t cap, uint32_t *n_out, int clear);
+
+/* Bump-allocate `bytes` (256-byte aligned) from the staging arena: pinned,
+ * host-mapped memory whose address is valid on the host and on the GPU, so
+ * GPU code can pass it to pread/pwrite/sendto/recvfrom.  NULL if exhausted. */
+void *genesys_staging(genesys_ctx *ctx, size_t bytes);
+int genesys_staging_reset(genesys_ctx *ctx);
+
+/* Message of the calling thread's last failure. */
+const char *genesys_last_error(void);
+
+/* GENESYS_INIT_HOST_ONLY contexts: make one call through the full protocol
+ * from a CPU thread standing in for a GPU lane (claim a slot, marshal,
+ * publish, ring the doorbell, wait if GENESYS_REQ_BLOCKING is in flags).
+ * Safe to call from many threads at once.  *ret receives the result. */
+int genesys_emulate_call(genesys_ctx *ctx, uint32_t nr, const uint64_t args[6], uint32_t flags, int64_t *ret);
+
+/* ------------------------------------------------------------ workloads
+ * Data-parallel kernels that make GPU system calls and consume their results.
+ * Each returns 0, a negative GENESYS_E* code, or GENESYS_EDEVICE when a
+ * device-side call failed or timed out (details via genesys_status).  All
+ * launch on `stream` and return after the kernel finished and its calls
+ * were drained. */
+
+/* Forms of a workload. */
+#define GENESYS_FORM_PLAIN   0u  /* work-group grain, strong ordering, blocking      */
+#define GENESYS_FORM_BATCHED 1u  /* relaxed, non-blocking, double-buffered prefetch  */
+
+/* C1, Sec. 6 pread microbenchmark (Fig. 5): `groups` thread blocks of `threads`
+ * threads read `file_bytes` bytes of `fd` with pread in `chunk`-byte pieces
+ * (chunk i by block i mod groups) at work-group granularity and build a
+ * 256-bin byte histogram, added into hist_dev[256] (device pointer, uint32).
+ * staging: host-mapped, >= groups * chunk * (form == BATCHED ? 2 : 1) bytes,
+ * 16-byte aligned; chunk a multiple of 16, threads a multiple of 32. */
+int genesys_c1_histogram(genesys_ctx *ctx, int fd, uint64_t file_bytes, uint64_t chunk, uint32_t groups,
+                         uint32_t threads, uint32_t form, void *staging, uint64_t staging_bytes,
+                         uint32_t *hist_dev, void *stream);
+
+/* C2, the pwrite microbenchmark (Sec. 4.1 "Invocation granularity", Sec. 6):
+ * n_threads GPU threads each write the 64 bytes splitmix64_at(seed, gid*8+k),
+ * k = 0..7 (little-endian) to `fd` at offset gid*64.  `gran` (GENESYS_GRAN_*)
+ * and `group_threads` (threads per block, 32..1024, multiple of 32) set the
+ * invocation granularity: one pwrite per thread, per warp, per block, or one
+ * for the whole kernel; `order_relaxed`/`nonblocking` the semantics.
+ * staging: host-mapped, >= n_threads * 64 bytes.  Work-item grain with relaxed
+ * ordering is GENESYS_EINVAL (Sec. 4.1); kernel grain with strong ordering runs
+ * as a cooperative launch (grid-stride over the threads).  Per-call
+ * latencies go to the context's sample buffer (genesys_latency). */
+int genesys_c2_pwrite(genesys_ctx *ctx, int fd, uint64_t n_threads, uint32_t gran, uint32_t group_threads,
+                      uint32_t order_relaxed, uint32_t nonblocking, uint64_t seed, void *staging,
+                      uint64_t staging_bytes, void *stream);
+
+/* Strong-ordering visibility probe (Sec. 4.1: strong ordering means every
+ * store before the call has completed): n_threads threads each store their
+ * 8-byte word splitmix64_at(seed, gid) into probe[gid] (host-mapped), then a
+ * group of the given grain calls GENESYS_NR_CHECK_VISIBLE on the group's
+ * words; the CPU counts the words that are not yet visible.  The sum over
+ * calls is written to *violations_dev (device pointer, uint64). */
+int genesys_visibility_probe(genesys_ctx *ctx, uint64_t n_threads, uint32_t gran, uint32_t group_threads,
+                             uint32_t order_relaxed, uint64_t seed, uint64_t *probe,
+                             unsigned long long *violations_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GENESYS_H */

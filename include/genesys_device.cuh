@@ -1,0 +1,510 @@
+/*
+ * genesys_device.cuh - device side of GPU system calls (sm_103a).
+ *
+ * A GPU kernel invokes a Linux system call with function-like semantics
+ * (Sec. 5, "Invoking GPU system calls"):
+ *
+ *     int64_t r = genesys::call<Gran, Order, Block>(dev, SYS_pread64, fd, buf, len, off);
+ *
+ *   Gran  - invocation granularity (Sec. 4.1): ITEM (every calling thread is its
+ *           own caller), WARP (the active lanes of a warp; the lowest active
+ *           lane calls for them), GROUP (the thread block, the paper's
+ *           work-group; thread 0 calls) or KERNEL (the whole grid; one
+ *           elected thread calls).  Every thread of the group must make the
+ *           call (uniform control flow per group); the designated caller's
+ *           arguments are used (Sec. 5).
+ *   Order - STRONG: a group barrier before and after the call; RELAXED: a
+ *           barrier only before a producer call (write/send-like) and only
+ *           after a consumer call (read/recv-like) (Sec. 4.1, Sec. 5).  ITEM is
+ *           always strong (Sec. 4.1).  KERNEL+STRONG needs a cooperative launch
+ *           (the paper forbids it because a grid larger than the resident set
+ *           would deadlock, Sec. 4.1; a cooperative launch caps the grid at the
+ *           resident set, which removes that case).
+ *   Block - BLOCKING: the caller waits for the result, which is then returned
+ *           to every thread that passes the barrier after the call (a relaxed
+ *           producer has no such barrier: only the caller waits, the paper's
+ *           "one wavefront waits"); NONBLOCKING: returns 0 at once, the CPU
+ *           processes the call later (Sec. 4.1 "Blocking versus non-blocking").
+ *
+ * Results follow the raw Linux convention: >= 0, or -errno.  No wait in this
+ * file is unbounded: every spin gives up after dev.deadline_ns, returns
+ * -ETIMEDOUT and records it in dev.status.
+ *
+ * Pointer arguments must be addresses the host can use: pinned host-mapped
+ * memory (genesys_staging), or memory the GPU obtained through mmap.
+ */
+#ifndef GENESYS_DEVICE_CUH
+#define GENESYS_DEVICE_CUH
+
+#include <stdint.h>
+#include <sys/syscall.h>
+
+#include "genesys_layout.h"
+
+namespace genesys {
+
+enum Gran { ITEM = 0, WARP = 1, GROUP = 2, KERNEL = 3 };
+enum Order { STRONG = 0, RELAXED = 1 };
+enum Block { BLOCKING = 0, NONBLOCKING = 1 };
+/* Role of a call (Sec. 4.1 "System call ordering semantics"). */
+enum Role { ROLE_AUTO = 0, ROLE_PRODUCER = 1, ROLE_CONSUMER = 2, ROLE_BOTH = 3 };
+
+constexpr int64_t kETIMEDOUT = 110;
+
+/* ------------------------------------------------------------ primitives */
+
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint64_t ld_acquire_sys(const uint64_t *p) {
+  uint64_t v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t ld_relaxed_sys(const uint64_t *p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_sys(uint64_t *p, uint64_t v) {
+  asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(uint32_t *p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_relaxed_gpu(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_gpu(uint32_t *p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+/* 16-byte store to (host-mapped) memory */
+__device__ __forceinline__ void st_v2(uint64_t *p, uint64_t a, uint64_t b) {
+  asm volatile("st.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+
+__device__ __forceinline__ uint32_t lane_id() {
+  uint32_t l;
+  asm("mov.u32 %0, %%laneid;" : "=r"(l));
+  return l;
+}
+
+/* Hardware id of the calling lane: (SM, warp slot, lane).  The paper indexes
+ * the syscall area by the hardware id of the active work-item (Sec. 5); here it
+ * is the first slot a lane tries, so that concurrent callers rarely collide. */
+__device__ __forceinline__ uint32_t hw_lane_id() {
+  uint32_t sm, w;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+  asm volatile("mov.u32 %0, %%warpid;" : "=r"(w));
+  return (sm * 64u + (w & 63u)) * 32u + lane_id();
+}
+
+__device__ __forceinline__ int role_of(uint32_t nr) {
+  switch (nr) {
+    case SYS_write: case SYS_pwrite64: case SYS_sendto: case SYS_sendmmsg:
+    case SYS_munmap: case SYS_madvise: case SYS_close:
+      return ROLE_PRODUCER;
+    case SYS_read: case SYS_pread64: case SYS_recvfrom: case SYS_recvmmsg:
+    case SYS_mmap: case SYS_open: case SYS_openat: case GENESYS_NR_PREAD_DEV:
+      return ROLE_CONSUMER;
+    default:
+      return ROLE_BOTH;
+  }
+}
+
+__device__ __forceinline__ void note_error(const genesys_dev &g, int64_t code) {
+  atomicCAS(reinterpret_cast<int *>(&g.status[GENESYS_ST_FIRST_ERROR]), 0, (int)code);
+  if (code == -kETIMEDOUT) atomicAdd(reinterpret_cast<int *>(&g.status[GENESYS_ST_TIMEOUTS]), 1);
+}
+
+__device__ __forceinline__ void note_latency(const genesys_dev &g, uint64_t t0) {
+  if (g.lat_cap == 0) return;
+  uint32_t i = atomicAdd(g.lat_count, 1u);
+  if (i < g.lat_cap) g.lat[i] = now_ns() - t0;
+}
+
+__device__ __forceinline__ bool expired(const genesys_dev &g, uint64_t t0) {
+  return now_ns() - t0 > g.deadline_ns;
+}
+
+__device__ __forceinline__ uint32_t ring_of(const genesys_dev &g, uint32_t slot) {
+  return (slot >> 5) % g.n_rings;
+}
+
+/* ------------------------------------------------------ slot protocol
+ * One thread.  Claim a slot (device-side lock in HBM, never an RMW on host
+ * memory), then make sure the CPU has finished the slot's previous request
+ * (a non-blocking call may still be in flight: Fig. 4, "if the slot is not
+ * free, system call invocation is delayed"). */
+__device__ __forceinline__ int64_t slot_claim(const genesys_dev &g, uint32_t hint, uint32_t *slot_out,
+                                              uint64_t t0) {
+  uint32_t s = hint % g.n_slots;
+  uint32_t probes = 0, ns = 32;
+  while (atomicCAS(&g.owner[s], 0u, 1u) != 0u) {
+    s = (s + 1 == g.n_slots) ? 0 : s + 1;
+    if (++probes >= 64) {
+      probes = 0;
+      __nanosleep(ns);
+      ns = ns < 4096 ? ns * 2 : ns;
+      if (expired(g, t0)) { note_error(g, -kETIMEDOUT); return -kETIMEDOUT; }
+    }
+  }
+  __threadfence();
+  const uint32_t sq = ld_relaxed_gpu(&g.seq[s]);
+  if (ld_relaxed_gpu(&g.known_done[s]) != sq) {
+    ns = 128;
+    while ((uint32_t)(ld_acquire_sys(&g.done[s]) >> 32) != sq) {
+      if (expired(g, t0)) {
+        __threadfence();
+        atomicExch(&g.owner[s], 0u);
+        note_error(g, -kETIMEDOUT);
+        return -kETIMEDOUT;
+      }
+      __nanosleep(ns);
+      ns = ns < 2048 ? ns * 2 : ns;
+    }
+    st_relaxed_gpu(&g.known_done[s], sq);
+  }
+  *slot_out = s;
+  return 0;
+}
+
+/* Marshal the request into the slot with 16-byte stores; returns its sequence.
+ * The caller fences (system scope) and rings the doorbell afterwards. */
+__device__ __forceinline__ uint32_t slot_fill(const genesys_dev &g, uint32_t s, uint32_t nr, uint32_t flags,
+                                              uint64_t a0, uint64_t a1, uint64_t a2, uint64_t a3, uint64_t a4,
+                                              uint64_t a5) {
+  const uint32_t sq = ld_relaxed_gpu(&g.seq[s]) + 1u;
+  st_relaxed_gpu(&g.seq[s], sq);
+  genesys_slot *sl = g.slots + s;
+  st_v2(&sl->args[0], a0, a1);
+  st_v2(&sl->args[2], a2, a3);
+  st_v2(&sl->args[4], a4, a5);
+  const uint64_t req = ((uint64_t)sq << 32) | ((uint64_t)(nr & 0xFFFFu) << 16) | (flags & 0xFFFFu);
+  asm volatile("st.global.u64 [%0], %1;" ::"l"(&sl->req), "l"(req) : "memory");
+  return sq;
+}
+
+/* Doorbell for one published slot (one thread). */
+__device__ __forceinline__ void ring_one(const genesys_dev &g, uint32_t s) {
+  const uint32_t r = ring_of(g, s);
+  const uint32_t pos = atomicAdd(&g.ring_tail[r * 32u], 1u);
+  st_release_sys(g.rings + (size_t)r * (g.ring_mask + 1u) + (pos & g.ring_mask), GENESYS_RING_ENTRY(pos, s));
+}
+
+/* Doorbell for the lanes of `mask` that each published slot `s`: one atomic per
+ * ring per warp (lanes are grouped with __match_any_sync). */
+__device__ __forceinline__ void ring_warp(const genesys_dev &g, uint32_t mask, uint32_t s) {
+  const uint32_t r = ring_of(g, s);
+  const uint32_t peers = __match_any_sync(mask, r);
+  const uint32_t lane = lane_id();
+  const uint32_t leader = __ffs(peers) - 1;
+  const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(&g.ring_tail[r * 32u], (uint32_t)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  const uint32_t pos = base + rank;
+  st_release_sys(g.rings + (size_t)r * (g.ring_mask + 1u) + (pos & g.ring_mask), GENESYS_RING_ENTRY(pos, s));
+}
+
+/* Wait until the CPU finished request `sq` of slot `s`; returns its result. */
+__device__ __forceinline__ int64_t slot_wait(const genesys_dev &g, uint32_t s, uint32_t sq, uint64_t t0) {
+  uint32_t ns = 256;
+  uint64_t d;
+  for (;;) {
+    d = ld_acquire_sys(&g.done[s]);
+    if ((uint32_t)(d >> 32) == sq) break;
+    if (expired(g, t0)) { note_error(g, -kETIMEDOUT); return -kETIMEDOUT; }
+    __nanosleep(ns);
+    ns = ns < 2048 ? ns + (ns >> 1) : ns;
+  }
+  st_relaxed_gpu(&g.known_done[s], sq);
+  const uint32_t lo = (uint32_t)d;
+  const int64_t ret = lo == GENESYS_RET_IN_SLOT ? (int64_t)ld_relaxed_sys(&g.slots[s].ret) : (int64_t)(int32_t)lo;
+  if (ret < 0) atomicAdd(reinterpret_cast<int *>(&g.status[GENESYS_ST_FAILED_CALLS]), 1);
+  return ret;
+}
+
+__device__ __forceinline__ void slot_release(const genesys_dev &g, uint32_t s) {
+  __threadfence();
+  atomicExch(&g.owner[s], 0u);
+}
+
+/* Whole request by one thread: claim, marshal, publish, optionally wait. */
+__device__ __forceinline__ int64_t single_call(const genesys_dev &g, uint32_t nr, uint32_t flags, bool wait,
+                                               uint64_t a0, uint64_t a1, uint64_t a2, uint64_t a3, uint64_t a4,
+                                               uint64_t a5) {
+  const uint64_t t0 = now_ns();
+  uint32_t s;
+  int64_t rc = slot_claim(g, hw_lane_id(), &s, t0);
+  if (rc < 0) return rc;
+  const uint32_t sq = slot_fill(g, s, nr, flags, a0, a1, a2, a3, a4, a5);
+  __threadfence_system();
+  ring_one(g, s);
+  int64_t ret = 0;
+  if (wait) {
+    ret = slot_wait(g, s, sq, t0);
+    if (ret == -kETIMEDOUT) {  /* the CPU may still finish it: keep the slot's
+                                  sequence so the next claimer waits for it */
+      slot_release(g, s);
+      return ret;
+    }
+  }
+  slot_release(g, s);
+  note_latency(g, t0);
+  return ret;
+}
+
+/* ------------------------------------------------ tickets (prefetching)
+ * A non-blocking call whose result is collected later: the paper's relaxed,
+ * non-blocking prefetching read (Sec. 4.1).  The slot stays owned by the
+ * caller until genesys::wait, so the result cannot be overwritten. */
+struct Ticket {
+  uint32_t slot;
+  uint32_t seq;
+  uint64_t t0;
+};
+
+__device__ __forceinline__ int64_t issue(const genesys_dev &g, Ticket *t, uint32_t nr, uint64_t a0 = 0,
+                                         uint64_t a1 = 0, uint64_t a2 = 0, uint64_t a3 = 0, uint64_t a4 = 0,
+                                         uint64_t a5 = 0) {
+  t->t0 = now_ns();
+  int64_t rc = slot_claim(g, hw_lane_id(), &t->slot, t->t0);
+  if (rc < 0) { t->slot = 0xFFFFFFFFu; return rc; }
+  t->seq = slot_fill(g, t->slot, nr, GENESYS_REQ_TICKET | GENESYS_REQ_RELAXED, a0, a1, a2, a3, a4, a5);
+  __threadfence_system();
+  ring_one(g, t->slot);
+  return 0;
+}
+
+__device__ __forceinline__ int64_t wait(const genesys_dev &g, const Ticket &t) {
+  if (t.slot == 0xFFFFFFFFu) return -kETIMEDOUT;
+  const int64_t ret = slot_wait(g, t.slot, t.seq, now_ns());
+  slot_release(g, t.slot);
+  if (ret != -kETIMEDOUT) note_latency(g, t.t0);
+  return ret;
+}
+
+/* ------------------------------------------------------ group barriers */
+
+/* Grid-wide barrier for cooperative launches (all CTAs co-resident).  Bounded:
+ * returns false (and records -ETIMEDOUT) if the other CTAs do not arrive. */
+__device__ __forceinline__ bool grid_sync(const genesys_dev &g) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {
+    const uint32_t nblocks = gridDim.x * gridDim.y * gridDim.z;
+    uint32_t *count = g.grid_bar, *gen = g.grid_bar + 32;
+    const uint32_t my_gen = ld_acquire_gpu(gen);
+    __threadfence_system();
+    const uint32_t arrived = atomicAdd(count, 1u);
+    int ok = 1;
+    if (arrived == nblocks - 1) {
+      st_relaxed_gpu(count, 0u);
+      st_release_gpu(gen, my_gen + 1u);
+    } else {
+      const uint64_t t0 = now_ns();
+      uint32_t ns = 32;
+      while (ld_acquire_gpu(gen) == my_gen) {
+        if (expired(g, t0)) { note_error(g, -kETIMEDOUT); ok = 0; break; }
+        __nanosleep(ns);
+        ns = ns < 1024 ? ns * 2 : ns;
+      }
+    }
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+template <int G>
+__device__ __forceinline__ void group_barrier(uint32_t warp_mask) {
+  if (G == WARP) __syncwarp(warp_mask);
+  if (G == GROUP) __syncthreads();
+}
+
+__device__ __forceinline__ bool is_block_leader() {
+  return threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0;
+}
+
+/* ------------------------------------------------------------- the call */
+
+template <int G, int O, int B, int R = ROLE_AUTO>
+__device__ __forceinline__ int64_t call_at(const genesys_dev &g, uint32_t site, uint32_t nr, uint64_t a0 = 0,
+                                           uint64_t a1 = 0, uint64_t a2 = 0, uint64_t a3 = 0, uint64_t a4 = 0,
+                                           uint64_t a5 = 0) {
+  static_assert(G != ITEM || O == STRONG, "work-item grain is implicitly strong (Sec. 4.1)");
+  const int role = R == ROLE_AUTO ? role_of(nr) : R;
+  const bool pre = O == STRONG || (role & ROLE_PRODUCER);
+  const bool post = O == STRONG || (role & ROLE_CONSUMER);
+  const uint32_t flags = (B == BLOCKING ? GENESYS_REQ_BLOCKING : 0u) | ((uint32_t)G << GENESYS_REQ_GRAN_SHIFT) |
+                         (O == RELAXED ? GENESYS_REQ_RELAXED : 0u);
+
+  if (G == ITEM) {
+    /* every calling lane is a caller; lanes of a warp that call together
+     * share one doorbell atomic per ring */
+    const uint32_t active = __activemask();
+    const uint64_t t0 = now_ns();
+    uint32_t s = 0;
+    int64_t rc = slot_claim(g, hw_lane_id(), &s, t0);
+    const bool ok = rc == 0;
+    uint32_t sq = 0;
+    if (ok) sq = slot_fill(g, s, nr, flags, a0, a1, a2, a3, a4, a5);
+    __threadfence_system();
+    const uint32_t okmask = __ballot_sync(active, ok);
+    if (ok) {
+      ring_warp(g, okmask, s);
+      if (B == BLOCKING) {
+        rc = slot_wait(g, s, sq, t0);
+      }
+      slot_release(g, s);
+      if (rc != -kETIMEDOUT) note_latency(g, t0);
+    }
+    return rc;
+  }
+
+  if (G == WARP || G == GROUP) {
+    const uint32_t active = G == WARP ? __activemask() : 0xFFFFFFFFu;
+    const bool leader = G == WARP ? lane_id() == (uint32_t)(__ffs(active) - 1) : is_block_leader();
+    if (pre) group_barrier<G>(active);
+    int64_t ret = 0;
+    if (leader) ret = single_call(g, nr, flags, B == BLOCKING, a0, a1, a2, a3, a4, a5);
+    if (!post) return ret;            /* relaxed producer: only the caller waited */
+    if (G == WARP) {
+      __syncwarp(active);
+      return __shfl_sync(active, ret, __ffs(active) - 1);
+    }
+    __shared__ int64_t ret_s;
+    if (leader) ret_s = ret;
+    __syncthreads();
+    ret = ret_s;
+    __syncthreads();                  /* ret_s may be rewritten by the next call */
+    return ret;
+  }
+
+  /* KERNEL grain: one caller for the whole grid. */
+  genesys_ksite *ks = g.ksite + (site % GENESYS_KSITES);
+  const uint32_t nblocks = gridDim.x * gridDim.y * gridDim.z;
+  __shared__ int64_t kret_s;
+  if (pre && post) {
+    /* strong: grid barriers before and after (cooperative launch only) */
+    if (!grid_sync(g)) return -kETIMEDOUT;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && is_block_leader()) {
+      const int64_t r = single_call(g, nr, flags, B == BLOCKING, a0, a1, a2, a3, a4, a5);
+      ks->ret = r;
+    }
+    if (!grid_sync(g)) return -kETIMEDOUT;
+    return *(volatile int64_t *)&ks->ret;
+  }
+  if (pre) {
+    /* relaxed producer: every CTA arrives; the last one to arrive calls, so no
+     * CTA ever waits for another (no deadlock whatever the grid size) */
+    __syncthreads();
+    int64_t r = 0;
+    if (is_block_leader()) {
+      __threadfence_system();
+      const uint32_t arrived = atomicAdd(&ks->arrive, 1u);
+      if (arrived == nblocks - 1) {
+        __threadfence_system();
+        r = single_call(g, nr, flags, B == BLOCKING, a0, a1, a2, a3, a4, a5);
+      }
+    }
+    return r;
+  }
+  /* relaxed consumer: the first CTA to arrive calls; the others wait for its
+   * result (the caller is resident by construction, so they cannot deadlock) */
+  if (is_block_leader()) {
+    int64_t r;
+    if (atomicAdd(&ks->ticket, 1u) == 0u) {
+      r = single_call(g, nr, flags, B == BLOCKING, a0, a1, a2, a3, a4, a5);
+      ks->ret = r;
+      __threadfence();
+      st_release_gpu(&ks->flag, 1u);
+    } else {
+      const uint64_t t0 = now_ns();
+      uint32_t ns = 64;
+      r = 0;
+      while (ld_acquire_gpu(&ks->flag) == 0u) {
+        if (expired(g, t0)) { note_error(g, -kETIMEDOUT); r = -kETIMEDOUT; break; }
+        __nanosleep(ns);
+        ns = ns < 2048 ? ns * 2 : ns;
+      }
+      if (r == 0) r = *(volatile int64_t *)&ks->ret;
+    }
+    kret_s = r;
+  }
+  __syncthreads();
+  const int64_t r = kret_s;
+  __syncthreads();
+  return r;
+}
+
+/* Warp grain with request coalescing.  Every active lane brings its own
+ * positional transfer (pread/pwrite-like: fd, buf, len, off).  Lanes are
+ * grouped by fd with __match_any_sync; within a group, lanes whose buffer and
+ * file range continue the previous lane's form one run, and the lowest lane of
+ * each run issues a single call covering the run.  Each lane gets the part of
+ * the run's result that covers its own range - what its own call would have
+ * returned.  Ordering and blocking as for call<WARP, O, B>. */
+template <int O, int B>
+__device__ __forceinline__ int64_t call_warp_coalesced(const genesys_dev &g, uint32_t nr, int fd, uint64_t buf,
+                                                       uint64_t len, uint64_t off) {
+  const int role = role_of(nr);
+  const bool pre = O == STRONG || (role & ROLE_PRODUCER);
+  const bool post = O == STRONG || (role & ROLE_CONSUMER);
+  const uint32_t flags = (B == BLOCKING ? GENESYS_REQ_BLOCKING : 0u) | (GENESYS_GRAN_WARP << GENESYS_REQ_GRAN_SHIFT) |
+                         (O == RELAXED ? GENESYS_REQ_RELAXED : 0u);
+  const uint32_t active = __activemask();
+  const uint32_t lane = lane_id();
+  if (pre) __syncwarp(active);
+  const uint32_t peers = __match_any_sync(active, fd);
+  const uint32_t below = peers & ((1u << lane) - 1u);
+  const int prev = below ? 31 - __clz(below) : (int)lane;
+  const uint64_t pbuf_end = __shfl_sync(peers, buf + len, prev);
+  const uint64_t poff_end = __shfl_sync(peers, off + len, prev);
+  const bool starts_run = below == 0 || pbuf_end != buf || poff_end != off;
+  const uint32_t starts = __ballot_sync(peers, starts_run);
+  /* my run's leader: the highest run start at or below me */
+  const uint32_t at_or_below = starts & ((2u << lane) - 1u);
+  const int leader = 31 - __clz(at_or_below);
+  /* my run's last lane: the highest peer below the next run start above me */
+  const uint32_t above = peers & ~((2u << lane) - 1u);
+  const uint32_t next_start = starts & above;
+  const uint32_t limit = next_start ? ((1u << (__ffs(next_start) - 1)) - 1u) : 0xFFFFFFFFu;
+  const int last = 31 - __clz(peers & limit);
+  const uint64_t run_end = __shfl_sync(peers, off + len, last);
+  const uint64_t run_off = __shfl_sync(peers, off, leader);
+  int64_t ret = 0;
+  if ((int)lane == leader) ret = single_call(g, nr, flags, B == BLOCKING, (uint64_t)fd, buf, run_end - off, off, 0, 0);
+  if (!post && B == NONBLOCKING) return 0;
+  if (post) __syncwarp(active);
+  if (!post) {
+    /* relaxed producer, blocking: only the run leaders waited */
+    return (int)lane == leader ? (int64_t)(ret < 0 ? ret : (ret < (int64_t)len ? ret : (int64_t)len)) : 0;
+  }
+  const int64_t run_ret = __shfl_sync(peers, ret, leader);
+  if (run_ret < 0) return run_ret;
+  const uint64_t before = off - run_off;
+  const uint64_t got = (uint64_t)run_ret > before ? (uint64_t)run_ret - before : 0;
+  return (int64_t)(got < len ? got : len);
+}
+
+template <int G, int O, int B, int R = ROLE_AUTO>
+__device__ __forceinline__ int64_t call(const genesys_dev &g, uint32_t nr, uint64_t a0 = 0, uint64_t a1 = 0,
+                                        uint64_t a2 = 0, uint64_t a3 = 0, uint64_t a4 = 0, uint64_t a5 = 0) {
+  return call_at<G, O, B, R>(g, 0u, nr, a0, a1, a2, a3, a4, a5);
+}
+
+}  // namespace genesys
+
+#endif /* GENESYS_DEVICE_CUH */

@@ -1,0 +1,131 @@
+/*
+ * genesys_layout.h - memory layout shared by the device invocation code
+ * (genesys_device.cuh) and the host service runtime.
+ *
+ * The syscall area (Sec. 5, "GPU to CPU communication", Fig. 3) is an array of
+ * 64-byte slots in pinned, host-mapped system memory that both the GPU and
+ * the CPU can reach.  A slot holds the system call number, the request state
+ * and up to six arguments; the argument field is reused for the return value.
+ *
+ * Differences from the paper's layout, forced by a discrete GPU behind PCIe
+ * without host-native atomics (device RMW on host memory is not atomic with
+ * respect to the CPU):
+ *   - every word has exactly one writer.  The request word and arguments are
+ *     written only by the GPU, the completion word only by the CPU, so no
+ *     read-modify-write on host memory is ever needed;
+ *   - the slot state of Fig. 4 is carried by sequence numbers instead of an
+ *     atomically updated state field: a slot is FREE when its completion
+ *     sequence equals its request sequence, READY/PROCESSING while the request
+ *     sequence is ahead, FINISHED once the CPU writes the completion sequence;
+ *   - completion words live in their own dense array, so that one warp polling
+ *     32 neighbouring slots reads 256 contiguous bytes instead of 32 lines;
+ *   - the CPU learns of new requests from doorbell rings (one per service
+ *     thread) instead of an interrupt carrying the wavefront's hardware ID
+ *     (Sec. 3 notes that interrupt versus polling is orthogonal to the design).
+ *
+ * All multi-byte fields are little-endian (x86-64 host, NVIDIA GPU).
+ */
+#ifndef GENESYS_LAYOUT_H
+#define GENESYS_LAYOUT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GENESYS_SLOT_BYTES 64u
+
+/* One request slot, written by the GPU only (Sec. 5, Fig. 3). */
+typedef struct genesys_slot {
+  uint64_t args[6];   /* Linux passes at most six arguments; 16-byte aligned
+                         so the GPU writes them with three vector stores    */
+  /* bits 63..32: request sequence number (1, 2, ... per slot)
+   * bits 31..16: system call number (host SYS_* number, or a GENESYS_NR_* op)
+   * bits 15..0 : GENESYS_REQ_* flags                                        */
+  uint64_t req;
+  uint64_t ret;       /* full 64-bit return value, written by the CPU when it
+                         does not fit in the completion word (see below)     */
+} genesys_slot;
+
+/* Completion word, written by the CPU only:
+ *   bits 63..32: sequence number of the last finished request of the slot
+ *   bits 31..0 : its return value as int32, or GENESYS_RET_IN_SLOT when the
+ *                value does not fit (then the full value is in slot.ret,
+ *                written before the completion word).                      */
+#define GENESYS_RET_IN_SLOT 0x80000000u
+
+/* Request flags (low 16 bits of slot.req). */
+#define GENESYS_REQ_BLOCKING   0x0001u  /* a GPU thread waits for the result          */
+#define GENESYS_REQ_GRAN_SHIFT 1        /* 2 bits: GENESYS_GRAN_*                     */
+#define GENESYS_REQ_RELAXED    0x0008u  /* relaxed ordering (Sec. 4.1)                */
+#define GENESYS_REQ_TICKET     0x0010u  /* non-blocking call whose result is collected
+                                           later with genesys_wait (slot stays owned) */
+
+/* Invocation granularities (Sec. 4.1), plus the warp grain of this design. */
+#define GENESYS_GRAN_ITEM   0u
+#define GENESYS_GRAN_WARP   1u
+#define GENESYS_GRAN_GROUP  2u
+#define GENESYS_GRAN_KERNEL 3u
+
+/* Operations that are not Linux system calls (numbers above any SYS_*). */
+#define GENESYS_NR_NOP            0x7F00u  /* returns args[0]; measures the protocol alone   */
+#define GENESYS_NR_CHECK_VISIBLE  0x7F01u  /* args: ptr, count, seed -> number of u64 words
+                                              in [ptr, ptr+count) that differ from
+                                              splitmix64_at(seed, i); the strong-ordering
+                                              visibility probe                            */
+#define GENESYS_NR_PREAD_DEV      0x7F02u  /* pread into device memory: args fd, dev_ptr,
+                                              len, off; the host reads into its own
+                                              bounce buffer and copies it to the GPU      */
+
+/* Doorbell ring entry: bits 63..32 = ring position + 1, bits 31..0 = slot. */
+#define GENESYS_RING_ENTRY(pos, slot) ((((uint64_t)(uint32_t)((pos) + 1u)) << 32) | (uint64_t)(uint32_t)(slot))
+
+/* Kernel-grain call sites per launch (GENESYS_GRAN_KERNEL). */
+#define GENESYS_KSITES 64u
+
+/* Device status words (int32 each), in device memory. */
+#define GENESYS_ST_FIRST_ERROR   0   /* first negative code seen by any device wait    */
+#define GENESYS_ST_TIMEOUTS      1   /* device waits that gave up (deadline)           */
+#define GENESYS_ST_FAILED_CALLS  2   /* calls that returned a negative value           */
+#define GENESYS_ST_BAD_ARGS      3   /* device-side argument checks that failed        */
+#define GENESYS_ST_WORDS         8
+
+/* Per-kernel-grain-site state in device memory, reset before each launch. */
+typedef struct genesys_ksite {
+  uint32_t arrive;    /* CTAs that reached the call                              */
+  uint32_t ticket;    /* first-arriver election (consumer role)                  */
+  uint32_t flag;      /* set to 1 when the result is available                   */
+  uint32_t pad;
+  int64_t ret;
+  uint64_t pad2;
+} genesys_ksite;
+
+/* The device view of a context: a plain struct passed to kernels by value. */
+typedef struct genesys_dev {
+  genesys_slot *slots;        /* host-mapped, n_slots entries                       */
+  uint64_t *done;             /* host-mapped, n_slots completion words              */
+  uint64_t *rings;            /* host-mapped, n_rings * ring_cap doorbell entries   */
+  uint32_t *owner;            /* device memory: slot claim locks                    */
+  uint32_t *seq;              /* device memory: last published sequence per slot    */
+  uint32_t *known_done;       /* device memory: last sequence seen finished         */
+  uint32_t *ring_tail;        /* device memory: producer positions, stride 32 words */
+  genesys_ksite *ksite;       /* device memory: GENESYS_KSITES entries              */
+  uint32_t *grid_bar;         /* device memory: {count, generation}                 */
+  int32_t *status;            /* device memory: GENESYS_ST_WORDS                    */
+  uint64_t *lat;              /* device memory: per-call latency samples (ns)       */
+  uint32_t *lat_count;        /* device memory: samples written (may exceed cap)    */
+  uint32_t lat_cap;
+  uint32_t n_slots;
+  uint32_t n_rings;
+  uint32_t ring_mask;         /* ring_cap - 1, ring_cap a power of two              */
+  uint64_t deadline_ns;       /* every device wait gives up after this long         */
+  uint32_t n_sms;
+  uint32_t reserved;
+} genesys_dev;
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GENESYS_LAYOUT_H */

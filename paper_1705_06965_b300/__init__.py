@@ -1,0 +1,263 @@
+"""Python binding of the B300 GPU system-call runtime (libgenesys.so).
+
+Argument marshalling only: every step of the path - the device-side
+invocation protocol, the CPU service threads and the scan kernels - runs in
+libgenesys.so (C++ and sm_103a CUDA).  PyTorch is used for device memory and
+streams.  The library must have been built (``__graft_entry__.build()`` or
+``python -m paper_1705_06965_b300.build``); importing this package without it
+raises, there is no fallback.
+
+Paper: Vesely et al., "GPU System Calls" (GENESYS), arXiv 1705.06965.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgenesys.so")
+
+# x86-64 system call numbers (<asm/unistd_64.h>)
+SYS_read, SYS_write, SYS_close, SYS_mmap, SYS_munmap = 0, 1, 3, 9, 11
+SYS_pread64, SYS_pwrite64, SYS_getpid = 17, 18, 39
+SYS_sendto, SYS_recvfrom, SYS_recvmmsg, SYS_sendmmsg = 44, 45, 299, 307
+NR_NOP, NR_CHECK_VISIBLE, NR_PREAD_DEV = 0x7F00, 0x7F01, 0x7F02
+
+GRAN_ITEM, GRAN_WARP, GRAN_GROUP, GRAN_KERNEL = 0, 1, 2, 3
+GRAN_NAMES = {GRAN_ITEM: "work-item", GRAN_WARP: "warp", GRAN_GROUP: "work-group", GRAN_KERNEL: "kernel"}
+REQ_BLOCKING, REQ_RELAXED, REQ_TICKET = 0x1, 0x8, 0x10
+INIT_HOST_ONLY, INIT_NO_THREADS, INIT_ANY_SYSCALL = 0x1, 0x2, 0x4
+FORM_PLAIN, FORM_BATCHED = 0, 1
+ST_FIRST_ERROR, ST_TIMEOUTS, ST_FAILED_CALLS, ST_BAD_ARGS, ST_WORDS = 0, 1, 2, 3, 8
+
+EINVAL, ENOMEM, ETIMEDOUT, ENODEV, EDEVICE, ECUDA = -22, -12, -110, -19, -1001, -1000
+
+# every entry point declared in include/genesys.h
+EXPORTS = [
+    "genesys_config_default", "genesys_init", "genesys_shutdown", "genesys_device_view", "genesys_launch",
+    "genesys_service", "genesys_drain", "genesys_stats_get", "genesys_stats_reset", "genesys_status",
+    "genesys_latency", "genesys_staging", "genesys_staging_reset", "genesys_last_error", "genesys_emulate_call",
+    "genesys_c1_histogram", "genesys_c2_pwrite", "genesys_visibility_probe",
+]
+
+
+class GenesysError(RuntimeError):
+    def __init__(self, code: int, what: str, msg: str):
+        super().__init__(f"{what} failed ({code}): {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("n_slots", ctypes.c_uint32), ("n_service_threads", ctypes.c_uint32),
+        ("service_cpus", ctypes.POINTER(ctypes.c_int32)), ("staging_bytes", ctypes.c_uint64),
+        ("coalesce_window_ns", ctypes.c_uint64), ("coalesce_max", ctypes.c_uint32), ("merge", ctypes.c_uint32),
+        ("device_deadline_ns", ctypes.c_uint64), ("lat_samples", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+        ("idle_spin_ns", ctypes.c_uint64),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in
+                ("requests", "os_calls", "failed", "nonblocking_failed", "bytes", "batches", "busy_ns")] + [
+        ("by_op", ctypes.c_uint64 * 8)]
+
+    OPS = ("pread", "pwrite", "sendto", "recvfrom", "mmap", "munmap", "internal", "other")
+
+    def as_dict(self) -> dict:
+        d = {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "by_op"}
+        d["by_op"] = {k: int(v) for k, v in zip(self.OPS, self.by_op)}
+        return d
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libgenesys.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1705_06965_b300.build` "
+                          "(the GPU path has no fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, u32, u64, i32, i64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "genesys_config_default": (ctypes.c_int, [ctypes.POINTER(Config)]),
+        "genesys_init": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(vp)]),
+        "genesys_shutdown": (ctypes.c_int, [vp]),
+        "genesys_device_view": (ctypes.c_int, [vp, vp]),
+        "genesys_launch": (ctypes.c_int, [vp, vp, ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.c_size_t,
+                                          ctypes.POINTER(vp), u32, vp]),
+        "genesys_service": (ctypes.c_int, [vp, u64]),
+        "genesys_drain": (ctypes.c_int, [vp, u64]),
+        "genesys_stats_get": (ctypes.c_int, [vp, ctypes.POINTER(Stats)]),
+        "genesys_stats_reset": (ctypes.c_int, [vp]),
+        "genesys_status": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.c_int]),
+        "genesys_latency": (ctypes.c_int, [vp, ctypes.POINTER(u64), u32, ctypes.POINTER(u32), ctypes.c_int]),
+        "genesys_staging": (vp, [vp, ctypes.c_size_t]),
+        "genesys_staging_reset": (ctypes.c_int, [vp]),
+        "genesys_last_error": (ctypes.c_char_p, []),
+        "genesys_emulate_call": (ctypes.c_int, [vp, u32, ctypes.POINTER(u64), u32, ctypes.POINTER(i64)]),
+        "genesys_c1_histogram": (ctypes.c_int, [vp, ctypes.c_int, u64, u64, u32, u32, u32, vp, u64, vp, vp]),
+        "genesys_c2_pwrite": (ctypes.c_int, [vp, ctypes.c_int, u64, u32, u32, u32, u32, u64, vp, u64, vp]),
+        "genesys_visibility_probe": (ctypes.c_int, [vp, u64, u32, u32, u32, u64, vp, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype, f.argtypes = res, args
+    _lib = L
+    return L
+
+
+def last_error() -> str:
+    m = lib().genesys_last_error()
+    return m.decode(errors="replace") if m else ""
+
+
+def _check(rc: int, what: str) -> int:
+    if rc < 0:
+        raise GenesysError(rc, what, last_error())
+    return rc
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream or None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+class Context:
+    """A GENESYS context: syscall area, doorbell rings, staging arena and CPU
+    service threads (genesys_init / genesys_shutdown)."""
+
+    def __init__(self, device: int = 0, n_slots: int = 0, service_threads: int = 4,
+                 staging_bytes: int = 256 << 20, coalesce_window_ns: int = 0, coalesce_max: int = 64,
+                 merge: bool = True, deadline_ns: int = 2_000_000_000, lat_samples: int = 1 << 20,
+                 host_only: bool = False, no_threads: bool = False, any_syscall: bool = False,
+                 idle_spin_ns: int = 200_000_000, service_cpus=None):
+        L = lib()
+        cfg = Config()
+        _check(L.genesys_config_default(ctypes.byref(cfg)), "genesys_config_default")
+        cfg.n_slots = n_slots
+        cfg.n_service_threads = service_threads
+        self._cpus = None
+        if service_cpus is not None:
+            self._cpus = (ctypes.c_int32 * len(service_cpus))(*service_cpus)
+            cfg.service_cpus = ctypes.cast(self._cpus, ctypes.POINTER(ctypes.c_int32))
+        cfg.staging_bytes = staging_bytes
+        cfg.coalesce_window_ns = coalesce_window_ns
+        cfg.coalesce_max = coalesce_max
+        cfg.merge = 1 if merge else 0
+        cfg.device_deadline_ns = int(deadline_ns)
+        cfg.lat_samples = lat_samples
+        cfg.idle_spin_ns = int(idle_spin_ns)
+        cfg.flags = (INIT_HOST_ONLY if host_only else 0) | (INIT_NO_THREADS if no_threads else 0) | (
+            INIT_ANY_SYSCALL if any_syscall else 0)
+        self.config = cfg
+        self.host_only = host_only
+        self.device = device
+        h = ctypes.c_void_p()
+        _check(L.genesys_init(ctypes.byref(cfg), device, ctypes.byref(h)), "genesys_init")
+        self._h = h
+
+    # -- lifetime
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("context is shut down")
+        return self._h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            h, self._h = self._h, None
+            _check(lib().genesys_shutdown(h), "genesys_shutdown")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- staging arena (pinned, host-mapped: one address valid on both sides)
+    def staging(self, nbytes: int) -> int:
+        p = lib().genesys_staging(self.handle, nbytes)
+        if not p:
+            raise GenesysError(ENOMEM, "genesys_staging", last_error())
+        return int(p)
+
+    def staging_reset(self) -> None:
+        _check(lib().genesys_staging_reset(self.handle), "genesys_staging_reset")
+
+    @staticmethod
+    def host_view(addr: int, nbytes: int, dtype=np.uint8) -> np.ndarray:
+        """numpy view (host side) of staging memory at `addr`."""
+        buf = (ctypes.c_uint8 * nbytes).from_address(addr)
+        return np.frombuffer(buf, dtype=dtype)
+
+    # -- service side
+    def drain(self, timeout_ns: int = 10_000_000_000) -> None:
+        _check(lib().genesys_drain(self.handle, timeout_ns), "genesys_drain")
+
+    def service(self, timeout_ns: int) -> int:
+        return _check(lib().genesys_service(self.handle, timeout_ns), "genesys_service")
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().genesys_stats_get(self.handle, ctypes.byref(s)), "genesys_stats_get")
+        return s.as_dict()
+
+    def stats_reset(self) -> None:
+        _check(lib().genesys_stats_reset(self.handle), "genesys_stats_reset")
+
+    def status(self, clear: bool = True) -> list:
+        out = (ctypes.c_int32 * ST_WORDS)()
+        _check(lib().genesys_status(self.handle, out, 1 if clear else 0), "genesys_status")
+        return list(out)
+
+    def latency(self, clear: bool = True, cap: Optional[int] = None) -> np.ndarray:
+        cap = self.config.lat_samples if cap is None else cap
+        out = np.zeros(max(cap, 1), np.uint64)
+        n = ctypes.c_uint32()
+        _check(lib().genesys_latency(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), cap,
+                                     ctypes.byref(n), 1 if clear else 0), "genesys_latency")
+        return out[:min(n.value, cap)]
+
+    def emulate_call(self, nr: int, args=(), flags: int = REQ_BLOCKING) -> int:
+        a = (ctypes.c_uint64 * 6)(*[int(x) & ((1 << 64) - 1) for x in list(args) + [0] * (6 - len(args))])
+        r = ctypes.c_int64()
+        _check(lib().genesys_emulate_call(self.handle, nr, a, flags, ctypes.byref(r)), "genesys_emulate_call")
+        return r.value
+
+    # -- workloads
+    def c1_histogram(self, fd: int, file_bytes: int, hist_dev_ptr: int, staging: int, staging_bytes: int,
+                     chunk: int = 4096, groups: int = 64, threads: int = 256, form: int = FORM_PLAIN,
+                     stream=None) -> None:
+        _check(lib().genesys_c1_histogram(self.handle, fd, file_bytes, chunk, groups, threads, form, staging,
+                                          staging_bytes, hist_dev_ptr, _stream_handle(stream)),
+               "genesys_c1_histogram")
+
+    def c2_pwrite(self, fd: int, n_threads: int, gran: int, group_threads: int, relaxed: bool, nonblocking: bool,
+                  seed: int, staging: int, staging_bytes: int, stream=None) -> None:
+        _check(lib().genesys_c2_pwrite(self.handle, fd, n_threads, gran, group_threads, 1 if relaxed else 0,
+                                       1 if nonblocking else 0, seed, staging, staging_bytes,
+                                       _stream_handle(stream)), "genesys_c2_pwrite")
+
+    def visibility_probe(self, n_threads: int, gran: int, group_threads: int, relaxed: bool, seed: int,
+                         probe: int, violations_dev_ptr: int, stream=None) -> None:
+        _check(lib().genesys_visibility_probe(self.handle, n_threads, gran, group_threads, 1 if relaxed else 0,
+                                              seed, probe, violations_dev_ptr, _stream_handle(stream)),
+               "genesys_visibility_probe")

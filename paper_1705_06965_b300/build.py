@@ -1,0 +1,58 @@
+"""Build libgenesys.so (runtime + sm_103a kernels) in-tree with nvcc.
+
+    python -m paper_1705_06965_b300.build
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+LIB = os.path.join(PKG, "libgenesys.so")
+
+SOURCES = ["runtime.cpp", "workloads.cu"]
+HEADERS = [os.path.join(INCLUDE, h) for h in ("genesys.h", "genesys_layout.h", "genesys_device.cuh")] + [
+    os.path.join(CSRC, "internal.h")]
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def nvcc() -> str:
+    for p in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if p and (os.path.isabs(p) and os.path.exists(p) or not os.path.isabs(p)):
+            return p
+    return "nvcc"
+
+
+def command(out: str = LIB, extra: list[str] | None = None) -> list[str]:
+    srcs = [os.path.join(CSRC, s) for s in SOURCES]
+    return [nvcc(), *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
+            "-shared", "-cudart", "shared", f"-I{INCLUDE}", f"-I{CSRC}", "-o", out, *srcs, "-lpthread",
+            *(extra or [])]
+
+
+def stale() -> bool:
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    deps = [os.path.join(CSRC, s) for s in SOURCES] + HEADERS
+    return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    if force or stale():
+        cmd = command(extra=["-Xptxas", "-v"] if verbose else None)
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
+        if verbose:
+            print(r.stdout + r.stderr)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

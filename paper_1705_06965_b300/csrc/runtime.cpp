@@ -1,0 +1,889 @@
+// Host side of GPU system calls: context, syscall area, doorbell rings and the
+// CPU service threads that carry out the GPU's requests.
+//
+// Paper: Vesely et al., "GPU System Calls", arXiv 1705.06965.
+//   Sec. 5 "CPU-side system call processing": a CPU worker scans the syscall
+//   area for ready requests, marks them as processing, executes the call and
+//   writes the result back (Fig. 4); coalescing batches several requests into
+//   one unit of work, bounded by a time window and a maximum count (Sec. 4.2).
+//   Sec. 8.3: a host function waits until all GPU calls have completed.
+//
+// B300 design (x86-64 host, PCIe Gen6, no host-native atomics): the service
+// threads are user-mode pollers (the model of the paper's related work, Sec. 9;
+// Sec. 3 calls interrupt vs polling orthogonal).  Each owns one doorbell ring
+// that GPU callers append slot numbers to, so a thread reads only the slots
+// that have work instead of scanning the whole syscall area.
+#include <cuda_runtime.h>
+#include <errno.h>
+#include <fcntl.h>
+#include <pthread.h>
+#include <sched.h>
+#include <string.h>
+#include <sys/mman.h>
+#include <sys/socket.h>
+#include <sys/syscall.h>
+#include <sys/uio.h>
+#include <time.h>
+#include <unistd.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <atomic>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "genesys.h"
+#include "internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (expr);                                                                 \
+    if (e_ != cudaSuccess) return fail(GENESYS_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+inline uint64_t mono_ns() {
+  timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
+}
+
+inline void cpu_relax() { __builtin_ia32_pause(); }
+
+inline uint64_t next_pow2(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// splitmix64 output function (Steele, Lea & Flood 2014), counter-based:
+// value i of the generator started at `seed`.  Used only by the visibility
+// probe op, which checks GPU stores of this pattern.
+inline uint64_t sm64_at(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+enum OpIdx { OP_PREAD = 0, OP_PWRITE, OP_SENDTO, OP_RECVFROM, OP_MMAP, OP_MUNMAP, OP_INTERNAL, OP_OTHER };
+
+struct alignas(64) Counters {
+  std::atomic<uint64_t> requests{0}, os_calls{0}, failed{0}, nb_failed{0}, bytes{0}, batches{0}, busy_ns{0};
+  std::atomic<uint64_t> by_op[8] = {};
+};
+
+struct Request {
+  uint32_t slot, seq, nr, flags;
+  uint64_t a[6];
+  int64_t ret;
+};
+
+}  // namespace
+
+struct genesys_ctx {
+  genesys_config cfg{};
+  int device = -1;
+  bool host_only = false;
+  uint32_t n_sms = 0;
+
+  // host-mapped (or plain host memory in host-only mode)
+  genesys_slot *slots = nullptr;
+  uint64_t *done = nullptr;
+  uint64_t *rings = nullptr;
+  uint32_t ring_cap = 0;
+  uint8_t *staging = nullptr;
+  std::atomic<uint64_t> staging_used{0};
+
+  // device-side state (device memory; host memory in host-only mode)
+  uint32_t *owner = nullptr, *seq = nullptr, *known_done = nullptr, *ring_tail = nullptr;
+  genesys_ksite *ksite = nullptr;
+  uint32_t *grid_bar = nullptr;
+  int32_t *status = nullptr;
+  uint64_t *lat = nullptr;
+  uint32_t *lat_count = nullptr;
+
+  // service side
+  std::vector<std::thread> threads;
+  std::atomic<bool> stop{false};
+  std::vector<uint64_t> head;                       // per ring, touched by its thread only
+  std::unique_ptr<std::atomic<uint64_t>[]> retired;  // per ring: positions fully processed
+  std::unique_ptr<Counters[]> counters;             // per ring
+  std::mutex svc_mu;                                // NO_THREADS mode: one caller at a time
+
+  // mmap'd regions registered for device access (for munmap)
+  std::mutex map_mu;
+  std::unordered_map<uintptr_t, std::pair<void *, size_t>> maps;  // device address -> host mapping
+
+  cudaStream_t aux = nullptr;  // private stream for small copies
+};
+
+namespace {
+
+// -------------------------------------------------------------- requests
+
+void complete(genesys_ctx *c, const Request &r, Counters &k) {
+  const bool fits = r.ret >= INT32_MIN + 1 && r.ret <= INT32_MAX;
+  uint64_t word = (uint64_t)r.seq << 32;
+  if (fits) {
+    word |= (uint32_t)(int32_t)r.ret;
+  } else {
+    __atomic_store_n(&c->slots[r.slot].ret, (uint64_t)r.ret, __ATOMIC_RELAXED);
+    word |= GENESYS_RET_IN_SLOT;
+  }
+  if (r.ret < 0) {
+    k.failed.fetch_add(1, std::memory_order_relaxed);
+    if (!(r.flags & GENESYS_REQ_BLOCKING) && !(r.flags & GENESYS_REQ_TICKET))
+      k.nb_failed.fetch_add(1, std::memory_order_relaxed);
+  }
+  __atomic_store_n(&c->done[r.slot], word, __ATOMIC_RELEASE);
+}
+
+int op_index(uint32_t nr) {
+  switch (nr) {
+    case SYS_pread64: return OP_PREAD;
+    case SYS_pwrite64: return OP_PWRITE;
+    case SYS_sendto: case SYS_sendmmsg: return OP_SENDTO;
+    case SYS_recvfrom: case SYS_recvmmsg: return OP_RECVFROM;
+    case SYS_mmap: return OP_MMAP;
+    case SYS_munmap: return OP_MUNMAP;
+    default: return nr >= 0x7F00u ? OP_INTERNAL : OP_OTHER;
+  }
+}
+
+bool allowed(const genesys_ctx *c, uint32_t nr) {
+  if (c->cfg.flags & GENESYS_INIT_ANY_SYSCALL) return true;
+  switch (nr) {
+    case SYS_read: case SYS_write: case SYS_pread64: case SYS_pwrite64: case SYS_open: case SYS_openat:
+    case SYS_close: case SYS_lseek: case SYS_sendto: case SYS_recvfrom: case SYS_sendmmsg:
+    case SYS_recvmmsg: case SYS_madvise: case SYS_getpid: case SYS_fsync:
+      return true;
+    default:
+      return false;
+  }
+}
+
+inline int64_t sys_ret(long r) { return r < 0 ? -(int64_t)errno : (int64_t)r; }
+
+// mmap from the GPU: map on the host, then register the range for device access.
+int64_t do_mmap(genesys_ctx *c, const uint64_t *a) {
+  void *p = mmap((void *)a[0], (size_t)a[1], (int)a[2], (int)a[3], (int)a[4], (off_t)a[5]);
+  if (p == MAP_FAILED) return -(int64_t)errno;
+  uintptr_t dev = (uintptr_t)p;
+  if (!c->host_only) {
+    if (cudaHostRegister(p, (size_t)a[1], cudaHostRegisterMapped | cudaHostRegisterPortable) != cudaSuccess) {
+      cudaGetLastError();
+      munmap(p, (size_t)a[1]);
+      return -ENOMEM;
+    }
+    void *d = nullptr;
+    if (cudaHostGetDevicePointer(&d, p, 0) != cudaSuccess) {
+      cudaGetLastError();
+      cudaHostUnregister(p);
+      munmap(p, (size_t)a[1]);
+      return -ENOMEM;
+    }
+    dev = (uintptr_t)d;
+  }
+  std::lock_guard<std::mutex> g(c->map_mu);
+  c->maps[dev] = {p, (size_t)a[1]};
+  return (int64_t)dev;
+}
+
+int64_t do_munmap(genesys_ctx *c, const uint64_t *a) {
+  void *host = nullptr;
+  size_t len = 0;
+  {
+    std::lock_guard<std::mutex> g(c->map_mu);
+    auto it = c->maps.find((uintptr_t)a[0]);
+    if (it == c->maps.end()) return -EINVAL;  // only GPU-made mappings
+    host = it->second.first;
+    len = it->second.second;
+    if ((size_t)a[1] != len) return -EINVAL;   // whole mappings only
+    c->maps.erase(it);
+  }
+  if (!c->host_only && cudaHostUnregister(host) != cudaSuccess) cudaGetLastError();
+  return munmap(host, len) == 0 ? 0 : -(int64_t)errno;
+}
+
+// pread into device memory through a pinned bounce buffer and a DMA copy.
+struct Bounce {
+  uint8_t *buf = nullptr;
+  size_t cap = 0;
+  cudaStream_t stream = nullptr;
+};
+
+int64_t do_pread_dev(genesys_ctx *c, Bounce &b, const uint64_t *a) {
+  if (c->host_only) return -ENOSYS;
+  if (!b.buf) {
+    b.cap = 8u << 20;
+    if (cudaHostAlloc((void **)&b.buf, b.cap, cudaHostAllocPortable) != cudaSuccess) {
+      cudaGetLastError();
+      b.buf = nullptr;
+      return -ENOMEM;
+    }
+    if (cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return -ENOMEM;
+    }
+  }
+  const int fd = (int)a[0];
+  uint8_t *dst = (uint8_t *)a[1];
+  const uint64_t len = a[2], off = a[3];
+  uint64_t got = 0;
+  while (got < len) {
+    const size_t want = (size_t)std::min<uint64_t>(b.cap, len - got);
+    ssize_t r = pread(fd, b.buf, want, (off_t)(off + got));
+    if (r < 0) {
+      if (errno == EINTR) continue;
+      if (got == 0) return -(int64_t)errno;
+      break;
+    }
+    if (r == 0) break;
+    if (cudaMemcpyAsync(dst + got, b.buf, (size_t)r, cudaMemcpyHostToDevice, b.stream) != cudaSuccess ||
+        cudaStreamSynchronize(b.stream) != cudaSuccess) {
+      cudaGetLastError();
+      return -EIO;
+    }
+    got += (uint64_t)r;
+  }
+  return (int64_t)got;
+}
+
+int64_t execute_one(genesys_ctx *c, Bounce &b, Request &r, Counters &k) {
+  const uint64_t *a = r.a;
+  k.os_calls.fetch_add(1, std::memory_order_relaxed);
+  switch (r.nr) {
+    case GENESYS_NR_NOP:
+      k.os_calls.fetch_sub(1, std::memory_order_relaxed);
+      return (int64_t)a[0];
+    case GENESYS_NR_CHECK_VISIBLE: {
+      k.os_calls.fetch_sub(1, std::memory_order_relaxed);
+      const volatile uint64_t *p = (const volatile uint64_t *)a[0];
+      int64_t bad = 0;
+      for (uint64_t i = 0; i < a[1]; ++i) bad += p[i] != sm64_at(a[2], a[3] + i);
+      return bad;
+    }
+    case GENESYS_NR_PREAD_DEV:
+      return do_pread_dev(c, b, a);
+    case SYS_mmap:
+      return do_mmap(c, a);
+    case SYS_munmap:
+      return do_munmap(c, a);
+    default:
+      if (!allowed(c, r.nr)) return -ENOSYS;
+      return sys_ret(syscall((long)r.nr, a[0], a[1], a[2], a[3], a[4], a[5]));
+  }
+}
+
+// Merge a run of pread/pwrite requests that continue each other in the file
+// (same fd, offset of each = offset + length of the previous) into one Linux
+// call.  Contiguous buffers become one pread/pwrite, others one
+// preadv/pwritev.  Each request then receives the part of the merged result
+// that covers its own range - the value its own call would have returned.
+size_t merge_run(genesys_ctx *c, Request *reqs, size_t i, size_t n, Counters &k) {
+  const uint32_t nr = reqs[i].nr;
+  const int fd = (int)reqs[i].a[0];
+  size_t j = i + 1;
+  bool contiguous_buf = true;
+  while (j < n && j - i < IOV_MAX && reqs[j].nr == nr && (int)reqs[j].a[0] == fd &&
+         reqs[j].a[3] == reqs[j - 1].a[3] + reqs[j - 1].a[2]) {
+    if (reqs[j].a[1] != reqs[j - 1].a[1] + reqs[j - 1].a[2]) contiguous_buf = false;
+    ++j;
+  }
+  const size_t m = j - i;
+  const uint64_t off = reqs[i].a[3];
+  uint64_t total = 0;
+  for (size_t t = i; t < j; ++t) total += reqs[t].a[2];
+  int64_t res;
+  k.os_calls.fetch_add(1, std::memory_order_relaxed);
+  if (m == 1 || contiguous_buf) {
+    void *buf = (void *)reqs[i].a[1];
+    long r = nr == SYS_pread64 ? pread(fd, buf, total, (off_t)off) : pwrite(fd, buf, total, (off_t)off);
+    res = sys_ret(r);
+  } else {
+    iovec iov[IOV_MAX];
+    for (size_t t = 0; t < m; ++t) iov[t] = {(void *)reqs[i + t].a[1], (size_t)reqs[i + t].a[2]};
+    long r = nr == SYS_pread64 ? preadv(fd, iov, (int)m, (off_t)off) : pwritev(fd, iov, (int)m, (off_t)off);
+    res = sys_ret(r);
+  }
+  uint64_t prefix = 0;
+  for (size_t t = i; t < j; ++t) {
+    const uint64_t len = reqs[t].a[2];
+    if (res < 0) {
+      reqs[t].ret = res;
+    } else {
+      const uint64_t got = (uint64_t)res > prefix ? (uint64_t)res - prefix : 0;
+      reqs[t].ret = (int64_t)std::min<uint64_t>(got, len);
+    }
+    prefix += len;
+  }
+  if (res > 0) k.bytes.fetch_add((uint64_t)res, std::memory_order_relaxed);
+  return j;
+}
+
+void process_batch(genesys_ctx *c, Bounce &b, Request *reqs, size_t n, Counters &k) {
+  const uint64_t t0 = mono_ns();
+  for (size_t i = 0; i < n;) {
+    Request &r = reqs[i];
+    if (c->cfg.merge && (r.nr == SYS_pread64 || r.nr == SYS_pwrite64)) {
+      i = merge_run(c, reqs, i, n, k);
+      continue;
+    }
+    r.ret = execute_one(c, b, r, k);
+    if (r.ret > 0 && (r.nr == SYS_pread64 || r.nr == SYS_pwrite64 || r.nr == SYS_read || r.nr == SYS_write ||
+                      r.nr == SYS_sendto || r.nr == SYS_recvfrom || r.nr == GENESYS_NR_PREAD_DEV))
+      k.bytes.fetch_add((uint64_t)r.ret, std::memory_order_relaxed);
+    ++i;
+  }
+  for (size_t i = 0; i < n; ++i) {
+    complete(c, reqs[i], k);
+    k.by_op[op_index(reqs[i].nr)].fetch_add(1, std::memory_order_relaxed);
+  }
+  k.requests.fetch_add(n, std::memory_order_relaxed);
+  k.batches.fetch_add(1, std::memory_order_relaxed);
+  k.busy_ns.fetch_add(mono_ns() - t0, std::memory_order_relaxed);
+}
+
+inline bool entry_ready(const uint64_t *ring, uint32_t mask, uint64_t pos, uint32_t *slot) {
+  const uint64_t e = __atomic_load_n(&ring[pos & mask], __ATOMIC_ACQUIRE);
+  if ((uint32_t)(e >> 32) != (uint32_t)(pos + 1)) return false;
+  *slot = (uint32_t)e;
+  return true;
+}
+
+inline void read_request(genesys_ctx *c, uint32_t s, Request *r) {
+  const genesys_slot *sl = &c->slots[s];
+  const uint64_t req = __atomic_load_n(&sl->req, __ATOMIC_ACQUIRE);
+  r->slot = s;
+  r->seq = (uint32_t)(req >> 32);
+  r->nr = (uint32_t)(req >> 16) & 0xFFFFu;
+  r->flags = (uint32_t)req & 0xFFFFu;
+  for (int i = 0; i < 6; ++i) r->a[i] = __atomic_load_n(&sl->args[i], __ATOMIC_RELAXED);
+  r->ret = 0;
+}
+
+// Take up to coalesce_max ready requests from ring `ri` and process them as one
+// batch (Sec. 4.2).  Returns the number processed.
+size_t poll_ring(genesys_ctx *c, uint32_t ri, std::vector<Request> &batch, Bounce &b) {
+  const uint64_t *ring = c->rings + (size_t)ri * c->ring_cap;
+  const uint32_t mask = c->ring_cap - 1;
+  uint64_t h = c->head[ri];
+  const size_t maxb = batch.size();
+  size_t n = 0;
+  uint32_t s;
+  while (n < maxb && entry_ready(ring, mask, h + n, &s)) {
+    read_request(c, s, &batch[n]);
+    ++n;
+  }
+  if (n == 0) return 0;
+  if (n < maxb && c->cfg.coalesce_window_ns) {
+    const uint64_t until = mono_ns() + c->cfg.coalesce_window_ns;
+    while (n < maxb && mono_ns() < until) {
+      if (entry_ready(ring, mask, h + n, &s)) {
+        read_request(c, s, &batch[n]);
+        ++n;
+      } else {
+        cpu_relax();
+      }
+    }
+  }
+  process_batch(c, b, batch.data(), n, c->counters[ri]);
+  c->head[ri] = h + n;
+  c->retired[ri].store(h + n, std::memory_order_release);
+  return n;
+}
+
+void service_main(genesys_ctx *c, uint32_t ri) {
+  if (c->cfg.service_cpus) {
+    cpu_set_t set;
+    CPU_ZERO(&set);
+    CPU_SET(c->cfg.service_cpus[ri], &set);
+    pthread_setaffinity_np(pthread_self(), sizeof set, &set);
+  }
+  if (!c->host_only) cudaSetDevice(c->device);
+  std::vector<Request> batch(std::max<uint32_t>(1, c->cfg.coalesce_max));
+  Bounce b;
+  uint64_t last_work = mono_ns();
+  uint32_t idle_polls = 0;
+  while (!c->stop.load(std::memory_order_relaxed)) {
+    if (poll_ring(c, ri, batch, b)) {
+      last_work = 0;
+      idle_polls = 0;
+      continue;
+    }
+    if (++idle_polls < 64) { cpu_relax(); continue; }
+    idle_polls = 0;
+    const uint64_t now = mono_ns();
+    if (last_work == 0) last_work = now;
+    if (now - last_work < c->cfg.idle_spin_ns) {
+      cpu_relax();
+    } else {
+      timespec ts{0, 20000};  // nap 20 us while idle
+      nanosleep(&ts, nullptr);
+    }
+  }
+  if (b.buf) cudaFreeHost(b.buf);
+  if (b.stream) cudaStreamDestroy(b.stream);
+}
+
+template <class T>
+int dev_alloc(genesys_ctx *c, T **p, size_t count) {
+  const size_t bytes = std::max<size_t>(count * sizeof(T), 256);
+  if (c->host_only) {
+    *p = (T *)aligned_alloc(256, (bytes + 255) & ~size_t(255));
+    if (!*p) return fail(GENESYS_ENOMEM, "host allocation of %zu bytes failed", bytes);
+    memset(*p, 0, bytes);
+    return 0;
+  }
+  CUDA_TRY(cudaMalloc((void **)p, bytes));
+  CUDA_TRY(cudaMemset(*p, 0, bytes));
+  return 0;
+}
+
+template <class T>
+int host_alloc(genesys_ctx *c, T **p, size_t bytes) {
+  bytes = std::max<size_t>(bytes, 256);
+  if (c->host_only) {
+    *p = (T *)aligned_alloc(4096, (bytes + 4095) & ~size_t(4095));
+    if (!*p) return fail(GENESYS_ENOMEM, "host allocation of %zu bytes failed", bytes);
+    memset(*p, 0, bytes);
+    return 0;
+  }
+  CUDA_TRY(cudaHostAlloc((void **)p, bytes, cudaHostAllocMapped | cudaHostAllocPortable));
+  memset(*p, 0, bytes);
+  return 0;
+}
+
+template <class T>
+void dev_free(genesys_ctx *c, T *p) {
+  if (!p) return;
+  if (c->host_only) free(p); else cudaFree(p);
+}
+template <class T>
+void host_free(genesys_ctx *c, T *p) {
+  if (!p) return;
+  if (c->host_only) free(p); else cudaFreeHost(p);
+}
+
+void free_all(genesys_ctx *c) {
+  host_free(c, c->slots);
+  host_free(c, c->done);
+  host_free(c, c->rings);
+  host_free(c, c->staging);
+  dev_free(c, c->owner);
+  dev_free(c, c->seq);
+  dev_free(c, c->known_done);
+  dev_free(c, c->ring_tail);
+  dev_free(c, c->ksite);
+  dev_free(c, c->grid_bar);
+  dev_free(c, c->status);
+  dev_free(c, c->lat);
+  dev_free(c, c->lat_count);
+  if (c->aux) cudaStreamDestroy(c->aux);
+  {
+    std::lock_guard<std::mutex> g(c->map_mu);
+    for (auto &kv : c->maps) {
+      if (!c->host_only) cudaHostUnregister(kv.second.first);
+      munmap(kv.second.first, kv.second.second);
+    }
+    c->maps.clear();
+  }
+}
+
+// Ring positions published so far, per ring.  Device memory: read after the
+// kernels have finished.
+int read_tails(genesys_ctx *c, std::vector<uint32_t> &tails) {
+  const uint32_t n = c->cfg.n_service_threads;
+  std::vector<uint32_t> raw((size_t)n * 32);
+  if (c->host_only) {
+    for (uint32_t r = 0; r < n; ++r) tails[r] = __atomic_load_n(&c->ring_tail[r * 32], __ATOMIC_ACQUIRE);
+    return 0;
+  }
+  CUDA_TRY(cudaMemcpyAsync(raw.data(), c->ring_tail, raw.size() * 4, cudaMemcpyDeviceToHost, c->aux));
+  CUDA_TRY(cudaStreamSynchronize(c->aux));
+  for (uint32_t r = 0; r < n; ++r) tails[r] = raw[(size_t)r * 32];
+  return 0;
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+
+extern "C" {
+
+const char *genesys_last_error(void) { return g_last_error.c_str(); }
+
+int genesys_internal_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
+int genesys_config_default(genesys_config *cfg) {
+  if (!cfg) return fail(GENESYS_EINVAL, "cfg is NULL");
+  memset(cfg, 0, sizeof *cfg);
+  cfg->n_slots = 0;
+  cfg->n_service_threads = 4;
+  cfg->staging_bytes = 256ull << 20;
+  cfg->coalesce_window_ns = 0;
+  cfg->coalesce_max = 64;
+  cfg->merge = 1;
+  cfg->device_deadline_ns = 2000000000ull;
+  cfg->lat_samples = 1u << 20;
+  cfg->idle_spin_ns = 200000000ull;
+  return 0;
+}
+
+int genesys_init(const genesys_config *cfg_in, int device, genesys_ctx **out) {
+  if (!out) return fail(GENESYS_EINVAL, "out is NULL");
+  *out = nullptr;
+  genesys_config cfg;
+  if (cfg_in) cfg = *cfg_in; else genesys_config_default(&cfg);
+  if (cfg.n_service_threads == 0 || cfg.n_service_threads > 256)
+    return fail(GENESYS_EINVAL, "n_service_threads must be 1..256");
+  if (cfg.coalesce_max == 0) cfg.coalesce_max = 1;
+  if (cfg.device_deadline_ns == 0) return fail(GENESYS_EINVAL, "device_deadline_ns must be > 0");
+
+  auto c = std::make_unique<genesys_ctx>();
+  c->host_only = (cfg.flags & GENESYS_INIT_HOST_ONLY) != 0;
+  c->device = device;
+  if (!c->host_only) {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+      cudaGetLastError();
+      return fail(GENESYS_ENODEV, "no CUDA device");
+    }
+    if (device < 0 || device >= ndev) return fail(GENESYS_EINVAL, "device %d out of range", device);
+    CUDA_TRY(cudaSetDevice(device));
+    int sms = 0, mapped = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    CUDA_TRY(cudaDeviceGetAttribute(&mapped, cudaDevAttrCanMapHostMemory, device));
+    if (!mapped) return fail(GENESYS_ENODEV, "device cannot map host memory");
+    c->n_sms = (uint32_t)sms;
+    CUDA_TRY(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+  } else {
+    c->n_sms = 0;
+  }
+  if (cfg.n_slots == 0) cfg.n_slots = c->host_only ? 65536u : c->n_sms * 2048u;
+  if (cfg.n_slots < 32) cfg.n_slots = 32;
+  c->cfg = cfg;
+
+  // doorbell rings: ring r receives the slots s with (s / 32) % n_rings == r,
+  // at most ceil(n_slots / 32 / n_rings) * 32 of them, each with at most one
+  // request outstanding - so a ring of that capacity can never overflow.
+  const uint64_t groups = (cfg.n_slots + 31) / 32;
+  const uint64_t per_ring = ((groups + cfg.n_service_threads - 1) / cfg.n_service_threads) * 32;
+  c->ring_cap = (uint32_t)next_pow2(std::max<uint64_t>(per_ring, 64));
+
+  int rc;
+  auto cleanup = [&](int code) { free_all(c.get()); return code; };
+  if ((rc = host_alloc(c.get(), &c->slots, (size_t)cfg.n_slots * sizeof(genesys_slot)))) return cleanup(rc);
+  if ((rc = host_alloc(c.get(), &c->done, (size_t)cfg.n_slots * 8))) return cleanup(rc);
+  if ((rc = host_alloc(c.get(), &c->rings, (size_t)cfg.n_service_threads * c->ring_cap * 8))) return cleanup(rc);
+  if (cfg.staging_bytes && (rc = host_alloc(c.get(), &c->staging, cfg.staging_bytes))) return cleanup(rc);
+  if ((rc = dev_alloc(c.get(), &c->owner, cfg.n_slots))) return cleanup(rc);
+  if ((rc = dev_alloc(c.get(), &c->seq, cfg.n_slots))) return cleanup(rc);
+  if ((rc = dev_alloc(c.get(), &c->known_done, cfg.n_slots))) return cleanup(rc);
+  if ((rc = dev_alloc(c.get(), &c->ring_tail, (size_t)cfg.n_service_threads * 32))) return cleanup(rc);
+  if ((rc = dev_alloc(c.get(), &c->ksite, GENESYS_KSITES))) return cleanup(rc);
+  if ((rc = dev_alloc(c.get(), &c->grid_bar, 64))) return cleanup(rc);
+  if ((rc = dev_alloc(c.get(), &c->status, GENESYS_ST_WORDS))) return cleanup(rc);
+  if ((rc = dev_alloc(c.get(), &c->lat, std::max<uint32_t>(cfg.lat_samples, 1)))) return cleanup(rc);
+  if ((rc = dev_alloc(c.get(), &c->lat_count, 1))) return cleanup(rc);
+
+  const uint32_t nr = cfg.n_service_threads;
+  c->head.assign(nr, 0);
+  c->retired.reset(new std::atomic<uint64_t>[nr]);
+  for (uint32_t r = 0; r < nr; ++r) c->retired[r].store(0);
+  c->counters.reset(new Counters[nr]);
+  if (!(cfg.flags & GENESYS_INIT_NO_THREADS)) {
+    for (uint32_t r = 0; r < nr; ++r) c->threads.emplace_back(service_main, c.get(), r);
+  }
+  *out = c.release();
+  return 0;
+}
+
+int genesys_drain(genesys_ctx *c, uint64_t timeout_ns) {
+  if (!c) return fail(GENESYS_EINVAL, "ctx is NULL");
+  std::vector<uint32_t> tails(c->cfg.n_service_threads);
+  int rc = read_tails(c, tails);
+  if (rc) return rc;
+  const uint64_t until = mono_ns() + timeout_ns;
+  for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) {
+    for (;;) {
+      // positions are 32-bit on the device: compare modulo 2^32
+      const uint32_t got = (uint32_t)c->retired[r].load(std::memory_order_acquire);
+      if ((int32_t)(got - tails[r]) >= 0) break;
+      if (c->cfg.flags & GENESYS_INIT_NO_THREADS) {
+        std::lock_guard<std::mutex> g(c->svc_mu);
+        std::vector<Request> batch(std::max<uint32_t>(1, c->cfg.coalesce_max));
+        Bounce b;
+        poll_ring(c, r, batch, b);
+        if (b.buf) cudaFreeHost(b.buf);
+        if (b.stream) cudaStreamDestroy(b.stream);
+      } else {
+        std::this_thread::sleep_for(std::chrono::microseconds(5));
+      }
+      if (mono_ns() > until)
+        return fail(GENESYS_ETIMEDOUT, "drain: ring %u retired %u of %u requests", r, got, tails[r]);
+    }
+  }
+  return 0;
+}
+
+int genesys_shutdown(genesys_ctx *c) {
+  if (!c) return 0;
+  int rc = 0;
+  if (!c->threads.empty()) {
+    rc = genesys_drain(c, 1000000000ull);
+    c->stop.store(true);
+    for (auto &t : c->threads) t.join();
+    c->threads.clear();
+  }
+  free_all(c);
+  delete c;
+  return rc;
+}
+
+int genesys_device_view(genesys_ctx *c, genesys_dev *d) {
+  if (!c || !d) return fail(GENESYS_EINVAL, "NULL argument");
+  memset(d, 0, sizeof *d);
+  d->slots = c->slots;
+  d->done = c->done;
+  d->rings = c->rings;
+  d->owner = c->owner;
+  d->seq = c->seq;
+  d->known_done = c->known_done;
+  d->ring_tail = c->ring_tail;
+  d->ksite = c->ksite;
+  d->grid_bar = c->grid_bar;
+  d->status = c->status;
+  d->lat = c->lat;
+  d->lat_count = c->lat_count;
+  d->lat_cap = c->cfg.lat_samples;
+  d->n_slots = c->cfg.n_slots;
+  d->n_rings = c->cfg.n_service_threads;
+  d->ring_mask = c->ring_cap - 1;
+  d->deadline_ns = c->cfg.device_deadline_ns;
+  d->n_sms = c->n_sms;
+  return 0;
+}
+
+int genesys_launch(genesys_ctx *c, const void *kernel, const uint32_t grid[3], const uint32_t block[3],
+                   size_t smem, void **args, uint32_t flags, void *stream) {
+  if (!c || !kernel || !grid || !block) return fail(GENESYS_EINVAL, "NULL argument");
+  if (c->host_only) return fail(GENESYS_EINVAL, "host-only context cannot launch kernels");
+  const uint32_t gran = flags & GENESYS_LAUNCH_GRAN_MASK;
+  const bool relaxed = flags & GENESYS_LAUNCH_RELAXED;
+  if (gran == GENESYS_GRAN_ITEM && relaxed)
+    return fail(GENESYS_EINVAL, "work-item grain calls are always strongly ordered (Sec. 4.1)");
+  bool coop = (flags & GENESYS_LAUNCH_COOPERATIVE) || (gran == GENESYS_GRAN_KERNEL && !relaxed);
+  const dim3 g(grid[0], grid[1], grid[2]), b(block[0], block[1], block[2]);
+  const uint64_t nblocks = (uint64_t)grid[0] * grid[1] * grid[2];
+  const uint64_t nthreads = (uint64_t)block[0] * block[1] * block[2];
+  if (nblocks == 0 || nthreads == 0) return fail(GENESYS_EINVAL, "empty grid or block");
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(cudaSetDevice(c->device));
+  if (coop) {
+    int per_sm = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, (int)nthreads, smem));
+    if (nblocks > (uint64_t)per_sm * c->n_sms)
+      return fail(GENESYS_EINVAL,
+                  "kernel-grain strong ordering needs every block resident: grid %llu > %d x %u (Sec. 4.1)",
+                  (unsigned long long)nblocks, per_sm, c->n_sms);
+  }
+  if (gran == GENESYS_GRAN_KERNEL) CUDA_TRY(cudaMemsetAsync(c->ksite, 0, GENESYS_KSITES * sizeof(genesys_ksite), s));
+  if (coop)
+    CUDA_TRY(cudaLaunchCooperativeKernel(kernel, g, b, args, smem, s));
+  else
+    CUDA_TRY(cudaLaunchKernel(kernel, g, b, args, smem, s));
+  if (flags & GENESYS_LAUNCH_SYNC) {
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return genesys_drain(c, 10ull * c->cfg.device_deadline_ns);
+  }
+  return 0;
+}
+
+int genesys_service(genesys_ctx *c, uint64_t timeout_ns) {
+  if (!c) return fail(GENESYS_EINVAL, "ctx is NULL");
+  const uint64_t until = mono_ns() + timeout_ns;
+  if (c->cfg.flags & GENESYS_INIT_NO_THREADS) {
+    std::lock_guard<std::mutex> g(c->svc_mu);
+    std::vector<Request> batch(std::max<uint32_t>(1, c->cfg.coalesce_max));
+    Bounce b;
+    int total = 0;
+    do {
+      size_t n = 0;
+      for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) n += poll_ring(c, r, batch, b);
+      total += (int)n;
+      if (n == 0) cpu_relax();
+    } while (mono_ns() < until);
+    if (b.buf) cudaFreeHost(b.buf);
+    if (b.stream) cudaStreamDestroy(b.stream);
+    return total;
+  }
+  return genesys_drain(c, timeout_ns);
+}
+
+int genesys_stats_get(genesys_ctx *c, genesys_stats *o) {
+  if (!c || !o) return fail(GENESYS_EINVAL, "NULL argument");
+  memset(o, 0, sizeof *o);
+  for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) {
+    Counters &k = c->counters[r];
+    o->requests += k.requests.load();
+    o->os_calls += k.os_calls.load();
+    o->failed += k.failed.load();
+    o->nonblocking_failed += k.nb_failed.load();
+    o->bytes += k.bytes.load();
+    o->batches += k.batches.load();
+    o->busy_ns += k.busy_ns.load();
+    for (int i = 0; i < 8; ++i) o->by_op[i] += k.by_op[i].load();
+  }
+  return 0;
+}
+
+int genesys_stats_reset(genesys_ctx *c) {
+  if (!c) return fail(GENESYS_EINVAL, "ctx is NULL");
+  for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) {
+    Counters &k = c->counters[r];
+    k.requests = 0; k.os_calls = 0; k.failed = 0; k.nb_failed = 0; k.bytes = 0; k.batches = 0; k.busy_ns = 0;
+    for (int i = 0; i < 8; ++i) k.by_op[i] = 0;
+  }
+  return 0;
+}
+
+int genesys_status(genesys_ctx *c, int32_t out[GENESYS_ST_WORDS], int clear) {
+  if (!c || !out) return fail(GENESYS_EINVAL, "NULL argument");
+  if (c->host_only) {
+    memcpy(out, c->status, GENESYS_ST_WORDS * 4);
+    if (clear) memset(c->status, 0, GENESYS_ST_WORDS * 4);
+    return 0;
+  }
+  CUDA_TRY(cudaMemcpyAsync(out, c->status, GENESYS_ST_WORDS * 4, cudaMemcpyDeviceToHost, c->aux));
+  if (clear) CUDA_TRY(cudaMemsetAsync(c->status, 0, GENESYS_ST_WORDS * 4, c->aux));
+  CUDA_TRY(cudaStreamSynchronize(c->aux));
+  return 0;
+}
+
+int genesys_latency(genesys_ctx *c, uint64_t *out, uint32_t cap, uint32_t *n_out, int clear) {
+  if (!c || !n_out) return fail(GENESYS_EINVAL, "NULL argument");
+  uint32_t n = 0;
+  if (c->host_only) {
+    n = *c->lat_count;
+  } else {
+    CUDA_TRY(cudaMemcpyAsync(&n, c->lat_count, 4, cudaMemcpyDeviceToHost, c->aux));
+    CUDA_TRY(cudaStreamSynchronize(c->aux));
+  }
+  *n_out = n;
+  const uint32_t m = std::min(std::min(n, cap), c->cfg.lat_samples);
+  if (out && m) {
+    if (c->host_only) memcpy(out, c->lat, (size_t)m * 8);
+    else CUDA_TRY(cudaMemcpyAsync(out, c->lat, (size_t)m * 8, cudaMemcpyDeviceToHost, c->aux));
+  }
+  if (clear) {
+    if (c->host_only) *c->lat_count = 0;
+    else CUDA_TRY(cudaMemsetAsync(c->lat_count, 0, 4, c->aux));
+  }
+  if (!c->host_only) CUDA_TRY(cudaStreamSynchronize(c->aux));
+  return 0;
+}
+
+void *genesys_staging(genesys_ctx *c, size_t bytes) {
+  if (!c || !c->staging) { fail(GENESYS_EINVAL, "no staging arena"); return nullptr; }
+  const uint64_t need = (bytes + 255) & ~uint64_t(255);
+  uint64_t cur = c->staging_used.load();
+  do {
+    if (cur + need > c->cfg.staging_bytes) {
+      fail(GENESYS_ENOMEM, "staging arena exhausted (%llu + %llu > %llu)", (unsigned long long)cur,
+           (unsigned long long)need, (unsigned long long)c->cfg.staging_bytes);
+      return nullptr;
+    }
+  } while (!c->staging_used.compare_exchange_weak(cur, cur + need));
+  return c->staging + cur;
+}
+
+int genesys_staging_reset(genesys_ctx *c) {
+  if (!c) return fail(GENESYS_EINVAL, "ctx is NULL");
+  c->staging_used.store(0);
+  return 0;
+}
+
+// Host emulation of one GPU lane making a call (GENESYS_INIT_HOST_ONLY): the
+// same claim / marshal / publish / doorbell / wait steps as genesys_device.cuh,
+// with CPU atomics on the host copies of the device-side state.
+int genesys_emulate_call(genesys_ctx *c, uint32_t nr, const uint64_t args[6], uint32_t flags, int64_t *ret) {
+  if (!c || !args || !ret) return fail(GENESYS_EINVAL, "NULL argument");
+  if (!c->host_only) return fail(GENESYS_EINVAL, "genesys_emulate_call needs a host-only context");
+  const uint64_t t0 = mono_ns();
+  const uint64_t deadline = c->cfg.device_deadline_ns;
+  static std::atomic<uint32_t> hint_ctr{0};
+  uint32_t s = hint_ctr.fetch_add(1) % c->cfg.n_slots;
+  for (uint32_t probes = 0;; ++probes) {
+    uint32_t expect = 0;
+    if (__atomic_compare_exchange_n(&c->owner[s], &expect, 1u, false, __ATOMIC_ACQUIRE, __ATOMIC_RELAXED)) break;
+    s = (s + 1) % c->cfg.n_slots;
+    if (probes % 64 == 63) {
+      if (mono_ns() - t0 > deadline) return fail(GENESYS_ETIMEDOUT, "no free slot");
+      std::this_thread::yield();
+    }
+  }
+  const uint32_t sq = __atomic_load_n(&c->seq[s], __ATOMIC_RELAXED);
+  if (__atomic_load_n(&c->known_done[s], __ATOMIC_RELAXED) != sq) {
+    while ((uint32_t)(__atomic_load_n(&c->done[s], __ATOMIC_ACQUIRE) >> 32) != sq) {
+      if (mono_ns() - t0 > deadline) {
+        __atomic_store_n(&c->owner[s], 0u, __ATOMIC_RELEASE);
+        return fail(GENESYS_ETIMEDOUT, "slot %u still busy", s);
+      }
+      cpu_relax();
+    }
+    __atomic_store_n(&c->known_done[s], sq, __ATOMIC_RELAXED);
+  }
+  const uint32_t nsq = sq + 1;
+  __atomic_store_n(&c->seq[s], nsq, __ATOMIC_RELAXED);
+  genesys_slot *sl = &c->slots[s];
+  for (int i = 0; i < 6; ++i) __atomic_store_n(&sl->args[i], args[i], __ATOMIC_RELAXED);
+  __atomic_store_n(&sl->req, ((uint64_t)nsq << 32) | ((uint64_t)(nr & 0xFFFFu) << 16) | (flags & 0xFFFFu),
+                   __ATOMIC_RELEASE);
+  const uint32_t r = (s >> 5) % c->cfg.n_service_threads;
+  const uint32_t pos = __atomic_fetch_add(&c->ring_tail[r * 32], 1u, __ATOMIC_ACQ_REL);
+  __atomic_store_n(&c->rings[(size_t)r * c->ring_cap + (pos & (c->ring_cap - 1))], GENESYS_RING_ENTRY(pos, s),
+                   __ATOMIC_RELEASE);
+  int64_t result = 0;
+  if (flags & GENESYS_REQ_BLOCKING) {
+    uint64_t d;
+    for (;;) {
+      d = __atomic_load_n(&c->done[s], __ATOMIC_ACQUIRE);
+      if ((uint32_t)(d >> 32) == nsq) break;
+      if (mono_ns() - t0 > deadline) {
+        __atomic_store_n(&c->owner[s], 0u, __ATOMIC_RELEASE);
+        return fail(GENESYS_ETIMEDOUT, "call not completed within the deadline");
+      }
+      if (c->cfg.flags & GENESYS_INIT_NO_THREADS) std::this_thread::yield(); else cpu_relax();
+    }
+    __atomic_store_n(&c->known_done[s], nsq, __ATOMIC_RELAXED);
+    const uint32_t lo = (uint32_t)d;
+    result = lo == GENESYS_RET_IN_SLOT ? (int64_t)__atomic_load_n(&sl->ret, __ATOMIC_RELAXED) : (int64_t)(int32_t)lo;
+  }
+  __atomic_store_n(&c->owner[s], 0u, __ATOMIC_RELEASE);
+  *ret = result;
+  return 0;
+}
+
+}  // extern "C"

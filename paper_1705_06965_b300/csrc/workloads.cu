@@ -1,0 +1,341 @@
+// Data-parallel kernels that make GPU system calls and consume their results,
+// and their C-ABI entry points (declared in genesys.h).
+//
+// Paper: Vesely et al., "GPU System Calls", arXiv 1705.06965.
+//   C1  Sec. 6 / Fig. 5   pread microbenchmark (here: pread + byte histogram)
+//   C2  Sec. 4.1 / Sec. 6 pwrite at work-item / warp / work-group / kernel grain
+//   probe Sec. 4.1        strong ordering: stores before the call are complete
+#include <cuda_runtime.h>
+#include <stdio.h>
+
+#include "genesys.h"
+#include "genesys_device.cuh"
+#include "internal.h"
+
+using namespace genesys;
+
+namespace {
+
+// splitmix64 (Steele, Lea & Flood 2014), counter-based: value i of the
+// generator whose state starts at `seed`.
+__device__ __forceinline__ uint64_t sm64_at(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+int set_err(int code, const char *msg) { return genesys_internal_error(code, msg); }
+
+// Launch through the runtime (legality checks, kernel-grain state reset,
+// synchronise + drain), then turn device-side failures into GENESYS_EDEVICE.
+int run(genesys_ctx *c, const void *kernel, uint32_t grid, uint32_t block, size_t smem, void **args, uint32_t flags,
+        void *stream) {
+  const uint32_t g3[3] = {grid, 1, 1}, b3[3] = {block, 1, 1};
+  int rc = genesys_launch(c, kernel, g3, b3, smem, args, flags | GENESYS_LAUNCH_SYNC, stream);
+  if (rc) return rc;
+  int32_t st[GENESYS_ST_WORDS];
+  rc = genesys_status(c, st, 1);
+  if (rc) return rc;
+  if (st[GENESYS_ST_TIMEOUTS] || st[GENESYS_ST_FAILED_CALLS] || st[GENESYS_ST_FIRST_ERROR] ||
+      st[GENESYS_ST_BAD_ARGS]) {
+    char msg[160];
+    snprintf(msg, sizeof msg, "device-side calls failed: first error %d, %d timeouts, %d failed calls",
+             st[GENESYS_ST_FIRST_ERROR], st[GENESYS_ST_TIMEOUTS], st[GENESYS_ST_FAILED_CALLS]);
+    return set_err(GENESYS_EDEVICE, msg);
+  }
+  return 0;
+}
+
+// ------------------------------------------------------------------- C1
+// Byte histogram of `n` bytes at `buf` (host-mapped staging, 16-byte aligned)
+// into the calling warp's shared-memory copy.  16-byte vector loads, one per
+// thread per step, so a block streams the chunk over the host link in as few
+// round trips as its width allows.
+__device__ __forceinline__ void hist_bytes(const uint8_t *buf, uint64_t n, uint32_t *my) {
+  const uint4 *v = reinterpret_cast<const uint4 *>(buf);
+  const uint64_t n16 = n >> 4;
+  for (uint64_t i = threadIdx.x; i < n16; i += blockDim.x) {
+    const uint4 x = v[i];
+    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+      for (int b = 0; b < 4; ++b) atomicAdd(&my[(w[k] >> (8 * b)) & 0xFFu], 1u);
+    }
+  }
+  for (uint64_t i = (n16 << 4) + threadIdx.x; i < n; i += blockDim.x) atomicAdd(&my[buf[i]], 1u);
+}
+
+__device__ __forceinline__ void hist_flush(uint32_t *sh, uint32_t *hist_out) {
+  __syncthreads();
+  const uint32_t nw = blockDim.x >> 5;
+  for (uint32_t b = threadIdx.x; b < 256; b += blockDim.x) {
+    uint32_t s = 0;
+    for (uint32_t w = 0; w < nw; ++w) s += sh[w * 256 + b];
+    if (s) atomicAdd(&hist_out[b], s);
+  }
+}
+
+// Plain form: work-group grain, strong ordering, blocking (the combination
+// the paper's microbenchmarks start from).  Block b reads chunks b, b+G, ...
+__global__ void __launch_bounds__(1024) c1_plain_kernel(genesys_dev g, int fd, uint64_t file_bytes, uint32_t chunk,
+                                                        uint8_t *staging, uint32_t *hist_out) {
+  extern __shared__ uint32_t sh[];
+  for (uint32_t i = threadIdx.x; i < (blockDim.x >> 5) * 256; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  uint32_t *my = sh + (threadIdx.x >> 5) * 256;
+  uint8_t *buf = staging + (size_t)blockIdx.x * chunk;
+  const uint64_t n_chunks = (file_bytes + chunk - 1) / chunk;
+  for (uint64_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+    const uint64_t off = c * chunk;
+    const uint64_t len = file_bytes - off < chunk ? file_bytes - off : chunk;
+    const int64_t r = call<GROUP, STRONG, BLOCKING>(g, SYS_pread64, (uint64_t)fd, (uint64_t)buf, len, off);
+    if (r <= 0) break;  // r is the same in every thread (broadcast after the call)
+    hist_bytes(buf, (uint64_t)r < len ? (uint64_t)r : len, my);
+  }
+  hist_flush(sh, hist_out);
+}
+
+// Batched form: relaxed, non-blocking preads double-buffered per block - the
+// read of chunk k+1 is in flight while chunk k is scanned (Sec. 4.1: weak
+// ordering with non-blocking prefetching reads).
+__global__ void __launch_bounds__(1024) c1_batched_kernel(genesys_dev g, int fd, uint64_t file_bytes, uint32_t chunk,
+                                                          uint8_t *staging, uint32_t *hist_out) {
+  extern __shared__ uint32_t sh[];
+  __shared__ int64_t r_s;
+  for (uint32_t i = threadIdx.x; i < (blockDim.x >> 5) * 256; i += blockDim.x) sh[i] = 0;
+  uint32_t *my = sh + (threadIdx.x >> 5) * 256;
+  uint8_t *bufs[2] = {staging + (size_t)(2 * blockIdx.x) * chunk, staging + (size_t)(2 * blockIdx.x + 1) * chunk};
+  const uint64_t n_chunks = (file_bytes + chunk - 1) / chunk;
+  const bool leader = threadIdx.x == 0;
+  Ticket cur{0xFFFFFFFFu, 0, 0}, nxt{0xFFFFFFFFu, 0, 0};
+  auto issue_chunk = [&](Ticket *t, uint64_t c, uint8_t *buf) {
+    const uint64_t off = c * chunk;
+    const uint64_t len = file_bytes - off < chunk ? file_bytes - off : chunk;
+    issue(g, t, SYS_pread64, (uint64_t)fd, (uint64_t)buf, len, off);
+  };
+  uint64_t c = blockIdx.x;
+  if (leader && c < n_chunks) issue_chunk(&cur, c, bufs[0]);
+  __syncthreads();
+  for (uint32_t k = 0; c < n_chunks; c += gridDim.x, ++k) {
+    if (leader) {
+      const uint64_t cn = c + gridDim.x;
+      bool has_next = cn < n_chunks;
+      if (has_next) issue_chunk(&nxt, cn, bufs[(k + 1) & 1]);
+      int64_t r = wait(g, cur);
+      if (r <= 0 && has_next) {  // stop early: collect the prefetch so its slot is released
+        wait(g, nxt);
+        has_next = false;
+      }
+      cur = nxt;
+      nxt = Ticket{0xFFFFFFFFu, 0, 0};
+      r_s = r;
+    }
+    __syncthreads();  // consumer: barrier after the read completes
+    const int64_t r = r_s;
+    if (r <= 0) break;
+    hist_bytes(bufs[k & 1], (uint64_t)r < chunk ? (uint64_t)r : chunk, my);
+    __syncthreads();  // buffer k&1 is free for the prefetch two chunks ahead
+  }
+  hist_flush(sh, hist_out);
+}
+
+// ------------------------------------------------------------------- C2
+// Marshal: the warp writes its 32 threads' 64-byte patterns (2 KiB, contiguous
+// in staging) with lane-interleaved 16-byte stores, so each store instruction
+// covers 512 contiguous bytes.  splitmix64 is counter-based, so any lane can
+// produce any thread's words.  Threads >= n write nothing.
+__device__ __forceinline__ void c2_marshal_warp(uint64_t warp_gid0, uint64_t n, uint64_t seed, uint8_t *staging) {
+  const uint32_t lane = lane_id();
+  uint64_t *base = reinterpret_cast<uint64_t *>(staging + warp_gid0 * 64);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t w = j * 64 + lane * 2;           // word index within the warp's 256 words
+    const uint64_t wi = warp_gid0 * 8 + w;          // global word index
+    if (wi / 8 < n) st_v2(base + w, sm64_at(seed, wi), sm64_at(seed, wi + 1));
+  }
+}
+
+template <int G, int O, int B>
+__global__ void __launch_bounds__(1024) c2_pwrite_kernel(genesys_dev g, int fd, uint64_t n, uint64_t seed,
+                                                         uint8_t *staging) {
+  const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (G == KERNEL) {
+    // grid-stride over warps' payloads (the grid may be smaller than n when the
+    // launch is cooperative), then one call for the whole kernel
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = gid - lane_id(); t < n; t += stride) c2_marshal_warp(t, n, seed, staging);
+    __syncwarp();
+    call<KERNEL, O, B>(g, SYS_pwrite64, (uint64_t)fd, (uint64_t)staging, n * 64, 0);
+    return;
+  }
+  const uint64_t warp0 = gid - lane_id();
+  if (warp0 < n) c2_marshal_warp(warp0, n, seed, staging);
+  __syncwarp();
+  if (G == GROUP) {
+    const uint64_t b0 = (uint64_t)blockIdx.x * blockDim.x;
+    const uint64_t cnt = n - b0 < blockDim.x ? n - b0 : blockDim.x;
+    call<GROUP, O, B>(g, SYS_pwrite64, (uint64_t)fd, (uint64_t)(staging + b0 * 64), cnt * 64, b0 * 64);
+    return;
+  }
+  if (gid >= n) return;
+  if (G == ITEM) {
+    call<ITEM, STRONG, B>(g, SYS_pwrite64, (uint64_t)fd, (uint64_t)(staging + gid * 64), 64, gid * 64);
+  } else {
+    call_warp_coalesced<O, B>(g, SYS_pwrite64, fd, (uint64_t)(staging + gid * 64), 64, gid * 64);
+  }
+}
+
+// ------------------------------------------------------- visibility probe
+// Every thread stores its word, then the group's caller asks the CPU to check
+// that all of the group's words are visible.  R = ROLE_PRODUCER puts the
+// barrier before the call under relaxed ordering (the stores must be
+// complete); R = ROLE_CONSUMER omits it, so stores may legitimately still be
+// in flight (violations allowed).
+template <int G, int O, int R>
+__global__ void __launch_bounds__(1024) visibility_kernel(genesys_dev g, uint64_t n, uint64_t seed, uint64_t *probe,
+                                                          unsigned long long *viol) {
+  const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (G == KERNEL) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = gid; t < n; t += stride) probe[t] = sm64_at(seed, t);
+    const int64_t r = call_at<KERNEL, O, BLOCKING, R>(g, 0, GENESYS_NR_CHECK_VISIBLE, (uint64_t)probe, n, seed, 0);
+    if (r > 0) atomicAdd(viol, (unsigned long long)r);
+    return;
+  }
+  if (gid < n) probe[gid] = sm64_at(seed, gid);
+  if (G == ITEM) {
+    if (gid >= n) return;
+    const int64_t r = call<ITEM, STRONG, BLOCKING, R>(g, GENESYS_NR_CHECK_VISIBLE, (uint64_t)(probe + gid), 1, seed, gid);
+    if (r > 0) atomicAdd(viol, (unsigned long long)r);
+    return;
+  }
+  if (G == WARP) {
+    if (gid >= n) return;
+    const uint32_t active = __activemask();
+    const uint64_t first = gid - lane_id();          // in-range lanes start at lane 0
+    const uint64_t cnt = __popc(active);
+    const int64_t r = call<WARP, O, BLOCKING, R>(g, GENESYS_NR_CHECK_VISIBLE, (uint64_t)(probe + first), cnt, seed, first);
+    if (lane_id() == 0 && r > 0) atomicAdd(viol, (unsigned long long)r);
+    return;
+  }
+  const uint64_t b0 = (uint64_t)blockIdx.x * blockDim.x;
+  const uint64_t cnt = n - b0 < blockDim.x ? n - b0 : blockDim.x;
+  const int64_t r = call<GROUP, O, BLOCKING, R>(g, GENESYS_NR_CHECK_VISIBLE, (uint64_t)(probe + b0), cnt, seed, b0);
+  if (threadIdx.x == 0 && r > 0) atomicAdd(viol, (unsigned long long)r);
+}
+
+template <int G, int O, int B>
+const void *c2_kernel_ptr() {
+  return reinterpret_cast<const void *>(&c2_pwrite_kernel<G, O, B>);
+}
+
+const void *c2_select(uint32_t gran, bool relaxed, bool nonblocking) {
+#define C2_CASE(G)                                                                      \
+  if (gran == G) {                                                                      \
+    if (!relaxed && !nonblocking) return c2_kernel_ptr<G, STRONG, BLOCKING>();          \
+    if (!relaxed && nonblocking) return c2_kernel_ptr<G, STRONG, NONBLOCKING>();        \
+    if (relaxed && !nonblocking) return c2_kernel_ptr<G, RELAXED, BLOCKING>();          \
+    return c2_kernel_ptr<G, RELAXED, NONBLOCKING>();                                    \
+  }
+  if (gran == ITEM) {
+    if (relaxed) return nullptr;
+    return nonblocking ? c2_kernel_ptr<ITEM, STRONG, NONBLOCKING>() : c2_kernel_ptr<ITEM, STRONG, BLOCKING>();
+  }
+  C2_CASE(WARP)
+  C2_CASE(GROUP)
+  C2_CASE(KERNEL)
+#undef C2_CASE
+  return nullptr;
+}
+
+template <int G, int O, int R>
+const void *vis_ptr() {
+  return reinterpret_cast<const void *>(&visibility_kernel<G, O, R>);
+}
+
+}  // namespace
+
+extern "C" {
+
+int genesys_c1_histogram(genesys_ctx *c, int fd, uint64_t file_bytes, uint64_t chunk, uint32_t groups,
+                         uint32_t threads, uint32_t form, void *staging, uint64_t staging_bytes, uint32_t *hist_dev,
+                         void *stream) {
+  if (!c || !staging || !hist_dev) return set_err(GENESYS_EINVAL, "NULL argument");
+  if (fd < 0) return set_err(GENESYS_EINVAL, "bad fd");
+  if (chunk == 0 || chunk % 16 || chunk > (1u << 30)) return set_err(GENESYS_EINVAL, "chunk must be a multiple of 16");
+  if (groups == 0 || threads < 32 || threads > 1024 || threads % 32) return set_err(GENESYS_EINVAL, "bad launch shape");
+  if ((uintptr_t)staging % 16) return set_err(GENESYS_EINVAL, "staging must be 16-byte aligned");
+  const uint64_t need = (uint64_t)groups * chunk * (form == GENESYS_FORM_BATCHED ? 2 : 1);
+  if (staging_bytes < need) return set_err(GENESYS_EINVAL, "staging too small");
+  if (file_bytes == 0) return 0;
+  genesys_dev g;
+  genesys_device_view(c, &g);
+  uint32_t ch = (uint32_t)chunk;
+  uint8_t *st = (uint8_t *)staging;
+  void *args[] = {&g, &fd, &file_bytes, &ch, &st, &hist_dev};
+  const size_t smem = (size_t)(threads / 32) * 256 * 4;
+  if (form == GENESYS_FORM_BATCHED)
+    return run(c, (const void *)&c1_batched_kernel, groups, threads, smem, args,
+               GENESYS_GRAN_GROUP | GENESYS_LAUNCH_RELAXED | GENESYS_LAUNCH_NONBLOCKING, stream);
+  return run(c, (const void *)&c1_plain_kernel, groups, threads, smem, args, GENESYS_GRAN_GROUP, stream);
+}
+
+int genesys_c2_pwrite(genesys_ctx *c, int fd, uint64_t n, uint32_t gran, uint32_t bt, uint32_t relaxed,
+                      uint32_t nonblocking, uint64_t seed, void *staging, uint64_t staging_bytes, void *stream) {
+  if (!c || !staging) return set_err(GENESYS_EINVAL, "NULL argument");
+  if (fd < 0) return set_err(GENESYS_EINVAL, "bad fd");
+  if (gran > GENESYS_GRAN_KERNEL || bt < 32 || bt > 1024 || bt % 32) return set_err(GENESYS_EINVAL, "bad shape");
+  if (staging_bytes < n * 64 || (uintptr_t)staging % 16) return set_err(GENESYS_EINVAL, "staging too small or unaligned");
+  if (n == 0) return 0;
+  const void *k = c2_select(gran, relaxed != 0, nonblocking != 0);
+  if (!k) return set_err(GENESYS_EINVAL, "work-item grain calls are always strongly ordered (Sec. 4.1)");
+  genesys_dev g;
+  genesys_device_view(c, &g);
+  uint64_t blocks = (n + bt - 1) / bt;
+  if (gran == GENESYS_GRAN_KERNEL && !relaxed) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, (int)bt, 0) != cudaSuccess || per_sm == 0)
+      return set_err(GENESYS_ECUDA, "occupancy query failed");
+    const uint64_t cap = (uint64_t)per_sm * g.n_sms;
+    if (blocks > cap) blocks = cap;
+  }
+  if (blocks > 0x7FFFFFFFull) return set_err(GENESYS_EINVAL, "too many threads");
+  uint8_t *st = (uint8_t *)staging;
+  void *args[] = {&g, &fd, &n, &seed, &st};
+  const uint32_t flags = gran | (relaxed ? GENESYS_LAUNCH_RELAXED : 0) | (nonblocking ? GENESYS_LAUNCH_NONBLOCKING : 0);
+  return run(c, k, (uint32_t)blocks, bt, 0, args, flags, stream);
+}
+
+int genesys_visibility_probe(genesys_ctx *c, uint64_t n, uint32_t gran, uint32_t bt, uint32_t relaxed, uint64_t seed,
+                             uint64_t *probe, unsigned long long *viol, void *stream) {
+  if (!c || !probe || !viol) return set_err(GENESYS_EINVAL, "NULL argument");
+  if (gran > GENESYS_GRAN_KERNEL || bt < 32 || bt > 1024 || bt % 32) return set_err(GENESYS_EINVAL, "bad shape");
+  if (n == 0) return 0;
+  const void *k = nullptr;
+  // relaxed runs use the consumer role (no barrier before the call): the
+  // configuration in which the check may legitimately see missing stores
+  switch (gran) {
+    case GENESYS_GRAN_ITEM: k = relaxed ? nullptr : vis_ptr<ITEM, STRONG, ROLE_PRODUCER>(); break;
+    case GENESYS_GRAN_WARP: k = relaxed ? vis_ptr<WARP, RELAXED, ROLE_CONSUMER>() : vis_ptr<WARP, STRONG, ROLE_PRODUCER>(); break;
+    case GENESYS_GRAN_GROUP: k = relaxed ? vis_ptr<GROUP, RELAXED, ROLE_CONSUMER>() : vis_ptr<GROUP, STRONG, ROLE_PRODUCER>(); break;
+    default: k = relaxed ? vis_ptr<KERNEL, RELAXED, ROLE_CONSUMER>() : vis_ptr<KERNEL, STRONG, ROLE_PRODUCER>(); break;
+  }
+  if (!k) return set_err(GENESYS_EINVAL, "work-item grain calls are always strongly ordered (Sec. 4.1)");
+  genesys_dev g;
+  genesys_device_view(c, &g);
+  uint64_t blocks = (n + bt - 1) / bt;
+  if (gran == GENESYS_GRAN_KERNEL && !relaxed) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, (int)bt, 0) != cudaSuccess || per_sm == 0)
+      return set_err(GENESYS_ECUDA, "occupancy query failed");
+    const uint64_t cap = (uint64_t)per_sm * g.n_sms;
+    if (blocks > cap) blocks = cap;
+  }
+  void *args[] = {&g, &n, &seed, &probe, &viol};
+  const uint32_t flags = gran | (relaxed ? GENESYS_LAUNCH_RELAXED : 0);
+  return run(c, k, (uint32_t)blocks, bt, 0, args, flags, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,171 @@
+"""GPU parity: C1 (pread + byte histogram) and C2 (pwrite at every granularity,
+ordering and blocking mode) against the CPU oracle, bit-exact; the strong
+ordering visibility probe; the legality rules of Sec. 4.1.
+
+All calls go through the C ABI (libgenesys.so) via the ctypes binding.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def G():
+    import paper_1705_06965_b300 as G
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return G
+
+
+@pytest.fixture(scope="module")
+def ctx(G):
+    c = G.Context(device=0, service_threads=4, staging_bytes=320 << 20, deadline_ns=5_000_000_000)
+    yield c
+    c.close()
+
+
+def _c1(ctx, G, path, nbytes, chunk, groups, threads, form):
+    hist = torch.zeros(256, dtype=torch.int32, device="cuda")
+    ctx.staging_reset()
+    need = groups * chunk * 2
+    st = ctx.staging(need)
+    fd = os.open(path, os.O_RDONLY)
+    try:
+        ctx.c1_histogram(fd, nbytes, hist.data_ptr(), st, need, chunk=chunk, groups=groups, threads=threads,
+                         form=form)
+    finally:
+        os.close(fd)
+    torch.cuda.synchronize()
+    return hist.cpu().numpy().view(np.uint32)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_c1_full_config_bit_exact(ctx, G, form):
+    """The C1 configuration: 4 MiB, 64 work-groups x 256 threads, 4 KiB preads."""
+    p = workloads.c1_file()
+    want = oracle.c1_histogram(p, 4096)
+    got = _c1(ctx, G, p, 4 << 20, 4096, 64, 256, form)
+    assert np.array_equal(got, want)
+    assert ctx.status() == [0] * G.ST_WORDS
+
+
+@pytest.mark.parametrize("nbytes,chunk,groups,threads", [
+    (1, 4096, 64, 256),               # less than one chunk
+    (4096 * 3 + 17, 4096, 64, 256),   # fewer chunks than groups, ragged tail
+    (1 << 20, 16, 8, 32),             # tiny chunks: many calls per group
+    ((1 << 20) + 123, 65536, 148, 1024),
+    (6 << 20, 1 << 20, 5, 512),
+])
+@pytest.mark.parametrize("form", [0, 1])
+def test_c1_shapes(ctx, G, tmp_path, nbytes, chunk, groups, threads, form):
+    p = workloads.c1_file(str(tmp_path / "c1.bin"), nbytes, seed=nbytes)
+    want = oracle.c1_histogram(p, chunk)
+    got = _c1(ctx, G, p, nbytes, chunk, groups, threads, form)
+    assert np.array_equal(got, want)
+
+
+def test_c1_empty_and_errors(ctx, G, tmp_path):
+    p = workloads.c1_file(str(tmp_path / "e.bin"), 0)
+    assert _c1(ctx, G, p, 0, 4096, 4, 64, 0).sum() == 0
+    hist = torch.zeros(256, dtype=torch.int32, device="cuda")
+    st = ctx.staging(4096)
+    with pytest.raises(G.GenesysError) as e:
+        ctx.c1_histogram(3, 4096, hist.data_ptr(), st, 4096, chunk=4000, groups=1, threads=64)
+    assert e.value.code == G.EINVAL        # chunk not a multiple of 16
+    # a file shorter than announced: preads return short, the histogram
+    # covers the bytes that exist
+    p2 = workloads.c1_file(str(tmp_path / "s.bin"), 5000, seed=3)
+    got = _c1(ctx, G, p2, 64 * 4096, 4096, 4, 64, 0)
+    assert np.array_equal(got, oracle.c1_histogram(p2, 4096))
+
+
+def _c2(ctx, G, path, n, gran, bt, relaxed, nonblocking, seed=workloads.SEED_C2):
+    ctx.staging_reset()
+    st = ctx.staging(n * 64)
+    fd = os.open(path, os.O_CREAT | os.O_TRUNC | os.O_WRONLY, 0o644)
+    try:
+        ctx.c2_pwrite(fd, n, gran, bt, relaxed, nonblocking, seed, st, n * 64)
+    finally:
+        os.close(fd)
+    with open(path, "rb") as f:
+        return f.read()
+
+
+COMBOS = [(g, r, nb) for g in range(4) for r in (False, True) for nb in (False, True) if not (g == 0 and r)]
+
+
+@pytest.mark.parametrize("gran,relaxed,nonblocking", COMBOS)
+@pytest.mark.parametrize("n,bt", [(1, 32), (4096 + 37, 256), (20000, 64), (1 << 14, 1024)])
+def test_c2_combos_bit_exact(ctx, G, tmp_path, gran, relaxed, nonblocking, n, bt):
+    want_path = str(tmp_path / "want.bin")
+    group = {0: 1, 1: 32, 2: bt, 3: n}[gran]
+    oracle.c2_pwrite(want_path, n, group)
+    want = open(want_path, "rb").read()
+    got = _c2(ctx, G, str(tmp_path / "got.bin"), n, gran, bt, relaxed, nonblocking)
+    assert got == want
+    assert ctx.status() == [0] * G.ST_WORDS
+
+
+@pytest.mark.parametrize("gran", [0, 1, 2, 3])
+def test_c2_full_size(ctx, G, gran):
+    """2^20 threads (the top of the C2 sweep), work-group of 256."""
+    n = 1 << 20
+    d = workloads.scratch_dir("tests")
+    want_path = os.path.join(d, "c2_want.bin")
+    if not os.path.exists(want_path) or os.path.getsize(want_path) != n * 64:
+        oracle.c2_pwrite(want_path, n, 256)
+    got = _c2(ctx, G, os.path.join(d, "c2_got.bin"), n, gran, 256, gran != 0, False)
+    assert got == open(want_path, "rb").read()
+
+
+def test_c2_call_counts_and_latency(ctx, G, tmp_path):
+    n = 8192
+    for gran, calls in [(0, n), (1, n // 32), (2, n // 256), (3, 1)]:
+        ctx.stats_reset()
+        ctx.latency(clear=True)
+        _c2(ctx, G, str(tmp_path / "x.bin"), n, gran, 256, gran != 0, False)
+        st = ctx.stats()
+        assert st["requests"] == calls, (gran, st)
+        lat = ctx.latency(clear=True)
+        assert len(lat) == calls and lat.min() > 0
+
+
+def test_c2_illegal_item_relaxed(ctx, G, tmp_path):
+    st = ctx.staging(64)
+    with pytest.raises(G.GenesysError) as e:
+        ctx.c2_pwrite(1, 1, 0, 32, True, False, 0, st, 64)
+    assert e.value.code == G.EINVAL
+
+
+@pytest.mark.parametrize("gran", [0, 1, 2, 3])
+@pytest.mark.parametrize("n,bt", [(4096, 256), (20000, 1024)])
+def test_strong_ordering_visibility(ctx, G, gran, n, bt):
+    """Strong ordering: every store made before the call is visible to the CPU
+    handler (Sec. 4.1).  Violations must be 0."""
+    ctx.staging_reset()
+    probe = ctx.staging(n * 8)
+    ctx.host_view(probe, n * 8)[:] = 0
+    viol = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ctx.visibility_probe(n, gran, bt, False, 0xABCDEF, probe, viol.data_ptr())
+    assert int(viol.item()) == 0
+
+
+def test_relaxed_consumer_runs(ctx, G):
+    """Relaxed consumer role has no barrier before the call: the check may see
+    stores still in flight (allowed); it must complete without errors."""
+    n = 1 << 16
+    ctx.staging_reset()
+    probe = ctx.staging(n * 8)
+    ctx.host_view(probe, n * 8)[:] = 0
+    viol = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for gran in (1, 2, 3):
+        ctx.visibility_probe(n, gran, 256, True, 7, probe, viol.data_ptr())
+    assert int(viol.item()) >= 0

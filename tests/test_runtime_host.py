@@ -1,0 +1,219 @@
+"""Host-side runtime tests (no GPU).
+
+The service threads, doorbell rings, slot protocol, request merging and error
+paths are exercised with CPU threads standing in for GPU lanes
+(genesys_emulate_call on a host-only context), the way the CUDA callers use
+them.  Failures are made on the host: bad file descriptors, unsupported calls,
+a stalled service (nobody polls) that makes the caller's deadline fire.
+"""
+import errno
+import os
+import re
+import threading
+
+import numpy as np
+import pytest
+
+import paper_1705_06965_b300 as G
+import workloads
+
+INCLUDE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+
+
+def test_library_exports_every_declared_symbol():
+    L = G.lib()
+    declared = set()
+    for h in os.listdir(INCLUDE):
+        if h.endswith(".h"):
+            txt = open(os.path.join(INCLUDE, h)).read()
+            declared |= set(re.findall(r"^(?:int|void|const char)\b[^;(]*?\b(genesys_\w+)\s*\(", txt, re.M))
+    assert declared, "no declarations found"
+    assert declared == set(G.EXPORTS), declared ^ set(G.EXPORTS)
+    for name in declared:
+        assert hasattr(L, name), name
+
+
+def test_config_defaults():
+    cfg = G.Config()
+    assert G.lib().genesys_config_default(cfg) == 0
+    assert cfg.n_service_threads == 4 and cfg.coalesce_max == 64 and cfg.merge == 1
+    assert cfg.device_deadline_ns == 2_000_000_000
+
+
+def _ctx(**kw):
+    kw.setdefault("host_only", True)
+    kw.setdefault("service_threads", 2)
+    kw.setdefault("staging_bytes", 1 << 20)
+    kw.setdefault("n_slots", 256)
+    kw.setdefault("deadline_ns", 2_000_000_000)
+    return G.Context(**kw)
+
+
+def test_nop_roundtrip_and_stats():
+    with _ctx() as c:
+        for v in (0, 1, 12345, 2**31 - 1, 2**40 + 7, -5 & ((1 << 64) - 1)):
+            r = c.emulate_call(G.NR_NOP, [v])
+            want = v if v < 2**63 else v - 2**64
+            assert r == want
+        st = c.stats()
+        assert st["requests"] == 6 and st["by_op"]["internal"] == 6 and st["os_calls"] == 0
+
+
+def test_pread_pwrite_through_protocol(tmp_path):
+    p = str(tmp_path / "f.bin")
+    data = workloads.stream_bytes(7, 4096)
+    with _ctx() as c:
+        buf = c.staging(8192)
+        view = c.host_view(buf, 8192)
+        view[:4096] = np.frombuffer(data, np.uint8)
+        fd = os.open(p, os.O_CREAT | os.O_RDWR, 0o644)
+        try:
+            assert c.emulate_call(G.SYS_pwrite64, [fd, buf, 4096, 100]) == 4096
+            assert c.emulate_call(G.SYS_pread64, [fd, buf + 4096, 4096, 100]) == 4096
+            assert bytes(view[4096:]) == data
+            # short read at end of file
+            assert c.emulate_call(G.SYS_pread64, [fd, buf + 4096, 4096, 4000]) == 196
+        finally:
+            os.close(fd)
+        with open(p, "rb") as f:
+            f.seek(100)
+            assert f.read() == data
+
+
+def test_errors_are_returned_not_raised(tmp_path):
+    with _ctx() as c:
+        buf = c.staging(64)
+        assert c.emulate_call(G.SYS_pread64, [987654, buf, 64, 0]) == -errno.EBADF
+        assert c.emulate_call(200, [0]) == -errno.ENOSYS          # not in the supported set
+        # a non-blocking failure is counted, never silently lost
+        c.emulate_call(G.SYS_pwrite64, [987654, buf, 64, 0], flags=0)
+        c.drain(2_000_000_000)
+        st = c.stats()
+        assert st["failed"] == 3 and st["nonblocking_failed"] == 1
+
+
+def test_any_syscall_flag():
+    with _ctx(any_syscall=True) as c:
+        assert c.emulate_call(G.SYS_getpid) == os.getpid()
+        assert c.emulate_call(102) == os.getuid()                  # SYS_getuid passes through
+
+
+@pytest.mark.parametrize("merge", [True, False])
+def test_concurrent_contiguous_pwrites_merge(tmp_path, merge):
+    """Many emulated lanes write their 64-byte pieces; with merging the service
+    issues fewer Linux calls, and the file is the same either way."""
+    n = 4096
+    p = str(tmp_path / "m.bin")
+    want = workloads.stream_bytes(workloads.SEED_C2, n * 64)
+    with _ctx(merge=merge, coalesce_window_ns=200_000, n_slots=1024) as c:
+        buf = c.staging(n * 64)
+        c.host_view(buf, n * 64)[:] = np.frombuffer(want, np.uint8)
+        fd = os.open(p, os.O_CREAT | os.O_TRUNC | os.O_RDWR, 0o644)
+        errs = []
+
+        def lane(t0, step):
+            for gid in range(t0, n, step):
+                r = c.emulate_call(G.SYS_pwrite64, [fd, buf + gid * 64, 64, gid * 64], flags=0)
+                if r != 0:
+                    errs.append(r)
+
+        th = [threading.Thread(target=lane, args=(i, 8)) for i in range(8)]
+        [t.start() for t in th]
+        [t.join() for t in th]
+        c.drain(5_000_000_000)
+        os.close(fd)
+        st = c.stats()
+        assert not errs
+        assert st["requests"] == n and st["failed"] == 0
+        if merge:
+            assert st["os_calls"] <= n
+        else:
+            assert st["os_calls"] == n
+    assert open(p, "rb").read() == want
+
+
+def test_ring_wraps_many_times():
+    # 256 slots, 2 rings of 256 entries: 20k calls wrap each ring ~40 times
+    with _ctx(n_slots=256) as c:
+        errs = []
+
+        def lane(k):
+            for i in range(2500):
+                if c.emulate_call(G.NR_NOP, [k * 100000 + i]) != k * 100000 + i:
+                    errs.append(i)
+
+        th = [threading.Thread(target=lane, args=(k,)) for k in range(8)]
+        [t.start() for t in th]
+        [t.join() for t in th]
+        assert not errs
+        assert c.stats()["requests"] == 20000
+
+
+def test_no_threads_mode_is_driven_by_service():
+    with _ctx(no_threads=True) as c:
+        out = {}
+
+        def caller():
+            out["r"] = c.emulate_call(G.NR_NOP, [42])
+
+        t = threading.Thread(target=caller)
+        t.start()
+        n = 0
+        for _ in range(200):
+            n += c.service(1_000_000)
+            if n:
+                break
+        t.join()
+        assert out["r"] == 42 and n == 1
+
+
+def test_stalled_service_makes_the_caller_time_out():
+    # nobody services the rings: the caller's bounded wait gives up
+    with _ctx(no_threads=True, deadline_ns=50_000_000) as c:
+        with pytest.raises(G.GenesysError) as e:
+            c.emulate_call(G.NR_NOP, [1])
+        assert e.value.code == G.ETIMEDOUT
+        # the request is still published; a late service completes it and the
+        # slot becomes reusable
+        assert c.service(5_000_000) >= 1
+        assert c.emulate_call(G.NR_NOP, [2], flags=0) == 0
+        assert c.service(5_000_000) >= 1
+
+
+def test_drain_waits_for_nonblocking_calls(tmp_path):
+    p = str(tmp_path / "d.bin")
+    with _ctx() as c:
+        buf = c.staging(64 * 100)
+        c.host_view(buf, 6400)[:] = 7
+        fd = os.open(p, os.O_CREAT | os.O_RDWR, 0o644)
+        for i in range(100):
+            assert c.emulate_call(G.SYS_pwrite64, [fd, buf + 64 * i, 64, 64 * i], flags=0) == 0
+        c.drain(5_000_000_000)
+        os.close(fd)
+    assert open(p, "rb").read() == b"\x07" * 6400
+
+
+def test_staging_arena_bounds():
+    with _ctx(staging_bytes=4096) as c:
+        a = c.staging(1000)
+        b = c.staging(1000)
+        assert a % 256 == 0 and b % 256 == 0 and b - a == 1024
+        with pytest.raises(G.GenesysError):
+            c.staging(4096)
+        c.staging_reset()
+        assert c.staging(4096) == a
+
+
+def test_bad_configs():
+    with pytest.raises(G.GenesysError):
+        G.Context(host_only=True, service_threads=0)
+    with pytest.raises(G.GenesysError):
+        G.Context(host_only=True, deadline_ns=0)
+
+
+def test_host_only_context_cannot_launch():
+    import ctypes
+    with _ctx() as c:
+        one = (ctypes.c_uint32 * 3)(1, 1, 1)
+        rc = G.lib().genesys_launch(c.handle, ctypes.c_void_p(1), one, one, 0, None, 0, None)
+        assert rc == G.EINVAL
