@@ -125,6 +125,12 @@ int genesys_device_view(genesys_ctx *ctx, genesys_dev *out);
 int genesys_launch(genesys_ctx *ctx, const void *kernel, const uint32_t grid[3], const uint32_t block[3],
                    size_t smem_bytes, void **args, uint32_t flags, void *stream);
 
+/* Device time (ms) of the kernel of the most recent genesys_launch, from CUDA
+ * events recorded immediately before and after it on its stream.  For
+ * non-blocking calls the kernel can end before the CPU has processed them;
+ * genesys_drain covers the rest. */
+int genesys_last_launch_ms(genesys_ctx *ctx, float *ms);
+
 /* With GENESYS_INIT_NO_THREADS: process ready requests on the calling thread
  * for up to timeout_ns; returns the number of requests processed.  With
  * service threads: waits up to timeout_ns for all published requests to be

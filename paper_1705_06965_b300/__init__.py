@@ -40,7 +40,7 @@ EXPORTS = [
     "genesys_config_default", "genesys_init", "genesys_shutdown", "genesys_device_view", "genesys_launch",
     "genesys_service", "genesys_drain", "genesys_stats_get", "genesys_stats_reset", "genesys_status",
     "genesys_latency", "genesys_staging", "genesys_staging_reset", "genesys_last_error", "genesys_emulate_call",
-    "genesys_c1_histogram", "genesys_c2_pwrite", "genesys_visibility_probe",
+    "genesys_c1_histogram", "genesys_c2_pwrite", "genesys_visibility_probe", "genesys_last_launch_ms",
 ]
 
 
@@ -106,6 +106,7 @@ def lib() -> ctypes.CDLL:
         "genesys_c1_histogram": (ctypes.c_int, [vp, ctypes.c_int, u64, u64, u32, u32, u32, vp, u64, vp, vp]),
         "genesys_c2_pwrite": (ctypes.c_int, [vp, ctypes.c_int, u64, u32, u32, u32, u32, u64, vp, u64, vp]),
         "genesys_visibility_probe": (ctypes.c_int, [vp, u64, u32, u32, u32, u64, vp, vp, vp]),
+        "genesys_last_launch_ms": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -235,6 +236,12 @@ class Context:
         _check(lib().genesys_latency(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), cap,
                                      ctypes.byref(n), 1 if clear else 0), "genesys_latency")
         return out[:min(n.value, cap)]
+
+    def last_launch_ms(self) -> float:
+        """Device time of the last launched kernel (CUDA events around it)."""
+        ms = ctypes.c_float()
+        _check(lib().genesys_last_launch_ms(self.handle, ctypes.byref(ms)), "genesys_last_launch_ms")
+        return float(ms.value)
 
     def emulate_call(self, nr: int, args=(), flags: int = REQ_BLOCKING) -> int:
         a = (ctypes.c_uint64 * 6)(*[int(x) & ((1 << 64) - 1) for x in list(args) + [0] * (6 - len(args))])

@@ -136,6 +136,7 @@ struct genesys_ctx {
   std::unordered_map<uintptr_t, std::pair<void *, size_t>> maps;  // device address -> host mapping
 
   cudaStream_t aux = nullptr;  // private stream for small copies
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr;  // around the last launched kernel
 };
 
 namespace {
@@ -501,6 +502,8 @@ void free_all(genesys_ctx *c) {
   dev_free(c, c->lat);
   dev_free(c, c->lat_count);
   if (c->aux) cudaStreamDestroy(c->aux);
+  if (c->ev_start) cudaEventDestroy(c->ev_start);
+  if (c->ev_end) cudaEventDestroy(c->ev_end);
   {
     std::lock_guard<std::mutex> g(c->map_mu);
     for (auto &kv : c->maps) {
@@ -578,6 +581,8 @@ int genesys_init(const genesys_config *cfg_in, int device, genesys_ctx **out) {
     if (!mapped) return fail(GENESYS_ENODEV, "device cannot map host memory");
     c->n_sms = (uint32_t)sms;
     CUDA_TRY(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreate(&c->ev_start));
+    CUDA_TRY(cudaEventCreate(&c->ev_end));
   } else {
     c->n_sms = 0;
   }
@@ -710,14 +715,24 @@ int genesys_launch(genesys_ctx *c, const void *kernel, const uint32_t grid[3], c
                   (unsigned long long)nblocks, per_sm, c->n_sms);
   }
   if (gran == GENESYS_GRAN_KERNEL) CUDA_TRY(cudaMemsetAsync(c->ksite, 0, GENESYS_KSITES * sizeof(genesys_ksite), s));
+  CUDA_TRY(cudaEventRecord(c->ev_start, s));
   if (coop)
     CUDA_TRY(cudaLaunchCooperativeKernel(kernel, g, b, args, smem, s));
   else
     CUDA_TRY(cudaLaunchKernel(kernel, g, b, args, smem, s));
+  CUDA_TRY(cudaEventRecord(c->ev_end, s));
   if (flags & GENESYS_LAUNCH_SYNC) {
     CUDA_TRY(cudaStreamSynchronize(s));
     return genesys_drain(c, 10ull * c->cfg.device_deadline_ns);
   }
+  return 0;
+}
+
+int genesys_last_launch_ms(genesys_ctx *c, float *ms) {
+  if (!c || !ms) return fail(GENESYS_EINVAL, "NULL argument");
+  if (c->host_only) return fail(GENESYS_EINVAL, "host-only context has no launches");
+  CUDA_TRY(cudaEventSynchronize(c->ev_end));
+  CUDA_TRY(cudaEventElapsedTime(ms, c->ev_start, c->ev_end));
   return 0;
 }
 

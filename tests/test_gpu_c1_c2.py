@@ -78,7 +78,7 @@ def test_c1_empty_and_errors(ctx, G, tmp_path):
     hist = torch.zeros(256, dtype=torch.int32, device="cuda")
     st = ctx.staging(4096)
     with pytest.raises(G.GenesysError) as e:
-        ctx.c1_histogram(3, 4096, hist.data_ptr(), st, 4096, chunk=4000, groups=1, threads=64)
+        ctx.c1_histogram(3, 4096, hist.data_ptr(), st, 4096, chunk=4008, groups=1, threads=64)
     assert e.value.code == G.EINVAL        # chunk not a multiple of 16
     # a file shorter than announced: preads return short, the histogram
     # covers the bytes that exist
