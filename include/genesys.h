@@ -203,6 +203,24 @@ int genesys_c2_pwrite(genesys_ctx *ctx, int fd, uint64_t n_threads, uint32_t gra
                       uint32_t order_relaxed, uint32_t nonblocking, uint64_t seed, void *staging,
                       uint64_t staging_bytes, void *stream);
 
+/* C3, wordcount (Sec. 7.1): count whole-token occurrences of nq query words
+ * (queries16[q*16 ..], qlen[q] bytes, 1..16 bytes, at most 64 queries; host
+ * arrays) in n_files open files (fds[f], file_bytes[f]; host arrays).  A token
+ * is a maximal run of bytes other than ' ' and '\n'.  One persistent kernel of
+ * `ctas` blocks x `threads` pulls (file, chunk)-sized work items from a queue
+ * and reads each with pread at work-group grain: GENESYS_FORM_PLAIN blocking
+ * and strongly ordered, GENESYS_FORM_BATCHED relaxed and non-blocking with the
+ * next item's read in flight while the current one is scanned.  Counts are
+ * added into counts_dev[nq] (device, uint64).  staging: host-mapped,
+ * >= ctas * (chunk + 64) * (BATCHED ? 2 : 1) bytes; chunk a multiple of 16.
+ * The work-item list lives in a context-owned device scratch buffer. */
+#define GENESYS_C3_MAX_QUERIES   64
+#define GENESYS_C3_MAX_QUERY_LEN 16
+int genesys_c3_wordcount(genesys_ctx *ctx, const int32_t *fds, const uint64_t *file_bytes, uint32_t n_files,
+                         const uint8_t *queries16, const uint8_t *qlen, uint32_t nq, uint64_t chunk, uint32_t ctas,
+                         uint32_t threads, uint32_t form, void *staging, uint64_t staging_bytes,
+                         unsigned long long *counts_dev, void *stream);
+
 /* Strong-ordering visibility probe (Sec. 4.1: strong ordering means every
  * store before the call has completed): n_threads threads each store their
  * 8-byte word splitmix64_at(seed, gid) into probe[gid] (host-mapped), then a

@@ -41,6 +41,7 @@ EXPORTS = [
     "genesys_service", "genesys_drain", "genesys_stats_get", "genesys_stats_reset", "genesys_status",
     "genesys_latency", "genesys_staging", "genesys_staging_reset", "genesys_last_error", "genesys_emulate_call",
     "genesys_c1_histogram", "genesys_c2_pwrite", "genesys_visibility_probe", "genesys_last_launch_ms",
+    "genesys_c3_wordcount",
 ]
 
 
@@ -107,6 +108,7 @@ def lib() -> ctypes.CDLL:
         "genesys_c2_pwrite": (ctypes.c_int, [vp, ctypes.c_int, u64, u32, u32, u32, u32, u64, vp, u64, vp]),
         "genesys_visibility_probe": (ctypes.c_int, [vp, u64, u32, u32, u32, u64, vp, vp, vp]),
         "genesys_last_launch_ms": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float)]),
+        "genesys_c3_wordcount": (ctypes.c_int, [vp, vp, vp, u32, vp, vp, u32, u64, u32, u32, u32, vp, u64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -262,6 +264,23 @@ class Context:
         _check(lib().genesys_c2_pwrite(self.handle, fd, n_threads, gran, group_threads, 1 if relaxed else 0,
                                        1 if nonblocking else 0, seed, staging, staging_bytes,
                                        _stream_handle(stream)), "genesys_c2_pwrite")
+
+    def c3_wordcount(self, fds, file_bytes, queries, counts_dev_ptr: int, staging: int, staging_bytes: int,
+                     chunk: int = 1 << 20, ctas: int = 296, threads: int = 512, form: int = FORM_BATCHED,
+                     stream=None) -> None:
+        """fds/file_bytes: sequences; queries: list of bytes (1..16 each)."""
+        f = np.ascontiguousarray(np.asarray(fds, dtype=np.int32))
+        sz = np.ascontiguousarray(np.asarray(file_bytes, dtype=np.uint64))
+        q = np.zeros((max(len(queries), 1), 16), np.uint8)
+        ql = np.zeros(max(len(queries), 1), np.uint8)
+        for i, s in enumerate(queries):
+            m = min(len(s), 16)                # longer queries are passed on for the library to reject
+            q[i, :m] = np.frombuffer(s[:m], np.uint8)
+            ql[i] = min(len(s), 255)
+        _check(lib().genesys_c3_wordcount(self.handle, f.ctypes.data, sz.ctypes.data, len(f), q.ctypes.data,
+                                          ql.ctypes.data, len(queries), chunk, ctas, threads, form, staging,
+                                          staging_bytes, counts_dev_ptr, _stream_handle(stream)),
+               "genesys_c3_wordcount")
 
     def visibility_probe(self, n_threads: int, gran: int, group_threads: int, relaxed: bool, seed: int,
                          probe: int, violations_dev_ptr: int, stream=None) -> None:

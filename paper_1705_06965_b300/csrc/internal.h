@@ -1,6 +1,8 @@
 // Internal helpers shared by the runtime and the workload entry points.
 #pragma once
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -8,6 +10,13 @@ extern "C" {
 /* Record `msg` as the calling thread's last error (genesys_last_error) and
  * return `code`. */
 int genesys_internal_error(int code, const char *msg);
+
+struct genesys_ctx;
+/* Device scratch arena owned by the context: returns (in *out) at least
+ * `bytes` of device memory, growing the arena with cudaMalloc when needed.
+ * The memory is reused by the next call; callers must be done with it (the
+ * workload entry points synchronise before returning). */
+int genesys_internal_scratch(struct genesys_ctx *ctx, size_t bytes, void **out);
 
 #ifdef __cplusplus
 }

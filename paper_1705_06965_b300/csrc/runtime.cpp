@@ -137,6 +137,9 @@ struct genesys_ctx {
 
   cudaStream_t aux = nullptr;  // private stream for small copies
   cudaEvent_t ev_start = nullptr, ev_end = nullptr;  // around the last launched kernel
+
+  void *scratch = nullptr;  // device scratch arena for workload entry points
+  size_t scratch_bytes = 0;
 };
 
 namespace {
@@ -501,6 +504,7 @@ void free_all(genesys_ctx *c) {
   dev_free(c, c->status);
   dev_free(c, c->lat);
   dev_free(c, c->lat_count);
+  if (c->scratch && !c->host_only) cudaFree(c->scratch);
   if (c->aux) cudaStreamDestroy(c->aux);
   if (c->ev_start) cudaEventDestroy(c->ev_start);
   if (c->ev_end) cudaEventDestroy(c->ev_end);
@@ -538,6 +542,24 @@ extern "C" {
 const char *genesys_last_error(void) { return g_last_error.c_str(); }
 
 int genesys_internal_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
+int genesys_internal_scratch(genesys_ctx *c, size_t bytes, void **out) {
+  if (!c || !out) return fail(GENESYS_EINVAL, "NULL argument");
+  if (c->host_only) return fail(GENESYS_EINVAL, "host-only context has no device scratch");
+  if (bytes > c->scratch_bytes) {
+    if (c->scratch) {
+      CUDA_TRY(cudaDeviceSynchronize());
+      CUDA_TRY(cudaFree(c->scratch));
+      c->scratch = nullptr;
+      c->scratch_bytes = 0;
+    }
+    const size_t grow = std::max<size_t>(bytes, 1u << 20);
+    CUDA_TRY(cudaMalloc(&c->scratch, grow));
+    c->scratch_bytes = grow;
+  }
+  *out = c->scratch;
+  return 0;
+}
 
 int genesys_config_default(genesys_config *cfg) {
   if (!cfg) return fail(GENESYS_EINVAL, "cfg is NULL");
