@@ -221,6 +221,33 @@ int genesys_c3_wordcount(genesys_ctx *ctx, const int32_t *fds, const uint64_t *f
                          uint32_t threads, uint32_t form, void *staging, uint64_t staging_bytes,
                          unsigned long long *counts_dev, void *stream);
 
+/* Allocation-free variant of genesys_c3_wordcount (the paper has no
+ * counterpart; this is a service for callers).  Some callers cannot allocate
+ * device memory while they run: a process that must keep a fixed device
+ * footprint after start-up, or a code path where a cudaMalloc/cudaFree - which
+ * can synchronise the whole device - is not acceptable.  This entry point
+ * makes no cudaMalloc, cudaFree or other allocating call: its per-call device
+ * scratch (queue head, query table, work-item list) is a file-scope device
+ * array of GENESYS_C3_NOALLOC_SCRATCH_BYTES (about 1 MiB) that every GPU which
+ * loads the library holds until the process exits.  The caller still passes
+ * all inputs and outputs, with the same meaning as for genesys_c3_wordcount.
+ *   - Limit: at most GENESYS_C3_NOALLOC_MAX_ITEMS work items, where a file of
+ *     n bytes takes ceil(n / chunk) of them; more returns GENESYS_EINVAL with
+ *     a message saying so.
+ *   - Set-up: the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current, and keeps it; make that
+ *     first call before any stream capture.
+ *   - Sharing: every call uses the same array, which keeps the last call's
+ *     contents (each call rewrites the part it reads, queue head included).
+ *     Calls are serialised on the host and each waits for its kernel, but
+ *     calls whose kernels overlap on the GPU would race on the array. */
+#define GENESYS_C3_NOALLOC_MAX_ITEMS 32768u
+#define GENESYS_C3_NOALLOC_SCRATCH_BYTES (1536u + GENESYS_C3_NOALLOC_MAX_ITEMS * 32u)
+int genesys_c3_wordcount_noalloc(genesys_ctx *ctx, const int32_t *fds, const uint64_t *file_bytes,
+                                 uint32_t n_files, const uint8_t *queries16, const uint8_t *qlen, uint32_t nq,
+                                 uint64_t chunk, uint32_t ctas, uint32_t threads, uint32_t form, void *staging,
+                                 uint64_t staging_bytes, unsigned long long *counts_dev, void *stream);
+
 /* Strong-ordering visibility probe (Sec. 4.1: strong ordering means every
  * store before the call has completed): n_threads threads each store their
  * 8-byte word splitmix64_at(seed, gid) into probe[gid] (host-mapped), then a

@@ -41,7 +41,7 @@ EXPORTS = [
     "genesys_service", "genesys_drain", "genesys_stats_get", "genesys_stats_reset", "genesys_status",
     "genesys_latency", "genesys_staging", "genesys_staging_reset", "genesys_last_error", "genesys_emulate_call",
     "genesys_c1_histogram", "genesys_c2_pwrite", "genesys_visibility_probe", "genesys_last_launch_ms",
-    "genesys_c3_wordcount",
+    "genesys_c3_wordcount", "genesys_c3_wordcount_noalloc",
 ]
 
 
@@ -109,6 +109,8 @@ def lib() -> ctypes.CDLL:
         "genesys_visibility_probe": (ctypes.c_int, [vp, u64, u32, u32, u32, u64, vp, vp, vp]),
         "genesys_last_launch_ms": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float)]),
         "genesys_c3_wordcount": (ctypes.c_int, [vp, vp, vp, u32, vp, vp, u32, u64, u32, u32, u32, vp, u64, vp, vp]),
+        "genesys_c3_wordcount_noalloc": (ctypes.c_int, [vp, vp, vp, u32, vp, vp, u32, u64, u32, u32, u32, vp, u64,
+                                                         vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -18,6 +18,9 @@ struct genesys_ctx;
  * workload entry points synchronise before returning). */
 int genesys_internal_scratch(struct genesys_ctx *ctx, size_t bytes, void **out);
 
+/* CUDA device ordinal of the context (-1 for NULL). */
+int genesys_internal_device(struct genesys_ctx *ctx);
+
 #ifdef __cplusplus
 }
 #endif

@@ -543,6 +543,8 @@ const char *genesys_last_error(void) { return g_last_error.c_str(); }
 
 int genesys_internal_error(int code, const char *msg) { return fail(code, "%s", msg); }
 
+int genesys_internal_device(genesys_ctx *c) { return c ? c->device : -1; }
+
 int genesys_internal_scratch(genesys_ctx *c, size_t bytes, void **out) {
   if (!c || !out) return fail(GENESYS_EINVAL, "NULL argument");
   if (c->host_only) return fail(GENESYS_EINVAL, "host-only context has no device scratch");

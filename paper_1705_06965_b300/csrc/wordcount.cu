@@ -334,3 +334,139 @@ int genesys_c3_wordcount(genesys_ctx *c, const int32_t *fds, const uint64_t *fil
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free wordcount.  Same kernels as genesys_c3_wordcount, but the
+// per-call device scratch (queue head, query table, work-item list) lives in
+// a fixed file-scope device array instead of memory obtained with cudaMalloc,
+// for callers that must not allocate device memory while they run.
+namespace {
+
+constexpr uint32_t kStaticMaxItems = GENESYS_C3_NOALLOC_MAX_ITEMS;
+constexpr size_t kStaticQOff = 256;
+constexpr size_t kStaticItemsOff = (kStaticQOff + sizeof(C3Queries) + 255) & ~size_t(255);
+constexpr size_t kStaticBytes = kStaticItemsOff + (size_t)kStaticMaxItems * sizeof(C3Item);
+constexpr int kStaticMaxDevices = 64;
+static_assert(kStaticBytes == GENESYS_C3_NOALLOC_SCRATCH_BYTES, "documented scratch size");
+
+// Every device that loads this library holds this array until the process
+// exits.  Host code must not pass `g_c3_noalloc_scratch` itself to a kernel:
+// on the host it names a stand-in object, not the device address, which is
+// looked up with cudaGetSymbolAddress (below) once per device.
+static __device__ __align__(256) unsigned char g_c3_noalloc_scratch[kStaticBytes];
+
+// Host image of the same layout, copied to the device array on each call.
+static unsigned char g_c3_noalloc_host[kStaticBytes];
+static std::mutex g_c3_noalloc_mu;
+static void *g_c3_noalloc_dev_addr[kStaticMaxDevices];
+
+}  // namespace
+
+extern "C" int genesys_c3_wordcount_noalloc(genesys_ctx *c, const int32_t *fds, const uint64_t *file_bytes,
+                                            uint32_t n_files, const uint8_t *queries16, const uint8_t *qlen,
+                                            uint32_t nq, uint64_t chunk, uint32_t ctas, uint32_t threads,
+                                            uint32_t form, void *staging, uint64_t staging_bytes,
+                                            unsigned long long *counts_dev, void *stream) {
+  if (!c || !fds || !file_bytes || !queries16 || !qlen || !staging || !counts_dev)
+    return set_err(GENESYS_EINVAL, "NULL argument");
+  if (nq == 0 || nq > (uint32_t)kMaxQ) return set_err(GENESYS_EINVAL, "1..64 queries");
+  for (uint32_t q = 0; q < nq; ++q)
+    if (qlen[q] == 0 || qlen[q] > kHalo) return set_err(GENESYS_EINVAL, "query length must be 1..16");
+  if (chunk < 64 || chunk % 16 || chunk > (1u << 30)) return set_err(GENESYS_EINVAL, "chunk: multiple of 16, >= 64");
+  if (ctas == 0 || threads < 32 || threads > 1024 || threads % 32) return set_err(GENESYS_EINVAL, "bad launch shape");
+  if ((uintptr_t)staging % 16) return set_err(GENESYS_EINVAL, "staging must be 16-byte aligned");
+  const uint64_t buf_bytes = chunk + 64;
+  const uint64_t need = (uint64_t)ctas * buf_bytes * (form == GENESYS_FORM_BATCHED ? 2 : 1);
+  if (staging_bytes < need) return set_err(GENESYS_EINVAL, "staging too small: ctas * (chunk + 64) per buffer");
+  uint64_t n_items = 0;
+  for (uint32_t f = 0; f < n_files; ++f) {
+    if (fds[f] < 0) return set_err(GENESYS_EINVAL, "bad fd");
+    n_items += (file_bytes[f] + chunk - 1) / chunk;
+  }
+  if (n_items > kStaticMaxItems) {
+    char msg[200];
+    snprintf(msg, sizeof msg,
+             "the files need %llu work items of %llu bytes; the allocation-free wordcount holds at most %u "
+             "(use a larger chunk or genesys_c3_wordcount)",
+             (unsigned long long)n_items, (unsigned long long)chunk, kStaticMaxItems);
+    return set_err(GENESYS_EINVAL, msg);
+  }
+  if (n_items == 0) return 0;
+  const int dev = genesys_internal_device(c);
+  if (dev < 0 || dev >= kStaticMaxDevices) return set_err(GENESYS_EINVAL, "device ordinal out of range");
+
+  std::lock_guard<std::mutex> lock(g_c3_noalloc_mu);
+  if (!g_c3_noalloc_dev_addr[dev]) {
+    // one-time set-up on this device: the device address of the array
+    if (cudaSetDevice(dev) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(GENESYS_ECUDA, "cudaSetDevice failed");
+    }
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_c3_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      char msg[160];
+      snprintf(msg, sizeof msg, "cudaGetSymbolAddress(g_c3_noalloc_scratch): %s", cudaGetErrorString(e));
+      return set_err(GENESYS_ECUDA, msg);
+    }
+    g_c3_noalloc_dev_addr[dev] = p;
+  }
+  unsigned char *h = g_c3_noalloc_host;
+  memset(h, 0, kStaticItemsOff);  // queue head starts at 0; unused query entries are 0
+  C3Queries *q = reinterpret_cast<C3Queries *>(h + kStaticQOff);
+  q->nq = nq;
+  for (uint32_t i = 0; i < nq; ++i) {
+    uint8_t tmp[16] = {0};
+    memcpy(tmp, queries16 + 16 * i, qlen[i]);
+    memcpy(&q->w[i][0], tmp, 8);
+    memcpy(&q->w[i][1], tmp + 8, 8);
+    q->len[i] = qlen[i];
+  }
+  C3Item *hi = reinterpret_cast<C3Item *>(h + kStaticItemsOff);
+  uint32_t n = 0;
+  for (uint32_t f = 0; f < n_files; ++f) {
+    for (uint64_t off = 0; off < file_bytes[f]; off += chunk) {
+      C3Item it{};
+      it.fd = fds[f];
+      it.len = (uint32_t)(file_bytes[f] - off < chunk ? file_bytes[f] - off : chunk);
+      it.off = off;
+      it.fsize = file_bytes[f];
+      hi[n++] = it;
+    }
+  }
+  unsigned char *scratch = (unsigned char *)g_c3_noalloc_dev_addr[dev];
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(scratch, h, kStaticItemsOff + (size_t)n * sizeof(C3Item), cudaMemcpyHostToDevice, s) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return set_err(GENESYS_ECUDA, "upload of work items failed");
+  }
+  genesys_dev g;
+  genesys_device_view(c, &g);
+  const C3Item *d_items = (const C3Item *)(scratch + kStaticItemsOff);
+  uint32_t *head = (uint32_t *)scratch;
+  const C3Queries *d_q = (const C3Queries *)(scratch + kStaticQOff);
+  uint8_t *st = (uint8_t *)staging;
+  uint64_t bb = buf_bytes;
+  uint32_t tile_bytes = threads * 16;
+  void *args[] = {&g, &d_items, &n, &head, &d_q, &st, &bb, &tile_bytes, &counts_dev};
+  const size_t smem = tile_bytes + 48;
+  const void *k = form == GENESYS_FORM_BATCHED ? (const void *)&c3_batched_kernel : (const void *)&c3_plain_kernel;
+  const uint32_t flags = form == GENESYS_FORM_BATCHED
+                             ? (GENESYS_GRAN_GROUP | GENESYS_LAUNCH_RELAXED | GENESYS_LAUNCH_NONBLOCKING)
+                             : GENESYS_GRAN_GROUP;
+  const uint32_t g3[3] = {ctas, 1, 1}, b3[3] = {threads, 1, 1};
+  int rc = genesys_launch(c, k, g3, b3, smem, args, flags | GENESYS_LAUNCH_SYNC, stream);
+  if (rc) return rc;
+  int32_t stw[GENESYS_ST_WORDS];
+  rc = genesys_status(c, stw, 1);
+  if (rc) return rc;
+  if (stw[GENESYS_ST_TIMEOUTS] || stw[GENESYS_ST_FAILED_CALLS] || stw[GENESYS_ST_FIRST_ERROR]) {
+    char msg[160];
+    snprintf(msg, sizeof msg, "device-side calls failed: first error %d, %d timeouts, %d failed calls",
+             stw[GENESYS_ST_FIRST_ERROR], stw[GENESYS_ST_TIMEOUTS], stw[GENESYS_ST_FAILED_CALLS]);
+    return set_err(GENESYS_EDEVICE, msg);
+  }
+  return 0;
+}
