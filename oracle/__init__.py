@@ -51,6 +51,11 @@ def _L():
         L.oracle_c3_wordcount_omp.restype = ctypes.c_int64
         L.oracle_c3_wordcount_omp.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int]
+        L.oracle_c5_checksum.restype = ctypes.c_uint64
+        L.oracle_c5_checksum.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
+        L.oracle_c5_request.restype = ctypes.c_int64
+        L.oracle_c5_request.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_int32,
+                                        ctypes.c_void_p]
         _lib = L
     return _lib
 
@@ -115,3 +120,39 @@ def c3_wordcount(paths, queries, chunk: int = 1 << 20, per_file: bool = False, t
                                           counts.ctypes.data, pf.ctypes.data if per_file else None),
                  "c3_wordcount")
     return (counts, tot, pf) if per_file else (counts, tot)
+
+
+def c5_checksum(data: bytes) -> int:
+    """C5 checksum: sum mod 2^64 of splitmix64's output function applied to
+    w_i + (i+1)*gamma over the little-endian 64-bit words w_i (zero padded)."""
+    buf = ctypes.create_string_buffer(data, max(len(data), 1))
+    return int(_L().oracle_c5_checksum(buf, len(data)))
+
+
+def c5_request(ops, n_ops: int, in_fds, out_fd: int) -> np.ndarray:
+    """C5 (Sec. 7 file and memory calls): run one request's operations in order
+    (pread+checksum, pwrite of a seeded stream, mmap-fill-checksum-munmap);
+    returns one uint64 result per operation."""
+    ops = np.ascontiguousarray(ops)
+    fds = np.ascontiguousarray(np.asarray(in_fds, dtype=np.int32))
+    res = np.zeros(max(n_ops, 1), np.uint64)
+    _check(_L().oracle_c5_request(ops.ctypes.data, n_ops, fds.ctypes.data, out_fd, res.ctypes.data), "c5_request")
+    return res[:n_ops]
+
+
+def c5_trace(trace, out_fd: int, in_fds=None) -> np.ndarray:
+    """All requests of a trace in arrival order; results [n, 8] (unused ops 0)."""
+    import os as _os
+    own = in_fds is None
+    if own:
+        in_fds = [_os.open(p, _os.O_RDONLY) for p in trace.in_paths]
+    try:
+        out = np.zeros((len(trace), 8), np.uint64)
+        for r in range(len(trace)):
+            n = int(trace.n_ops[r])
+            out[r, :n] = c5_request(trace.ops[r], n, in_fds, out_fd)
+        return out
+    finally:
+        if own:
+            for fd in in_fds:
+                _os.close(fd)

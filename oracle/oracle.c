@@ -16,6 +16,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <sys/mman.h>
 #include <unistd.h>
 
 /* ------------------------------------------------------------------ common */
@@ -227,4 +228,74 @@ int64_t oracle_c3_wordcount_omp(const char **paths, int n_files, const uint8_t *
     free(buf); free(fc); free(mine);
   }
   return err ? err : total;
+}
+
+/* ---------------------------------------------------------------------- C5
+ * Mixed trace of GPU kernels making file and memory system calls (Sec. 7:
+ * the filesystem calls pread/pwrite and the memory calls mmap/munmap of the
+ * paper's 11-call set, Sec. 8.1).  Each request is a list of operations, run
+ * in order:
+ *   kind 0  pread  `len` bytes of input file `file` at `off`; result: the
+ *           checksum of the bytes read;
+ *   kind 1  pwrite `len` bytes of the stream of `seed` to the output file at
+ *           `out_off`; result: the byte count written;
+ *   kind 2  mmap an anonymous `len`-byte region, fill word i with
+ *           splitmix64_at(seed, i), checksum the region, munmap it; result:
+ *           the checksum.
+ * Checksum of a byte string (zero padded to whole 64-bit little-endian words
+ * w_0, w_1, ...): the sum mod 2^64 of splitmix64's output function applied to
+ * w_i + (i + 1) * 0x9E3779B97F4A7C15 - i.e. for an all-zero string, the sum of
+ * the first outputs of splitmix64 started at 0.  A sum, so any partition of
+ * the string can be checksummed in parallel. */
+typedef struct oracle_c5_op {
+  uint32_t kind, file;
+  uint64_t off, len, seed, out_off;
+} oracle_c5_op;
+
+static uint64_t sm_out(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+uint64_t oracle_c5_checksum(const uint8_t *buf, uint64_t len) {
+  uint64_t s = 0;
+  for (uint64_t i = 0; 8 * i < len; ++i) {
+    uint64_t w = 0;
+    for (uint64_t b = 0; b < 8 && 8 * i + b < len; ++b) w |= (uint64_t)buf[8 * i + b] << (8 * b);
+    s += sm_out(w + (i + 1) * 0x9E3779B97F4A7C15ULL);
+  }
+  return s;
+}
+
+/* results[k] receives operation k's result (or -errno as uint64). */
+int64_t oracle_c5_request(const oracle_c5_op *ops, uint32_t n_ops, const int32_t *in_fds, int32_t out_fd,
+                          uint64_t *results) {
+  for (uint32_t k = 0; k < n_ops; ++k) {
+    const oracle_c5_op *op = &ops[k];
+    if (op->kind == 0) {
+      uint8_t *buf = (uint8_t *)malloc(op->len ? op->len : 1);
+      if (!buf) return -ENOMEM;
+      int64_t r = pread_full(in_fds[op->file], buf, op->len, op->off);
+      results[k] = r < 0 ? (uint64_t)r : oracle_c5_checksum(buf, (uint64_t)r);
+      free(buf);
+    } else if (op->kind == 1) {
+      uint8_t *buf = (uint8_t *)malloc(op->len ? op->len : 1);
+      if (!buf) return -ENOMEM;
+      for (uint64_t b = 0; b < op->len; ++b)
+        buf[b] = (uint8_t)(oracle_splitmix64_at(op->seed, b >> 3) >> (8 * (b & 7)));
+      int64_t r = pwrite_full(out_fd, buf, op->len, op->out_off);
+      results[k] = (uint64_t)r;
+      free(buf);
+    } else if (op->kind == 2) {
+      uint64_t *p = (uint64_t *)mmap(NULL, op->len, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+      if (p == MAP_FAILED) { results[k] = (uint64_t)(int64_t)-errno; continue; }
+      for (uint64_t i = 0; i < op->len / 8; ++i) p[i] = oracle_splitmix64_at(op->seed, i);
+      results[k] = oracle_c5_checksum((const uint8_t *)p, op->len);
+      munmap(p, op->len);
+    } else {
+      return -EINVAL;
+    }
+  }
+  return 0;
 }

@@ -197,3 +197,77 @@ def test_c3_files_are_well_formed():
         assert re.fullmatch(rb"[a-z \n]*", data)
         assert not data.startswith((b" ", b"\n"))
         assert b"  " not in data and b"\n\n" not in data and b" \n" not in data and b"\n " not in data
+
+
+# ------------------------------------------------------------------------- C5
+
+SM0 = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]   # published, state 0
+
+
+def test_c5_checksum_zero_words_are_the_published_stream():
+    # the checksum of k zero words is the sum of the first k outputs of
+    # splitmix64 started at 0; a partial word is zero padded
+    assert oracle.c5_checksum(b"\0" * 8) == SM0[0]
+    assert oracle.c5_checksum(b"\0" * 16) == (SM0[0] + SM0[1]) % 2**64
+    assert oracle.c5_checksum(b"\0" * 24) == sum(SM0) % 2**64
+    assert oracle.c5_checksum(b"\0" * 20) == sum(SM0) % 2**64
+    assert oracle.c5_checksum(b"") == 0
+
+
+def test_c5_checksum_is_order_sensitive_and_word_local():
+    a = bytes(range(64))
+    b = bytearray(a)
+    b[8:16], b[16:24] = a[16:24], a[8:16]           # swap two words: a different sum
+    assert oracle.c5_checksum(a) != oracle.c5_checksum(bytes(b))
+    c = bytearray(a)
+    c[63] ^= 1                                       # one flipped bit changes it
+    assert oracle.c5_checksum(a) != oracle.c5_checksum(bytes(c))
+
+
+def _ops(*rows):
+    ops = np.zeros(8, workloads.C5_OP)
+    for k, r in enumerate(rows):
+        for f, v in r.items():
+            ops[k][f] = v
+    return ops
+
+
+def test_c5_ops_against_independent_paths(tmp_path):
+    src = workloads.c1_file(str(tmp_path / "in.bin"), 100_000, seed=99)
+    data = open(src, "rb").read()
+    out = str(tmp_path / "out.bin")
+    in_fd = os.open(src, os.O_RDONLY)
+    out_fd = os.open(out, os.O_CREAT | os.O_TRUNC | os.O_RDWR, 0o644)
+    try:
+        ops = _ops({"kind": 0, "file": 0, "off": 1000, "len": 5000},
+                   {"kind": 1, "len": 4099, "seed": 77, "out_off": 10},
+                   {"kind": 2, "len": 65536, "seed": 5},
+                   {"kind": 0, "file": 0, "off": 99_000, "len": 4096})      # short read at end of file
+        res = oracle.c5_request(ops, 4, [in_fd], out_fd)
+    finally:
+        os.close(in_fd)
+        os.close(out_fd)
+    # pread: the checksum of the bytes a plain file read returns
+    assert res[0] == oracle.c5_checksum(data[1000:6000])
+    assert res[3] == oracle.c5_checksum(data[99_000:])
+    # pwrite: the byte count, and the file holds the generator's stream at out_off
+    assert res[1] == 4099
+    got = open(out, "rb").read()
+    assert got[10:] == workloads.stream_bytes(77, 4099) and got[:10] == b"\0" * 10
+    # mmap fill: the checksum of the generator's stream of the same seed
+    assert res[2] == oracle.c5_checksum(workloads.stream_bytes(5, 65536))
+
+
+def test_c5_trace_shape():
+    tr = workloads.c5_trace(workloads.C5_SMALL)
+    assert len(tr) == 200
+    assert tr.threads.min() >= 64 and tr.threads.max() <= 65536
+    assert np.all(np.diff(tr.arrival_ns.astype(np.int64)) >= 0)
+    live = np.arange(8)[None, :] < tr.n_ops[:, None]
+    kinds = tr.ops["kind"][live]
+    assert set(np.unique(kinds)) <= {0, 1, 2}
+    pw = tr.ops[live & (tr.ops["kind"] == 1)]
+    ends = np.sort(pw["out_off"]) + pw["len"][np.argsort(pw["out_off"])]
+    assert np.all(np.sort(pw["out_off"])[1:] >= ends[:-1])          # disjoint pwrite ranges
+    mm = tr.ops[live & (tr.ops["kind"] == 2)]
+    assert np.all(mm["len"] % 4096 == 0) and mm["len"].min() >= 4096

@@ -175,3 +175,71 @@ def vocab_word(seed: int, vocab_n: int, idx: int) -> bytes:
     if n < 0:
         raise OSError(-n, "gen_vocab_word")
     return buf.raw[:n]
+
+
+# ------------------------------------------------------------------------ C5
+# Mixed serving trace: requests (GPU kernels) arrive as a Poisson process;
+# each has a log-uniform thread count and a list of 1..8 operations drawn
+# pread 50% / pwrite 25% / mmap-fill-munmap 25%.
+
+C5_OP = np.dtype([("kind", "<u4"), ("file", "<u4"), ("off", "<u8"), ("len", "<u8"), ("seed", "<u8"),
+                  ("out_off", "<u8")])
+C5_MAX_OPS = 8
+OP_PREAD, OP_PWRITE, OP_MMAP = 0, 1, 2
+
+C5_FULL = dict(n_requests=10000, rate_per_s=20000.0, n_files=16, file_bytes=32 << 20, seed=SEED_C5)
+C5_SMALL = dict(n_requests=200, rate_per_s=50000.0, n_files=4, file_bytes=4 << 20, seed=SEED_C5)
+
+
+@dataclass
+class Trace:
+    arrival_ns: np.ndarray     # uint64 [n]
+    threads: np.ndarray        # uint32 [n]
+    n_ops: np.ndarray          # uint32 [n]
+    ops: np.ndarray            # C5_OP [n, 8]
+    in_paths: list
+    out_bytes: int             # size of the output file (sum of pwrite lengths)
+    params: dict = field(default_factory=dict)
+
+    def __len__(self):
+        return len(self.threads)
+
+    def subset(self, idx) -> "Trace":
+        idx = np.asarray(idx)
+        return Trace(self.arrival_ns[idx], self.threads[idx], self.n_ops[idx], self.ops[idx], self.in_paths,
+                     self.out_bytes, self.params)
+
+
+def c5_trace(params: dict | None = None) -> Trace:
+    """Generate the mixed trace (numpy, seeded) and its input files on tmpfs."""
+    p = dict(C5_FULL if params is None else params)
+    rng = np.random.default_rng(p["seed"])
+    n = p["n_requests"]
+    arrival = np.cumsum(rng.exponential(1.0 / p["rate_per_s"], n)) * 1e9
+    threads = np.floor(np.exp(rng.uniform(np.log(64), np.log(65537), n))).astype(np.uint32)
+    n_ops = rng.integers(1, C5_MAX_OPS + 1, n).astype(np.uint32)
+    ops = np.zeros((n, C5_MAX_OPS), C5_OP)
+    out_off = 0
+    fb = p["file_bytes"]
+    for r in range(n):
+        for k in range(int(n_ops[r])):
+            kind = int(rng.choice(3, p=[0.5, 0.25, 0.25]))
+            op = ops[r, k]
+            op["kind"] = kind
+            op["seed"] = int(rng.integers(0, 1 << 62))
+            if kind == OP_PREAD:
+                ln = int(rng.integers(4096, 262145))
+                op["file"] = int(rng.integers(0, p["n_files"]))
+                op["len"] = ln
+                op["off"] = int(rng.integers(0, fb - ln + 1))
+            elif kind == OP_PWRITE:
+                ln = int(rng.integers(4096, 262145))
+                op["len"] = ln
+                op["out_off"] = out_off
+                out_off += ln
+            else:
+                ln = int(np.exp(rng.uniform(np.log(64 << 10), np.log((16 << 20) + 1))))
+                op["len"] = max(4096, ln // 4096 * 4096)
+    d = scratch_dir("c5_%x_%d_%d" % (p["seed"], p["n_files"], fb))
+    paths = [c1_file(os.path.join(d, f"in{f:02d}.bin"), fb, seed=p["seed"] + 1 + f) for f in range(p["n_files"])]
+    return Trace(arrival.astype(np.uint64), threads, n_ops, ops, paths, out_off, p)
