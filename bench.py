@@ -9,11 +9,14 @@ relaxed} x blocking {blocking, non-blocking} (22 combinations, 132 kernels)
 - followed by the C1 pread pass (a 4 MiB file read in 4 KiB preads by 64
 work-groups of 256 threads into a 256-bin histogram, plain and batched).
 
-value = GPU system calls retired per second over the step (device-event
-timing around the whole step; every entry point synchronises and drains, so
-the step's calls are all complete inside the timed region).
+value = GPU system calls retired per second over the step (CUDA-event timing
+around the whole step; every entry point synchronises and drains, so the
+step's calls are all complete inside the timed region).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl genesys|reference]
+    python bench.py --only c2:work-item/strong/blocking:65536   # one case (profiling)
+    python bench.py --only c1:batched:1073741824
+    python bench.py --only c3:batched
 
 --impl reference times the CPU oracle (a sequential C program issuing the
 same pwrite/pread calls) on the same workload on the host cores.
@@ -42,7 +45,8 @@ COMBOS = [(name, g, bt, relaxed, nb) for name, g, bt in GRAINS for relaxed in (F
 SEED_C2 = 0x5EED0002
 C1_BYTES, C1_CHUNK, C1_GROUPS, C1_THREADS = 4 << 20, 4096, 64, 256
 SCAN_BYTES, SCAN_CHUNK, SCAN_GROUPS, SCAN_THREADS = 1 << 30, 1 << 20, 148, 1024
-SERVICE_THREADS = 4
+C3_CHUNK, C3_CTAS, C3_THREADS = 1 << 20, 296, 512
+GRAN_BY_NAME = {name: (g, bt) for name, g, bt in GRAINS}
 
 
 def combo_key(name, relaxed, nb):
@@ -123,7 +127,7 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- helpers
 def host_link_peak(torch):
-    """Pinned cudaMemcpy H2D / D2H bandwidth at 256 MiB (best of 5), GB/s."""
+    """Pinned cudaMemcpy H2D / D2H bandwidth at 256 MiB (best of 6), GB/s."""
     n = 256 << 20
     h = torch.empty(n, dtype=torch.uint8, pin_memory=True)
     d = torch.empty(n, dtype=torch.uint8, device="cuda")
@@ -148,7 +152,7 @@ def pctl(a, q):
 
 
 def load_traffic(kernel: str):
-    """ncu host-link traffic (bytes per launch) for `kernel` from the committed
+    """ncu host-link traffic (bytes per launch) of `kernel` from the committed
     profile summary, or None if the kernel source changed since the capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.txt")
@@ -165,34 +169,304 @@ def load_traffic(kernel: str):
     return None
 
 
+class Rig:
+    """Context, files and buffers of the GPU arm."""
+
+    def __init__(self, args, local, rank, need_scan=True, service_threads=None, coalesce_max=64, need_c3=True):
+        import torch
+        import paper_1705_06965_b300 as G
+        import workloads
+        self.G, self.torch = G, torch
+        st_threads = service_threads or args.service_threads
+        self.dev = torch.device("cuda", local)
+        self.d = workloads.scratch_dir(f"bench_r{rank}")
+        self.c1_path = workloads.c1_file(os.path.join(self.d, "c1.bin"), C1_BYTES, seed=workloads.SEED_C1)
+        self.scan_path = (workloads.c1_file(os.path.join(self.d, "scan.bin"), SCAN_BYTES, seed=0x5EED00F1)
+                          if need_scan else None)
+        self.c1_stage_bytes = max(2 * C1_GROUPS * C1_CHUNK, 2 * SCAN_GROUPS * SCAN_CHUNK if need_scan else 0)
+        self.c3_stage_bytes = C3_CTAS * (C3_CHUNK + 64) * 2 if need_c3 else 0
+        self.ctx = G.Context(device=local, service_threads=st_threads, coalesce_max=coalesce_max,
+                             staging_bytes=max(SIZES) * 64 + self.c1_stage_bytes + self.c3_stage_bytes + (4 << 20),
+                             deadline_ns=10_000_000_000)
+        self.c2_stage = self.ctx.staging(max(SIZES) * 64)
+        self.c1_stage = self.ctx.staging(self.c1_stage_bytes)
+        self.c3_stage = self.ctx.staging(self.c3_stage_bytes) if need_c3 else 0
+        self.fds = {n: os.open(os.path.join(self.d, f"c2_{n}.bin"), os.O_CREAT | os.O_RDWR, 0o644) for n in SIZES}
+        self.fd_c1 = os.open(self.c1_path, os.O_RDONLY)
+        self.fd_scan = os.open(self.scan_path, os.O_RDONLY) if self.scan_path else -1
+        self.hist = torch.zeros((2, 256), dtype=torch.int32, device=self.dev)
+        self.stream = torch.cuda.current_stream()
+
+    def c2(self, n, g, bt, relaxed, nb):
+        self.ctx.c2_pwrite(self.fds[n], n, g, bt, relaxed, nb, SEED_C2, self.c2_stage, n * 64)
+
+    def c1(self, form, which=0):
+        self.ctx.c1_histogram(self.fd_c1, C1_BYTES, self.hist[which].data_ptr(), self.c1_stage, self.c1_stage_bytes,
+                              chunk=C1_CHUNK, groups=C1_GROUPS, threads=C1_THREADS, form=form)
+
+    def scan(self, form, nbytes=SCAN_BYTES):
+        self.ctx.c1_histogram(self.fd_scan, nbytes, self.hist[0].data_ptr(), self.c1_stage, self.c1_stage_bytes,
+                              chunk=SCAN_CHUNK, groups=SCAN_GROUPS, threads=SCAN_THREADS, form=form)
+
+    def timed(self, fn):
+        torch = self.torch
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(self.stream)
+        fn()
+        e.record(self.stream)
+        e.synchronize()
+        return s.elapsed_time(e)
+
+    def close(self):
+        for fd in list(self.fds.values()) + [self.fd_c1, self.fd_scan]:
+            if fd >= 0:
+                os.close(fd)
+        self.ctx.close()
+
+
+def c3_run(rig, form):
+    """Wordcount over the full corpus; returns (ms, bytes, counts ok)."""
+    import numpy as np
+    import workloads
+    torch = rig.torch
+    c = workloads.corpus(workloads.C3_FULL)
+    fds = [os.open(p, os.O_RDONLY) for p in c.paths]
+    try:
+        counts = torch.zeros(len(c.queries), dtype=torch.int64, device=rig.dev)
+        ms = rig.timed(lambda: rig.ctx.c3_wordcount(fds, c.sizes, c.queries, counts.data_ptr(), rig.c3_stage,
+                                                     rig.c3_stage_bytes, chunk=C3_CHUNK, ctas=C3_CTAS,
+                                                     threads=C3_THREADS, form=form))
+        ok = np.array_equal(counts.cpu().numpy().astype(np.uint64), c.truth_total())
+    finally:
+        for fd in fds:
+            os.close(fd)
+    return ms, c.total_bytes, ok
+
+
+def sweep_step(rig, note=None):
+    """One step: the C2 sweep (every size x legal combination) and C1 (plain,
+    batched)."""
+    G = rig.G
+    for n in SIZES:
+        for name, g, bt, relaxed, nb in COMBOS:
+            rig.c2(n, g, bt, relaxed, nb)
+            if note:
+                note(f"c2_pwrite_kernel<{G.GRAN_NAMES[g]},{'relaxed' if relaxed else 'strong'},"
+                     f"{'nonblocking' if nb else 'blocking'}>")
+    for form in (G.FORM_PLAIN, G.FORM_BATCHED):
+        rig.c1(form, which=form)
+        if note:
+            note("c1_plain_kernel" if form == G.FORM_PLAIN else "c1_batched_kernel")
+
+
+def tune_step(args, local, rank):
+    """Autotune the context knobs of the timed step (service threads, batch
+    size); cached per machine."""
+    from paper_1705_06965_b300 import autotune
+    tuner = autotune.Autotuner()
+    key = tuner.key("bench-step", sizes=len(SIZES), combos=len(COMBOS))
+
+    def run(cfg):
+        rig = Rig(args, local, rank, need_scan=False, need_c3=False, service_threads=cfg["service_threads"],
+                  coalesce_max=cfg["coalesce_max"])
+        try:
+            sweep_step(rig)
+            return rig.timed(lambda: sweep_step(rig)) * 1e-3
+        finally:
+            rig.close()
+
+    best, table = tuner.tune(key, autotune.grid(service_threads=(2, 4, 8), coalesce_max=(64, 256)), run, repeats=1)
+    return best, table
+
+
+# ---------------------------------------------------------------- one case
+def run_only(args):
+    """Run a single case once (after one warm-up) and print its timing: used
+    to profile one kernel with small, bounded commands."""
+    import torch
+    rank, local, _ = dist_env()
+    torch.cuda.set_device(local)
+    kind, _, rest = args.only.partition(":")
+    rig = Rig(args, local, rank, need_scan=kind == "c1" and rest.split(":")[-1] != str(C1_BYTES))
+    G = rig.G
+    out = {"only": args.only}
+    try:
+        if kind == "c2":
+            key, n = rest.rsplit(":", 1)
+            name, order, block = key.split("/")
+            g, bt = GRAN_BY_NAME[name]
+            n = int(n)
+            fn = lambda: rig.c2(n, g, bt, order == "relaxed", block == "nonblocking")  # noqa: E731
+            calls = calls_for(g, bt, n)
+        elif kind == "c1":
+            form_s, nbytes = rest.split(":")
+            form = G.FORM_BATCHED if form_s == "batched" else G.FORM_PLAIN
+            nbytes = int(nbytes)
+            fn = (lambda: rig.c1(form)) if nbytes == C1_BYTES else (lambda: rig.scan(form, nbytes))  # noqa: E731
+            calls = nbytes // (C1_CHUNK if nbytes == C1_BYTES else SCAN_CHUNK)
+        elif kind == "c3":
+            form = G.FORM_BATCHED if rest == "batched" else G.FORM_PLAIN
+            c3_run(rig, form)
+            ms, nbytes, ok = c3_run(rig, form)
+            out.update({"ms": round(ms, 3), "GB_per_s": round(nbytes / (ms * 1e-3) / 1e9, 2), "counts_ok": ok})
+            print(json.dumps(out), flush=True)
+            return
+        else:
+            raise SystemExit(f"unknown --only kind {kind}")
+        fn()
+        ms = rig.timed(fn)
+        out.update({"ms": round(ms, 3), "calls": calls, "calls_per_s": round(calls / (ms * 1e-3), 1),
+                    "kernel_ms": round(rig.ctx.last_launch_ms(), 3)})
+        print(json.dumps(out), flush=True)
+    finally:
+        rig.close()
+
+
+# ---------------------------------------------------------------- extras
+def profile_extras(args, rig, local, rank, link):
+    """Untimed measurements reported beside the headline: pread+scan and
+    wordcount GB/s at autotuned settings (fractions of the measured host
+    link), the served C5 trace against its plain one-at-a-time form, and the
+    C4 key-value service at swept offered rates."""
+    import numpy as np
+    import torch
+    import workloads
+    from paper_1705_06965_b300 import autotune
+    G = rig.G
+    out = {}
+    # pread + histogram over 1 GiB
+    best = autotune.tune_scan(local, rig.fd_scan, SCAN_BYTES)
+    with G.Context(device=local, service_threads=best["service_threads"],
+                   staging_bytes=2 * best["groups"] * best["chunk"] + (1 << 20)) as ctx:
+        sb = 2 * best["groups"] * best["chunk"]
+        st = ctx.staging(sb)
+        res = {}
+        for form in (G.FORM_PLAIN, G.FORM_BATCHED):
+            fn = lambda: ctx.c1_histogram(rig.fd_scan, SCAN_BYTES, rig.hist[0].data_ptr(), st, sb,  # noqa: E731
+                                          chunk=best["chunk"], groups=best["groups"], threads=1024, form=form)
+            fn()
+            ms = min(rig.timed(fn) for _ in range(3))
+            gbs = SCAN_BYTES / (ms * 1e-3) / 1e9
+            res["plain" if form == G.FORM_PLAIN else "batched"] = {
+                "GB_per_s": round(gbs, 2), "frac_of_host_link_h2d": round(gbs / link["h2d"], 4), "ms": round(ms, 2)}
+        out["pread_scan_1GiB"] = {"autotuned": best, **res}
+    # C3 wordcount over the full corpus
+    c = workloads.corpus(workloads.C3_FULL)
+    fds = [os.open(p, os.O_RDONLY) for p in c.paths]
+    try:
+        best = autotune.tune_wordcount(local, fds, c.sizes, c.queries)
+        sb = 2 * best["ctas"] * (best["chunk"] + 64)
+        with G.Context(device=local, service_threads=best["service_threads"], staging_bytes=sb + (1 << 20)) as ctx:
+            st = ctx.staging(sb)
+            res = {}
+            for form in (G.FORM_PLAIN, G.FORM_BATCHED):
+                counts = torch.zeros(len(c.queries), dtype=torch.int64, device=rig.dev)
+                fn = lambda: ctx.c3_wordcount(fds, c.sizes, c.queries, counts.data_ptr(), st, sb,  # noqa: E731
+                                              chunk=best["chunk"], ctas=best["ctas"], threads=512, form=form)
+                fn()
+                counts.zero_()
+                ms = rig.timed(fn)
+                ok = bool(np.array_equal(counts.cpu().numpy().astype(np.uint64), c.truth_total()))
+                ms = min(ms, *(rig.timed(fn) for _ in range(2)))
+                gbs = c.total_bytes / (ms * 1e-3) / 1e9
+                res["plain" if form == G.FORM_PLAIN else "batched"] = {
+                    "GB_per_s": round(gbs, 2), "frac_of_host_link_h2d": round(gbs / link["h2d"], 4),
+                    "ms": round(ms, 2), "counts_equal_ground_truth": ok}
+            out["wordcount_c3"] = {"autotuned": best, "corpus_bytes": c.total_bytes, **res}
+    finally:
+        for fd in fds:
+            os.close(fd)
+    out["served_c5"] = serve_c5(G, local, rank)
+    out["kv_c4"] = serve_c4(G, local, rank)
+    return out
+
+
+def serve_c5(G, local, rank):
+    """C5: the 10,000-request trace served with continuous admission (up to 64
+    kernels in flight, graph relaunch), and its first 1,000 requests both
+    served and in the plain one-at-a-time form."""
+    import numpy as np
+    import workloads
+    tr = workloads.c5_trace(workloads.C5_FULL)
+    d = workloads.scratch_dir(f"bench_c5_r{rank}")
+    in_fds = [os.open(p, os.O_RDONLY) for p in tr.in_paths]
+    out = {}
+    try:
+        with G.Context(device=local, service_threads=8, staging_bytes=512 << 20) as ctx:
+            def run(sub, **cfg):
+                ofd = os.open(os.path.join(d, "out.bin"), os.O_CREAT | os.O_RDWR, 0o644)
+                try:
+                    t0 = time.perf_counter()
+                    res, lat, st = ctx.c5_serve(sub.arrival_ns, sub.threads, sub.n_ops, sub.ops, in_fds, ofd, **cfg)
+                    wall = time.perf_counter() - t0
+                finally:
+                    os.close(ofd)
+                span = st["makespan_ns"] * 1e-9
+                return res, {"requests": st["requests"], "syscalls": st["syscalls"],
+                             "syscalls_per_s": round(st["syscalls"] / span, 1),
+                             "requests_per_s": round(st["requests"] / span, 1),
+                             "p50_ms": round(float(np.percentile(lat, 50)) / 1e6, 3),
+                             "p99_ms": round(float(np.percentile(lat, 99)) / 1e6, 3),
+                             "makespan_s": round(span, 3), "wall_s": round(wall, 3),
+                             "max_inflight": st["max_inflight"], "graph_launches": st["graph_launches"]}
+            first = tr.subset(np.arange(1000))
+            r_plain, out["plain_first1000"] = run(first, max_inflight=1, use_graphs=0)
+            r_served, out["served_first1000"] = run(first, max_inflight=64)
+            m = np.arange(8)[None, :] < first.n_ops[:, None]
+            out["first1000_alone_equals_mix"] = bool(np.array_equal(r_plain[m], r_served[m]))
+            _, out["served_full"] = run(tr, max_inflight=64)
+    finally:
+        for fd in in_fds:
+            os.close(fd)
+    out["trace"] = {"requests": len(tr), "rate_per_s": tr.params["rate_per_s"]}
+    return out
+
+
+def serve_c4(G, local, rank, rates=(100_000.0, 200_000.0, 400_000.0), n_req=200_000):
+    """C4: 1M-key table in HBM, 200k requests (Zipf 0.99, 90% GET) per offered
+    rate; achieved requests/s and send-to-reply latency."""
+    import numpy as np
+    import workloads
+    p = dict(workloads.C4_FULL, n_requests=n_req)
+    tr = workloads.kv_trace(p)
+    reqs, off = workloads.kv_request_bytes(tr)
+    base_rate = p["rate_per_s"]
+    port = 41000 + 200 * rank
+    out = {"keys": len(tr.keys), "requests_per_rate": n_req, "sockets": 32, "rates": {}}
+    with G.Context(device=local, service_threads=8, staging_bytes=64 << 20) as ctx:
+        for rate in rates:
+            srv = G.KVServer(ctx, tr.keys, tr.vlen0, tr.vseed0, n_sockets=32, batch=64, port_base=port)
+            try:
+                arr = (tr.arrival_ns.astype(np.float64) * (base_rate / rate)).astype(np.uint64)
+                reps, lat, st = G.kv_client(reqs, off, arr, port, 32, timeout_ns=10_000_000_000)
+            finally:
+                served = srv.stop()
+            got = lat[lat > 0]
+            out["rates"][str(int(rate))] = {
+                "received": st["received"], "served": served,
+                "achieved_req_per_s": round(st["received"] / (st["span_ns"] * 1e-9), 1) if st["span_ns"] else None,
+                "p50_us": round(float(np.percentile(got, 50)) / 1e3, 2) if len(got) else None,
+                "p99_us": round(float(np.percentile(got, 99)) / 1e3, 2) if len(got) else None,
+                "max_send_late_us": round(st["max_send_late_ns"] / 1e3, 1)}
+            port += 40
+    return out
+
+
 # ---------------------------------------------------------------- GPU arm
 def run_genesys(args):
     import numpy as np
     import torch
-
-    import paper_1705_06965_b300 as G
-    import workloads
 
     rank, local, world = dist_env()
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    dev = torch.device("cuda", local)
-    d = workloads.scratch_dir(f"bench_r{rank}")
-    c1_path = workloads.c1_file(os.path.join(d, "c1.bin"), C1_BYTES, seed=workloads.SEED_C1)
-    scan_path = workloads.c1_file(os.path.join(d, "scan.bin"), SCAN_BYTES, seed=0x5EED00F1)
-    ctx = G.Context(device=local, service_threads=SERVICE_THREADS, staging_bytes=400 << 20,
-                    deadline_ns=10_000_000_000)
-    c2_stage = ctx.staging(max(SIZES) * 64)
-    c1_stage = ctx.staging(max(2 * C1_GROUPS * C1_CHUNK, 2 * SCAN_GROUPS * SCAN_CHUNK))
-    c1_stage_bytes = max(2 * C1_GROUPS * C1_CHUNK, 2 * SCAN_GROUPS * SCAN_CHUNK)
-    fds = {n: os.open(os.path.join(d, f"c2_{n}.bin"), os.O_CREAT | os.O_RDWR, 0o644) for n in SIZES}
-    fd_c1 = os.open(c1_path, os.O_RDONLY)
-    fd_scan = os.open(scan_path, os.O_RDONLY)
-    hist = torch.zeros((2, 256), dtype=torch.int32, device=dev)
+    step_cfg, step_table = tune_step(args, local, rank) if args.autotune else (
+        {"service_threads": args.service_threads, "coalesce_max": 64}, [])
+    rig = Rig(args, local, rank, service_threads=step_cfg["service_threads"], coalesce_max=step_cfg["coalesce_max"])
+    G, ctx, dev = rig.G, rig.ctx, rig.dev
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
     kernel_ms = {}
     launches = [0]
 
@@ -200,23 +474,12 @@ def run_genesys(args):
         kernel_ms.setdefault(kname, []).append(ctx.last_launch_ms())
         launches[0] += 1
 
-    def one_step(collect_kernels=True):
-        for n in SIZES:
-            for name, g, bt, relaxed, nb in COMBOS:
-                ctx.c2_pwrite(fds[n], n, g, bt, relaxed, nb, SEED_C2, c2_stage, n * 64)
-                if collect_kernels:
-                    note(f"c2_pwrite_kernel<{G.GRAN_NAMES[g]},{'relaxed' if relaxed else 'strong'},"
-                         f"{'nonblocking' if nb else 'blocking'}>")
-        for form in (G.FORM_PLAIN, G.FORM_BATCHED):
-            ctx.c1_histogram(fd_c1, C1_BYTES, hist[form].data_ptr(), c1_stage, c1_stage_bytes, chunk=C1_CHUNK,
-                             groups=C1_GROUPS, threads=C1_THREADS, form=form)
-            if collect_kernels:
-                note("c1_plain_kernel" if form == G.FORM_PLAIN else "c1_batched_kernel")
+    def one_step(collect=True):
+        sweep_step(rig, note if collect else None)
 
-    # warm-up (untimed)
     for _ in range(max(args.warmup, 0)):
-        hist.zero_()
-        one_step(collect_kernels=False)
+        rig.hist.zero_()
+        one_step(collect=False)
     torch.cuda.synchronize()
     kernel_ms.clear()
     launches[0] = 0
@@ -227,54 +490,43 @@ def run_genesys(args):
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             flush.zero_()                      # L2 flush between timed steps
-            hist.zero_()
+            rig.hist.zero_()
             if world > 1:
                 torch.distributed.barrier()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s.record(stream)
-            one_step()
-            e.record(stream)
-            h = hist.cpu()                     # the step's result back on the host
+            ms = rig.timed(one_step)
+            h = rig.hist.cpu()                 # the step's result back on the host
             st = ctx.status()
-            e.synchronize()
             e2e_s.append(time.perf_counter() - t0)
-            step_ms.append(s.elapsed_time(e))
+            step_ms.append(ms)
             if any(st):
                 raise RuntimeError(f"device status {st}")
     stats = ctx.stats()
     clocks = clk.summary()
 
-    # correctness spot check outside the timed region (parity tests cover it in full)
     import oracle
-    want = oracle.c1_histogram(c1_path, C1_CHUNK)
+    want = oracle.c1_histogram(rig.c1_path, C1_CHUNK)
     if not (np.array_equal(h[0].numpy().view(np.uint32), want) and np.array_equal(h[1].numpy().view(np.uint32), want)):
         raise RuntimeError("C1 histogram differs from the oracle")
 
-    tot_ms = sum(step_ms)
+    tot_ms, e2e_tot = sum(step_ms), sum(e2e_s)
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([tot_ms, sum(e2e_s)], dtype=torch.float64, device=dev)
+        t = torch.tensor([tot_ms, e2e_tot], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         tot_ms, e2e_tot = float(t[0]), float(t[1])
-    else:
-        e2e_tot = sum(e2e_s)
     calls_step = c2_calls + c1_calls
     value = world * calls_step * args.steps / (tot_ms * 1e-3)
 
     # ---- profile pass (untimed): per-combination rate and latency at 2^20,
-    # plain vs batched forms, pread+scan GB/s at 1 GiB
+    # latency of the plain form at every size, plain vs batched forms,
+    # pread+scan GB/s at 1 GiB and over the C3 corpus
     sweep = {}
     n = max(SIZES)
     for name, g, bt, relaxed, nb in COMBOS:
         ctx.latency(clear=True)
-        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s.record(stream)
-        ctx.c2_pwrite(fds[n], n, g, bt, relaxed, nb, SEED_C2, c2_stage, n * 64)
-        e.record(stream)
-        e.synchronize()
-        ms = s.elapsed_time(e)
+        ms = rig.timed(lambda: rig.c2(n, g, bt, relaxed, nb))
         lat = ctx.latency(clear=True)
         calls = calls_for(g, bt, n)
         sweep[combo_key(name, relaxed, nb)] = {
@@ -282,29 +534,18 @@ def run_genesys(args):
             "requests_per_s": round(n / (ms * 1e-3), 1),
             "p50_us": round(pctl(lat, 50) / 1e3, 2) if len(lat) else None,
             "p99_us": round(pctl(lat, 99) / 1e3, 2) if len(lat) else None}
+    lat_by_size = {}
+    for nn in SIZES:
+        ctx.latency(clear=True)
+        rig.c2(nn, 0, 256, False, False)
+        lat = ctx.latency(clear=True)
+        lat_by_size[str(nn)] = {"p50_us": round(pctl(lat, 50) / 1e3, 2), "p99_us": round(pctl(lat, 99) / 1e3, 2)}
     plain = sweep[combo_key("work-item", False, False)]
-    batched = max((v for k, v in sweep.items() if "relaxed" in k), key=lambda v: v["requests_per_s"])
-    batched_key = [k for k, v in sweep.items() if v is batched][0]
+    batched_key = max((k for k in sweep if "relaxed" in k), key=lambda k: sweep[k]["requests_per_s"])
+    batched = sweep[batched_key]
 
     link = host_link_peak(torch)
-    scan = {}
-    for form in (G.FORM_PLAIN, G.FORM_BATCHED):
-        ctx.stats_reset()
-        best = None
-        for _ in range(3):
-            hist.zero_()
-            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s.record(stream)
-            ctx.c1_histogram(fd_scan, SCAN_BYTES, hist[0].data_ptr(), c1_stage, c1_stage_bytes, chunk=SCAN_CHUNK,
-                             groups=SCAN_GROUPS, threads=SCAN_THREADS, form=form)
-            e.record(stream)
-            e.synchronize()
-            ms = s.elapsed_time(e)
-            best = ms if best is None else min(best, ms)
-        gbs = SCAN_BYTES / (best * 1e-3) / 1e9
-        scan["plain" if form == G.FORM_PLAIN else "batched"] = {
-            "GB_per_s": round(gbs, 2), "frac_of_host_link_h2d": round(gbs / link["h2d"], 4), "ms": round(best, 2)}
-
+    extras = profile_extras(args, rig, local, rank, link)
     # dominant kernel of the timed region and its host-link roofline
     tot = {k: sum(v) for k, v in kernel_ms.items()}
     dom = max(tot, key=tot.get)
@@ -316,12 +557,8 @@ def run_genesys(args):
     if dom.startswith("c2_pwrite_kernel"):
         gname = dom.split("<")[1].split(",")[0]
         gr = {v: k for k, v in G.GRAN_NAMES.items()}[gname]
-        per = []
-        for nn in SIZES:
-            for name, g, bt, relaxed, nb in COMBOS:
-                if g == gr and f"{'relaxed' if relaxed else 'strong'}" in dom and (
-                        ("nonblocking" in dom) == nb):
-                    per.append(nn * 64 + calls_for(g, bt, nn) * 80)
+        per = [nn * 64 + calls_for(g, bt, nn) * 80 for nn in SIZES for name, g, bt, relaxed, nb in COMBOS
+               if g == gr and ("relaxed" if relaxed else "strong") in dom and ("nonblocking" in dom) == nb]
         alg_bytes = statistics.mean(per)
     else:
         alg_bytes = C1_BYTES + (C1_BYTES // C1_CHUNK) * 80
@@ -333,12 +570,8 @@ def run_genesys(args):
                 "alg_bytes_per_launch": int(alg_bytes), "avg_launch_ms": round(avg_ms, 4),
                 "share_of_timed_device_time": round(tot[dom] / sum(tot.values()), 4)}
 
-    # CPU baseline: the oracle as it stands, on this host, bounded sample
-    cpu = None
-    if rank == 0:
-        cpu = cpu_baseline_sample(budget_s=20.0)
+    cpu = cpu_baseline_sample(budget_s=20.0) if rank == 0 else None
 
-    lat_all = []
     line = {
         "metric": "GPU syscalls/s (C2 pwrite invocation sweep + C1 pread pass)",
         "value": round(value, 1), "unit": "syscalls/s", "n_gpus": world, "steps": args.steps,
@@ -349,14 +582,17 @@ def run_genesys(args):
                                "64-byte pwrite per thread to a tmpfs file at gid*64; then C1 (4 MiB file, 4 KiB "
                                "preads, 64 work-groups x 256 threads, 256-bin histogram, plain and batched)",
                    "threads": SIZES, "combinations": len(COMBOS), "kernels_per_step": len(SIZES) * len(COMBOS) + 2,
-                   "syscalls_per_step": calls_step, "service_threads": SERVICE_THREADS,
+                   "syscalls_per_step": calls_step, "service_threads": step_cfg["service_threads"],
+                   "coalesce_max": step_cfg["coalesce_max"],
                    "l2": "256 MiB device buffer written between timed steps (L2 flush)",
                    "parallelism": f"replicas x{world}"},
         "requests_per_s": round(world * (sum(SIZES) * len(COMBOS) + c1_calls) * args.steps / (tot_ms * 1e-3), 1),
         "forms": {"plain_blocking_strong": {"combo": "work-item/strong/blocking", **plain},
                   "batched": {"combo": batched_key, **batched}},
+        "plain_latency_by_threads": lat_by_size,
         "sweep_2p20": sweep,
-        "pread_scan_1GiB": scan,
+        **extras,
+        "autotuned_step": {"best": step_cfg, "table": step_table},
         "host_link_GB_per_s": link,
         "service": {k: stats[k] for k in ("requests", "os_calls", "batches", "bytes", "failed")},
         "roofline": roofline,
@@ -367,10 +603,7 @@ def run_genesys(args):
         "clocks": clocks,
         "gpu_launches": launches[0],
     }
-    del lat_all
-    for fd in list(fds.values()) + [fd_c1, fd_scan]:
-        os.close(fd)
-    ctx.close()
+    rig.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -382,7 +615,7 @@ def run_genesys(args):
 def oracle_step(d, budget_s=None):
     """One step of the workload by the CPU oracle: the same sweep of pwrites
     (grouped as each granularity issues them) and the C1 preads.  Returns
-    (syscalls, seconds)."""
+    (syscalls, seconds, complete)."""
     import oracle
     import workloads
     c1_path = workloads.c1_file(os.path.join(d, "c1.bin"), C1_BYTES, seed=workloads.SEED_C1)
@@ -442,9 +675,15 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="genesys", choices=["genesys", "reference"])
+    ap.add_argument("--service-threads", type=int, default=4)
+    ap.add_argument("--autotune", type=int, default=1, help="autotune the step's context knobs (cached)")
+    ap.add_argument("--only", default=None, help="run one case: c2:<grain>/<order>/<block>:<threads>, "
+                                                 "c1:<plain|batched>:<bytes>, c3:<plain|batched>")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.only:
+        run_only(args)
     else:
         run_genesys(args)
 

@@ -83,6 +83,10 @@ typedef struct genesys_stats {
   uint64_t busy_ns;            /* service-thread time spent processing batches         */
   uint64_t by_op[8];           /* requests per op: pread, pwrite, sendto, recvfrom,
                                   mmap, munmap, internal ops, other                    */
+  uint64_t op_ns[8];           /* service time per op (unmerged requests)              */
+  uint64_t op_max_ns[8];       /* longest single request per op                        */
+  uint64_t mmap_new;           /* GPU mmaps served by mmap(2) + registration           */
+  uint64_t mmap_reused;        /* GPU mmaps served by a released region                */
 } genesys_stats;
 
 typedef struct genesys_ctx genesys_ctx;
@@ -141,6 +145,22 @@ int genesys_service(genesys_ctx *ctx, uint64_t timeout_ns);
  * included) has completed.  Call it after the kernels that made the calls
  * have finished (e.g. after a stream synchronize).  0 or GENESYS_ETIMEDOUT. */
 int genesys_drain(genesys_ctx *ctx, uint64_t timeout_ns);
+
+/* Unregister and unmap the regions GPU code released with munmap.  A GPU
+ * munmap cannot do this itself: cudaHostUnregister waits until no kernel is
+ * running, and the calling kernel is running.  Released regions stay pinned
+ * until this call (or genesys_shutdown) and are reused by later GPU mmaps of
+ * a size they fit.  Call it when no kernel that makes calls on this context is
+ * running. */
+int genesys_reclaim(genesys_ctx *ctx);
+
+/* Map (mmap(2), anonymous) and register n regions of the given sizes (rounded
+ * up to pages) ahead of time, into the pool GPU mmaps are served from.
+ * cudaHostRegister can stall while the GPU is busy with other kernels (on the
+ * B300 test box a registration waited tens of seconds behind a stream of
+ * kernels), and a kernel waiting for its mmap keeps the GPU busy: reserving
+ * before the kernels start keeps registration off the path. */
+int genesys_mmap_reserve(genesys_ctx *ctx, const uint64_t *sizes, uint32_t n);
 
 int genesys_stats_get(genesys_ctx *ctx, genesys_stats *out);
 int genesys_stats_reset(genesys_ctx *ctx);
@@ -247,6 +267,113 @@ int genesys_c3_wordcount_noalloc(genesys_ctx *ctx, const int32_t *fds, const uin
                                  uint32_t n_files, const uint8_t *queries16, const uint8_t *qlen, uint32_t nq,
                                  uint64_t chunk, uint32_t ctas, uint32_t threads, uint32_t form, void *staging,
                                  uint64_t staging_bytes, unsigned long long *counts_dev, void *stream);
+
+/* C5: serving a trace of syscall-issuing GPU kernels.  Each request is one
+ * kernel of `threads` threads (blocks of block_threads) that runs up to
+ * GENESYS_C5_MAX_OPS operations in order (Sec. 7 filesystem and memory calls):
+ *   GENESYS_C5_PREAD  pread `len` bytes of in_fds[file] at `off`, split over
+ *                     blocks (work-group grain, relaxed, blocking); result =
+ *                     checksum of the bytes (see below);
+ *   GENESYS_C5_PWRITE write `len` bytes of the splitmix64 stream of `seed` to
+ *                     out_fd at `out_off` (work-group grain parts); result =
+ *                     bytes written;
+ *   GENESYS_C5_MMAP   mmap `len` (a multiple of 16) anonymous bytes at kernel grain (registered
+ *                     for device access), fill word i with
+ *                     splitmix64_at(seed, i), checksum it, munmap it at kernel
+ *                     grain; result = checksum.
+ * Checksum of a byte string: sum mod 2^64 over its little-endian 64-bit words
+ * w_i (zero padded) of splitmix64's output function applied to
+ * w_i + (i + 1) * 0x9E3779B97F4A7C15.
+ * The server admits requests in arrival order once they have arrived
+ * (arrival_ns after the call starts, if honor_arrivals) and a launch slot,
+ * syscall slots, staging bytes and HBM bytes are free; launches them on
+ * n_streams streams (as relaunched single-kernel CUDA graphs if use_graphs);
+ * retires them when their completion event fires.  Outputs (host arrays):
+ * results[n_req * 8] (negative errno on failure), latency_ns[n_req]
+ * (retirement - arrival); *stats if non-NULL. */
+#define GENESYS_C5_MAX_OPS 8u
+#define GENESYS_C5_MAX_PARTS 256u
+#define GENESYS_C5_PREAD 0u
+#define GENESYS_C5_PWRITE 1u
+#define GENESYS_C5_MMAP 2u
+
+typedef struct genesys_c5_op {
+  uint32_t kind, file;
+  uint64_t off, len, seed, out_off;
+} genesys_c5_op;
+
+typedef struct genesys_c5_request {
+  uint64_t arrival_ns;
+  uint32_t threads, n_ops;
+  genesys_c5_op ops[GENESYS_C5_MAX_OPS];
+} genesys_c5_request;
+
+typedef struct genesys_serve_config {
+  uint32_t max_inflight;    /* launch slots: requests on the GPU at once          */
+  uint32_t n_streams;
+  uint64_t staging_budget;  /* pinned bytes for in-flight requests' pwrite data    */
+  uint64_t hbm_budget;      /* device bytes for in-flight requests' pread landing  */
+  uint32_t slot_budget;     /* syscall-area slots in-flight requests may hold      */
+  uint32_t block_threads;
+  uint32_t min_part;        /* smallest per-block share of a pread/pwrite (bytes): the
+                               invocation granularity knob the autotuner sets      */
+  uint32_t use_graphs;
+  uint32_t pread_to_hbm;    /* 1: pread data is moved to HBM and scanned there     */
+  uint32_t honor_arrivals;  /* 1: open loop on arrival_ns; 0: all present at start */
+  uint32_t reserve_mmaps;   /* 1: map and register the trace's mmap regions before
+                               the first request (genesys_mmap_reserve)            */
+  uint64_t timeout_ns;      /* give up (GENESYS_ETIMEDOUT) after this long         */
+} genesys_serve_config;
+
+typedef struct genesys_serve_stats {
+  uint64_t requests, syscalls, makespan_ns, max_inflight, admission_wait_ns, graph_launches;
+} genesys_serve_stats;
+
+int genesys_serve_config_default(genesys_serve_config *cfg);
+int genesys_c5_serve(genesys_ctx *ctx, const genesys_c5_request *reqs, uint32_t n_req, const int32_t *in_fds,
+                     uint32_t n_in, int32_t out_fd, const genesys_serve_config *cfg, uint64_t *results,
+                     uint64_t *latency_ns, genesys_serve_stats *stats);
+
+/* C4, key-value service over UDP (Sec. 7.3 networking): the server is a
+ * persistent GPU kernel, one block per UDP socket on 127.0.0.1:port_base + w,
+ * that receives request batches with recvmmsg and answers them with sendmmsg
+ * (work-group grain GPU system calls; non-blocking receive polls).  The table
+ * lives in device memory: n_keys 16-byte keys (keys[16 * i]) in an
+ * open-addressing index, values in GENESYS_KV_VALUE_MAX-byte slots, preloaded
+ * with value i = the first vlen0[i] bytes of the splitmix64 stream of seed
+ * vseed0[i] (host arrays).  Requests for one key must all go to one socket
+ * (the client sends to (first four key bytes, little-endian) mod n_sockets);
+ * a block applies a batch's requests in arrival order per key.
+ * Request: op u8 (GENESYS_KV_GET/SET/STOP), pad u8, vlen u16, seq u32,
+ * key[16], value[vlen] (SET).  Reply: op|0x80 u8, status u8 (0 ok, 1 no such
+ * key), vlen u16, seq u32, value[vlen] (GET of a present key).  A block leaves
+ * on a STOP datagram, when genesys_kv_stop sets the stop flag and it is idle,
+ * or after idle_timeout_ns without datagrams. */
+#define GENESYS_KV_VALUE_MAX 1024u
+#define GENESYS_KV_MAX_BATCH 64u
+#define GENESYS_KV_GET 0u
+#define GENESYS_KV_SET 1u
+#define GENESYS_KV_STOP 2u
+typedef struct genesys_kv_server genesys_kv_server;
+int genesys_kv_start(genesys_ctx *ctx, const uint8_t *keys, const uint16_t *vlen0, const uint64_t *vseed0,
+                     uint32_t n_keys, uint32_t n_sockets, uint32_t batch, uint32_t threads, uint16_t port_base,
+                     uint64_t idle_timeout_ns, genesys_kv_server **out);
+/* Stop the server (bounded by timeout_ns), drain its calls, free it; *served
+ * (if non-NULL) = replies sent. */
+int genesys_kv_stop(genesys_kv_server *srv, uint64_t timeout_ns, uint64_t *served);
+/* Current value of key k (copied to out, GENESYS_KV_VALUE_MAX bytes room);
+ * returns its length. */
+int genesys_kv_value(genesys_kv_server *srv, uint32_t k, uint8_t *out);
+/* Open-loop UDP load generator on host threads: request j (reqs + req_off[j],
+ * req_off[n] = end) is sent arrival_ns[j] after start to the socket its key
+ * maps to; replies are matched by seq into replies[seq * (8 + VALUE_MAX)],
+ * reply_len[seq], latency_ns[seq] (send to receive).  Then sends STOP to every
+ * socket.  stats[6]: received, duplicates, malformed, send errors, largest
+ * send lateness (ns), first send to last reply (ns).  GENESYS_ETIMEDOUT if
+ * replies are still missing timeout_ns after the last arrival. */
+int genesys_kv_client(const uint8_t *reqs, const uint64_t *req_off, uint64_t n, const uint64_t *arrival_ns,
+                      uint16_t port_base, uint32_t n_sockets, uint64_t timeout_ns, uint8_t *replies,
+                      uint32_t *reply_len, uint64_t *latency_ns, uint64_t *stats);
 
 /* Strong-ordering visibility probe (Sec. 4.1: strong ordering means every
  * store before the call has completed): n_threads threads each store their

@@ -88,6 +88,10 @@ __device__ __forceinline__ uint32_t ld_relaxed_gpu(const uint32_t *p) {
 __device__ __forceinline__ void st_relaxed_gpu(uint32_t *p, uint32_t v) {
   asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ void fence_acq_rel_sys() { asm volatile("fence.acq_rel.sys;" ::: "memory"); }
+__device__ __forceinline__ void st_relaxed_sys(uint64_t *p, uint64_t v) {
+  asm volatile("st.relaxed.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 /* 16-byte store to (host-mapped) memory */
 __device__ __forceinline__ void st_v2(uint64_t *p, uint64_t a, uint64_t b) {
   asm volatile("st.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
@@ -115,7 +119,7 @@ __device__ __forceinline__ int role_of(uint32_t nr) {
     case SYS_munmap: case SYS_madvise: case SYS_close:
       return ROLE_PRODUCER;
     case SYS_read: case SYS_pread64: case SYS_recvfrom: case SYS_recvmmsg:
-    case SYS_mmap: case SYS_open: case SYS_openat: case GENESYS_NR_PREAD_DEV:
+    case SYS_mmap: case SYS_open: case SYS_openat:
       return ROLE_CONSUMER;
     default:
       return ROLE_BOTH;
@@ -138,7 +142,7 @@ __device__ __forceinline__ bool expired(const genesys_dev &g, uint64_t t0) {
 }
 
 __device__ __forceinline__ uint32_t ring_of(const genesys_dev &g, uint32_t slot) {
-  return (slot >> 5) % g.n_rings;
+  return genesys_ring_of(slot, g.n_rings);
 }
 
 /* ------------------------------------------------------ slot protocol
@@ -202,32 +206,46 @@ __device__ __forceinline__ void ring_one(const genesys_dev &g, uint32_t s) {
   st_release_sys(g.rings + (size_t)r * (g.ring_mask + 1u) + (pos & g.ring_mask), GENESYS_RING_ENTRY(pos, s));
 }
 
-/* Doorbell for the lanes of `mask` that each published slot `s`: one atomic per
- * ring per warp (lanes are grouped with __match_any_sync). */
+/* Doorbell for the lanes of `mask` that each filled slot `s`.  Lanes going to
+ * the same ring (grouped with __match_any_sync) take consecutive positions with
+ * one atomic; after a warp barrier the group's first lane makes one system-scope
+ * release fence and writes all of the group's entries, so every lane's slot
+ * stores happen before its entry becomes visible, at one fence per group
+ * instead of one per lane. */
 __device__ __forceinline__ void ring_warp(const genesys_dev &g, uint32_t mask, uint32_t s) {
   const uint32_t r = ring_of(g, s);
   const uint32_t peers = __match_any_sync(mask, r);
   const uint32_t lane = lane_id();
   const uint32_t leader = __ffs(peers) - 1;
-  const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
   uint32_t base = 0;
   if (lane == leader) base = atomicAdd(&g.ring_tail[r * 32u], (uint32_t)__popc(peers));
   base = __shfl_sync(peers, base, leader);
-  const uint32_t pos = base + rank;
-  st_release_sys(g.rings + (size_t)r * (g.ring_mask + 1u) + (pos & g.ring_mask), GENESYS_RING_ENTRY(pos, s));
+  __syncwarp(peers);
+  if (lane == leader) fence_acq_rel_sys();
+  uint64_t *ring = g.rings + (size_t)r * (g.ring_mask + 1u);
+  uint32_t rem = peers;
+  for (uint32_t k = 0; rem; ++k) {
+    const uint32_t j = __ffs(rem) - 1;
+    rem &= rem - 1;
+    const uint32_t sj = __shfl_sync(peers, s, j);
+    if (lane == leader) st_relaxed_sys(ring + ((base + k) & g.ring_mask), GENESYS_RING_ENTRY(base + k, sj));
+  }
 }
 
-/* Wait until the CPU finished request `sq` of slot `s`; returns its result. */
+/* Wait until the CPU finished request `sq` of slot `s`; returns its result.
+ * Polls with relaxed loads and makes the acquire once, with a fence after the
+ * load that saw the completion (an acquire pattern). */
 __device__ __forceinline__ int64_t slot_wait(const genesys_dev &g, uint32_t s, uint32_t sq, uint64_t t0) {
   uint32_t ns = 256;
   uint64_t d;
   for (;;) {
-    d = ld_acquire_sys(&g.done[s]);
+    d = ld_relaxed_sys(&g.done[s]);
     if ((uint32_t)(d >> 32) == sq) break;
     if (expired(g, t0)) { note_error(g, -kETIMEDOUT); return -kETIMEDOUT; }
     __nanosleep(ns);
     ns = ns < 2048 ? ns + (ns >> 1) : ns;
   }
+  fence_acq_rel_sys();
   st_relaxed_gpu(&g.known_done[s], sq);
   const uint32_t lo = (uint32_t)d;
   const int64_t ret = lo == GENESYS_RET_IN_SLOT ? (int64_t)ld_relaxed_sys(&g.slots[s].ret) : (int64_t)(int32_t)lo;
@@ -249,8 +267,8 @@ __device__ __forceinline__ int64_t single_call(const genesys_dev &g, uint32_t nr
   int64_t rc = slot_claim(g, hw_lane_id(), &s, t0);
   if (rc < 0) return rc;
   const uint32_t sq = slot_fill(g, s, nr, flags, a0, a1, a2, a3, a4, a5);
-  __threadfence_system();
-  ring_one(g, s);
+  ring_one(g, s);  // st.release.sys: the slot stores (and, through the group's
+                   // barrier, the group's earlier stores) are visible first
   int64_t ret = 0;
   if (wait) {
     ret = slot_wait(g, s, sq, t0);
@@ -282,7 +300,6 @@ __device__ __forceinline__ int64_t issue(const genesys_dev &g, Ticket *t, uint32
   int64_t rc = slot_claim(g, hw_lane_id(), &t->slot, t->t0);
   if (rc < 0) { t->slot = 0xFFFFFFFFu; return rc; }
   t->seq = slot_fill(g, t->slot, nr, GENESYS_REQ_TICKET | GENESYS_REQ_RELAXED, a0, a1, a2, a3, a4, a5);
-  __threadfence_system();
   ring_one(g, t->slot);
   return 0;
 }
@@ -360,7 +377,6 @@ __device__ __forceinline__ int64_t call_at(const genesys_dev &g, uint32_t site, 
     const bool ok = rc == 0;
     uint32_t sq = 0;
     if (ok) sq = slot_fill(g, s, nr, flags, a0, a1, a2, a3, a4, a5);
-    __threadfence_system();
     const uint32_t okmask = __ballot_sync(active, ok);
     if (ok) {
       ring_warp(g, okmask, s);

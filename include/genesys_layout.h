@@ -20,7 +20,8 @@
  *   - completion words live in their own dense array, so that one warp polling
  *     32 neighbouring slots reads 256 contiguous bytes instead of 32 lines;
  *   - the CPU learns of new requests from doorbell rings (one per service
- *     thread) instead of an interrupt carrying the wavefront's hardware ID
+ *     thread, see genesys_ring_of) instead of an interrupt carrying the
+ *     wavefront's hardware ID
  *     (Sec. 3 notes that interrupt versus polling is orthogonal to the design).
  *
  * All multi-byte fields are little-endian (x86-64 host, NVIDIA GPU).
@@ -74,9 +75,26 @@ typedef struct genesys_slot {
                                               in [ptr, ptr+count) that differ from
                                               splitmix64_at(seed, i); the strong-ordering
                                               visibility probe                            */
-#define GENESYS_NR_PREAD_DEV      0x7F02u  /* pread into device memory: args fd, dev_ptr,
-                                              len, off; the host reads into its own
-                                              bounce buffer and copies it to the GPU      */
+
+#ifdef __CUDACC__
+#define GENESYS_HD __host__ __device__
+#else
+#define GENESYS_HD
+#endif
+
+/* Doorbell ring of a slot.  Slots are taken in groups of 256 (eight warps of
+ * one SM: the slot a lane tries first is its hardware id), so the requests of
+ * one thread block - usually neighbours in a file - meet in one ring, where
+ * the service thread can merge them; the group number is hashed so that the
+ * callers of different SMs and warp slots spread over all rings. */
+#define GENESYS_RING_GROUP_SHIFT 8u
+static inline GENESYS_HD uint32_t genesys_ring_of(uint32_t slot, uint32_t n_rings) {
+  uint32_t g = slot >> GENESYS_RING_GROUP_SHIFT;
+  g ^= g >> 7;
+  g *= 0x9E3779B1u;
+  g ^= g >> 15;
+  return g % n_rings;
+}
 
 /* Doorbell ring entry: bits 63..32 = ring position + 1, bits 31..0 = slot. */
 #define GENESYS_RING_ENTRY(pos, slot) ((((uint64_t)(uint32_t)((pos) + 1u)) << 32) | (uint64_t)(uint32_t)(slot))

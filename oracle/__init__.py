@@ -51,6 +51,9 @@ def _L():
         L.oracle_c3_wordcount_omp.restype = ctypes.c_int64
         L.oracle_c3_wordcount_omp.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int]
+        L.oracle_c4_replay.restype = ctypes.c_int64
+        L.oracle_c4_replay.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]
         L.oracle_c5_checksum.restype = ctypes.c_uint64
         L.oracle_c5_checksum.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
         L.oracle_c5_request.restype = ctypes.c_int64
@@ -156,3 +159,24 @@ def c5_trace(trace, out_fd: int, in_fds=None) -> np.ndarray:
         if own:
             for fd in in_fds:
                 _os.close(fd)
+
+
+def c4_replay(trace, idx=None):
+    """C4 (Sec. 7.3 UDP service): the sequential server's reply to each request
+    of the trace (in the given order, default seq order), as a list of bytes."""
+    import workloads
+    nk = len(trace.keys)
+    vals = np.zeros((nk, 1024), np.uint8)
+    for i in range(nk):
+        v = trace.value0(i)
+        vals[i, :len(v)] = np.frombuffer(v, np.uint8)
+    vlens = trace.vlen0.astype(np.uint16).copy()
+    reqs, _ = workloads.kv_request_bytes(trace, idx)
+    n = len(trace) if idx is None else len(idx)
+    out = np.zeros(n * (8 + 1024) + 8, np.uint8)
+    off = np.zeros(n + 1, np.uint64)
+    keys = np.ascontiguousarray(trace.keys)
+    rb = ctypes.create_string_buffer(reqs, max(len(reqs), 1))
+    _check(_L().oracle_c4_replay(keys.ctypes.data, nk, vals.ctypes.data, vlens.ctypes.data, rb, n,
+                                 out.ctypes.data, off.ctypes.data), "c4_replay")
+    return [out[int(off[i]):int(off[i + 1])].tobytes() for i in range(n)]

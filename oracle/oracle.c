@@ -299,3 +299,73 @@ int64_t oracle_c5_request(const oracle_c5_op *ops, uint32_t n_ops, const int32_t
   }
   return 0;
 }
+
+/* ---------------------------------------------------------------------- C4
+ * Key-value service over UDP (Sec. 7.3 networking: the GPU receives and sends
+ * datagrams with recvfrom/sendto at work-group grain).  The oracle is the
+ * sequential server: a table of n_keys keys (16 bytes each) with their values,
+ * requests applied one after the other in client sequence order.
+ * Request datagram: op u8 (0 GET, 1 SET), pad u8, vlen u16, seq u32, key[16],
+ *                   value[vlen] (SET only); little-endian.
+ * Reply datagram:   op|0x80 u8, status u8 (0 ok, 1 no such key), vlen u16,
+ *                   seq u32, value[vlen] (GET of a present key only).
+ * `reqs` holds n requests back to back (each a datagram); replies are written
+ * back to back into `out` (at most n * (8 + 1024) bytes) with their offsets in
+ * `out_off[n + 1]`.  Values: vals[i * 1024 .. + vlens[i]] (updated by SETs). */
+static int key_cmp(const uint8_t *a, const uint8_t *b) { return memcmp(a, b, 16); }
+
+static int64_t find_key(const uint8_t *keys, const uint32_t *order, uint32_t n_keys, const uint8_t *key) {
+  uint32_t lo = 0, hi = n_keys;
+  while (lo < hi) {
+    uint32_t mid = lo + (hi - lo) / 2;
+    int c = key_cmp(keys + 16 * (size_t)order[mid], key);
+    if (c == 0) return order[mid];
+    if (c < 0) lo = mid + 1; else hi = mid;
+  }
+  return -1;
+}
+
+static const uint8_t *sort_keys;
+static int order_cmp(const void *x, const void *y) {
+  return key_cmp(sort_keys + 16 * (size_t)*(const uint32_t *)x, sort_keys + 16 * (size_t)*(const uint32_t *)y);
+}
+
+int64_t oracle_c4_replay(const uint8_t *keys, uint32_t n_keys, uint8_t *vals, uint16_t *vlens, const uint8_t *reqs,
+                         uint64_t n, uint8_t *out, uint64_t *out_off) {
+  uint32_t *order = (uint32_t *)malloc(sizeof(uint32_t) * (n_keys ? n_keys : 1));
+  if (!order) return -ENOMEM;
+  for (uint32_t i = 0; i < n_keys; ++i) order[i] = i;
+  sort_keys = keys;
+  qsort(order, n_keys, sizeof(uint32_t), order_cmp);
+  uint64_t pos = 0, o = 0;
+  for (uint64_t r = 0; r < n; ++r) {
+    const uint8_t *q = reqs + pos;
+    const uint8_t op = q[0];
+    const uint16_t vlen = (uint16_t)(q[2] | (q[3] << 8));
+    const uint8_t *seq = q + 4;
+    const int64_t k = find_key(keys, order, n_keys, q + 8);
+    uint8_t *rep = out + o;
+    rep[0] = (uint8_t)(op | 0x80);
+    memcpy(rep + 4, seq, 4);
+    uint16_t rlen = 0;
+    if (k < 0) {
+      rep[1] = 1;
+    } else if (op == 0) {
+      rep[1] = 0;
+      rlen = vlens[k];
+      memcpy(rep + 8, vals + (size_t)k * 1024, rlen);
+    } else {
+      rep[1] = 0;
+      vlens[k] = vlen;
+      memcpy(vals + (size_t)k * 1024, q + 24, vlen);
+    }
+    rep[2] = (uint8_t)rlen;
+    rep[3] = (uint8_t)(rlen >> 8);
+    out_off[r] = o;
+    o += 8 + rlen;
+    pos += 24 + (op == 1 ? vlen : 0);
+  }
+  out_off[n] = o;
+  free(order);
+  return (int64_t)o;
+}

@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_PKG, "libgenesys.so")
 SYS_read, SYS_write, SYS_close, SYS_mmap, SYS_munmap = 0, 1, 3, 9, 11
 SYS_pread64, SYS_pwrite64, SYS_getpid = 17, 18, 39
 SYS_sendto, SYS_recvfrom, SYS_recvmmsg, SYS_sendmmsg = 44, 45, 299, 307
-NR_NOP, NR_CHECK_VISIBLE, NR_PREAD_DEV = 0x7F00, 0x7F01, 0x7F02
+NR_NOP, NR_CHECK_VISIBLE = 0x7F00, 0x7F01
 
 GRAN_ITEM, GRAN_WARP, GRAN_GROUP, GRAN_KERNEL = 0, 1, 2, 3
 GRAN_NAMES = {GRAN_ITEM: "work-item", GRAN_WARP: "warp", GRAN_GROUP: "work-group", GRAN_KERNEL: "kernel"}
@@ -41,7 +41,9 @@ EXPORTS = [
     "genesys_service", "genesys_drain", "genesys_stats_get", "genesys_stats_reset", "genesys_status",
     "genesys_latency", "genesys_staging", "genesys_staging_reset", "genesys_last_error", "genesys_emulate_call",
     "genesys_c1_histogram", "genesys_c2_pwrite", "genesys_visibility_probe", "genesys_last_launch_ms",
-    "genesys_c3_wordcount", "genesys_c3_wordcount_noalloc",
+    "genesys_c3_wordcount", "genesys_c3_wordcount_noalloc", "genesys_serve_config_default", "genesys_c5_serve",
+    "genesys_reclaim", "genesys_mmap_reserve", "genesys_kv_start", "genesys_kv_stop", "genesys_kv_value",
+    "genesys_kv_client",
 ]
 
 
@@ -61,16 +63,38 @@ class Config(ctypes.Structure):
     ]
 
 
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("max_inflight", ctypes.c_uint32), ("n_streams", ctypes.c_uint32),
+                ("staging_budget", ctypes.c_uint64), ("hbm_budget", ctypes.c_uint64),
+                ("slot_budget", ctypes.c_uint32), ("block_threads", ctypes.c_uint32), ("min_part", ctypes.c_uint32),
+                ("use_graphs", ctypes.c_uint32), ("pread_to_hbm", ctypes.c_uint32),
+                ("honor_arrivals", ctypes.c_uint32), ("reserve_mmaps", ctypes.c_uint32),
+                ("timeout_ns", ctypes.c_uint64)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("requests", "syscalls", "makespan_ns", "max_inflight",
+                                               "admission_wait_ns", "graph_launches")]
+
+
+C5_OP_DTYPE = np.dtype([("kind", "<u4"), ("file", "<u4"), ("off", "<u8"), ("len", "<u8"), ("seed", "<u8"),
+                        ("out_off", "<u8")])
+C5_REQ_DTYPE = np.dtype([("arrival_ns", "<u8"), ("threads", "<u4"), ("n_ops", "<u4"), ("ops", C5_OP_DTYPE, (8,))])
+
+
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in
                 ("requests", "os_calls", "failed", "nonblocking_failed", "bytes", "batches", "busy_ns")] + [
-        ("by_op", ctypes.c_uint64 * 8)]
+        ("by_op", ctypes.c_uint64 * 8), ("op_ns", ctypes.c_uint64 * 8), ("op_max_ns", ctypes.c_uint64 * 8),
+        ("mmap_new", ctypes.c_uint64), ("mmap_reused", ctypes.c_uint64)]
 
     OPS = ("pread", "pwrite", "sendto", "recvfrom", "mmap", "munmap", "internal", "other")
 
     def as_dict(self) -> dict:
-        d = {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "by_op"}
+        d = {n: int(getattr(self, n)) for n, _ in self._fields_ if n not in ("by_op", "op_ns", "op_max_ns")}
         d["by_op"] = {k: int(v) for k, v in zip(self.OPS, self.by_op)}
+        d["op_ns"] = {k: int(v) for k, v in zip(self.OPS, self.op_ns)}
+        d["op_max_ns"] = {k: int(v) for k, v in zip(self.OPS, self.op_max_ns)}
         return d
 
 
@@ -111,6 +135,16 @@ def lib() -> ctypes.CDLL:
         "genesys_c3_wordcount": (ctypes.c_int, [vp, vp, vp, u32, vp, vp, u32, u64, u32, u32, u32, vp, u64, vp, vp]),
         "genesys_c3_wordcount_noalloc": (ctypes.c_int, [vp, vp, vp, u32, vp, vp, u32, u64, u32, u32, u32, vp, u64,
                                                          vp, vp]),
+        "genesys_serve_config_default": (ctypes.c_int, [ctypes.POINTER(ServeConfig)]),
+        "genesys_reclaim": (ctypes.c_int, [vp]),
+        "genesys_mmap_reserve": (ctypes.c_int, [vp, vp, u32]),
+        "genesys_kv_start": (ctypes.c_int, [vp, vp, vp, vp, u32, u32, u32, u32, ctypes.c_uint16, u64,
+                                            ctypes.POINTER(vp)]),
+        "genesys_kv_stop": (ctypes.c_int, [vp, u64, ctypes.POINTER(u64)]),
+        "genesys_kv_value": (ctypes.c_int, [vp, u32, vp]),
+        "genesys_kv_client": (ctypes.c_int, [vp, vp, u64, vp, ctypes.c_uint16, u32, u64, vp, vp, vp, vp]),
+        "genesys_c5_serve": (ctypes.c_int, [vp, vp, u32, vp, u32, ctypes.c_int32, ctypes.POINTER(ServeConfig), vp, vp,
+                                            ctypes.POINTER(ServeStats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -225,6 +259,11 @@ class Context:
         _check(lib().genesys_stats_get(self.handle, ctypes.byref(s)), "genesys_stats_get")
         return s.as_dict()
 
+    def reclaim(self) -> None:
+        """Unpin and unmap regions GPU code released with munmap (call when no
+        kernel using this context runs)."""
+        _check(lib().genesys_reclaim(self.handle), "genesys_reclaim")
+
     def stats_reset(self) -> None:
         _check(lib().genesys_stats_reset(self.handle), "genesys_stats_reset")
 
@@ -284,8 +323,81 @@ class Context:
                                           staging_bytes, counts_dev_ptr, _stream_handle(stream)),
                "genesys_c3_wordcount")
 
+    def c5_serve(self, arrival_ns, threads, n_ops, ops, in_fds, out_fd: int, **cfg):
+        """Serve a trace (arrays of arrival ns, thread counts, op counts and a
+        [n, 8] C5_OP_DTYPE op table).  cfg: ServeConfig fields.  Returns
+        (results [n, 8] uint64, latency_ns [n] uint64, stats dict)."""
+        n = len(threads)
+        reqs = np.zeros(n, C5_REQ_DTYPE)
+        reqs["arrival_ns"] = arrival_ns
+        reqs["threads"] = threads
+        reqs["n_ops"] = n_ops
+        reqs["ops"] = np.asarray(ops).astype(C5_OP_DTYPE)
+        sc = ServeConfig()
+        _check(lib().genesys_serve_config_default(ctypes.byref(sc)), "genesys_serve_config_default")
+        for k, v in cfg.items():
+            setattr(sc, k, int(v))
+        fds = np.ascontiguousarray(np.asarray(in_fds, dtype=np.int32))
+        res = np.zeros((max(n, 1), 8), np.uint64)
+        lat = np.zeros(max(n, 1), np.uint64)
+        st = ServeStats()
+        _check(lib().genesys_c5_serve(self.handle, reqs.ctypes.data, n, fds.ctypes.data, len(fds), out_fd,
+                                      ctypes.byref(sc), res.ctypes.data, lat.ctypes.data, ctypes.byref(st)),
+               "genesys_c5_serve")
+        return res[:n], lat[:n], {f: int(getattr(st, f)) for f, _ in ServeStats._fields_}
+
     def visibility_probe(self, n_threads: int, gran: int, group_threads: int, relaxed: bool, seed: int,
                          probe: int, violations_dev_ptr: int, stream=None) -> None:
         _check(lib().genesys_visibility_probe(self.handle, n_threads, gran, group_threads, 1 if relaxed else 0,
                                               seed, probe, violations_dev_ptr, _stream_handle(stream)),
                "genesys_visibility_probe")
+
+
+KV_REPLY_STRIDE = 8 + 1024
+
+
+class KVServer:
+    """GPU key-value server (genesys_kv_start / genesys_kv_stop)."""
+
+    def __init__(self, ctx: Context, keys, vlen0, vseed0, n_sockets: int = 16, batch: int = 64, threads: int = 256,
+                 port_base: int = 47000, idle_timeout_ns: int = 20_000_000_000):
+        self.keys = np.ascontiguousarray(np.asarray(keys, np.uint8))
+        self.vlen0 = np.ascontiguousarray(np.asarray(vlen0, np.uint16))
+        self.vseed0 = np.ascontiguousarray(np.asarray(vseed0, np.uint64))
+        self.n_sockets, self.port_base = n_sockets, port_base
+        h = ctypes.c_void_p()
+        _check(lib().genesys_kv_start(ctx.handle, self.keys.ctypes.data, self.vlen0.ctypes.data,
+                                      self.vseed0.ctypes.data, len(self.vlen0), n_sockets, batch, threads, port_base,
+                                      idle_timeout_ns, ctypes.byref(h)), "genesys_kv_start")
+        self._h = h
+
+    def value(self, k: int) -> bytes:
+        buf = ctypes.create_string_buffer(1024)
+        n = _check(lib().genesys_kv_value(self._h, k, buf), "genesys_kv_value")
+        return buf.raw[:n]
+
+    def stop(self, timeout_ns: int = 30_000_000_000) -> int:
+        served = ctypes.c_uint64()
+        if self._h:
+            h, self._h = self._h, None
+            _check(lib().genesys_kv_stop(h, timeout_ns, ctypes.byref(served)), "genesys_kv_stop")
+        return served.value
+
+
+def kv_client(reqs: bytes, req_off, arrival_ns, port_base: int, n_sockets: int, timeout_ns: int = 20_000_000_000):
+    """Run the UDP load generator; returns (replies list, latency_ns, stats dict)."""
+    n = len(arrival_ns)
+    off = np.ascontiguousarray(np.asarray(req_off, np.uint64))
+    arr = np.ascontiguousarray(np.asarray(arrival_ns, np.uint64))
+    rb = ctypes.create_string_buffer(reqs, max(len(reqs), 1))
+    out = np.zeros(max(n, 1) * KV_REPLY_STRIDE, np.uint8)
+    rlen = np.zeros(max(n, 1), np.uint32)
+    lat = np.zeros(max(n, 1), np.uint64)
+    st = np.zeros(6, np.uint64)
+    rc = lib().genesys_kv_client(rb, off.ctypes.data, n, arr.ctypes.data, port_base, n_sockets, timeout_ns,
+                                 out.ctypes.data, rlen.ctypes.data, lat.ctypes.data, st.ctypes.data)
+    names = ("received", "duplicates", "malformed", "send_errors", "max_send_late_ns", "span_ns")
+    stats = {k: int(v) for k, v in zip(names, st)}
+    stats["rc"] = rc
+    reps = [out[j * KV_REPLY_STRIDE: j * KV_REPLY_STRIDE + int(rlen[j])].tobytes() for j in range(n)]
+    return reps, lat[:n], stats

@@ -18,6 +18,10 @@ struct genesys_ctx;
  * workload entry points synchronise before returning). */
 int genesys_internal_scratch(struct genesys_ctx *ctx, size_t bytes, void **out);
 
+/* Staging arena position, and giving back everything allocated after it. */
+uint64_t genesys_internal_staging_mark(struct genesys_ctx *ctx);
+void genesys_internal_staging_release(struct genesys_ctx *ctx, uint64_t mark);
+
 /* CUDA device ordinal of the context (-1 for NULL). */
 int genesys_internal_device(struct genesys_ctx *ctx);
 

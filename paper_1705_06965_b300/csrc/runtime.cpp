@@ -35,6 +35,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <map>
 #include <unordered_map>
 #include <vector>
 
@@ -91,6 +92,7 @@ enum OpIdx { OP_PREAD = 0, OP_PWRITE, OP_SENDTO, OP_RECVFROM, OP_MMAP, OP_MUNMAP
 struct alignas(64) Counters {
   std::atomic<uint64_t> requests{0}, os_calls{0}, failed{0}, nb_failed{0}, bytes{0}, batches{0}, busy_ns{0};
   std::atomic<uint64_t> by_op[8] = {};
+  std::atomic<uint64_t> op_ns[8] = {}, op_max_ns[8] = {};
 };
 
 struct Request {
@@ -131,9 +133,21 @@ struct genesys_ctx {
   std::unique_ptr<Counters[]> counters;             // per ring
   std::mutex svc_mu;                                // NO_THREADS mode: one caller at a time
 
-  // mmap'd regions registered for device access (for munmap)
+  // Regions the GPU mapped with mmap, registered for device access.
+  // cudaHostUnregister waits until no kernel is running, so a GPU munmap
+  // cannot unregister while its own kernel waits for the answer: the region
+  // moves to `released` (still mapped and pinned) and is unregistered and
+  // unmapped at the next genesys_reclaim / shutdown; a later GPU mmap of a
+  // size it fits reuses it instead of mapping and pinning new memory.
+  struct Mapping {
+    void *host;
+    size_t region;     // bytes mapped and registered
+    size_t len;        // bytes the GPU asked for
+  };
   std::mutex map_mu;
-  std::unordered_map<uintptr_t, std::pair<void *, size_t>> maps;  // device address -> host mapping
+  std::unordered_map<uintptr_t, Mapping> maps;      // live: device address -> mapping
+  std::multimap<size_t, std::pair<uintptr_t, Mapping>> released;  // by region size
+  std::atomic<uint64_t> mmap_new{0}, mmap_reused{0};
 
   cudaStream_t aux = nullptr;  // private stream for small copies
   cudaEvent_t ev_start = nullptr, ev_end = nullptr;  // around the last launched kernel
@@ -189,92 +203,90 @@ bool allowed(const genesys_ctx *c, uint32_t nr) {
 
 inline int64_t sys_ret(long r) { return r < 0 ? -(int64_t)errno : (int64_t)r; }
 
-// mmap from the GPU: map on the host, then register the range for device access.
+// mmap from the GPU: an anonymous private mapping is served from a released
+// region of a fitting size when there is one (zeroed, unless the caller passed
+// MAP_UNINITIALIZED because it overwrites the whole region), otherwise mapped
+// with mmap(2) and registered for device access.  Other mappings go straight
+// to mmap(2) + registration.  Returns the device address.
+#ifndef MAP_UNINITIALIZED
+#define MAP_UNINITIALIZED 0x4000000
+#endif
 int64_t do_mmap(genesys_ctx *c, const uint64_t *a) {
-  void *p = mmap((void *)a[0], (size_t)a[1], (int)a[2], (int)a[3], (int)a[4], (off_t)a[5]);
+  const size_t len = (size_t)a[1];
+  const int prot = (int)a[2], flags = (int)a[3], fd = (int)a[4];
+  if (len == 0) return -EINVAL;
+  const bool anon = a[0] == 0 && (flags & MAP_ANONYMOUS) && (flags & MAP_PRIVATE) && a[5] == 0;
+  if (anon && !c->host_only) {
+    std::lock_guard<std::mutex> g(c->map_mu);
+    auto it = c->released.lower_bound(len);
+    if (it != c->released.end() && it->first <= 2 * len) {
+      auto m = it->second;
+      c->released.erase(it);
+      if (!(flags & MAP_UNINITIALIZED)) memset(m.second.host, 0, m.second.region);
+      m.second.len = len;
+      c->maps[m.first] = m.second;
+      c->mmap_reused.fetch_add(1, std::memory_order_relaxed);
+      return (int64_t)m.first;
+    }
+  }
+  void *p = mmap((void *)a[0], len, prot, flags & ~MAP_UNINITIALIZED, fd, (off_t)a[5]);
   if (p == MAP_FAILED) return -(int64_t)errno;
   uintptr_t dev = (uintptr_t)p;
   if (!c->host_only) {
-    if (cudaHostRegister(p, (size_t)a[1], cudaHostRegisterMapped | cudaHostRegisterPortable) != cudaSuccess) {
+    if (cudaHostRegister(p, len, cudaHostRegisterMapped | cudaHostRegisterPortable) != cudaSuccess) {
       cudaGetLastError();
-      munmap(p, (size_t)a[1]);
+      munmap(p, len);
       return -ENOMEM;
     }
     void *d = nullptr;
     if (cudaHostGetDevicePointer(&d, p, 0) != cudaSuccess) {
       cudaGetLastError();
-      cudaHostUnregister(p);
-      munmap(p, (size_t)a[1]);
+      c->released.emplace(len, std::make_pair((uintptr_t)p, genesys_ctx::Mapping{p, len, len}));
       return -ENOMEM;
     }
     dev = (uintptr_t)d;
   }
+  c->mmap_new.fetch_add(1, std::memory_order_relaxed);
   std::lock_guard<std::mutex> g(c->map_mu);
-  c->maps[dev] = {p, (size_t)a[1]};
+  c->maps[dev] = {p, len, len};
   return (int64_t)dev;
 }
 
+// munmap from the GPU (whole GPU-made mappings only): the region is released
+// for reuse; genesys_reclaim unregisters and unmaps it once no kernel runs.
 int64_t do_munmap(genesys_ctx *c, const uint64_t *a) {
-  void *host = nullptr;
-  size_t len = 0;
-  {
-    std::lock_guard<std::mutex> g(c->map_mu);
-    auto it = c->maps.find((uintptr_t)a[0]);
-    if (it == c->maps.end()) return -EINVAL;  // only GPU-made mappings
-    host = it->second.first;
-    len = it->second.second;
-    if ((size_t)a[1] != len) return -EINVAL;   // whole mappings only
+  std::lock_guard<std::mutex> g(c->map_mu);
+  auto it = c->maps.find((uintptr_t)a[0]);
+  if (it == c->maps.end()) return -EINVAL;
+  if ((size_t)a[1] != it->second.len) return -EINVAL;
+  if (c->host_only) {
+    const int r = munmap(it->second.host, it->second.region);
     c->maps.erase(it);
+    return r == 0 ? 0 : -(int64_t)errno;
   }
-  if (!c->host_only && cudaHostUnregister(host) != cudaSuccess) cudaGetLastError();
-  return munmap(host, len) == 0 ? 0 : -(int64_t)errno;
+  c->released.emplace(it->second.region, std::make_pair(it->first, it->second));
+  c->maps.erase(it);
+  return 0;
 }
 
-// pread into device memory through a pinned bounce buffer and a DMA copy.
-struct Bounce {
-  uint8_t *buf = nullptr;
-  size_t cap = 0;
-  cudaStream_t stream = nullptr;
-};
-
-int64_t do_pread_dev(genesys_ctx *c, Bounce &b, const uint64_t *a) {
-  if (c->host_only) return -ENOSYS;
-  if (!b.buf) {
-    b.cap = 8u << 20;
-    if (cudaHostAlloc((void **)&b.buf, b.cap, cudaHostAllocPortable) != cudaSuccess) {
-      cudaGetLastError();
-      b.buf = nullptr;
-      return -ENOMEM;
-    }
-    if (cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) != cudaSuccess) {
-      cudaGetLastError();
-      return -ENOMEM;
-    }
+// Unregister and unmap released regions (and, at shutdown, live ones).
+void reclaim(genesys_ctx *c, bool all) {
+  std::lock_guard<std::mutex> g(c->map_mu);
+  for (auto &kv : c->released) {
+    if (!c->host_only) cudaHostUnregister(kv.second.second.host);
+    munmap(kv.second.second.host, kv.second.second.region);
   }
-  const int fd = (int)a[0];
-  uint8_t *dst = (uint8_t *)a[1];
-  const uint64_t len = a[2], off = a[3];
-  uint64_t got = 0;
-  while (got < len) {
-    const size_t want = (size_t)std::min<uint64_t>(b.cap, len - got);
-    ssize_t r = pread(fd, b.buf, want, (off_t)(off + got));
-    if (r < 0) {
-      if (errno == EINTR) continue;
-      if (got == 0) return -(int64_t)errno;
-      break;
+  c->released.clear();
+  if (all) {
+    for (auto &kv : c->maps) {
+      if (!c->host_only) cudaHostUnregister(kv.second.host);
+      munmap(kv.second.host, kv.second.region);
     }
-    if (r == 0) break;
-    if (cudaMemcpyAsync(dst + got, b.buf, (size_t)r, cudaMemcpyHostToDevice, b.stream) != cudaSuccess ||
-        cudaStreamSynchronize(b.stream) != cudaSuccess) {
-      cudaGetLastError();
-      return -EIO;
-    }
-    got += (uint64_t)r;
+    c->maps.clear();
   }
-  return (int64_t)got;
 }
 
-int64_t execute_one(genesys_ctx *c, Bounce &b, Request &r, Counters &k) {
+int64_t execute_one(genesys_ctx *c, Request &r, Counters &k) {
   const uint64_t *a = r.a;
   k.os_calls.fetch_add(1, std::memory_order_relaxed);
   switch (r.nr) {
@@ -288,8 +300,6 @@ int64_t execute_one(genesys_ctx *c, Bounce &b, Request &r, Counters &k) {
       for (uint64_t i = 0; i < a[1]; ++i) bad += p[i] != sm64_at(a[2], a[3] + i);
       return bad;
     }
-    case GENESYS_NR_PREAD_DEV:
-      return do_pread_dev(c, b, a);
     case SYS_mmap:
       return do_mmap(c, a);
     case SYS_munmap:
@@ -346,17 +356,37 @@ size_t merge_run(genesys_ctx *c, Request *reqs, size_t i, size_t n, Counters &k)
   return j;
 }
 
-void process_batch(genesys_ctx *c, Bounce &b, Request *reqs, size_t n, Counters &k) {
+inline bool is_rw(uint32_t nr) { return nr == SYS_pread64 || nr == SYS_pwrite64; }
+
+void process_batch(genesys_ctx *c, Request *reqs, size_t n, Counters &k) {
   const uint64_t t0 = mono_ns();
+  if (c->cfg.merge && n > 1) {
+    // the requests of a batch are concurrent, so any order is a legal
+    // schedule: put pread/pwrite requests in (call, fd, offset) order so that
+    // neighbours in a file become adjacent and merge
+    std::stable_sort(reqs, reqs + n, [](const Request &x, const Request &y) {
+      const bool rx = is_rw(x.nr), ry = is_rw(y.nr);
+      if (rx != ry) return rx;
+      if (!rx) return false;
+      if (x.nr != y.nr) return x.nr < y.nr;
+      if ((int)x.a[0] != (int)y.a[0]) return (int)x.a[0] < (int)y.a[0];
+      return x.a[3] < y.a[3];
+    });
+  }
   for (size_t i = 0; i < n;) {
     Request &r = reqs[i];
     if (c->cfg.merge && (r.nr == SYS_pread64 || r.nr == SYS_pwrite64)) {
       i = merge_run(c, reqs, i, n, k);
       continue;
     }
-    r.ret = execute_one(c, b, r, k);
+    const uint64_t e0 = mono_ns();
+    r.ret = execute_one(c, r, k);
+    const uint64_t dt = mono_ns() - e0;
+    const int oi = op_index(r.nr);
+    k.op_ns[oi].fetch_add(dt, std::memory_order_relaxed);
+    if (dt > k.op_max_ns[oi].load(std::memory_order_relaxed)) k.op_max_ns[oi].store(dt, std::memory_order_relaxed);
     if (r.ret > 0 && (r.nr == SYS_pread64 || r.nr == SYS_pwrite64 || r.nr == SYS_read || r.nr == SYS_write ||
-                      r.nr == SYS_sendto || r.nr == SYS_recvfrom || r.nr == GENESYS_NR_PREAD_DEV))
+                      r.nr == SYS_sendto || r.nr == SYS_recvfrom))
       k.bytes.fetch_add((uint64_t)r.ret, std::memory_order_relaxed);
     ++i;
   }
@@ -389,7 +419,7 @@ inline void read_request(genesys_ctx *c, uint32_t s, Request *r) {
 
 // Take up to coalesce_max ready requests from ring `ri` and process them as one
 // batch (Sec. 4.2).  Returns the number processed.
-size_t poll_ring(genesys_ctx *c, uint32_t ri, std::vector<Request> &batch, Bounce &b) {
+size_t poll_ring(genesys_ctx *c, uint32_t ri, std::vector<Request> &batch) {
   const uint64_t *ring = c->rings + (size_t)ri * c->ring_cap;
   const uint32_t mask = c->ring_cap - 1;
   uint64_t h = c->head[ri];
@@ -412,7 +442,7 @@ size_t poll_ring(genesys_ctx *c, uint32_t ri, std::vector<Request> &batch, Bounc
       }
     }
   }
-  process_batch(c, b, batch.data(), n, c->counters[ri]);
+  process_batch(c, batch.data(), n, c->counters[ri]);
   c->head[ri] = h + n;
   c->retired[ri].store(h + n, std::memory_order_release);
   return n;
@@ -427,11 +457,10 @@ void service_main(genesys_ctx *c, uint32_t ri) {
   }
   if (!c->host_only) cudaSetDevice(c->device);
   std::vector<Request> batch(std::max<uint32_t>(1, c->cfg.coalesce_max));
-  Bounce b;
   uint64_t last_work = mono_ns();
   uint32_t idle_polls = 0;
   while (!c->stop.load(std::memory_order_relaxed)) {
-    if (poll_ring(c, ri, batch, b)) {
+    if (poll_ring(c, ri, batch)) {
       last_work = 0;
       idle_polls = 0;
       continue;
@@ -447,8 +476,6 @@ void service_main(genesys_ctx *c, uint32_t ri) {
       nanosleep(&ts, nullptr);
     }
   }
-  if (b.buf) cudaFreeHost(b.buf);
-  if (b.stream) cudaStreamDestroy(b.stream);
 }
 
 template <class T>
@@ -508,14 +535,7 @@ void free_all(genesys_ctx *c) {
   if (c->aux) cudaStreamDestroy(c->aux);
   if (c->ev_start) cudaEventDestroy(c->ev_start);
   if (c->ev_end) cudaEventDestroy(c->ev_end);
-  {
-    std::lock_guard<std::mutex> g(c->map_mu);
-    for (auto &kv : c->maps) {
-      if (!c->host_only) cudaHostUnregister(kv.second.first);
-      munmap(kv.second.first, kv.second.second);
-    }
-    c->maps.clear();
-  }
+  reclaim(c, true);
 }
 
 // Ring positions published so far, per ring.  Device memory: read after the
@@ -544,6 +564,12 @@ const char *genesys_last_error(void) { return g_last_error.c_str(); }
 int genesys_internal_error(int code, const char *msg) { return fail(code, "%s", msg); }
 
 int genesys_internal_device(genesys_ctx *c) { return c ? c->device : -1; }
+
+uint64_t genesys_internal_staging_mark(genesys_ctx *c) { return c ? c->staging_used.load() : 0; }
+
+void genesys_internal_staging_release(genesys_ctx *c, uint64_t mark) {
+  if (c) c->staging_used.store(mark);
+}
 
 int genesys_internal_scratch(genesys_ctx *c, size_t bytes, void **out) {
   if (!c || !out) return fail(GENESYS_EINVAL, "NULL argument");
@@ -614,12 +640,17 @@ int genesys_init(const genesys_config *cfg_in, int device, genesys_ctx **out) {
   if (cfg.n_slots < 32) cfg.n_slots = 32;
   c->cfg = cfg;
 
-  // doorbell rings: ring r receives the slots s with (s / 32) % n_rings == r,
-  // at most ceil(n_slots / 32 / n_rings) * 32 of them, each with at most one
-  // request outstanding - so a ring of that capacity can never overflow.
-  const uint64_t groups = (cfg.n_slots + 31) / 32;
-  const uint64_t per_ring = ((groups + cfg.n_service_threads - 1) / cfg.n_service_threads) * 32;
-  c->ring_cap = (uint32_t)next_pow2(std::max<uint64_t>(per_ring, 64));
+  // doorbell rings: ring r receives the slots s with genesys_ring_of(s) == r,
+  // each with at most one request outstanding - so a ring whose capacity is
+  // the largest number of slots that map to one ring can never overflow.
+  {
+    std::vector<uint64_t> per(cfg.n_service_threads, 0);
+    const uint32_t gsz = 1u << GENESYS_RING_GROUP_SHIFT;
+    for (uint64_t s0 = 0; s0 < cfg.n_slots; s0 += gsz)
+      per[genesys_ring_of((uint32_t)s0, cfg.n_service_threads)] += std::min<uint64_t>(gsz, cfg.n_slots - s0);
+    const uint64_t most = *std::max_element(per.begin(), per.end());
+    c->ring_cap = (uint32_t)next_pow2(std::max<uint64_t>(most, 64));
+  }
 
   int rc;
   auto cleanup = [&](int code) { free_all(c.get()); return code; };
@@ -663,10 +694,7 @@ int genesys_drain(genesys_ctx *c, uint64_t timeout_ns) {
       if (c->cfg.flags & GENESYS_INIT_NO_THREADS) {
         std::lock_guard<std::mutex> g(c->svc_mu);
         std::vector<Request> batch(std::max<uint32_t>(1, c->cfg.coalesce_max));
-        Bounce b;
-        poll_ring(c, r, batch, b);
-        if (b.buf) cudaFreeHost(b.buf);
-        if (b.stream) cudaStreamDestroy(b.stream);
+        poll_ring(c, r, batch);
       } else {
         std::this_thread::sleep_for(std::chrono::microseconds(5));
       }
@@ -766,19 +794,48 @@ int genesys_service(genesys_ctx *c, uint64_t timeout_ns) {
   if (c->cfg.flags & GENESYS_INIT_NO_THREADS) {
     std::lock_guard<std::mutex> g(c->svc_mu);
     std::vector<Request> batch(std::max<uint32_t>(1, c->cfg.coalesce_max));
-    Bounce b;
     int total = 0;
     do {
       size_t n = 0;
-      for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) n += poll_ring(c, r, batch, b);
+      for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) n += poll_ring(c, r, batch);
       total += (int)n;
       if (n == 0) cpu_relax();
     } while (mono_ns() < until);
-    if (b.buf) cudaFreeHost(b.buf);
-    if (b.stream) cudaStreamDestroy(b.stream);
     return total;
   }
   return genesys_drain(c, timeout_ns);
+}
+
+int genesys_mmap_reserve(genesys_ctx *c, const uint64_t *sizes, uint32_t n) {
+  if (!c || (!sizes && n)) return fail(GENESYS_EINVAL, "NULL argument");
+  if (c->host_only) return fail(GENESYS_EINVAL, "host-only context");
+  for (uint32_t i = 0; i < n; ++i) {
+    const size_t len = (size_t)((sizes[i] + 4095) & ~uint64_t(4095));
+    if (len == 0) continue;
+    void *p = mmap(nullptr, len, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+    if (p == MAP_FAILED) return fail(GENESYS_ENOMEM, "mmap of %zu bytes failed", len);
+    if (cudaHostRegister(p, len, cudaHostRegisterMapped | cudaHostRegisterPortable) != cudaSuccess) {
+      cudaGetLastError();
+      munmap(p, len);
+      return fail(GENESYS_ECUDA, "cudaHostRegister of %zu bytes failed", len);
+    }
+    void *d = nullptr;
+    if (cudaHostGetDevicePointer(&d, p, 0) != cudaSuccess) {
+      cudaGetLastError();
+      cudaHostUnregister(p);
+      munmap(p, len);
+      return fail(GENESYS_ECUDA, "cudaHostGetDevicePointer failed");
+    }
+    std::lock_guard<std::mutex> g(c->map_mu);
+    c->released.emplace(len, std::make_pair((uintptr_t)d, genesys_ctx::Mapping{p, len, len}));
+  }
+  return 0;
+}
+
+int genesys_reclaim(genesys_ctx *c) {
+  if (!c) return fail(GENESYS_EINVAL, "ctx is NULL");
+  reclaim(c, false);
+  return 0;
 }
 
 int genesys_stats_get(genesys_ctx *c, genesys_stats *o) {
@@ -793,8 +850,14 @@ int genesys_stats_get(genesys_ctx *c, genesys_stats *o) {
     o->bytes += k.bytes.load();
     o->batches += k.batches.load();
     o->busy_ns += k.busy_ns.load();
-    for (int i = 0; i < 8; ++i) o->by_op[i] += k.by_op[i].load();
+    for (int i = 0; i < 8; ++i) {
+      o->by_op[i] += k.by_op[i].load();
+      o->op_ns[i] += k.op_ns[i].load();
+      o->op_max_ns[i] = std::max<uint64_t>(o->op_max_ns[i], k.op_max_ns[i].load());
+    }
   }
+  o->mmap_new = c->mmap_new.load();
+  o->mmap_reused = c->mmap_reused.load();
   return 0;
 }
 
@@ -803,7 +866,7 @@ int genesys_stats_reset(genesys_ctx *c) {
   for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) {
     Counters &k = c->counters[r];
     k.requests = 0; k.os_calls = 0; k.failed = 0; k.nb_failed = 0; k.bytes = 0; k.batches = 0; k.busy_ns = 0;
-    for (int i = 0; i < 8; ++i) k.by_op[i] = 0;
+    for (int i = 0; i < 8; ++i) k.by_op[i] = 0, k.op_ns[i] = 0, k.op_max_ns[i] = 0;
   }
   return 0;
 }
@@ -900,7 +963,7 @@ int genesys_emulate_call(genesys_ctx *c, uint32_t nr, const uint64_t args[6], ui
   for (int i = 0; i < 6; ++i) __atomic_store_n(&sl->args[i], args[i], __ATOMIC_RELAXED);
   __atomic_store_n(&sl->req, ((uint64_t)nsq << 32) | ((uint64_t)(nr & 0xFFFFu) << 16) | (flags & 0xFFFFu),
                    __ATOMIC_RELEASE);
-  const uint32_t r = (s >> 5) % c->cfg.n_service_threads;
+  const uint32_t r = genesys_ring_of(s, c->cfg.n_service_threads);
   const uint32_t pos = __atomic_fetch_add(&c->ring_tail[r * 32], 1u, __ATOMIC_ACQ_REL);
   __atomic_store_n(&c->rings[(size_t)r * c->ring_cap + (pos & (c->ring_cap - 1))], GENESYS_RING_ENTRY(pos, s),
                    __ATOMIC_RELEASE);

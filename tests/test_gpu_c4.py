@@ -1,0 +1,62 @@
+"""GPU parity for C4 (key-value service over UDP, Sec. 7.3): a persistent GPU
+kernel receives request batches with recvmmsg and answers with sendmmsg; every
+reply's bytes equal the sequential CPU server's (the oracle replays the same
+requests in client sequence order), and the table's final values match."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def G():
+    import paper_1705_06965_b300 as G
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return G
+
+
+@pytest.fixture(scope="module")
+def ctx(G):
+    c = G.Context(device=0, service_threads=8, staging_bytes=128 << 20, deadline_ns=10_000_000_000)
+    yield c
+    c.close()
+
+
+def _port():
+    return 20000 + (os.getpid() * 97) % 30000
+
+
+@pytest.mark.parametrize("n_sockets,batch,rate", [(8, 64, 100_000.0), (1, 16, 50_000.0), (32, 32, 200_000.0)])
+def test_c4_replies_bit_exact(G, ctx, n_sockets, batch, rate):
+    p = dict(workloads.C4_SMALL, rate_per_s=rate)
+    tr = workloads.kv_trace(p)
+    want = oracle.c4_replay(tr)
+    reqs, off = workloads.kv_request_bytes(tr)
+    port = _port() + n_sockets
+    srv = G.KVServer(ctx, tr.keys, tr.vlen0, tr.vseed0, n_sockets=n_sockets, batch=batch, port_base=port)
+    try:
+        reps, lat, st = G.kv_client(reqs, off, tr.arrival_ns, port, n_sockets)
+        # final value of the most popular keys, read back from device memory
+        hot = np.bincount(tr.key_idx, minlength=len(tr.keys)).argsort()[::-1][:5]
+        final = {int(k): srv.value(int(k)) for k in hot}
+    finally:
+        served = srv.stop()
+    assert st["rc"] == 0 and st["received"] == len(tr), st
+    assert st["duplicates"] == 0 and st["malformed"] == 0
+    bad = [j for j in range(len(tr)) if reps[j] != want[j]]
+    assert not bad, (len(bad), bad[:5])
+    assert served == len(tr)
+    assert np.all(lat > 0)
+    for k, v in final.items():
+        sets = np.where((tr.key_idx == k) & (tr.op == workloads.KV_SET))[0]
+        expect = (workloads.stream_bytes(int(tr.vseed[sets[-1]]), int(tr.vlen[sets[-1]])) if len(sets)
+                  else tr.value0(k))
+        assert v == expect

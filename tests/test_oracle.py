@@ -271,3 +271,57 @@ def test_c5_trace_shape():
     assert np.all(np.sort(pw["out_off"])[1:] >= ends[:-1])          # disjoint pwrite ranges
     mm = tr.ops[live & (tr.ops["kind"] == 2)]
     assert np.all(mm["len"] % 4096 == 0) and mm["len"].min() >= 4096
+
+
+# ------------------------------------------------------------------------- C4
+
+def test_c4_replay_closed_forms():
+    p = dict(workloads.C4_SMALL, n_keys=512, n_requests=3000)
+    tr = workloads.kv_trace(p)
+    reps = oracle.c4_replay(tr)
+    last_set = {}
+    for j in range(len(tr)):
+        k, op, r = int(tr.key_idx[j]), int(tr.op[j]), reps[j]
+        assert r[4:8] == j.to_bytes(4, "little")                 # seq echoed
+        if op == workloads.KV_SET:
+            assert r == bytes([0x81, 0, 0, 0]) + j.to_bytes(4, "little")
+            last_set[k] = j
+        else:
+            assert r[0] == 0x80 and r[1] == 0
+            if k in last_set:                                    # the latest SET of the key
+                js = last_set[k]
+                want = workloads.stream_bytes(int(tr.vseed[js]), int(tr.vlen[js]))
+            else:                                                # never SET: the preload value
+                want = tr.value0(k)
+            assert int.from_bytes(r[2:4], "little") == len(want) and r[8:] == want
+
+
+def test_c4_unknown_key_and_get_only_trace():
+    p = dict(workloads.C4_SMALL, n_keys=64, n_requests=200, get_frac=1.0)
+    tr = workloads.kv_trace(p)
+    reps = oracle.c4_replay(tr)
+    for j in range(len(tr)):
+        assert reps[j][8:] == tr.value0(int(tr.key_idx[j]))    # pure function of the key
+    # a key that is not in the table: status 1, no value (hand-made datagram)
+    import ctypes
+    absent = bytes(16)
+    assert absent not in {k.tobytes() for k in tr.keys}
+    dgram = bytes([0, 0, 0, 0]) + (7).to_bytes(4, "little") + absent
+    vals = np.zeros((len(tr.keys), 1024), np.uint8)
+    vl = tr.vlen0.astype(np.uint16).copy()
+    out = np.zeros(64, np.uint8)
+    off = np.zeros(2, np.uint64)
+    keys = np.ascontiguousarray(tr.keys)
+    n = oracle._L().oracle_c4_replay(keys.ctypes.data, len(keys), vals.ctypes.data, vl.ctypes.data,
+                                     ctypes.create_string_buffer(dgram, len(dgram)), 1, out.ctypes.data,
+                                     off.ctypes.data)
+    assert n == 8 and out[:8].tobytes() == bytes([0x80, 1, 0, 0, 7, 0, 0, 0])
+
+
+def test_c4_zipf_and_mix():
+    tr = workloads.kv_trace(workloads.C4_SMALL)
+    frac_set = (tr.op == workloads.KV_SET).mean()
+    assert 0.08 < frac_set < 0.12
+    counts = np.bincount(tr.key_idx, minlength=len(tr.keys))
+    assert counts[0] == counts.max()                              # rank 1 is the most popular key
+    assert tr.vlen0.min() >= 64 and tr.vlen0.max() <= 1024

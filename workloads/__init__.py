@@ -243,3 +243,84 @@ def c5_trace(params: dict | None = None) -> Trace:
     d = scratch_dir("c5_%x_%d_%d" % (p["seed"], p["n_files"], fb))
     paths = [c1_file(os.path.join(d, f"in{f:02d}.bin"), fb, seed=p["seed"] + 1 + f) for f in range(p["n_files"])]
     return Trace(arrival.astype(np.uint64), threads, n_ops, ops, paths, out_off, p)
+
+
+# ------------------------------------------------------------------------ C4
+# Key-value serving over UDP: 1M 16-byte keys preloaded with values of
+# 64..1024 bytes; requests GET (90%) / SET (10%) with Zipf(0.99) key popularity
+# and Poisson arrivals.  All byte strings derive from splitmix64 streams.
+
+C4_FULL = dict(n_keys=1 << 20, n_requests=1 << 20, zipf_s=0.99, get_frac=0.9, rate_per_s=200_000.0,
+               seed=SEED_C4)
+C4_SMALL = dict(n_keys=1 << 14, n_requests=20_000, zipf_s=0.99, get_frac=0.9, rate_per_s=100_000.0, seed=SEED_C4)
+KV_GET, KV_SET, KV_STOP = 0, 1, 2
+KV_VMIN, KV_VMAX = 64, 1024
+
+
+def _sm_vec(seed: int, idx: np.ndarray) -> np.ndarray:
+    """splitmix64_at(seed, idx) for an index array (numpy uint64 arithmetic)."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + (idx.astype(np.uint64) + np.uint64(1)) * np.uint64(GAMMA)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+@dataclass
+class KVTrace:
+    keys: np.ndarray          # uint8 [n_keys, 16]
+    vlen0: np.ndarray         # uint16 [n_keys]: preload value lengths
+    vseed0: np.ndarray        # uint64 [n_keys]: preload value = stream_bytes(vseed0[i], vlen0[i])
+    op: np.ndarray            # uint8 [n]
+    key_idx: np.ndarray       # uint32 [n]
+    vlen: np.ndarray          # uint16 [n] (SET)
+    vseed: np.ndarray         # uint64 [n] (SET value = stream_bytes(vseed[j], vlen[j]))
+    arrival_ns: np.ndarray    # uint64 [n]
+    params: dict = field(default_factory=dict)
+
+    def __len__(self):
+        return len(self.op)
+
+    def value0(self, i: int) -> bytes:
+        return stream_bytes(int(self.vseed0[i]), int(self.vlen0[i]))
+
+
+def kv_trace(params: dict | None = None) -> KVTrace:
+    p = dict(C4_FULL if params is None else params)
+    s = p["seed"]
+    nk, n = p["n_keys"], p["n_requests"]
+    kw = _sm_vec(s ^ 0x1111, np.arange(2 * nk, dtype=np.uint64)).reshape(nk, 2)
+    keys = kw.view(np.uint8).reshape(nk, 16).copy()
+    if len(np.unique(keys.view([("a", "<u8"), ("b", "<u8")]))) != nk:
+        raise RuntimeError("duplicate keys")
+    vlen0 = (KV_VMIN + _sm_vec(s ^ 0x2222, np.arange(nk)) % np.uint64(KV_VMAX - KV_VMIN + 1)).astype(np.uint16)
+    vseed0 = _sm_vec(s ^ 0x3333, np.arange(nk))
+    rng = np.random.default_rng(s)
+    ranks = np.arange(1, nk + 1, dtype=np.float64)
+    cdf = np.cumsum(ranks ** -p["zipf_s"])
+    cdf /= cdf[-1]
+    key_idx = np.searchsorted(cdf, rng.random(n), side="right").astype(np.uint32)
+    key_idx = np.minimum(key_idx, nk - 1)
+    op = np.where(rng.random(n) < p["get_frac"], KV_GET, KV_SET).astype(np.uint8)
+    vlen = np.where(op == KV_SET, rng.integers(KV_VMIN, KV_VMAX + 1, n), 0).astype(np.uint16)
+    vseed = _sm_vec(s ^ 0x4444, np.arange(n))
+    arrival = (np.cumsum(rng.exponential(1.0 / p["rate_per_s"], n)) * 1e9).astype(np.uint64)
+    return KVTrace(keys, vlen0, vseed0, op, key_idx, vlen, vseed, arrival, p)
+
+
+def kv_request_bytes(trace: KVTrace, idx=None) -> tuple[bytes, np.ndarray]:
+    """Request datagrams of a KV trace (in the given order), back to back, and
+    their offsets (n + 1).  Layout: op u8, pad u8, vlen u16, seq u32, key[16],
+    value[vlen] (SET)."""
+    idx = np.arange(len(trace)) if idx is None else np.asarray(idx)
+    parts, offs, pos = [], [], 0
+    for j in idx:
+        op, kl = int(trace.op[j]), int(trace.vlen[j])
+        d = bytes([op, 0]) + kl.to_bytes(2, "little") + int(j).to_bytes(4, "little")
+        d += trace.keys[trace.key_idx[j]].tobytes()
+        if op == KV_SET:
+            d += stream_bytes(int(trace.vseed[j]), kl)
+        offs.append(pos)
+        parts.append(d)
+        pos += len(d)
+    return b"".join(parts), np.array(offs + [pos], np.uint64)
