@@ -73,6 +73,25 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+# ---------------------------------------------------------------- replicas
+def reduce_max(values, device=None):
+    """Element-wise max of per-rank values over all ranks (identity with one
+    rank).  Multi-GPU runs are independent replicas: the slowest rank's time
+    is the job's time."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_value(world: int, units_per_rank: float, max_seconds: float) -> float:
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / max_seconds
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
@@ -151,21 +170,33 @@ def pctl(a, q):
     return float(np.percentile(a, q)) if len(a) else None
 
 
-def load_traffic(kernel: str):
-    """ncu host-link traffic (bytes per launch) of `kernel` from the committed
-    profile summary, or None if the kernel source changed since the capture."""
+def kernel_src_hash(kernel: str) -> str:
+    """Hash of what a kernel's counters depend on: the device protocol headers
+    and the kernel's own section of its source file."""
     import hashlib
+    h = hashlib.sha1()
+    for f in ("include/genesys_device.cuh", "include/genesys_layout.h"):
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if kernel.startswith("c2_pwrite_kernel"):
+        src = open(os.path.join(ROOT, "paper_1705_06965_b300/csrc/workloads.cu")).read()
+        a = src.index("// ------------------------------------------------------------------- C2")
+        b = src.index("// ------------------------------------------------------- visibility probe")
+        h.update(src[a:b].encode())
+    return h.hexdigest()[:12]
+
+
+def load_traffic(kernel: str, units_per_launch: float):
+    """ncu host-link traffic (bytes per launch) of `kernel`: the committed
+    per-unit figure times the units of an average launch, or None if there is
+    no figure or the kernel's source changed since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    h = hashlib.sha1()
-    for f in ("paper_1705_06965_b300/csrc/workloads.cu", "include/genesys_device.cuh"):
-        h.update(open(os.path.join(ROOT, f), "rb").read())
-    src = h.hexdigest()[:12]
+    src = kernel_src_hash(kernel)
     for ln in open(path):
         parts = ln.split()
-        if len(parts) >= 3 and parts[0] == kernel and parts[1] == src:
-            return float(parts[2])
+        if len(parts) >= 4 and not ln.startswith("#") and parts[0] == kernel and parts[1] == src:
+            return round(float(parts[2]) * units_per_launch)
     return None
 
 
@@ -287,7 +318,8 @@ def run_only(args):
     rank, local, _ = dist_env()
     torch.cuda.set_device(local)
     kind, _, rest = args.only.partition(":")
-    rig = Rig(args, local, rank, need_scan=kind == "c1" and rest.split(":")[-1] != str(C1_BYTES))
+    rig = Rig(args, local, rank, need_scan=kind == "c1" and rest.split(":")[-1] != str(C1_BYTES),
+              need_c3=kind == "c3", service_threads=args.service_threads)
     G = rig.G
     out = {"only": args.only}
     try:
@@ -378,6 +410,71 @@ def profile_extras(args, rig, local, rank, link):
             os.close(fd)
     out["served_c5"] = serve_c5(G, local, rank)
     out["kv_c4"] = serve_c4(G, local, rank)
+    out["fig6_block_permutation"] = study_fig6(G, rig, local)
+    out["fig7_coalescing"] = study_fig7(G, rig, local, rank)
+    return out
+
+
+def study_fig6(G, rig, local, n_blocks=4096, iters=(1, 2, 4, 8, 16, 32, 64)):
+    """Sec. 6 / Fig. 6: time per permutation iteration of 8 KiB blocks (1024
+    threads per work-group) followed by a work-group pwrite, for the four
+    ordering x blocking combinations."""
+    import numpy as np
+    import torch
+    import workloads
+    data, perm = workloads.c6_inputs(n_blocks)
+    d_in = torch.from_numpy(data).to(rig.dev)
+    d_perm = torch.from_numpy(perm.view(np.int16)).to(rig.dev)
+    path = os.path.join(rig.d, "c6.bin")
+    out = {"blocks": n_blocks, "us_per_iteration": {}}
+    with G.Context(device=local, service_threads=4, staging_bytes=n_blocks * 8192 + (1 << 20)) as ctx:
+        st = ctx.staging(n_blocks * 8192)
+        fd = os.open(path, os.O_CREAT | os.O_RDWR, 0o644)
+        try:
+            for relaxed in (False, True):
+                for nb in (False, True):
+                    key = f"{'weak' if relaxed else 'strong'}-{'non-block' if nb else 'block'}"
+                    row = {}
+                    for it in iters:
+                        fn = lambda: ctx.c6_permute(fd, d_in.data_ptr(), d_perm.data_ptr(), n_blocks, it,  # noqa
+                                                    relaxed, nb, st, n_blocks * 8192)
+                        fn()
+                        ms = min(rig.timed(fn) for _ in range(3))
+                        row[str(it)] = round(ms * 1e3 / it, 2)
+                    out["us_per_iteration"][key] = row
+        finally:
+            os.close(fd)
+    return out
+
+
+def study_fig7(G, rig, local, rank, sizes=(256 << 10, 1 << 20, 4 << 20, 16 << 20, 64 << 20), groups=64):
+    """Sec. 6 / Fig. 7: a fixed number of work-groups each read 1/64 of a file
+    with one pread (more bytes per call for larger files); time per requested
+    byte without coalescing, with up to 8 requests per service batch (20 us
+    window), and with batching plus merging of contiguous reads."""
+    import workloads
+    d = workloads.scratch_dir(f"bench_fig7_r{rank}")
+    paths = {n: workloads.c1_file(os.path.join(d, f"f{n}.bin"), n, seed=0x5EED0007) for n in sizes}
+    modes = {"no_coalescing": dict(coalesce_max=1, merge=False),
+             "batch_le_8": dict(coalesce_max=8, coalesce_window_ns=20_000, merge=False),
+             "batch_le_8_merge": dict(coalesce_max=8, coalesce_window_ns=20_000, merge=True)}
+    out = {"groups": groups, "ns_per_byte": {}}
+    for mode, kw in modes.items():
+        row = {}
+        with G.Context(device=local, service_threads=4, staging_bytes=(64 << 20) + (1 << 20), **kw) as ctx:
+            st = ctx.staging(64 << 20)
+            for n, p in paths.items():
+                fd = os.open(p, os.O_RDONLY)
+                try:
+                    chunk = n // groups
+                    fn = lambda: ctx.c1_histogram(fd, n, rig.hist[0].data_ptr(), st, 64 << 20, chunk=chunk,  # noqa
+                                                  groups=groups, threads=256, form=G.FORM_PLAIN)
+                    fn()
+                    ms = min(rig.timed(fn) for _ in range(3))
+                    row[str(n)] = round(ms * 1e6 / n, 4)
+                finally:
+                    os.close(fd)
+        out["ns_per_byte"][mode] = row
     return out
 
 
@@ -510,14 +607,9 @@ def run_genesys(args):
     if not (np.array_equal(h[0].numpy().view(np.uint32), want) and np.array_equal(h[1].numpy().view(np.uint32), want)):
         raise RuntimeError("C1 histogram differs from the oracle")
 
-    tot_ms, e2e_tot = sum(step_ms), sum(e2e_s)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([tot_ms, e2e_tot], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms, e2e_tot = float(t[0]), float(t[1])
+    tot_ms, e2e_tot = reduce_max([sum(step_ms), sum(e2e_s)], dev)
     calls_step = c2_calls + c1_calls
-    value = world * calls_step * args.steps / (tot_ms * 1e-3)
+    value = job_value(world, calls_step * args.steps, tot_ms * 1e-3)
 
     # ---- profile pass (untimed): per-combination rate and latency at 2^20,
     # latency of the plain form at every size, plain vs batched forms,
@@ -545,7 +637,7 @@ def run_genesys(args):
     batched = sweep[batched_key]
 
     link = host_link_peak(torch)
-    extras = profile_extras(args, rig, local, rank, link)
+    extras = profile_extras(args, rig, local, rank, link) if args.extras else {}
     # dominant kernel of the timed region and its host-link roofline
     tot = {k: sum(v) for k, v in kernel_ms.items()}
     dom = max(tot, key=tot.get)
@@ -557,20 +649,22 @@ def run_genesys(args):
     if dom.startswith("c2_pwrite_kernel"):
         gname = dom.split("<")[1].split(",")[0]
         gr = {v: k for k, v in G.GRAN_NAMES.items()}[gname]
-        per = [nn * 64 + calls_for(g, bt, nn) * 80 for nn in SIZES for name, g, bt, relaxed, nb in COMBOS
+        sel = [(nn, g, bt) for nn in SIZES for name, g, bt, relaxed, nb in COMBOS
                if g == gr and ("relaxed" if relaxed else "strong") in dom and ("nonblocking" in dom) == nb]
-        alg_bytes = statistics.mean(per)
+        alg_bytes = statistics.mean(nn * 64 + calls_for(g, bt, nn) * 80 for nn, g, bt in sel)
+        units = statistics.mean(nn for nn, _, _ in sel)
     else:
         alg_bytes = C1_BYTES + (C1_BYTES // C1_CHUNK) * 80
+        units = C1_BYTES
     achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
     peak = link["d2h"] if dom.startswith("c2") else link["h2d"]
     roofline = {"bound": "host_link", "kernel": dom, "achieved": round(achieved, 3), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 5), "traffic": load_traffic(dom),
+                "frac": round(achieved / peak, 5), "traffic": load_traffic(dom, units),
                 "peak_source": "pinned cudaMemcpy 256 MiB in this run (of measured)",
                 "alg_bytes_per_launch": int(alg_bytes), "avg_launch_ms": round(avg_ms, 4),
                 "share_of_timed_device_time": round(tot[dom] / sum(tot.values()), 4)}
 
-    cpu = cpu_baseline_sample(budget_s=20.0) if rank == 0 else None
+    cpu = cpu_baseline_sample(budget_s=20.0) if rank == 0 and args.extras else None
 
     line = {
         "metric": "GPU syscalls/s (C2 pwrite invocation sweep + C1 pread pass)",
@@ -586,7 +680,7 @@ def run_genesys(args):
                    "coalesce_max": step_cfg["coalesce_max"],
                    "l2": "256 MiB device buffer written between timed steps (L2 flush)",
                    "parallelism": f"replicas x{world}"},
-        "requests_per_s": round(world * (sum(SIZES) * len(COMBOS) + c1_calls) * args.steps / (tot_ms * 1e-3), 1),
+        "requests_per_s": round(job_value(world, (sum(SIZES) * len(COMBOS) + c1_calls) * args.steps, tot_ms * 1e-3), 1),
         "forms": {"plain_blocking_strong": {"combo": "work-item/strong/blocking", **plain},
                   "batched": {"combo": batched_key, **batched}},
         "plain_latency_by_threads": lat_by_size,
@@ -594,10 +688,10 @@ def run_genesys(args):
         **extras,
         "autotuned_step": {"best": step_cfg, "table": step_table},
         "host_link_GB_per_s": link,
-        "service": {k: stats[k] for k in ("requests", "os_calls", "batches", "bytes", "failed")},
+        "service": {k: stats[k] for k in ("requests", "os_calls", "batches", "bytes", "failed", "busy_ns")},
         "roofline": roofline,
         "cpu_baseline": cpu,
-        "e2e": {"value": round(world * calls_step * args.steps / e2e_tot, 1), "unit": "syscalls/s",
+        "e2e": {"value": round(job_value(world, calls_step * args.steps, e2e_tot), 1), "unit": "syscalls/s",
                 "h2d_bytes_per_step": 2 * C1_BYTES,
                 "d2h_bytes_per_step": sum(SIZES) * 64 * len(COMBOS) + 2 * 1024 + 32},
         "clocks": clocks,
@@ -677,6 +771,7 @@ def main():
     ap.add_argument("--impl", default="genesys", choices=["genesys", "reference"])
     ap.add_argument("--service-threads", type=int, default=4)
     ap.add_argument("--autotune", type=int, default=1, help="autotune the step's context knobs (cached)")
+    ap.add_argument("--extras", type=int, default=1, help="0: only the timed step (for launch lists)")
     ap.add_argument("--only", default=None, help="run one case: c2:<grain>/<order>/<block>:<threads>, "
                                                  "c1:<plain|batched>:<bytes>, c3:<plain|batched>")
     args = ap.parse_args()

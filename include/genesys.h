@@ -375,6 +375,25 @@ int genesys_kv_client(const uint8_t *reqs, const uint64_t *req_off, uint64_t n, 
                       uint16_t port_base, uint32_t n_sockets, uint64_t timeout_ns, uint8_t *replies,
                       uint32_t *reply_len, uint64_t *latency_ns, uint64_t *stats);
 
+/* C6, block permutation (Sec. 6, Fig. 6): n_blocks thread blocks of 1024
+ * threads each take one 8 KiB block of input_dev (device), permute it `iters`
+ * times with out[i] = in[perm_dev[i]] (perm_dev: 8192 uint16, device), copy it
+ * to staging + b * 8 KiB (host-mapped, >= n_blocks * 8 KiB) and pwrite it to
+ * fd at offset b * 8 KiB at work-group grain, strong or relaxed, blocking or
+ * non-blocking - the four combinations of Fig. 6. */
+int genesys_c6_permute(genesys_ctx *ctx, int fd, const uint8_t *input_dev, const uint16_t *perm_dev, uint64_t n_blocks,
+                       uint32_t iters, uint32_t relaxed, uint32_t nonblocking, void *staging, uint64_t staging_bytes,
+                       void *stream);
+
+/* One system call made from GPU code (Sec. 5: any system call, function-like):
+ * one block of `threads` threads calls `nr` with args[6] at work-item (1
+ * thread), warp or work-group grain, strong and blocking; the result (>= 0 or
+ * -errno) is stored to *ret_dev (device, int64).  Pointer arguments must be
+ * host-usable addresses (staging).  A failed call is a result, not an error
+ * of this function; a device-side timeout is GENESYS_EDEVICE. */
+int genesys_gpu_call(genesys_ctx *ctx, uint32_t nr, const uint64_t args[6], uint32_t gran, uint32_t threads,
+                     long long *ret_dev, void *stream);
+
 /* Strong-ordering visibility probe (Sec. 4.1: strong ordering means every
  * store before the call has completed): n_threads threads each store their
  * 8-byte word splitmix64_at(seed, gid) into probe[gid] (host-mapped), then a

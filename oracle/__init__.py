@@ -54,6 +54,9 @@ def _L():
         L.oracle_c4_replay.restype = ctypes.c_int64
         L.oracle_c4_replay.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]
+        L.oracle_c6_permute.restype = ctypes.c_int64
+        L.oracle_c6_permute.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint32,
+                                        ctypes.c_char_p]
         L.oracle_c5_checksum.restype = ctypes.c_uint64
         L.oracle_c5_checksum.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
         L.oracle_c5_request.restype = ctypes.c_int64
@@ -180,3 +183,15 @@ def c4_replay(trace, idx=None):
     _check(_L().oracle_c4_replay(keys.ctypes.data, nk, vals.ctypes.data, vlens.ctypes.data, rb, n,
                                  out.ctypes.data, off.ctypes.data), "c4_replay")
     return [out[int(off[i]):int(off[i + 1])].tobytes() for i in range(n)]
+
+
+def c6_permute(input_bytes: np.ndarray, perm: np.ndarray, iters: int, path: str) -> int:
+    """C6 (Sec. 6, Fig. 6 block permutation): permute each 8 KiB block `iters`
+    times (out[i] = in[perm[i]]) and pwrite it at its own offset; returns the
+    number of pwrite calls."""
+    a = np.ascontiguousarray(input_bytes, dtype=np.uint8)
+    p = np.ascontiguousarray(perm, dtype=np.uint16)
+    if a.size % 8192 or p.size != 8192:
+        raise ValueError("input must be whole 8 KiB blocks, perm 8192 entries")
+    return _check(_L().oracle_c6_permute(a.ctypes.data, a.size // 8192, p.ctypes.data, iters, path.encode()),
+                  "c6_permute")

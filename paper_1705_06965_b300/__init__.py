@@ -43,7 +43,7 @@ EXPORTS = [
     "genesys_c1_histogram", "genesys_c2_pwrite", "genesys_visibility_probe", "genesys_last_launch_ms",
     "genesys_c3_wordcount", "genesys_c3_wordcount_noalloc", "genesys_serve_config_default", "genesys_c5_serve",
     "genesys_reclaim", "genesys_mmap_reserve", "genesys_kv_start", "genesys_kv_stop", "genesys_kv_value",
-    "genesys_kv_client",
+    "genesys_kv_client", "genesys_c6_permute", "genesys_gpu_call",
 ]
 
 
@@ -142,6 +142,8 @@ def lib() -> ctypes.CDLL:
                                             ctypes.POINTER(vp)]),
         "genesys_kv_stop": (ctypes.c_int, [vp, u64, ctypes.POINTER(u64)]),
         "genesys_kv_value": (ctypes.c_int, [vp, u32, vp]),
+        "genesys_c6_permute": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, u64, u32, u32, u32, vp, u64, vp]),
+        "genesys_gpu_call": (ctypes.c_int, [vp, u32, ctypes.POINTER(u64), u32, u32, vp, vp]),
         "genesys_kv_client": (ctypes.c_int, [vp, vp, u64, vp, ctypes.c_uint16, u32, u64, vp, vp, vp, vp]),
         "genesys_c5_serve": (ctypes.c_int, [vp, vp, u32, vp, u32, ctypes.c_int32, ctypes.POINTER(ServeConfig), vp, vp,
                                             ctypes.POINTER(ServeStats)]),
@@ -345,6 +347,21 @@ class Context:
                                       ctypes.byref(sc), res.ctypes.data, lat.ctypes.data, ctypes.byref(st)),
                "genesys_c5_serve")
         return res[:n], lat[:n], {f: int(getattr(st, f)) for f, _ in ServeStats._fields_}
+
+    def gpu_call(self, nr: int, args=(), gran: int = GRAN_GROUP, threads: int = 128, stream=None) -> int:
+        """Make one system call from GPU code; returns its result (>= 0 or -errno)."""
+        import torch
+        a = (ctypes.c_uint64 * 6)(*[int(x) & ((1 << 64) - 1) for x in list(args) + [0] * (6 - len(args))])
+        out = torch.zeros(1, dtype=torch.int64, device=f"cuda:{self.device}")
+        _check(lib().genesys_gpu_call(self.handle, nr, a, gran, threads, out.data_ptr(), _stream_handle(stream)),
+               "genesys_gpu_call")
+        return int(out.item())
+
+    def c6_permute(self, fd: int, input_dev_ptr: int, perm_dev_ptr: int, n_blocks: int, iters: int, relaxed: bool,
+                   nonblocking: bool, staging: int, staging_bytes: int, stream=None) -> None:
+        _check(lib().genesys_c6_permute(self.handle, fd, input_dev_ptr, perm_dev_ptr, n_blocks, iters,
+                                        1 if relaxed else 0, 1 if nonblocking else 0, staging, staging_bytes,
+                                        _stream_handle(stream)), "genesys_c6_permute")
 
     def visibility_probe(self, n_threads: int, gran: int, group_threads: int, relaxed: bool, seed: int,
                          probe: int, violations_dev_ptr: int, stream=None) -> None:

@@ -4,6 +4,7 @@
 // Paper: Vesely et al., "GPU System Calls", arXiv 1705.06965.
 //   C1  Sec. 6 / Fig. 5   pread microbenchmark (here: pread + byte histogram)
 //   C2  Sec. 4.1 / Sec. 6 pwrite at work-item / warp / work-group / kernel grain
+//   C6  Sec. 6 / Fig. 6   block permutation + work-group pwrite, 4 ordering x blocking modes
 //   probe Sec. 4.1        strong ordering: stores before the call are complete
 #include <cuda_runtime.h>
 #include <stdio.h>
@@ -226,6 +227,46 @@ __global__ void __launch_bounds__(1024) visibility_kernel(genesys_dev g, uint64_
   if (threadIdx.x == 0 && r > 0) atomicAdd(viol, (unsigned long long)r);
 }
 
+// ------------------------------------------------------------------- C6
+// Block permutation (Sec. 6, Fig. 6): block b of the input (8 KiB) is staged
+// in shared memory, permuted `iters` times with out[i] = in[perm[i]], written
+// to host-mapped staging and then to the file with a work-group pwrite at
+// offset b * 8 KiB.  Ordering and blocking of that pwrite are the four
+// combinations the paper compares.
+template <int O, int B>
+__global__ void __launch_bounds__(1024) c6_permute_kernel(genesys_dev g, int fd, const uint8_t *input,
+                                                          const uint16_t *perm, uint32_t iters, uint8_t *staging) {
+  __shared__ __align__(16) uint8_t buf[2][8192];
+  __shared__ __align__(16) uint16_t p[8192];
+  const uint64_t blk = blockIdx.x;
+  const uint4 *in4 = reinterpret_cast<const uint4 *>(input + blk * 8192);
+  for (uint32_t i = threadIdx.x; i < 512; i += blockDim.x) reinterpret_cast<uint4 *>(buf[0])[i] = in4[i];
+  for (uint32_t i = threadIdx.x; i < 1024; i += blockDim.x)
+    reinterpret_cast<uint4 *>(p)[i] = reinterpret_cast<const uint4 *>(perm)[i];
+  __syncthreads();
+  uint32_t cur = 0;
+  for (uint32_t it = 0; it < iters; ++it) {
+    for (uint32_t i = threadIdx.x; i < 8192; i += blockDim.x) buf[cur ^ 1][i] = buf[cur][p[i]];
+    __syncthreads();
+    cur ^= 1;
+  }
+  uint8_t *dst = staging + blk * 8192;
+  for (uint32_t i = threadIdx.x; i < 512; i += blockDim.x)
+    reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(buf[cur])[i];
+  call<GROUP, O, B>(g, SYS_pwrite64, (uint64_t)fd, (uint64_t)dst, 8192, blk * 8192);
+}
+
+// One system call made by GPU code: every thread of a `threads`-wide block
+// takes part at the given granularity (the caller is the designated thread),
+// and thread 0 stores the result.  Any call the context allows can be made
+// this way (open, read, write, lseek, close, madvise, ...).
+template <int G>
+__global__ void one_call_kernel(genesys_dev g, uint32_t nr, uint64_t a0, uint64_t a1, uint64_t a2, uint64_t a3,
+                                uint64_t a4, uint64_t a5, long long *ret) {
+  const int64_t r = call<G, STRONG, BLOCKING>(g, nr, a0, a1, a2, a3, a4, a5);
+  if (threadIdx.x == 0) *ret = r;
+}
+
 template <int G, int O, int B>
 const void *c2_kernel_ptr() {
   return reinterpret_cast<const void *>(&c2_pwrite_kernel<G, O, B>);
@@ -306,6 +347,52 @@ int genesys_c2_pwrite(genesys_ctx *c, int fd, uint64_t n, uint32_t gran, uint32_
   void *args[] = {&g, &fd, &n, &seed, &st};
   const uint32_t flags = gran | (relaxed ? GENESYS_LAUNCH_RELAXED : 0) | (nonblocking ? GENESYS_LAUNCH_NONBLOCKING : 0);
   return run(c, k, (uint32_t)blocks, bt, 0, args, flags, stream);
+}
+
+int genesys_c6_permute(genesys_ctx *c, int fd, const uint8_t *input_dev, const uint16_t *perm_dev, uint64_t n_blocks,
+                       uint32_t iters, uint32_t relaxed, uint32_t nonblocking, void *staging, uint64_t staging_bytes,
+                       void *stream) {
+  if (!c || !input_dev || !perm_dev || !staging) return set_err(GENESYS_EINVAL, "NULL argument");
+  if (fd < 0) return set_err(GENESYS_EINVAL, "bad fd");
+  if (n_blocks == 0) return 0;
+  if (n_blocks > 0x7FFFFFFFull) return set_err(GENESYS_EINVAL, "too many blocks");
+  if (staging_bytes < n_blocks * 8192 || (uintptr_t)staging % 16 || (uintptr_t)input_dev % 16 ||
+      (uintptr_t)perm_dev % 16)
+    return set_err(GENESYS_EINVAL, "staging >= n_blocks * 8 KiB; 16-byte aligned buffers");
+  const void *k = relaxed ? (nonblocking ? (const void *)&c6_permute_kernel<RELAXED, NONBLOCKING>
+                                         : (const void *)&c6_permute_kernel<RELAXED, BLOCKING>)
+                          : (nonblocking ? (const void *)&c6_permute_kernel<STRONG, NONBLOCKING>
+                                         : (const void *)&c6_permute_kernel<STRONG, BLOCKING>);
+  genesys_dev g;
+  genesys_device_view(c, &g);
+  uint8_t *st = (uint8_t *)staging;
+  void *args[] = {&g, &fd, &input_dev, &perm_dev, &iters, &st};
+  const uint32_t flags = GENESYS_GRAN_GROUP | (relaxed ? GENESYS_LAUNCH_RELAXED : 0) |
+                         (nonblocking ? GENESYS_LAUNCH_NONBLOCKING : 0);
+  return run(c, k, (uint32_t)n_blocks, 1024, 0, args, flags, stream);
+}
+
+int genesys_gpu_call(genesys_ctx *c, uint32_t nr, const uint64_t args[6], uint32_t gran, uint32_t threads,
+                     long long *ret_dev, void *stream) {
+  if (!c || !args || !ret_dev) return set_err(GENESYS_EINVAL, "NULL argument");
+  if (threads == 0 || threads > 1024 || (gran == GENESYS_GRAN_WARP && threads > 32) || gran > GENESYS_GRAN_GROUP)
+    return set_err(GENESYS_EINVAL, "one block of 1..1024 threads; work-item, warp (<= 32 threads) or work-group");
+  if (gran == GENESYS_GRAN_ITEM && threads != 1) return set_err(GENESYS_EINVAL, "work-item grain: one thread");
+  genesys_dev g;
+  genesys_device_view(c, &g);
+  uint64_t a0 = args[0], a1 = args[1], a2 = args[2], a3 = args[3], a4 = args[4], a5 = args[5];
+  void *kargs[] = {&g, &nr, &a0, &a1, &a2, &a3, &a4, &a5, &ret_dev};
+  const void *k = gran == GENESYS_GRAN_ITEM   ? (const void *)&one_call_kernel<ITEM>
+                  : gran == GENESYS_GRAN_WARP ? (const void *)&one_call_kernel<WARP>
+                                              : (const void *)&one_call_kernel<GROUP>;
+  const uint32_t g3[3] = {1, 1, 1}, b3[3] = {threads, 1, 1};
+  int rc = genesys_launch(c, k, g3, b3, 0, kargs, gran | GENESYS_LAUNCH_SYNC, stream);
+  if (rc) return rc;
+  int32_t st[GENESYS_ST_WORDS];
+  rc = genesys_status(c, st, 1);
+  if (rc) return rc;
+  if (st[GENESYS_ST_TIMEOUTS] || st[GENESYS_ST_FIRST_ERROR]) return set_err(GENESYS_EDEVICE, "device wait timed out");
+  return 0;
 }
 
 int genesys_visibility_probe(genesys_ctx *c, uint64_t n, uint32_t gran, uint32_t bt, uint32_t relaxed, uint64_t seed,

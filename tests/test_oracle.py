@@ -325,3 +325,50 @@ def test_c4_zipf_and_mix():
     counts = np.bincount(tr.key_idx, minlength=len(tr.keys))
     assert counts[0] == counts.max()                              # rank 1 is the most popular key
     assert tr.vlen0.min() >= 64 and tr.vlen0.max() <= 1024
+
+
+# ------------------------------------------------------------------------- C6
+
+def _c6(tmp_path, data, perm, iters, name="c6.bin"):
+    p = str(tmp_path / name)
+    oracle.c6_permute(data, perm, iters, p)
+    return np.frombuffer(open(p, "rb").read(), np.uint8)
+
+
+def test_c6_rotation_is_a_gather(tmp_path):
+    # perm[i] = i + 1 (mod 8192): one gather step moves every byte one place
+    # towards the block start, so k steps rotate left by k
+    data = np.arange(2 * 8192, dtype=np.uint64).astype(np.uint8)
+    rot = ((np.arange(8192) + 1) % 8192).astype(np.uint16)
+    for k in (0, 1, 5):
+        got = _c6(tmp_path, data, rot, k).reshape(2, 8192)
+        for b in range(2):
+            assert np.array_equal(got[b], np.roll(data.reshape(2, 8192)[b], -k))
+
+
+def test_c6_group_invariants(tmp_path):
+    data, perm = workloads.c6_inputs(3)
+    assert sorted(perm.tolist()) == list(range(8192))              # a bijection
+    # cycle decomposition -> order of the permutation
+    seen, lens = np.zeros(8192, bool), []
+    for i in range(8192):
+        if not seen[i]:
+            n, j = 0, i
+            while not seen[j]:
+                seen[j] = True
+                j = int(perm[j])
+                n += 1
+            lens.append(n)
+    order = int(np.lcm.reduce(np.array(lens, dtype=np.int64)))
+    if order < 10_000:
+        assert np.array_equal(_c6(tmp_path, data, perm, order), data)   # pi^order = identity
+    # composition: 3 steps then 4 steps == 7 steps
+    a3 = _c6(tmp_path, data, perm, 3, "a3.bin")
+    assert np.array_equal(_c6(tmp_path, a3, perm, 4, "a7.bin"), _c6(tmp_path, data, perm, 7, "b7.bin"))
+    # a permutation keeps each block's multiset of bytes
+    out = _c6(tmp_path, data, perm, 9).reshape(3, 8192)
+    for b in range(3):
+        assert np.array_equal(np.sort(out[b]), np.sort(data.reshape(3, 8192)[b]))
+    # the identity permutation changes nothing
+    ident = np.arange(8192, dtype=np.uint16)
+    assert np.array_equal(_c6(tmp_path, data, ident, 11), data)

@@ -324,3 +324,22 @@ def kv_request_bytes(trace: KVTrace, idx=None) -> tuple[bytes, np.ndarray]:
         parts.append(d)
         pos += len(d)
     return b"".join(parts), np.array(offs + [pos], np.uint64)
+
+
+
+# ------------------------------------------------------------------------ C6
+# Block permutation study (Fig. 6): random input blocks of 8 KiB and one
+# seeded byte permutation of a block.
+
+SEED_C6 = 0x5EED0006
+C6_BLOCK = 8192
+
+
+def c6_inputs(n_blocks: int, seed: int = SEED_C6) -> tuple[np.ndarray, np.ndarray]:
+    """(input bytes [n_blocks * 8192] uint8, permutation [8192] uint16): the
+    input is the splitmix64 stream of `seed`; the permutation sorts the
+    stream of seed+1 (a uniformly random permutation)."""
+    data = np.frombuffer(stream_bytes(seed, n_blocks * C6_BLOCK), np.uint8).copy()
+    keys = _sm_vec(seed + 1, np.arange(C6_BLOCK))
+    perm = np.argsort(keys, kind="stable").astype(np.uint16)
+    return data, perm
