@@ -203,7 +203,8 @@ def load_traffic(kernel: str, units_per_launch: float):
 class Rig:
     """Context, files and buffers of the GPU arm."""
 
-    def __init__(self, args, local, rank, need_scan=True, service_threads=None, coalesce_max=64, need_c3=True):
+    def __init__(self, args, local, rank, need_scan=True, service_threads=None, coalesce_max=64, need_c3=True,
+                 poll_max_ns=2048):
         import torch
         import paper_1705_06965_b300 as G
         import workloads
@@ -216,7 +217,7 @@ class Rig:
                           if need_scan else None)
         self.c1_stage_bytes = max(2 * C1_GROUPS * C1_CHUNK, 2 * SCAN_GROUPS * SCAN_CHUNK if need_scan else 0)
         self.c3_stage_bytes = C3_CTAS * (C3_CHUNK + 64) * 2 if need_c3 else 0
-        self.ctx = G.Context(device=local, service_threads=st_threads, coalesce_max=coalesce_max,
+        self.ctx = G.Context(device=local, service_threads=st_threads, coalesce_max=coalesce_max, poll_max_ns=poll_max_ns,
                              staging_bytes=max(SIZES) * 64 + self.c1_stage_bytes + self.c3_stage_bytes + (4 << 20),
                              deadline_ns=10_000_000_000)
         self.c2_stage = self.ctx.staging(max(SIZES) * 64)
@@ -299,14 +300,15 @@ def tune_step(args, local, rank):
 
     def run(cfg):
         rig = Rig(args, local, rank, need_scan=False, need_c3=False, service_threads=cfg["service_threads"],
-                  coalesce_max=cfg["coalesce_max"])
+                  coalesce_max=cfg["coalesce_max"], poll_max_ns=cfg["poll_max_ns"])
         try:
             sweep_step(rig)
             return rig.timed(lambda: sweep_step(rig)) * 1e-3
         finally:
             rig.close()
 
-    best, table = tuner.tune(key, autotune.grid(service_threads=(2, 4, 8), coalesce_max=(64, 256)), run, repeats=1)
+    best, table = tuner.tune(key, autotune.grid(service_threads=(2, 4), coalesce_max=(64, 256),
+                                                poll_max_ns=(2048, 32768)), run, repeats=2)
     return best, table
 
 
@@ -319,7 +321,8 @@ def run_only(args):
     torch.cuda.set_device(local)
     kind, _, rest = args.only.partition(":")
     rig = Rig(args, local, rank, need_scan=kind == "c1" and rest.split(":")[-1] != str(C1_BYTES),
-              need_c3=kind == "c3", service_threads=args.service_threads)
+              need_c3=kind == "c3", service_threads=args.service_threads, coalesce_max=args.coalesce_max,
+              poll_max_ns=args.poll_max_ns)
     G = rig.G
     out = {"only": args.only}
     try:
@@ -560,8 +563,9 @@ def run_genesys(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     step_cfg, step_table = tune_step(args, local, rank) if args.autotune else (
-        {"service_threads": args.service_threads, "coalesce_max": 64}, [])
-    rig = Rig(args, local, rank, service_threads=step_cfg["service_threads"], coalesce_max=step_cfg["coalesce_max"])
+        {"service_threads": args.service_threads, "coalesce_max": 64, "poll_max_ns": 2048}, [])
+    rig = Rig(args, local, rank, service_threads=step_cfg["service_threads"], coalesce_max=step_cfg["coalesce_max"],
+              poll_max_ns=step_cfg["poll_max_ns"])
     G, ctx, dev = rig.G, rig.ctx, rig.dev
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     kernel_ms = {}
@@ -677,7 +681,7 @@ def run_genesys(args):
                                "preads, 64 work-groups x 256 threads, 256-bin histogram, plain and batched)",
                    "threads": SIZES, "combinations": len(COMBOS), "kernels_per_step": len(SIZES) * len(COMBOS) + 2,
                    "syscalls_per_step": calls_step, "service_threads": step_cfg["service_threads"],
-                   "coalesce_max": step_cfg["coalesce_max"],
+                   "coalesce_max": step_cfg["coalesce_max"], "poll_max_ns": step_cfg["poll_max_ns"],
                    "l2": "256 MiB device buffer written between timed steps (L2 flush)",
                    "parallelism": f"replicas x{world}"},
         "requests_per_s": round(job_value(world, (sum(SIZES) * len(COMBOS) + c1_calls) * args.steps, tot_ms * 1e-3), 1),
@@ -772,6 +776,8 @@ def main():
     ap.add_argument("--service-threads", type=int, default=4)
     ap.add_argument("--autotune", type=int, default=1, help="autotune the step's context knobs (cached)")
     ap.add_argument("--extras", type=int, default=1, help="0: only the timed step (for launch lists)")
+    ap.add_argument("--coalesce-max", type=int, default=64, help="--only: service batch size")
+    ap.add_argument("--poll-max-ns", type=int, default=2048, help="--only: largest completion-poll back-off")
     ap.add_argument("--only", default=None, help="run one case: c2:<grain>/<order>/<block>:<threads>, "
                                                  "c1:<plain|batched>:<bytes>, c3:<plain|batched>")
     args = ap.parse_args()

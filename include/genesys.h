@@ -71,6 +71,9 @@ typedef struct genesys_config {
   uint32_t flags;              /* GENESYS_INIT_*                                       */
   uint64_t idle_spin_ns;       /* a service thread busy-polls this long after its last
                                   request before it starts napping                     */
+  uint32_t poll_min_ns;        /* GPU completion polls: first back-off (ns) ...         */
+  uint32_t poll_max_ns;        /* ... growing 1.5x per poll up to this; more polls cost
+                                  host-link read requests, fewer add latency           */
 } genesys_config;
 
 typedef struct genesys_stats {
@@ -93,7 +96,7 @@ typedef struct genesys_ctx genesys_ctx;
 
 /* Fill *cfg with defaults: slots = SMs x 2048 (or 65536 without a GPU), 4
  * service threads, 256 MiB staging, no coalescing window, coalesce_max 64,
- * merge on, 2 s device deadline, 1 M latency samples. */
+ * merge on, 2 s device deadline, 1 M latency samples, polls 256 ns .. 2 us. */
 int genesys_config_default(genesys_config *cfg);
 
 /* Create a context on CUDA device `device`: allocates the syscall area, the

@@ -146,41 +146,57 @@ __device__ __forceinline__ uint32_t ring_of(const genesys_dev &g, uint32_t slot)
 }
 
 /* ------------------------------------------------------ slot protocol
- * One thread.  Claim a slot (device-side lock in HBM, never an RMW on host
- * memory), then make sure the CPU has finished the slot's previous request
- * (a non-blocking call may still be in flight: Fig. 4, "if the slot is not
- * free, system call invocation is delayed"). */
+ * One thread.  Try to claim a slot (device-side lock in HBM, never an RMW on
+ * host memory): up to 32 slots from `hint` on.  A claimed slot whose previous
+ * request the CPU has not finished yet (a non-blocking call may still be in
+ * flight: Fig. 4, "if the slot is not free, system call invocation is
+ * delayed") is waited for, bounded.  Returns 1 with *slot_out set, 0 if every
+ * slot tried is taken, or -ETIMEDOUT. */
+__device__ __forceinline__ int64_t slot_try_claim(const genesys_dev &g, uint32_t hint, uint32_t *slot_out,
+                                                  uint64_t t0) {
+  uint32_t s = hint % g.n_slots;
+  for (uint32_t probe = 0; probe < 32; ++probe) {
+    if (atomicCAS(&g.owner[s], 0u, 1u) == 0u) {
+      __threadfence();
+      const uint32_t sq = ld_relaxed_gpu(&g.seq[s]);
+      if (ld_relaxed_gpu(&g.known_done[s]) != sq) {
+        uint32_t ns = 128;
+        while ((uint32_t)(ld_relaxed_sys(&g.done[s]) >> 32) != sq) {
+          if (expired(g, t0)) {
+            __threadfence();
+            atomicExch(&g.owner[s], 0u);
+            note_error(g, -kETIMEDOUT);
+            return -kETIMEDOUT;
+          }
+          __nanosleep(ns);
+          ns = ns < 2048 ? ns * 2 : ns;
+        }
+        fence_acq_rel_sys();
+        st_relaxed_gpu(&g.known_done[s], sq);
+      }
+      *slot_out = s;
+      return 1;
+    }
+    s = (s + 1 == g.n_slots) ? 0 : s + 1;
+  }
+  if (expired(g, t0)) {
+    note_error(g, -kETIMEDOUT);
+    return -kETIMEDOUT;
+  }
+  return 0;
+}
+
+/* One thread: claim a slot, waiting (bounded, with back-off) while all are
+ * taken.  The caller must not hold anything other callers need meanwhile. */
 __device__ __forceinline__ int64_t slot_claim(const genesys_dev &g, uint32_t hint, uint32_t *slot_out,
                                               uint64_t t0) {
-  uint32_t s = hint % g.n_slots;
-  uint32_t probes = 0, ns = 32;
-  while (atomicCAS(&g.owner[s], 0u, 1u) != 0u) {
-    s = (s + 1 == g.n_slots) ? 0 : s + 1;
-    if (++probes >= 64) {
-      probes = 0;
-      __nanosleep(ns);
-      ns = ns < 4096 ? ns * 2 : ns;
-      if (expired(g, t0)) { note_error(g, -kETIMEDOUT); return -kETIMEDOUT; }
-    }
+  uint32_t ns = 32;
+  for (uint32_t round = 0;; ++round) {
+    const int64_t r = slot_try_claim(g, hint + round * 32u, slot_out, t0);
+    if (r != 0) return r < 0 ? r : 0;
+    __nanosleep(ns);
+    ns = ns < 4096 ? ns * 2 : ns;
   }
-  __threadfence();
-  const uint32_t sq = ld_relaxed_gpu(&g.seq[s]);
-  if (ld_relaxed_gpu(&g.known_done[s]) != sq) {
-    ns = 128;
-    while ((uint32_t)(ld_acquire_sys(&g.done[s]) >> 32) != sq) {
-      if (expired(g, t0)) {
-        __threadfence();
-        atomicExch(&g.owner[s], 0u);
-        note_error(g, -kETIMEDOUT);
-        return -kETIMEDOUT;
-      }
-      __nanosleep(ns);
-      ns = ns < 2048 ? ns * 2 : ns;
-    }
-    st_relaxed_gpu(&g.known_done[s], sq);
-  }
-  *slot_out = s;
-  return 0;
 }
 
 /* Marshal the request into the slot with 16-byte stores; returns its sequence.
@@ -236,14 +252,15 @@ __device__ __forceinline__ void ring_warp(const genesys_dev &g, uint32_t mask, u
  * Polls with relaxed loads and makes the acquire once, with a fence after the
  * load that saw the completion (an acquire pattern). */
 __device__ __forceinline__ int64_t slot_wait(const genesys_dev &g, uint32_t s, uint32_t sq, uint64_t t0) {
-  uint32_t ns = 256;
+  uint32_t ns = g.poll_min_ns;
+  const uint32_t cap = g.poll_max_ns;
   uint64_t d;
   for (;;) {
     d = ld_relaxed_sys(&g.done[s]);
     if ((uint32_t)(d >> 32) == sq) break;
     if (expired(g, t0)) { note_error(g, -kETIMEDOUT); return -kETIMEDOUT; }
     __nanosleep(ns);
-    ns = ns < 2048 ? ns + (ns >> 1) : ns;
+    ns = ns < cap ? ns + (ns >> 1) + 1 : cap;
   }
   fence_acq_rel_sys();
   st_relaxed_gpu(&g.known_done[s], sq);
@@ -369,22 +386,37 @@ __device__ __forceinline__ int64_t call_at(const genesys_dev &g, uint32_t site, 
 
   if (G == ITEM) {
     /* every calling lane is a caller; lanes of a warp that call together
-     * share one doorbell atomic per ring */
+     * share one doorbell atomic per ring.  Lanes claim in rounds: the lanes
+     * that got a slot in a round publish together, complete and release it
+     * before the next round, so no lane holds a slot while it waits for a
+     * sibling that has none (with fewer slots than callers, holding and
+     * waiting would deadlock). */
     const uint32_t active = __activemask();
     const uint64_t t0 = now_ns();
-    uint32_t s = 0;
-    int64_t rc = slot_claim(g, hw_lane_id(), &s, t0);
-    const bool ok = rc == 0;
-    uint32_t sq = 0;
-    if (ok) sq = slot_fill(g, s, nr, flags, a0, a1, a2, a3, a4, a5);
-    const uint32_t okmask = __ballot_sync(active, ok);
-    if (ok) {
-      ring_warp(g, okmask, s);
-      if (B == BLOCKING) {
-        rc = slot_wait(g, s, sq, t0);
+    const uint32_t hint = hw_lane_id();
+    bool pending = true;
+    int64_t rc = 0;
+    uint32_t ns = 32;
+    for (uint32_t round = 0; __ballot_sync(active, pending); ++round) {
+      uint32_t s = 0;
+      bool ok = false;
+      if (pending) {
+        const int64_t t = slot_try_claim(g, hint + round * 32u, &s, t0);
+        if (t < 0) { rc = t; pending = false; }
+        ok = t > 0;
       }
-      slot_release(g, s);
-      if (rc != -kETIMEDOUT) note_latency(g, t0);
+      const uint32_t okmask = __ballot_sync(active, ok);
+      if (ok) {
+        const uint32_t sq = slot_fill(g, s, nr, flags, a0, a1, a2, a3, a4, a5);
+        ring_warp(g, okmask, s);
+        rc = B == BLOCKING ? slot_wait(g, s, sq, t0) : 0;
+        slot_release(g, s);
+        if (rc != -kETIMEDOUT) note_latency(g, t0);
+        pending = false;
+      } else if (pending) {
+        __nanosleep(ns);
+        ns = ns < 4096 ? ns * 2 : ns;
+      }
     }
     return rc;
   }

@@ -139,6 +139,8 @@ typedef struct genesys_dev {
   uint32_t ring_mask;         /* ring_cap - 1, ring_cap a power of two              */
   uint64_t deadline_ns;       /* every device wait gives up after this long         */
   uint32_t n_sms;
+  uint32_t poll_min_ns;       /* completion polls: first back-off ...                */
+  uint32_t poll_max_ns;       /* ... growing 1.5x per poll up to this                */
   uint32_t reserved;
 } genesys_dev;
 

@@ -59,7 +59,7 @@ class Config(ctypes.Structure):
         ("service_cpus", ctypes.POINTER(ctypes.c_int32)), ("staging_bytes", ctypes.c_uint64),
         ("coalesce_window_ns", ctypes.c_uint64), ("coalesce_max", ctypes.c_uint32), ("merge", ctypes.c_uint32),
         ("device_deadline_ns", ctypes.c_uint64), ("lat_samples", ctypes.c_uint32), ("flags", ctypes.c_uint32),
-        ("idle_spin_ns", ctypes.c_uint64),
+        ("idle_spin_ns", ctypes.c_uint64), ("poll_min_ns", ctypes.c_uint32), ("poll_max_ns", ctypes.c_uint32),
     ]
 
 
@@ -183,7 +183,8 @@ class Context:
                  staging_bytes: int = 256 << 20, coalesce_window_ns: int = 0, coalesce_max: int = 64,
                  merge: bool = True, deadline_ns: int = 2_000_000_000, lat_samples: int = 1 << 20,
                  host_only: bool = False, no_threads: bool = False, any_syscall: bool = False,
-                 idle_spin_ns: int = 200_000_000, service_cpus=None):
+                 idle_spin_ns: int = 200_000_000, service_cpus=None, poll_min_ns: int = 256,
+                 poll_max_ns: int = 2048):
         L = lib()
         cfg = Config()
         _check(L.genesys_config_default(ctypes.byref(cfg)), "genesys_config_default")
@@ -200,6 +201,8 @@ class Context:
         cfg.device_deadline_ns = int(deadline_ns)
         cfg.lat_samples = lat_samples
         cfg.idle_spin_ns = int(idle_spin_ns)
+        cfg.poll_min_ns = int(poll_min_ns)
+        cfg.poll_max_ns = int(poll_max_ns)
         cfg.flags = (INIT_HOST_ONLY if host_only else 0) | (INIT_NO_THREADS if no_threads else 0) | (
             INIT_ANY_SYSCALL if any_syscall else 0)
         self.config = cfg

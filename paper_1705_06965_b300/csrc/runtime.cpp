@@ -426,10 +426,16 @@ size_t poll_ring(genesys_ctx *c, uint32_t ri, std::vector<Request> &batch) {
   const size_t maxb = batch.size();
   size_t n = 0;
   uint32_t s;
-  while (n < maxb && entry_ready(ring, mask, h + n, &s)) {
-    read_request(c, s, &batch[n]);
+  // take the ready entries first and prefetch their slots (written by the GPU,
+  // so their lines are not in the CPU's caches), then read the slots
+  uint32_t slots[1024];
+  const size_t cap_n = std::min<size_t>(maxb, 1024);
+  while (n < cap_n && entry_ready(ring, mask, h + n, &s)) {
+    slots[n] = s;
+    __builtin_prefetch(&c->slots[s], 0, 0);
     ++n;
   }
+  for (size_t i = 0; i < n; ++i) read_request(c, slots[i], &batch[i]);
   if (n == 0) return 0;
   if (n < maxb && c->cfg.coalesce_window_ns) {
     const uint64_t until = mono_ns() + c->cfg.coalesce_window_ns;
@@ -601,6 +607,8 @@ int genesys_config_default(genesys_config *cfg) {
   cfg->device_deadline_ns = 2000000000ull;
   cfg->lat_samples = 1u << 20;
   cfg->idle_spin_ns = 200000000ull;
+  cfg->poll_min_ns = 256;
+  cfg->poll_max_ns = 2048;
   return 0;
 }
 
@@ -613,6 +621,9 @@ int genesys_init(const genesys_config *cfg_in, int device, genesys_ctx **out) {
     return fail(GENESYS_EINVAL, "n_service_threads must be 1..256");
   if (cfg.coalesce_max == 0) cfg.coalesce_max = 1;
   if (cfg.device_deadline_ns == 0) return fail(GENESYS_EINVAL, "device_deadline_ns must be > 0");
+  if (cfg.poll_min_ns == 0) cfg.poll_min_ns = 256;
+  if (cfg.poll_max_ns < cfg.poll_min_ns) cfg.poll_max_ns = cfg.poll_min_ns;
+  if (cfg.poll_max_ns > 1000000) return fail(GENESYS_EINVAL, "poll_max_ns above 1 ms");
 
   auto c = std::make_unique<genesys_ctx>();
   c->host_only = (cfg.flags & GENESYS_INIT_HOST_ONLY) != 0;
@@ -740,6 +751,8 @@ int genesys_device_view(genesys_ctx *c, genesys_dev *d) {
   d->ring_mask = c->ring_cap - 1;
   d->deadline_ns = c->cfg.device_deadline_ns;
   d->n_sms = c->n_sms;
+  d->poll_min_ns = c->cfg.poll_min_ns;
+  d->poll_max_ns = c->cfg.poll_max_ns;
   return 0;
 }
 

@@ -305,6 +305,8 @@ int genesys_c3_wordcount(genesys_ctx *c, const int32_t *fds, const uint64_t *fil
   }
   genesys_dev g;
   genesys_device_view(c, &g);
+  if (form == GENESYS_FORM_BATCHED && g.n_slots < 2ull * ctas)
+    return set_err(GENESYS_EINVAL, "the batched form holds two slots per block: n_slots must be >= 2 * ctas");
   const C3Item *d_items = (const C3Item *)((uint8_t *)scratch + items_off);
   uint32_t n_items = (uint32_t)items.size();
   uint32_t *head = (uint32_t *)scratch;
@@ -444,6 +446,8 @@ extern "C" int genesys_c3_wordcount_noalloc(genesys_ctx *c, const int32_t *fds, 
   }
   genesys_dev g;
   genesys_device_view(c, &g);
+  if (form == GENESYS_FORM_BATCHED && g.n_slots < 2ull * ctas)
+    return set_err(GENESYS_EINVAL, "the batched form holds two slots per block: n_slots must be >= 2 * ctas");
   const C3Item *d_items = (const C3Item *)(scratch + kStaticItemsOff);
   uint32_t *head = (uint32_t *)scratch;
   const C3Queries *d_q = (const C3Queries *)(scratch + kStaticQOff);

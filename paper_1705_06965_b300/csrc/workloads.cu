@@ -313,6 +313,8 @@ int genesys_c1_histogram(genesys_ctx *c, int fd, uint64_t file_bytes, uint64_t c
   if (file_bytes == 0) return 0;
   genesys_dev g;
   genesys_device_view(c, &g);
+  if (form == GENESYS_FORM_BATCHED && g.n_slots < 2ull * groups)
+    return set_err(GENESYS_EINVAL, "the batched form holds two slots per block: n_slots must be >= 2 * groups");
   uint32_t ch = (uint32_t)chunk;
   uint8_t *st = (uint8_t *)staging;
   void *args[] = {&g, &fd, &file_bytes, &ch, &st, &hist_dev};

@@ -169,3 +169,20 @@ def test_relaxed_consumer_runs(ctx, G):
     for gran in (1, 2, 3):
         ctx.visibility_probe(n, gran, 256, True, 7, probe, viol.data_ptr())
     assert int(viol.item()) >= 0
+
+
+@pytest.mark.parametrize("n_slots,threads,window", [(64, 1, 0), (256, 3, 0), (1024, 2, 50_000)])
+def test_c2_small_slot_area_and_coalescing_window(G, tmp_path, n_slots, threads, window):
+    """A slot area far smaller than the number of callers (claims probe and wait
+    for slots to free up, rings wrap many times), and a coalescing window:
+    the file is still the oracle's."""
+    n = 1 << 14
+    want_path = str(tmp_path / "want.bin")
+    oracle.c2_pwrite(want_path, n, 1)
+    with G.Context(device=0, n_slots=n_slots, service_threads=threads, coalesce_window_ns=window,
+                   staging_bytes=(n * 64) + (1 << 20), deadline_ns=10_000_000_000) as c:
+        for gran, relaxed, nb in [(0, False, False), (0, False, True), (1, True, True), (2, False, False)]:
+            got = _c2(c, G, str(tmp_path / "got.bin"), n, gran, 256, relaxed, nb)
+            assert got == open(want_path, "rb").read(), (gran, relaxed, nb)
+        st = c.stats()
+        assert st["failed"] == 0
