@@ -89,6 +89,13 @@ inline uint64_t sm64_at(uint64_t seed, uint64_t i) {
 
 enum OpIdx { OP_PREAD = 0, OP_PWRITE, OP_SENDTO, OP_RECVFROM, OP_MMAP, OP_MUNMAP, OP_INTERNAL, OP_OTHER };
 
+// Each ring's counters are written by its service thread only (or under the
+// service mutex), so an increment is a relaxed load and store, not a locked
+// read-modify-write; genesys_stats_get reads them with relaxed loads.
+inline void bump(std::atomic<uint64_t> &a, uint64_t v) {
+  a.store(a.load(std::memory_order_relaxed) + v, std::memory_order_relaxed);
+}
+
 struct alignas(64) Counters {
   std::atomic<uint64_t> requests{0}, os_calls{0}, failed{0}, nb_failed{0}, bytes{0}, batches{0}, busy_ns{0};
   std::atomic<uint64_t> by_op[8] = {};
@@ -170,9 +177,9 @@ void complete(genesys_ctx *c, const Request &r, Counters &k) {
     word |= GENESYS_RET_IN_SLOT;
   }
   if (r.ret < 0) {
-    k.failed.fetch_add(1, std::memory_order_relaxed);
+    bump(k.failed, 1);
     if (!(r.flags & GENESYS_REQ_BLOCKING) && !(r.flags & GENESYS_REQ_TICKET))
-      k.nb_failed.fetch_add(1, std::memory_order_relaxed);
+      bump(k.nb_failed, 1);
   }
   __atomic_store_n(&c->done[r.slot], word, __ATOMIC_RELEASE);
 }
@@ -288,13 +295,13 @@ void reclaim(genesys_ctx *c, bool all) {
 
 int64_t execute_one(genesys_ctx *c, Request &r, Counters &k) {
   const uint64_t *a = r.a;
-  k.os_calls.fetch_add(1, std::memory_order_relaxed);
+  bump(k.os_calls, 1);
   switch (r.nr) {
     case GENESYS_NR_NOP:
-      k.os_calls.fetch_sub(1, std::memory_order_relaxed);
+      bump(k.os_calls, (uint64_t)-1);
       return (int64_t)a[0];
     case GENESYS_NR_CHECK_VISIBLE: {
-      k.os_calls.fetch_sub(1, std::memory_order_relaxed);
+      bump(k.os_calls, (uint64_t)-1);
       const volatile uint64_t *p = (const volatile uint64_t *)a[0];
       int64_t bad = 0;
       for (uint64_t i = 0; i < a[1]; ++i) bad += p[i] != sm64_at(a[2], a[3] + i);
@@ -330,7 +337,7 @@ size_t merge_run(genesys_ctx *c, Request *reqs, size_t i, size_t n, Counters &k)
   uint64_t total = 0;
   for (size_t t = i; t < j; ++t) total += reqs[t].a[2];
   int64_t res;
-  k.os_calls.fetch_add(1, std::memory_order_relaxed);
+  bump(k.os_calls, 1);
   if (m == 1 || contiguous_buf) {
     void *buf = (void *)reqs[i].a[1];
     long r = nr == SYS_pread64 ? pread(fd, buf, total, (off_t)off) : pwrite(fd, buf, total, (off_t)off);
@@ -352,7 +359,7 @@ size_t merge_run(genesys_ctx *c, Request *reqs, size_t i, size_t n, Counters &k)
     }
     prefix += len;
   }
-  if (res > 0) k.bytes.fetch_add((uint64_t)res, std::memory_order_relaxed);
+  if (res > 0) bump(k.bytes, (uint64_t)res);
   return j;
 }
 
@@ -363,15 +370,27 @@ void process_batch(genesys_ctx *c, Request *reqs, size_t n, Counters &k) {
   if (c->cfg.merge && n > 1) {
     // the requests of a batch are concurrent, so any order is a legal
     // schedule: put pread/pwrite requests in (call, fd, offset) order so that
-    // neighbours in a file become adjacent and merge
-    std::stable_sort(reqs, reqs + n, [](const Request &x, const Request &y) {
+    // neighbours in a file become adjacent and merge.  A batch usually
+    // arrives nearly in order (a warp's lanes are consecutive), so an
+    // insertion sort is close to one pass.
+    auto before = [](const Request &x, const Request &y) {
       const bool rx = is_rw(x.nr), ry = is_rw(y.nr);
       if (rx != ry) return rx;
       if (!rx) return false;
       if (x.nr != y.nr) return x.nr < y.nr;
       if ((int)x.a[0] != (int)y.a[0]) return (int)x.a[0] < (int)y.a[0];
       return x.a[3] < y.a[3];
-    });
+    };
+    for (size_t i = 1; i < n; ++i) {
+      if (!before(reqs[i], reqs[i - 1])) continue;
+      Request t = reqs[i];
+      size_t j = i;
+      while (j > 0 && before(t, reqs[j - 1])) {
+        reqs[j] = reqs[j - 1];
+        --j;
+      }
+      reqs[j] = t;
+    }
   }
   for (size_t i = 0; i < n;) {
     Request &r = reqs[i];
@@ -383,20 +402,23 @@ void process_batch(genesys_ctx *c, Request *reqs, size_t n, Counters &k) {
     r.ret = execute_one(c, r, k);
     const uint64_t dt = mono_ns() - e0;
     const int oi = op_index(r.nr);
-    k.op_ns[oi].fetch_add(dt, std::memory_order_relaxed);
+    bump(k.op_ns[oi], dt);
     if (dt > k.op_max_ns[oi].load(std::memory_order_relaxed)) k.op_max_ns[oi].store(dt, std::memory_order_relaxed);
     if (r.ret > 0 && (r.nr == SYS_pread64 || r.nr == SYS_pwrite64 || r.nr == SYS_read || r.nr == SYS_write ||
                       r.nr == SYS_sendto || r.nr == SYS_recvfrom))
-      k.bytes.fetch_add((uint64_t)r.ret, std::memory_order_relaxed);
+      bump(k.bytes, (uint64_t)r.ret);
     ++i;
   }
+  uint64_t per_op[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (size_t i = 0; i < n; ++i) {
     complete(c, reqs[i], k);
-    k.by_op[op_index(reqs[i].nr)].fetch_add(1, std::memory_order_relaxed);
+    ++per_op[op_index(reqs[i].nr)];
   }
-  k.requests.fetch_add(n, std::memory_order_relaxed);
-  k.batches.fetch_add(1, std::memory_order_relaxed);
-  k.busy_ns.fetch_add(mono_ns() - t0, std::memory_order_relaxed);
+  for (int o = 0; o < 8; ++o)
+    if (per_op[o]) bump(k.by_op[o], per_op[o]);
+  bump(k.requests, n);
+  bump(k.batches, 1);
+  bump(k.busy_ns, mono_ns() - t0);
 }
 
 inline bool entry_ready(const uint64_t *ring, uint32_t mask, uint64_t pos, uint32_t *slot) {
