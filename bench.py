@@ -17,6 +17,8 @@ step's calls are all complete inside the timed region).
     python bench.py --only c2:work-item/strong/blocking:65536   # one case (profiling)
     python bench.py --only c1:batched:1073741824
     python bench.py --only c3:batched
+    python bench.py --only c4          # key-value service rate sweep (+ oracle server)
+    python bench.py --only fig10       # echo bandwidth versus packet size
 
 --impl reference times the CPU oracle (a sequential C program issuing the
 same pwrite/pread calls) on the same workload on the host cores.
@@ -320,6 +322,11 @@ def run_only(args):
     rank, local, _ = dist_env()
     torch.cuda.set_device(local)
     kind, _, rest = args.only.partition(":")
+    if kind in ("c4", "fig10"):
+        import paper_1705_06965_b300 as G
+        res = serve_c4(G, local, rank) if kind == "c4" else study_fig10(G, local, rank)
+        print(json.dumps({"only": args.only, kind: res}), flush=True)
+        return
     rig = Rig(args, local, rank, need_scan=kind == "c1" and rest.split(":")[-1] != str(C1_BYTES),
               need_c3=kind == "c3", service_threads=args.service_threads, coalesce_max=args.coalesce_max,
               poll_max_ns=args.poll_max_ns)
@@ -415,6 +422,7 @@ def profile_extras(args, rig, local, rank, link):
     out["kv_c4"] = serve_c4(G, local, rank)
     out["fig6_block_permutation"] = study_fig6(G, rig, local)
     out["fig7_coalescing"] = study_fig7(G, rig, local, rank)
+    out["fig10_echo"] = study_fig10(G, local, rank)
     return out
 
 
@@ -522,33 +530,110 @@ def serve_c5(G, local, rank):
     return out
 
 
-def serve_c4(G, local, rank, rates=(100_000.0, 200_000.0, 400_000.0), n_req=200_000):
-    """C4: 1M-key table in HBM, 200k requests (Zipf 0.99, 90% GET) per offered
-    rate; achieved requests/s and send-to-reply latency."""
+def _kv_point(tr, reqs, off, rate, run_server, port):
+    """Offer the trace at `rate` requests/s to a server started by
+    run_server(port); achieved rate and send-to-reply latency."""
     import numpy as np
+    import paper_1705_06965_b300 as G
+    arr = (tr.arrival_ns.astype(np.float64) * (tr.params["rate_per_s"] / rate)).astype(np.uint64)
+    stop = run_server(port)
+    try:
+        reps, lat, st = G.kv_client(reqs, off, arr, port, 32, timeout_ns=10_000_000_000)
+    finally:
+        served = stop()
+    got = lat[lat > 0]
+    achieved = st["received"] / (st["span_ns"] * 1e-9) if st["span_ns"] else 0.0
+    return {"received": st["received"], "served": served, "achieved_req_per_s": round(achieved, 1),
+            "p50_us": round(float(np.percentile(got, 50)) / 1e3, 2) if len(got) else None,
+            "p99_us": round(float(np.percentile(got, 99)) / 1e3, 2) if len(got) else None,
+            "max_send_late_us": round(st["max_send_late_ns"] / 1e3, 1)}
+
+
+def _kv_sweep(tr, reqs, off, run_server, port, rates):
+    """Offered rates from the first, doubling, until the server saturates
+    (achieved below 90 % of offered, or replies missing)."""
+    out = {}
+    for rate in rates:
+        pt = _kv_point(tr, reqs, off, rate, run_server, port)
+        out[str(int(rate))] = pt
+        port += 40
+        if pt["received"] < len(tr) or pt["achieved_req_per_s"] < 0.9 * rate:
+            break
+    return out
+
+
+def serve_c4(G, local, rank, rates=tuple(50_000.0 * 2 ** i for i in range(7)), n_req=200_000):
+    """C4: 1M-key table in HBM, 200k requests (Zipf 0.99, 90% GET) per offered
+    rate, rates 50k/s doubling to saturation; achieved requests/s and
+    send-to-reply latency.  The oracle's single-thread CPU server is offered
+    the same rates (its own saturation point is the CPU baseline)."""
     import workloads
     p = dict(workloads.C4_FULL, n_requests=n_req)
     tr = workloads.kv_trace(p)
     reqs, off = workloads.kv_request_bytes(tr)
-    base_rate = p["rate_per_s"]
-    port = 41000 + 200 * rank
-    out = {"keys": len(tr.keys), "requests_per_rate": n_req, "sockets": 32, "rates": {}}
+    out = {"keys": len(tr.keys), "requests_per_rate": n_req, "sockets": 32}
     with G.Context(device=local, service_threads=8, staging_bytes=64 << 20) as ctx:
-        for rate in rates:
+        def gpu_server(port):
             srv = G.KVServer(ctx, tr.keys, tr.vlen0, tr.vseed0, n_sockets=32, batch=64, port_base=port)
-            try:
-                arr = (tr.arrival_ns.astype(np.float64) * (base_rate / rate)).astype(np.uint64)
-                reps, lat, st = G.kv_client(reqs, off, arr, port, 32, timeout_ns=10_000_000_000)
-            finally:
-                served = srv.stop()
-            got = lat[lat > 0]
-            out["rates"][str(int(rate))] = {
-                "received": st["received"], "served": served,
-                "achieved_req_per_s": round(st["received"] / (st["span_ns"] * 1e-9), 1) if st["span_ns"] else None,
-                "p50_us": round(float(np.percentile(got, 50)) / 1e3, 2) if len(got) else None,
-                "p99_us": round(float(np.percentile(got, 99)) / 1e3, 2) if len(got) else None,
-                "max_send_late_us": round(st["max_send_late_ns"] / 1e3, 1)}
-            port += 40
+            return srv.stop
+        out["rates"] = _kv_sweep(tr, reqs, off, gpu_server, 41000 + 400 * rank, rates)
+    if rank == 0:
+        out["cpu_baseline_oracle_server"] = cpu_baseline_c4(tr, reqs, off, 41000 + 400 * rank + 200, rates)
+    best = max((v["achieved_req_per_s"] for v in out["rates"].values()), default=None)
+    out["saturation_req_per_s"] = best
+    return out
+
+
+def cpu_baseline_c4(tr, reqs, off, port, rates):
+    """The oracle's key-value server (one host thread, recvfrom/sendto one
+    datagram at a time) offered the same rates."""
+    import oracle
+    table = tr.values0_table()
+
+    def cpu_server(port):
+        srv = oracle.UdpServer("kv", port, 32, trace=tr, idle_ns=5_000_000_000, values0=table)
+        return lambda: srv.join()["answered"]
+    res = _kv_sweep(tr, reqs, off, cpu_server, port, rates)
+    return {"threads": 1, "rates": res,
+            "saturation_req_per_s": max((v["achieved_req_per_s"] for v in res.values()), default=None)}
+
+
+def study_fig10(G, local, rank, sizes=(64, 256, 1024, 4096, 16384, 65504), n_sockets=8):
+    """Sec. 7.3 / Fig. 10: bandwidth of a UDP echo server versus packet size,
+    with the packets processed on the GPU (recvfrom/sendto at work-group
+    grain, and the recvmmsg/sendmmsg batch form) and on the CPU (the
+    oracle's plain server on as many host threads as the GPU arm has service
+    threads).  Closed-loop client, 4 datagrams in flight per socket, every
+    reply compared byte for byte."""
+    port = 43000 + 400 * rank
+    service = 4
+    out = {"sockets": n_sockets, "window": 4, "service_threads": service, "GB_per_s": {}, "all_echoed": True}
+    arms = {"gpu_recvfrom_sendto": ("gpu", G.ECHO_SINGLE), "gpu_recvmmsg_sendmmsg": ("gpu", G.ECHO_BATCH)}
+    if rank == 0:
+        arms["cpu_baseline_oracle_server"] = ("cpu", None)
+    with G.Context(device=local, service_threads=service,
+                   staging_bytes=(2 * 16 * 65536 + 65536) * n_sockets + (1 << 20)) as ctx:
+        for arm, (where, form) in arms.items():
+            row = {}
+            for size in sizes:
+                n = int(min(100_000, max(5_000, 1.5e9 // size)))
+                if where == "gpu":
+                    srv = G.EchoServer(ctx, n_sockets=n_sockets, max_packet=size, form=form, batch=16, threads=256,
+                                       port_base=port)
+                    stop = srv.stop
+                else:
+                    import oracle
+                    srv = oracle.UdpServer("echo", port, n_sockets, threads=service, max_packet=size,
+                                           idle_ns=5_000_000_000)
+                    stop = srv.join
+                try:
+                    st = G.echo_client(port, n_sockets, size, n, window=4, threads=4)
+                finally:
+                    stop()
+                port += 20
+                out["all_echoed"] &= st["echoed"] == n and st["bad"] == 0
+                row[str(size)] = round(st["GB_per_s"], 3) if st["GB_per_s"] else None
+            out["GB_per_s"][arm] = row
     return out
 
 

@@ -378,6 +378,44 @@ int genesys_kv_client(const uint8_t *reqs, const uint64_t *req_off, uint64_t n, 
                       uint16_t port_base, uint32_t n_sockets, uint64_t timeout_ns, uint8_t *replies,
                       uint32_t *reply_len, uint64_t *latency_ns, uint64_t *stats);
 
+/* UDP echo server (Sec. 7.3, Fig. 10: bandwidth versus packet size; the GPU
+ * part of the paper's echo server calls recvfrom/sendto at work-group grain,
+ * blocking, weak ordering).  A persistent GPU kernel, one block per UDP
+ * socket on 127.0.0.1:port_base + w.  form GENESYS_ECHO_SINGLE: a block
+ * receives one datagram with recvfrom; GENESYS_ECHO_BATCH: up to `batch`
+ * (1..GENESYS_ECHO_MAX_BATCH) with recvmmsg.  The block copies each datagram
+ * through its SMs from a receive buffer to a send buffer (both in the
+ * context's host-mapped staging, 2 * batch * max_packet bytes per socket plus
+ * headers) and sends it back to its sender (sendto / sendmmsg).  Datagrams
+ * are at most max_packet (8..GENESYS_ECHO_PACKET_MAX) bytes; a datagram of
+ * GENESYS_ECHO_STOP_BYTES bytes ends its block, as do genesys_echo_stop and
+ * idle_timeout_ns without datagrams (0 = 10 s).  Errors: GENESYS_EINVAL
+ * (argument ranges, bind failure), GENESYS_ENOMEM (staging too small). */
+#define GENESYS_ECHO_PACKET_MAX 65504u
+#define GENESYS_ECHO_MAX_BATCH 64u
+#define GENESYS_ECHO_STOP_BYTES 4u
+#define GENESYS_ECHO_SINGLE 0u
+#define GENESYS_ECHO_BATCH 1u
+typedef struct genesys_echo_server genesys_echo_server;
+int genesys_echo_start(genesys_ctx *ctx, uint32_t n_sockets, uint32_t max_packet, uint32_t form, uint32_t batch,
+                       uint32_t threads, uint16_t port_base, uint64_t idle_timeout_ns, genesys_echo_server **out);
+/* Stop the echo server (bounded by timeout_ns), drain its calls and free it;
+ * stats[2] (if non-NULL): datagrams echoed, bytes echoed. */
+int genesys_echo_stop(genesys_echo_server *srv, uint64_t timeout_ns, uint64_t *stats);
+/* Closed-loop UDP echo load generator on n_threads host threads (each with
+ * its own socket and the server sockets s = t, t + n_threads, ...): `window`
+ * datagrams of packet_bytes (8..GENESYS_ECHO_PACKET_MAX) in flight per server
+ * socket (fewer if the replies would not fit in half of the thread's receive
+ * buffer), n_packets in total.  A datagram is lane u32, generation u32, then
+ * seeded bytes; a reply counts as echoed when it equals the datagram byte for
+ * byte.  Ends when every datagram is answered or no reply came for stall_ns
+ * (0 = 200 ms); then, if send_stop, sends a GENESYS_ECHO_STOP_BYTES datagram
+ * to every server socket.  stats[7]: sent, echoed, bad replies, lost (no
+ * reply), first send to last reply (ns), echoed bytes, send errors. */
+int genesys_echo_client(uint16_t port_base, uint32_t n_sockets, uint32_t packet_bytes, uint64_t n_packets,
+                        uint32_t window, uint32_t n_threads, uint64_t seed, uint64_t stall_ns, uint32_t send_stop,
+                        uint64_t *stats);
+
 /* C6, block permutation (Sec. 6, Fig. 6): n_blocks thread blocks of 1024
  * threads each take one 8 KiB block of input_dev (device), permute it `iters`
  * times with out[i] = in[perm_dev[i]] (perm_dev: 8192 uint16, device), copy it

@@ -54,6 +54,15 @@ def _L():
         L.oracle_c4_replay.restype = ctypes.c_int64
         L.oracle_c4_replay.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]
+        L.oracle_kv_index.restype = ctypes.c_int64
+        L.oracle_kv_index.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]
+        L.oracle_kv_serve.restype = ctypes.c_int64
+        L.oracle_kv_serve.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                      ctypes.c_void_p]
+        L.oracle_udp_echo.restype = ctypes.c_int64
+        L.oracle_udp_echo.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
+                                      ctypes.c_void_p]
         L.oracle_c6_permute.restype = ctypes.c_int64
         L.oracle_c6_permute.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint32,
                                         ctypes.c_char_p]
@@ -169,10 +178,7 @@ def c4_replay(trace, idx=None):
     of the trace (in the given order, default seq order), as a list of bytes."""
     import workloads
     nk = len(trace.keys)
-    vals = np.zeros((nk, 1024), np.uint8)
-    for i in range(nk):
-        v = trace.value0(i)
-        vals[i, :len(v)] = np.frombuffer(v, np.uint8)
+    vals = trace.values0_table()
     vlens = trace.vlen0.astype(np.uint16).copy()
     reqs, _ = workloads.kv_request_bytes(trace, idx)
     n = len(trace) if idx is None else len(idx)
@@ -183,6 +189,74 @@ def c4_replay(trace, idx=None):
     _check(_L().oracle_c4_replay(keys.ctypes.data, nk, vals.ctypes.data, vlens.ctypes.data, rb, n,
                                  out.ctypes.data, off.ctypes.data), "c4_replay")
     return [out[int(off[i]):int(off[i + 1])].tobytes() for i in range(n)]
+
+
+def _udp_sockets(port_base: int, n: int):
+    import socket
+    socks = []
+    try:
+        for w in range(n):
+            so = socket.socket(socket.AF_INET, socket.SOCK_DGRAM)
+            socks.append(so)
+            for opt, force in ((socket.SO_RCVBUF, 33), (socket.SO_SNDBUF, 32)):  # *BUFFORCE when permitted
+                try:
+                    so.setsockopt(socket.SOL_SOCKET, force, 64 << 20)
+                except OSError:
+                    so.setsockopt(socket.SOL_SOCKET, opt, 64 << 20)
+            so.bind(("127.0.0.1", port_base + w))
+    except OSError:
+        for so in socks:
+            so.close()
+        raise
+    return socks
+
+
+class UdpServer:
+    """A plain CPU server (Sec. 7.3) on 127.0.0.1:port_base + w, w < n_sockets,
+    run by `threads` host threads (thread t answers sockets t, t + threads, ...)
+    until every socket gets its stop datagram or idle_ns passes without one.
+    kind "echo": each datagram goes back unchanged.  kind "kv": each request is
+    applied like c4_replay to the table of `trace` (keys and preloaded values).
+    The sockets are bound before the constructor returns."""
+
+    def __init__(self, kind: str, port_base: int, n_sockets: int, threads: int = 1, trace=None,
+                 max_packet: int = 65504, idle_ns: int = 10_000_000_000, values0=None):
+        import threading
+        self.socks = _udp_sockets(port_base, n_sockets)
+        self.stats = np.zeros((threads, 2), np.uint64)
+        L = _L()
+        if kind == "kv":
+            nk = len(trace.keys)
+            self._keys = np.ascontiguousarray(trace.keys)
+            self._order = np.zeros(max(nk, 1), np.uint32)
+            L.oracle_kv_index(self._keys.ctypes.data, nk, self._order.ctypes.data)
+            # values0: trace.values0_table() computed once by the caller (copied here)
+            self.vals = trace.values0_table() if values0 is None else np.array(values0, np.uint8, copy=True)
+            self.vlens = trace.vlen0.astype(np.uint16).copy()
+            if threads != 1:
+                raise ValueError("the key-value oracle server is single-threaded (one table, one order)")
+        self._fds = [np.array([s.fileno() for s in self.socks[t::threads]], np.int32) for t in range(threads)]
+
+        def run(t):
+            fds = self._fds[t]
+            st = self.stats[t]
+            if kind == "echo":
+                L.oracle_udp_echo(fds.ctypes.data, len(fds), max_packet, idle_ns, st.ctypes.data)
+            else:
+                L.oracle_kv_serve(fds.ctypes.data, len(fds), self._keys.ctypes.data, self._order.ctypes.data,
+                                  len(self._keys), self.vals.ctypes.data, self.vlens.ctypes.data, idle_ns,
+                                  st.ctypes.data)
+
+        self._threads = [threading.Thread(target=run, args=(t,), daemon=True) for t in range(threads)]
+        for th in self._threads:
+            th.start()
+
+    def join(self, timeout: float = 60.0) -> dict:
+        for th in self._threads:
+            th.join(timeout)
+        for s in self.socks:
+            s.close()
+        return {"answered": int(self.stats[:, 0].sum()), "bytes": int(self.stats[:, 1].sum())}
 
 
 def c6_permute(input_bytes: np.ndarray, perm: np.ndarray, iters: int, path: str) -> int:

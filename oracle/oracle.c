@@ -16,7 +16,10 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <netinet/in.h>
 #include <sys/mman.h>
+#include <sys/socket.h>
+#include <time.h>
 #include <unistd.h>
 
 /* ------------------------------------------------------------------ common */
@@ -330,44 +333,137 @@ static int order_cmp(const void *x, const void *y) {
   return key_cmp(sort_keys + 16 * (size_t)*(const uint32_t *)x, sort_keys + 16 * (size_t)*(const uint32_t *)y);
 }
 
+/* Apply one request datagram q to the table and write its reply to rep;
+ * returns the reply length. */
+static uint64_t c4_apply(const uint8_t *keys, const uint32_t *order, uint32_t n_keys, uint8_t *vals, uint16_t *vlens,
+                         const uint8_t *q, uint8_t *rep) {
+  const uint8_t op = q[0];
+  const uint16_t vlen = (uint16_t)(q[2] | (q[3] << 8));
+  const int64_t k = find_key(keys, order, n_keys, q + 8);
+  rep[0] = (uint8_t)(op | 0x80);
+  memcpy(rep + 4, q + 4, 4);
+  uint16_t rlen = 0;
+  if (k < 0) {
+    rep[1] = 1;
+  } else if (op == 0) {
+    rep[1] = 0;
+    rlen = vlens[k];
+    memcpy(rep + 8, vals + (size_t)k * 1024, rlen);
+  } else {
+    rep[1] = 0;
+    vlens[k] = vlen;
+    memcpy(vals + (size_t)k * 1024, q + 24, vlen);
+  }
+  rep[2] = (uint8_t)rlen;
+  rep[3] = (uint8_t)(rlen >> 8);
+  return 8 + (uint64_t)rlen;
+}
+
+/* order[i] = the key numbers sorted by key bytes (the lookup index). */
+int64_t oracle_kv_index(const uint8_t *keys, uint32_t n_keys, uint32_t *order) {
+  for (uint32_t i = 0; i < n_keys; ++i) order[i] = i;
+  sort_keys = keys;
+  qsort(order, n_keys, sizeof(uint32_t), order_cmp);
+  return 0;
+}
+
 int64_t oracle_c4_replay(const uint8_t *keys, uint32_t n_keys, uint8_t *vals, uint16_t *vlens, const uint8_t *reqs,
                          uint64_t n, uint8_t *out, uint64_t *out_off) {
   uint32_t *order = (uint32_t *)malloc(sizeof(uint32_t) * (n_keys ? n_keys : 1));
   if (!order) return -ENOMEM;
-  for (uint32_t i = 0; i < n_keys; ++i) order[i] = i;
-  sort_keys = keys;
-  qsort(order, n_keys, sizeof(uint32_t), order_cmp);
+  oracle_kv_index(keys, n_keys, order);
   uint64_t pos = 0, o = 0;
   for (uint64_t r = 0; r < n; ++r) {
     const uint8_t *q = reqs + pos;
-    const uint8_t op = q[0];
-    const uint16_t vlen = (uint16_t)(q[2] | (q[3] << 8));
-    const uint8_t *seq = q + 4;
-    const int64_t k = find_key(keys, order, n_keys, q + 8);
-    uint8_t *rep = out + o;
-    rep[0] = (uint8_t)(op | 0x80);
-    memcpy(rep + 4, seq, 4);
-    uint16_t rlen = 0;
-    if (k < 0) {
-      rep[1] = 1;
-    } else if (op == 0) {
-      rep[1] = 0;
-      rlen = vlens[k];
-      memcpy(rep + 8, vals + (size_t)k * 1024, rlen);
-    } else {
-      rep[1] = 0;
-      vlens[k] = vlen;
-      memcpy(vals + (size_t)k * 1024, q + 24, vlen);
-    }
-    rep[2] = (uint8_t)rlen;
-    rep[3] = (uint8_t)(rlen >> 8);
     out_off[r] = o;
-    o += 8 + rlen;
-    pos += 24 + (op == 1 ? vlen : 0);
+    o += c4_apply(keys, order, n_keys, vals, vlens, q, out + o);
+    pos += 24 + (q[0] == 1 ? (uint16_t)(q[2] | (q[3] << 8)) : 0);
   }
   out_off[n] = o;
   free(order);
   return (int64_t)o;
+}
+
+/* ------------------------------------------------------------ UDP servers
+ * Plain CPU servers for the network workloads (Sec. 7.3: the echo server can
+ * process packets on the CPU or on the GPU, both with recvfrom/sendto).  One
+ * host thread answers the datagrams of the given sockets (bound by the
+ * caller) one at a time: it polls them round robin with non-blocking
+ * recvfrom and answers with sendto to the sender.  It returns when every
+ * socket got its stop datagram, or when nothing arrived for idle_ns. */
+static uint64_t mono_ns(void) {
+  struct timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
+}
+
+/* Echo: each datagram goes back unchanged; a 4-byte datagram is the stop
+ * datagram.  stats[2]: datagrams echoed, bytes echoed. */
+int64_t oracle_udp_echo(const int32_t *fds, uint32_t n_fds, uint32_t max_packet, uint64_t idle_ns, uint64_t *stats) {
+  uint8_t *buf = (uint8_t *)malloc(max_packet ? max_packet : 1);
+  uint8_t *done = (uint8_t *)calloc(n_fds ? n_fds : 1, 1);
+  if (!buf || !done) { free(buf); free(done); return -ENOMEM; }
+  uint32_t open = n_fds;
+  uint64_t last = mono_ns();
+  stats[0] = stats[1] = 0;
+  while (open > 0) {
+    int got = 0;
+    for (uint32_t i = 0; i < n_fds; ++i) {
+      if (done[i]) continue;
+      struct sockaddr_storage from;
+      socklen_t flen = sizeof from;
+      const ssize_t n = recvfrom(fds[i], buf, max_packet, MSG_DONTWAIT, (struct sockaddr *)&from, &flen);
+      if (n < 0) continue;
+      got = 1;
+      if (n == 4) { done[i] = 1; --open; continue; }
+      if (sendto(fds[i], buf, (size_t)n, 0, (struct sockaddr *)&from, flen) == n) {
+        stats[0] += 1;
+        stats[1] += (uint64_t)n;
+      }
+    }
+    const uint64_t now = mono_ns();
+    if (got) last = now;
+    else if (now - last > idle_ns) break;
+  }
+  free(buf);
+  free(done);
+  return (int64_t)stats[0];
+}
+
+/* Key-value: each request datagram is applied in arrival order with the same
+ * rule as oracle_c4_replay (order from oracle_kv_index); op 2 is the stop
+ * datagram.  stats[2]: requests answered, reply bytes. */
+int64_t oracle_kv_serve(const int32_t *fds, uint32_t n_fds, const uint8_t *keys, const uint32_t *order,
+                        uint32_t n_keys, uint8_t *vals, uint16_t *vlens, uint64_t idle_ns, uint64_t *stats) {
+  uint8_t q[24 + 1024 + 64], rep[8 + 1024];
+  uint8_t *done = (uint8_t *)calloc(n_fds ? n_fds : 1, 1);
+  if (!done) return -ENOMEM;
+  uint32_t open = n_fds;
+  uint64_t last = mono_ns();
+  stats[0] = stats[1] = 0;
+  while (open > 0) {
+    int got = 0;
+    for (uint32_t i = 0; i < n_fds; ++i) {
+      if (done[i]) continue;
+      struct sockaddr_storage from;
+      socklen_t flen = sizeof from;
+      const ssize_t n = recvfrom(fds[i], q, sizeof q, MSG_DONTWAIT, (struct sockaddr *)&from, &flen);
+      if (n < 0) continue;
+      got = 1;
+      if (n >= 1 && q[0] == 2) { done[i] = 1; --open; continue; }
+      if (n < 24) continue;
+      const uint64_t r = c4_apply(keys, order, n_keys, vals, vlens, q, rep);
+      if (sendto(fds[i], rep, r, 0, (struct sockaddr *)&from, flen) == (ssize_t)r) {
+        stats[0] += 1;
+        stats[1] += r;
+      }
+    }
+    const uint64_t now = mono_ns();
+    if (got) last = now;
+    else if (now - last > idle_ns) break;
+  }
+  free(done);
+  return (int64_t)stats[0];
 }
 
 /* ---------------------------------------------------------------------- C6

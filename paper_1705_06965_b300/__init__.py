@@ -43,7 +43,8 @@ EXPORTS = [
     "genesys_c1_histogram", "genesys_c2_pwrite", "genesys_visibility_probe", "genesys_last_launch_ms",
     "genesys_c3_wordcount", "genesys_c3_wordcount_noalloc", "genesys_serve_config_default", "genesys_c5_serve",
     "genesys_reclaim", "genesys_mmap_reserve", "genesys_kv_start", "genesys_kv_stop", "genesys_kv_value",
-    "genesys_kv_client", "genesys_c6_permute", "genesys_gpu_call",
+    "genesys_kv_client", "genesys_c6_permute", "genesys_gpu_call", "genesys_echo_start", "genesys_echo_stop",
+    "genesys_echo_client",
 ]
 
 
@@ -147,6 +148,9 @@ def lib() -> ctypes.CDLL:
         "genesys_kv_client": (ctypes.c_int, [vp, vp, u64, vp, ctypes.c_uint16, u32, u64, vp, vp, vp, vp]),
         "genesys_c5_serve": (ctypes.c_int, [vp, vp, u32, vp, u32, ctypes.c_int32, ctypes.POINTER(ServeConfig), vp, vp,
                                             ctypes.POINTER(ServeStats)]),
+        "genesys_echo_start": (ctypes.c_int, [vp, u32, u32, u32, u32, u32, ctypes.c_uint16, u64, ctypes.POINTER(vp)]),
+        "genesys_echo_stop": (ctypes.c_int, [vp, u64, vp]),
+        "genesys_echo_client": (ctypes.c_int, [ctypes.c_uint16, u32, u32, u64, u32, u32, u64, u64, u32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -421,3 +425,39 @@ def kv_client(reqs: bytes, req_off, arrival_ns, port_base: int, n_sockets: int, 
     stats["rc"] = rc
     reps = [out[j * KV_REPLY_STRIDE: j * KV_REPLY_STRIDE + int(rlen[j])].tobytes() for j in range(n)]
     return reps, lat[:n], stats
+
+
+ECHO_SINGLE, ECHO_BATCH = 0, 1
+ECHO_PACKET_MAX, ECHO_MAX_BATCH, ECHO_STOP_BYTES = 65504, 64, 4
+
+
+class EchoServer:
+    """GPU UDP echo server (genesys_echo_start / genesys_echo_stop)."""
+
+    def __init__(self, ctx: Context, n_sockets: int = 8, max_packet: int = ECHO_PACKET_MAX, form: int = ECHO_SINGLE,
+                 batch: int = 16, threads: int = 256, port_base: int = 45000, idle_timeout_ns: int = 20_000_000_000):
+        self.n_sockets, self.port_base = n_sockets, port_base
+        h = ctypes.c_void_p()
+        _check(lib().genesys_echo_start(ctx.handle, n_sockets, max_packet, form, batch, threads, port_base,
+                                        idle_timeout_ns, ctypes.byref(h)), "genesys_echo_start")
+        self._h = h
+
+    def stop(self, timeout_ns: int = 30_000_000_000) -> dict:
+        st = np.zeros(2, np.uint64)
+        if self._h:
+            h, self._h = self._h, None
+            _check(lib().genesys_echo_stop(h, timeout_ns, st.ctypes.data), "genesys_echo_stop")
+        return {"packets": int(st[0]), "bytes": int(st[1])}
+
+
+def echo_client(port_base: int, n_sockets: int, packet_bytes: int, n_packets: int, window: int = 4,
+                threads: int = 4, seed: int = 0x5EED0010, stall_ns: int = 0, send_stop: bool = True) -> dict:
+    """Closed-loop UDP echo load generator (genesys_echo_client); returns its
+    counters, and GB/s of echoed bytes over the first-send-to-last-reply span."""
+    st = np.zeros(7, np.uint64)
+    _check(lib().genesys_echo_client(port_base, n_sockets, packet_bytes, n_packets, window, threads, seed, stall_ns,
+                                     int(send_stop), st.ctypes.data), "genesys_echo_client")
+    names = ("sent", "echoed", "bad", "lost", "span_ns", "bytes", "send_errors")
+    out = {k: int(v) for k, v in zip(names, st)}
+    out["GB_per_s"] = out["bytes"] / out["span_ns"] if out["span_ns"] else None
+    return out

@@ -14,7 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libgenesys.so")
 
-SOURCES = ["runtime.cpp", "workloads.cu", "wordcount.cu", "serve.cu", "kv.cu"]
+SOURCES = ["runtime.cpp", "workloads.cu", "wordcount.cu", "serve.cu", "kv.cu", "echo.cu"]
 HEADERS = [os.path.join(INCLUDE, h) for h in ("genesys.h", "genesys_layout.h", "genesys_device.cuh")] + [
     os.path.join(CSRC, "internal.h")]
 

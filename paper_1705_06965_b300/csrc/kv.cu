@@ -147,7 +147,10 @@ __global__ void __launch_bounds__(1024) kv_server_kernel(genesys_dev g, const in
   unsigned long long my_served = 0;
   for (;;) {
     for (uint32_t i = threadIdx.x; i < batch; i += blockDim.x) A->rhdr[i].msg_hdr.msg_namelen = sizeof(sockaddr_in6);
-    // consumer role: the barrier before is not needed, the one after is
+    // the consumer-role call has no barrier before it: these stores of other
+    // threads reach the host ahead of the request through this barrier and
+    // the caller's release
+    __syncthreads();
     const int64_t n = call<GROUP, RELAXED, BLOCKING, ROLE_CONSUMER>(g, SYS_recvmmsg, (uint64_t)fd, (uint64_t)A->rhdr,
                                                                     batch, MSG_DONTWAIT, 0);
     if (n == -EAGAIN || n == 0) {
@@ -429,27 +432,61 @@ extern "C" int genesys_kv_client(const uint8_t *reqs, const uint64_t *req_off, u
   std::vector<uint64_t> t_send(n, 0);
   memset(reply_len, 0, sizeof(uint32_t) * n);
   std::atomic<uint64_t> received{0};
-  std::atomic<bool> sender_done{false};
-  const uint64_t t0 = mono_ns() + 1000000;  // start in 1 ms
-  uint64_t send_err = 0, late_ns_max = 0;
-  std::thread sender([&] {
-    for (uint64_t j = 0; j < n; ++j) {
-      const uint64_t at = t0 + arrival_ns[j];
-      while (mono_ns() < at) __builtin_ia32_pause();
-      const uint8_t *q = reqs + req_off[j];
-      uint32_t k0;
-      memcpy(&k0, q + 8, 4);
-      sockaddr_in to{};
-      to.sin_family = AF_INET;
-      to.sin_port = htons((uint16_t)(port_base + k0 % n_sockets));
-      to.sin_addr.s_addr = htonl(INADDR_LOOPBACK);
-      const uint64_t now = mono_ns();
-      late_ns_max = std::max(late_ns_max, now - at);
-      t_send[j] = now;
-      if (sendto(fd, q, req_off[j + 1] - req_off[j], 0, (sockaddr *)&to, sizeof to) < 0) ++send_err;
-    }
-    sender_done = true;
-  });
+  // senders: thread w owns the sockets s with s % n_senders == w, sends its
+  // requests in sequence order, and batches every request that is due into
+  // one sendmmsg
+  const uint32_t n_senders = std::min<uint32_t>(n_sockets, 4);
+  std::vector<std::vector<uint64_t>> owned(n_senders);
+  for (uint64_t j = 0; j < n; ++j) {
+    uint32_t k0;
+    memcpy(&k0, reqs + req_off[j] + 8, 4);
+    owned[(k0 % n_sockets) % n_senders].push_back(j);
+  }
+  std::vector<uint64_t> send_err(n_senders, 0), late_max(n_senders, 0);
+  std::vector<std::thread> senders;
+  const uint64_t t0 = mono_ns() + 2000000;  // start in 2 ms, once the threads run
+  for (uint32_t w = 0; w < n_senders; ++w) {
+    senders.emplace_back([&, w] {
+      const std::vector<uint64_t> &mine = owned[w];
+      constexpr int kB = 64;
+      std::vector<mmsghdr> hdr(kB);
+      std::vector<iovec> iov(kB);
+      std::vector<sockaddr_in> to(kB);
+      size_t i = 0;
+      while (i < mine.size()) {
+        const uint64_t at = t0 + arrival_ns[mine[i]];
+        uint64_t now = mono_ns();
+        if (now < at) { __builtin_ia32_pause(); continue; }
+        int m = 0;
+        while (m < kB && i + m < mine.size() && t0 + arrival_ns[mine[i + m]] <= now) {
+          const uint64_t j = mine[i + m];
+          const uint8_t *q = reqs + req_off[j];
+          uint32_t k0;
+          memcpy(&k0, q + 8, 4);
+          to[m] = sockaddr_in{};
+          to[m].sin_family = AF_INET;
+          to[m].sin_port = htons((uint16_t)(port_base + k0 % n_sockets));
+          to[m].sin_addr.s_addr = htonl(INADDR_LOOPBACK);
+          iov[m] = {(void *)q, (size_t)(req_off[j + 1] - req_off[j])};
+          memset(&hdr[m], 0, sizeof(mmsghdr));
+          hdr[m].msg_hdr.msg_name = &to[m];
+          hdr[m].msg_hdr.msg_namelen = sizeof(sockaddr_in);
+          hdr[m].msg_hdr.msg_iov = &iov[m];
+          hdr[m].msg_hdr.msg_iovlen = 1;
+          late_max[w] = std::max(late_max[w], now - (t0 + arrival_ns[j]));
+          t_send[j] = now;
+          ++m;
+        }
+        int sent = 0;
+        while (sent < m) {
+          const int r = sendmmsg(fd, hdr.data() + sent, m - sent, 0);
+          if (r <= 0) { send_err[w] += m - sent; break; }
+          sent += r;
+        }
+        i += m;
+      }
+    });
+  }
   const uint64_t deadline = t0 + (n ? arrival_ns[n - 1] : 0) + timeout_ns;
   std::vector<mmsghdr> hdr(64);
   std::vector<iovec> iov(64);
@@ -484,7 +521,7 @@ extern "C" int genesys_kv_client(const uint8_t *reqs, const uint64_t *req_off, u
       received.fetch_add(1);
     }
   }
-  sender.join();
+  for (auto &t : senders) t.join();
   // STOP to every socket (no reply)
   for (uint32_t w = 0; w < n_sockets; ++w) {
     uint8_t stop[24] = {GENESYS_KV_STOP};
@@ -499,8 +536,10 @@ extern "C" int genesys_kv_client(const uint8_t *reqs, const uint64_t *req_off, u
     stats[0] = received.load();
     stats[1] = dup;
     stats[2] = bad;
-    stats[3] = send_err;
-    stats[4] = late_ns_max;
+    uint64_t se = 0, lm = 0;
+    for (uint32_t w = 0; w < n_senders; ++w) { se += send_err[w]; lm = std::max(lm, late_max[w]); }
+    stats[3] = se;
+    stats[4] = lm;
     uint64_t first = ~0ull, last = 0;
     for (uint64_t j = 0; j < n; ++j) {
       if (!reply_len[j]) continue;

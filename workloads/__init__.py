@@ -284,6 +284,24 @@ class KVTrace:
     def value0(self, i: int) -> bytes:
         return stream_bytes(int(self.vseed0[i]), int(self.vlen0[i]))
 
+    def values0_table(self, width: int = 1024) -> np.ndarray:
+        """All preload values as a [n_keys, width] byte table (row i = value0(i),
+        zero padded), generated in blocks of keys."""
+        nk = len(self.vlen0)
+        out = np.zeros((nk, width), np.uint8)
+        w = np.arange(width // 8, dtype=np.uint64)
+        col = np.arange(width)
+        for a in range(0, nk, 1 << 16):
+            b = min(nk, a + (1 << 16))
+            with np.errstate(over="ignore"):
+                z = self.vseed0[a:b, None].astype(np.uint64) + (w[None, :] + np.uint64(1)) * np.uint64(GAMMA)
+                z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+                z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+                z = z ^ (z >> np.uint64(31))
+            rows = z.astype("<u8").view(np.uint8).reshape(b - a, width)
+            out[a:b] = np.where(col[None, :] < self.vlen0[a:b, None], rows, 0)
+        return out
+
 
 def kv_trace(params: dict | None = None) -> KVTrace:
     p = dict(C4_FULL if params is None else params)
