@@ -356,9 +356,18 @@ def run_only(args):
         else:
             raise SystemExit(f"unknown --only kind {kind}")
         fn()
+        before = rig.ctx.stats()
         ms = rig.timed(fn)
+        after = rig.ctx.stats()
+        d = {k: after[k] - before[k] for k in ("requests", "os_calls", "batches", "busy_ns")}
+        d["syscall_ns"] = sum(after["op_ns"][o] - before["op_ns"][o] for o in after["op_ns"])
         out.update({"ms": round(ms, 3), "calls": calls, "calls_per_s": round(calls / (ms * 1e-3), 1),
-                    "kernel_ms": round(rig.ctx.last_launch_ms(), 3)})
+                    "kernel_ms": round(rig.ctx.last_launch_ms(), 3),
+                    "service": {**d, "requests_per_os_call": round(d["requests"] / max(d["os_calls"], 1), 2),
+                                "requests_per_batch": round(d["requests"] / max(d["batches"], 1), 2),
+                                "busy_frac": round(d["busy_ns"] / (ms * 1e6 * args.service_threads), 4)}})
+        if kind == "c2" and g == 0:
+            out["service_probe_calls_per_s"] = round(rig.ctx.service_probe(rig.fds[n], rig.c2_stage, 64, n), 1)
         print(json.dumps(out), flush=True)
     finally:
         rig.close()
@@ -725,6 +734,17 @@ def run_genesys(args):
     batched_key = max((k for k in sweep if "relaxed" in k), key=lambda k: sweep[k]["requests_per_s"])
     batched = sweep[batched_key]
 
+    # The work-item kernels are bound by the service threads' rate, not by the
+    # link: their calls/s against the ceiling of the same requests published
+    # by a host thread (no GPU in the loop; same threads and batch size).
+    torch.cuda.synchronize()
+    n_probe = SIZES[-1]
+    ceiling = max(ctx.service_probe(rig.fds[n_probe], rig.c2_stage, 64, n_probe) for _ in range(3))
+    service_roofline = {"bound": "host_service", "kernel": "c2_pwrite_kernel<work-item,strong,blocking>",
+                        "threads": n_probe, "achieved": plain["syscalls_per_s"], "peak": round(ceiling, 1),
+                        "unit": "calls/s", "frac": round(plain["syscalls_per_s"] / ceiling, 4),
+                        "peak_source": "genesys_service_probe: the same 2^20 64-byte pwrites published by a host "
+                                       "thread, same service threads and batch size, best of 3 (measured)"}
     link = host_link_peak(torch)
     extras = profile_extras(args, rig, local, rank, link) if args.extras else {}
     # dominant kernel of the timed region and its host-link roofline
@@ -751,7 +771,8 @@ def run_genesys(args):
                 "frac": round(achieved / peak, 5), "traffic": load_traffic(dom, units),
                 "peak_source": "pinned cudaMemcpy 256 MiB in this run (of measured)",
                 "alg_bytes_per_launch": int(alg_bytes), "avg_launch_ms": round(avg_ms, 4),
-                "share_of_timed_device_time": round(tot[dom] / sum(tot.values()), 4)}
+                "share_of_timed_device_time": round(tot[dom] / sum(tot.values()), 4),
+                "service": service_roofline}
 
     cpu = cpu_baseline_sample(budget_s=20.0) if rank == 0 and args.extras else None
 

@@ -416,6 +416,20 @@ int genesys_echo_client(uint16_t port_base, uint32_t n_sockets, uint32_t packet_
                         uint32_t window, uint32_t n_threads, uint64_t seed, uint64_t stall_ns, uint32_t send_stop,
                         uint64_t *stats);
 
+/* Service-rate ceiling for work-item pwrites (Sec. 5, CPU-side system call
+ * processing): the calling host thread publishes n_calls requests
+ * pwrite(fd, payload + i * bytes_per_call, bytes_per_call, i * bytes_per_call)
+ * into the slot area, one slot each, as a work-item-grain blocking launch
+ * would (slots filled first, in rounds of n_slots), and *elapsed_ns is the
+ * time from the first doorbell entry to the last completion, summed over the
+ * rounds: the service threads' time alone, with no GPU in the loop.  payload
+ * is a host address.  The context must be idle (no kernel running, no slot
+ * claimed: GENESYS_EINVAL otherwise); its device-side sequence numbers and
+ * ring tails are updated so that kernels can continue to use it.  A call that
+ * wrote fewer bytes than asked makes it return GENESYS_EINVAL. */
+int genesys_service_probe(genesys_ctx *ctx, int fd, const void *payload, uint32_t bytes_per_call, uint64_t n_calls,
+                          uint64_t *elapsed_ns);
+
 /* C6, block permutation (Sec. 6, Fig. 6): n_blocks thread blocks of 1024
  * threads each take one 8 KiB block of input_dev (device), permute it `iters`
  * times with out[i] = in[perm_dev[i]] (perm_dev: 8192 uint16, device), copy it

@@ -44,7 +44,7 @@ EXPORTS = [
     "genesys_c3_wordcount", "genesys_c3_wordcount_noalloc", "genesys_serve_config_default", "genesys_c5_serve",
     "genesys_reclaim", "genesys_mmap_reserve", "genesys_kv_start", "genesys_kv_stop", "genesys_kv_value",
     "genesys_kv_client", "genesys_c6_permute", "genesys_gpu_call", "genesys_echo_start", "genesys_echo_stop",
-    "genesys_echo_client",
+    "genesys_echo_client", "genesys_service_probe",
 ]
 
 
@@ -148,6 +148,7 @@ def lib() -> ctypes.CDLL:
         "genesys_kv_client": (ctypes.c_int, [vp, vp, u64, vp, ctypes.c_uint16, u32, u64, vp, vp, vp, vp]),
         "genesys_c5_serve": (ctypes.c_int, [vp, vp, u32, vp, u32, ctypes.c_int32, ctypes.POINTER(ServeConfig), vp, vp,
                                             ctypes.POINTER(ServeStats)]),
+        "genesys_service_probe": (ctypes.c_int, [vp, ctypes.c_int, vp, u32, u64, ctypes.POINTER(u64)]),
         "genesys_echo_start": (ctypes.c_int, [vp, u32, u32, u32, u32, u32, ctypes.c_uint16, u64, ctypes.POINTER(vp)]),
         "genesys_echo_stop": (ctypes.c_int, [vp, u64, vp]),
         "genesys_echo_client": (ctypes.c_int, [ctypes.c_uint16, u32, u32, u64, u32, u32, u64, u64, u32, vp]),
@@ -275,6 +276,14 @@ class Context:
 
     def stats_reset(self) -> None:
         _check(lib().genesys_stats_reset(self.handle), "genesys_stats_reset")
+
+    def service_probe(self, fd: int, payload: int, bytes_per_call: int, n_calls: int) -> float:
+        """Service-thread ceiling for work-item pwrites (genesys_service_probe):
+        the host publishes the requests itself; returns calls per second."""
+        ns = ctypes.c_uint64()
+        _check(lib().genesys_service_probe(self.handle, fd, payload, bytes_per_call, n_calls, ctypes.byref(ns)),
+               "genesys_service_probe")
+        return n_calls / (ns.value * 1e-9) if ns.value else float("inf")
 
     def status(self, clear: bool = True) -> list:
         out = (ctypes.c_int32 * ST_WORDS)()

@@ -338,6 +338,7 @@ size_t merge_run(genesys_ctx *c, Request *reqs, size_t i, size_t n, Counters &k)
   for (size_t t = i; t < j; ++t) total += reqs[t].a[2];
   int64_t res;
   bump(k.os_calls, 1);
+  const uint64_t e0 = mono_ns();
   if (m == 1 || contiguous_buf) {
     void *buf = (void *)reqs[i].a[1];
     long r = nr == SYS_pread64 ? pread(fd, buf, total, (off_t)off) : pwrite(fd, buf, total, (off_t)off);
@@ -348,6 +349,10 @@ size_t merge_run(genesys_ctx *c, Request *reqs, size_t i, size_t n, Counters &k)
     long r = nr == SYS_pread64 ? preadv(fd, iov, (int)m, (off_t)off) : pwritev(fd, iov, (int)m, (off_t)off);
     res = sys_ret(r);
   }
+  const uint64_t dt = mono_ns() - e0;
+  const int oi = nr == SYS_pread64 ? OP_PREAD : OP_PWRITE;
+  bump(k.op_ns[oi], dt);
+  if (dt > k.op_max_ns[oi].load(std::memory_order_relaxed)) k.op_max_ns[oi].store(dt, std::memory_order_relaxed);
   uint64_t prefix = 0;
   for (size_t t = i; t < j; ++t) {
     const uint64_t len = reqs[t].a[2];
@@ -370,9 +375,11 @@ void process_batch(genesys_ctx *c, Request *reqs, size_t n, Counters &k) {
   if (c->cfg.merge && n > 1) {
     // the requests of a batch are concurrent, so any order is a legal
     // schedule: put pread/pwrite requests in (call, fd, offset) order so that
-    // neighbours in a file become adjacent and merge.  A batch usually
-    // arrives nearly in order (a warp's lanes are consecutive), so an
-    // insertion sort is close to one pass.
+    // neighbours in a file become adjacent and merge.  A batch arrives as
+    // ascending runs (a warp's lanes publish in lane order), so the sort
+    // orders whole runs by their first request and concatenates them when
+    // they do not overlap; otherwise it sorts an index.  Each request is then
+    // moved once.
     auto before = [](const Request &x, const Request &y) {
       const bool rx = is_rw(x.nr), ry = is_rw(y.nr);
       if (rx != ry) return rx;
@@ -381,15 +388,40 @@ void process_batch(genesys_ctx *c, Request *reqs, size_t n, Counters &k) {
       if ((int)x.a[0] != (int)y.a[0]) return (int)x.a[0] < (int)y.a[0];
       return x.a[3] < y.a[3];
     };
-    for (size_t i = 1; i < n; ++i) {
-      if (!before(reqs[i], reqs[i - 1])) continue;
-      Request t = reqs[i];
-      size_t j = i;
-      while (j > 0 && before(t, reqs[j - 1])) {
-        reqs[j] = reqs[j - 1];
-        --j;
+    thread_local std::vector<uint32_t> run_start, order;
+    thread_local std::vector<Request> sorted;
+    run_start.clear();
+    run_start.push_back(0);
+    for (size_t i = 1; i < n; ++i)
+      if (before(reqs[i], reqs[i - 1])) run_start.push_back((uint32_t)i);
+    const size_t runs = run_start.size();
+    if (runs > 1) {
+      run_start.push_back((uint32_t)n);
+      // runs by first request (insertion sort of the run numbers: few runs)
+      order.resize(runs);
+      for (size_t r = 0; r < runs; ++r) {
+        size_t j = r;
+        while (j > 0 && before(reqs[run_start[r]], reqs[run_start[order[j - 1]]])) {
+          order[j] = order[j - 1];
+          --j;
+        }
+        order[j] = (uint32_t)r;
       }
-      reqs[j] = t;
+      bool disjoint = true;
+      for (size_t r = 1; r < runs && disjoint; ++r)
+        disjoint = !before(reqs[run_start[order[r]]], reqs[run_start[order[r - 1] + 1] - 1]);
+      sorted.resize(n);
+      size_t o = 0;
+      if (disjoint) {
+        for (size_t r = 0; r < runs; ++r)
+          for (uint32_t i = run_start[order[r]]; i < run_start[order[r] + 1]; ++i) sorted[o++] = reqs[i];
+      } else {
+        order.resize(n);
+        for (size_t i = 0; i < n; ++i) order[i] = (uint32_t)i;
+        std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return before(reqs[x], reqs[y]); });
+        for (size_t i = 0; i < n; ++i) sorted[o++] = reqs[order[i]];
+      }
+      std::copy(sorted.begin(), sorted.begin() + n, reqs);
     }
   }
   for (size_t i = 0; i < n;) {
@@ -965,6 +997,94 @@ int genesys_staging_reset(genesys_ctx *c) {
 // Host emulation of one GPU lane making a call (GENESYS_INIT_HOST_ONLY): the
 // same claim / marshal / publish / doorbell / wait steps as genesys_device.cuh,
 // with CPU atomics on the host copies of the device-side state.
+// Host-side ceiling of the service path for work-item pwrites: the requests
+// a GPU work-item launch would publish (one slot each), published by this
+// thread instead, so that the time is the service threads' alone.  Slots are
+// filled first; the clock runs from the first doorbell entry to the last
+// completion word.  The context's device-side claim state (sequence numbers,
+// ring tails) is read before and written back after, so the context stays
+// usable by kernels.  No kernel may be running on the context meanwhile.
+int genesys_service_probe(genesys_ctx *c, int fd, const void *payload, uint32_t bytes_per_call, uint64_t n_calls,
+                          uint64_t *elapsed_ns) {
+  if (!c || !payload || !elapsed_ns || bytes_per_call == 0) return fail(GENESYS_EINVAL, "NULL argument");
+  if (c->threads.empty()) return fail(GENESYS_EINVAL, "genesys_service_probe needs service threads");
+  const uint32_t S = c->cfg.n_slots, R = c->cfg.n_service_threads;
+  std::vector<uint32_t> seq(S), kd(S), owner(S), tails_raw((size_t)R * 32);
+  auto copy = [&](void *dst, const void *src, size_t bytes, cudaMemcpyKind kind) -> int {
+    if (c->host_only) { memcpy(dst, src, bytes); return 0; }
+    CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, kind, c->aux));
+    CUDA_TRY(cudaStreamSynchronize(c->aux));
+    return 0;
+  };
+  int rc;
+  if ((rc = copy(seq.data(), c->seq, 4ull * S, cudaMemcpyDeviceToHost)) ||
+      (rc = copy(kd.data(), c->known_done, 4ull * S, cudaMemcpyDeviceToHost)) ||
+      (rc = copy(owner.data(), c->owner, 4ull * S, cudaMemcpyDeviceToHost)) ||
+      (rc = copy(tails_raw.data(), c->ring_tail, tails_raw.size() * 4, cudaMemcpyDeviceToHost)))
+    return rc;
+  for (uint32_t s = 0; s < S; ++s) {
+    if (owner[s] != 0) return fail(GENESYS_EINVAL, "service probe: slot %u is claimed (a kernel is running?)", s);
+    if ((uint32_t)(__atomic_load_n(&c->done[s], __ATOMIC_ACQUIRE) >> 32) != seq[s])
+      return fail(GENESYS_EINVAL, "service probe: slot %u has a request in flight", s);
+  }
+  const uint64_t deadline = c->cfg.device_deadline_ns;
+  const uint16_t flags = GENESYS_REQ_BLOCKING | (GENESYS_GRAN_ITEM << GENESYS_REQ_GRAN_SHIFT);
+  const uint8_t *base = (const uint8_t *)payload;
+  uint64_t total = 0, bad = 0;
+  for (uint64_t i0 = 0; i0 < n_calls;) {
+    const uint32_t m = (uint32_t)std::min<uint64_t>(S, n_calls - i0);
+    for (uint32_t s = 0; s < m; ++s) {
+      const uint64_t i = i0 + s;
+      genesys_slot *sl = &c->slots[s];
+      const uint64_t a[6] = {(uint64_t)fd, (uint64_t)(uintptr_t)(base + i * bytes_per_call), bytes_per_call,
+                             i * bytes_per_call, 0, 0};
+      for (int k = 0; k < 6; ++k) __atomic_store_n(&sl->args[k], a[k], __ATOMIC_RELAXED);
+      ++seq[s];
+      __atomic_store_n(&sl->req, ((uint64_t)seq[s] << 32) | ((uint64_t)(SYS_pwrite64 & 0xFFFF) << 16) | flags,
+                       __ATOMIC_RELEASE);
+    }
+    const uint64_t t0 = mono_ns();
+    for (uint32_t s = 0; s < m; ++s) {
+      const uint32_t r = genesys_ring_of(s, R);
+      const uint32_t pos = tails_raw[(size_t)r * 32]++;
+      __atomic_store_n(&c->rings[(size_t)r * c->ring_cap + (pos & (c->ring_cap - 1))], GENESYS_RING_ENTRY(pos, s),
+                       __ATOMIC_RELEASE);
+    }
+    for (uint32_t s = 0; s < m; ++s) {
+      uint64_t d;
+      while ((uint32_t)((d = __atomic_load_n(&c->done[s], __ATOMIC_ACQUIRE)) >> 32) != seq[s]) {
+        if (mono_ns() - t0 > deadline) {
+          rc = fail(GENESYS_ETIMEDOUT, "service probe: slot %u not completed within the deadline", s);
+          break;
+        }
+        cpu_relax();
+      }
+      if (rc) break;
+      if ((int32_t)(uint32_t)d != (int32_t)bytes_per_call) ++bad;
+      kd[s] = seq[s];
+    }
+    total += mono_ns() - t0;
+    if (rc) break;
+    i0 += m;
+  }
+  // the device-side state the kernels continue from
+  if (c->host_only) {
+    memcpy(c->seq, seq.data(), 4ull * S);
+    memcpy(c->known_done, kd.data(), 4ull * S);
+    for (uint32_t r = 0; r < R; ++r) __atomic_store_n(&c->ring_tail[r * 32], tails_raw[(size_t)r * 32], __ATOMIC_RELEASE);
+  } else {
+    int wrc;
+    if ((wrc = copy(c->seq, seq.data(), 4ull * S, cudaMemcpyHostToDevice)) ||
+        (wrc = copy(c->known_done, kd.data(), 4ull * S, cudaMemcpyHostToDevice)) ||
+        (wrc = copy(c->ring_tail, tails_raw.data(), tails_raw.size() * 4, cudaMemcpyHostToDevice)))
+      return wrc;
+  }
+  if (rc) return rc;
+  *elapsed_ns = total;
+  if (bad) return fail(GENESYS_EINVAL, "service probe: %llu calls returned a short count", (unsigned long long)bad);
+  return 0;
+}
+
 int genesys_emulate_call(genesys_ctx *c, uint32_t nr, const uint64_t args[6], uint32_t flags, int64_t *ret) {
   if (!c || !args || !ret) return fail(GENESYS_EINVAL, "NULL argument");
   if (!c->host_only) return fail(GENESYS_EINVAL, "genesys_emulate_call needs a host-only context");

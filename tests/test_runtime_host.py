@@ -217,3 +217,68 @@ def test_host_only_context_cannot_launch():
         one = (ctypes.c_uint32 * 3)(1, 1, 1)
         rc = G.lib().genesys_launch(c.handle, ctypes.c_void_p(1), one, one, 0, None, 0, None)
         assert rc == G.EINVAL
+
+
+@pytest.mark.parametrize("n_slots,threads,n", [(256, 2, 1000), (64, 3, 64 * 7 + 5)])
+def test_service_probe_writes_the_file_and_keeps_state(tmp_path, n_slots, threads, n):
+    """The service ceiling probe publishes work-item pwrites itself: the file
+    must hold the payload, and the context's claim state must let later calls
+    (emulated callers) reuse the same slots."""
+    p = str(tmp_path / "probe.bin")
+    payload = np.frombuffer(workloads.stream_bytes(11, 64 * n), np.uint8).copy()
+    with _ctx(n_slots=n_slots, service_threads=threads) as c:
+        fd = os.open(p, os.O_CREAT | os.O_RDWR | os.O_TRUNC, 0o644)
+        try:
+            rate = c.service_probe(fd, payload.ctypes.data, 64, n)
+            assert rate > 0
+            st = c.stats()
+            assert st["requests"] == n and st["failed"] == 0
+            for k in range(2 * n_slots):  # every slot is claimed again afterwards
+                assert c.emulate_call(G.NR_NOP, [k]) == k
+            c.drain()
+        finally:
+            os.close(fd)
+    with open(p, "rb") as f:
+        assert f.read() == payload.tobytes()
+
+
+def test_service_probe_needs_threads():
+    with _ctx(no_threads=True) as c:
+        with pytest.raises(G.GenesysError):
+            c.service_probe(0, 1, 64, 1)
+
+
+@pytest.mark.parametrize("pattern", ["in_order", "runs_shuffled", "interleaved", "reversed"])
+def test_one_batch_of_neighbours_becomes_one_call(tmp_path, pattern):
+    """A batch's pwrites are put in file order before merging, whatever order
+    they were published in: 64 neighbouring 64-byte pwrites published as one
+    batch become one Linux call, and the file is right."""
+    n = 64
+    idx = np.arange(n)
+    if pattern == "runs_shuffled":   # warps' runs arriving out of order
+        idx = np.concatenate([idx[r * 8:(r + 1) * 8] for r in (5, 2, 7, 0, 3, 6, 1, 4)])
+    elif pattern == "interleaved":   # two lanes' requests alternating: 0, 32, 1, 33, ...
+        idx = np.stack([idx[:n // 2], idx[n // 2:]]).T.ravel()
+    elif pattern == "reversed":
+        idx = idx[::-1]
+    assert sorted(idx.tolist()) == list(range(n))
+    p = str(tmp_path / "o.bin")
+    want = workloads.stream_bytes(3, n * 64)
+    with _ctx(no_threads=True, service_threads=1, n_slots=256, coalesce_max=n) as c:
+        buf = c.staging(n * 64)
+        c.host_view(buf, n * 64)[:] = np.frombuffer(want, np.uint8)
+        fd = os.open(p, os.O_CREAT | os.O_TRUNC | os.O_RDWR, 0o644)
+        try:
+            for gid in idx.tolist():
+                assert c.emulate_call(G.SYS_pwrite64, [fd, buf + gid * 64, 64, gid * 64], flags=0) == 0
+            done = 0
+            for _ in range(100):
+                done += c.service(1_000_000)
+                if done == n:
+                    break
+            st = c.stats()
+        finally:
+            os.close(fd)
+    assert done == n and st["requests"] == n and st["failed"] == 0
+    assert st["os_calls"] == 1, st
+    assert open(p, "rb").read() == want
