@@ -309,8 +309,8 @@ def tune_step(args, local, rank):
         finally:
             rig.close()
 
-    best, table = tuner.tune(key, autotune.grid(service_threads=(2, 4), coalesce_max=(64, 256),
-                                                poll_max_ns=(2048, 32768)), run, repeats=2)
+    best, table = tuner.tune(key, autotune.grid(service_threads=(1, 2, 4), coalesce_max=(64, 256),
+                                                poll_max_ns=(2048,)), run, repeats=2)
     return best, table
 
 

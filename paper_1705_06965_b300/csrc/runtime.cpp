@@ -108,6 +108,24 @@ struct Request {
   int64_t ret;
 };
 
+// One service batch and the scratch its processing needs (owned by one
+// service thread, or by the caller of genesys_service / genesys_drain).
+struct Batch {
+  std::vector<Request> req;
+  std::vector<Request *> ptr;      // processing order
+  std::vector<uint32_t> run;       // first request of each run, then n
+  std::vector<int32_t> next;       // run that continues this one in its file, or -1
+  std::vector<uint8_t> has_pred;
+  std::vector<uint32_t> hidx, hgen;  // open-addressing table: (call, fd, offset) -> run
+  uint32_t gen = 0;
+  explicit Batch(size_t n) : req(n), ptr(n), run(n + 1), next(n), has_pred(n) {
+    size_t cap = 16;
+    while (cap < 2 * n) cap <<= 1;
+    hidx.assign(cap, 0);
+    hgen.assign(cap, 0);
+  }
+};
+
 }  // namespace
 
 struct genesys_ctx {
@@ -322,30 +340,30 @@ int64_t execute_one(genesys_ctx *c, Request &r, Counters &k) {
 // call.  Contiguous buffers become one pread/pwrite, others one
 // preadv/pwritev.  Each request then receives the part of the merged result
 // that covers its own range - the value its own call would have returned.
-size_t merge_run(genesys_ctx *c, Request *reqs, size_t i, size_t n, Counters &k) {
-  const uint32_t nr = reqs[i].nr;
-  const int fd = (int)reqs[i].a[0];
+size_t merge_run(genesys_ctx *c, Request *const *reqs, size_t i, size_t n, Counters &k) {
+  const uint32_t nr = reqs[i]->nr;
+  const int fd = (int)reqs[i]->a[0];
   size_t j = i + 1;
   bool contiguous_buf = true;
-  while (j < n && j - i < IOV_MAX && reqs[j].nr == nr && (int)reqs[j].a[0] == fd &&
-         reqs[j].a[3] == reqs[j - 1].a[3] + reqs[j - 1].a[2]) {
-    if (reqs[j].a[1] != reqs[j - 1].a[1] + reqs[j - 1].a[2]) contiguous_buf = false;
+  while (j < n && j - i < IOV_MAX && reqs[j]->nr == nr && (int)reqs[j]->a[0] == fd &&
+         reqs[j]->a[3] == reqs[j - 1]->a[3] + reqs[j - 1]->a[2]) {
+    if (reqs[j]->a[1] != reqs[j - 1]->a[1] + reqs[j - 1]->a[2]) contiguous_buf = false;
     ++j;
   }
   const size_t m = j - i;
-  const uint64_t off = reqs[i].a[3];
+  const uint64_t off = reqs[i]->a[3];
   uint64_t total = 0;
-  for (size_t t = i; t < j; ++t) total += reqs[t].a[2];
+  for (size_t t = i; t < j; ++t) total += reqs[t]->a[2];
   int64_t res;
   bump(k.os_calls, 1);
   const uint64_t e0 = mono_ns();
   if (m == 1 || contiguous_buf) {
-    void *buf = (void *)reqs[i].a[1];
+    void *buf = (void *)reqs[i]->a[1];
     long r = nr == SYS_pread64 ? pread(fd, buf, total, (off_t)off) : pwrite(fd, buf, total, (off_t)off);
     res = sys_ret(r);
   } else {
     iovec iov[IOV_MAX];
-    for (size_t t = 0; t < m; ++t) iov[t] = {(void *)reqs[i + t].a[1], (size_t)reqs[i + t].a[2]};
+    for (size_t t = 0; t < m; ++t) iov[t] = {(void *)reqs[i + t]->a[1], (size_t)reqs[i + t]->a[2]};
     long r = nr == SYS_pread64 ? preadv(fd, iov, (int)m, (off_t)off) : pwritev(fd, iov, (int)m, (off_t)off);
     res = sys_ret(r);
   }
@@ -355,12 +373,12 @@ size_t merge_run(genesys_ctx *c, Request *reqs, size_t i, size_t n, Counters &k)
   if (dt > k.op_max_ns[oi].load(std::memory_order_relaxed)) k.op_max_ns[oi].store(dt, std::memory_order_relaxed);
   uint64_t prefix = 0;
   for (size_t t = i; t < j; ++t) {
-    const uint64_t len = reqs[t].a[2];
+    const uint64_t len = reqs[t]->a[2];
     if (res < 0) {
-      reqs[t].ret = res;
+      reqs[t]->ret = res;
     } else {
       const uint64_t got = (uint64_t)res > prefix ? (uint64_t)res - prefix : 0;
-      reqs[t].ret = (int64_t)std::min<uint64_t>(got, len);
+      reqs[t]->ret = (int64_t)std::min<uint64_t>(got, len);
     }
     prefix += len;
   }
@@ -370,64 +388,86 @@ size_t merge_run(genesys_ctx *c, Request *reqs, size_t i, size_t n, Counters &k)
 
 inline bool is_rw(uint32_t nr) { return nr == SYS_pread64 || nr == SYS_pwrite64; }
 
-void process_batch(genesys_ctx *c, Request *reqs, size_t n, Counters &k) {
+void process_batch(genesys_ctx *c, Batch &b, size_t n, Counters &k) {
   const uint64_t t0 = mono_ns();
+  Request *const req = b.req.data();
+  Request **p = b.ptr.data();
+  for (size_t i = 0; i < n; ++i) p[i] = req + i;
   if (c->cfg.merge && n > 1) {
-    // the requests of a batch are concurrent, so any order is a legal
-    // schedule: put pread/pwrite requests in (call, fd, offset) order so that
-    // neighbours in a file become adjacent and merge.  A batch arrives as
-    // ascending runs (a warp's lanes publish in lane order), so the sort
-    // orders whole runs by their first request and concatenates them when
-    // they do not overlap; otherwise it sorts an index.  Each request is then
-    // moved once.
-    auto before = [](const Request &x, const Request &y) {
-      const bool rx = is_rw(x.nr), ry = is_rw(y.nr);
-      if (rx != ry) return rx;
-      if (!rx) return false;
-      if (x.nr != y.nr) return x.nr < y.nr;
-      if ((int)x.a[0] != (int)y.a[0]) return (int)x.a[0] < (int)y.a[0];
-      return x.a[3] < y.a[3];
+    // The requests of a batch are concurrent, so any order is a legal
+    // schedule.  A batch arrives as runs of requests that already continue
+    // each other in their file (a warp's lanes publish in lane order).  Each
+    // run is chained to the run of the same call and fd that starts where it
+    // ends (a hash table keyed by call, fd and start offset; a run gets at
+    // most one predecessor), and the chains are laid out one after the other,
+    // so that neighbours in a file become adjacent and merge into one Linux
+    // call.  Linear in the batch; the hashing is per run, not per request.
+    auto continues = [](const Request &prev, const Request &r) {
+      return is_rw(r.nr) && r.nr == prev.nr && (int)r.a[0] == (int)prev.a[0] && r.a[3] == prev.a[3] + prev.a[2];
     };
-    thread_local std::vector<uint32_t> run_start, order;
-    thread_local std::vector<Request> sorted;
-    run_start.clear();
-    run_start.push_back(0);
+    uint32_t k = 0;
+    b.run[k++] = 0;
     for (size_t i = 1; i < n; ++i)
-      if (before(reqs[i], reqs[i - 1])) run_start.push_back((uint32_t)i);
-    const size_t runs = run_start.size();
-    if (runs > 1) {
-      run_start.push_back((uint32_t)n);
-      // runs by first request (insertion sort of the run numbers: few runs)
-      order.resize(runs);
-      for (size_t r = 0; r < runs; ++r) {
-        size_t j = r;
-        while (j > 0 && before(reqs[run_start[r]], reqs[run_start[order[j - 1]]])) {
-          order[j] = order[j - 1];
-          --j;
+      if (!continues(req[i - 1], req[i])) b.run[k++] = (uint32_t)i;
+    b.run[k] = (uint32_t)n;
+    if (k > 1) {
+      const uint32_t mask = (uint32_t)b.hidx.size() - 1;
+      if (++b.gen == 0) {
+        std::fill(b.hgen.begin(), b.hgen.end(), 0u);
+        b.gen = 1;
+      }
+      const uint32_t gen = b.gen;
+      auto slot_of = [&](uint32_t nr, int fd, uint64_t off) {
+        const uint64_t z =
+            (off * 0x9E3779B97F4A7C15ull) ^ ((((uint64_t)(uint32_t)fd << 16) | nr) * 0xC2B2AE3D27D4EB4Full);
+        return (uint32_t)(z >> 32) & mask;
+      };
+      auto starts = [&](uint32_t r, uint32_t nr, int fd, uint64_t off) {
+        const Request &q = req[b.run[r]];
+        return q.nr == nr && (int)q.a[0] == fd && q.a[3] == off;
+      };
+      for (uint32_t r = 0; r < k; ++r) {
+        b.next[r] = -1;
+        b.has_pred[r] = 0;
+        const Request &q = req[b.run[r]];
+        if (!is_rw(q.nr)) continue;
+        uint32_t h = slot_of(q.nr, (int)q.a[0], q.a[3]);
+        while (b.hgen[h] == gen && !starts(b.hidx[h], q.nr, (int)q.a[0], q.a[3])) h = (h + 1) & mask;
+        if (b.hgen[h] != gen) {
+          b.hgen[h] = gen;
+          b.hidx[h] = r;
         }
-        order[j] = (uint32_t)r;
       }
-      bool disjoint = true;
-      for (size_t r = 1; r < runs && disjoint; ++r)
-        disjoint = !before(reqs[run_start[order[r]]], reqs[run_start[order[r - 1] + 1] - 1]);
-      sorted.resize(n);
+      for (uint32_t r = 0; r < k; ++r) {
+        const Request &last = req[b.run[r + 1] - 1];
+        if (!is_rw(last.nr) || last.a[2] == 0) continue;
+        const uint64_t end = last.a[3] + last.a[2];
+        uint32_t h = slot_of(last.nr, (int)last.a[0], end);
+        while (b.hgen[h] == gen) {
+          const uint32_t r2 = b.hidx[h];
+          if (starts(r2, last.nr, (int)last.a[0], end)) {
+            if (!b.has_pred[r2] && r2 != r) {
+              b.next[r] = (int32_t)r2;
+              b.has_pred[r2] = 1;
+            }
+            break;
+          }
+          h = (h + 1) & mask;
+        }
+      }
       size_t o = 0;
-      if (disjoint) {
-        for (size_t r = 0; r < runs; ++r)
-          for (uint32_t i = run_start[order[r]]; i < run_start[order[r] + 1]; ++i) sorted[o++] = reqs[i];
-      } else {
-        order.resize(n);
-        for (size_t i = 0; i < n; ++i) order[i] = (uint32_t)i;
-        std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return before(reqs[x], reqs[y]); });
-        for (size_t i = 0; i < n; ++i) sorted[o++] = reqs[order[i]];
-      }
-      std::copy(sorted.begin(), sorted.begin() + n, reqs);
+      for (uint32_t r = 0; r < k; ++r)
+        if (!b.has_pred[r])
+          for (int32_t q = (int32_t)r; q >= 0 && o < n; q = b.next[q])
+            for (uint32_t i = b.run[q]; i < b.run[q + 1] && o < n; ++i) p[o++] = req + i;
+      if (o != n)  // not reachable (offsets grow along a chain), kept as a guard
+        for (size_t i = 0; i < n; ++i) p[i] = req + i;
     }
   }
   for (size_t i = 0; i < n;) {
-    Request &r = reqs[i];
+    Request &r = *p[i];
     if (c->cfg.merge && (r.nr == SYS_pread64 || r.nr == SYS_pwrite64)) {
-      i = merge_run(c, reqs, i, n, k);
+      i = merge_run(c, p, i, n, k);
       continue;
     }
     const uint64_t e0 = mono_ns();
@@ -443,8 +483,8 @@ void process_batch(genesys_ctx *c, Request *reqs, size_t n, Counters &k) {
   }
   uint64_t per_op[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (size_t i = 0; i < n; ++i) {
-    complete(c, reqs[i], k);
-    ++per_op[op_index(reqs[i].nr)];
+    complete(c, req[i], k);
+    ++per_op[op_index(req[i].nr)];
   }
   for (int o = 0; o < 8; ++o)
     if (per_op[o]) bump(k.by_op[o], per_op[o]);
@@ -473,10 +513,11 @@ inline void read_request(genesys_ctx *c, uint32_t s, Request *r) {
 
 // Take up to coalesce_max ready requests from ring `ri` and process them as one
 // batch (Sec. 4.2).  Returns the number processed.
-size_t poll_ring(genesys_ctx *c, uint32_t ri, std::vector<Request> &batch) {
+size_t poll_ring(genesys_ctx *c, uint32_t ri, Batch &b) {
   const uint64_t *ring = c->rings + (size_t)ri * c->ring_cap;
   const uint32_t mask = c->ring_cap - 1;
   uint64_t h = c->head[ri];
+  std::vector<Request> &batch = b.req;
   const size_t maxb = batch.size();
   size_t n = 0;
   uint32_t s;
@@ -502,7 +543,7 @@ size_t poll_ring(genesys_ctx *c, uint32_t ri, std::vector<Request> &batch) {
       }
     }
   }
-  process_batch(c, batch.data(), n, c->counters[ri]);
+  process_batch(c, b, n, c->counters[ri]);
   c->head[ri] = h + n;
   c->retired[ri].store(h + n, std::memory_order_release);
   return n;
@@ -516,7 +557,7 @@ void service_main(genesys_ctx *c, uint32_t ri) {
     pthread_setaffinity_np(pthread_self(), sizeof set, &set);
   }
   if (!c->host_only) cudaSetDevice(c->device);
-  std::vector<Request> batch(std::max<uint32_t>(1, c->cfg.coalesce_max));
+  Batch batch(std::max<uint32_t>(1, c->cfg.coalesce_max));
   uint64_t last_work = mono_ns();
   uint32_t idle_polls = 0;
   while (!c->stop.load(std::memory_order_relaxed)) {
@@ -758,7 +799,7 @@ int genesys_drain(genesys_ctx *c, uint64_t timeout_ns) {
       if ((int32_t)(got - tails[r]) >= 0) break;
       if (c->cfg.flags & GENESYS_INIT_NO_THREADS) {
         std::lock_guard<std::mutex> g(c->svc_mu);
-        std::vector<Request> batch(std::max<uint32_t>(1, c->cfg.coalesce_max));
+        Batch batch(std::max<uint32_t>(1, c->cfg.coalesce_max));
         poll_ring(c, r, batch);
       } else {
         std::this_thread::sleep_for(std::chrono::microseconds(5));
@@ -860,7 +901,7 @@ int genesys_service(genesys_ctx *c, uint64_t timeout_ns) {
   const uint64_t until = mono_ns() + timeout_ns;
   if (c->cfg.flags & GENESYS_INIT_NO_THREADS) {
     std::lock_guard<std::mutex> g(c->svc_mu);
-    std::vector<Request> batch(std::max<uint32_t>(1, c->cfg.coalesce_max));
+    Batch batch(std::max<uint32_t>(1, c->cfg.coalesce_max));
     int total = 0;
     do {
       size_t n = 0;
