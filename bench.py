@@ -147,6 +147,26 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- helpers
+def host_pwrite_peak(fd, buf, nbytes, repeats=3):
+    """GB/s of one host thread writing nbytes from host address buf to fd at
+    offset 0 with pwrite (best of `repeats`)."""
+    import ctypes
+    libc = ctypes.CDLL(None, use_errno=True)
+    libc.pwrite.restype = ctypes.c_ssize_t
+    libc.pwrite.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_long]
+    best = 0.0
+    for _ in range(repeats):
+        t = time.perf_counter()
+        done = 0
+        while done < nbytes:
+            r = libc.pwrite(fd, buf + done, nbytes - done, done)
+            if r <= 0:
+                raise OSError(ctypes.get_errno(), "pwrite")
+            done += r
+        best = max(best, nbytes / (time.perf_counter() - t) / 1e9)
+    return best
+
+
 def host_link_peak(torch):
     """Pinned cudaMemcpy H2D / D2H bandwidth at 256 MiB (best of 6), GB/s."""
     n = 256 << 20
@@ -657,7 +677,8 @@ def run_genesys(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     step_cfg, step_table = tune_step(args, local, rank) if args.autotune else (
-        {"service_threads": args.service_threads, "coalesce_max": 64, "poll_max_ns": 2048}, [])
+        {"service_threads": args.service_threads, "coalesce_max": args.coalesce_max, "poll_max_ns": args.poll_max_ns},
+        [])
     rig = Rig(args, local, rank, service_threads=step_cfg["service_threads"], coalesce_max=step_cfg["coalesce_max"],
               poll_max_ns=step_cfg["poll_max_ns"])
     G, ctx, dev = rig.G, rig.ctx, rig.dev
@@ -745,6 +766,18 @@ def run_genesys(args):
                         "unit": "calls/s", "frac": round(plain["syscalls_per_s"] / ceiling, 4),
                         "peak_source": "genesys_service_probe: the same 2^20 64-byte pwrites published by a host "
                                        "thread, same service threads and batch size, best of 3 (measured)"}
+    # Coarse-grain pwrites move 64 bytes per thread through one merged Linux
+    # call per group: their bound is the host's write bandwidth into the file
+    # (one tmpfs inode, writers serialised), measured here with the same
+    # buffer and file by one host thread.
+    host_write = host_pwrite_peak(rig.fds[n_probe], rig.c2_stage, n_probe * 64)
+    coarse = sweep[combo_key("wg1024", True, False)]
+    coarse_gbs = n_probe * 64 / (coarse["ms"] * 1e-3) / 1e9
+    coarse_roofline = {"bound": "host_file_write", "kernel": "c2_pwrite_kernel<work-group,relaxed,blocking>",
+                       "threads": n_probe, "group": 1024, "achieved": round(coarse_gbs, 3),
+                       "peak": round(host_write, 3), "unit": "GB/s", "frac": round(coarse_gbs / host_write, 4),
+                       "peak_source": "one host thread pwrite of the same 64 MiB from the same pinned buffer to the "
+                                      "same tmpfs file, best of 3 (measured)"}
     link = host_link_peak(torch)
     extras = profile_extras(args, rig, local, rank, link) if args.extras else {}
     # dominant kernel of the timed region and its host-link roofline
@@ -772,7 +805,7 @@ def run_genesys(args):
                 "peak_source": "pinned cudaMemcpy 256 MiB in this run (of measured)",
                 "alg_bytes_per_launch": int(alg_bytes), "avg_launch_ms": round(avg_ms, 4),
                 "share_of_timed_device_time": round(tot[dom] / sum(tot.values()), 4),
-                "service": service_roofline}
+                "service": service_roofline, "coarse": coarse_roofline}
 
     cpu = cpu_baseline_sample(budget_s=20.0) if rank == 0 and args.extras else None
 
