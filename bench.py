@@ -18,6 +18,7 @@ step's calls are all complete inside the timed region).
     python bench.py --only c1:batched:1073741824
     python bench.py --only c3:batched
     python bench.py --only c4          # key-value service rate sweep (+ oracle server)
+    python bench.py --only c5          # the served mixed trace
     python bench.py --only fig10       # echo bandwidth versus packet size
 
 --impl reference times the CPU oracle (a sequential C program issuing the
@@ -342,9 +343,9 @@ def run_only(args):
     rank, local, _ = dist_env()
     torch.cuda.set_device(local)
     kind, _, rest = args.only.partition(":")
-    if kind in ("c4", "fig10"):
+    if kind in ("c4", "c5", "fig10"):
         import paper_1705_06965_b300 as G
-        res = serve_c4(G, local, rank) if kind == "c4" else study_fig10(G, local, rank)
+        res = {"c4": serve_c4, "c5": serve_c5, "fig10": study_fig10}[kind](G, local, rank)
         print(json.dumps({"only": args.only, kind: res}), flush=True)
         return
     rig = Rig(args, local, rank, need_scan=kind == "c1" and rest.split(":")[-1] != str(C1_BYTES),

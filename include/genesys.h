@@ -290,7 +290,8 @@ int genesys_c3_wordcount_noalloc(genesys_ctx *ctx, const int32_t *fds, const uin
  * The server admits requests in arrival order once they have arrived
  * (arrival_ns after the call starts, if honor_arrivals) and a launch slot,
  * syscall slots, staging bytes and HBM bytes are free; launches them on
- * n_streams streams (as relaunched single-kernel CUDA graphs if use_graphs);
+ * n_streams streams (launch slot i on stream i mod n_streams; as relaunched
+ * single-kernel CUDA graphs if use_graphs);
  * retires them when their completion event fires.  Outputs (host arrays):
  * results[n_req * 8] (negative errno on failure), latency_ns[n_req]
  * (retirement - arrival); *stats if non-NULL. */

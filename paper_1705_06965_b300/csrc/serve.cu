@@ -118,22 +118,31 @@ __global__ void __launch_bounds__(1024) c5_request_kernel(genesys_dev g, const g
                                                                    op.off + p0);
         if (r > (int64_t)plen) r = (int64_t)plen;
         uint8_t *dst = region + p0;
+        // 16-byte loads, eight in flight per thread: the bytes cross the host
+        // link, so a thread's loads must overlap to cover its latency
         if (pread_to_hbm && r > 0) {
           const uint4 *src = reinterpret_cast<const uint4 *>(st_part);
           uint4 *to = reinterpret_cast<uint4 *>(dst);
+#pragma unroll 8
           for (uint64_t i = threadIdx.x; i < ((uint64_t)r + 15) / 16; i += blockDim.x) to[i] = src[i];
           __syncthreads();
         }
         uint64_t s = 0;
         if (r > 0) {
-          const uint64_t nfull = (uint64_t)r >> 3;
-          const uint64_t *w = reinterpret_cast<const uint64_t *>(dst);
-          for (uint64_t i = threadIdx.x; i < nfull; i += blockDim.x) s += cs_term(w[i], (p0 >> 3) + i);
-          if ((r & 7) && threadIdx.x == 0) {
-            uint64_t last = 0;
-            for (uint64_t q = 0; q < ((uint64_t)r & 7); ++q) last |= (uint64_t)dst[(nfull << 3) + q] << (8 * q);
-            s += cs_term(last, (p0 >> 3) + nfull);
+          const uint64_t n16 = (uint64_t)r >> 4;
+          const uint4 *w4 = reinterpret_cast<const uint4 *>(dst);
+#pragma unroll 8
+          for (uint64_t i = threadIdx.x; i < n16; i += blockDim.x) {
+            const uint4 v = w4[i];
+            s += cs_term((uint64_t)v.x | ((uint64_t)v.y << 32), (p0 >> 3) + 2 * i) +
+                 cs_term((uint64_t)v.z | ((uint64_t)v.w << 32), (p0 >> 3) + 2 * i + 1);
           }
+          if (threadIdx.x == 0)  // the last 0-15 bytes: whole words, then a zero-padded one
+            for (uint64_t wd = 2 * n16; wd * 8 < (uint64_t)r; ++wd) {
+              uint64_t val = 0;
+              for (uint64_t q = 0; q < 8 && wd * 8 + q < (uint64_t)r; ++q) val |= (uint64_t)dst[wd * 8 + q] << (8 * q);
+              s += cs_term(val, (p0 >> 3) + wd);
+            }
         }
         s = block_sum(s);
         if (threadIdx.x == 0) {
@@ -181,7 +190,7 @@ __global__ void __launch_bounds__(1024) c5_request_kernel(genesys_dev g, const g
       const uint64_t first = (uint64_t)b * blockDim.x + threadIdx.x;
       for (uint64_t i = first; i < pairs; i += stride) m[i] = make_ulonglong2(sm_at(op.seed, 2 * i), sm_at(op.seed, 2 * i + 1));
       uint64_t s = 0;
-#pragma unroll 4
+#pragma unroll 8
       for (uint64_t i = first; i < pairs; i += stride) {
         const ulonglong2 v = __ldcv(m + i);
         s += cs_term(v.x, 2 * i) + cs_term(v.y, 2 * i + 1);
@@ -277,7 +286,7 @@ extern "C" int genesys_serve_config_default(genesys_serve_config *cfg) {
   if (!cfg) return set_err(GENESYS_EINVAL, "cfg is NULL");
   memset(cfg, 0, sizeof *cfg);
   cfg->max_inflight = 64;
-  cfg->n_streams = 8;
+  cfg->n_streams = 64;
   cfg->staging_budget = 64ull << 20;
   cfg->hbm_budget = 64ull << 20;
   cfg->slot_budget = 16384;
@@ -445,7 +454,6 @@ extern "C" int genesys_c5_serve(genesys_ctx *c, const genesys_c5_request *reqs, 
     return 0;
   };
 
-  uint32_t stream_rr = 0;
   const uint64_t deadline = t0 + cfg.timeout_ns;
   while (retired < n_req && !err) {
     bool progress = false;
@@ -488,7 +496,9 @@ extern "C" int genesys_c5_serve(genesys_ctx *c, const genesys_c5_request *reqs, 
       L.need = nd;
       L.st_off = so;
       L.hbm_off = ho;
-      L.stream = (int)(stream_rr++ % cfg.n_streams);
+      // launch slot si owns stream si mod n_streams: with as many streams as
+      // launch slots a request never queues behind another on its stream
+      L.stream = (int)(si % cfg.n_streams);
       slots_free -= nd.slots;
       admitted_wait_ns += now - arrival_abs[next];
       if (launch(si, (uint32_t)next) != 0) { err = GENESYS_ECUDA; break; }
