@@ -560,20 +560,28 @@ def serve_c5(G, local, rank):
     return out
 
 
+def _kv_requests_at(rate, n_max):
+    """Requests offered at one rate: 1.25 s of traffic, at least 200k and at
+    most the trace's length."""
+    return int(min(n_max, max(200_000, rate * 1.25)))
+
+
 def _kv_point(tr, reqs, off, rate, run_server, port):
-    """Offer the trace at `rate` requests/s to a server started by
-    run_server(port); achieved rate and send-to-reply latency."""
+    """Offer the first requests of the trace (_kv_requests_at) at `rate`
+    requests/s to a server started by run_server(port); achieved rate and
+    send-to-reply latency."""
     import numpy as np
     import paper_1705_06965_b300 as G
-    arr = (tr.arrival_ns.astype(np.float64) * (tr.params["rate_per_s"] / rate)).astype(np.uint64)
+    n = _kv_requests_at(rate, len(tr))
+    arr = (tr.arrival_ns[:n].astype(np.float64) * (tr.params["rate_per_s"] / rate)).astype(np.uint64)
     stop = run_server(port)
     try:
-        reps, lat, st = G.kv_client(reqs, off, arr, port, 32, timeout_ns=10_000_000_000)
+        reps, lat, st = G.kv_client(reqs[:int(off[n])], off[:n + 1], arr, port, 32, timeout_ns=10_000_000_000)
     finally:
         served = stop()
     got = lat[lat > 0]
     achieved = st["received"] / (st["span_ns"] * 1e-9) if st["span_ns"] else 0.0
-    return {"received": st["received"], "served": served, "achieved_req_per_s": round(achieved, 1),
+    return {"requests": n, "received": st["received"], "served": served, "achieved_req_per_s": round(achieved, 1),
             "p50_us": round(float(np.percentile(got, 50)) / 1e3, 2) if len(got) else None,
             "p99_us": round(float(np.percentile(got, 99)) / 1e3, 2) if len(got) else None,
             "max_send_late_us": round(st["max_send_late_ns"] / 1e3, 1)}
@@ -587,21 +595,23 @@ def _kv_sweep(tr, reqs, off, run_server, port, rates):
         pt = _kv_point(tr, reqs, off, rate, run_server, port)
         out[str(int(rate))] = pt
         port += 40
-        if pt["received"] < len(tr) or pt["achieved_req_per_s"] < 0.9 * rate:
+        if pt["received"] < pt["requests"] or pt["achieved_req_per_s"] < 0.9 * rate:
             break
     return out
 
 
-def serve_c4(G, local, rank, rates=tuple(50_000.0 * 2 ** i for i in range(7)), n_req=200_000):
-    """C4: 1M-key table in HBM, 200k requests (Zipf 0.99, 90% GET) per offered
-    rate, rates 50k/s doubling to saturation; achieved requests/s and
-    send-to-reply latency.  The oracle's single-thread CPU server is offered
-    the same rates (its own saturation point is the CPU baseline)."""
+def serve_c4(G, local, rank, rates=tuple(50_000.0 * 2 ** i for i in range(7)), n_req=1_000_000):
+    """C4: 1M-key table in HBM, Zipf 0.99 keys, 90% GET; offered rates 50k/s
+    doubling to saturation, 1.25 s of requests per rate (200k to 1M);
+    achieved requests/s and send-to-reply latency.  The oracle's single-thread
+    CPU server is offered the same rates (its own saturation point is the CPU
+    baseline)."""
     import workloads
     p = dict(workloads.C4_FULL, n_requests=n_req)
     tr = workloads.kv_trace(p)
     reqs, off = workloads.kv_request_bytes(tr)
-    out = {"keys": len(tr.keys), "requests_per_rate": n_req, "sockets": 32}
+    out = {"keys": len(tr.keys), "requests_per_rate": {str(int(r)): _kv_requests_at(r, n_req) for r in rates},
+           "sockets": 32}
     with G.Context(device=local, service_threads=8, staging_bytes=64 << 20) as ctx:
         def gpu_server(port):
             srv = G.KVServer(ctx, tr.keys, tr.vlen0, tr.vseed0, n_sockets=32, batch=64, port_base=port)

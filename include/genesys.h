@@ -368,9 +368,11 @@ int genesys_kv_stop(genesys_kv_server *srv, uint64_t timeout_ns, uint64_t *serve
 /* Current value of key k (copied to out, GENESYS_KV_VALUE_MAX bytes room);
  * returns its length. */
 int genesys_kv_value(genesys_kv_server *srv, uint32_t k, uint8_t *out);
-/* Open-loop UDP load generator on host threads: request j (reqs + req_off[j],
- * req_off[n] = end) is sent arrival_ns[j] after start to the socket its key
- * maps to; replies are matched by seq into replies[seq * (8 + VALUE_MAX)],
+/* Open-loop UDP load generator on up to 4 host threads, each with its own
+ * socket: request j (reqs + req_off[j], req_off[n] = end) is sent
+ * arrival_ns[j] after start to the socket its key maps to, by the thread that
+ * owns that socket (so one key's requests leave in order), and its reply comes
+ * back to that thread; replies are matched by seq into replies[seq * (8 + VALUE_MAX)],
  * reply_len[seq], latency_ns[seq] (send to receive).  Then sends STOP to every
  * socket.  stats[6]: received, duplicates, malformed, send errors, largest
  * send lateness (ns), first send to last reply (ns).  GENESYS_ETIMEDOUT if

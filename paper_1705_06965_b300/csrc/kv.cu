@@ -412,116 +412,139 @@ extern "C" int genesys_kv_value(genesys_kv_server *s, uint32_t k, uint8_t *out) 
 }
 
 // ---------------------------------------------------------------- client
-// Open-loop load generator on host threads: a sender that sends request j at
-// its arrival time to port_base + (first four key bytes mod n_sockets), and a
-// receiver that matches replies to requests by sequence number.
+// Open-loop load generator on host threads.  Thread w owns the server
+// sockets s with s % n_threads == w and its own client socket: it sends its
+// requests (those whose key maps to one of its sockets) in sequence order at
+// their arrival times, batching every request that is due into one sendmmsg,
+// and receives their replies on its socket (the server answers the sender),
+// matching them by sequence number.  Requests of one key therefore leave in
+// sequence order from one thread, and every reply is handled by the thread
+// that sent its request.
+namespace {
+
+struct KvClientTally {
+  uint64_t received = 0, dup = 0, bad = 0, send_err = 0, late_max = 0;
+  bool timed_out = false;
+};
+
+void kv_client_thread(int fd, const std::vector<uint64_t> &mine, const uint8_t *reqs, const uint64_t *req_off,
+                      uint64_t n, const uint64_t *arrival_ns, uint64_t t0, uint16_t port_base, uint32_t n_sockets,
+                      uint64_t deadline, uint8_t *replies, uint32_t *reply_len, uint64_t *latency_ns,
+                      uint64_t *t_send, KvClientTally *out) {
+  KvClientTally T;
+  constexpr int kB = 64;
+  std::vector<mmsghdr> sh(kB), rh(kB);
+  std::vector<iovec> siov(kB), riov(kB);
+  std::vector<sockaddr_in> to(kB);
+  std::vector<uint8_t> rb((size_t)kB * kRep);
+  size_t i = 0;  // next request of `mine` to send
+  uint64_t pending = mine.size();
+  while (pending > 0) {
+    // replies first: they free the server's buffers
+    for (int q = 0; q < kB; ++q) {
+      riov[q] = {rb.data() + (size_t)q * kRep, kRep};
+      memset(&rh[q], 0, sizeof(mmsghdr));
+      rh[q].msg_hdr.msg_iov = &riov[q];
+      rh[q].msg_hdr.msg_iovlen = 1;
+    }
+    const int got = recvmmsg(fd, rh.data(), kB, MSG_DONTWAIT, nullptr);
+    uint64_t now = mono_ns();
+    for (int q = 0; q < got; ++q) {
+      const uint8_t *r = rb.data() + (size_t)q * kRep;
+      const uint32_t len = rh[q].msg_len;
+      uint32_t seq = ~0u;
+      if (len >= 8) memcpy(&seq, r + 4, 4);
+      if (len < 8 || seq >= n || t_send[seq] == 0) { ++T.bad; continue; }
+      if (reply_len[seq]) { ++T.dup; continue; }
+      memcpy(replies + (size_t)seq * kRep, r, len);
+      reply_len[seq] = len;
+      latency_ns[seq] = now - t_send[seq];
+      ++T.received;
+      --pending;
+    }
+    // then every request that is due
+    int m = 0;
+    while (m < kB && i + m < mine.size() && t0 + arrival_ns[mine[i + m]] <= now) {
+      const uint64_t j = mine[i + m];
+      const uint8_t *q = reqs + req_off[j];
+      uint32_t k0;
+      memcpy(&k0, q + 8, 4);
+      to[m] = sockaddr_in{};
+      to[m].sin_family = AF_INET;
+      to[m].sin_port = htons((uint16_t)(port_base + k0 % n_sockets));
+      to[m].sin_addr.s_addr = htonl(INADDR_LOOPBACK);
+      siov[m] = {(void *)q, (size_t)(req_off[j + 1] - req_off[j])};
+      memset(&sh[m], 0, sizeof(mmsghdr));
+      sh[m].msg_hdr.msg_name = &to[m];
+      sh[m].msg_hdr.msg_namelen = sizeof(sockaddr_in);
+      sh[m].msg_hdr.msg_iov = &siov[m];
+      sh[m].msg_hdr.msg_iovlen = 1;
+      T.late_max = std::max(T.late_max, now - (t0 + arrival_ns[j]));
+      t_send[j] = now;
+      ++m;
+    }
+    int sent = 0;
+    while (sent < m) {
+      const int r = sendmmsg(fd, sh.data() + sent, m - sent, 0);
+      if (r <= 0) {
+        T.send_err += m - sent;
+        pending -= m - sent;
+        break;
+      }
+      sent += r;
+    }
+    i += m;
+    if (got <= 0 && m == 0) {
+      if (now > deadline) { T.timed_out = true; break; }
+      __builtin_ia32_pause();
+    }
+  }
+  *out = T;
+}
+
+}  // namespace
+
 extern "C" int genesys_kv_client(const uint8_t *reqs, const uint64_t *req_off, uint64_t n, const uint64_t *arrival_ns,
                                  uint16_t port_base, uint32_t n_sockets, uint64_t timeout_ns, uint8_t *replies,
                                  uint32_t *reply_len, uint64_t *latency_ns, uint64_t *stats) {
   if (!reqs || !req_off || !arrival_ns || !replies || !reply_len || !latency_ns || n_sockets == 0)
     return set_err(GENESYS_EINVAL, "NULL argument");
-  int fd = socket(AF_INET, SOCK_DGRAM, 0);
-  if (fd < 0) return set_err(GENESYS_EINVAL, "socket failed");
-  int buf = 64 << 20;
-  setsockopt(fd, SOL_SOCKET, SO_RCVBUF, &buf, sizeof buf);
-  setsockopt(fd, SOL_SOCKET, SO_SNDBUF, &buf, sizeof buf);
-  sockaddr_in me{};
-  me.sin_family = AF_INET;
-  me.sin_addr.s_addr = htonl(INADDR_LOOPBACK);
-  if (bind(fd, (sockaddr *)&me, sizeof me) != 0) { close(fd); return set_err(GENESYS_EINVAL, "bind failed"); }
+  const uint32_t n_threads = std::min<uint32_t>(n_sockets, 4);
+  std::vector<int> fds;
+  for (uint32_t w = 0; w < n_threads; ++w) {
+    int fd = socket(AF_INET, SOCK_DGRAM, 0);
+    if (fd < 0) break;
+    int want = 64 << 20;
+    if (setsockopt(fd, SOL_SOCKET, SO_RCVBUFFORCE, &want, sizeof want) != 0)
+      setsockopt(fd, SOL_SOCKET, SO_RCVBUF, &want, sizeof want);
+    if (setsockopt(fd, SOL_SOCKET, SO_SNDBUFFORCE, &want, sizeof want) != 0)
+      setsockopt(fd, SOL_SOCKET, SO_SNDBUF, &want, sizeof want);
+    sockaddr_in me{};
+    me.sin_family = AF_INET;
+    me.sin_addr.s_addr = htonl(INADDR_LOOPBACK);
+    if (bind(fd, (sockaddr *)&me, sizeof me) != 0) { close(fd); break; }
+    fds.push_back(fd);
+  }
+  if (fds.size() != n_threads) {
+    for (int fd : fds) close(fd);
+    return set_err(GENESYS_EINVAL, "client socket or bind failed");
+  }
   std::vector<uint64_t> t_send(n, 0);
   memset(reply_len, 0, sizeof(uint32_t) * n);
-  std::atomic<uint64_t> received{0};
-  // senders: thread w owns the sockets s with s % n_senders == w, sends its
-  // requests in sequence order, and batches every request that is due into
-  // one sendmmsg
-  const uint32_t n_senders = std::min<uint32_t>(n_sockets, 4);
-  std::vector<std::vector<uint64_t>> owned(n_senders);
+  std::vector<std::vector<uint64_t>> owned(n_threads);
   for (uint64_t j = 0; j < n; ++j) {
     uint32_t k0;
     memcpy(&k0, reqs + req_off[j] + 8, 4);
-    owned[(k0 % n_sockets) % n_senders].push_back(j);
+    owned[(k0 % n_sockets) % n_threads].push_back(j);
   }
-  std::vector<uint64_t> send_err(n_senders, 0), late_max(n_senders, 0);
-  std::vector<std::thread> senders;
+  std::vector<KvClientTally> tally(n_threads);
   const uint64_t t0 = mono_ns() + 2000000;  // start in 2 ms, once the threads run
-  for (uint32_t w = 0; w < n_senders; ++w) {
-    senders.emplace_back([&, w] {
-      const std::vector<uint64_t> &mine = owned[w];
-      constexpr int kB = 64;
-      std::vector<mmsghdr> hdr(kB);
-      std::vector<iovec> iov(kB);
-      std::vector<sockaddr_in> to(kB);
-      size_t i = 0;
-      while (i < mine.size()) {
-        const uint64_t at = t0 + arrival_ns[mine[i]];
-        uint64_t now = mono_ns();
-        if (now < at) { __builtin_ia32_pause(); continue; }
-        int m = 0;
-        while (m < kB && i + m < mine.size() && t0 + arrival_ns[mine[i + m]] <= now) {
-          const uint64_t j = mine[i + m];
-          const uint8_t *q = reqs + req_off[j];
-          uint32_t k0;
-          memcpy(&k0, q + 8, 4);
-          to[m] = sockaddr_in{};
-          to[m].sin_family = AF_INET;
-          to[m].sin_port = htons((uint16_t)(port_base + k0 % n_sockets));
-          to[m].sin_addr.s_addr = htonl(INADDR_LOOPBACK);
-          iov[m] = {(void *)q, (size_t)(req_off[j + 1] - req_off[j])};
-          memset(&hdr[m], 0, sizeof(mmsghdr));
-          hdr[m].msg_hdr.msg_name = &to[m];
-          hdr[m].msg_hdr.msg_namelen = sizeof(sockaddr_in);
-          hdr[m].msg_hdr.msg_iov = &iov[m];
-          hdr[m].msg_hdr.msg_iovlen = 1;
-          late_max[w] = std::max(late_max[w], now - (t0 + arrival_ns[j]));
-          t_send[j] = now;
-          ++m;
-        }
-        int sent = 0;
-        while (sent < m) {
-          const int r = sendmmsg(fd, hdr.data() + sent, m - sent, 0);
-          if (r <= 0) { send_err[w] += m - sent; break; }
-          sent += r;
-        }
-        i += m;
-      }
-    });
-  }
   const uint64_t deadline = t0 + (n ? arrival_ns[n - 1] : 0) + timeout_ns;
-  std::vector<mmsghdr> hdr(64);
-  std::vector<iovec> iov(64);
-  std::vector<uint8_t> rb(64 * (size_t)kRep);
-  int rc = 0;
-  uint64_t dup = 0, bad = 0;
-  while (received.load() < n) {
-    for (int i = 0; i < 64; ++i) {
-      iov[i] = {rb.data() + (size_t)i * kRep, kRep};
-      memset(&hdr[i], 0, sizeof(mmsghdr));
-      hdr[i].msg_hdr.msg_iov = &iov[i];
-      hdr[i].msg_hdr.msg_iovlen = 1;
-    }
-    const int m = recvmmsg(fd, hdr.data(), 64, MSG_DONTWAIT, nullptr);
-    const uint64_t now = mono_ns();
-    if (m <= 0) {
-      if (now > deadline) { rc = set_err(GENESYS_ETIMEDOUT, "kv client: replies missing at the deadline"); break; }
-      __builtin_ia32_pause();
-      continue;
-    }
-    for (int i = 0; i < m; ++i) {
-      const uint8_t *r = rb.data() + (size_t)i * kRep;
-      const uint32_t len = hdr[i].msg_len;
-      if (len < 8) { ++bad; continue; }
-      uint32_t seq;
-      memcpy(&seq, r + 4, 4);
-      if (seq >= n) { ++bad; continue; }
-      if (reply_len[seq]) { ++dup; continue; }
-      memcpy(replies + (size_t)seq * kRep, r, len);
-      reply_len[seq] = len;
-      latency_ns[seq] = now - t_send[seq];
-      received.fetch_add(1);
-    }
-  }
-  for (auto &t : senders) t.join();
+  std::vector<std::thread> th;
+  for (uint32_t w = 0; w < n_threads; ++w)
+    th.emplace_back(kv_client_thread, fds[w], std::cref(owned[w]), reqs, req_off, n, arrival_ns, t0, port_base,
+                    n_sockets, deadline, replies, reply_len, latency_ns, t_send.data(), &tally[w]);
+  for (auto &t : th) t.join();
   // STOP to every socket (no reply)
   for (uint32_t w = 0; w < n_sockets; ++w) {
     uint8_t stop[24] = {GENESYS_KV_STOP};
@@ -529,17 +552,24 @@ extern "C" int genesys_kv_client(const uint8_t *reqs, const uint64_t *req_off, u
     to.sin_family = AF_INET;
     to.sin_port = htons((uint16_t)(port_base + w));
     to.sin_addr.s_addr = htonl(INADDR_LOOPBACK);
-    sendto(fd, stop, sizeof stop, 0, (sockaddr *)&to, sizeof to);
+    sendto(fds[0], stop, sizeof stop, 0, (sockaddr *)&to, sizeof to);
   }
-  close(fd);
+  for (int fd : fds) close(fd);
+  KvClientTally S;
+  for (auto &T : tally) {
+    S.received += T.received;
+    S.dup += T.dup;
+    S.bad += T.bad;
+    S.send_err += T.send_err;
+    S.late_max = std::max(S.late_max, T.late_max);
+    S.timed_out |= T.timed_out;
+  }
   if (stats) {
-    stats[0] = received.load();
-    stats[1] = dup;
-    stats[2] = bad;
-    uint64_t se = 0, lm = 0;
-    for (uint32_t w = 0; w < n_senders; ++w) { se += send_err[w]; lm = std::max(lm, late_max[w]); }
-    stats[3] = se;
-    stats[4] = lm;
+    stats[0] = S.received;
+    stats[1] = S.dup;
+    stats[2] = S.bad;
+    stats[3] = S.send_err;
+    stats[4] = S.late_max;
     uint64_t first = ~0ull, last = 0;
     for (uint64_t j = 0; j < n; ++j) {
       if (!reply_len[j]) continue;
@@ -548,5 +578,6 @@ extern "C" int genesys_kv_client(const uint8_t *reqs, const uint64_t *req_off, u
     }
     stats[5] = last > first ? last - first : 0;  // first send to last reply
   }
-  return rc;
+  if (S.timed_out) return set_err(GENESYS_ETIMEDOUT, "kv client: replies missing at the deadline");
+  return 0;
 }
