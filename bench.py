@@ -227,7 +227,7 @@ class Rig:
     """Context, files and buffers of the GPU arm."""
 
     def __init__(self, args, local, rank, need_scan=True, service_threads=None, coalesce_max=64, need_c3=True,
-                 poll_max_ns=2048):
+                 poll_max_ns=2048, n_slots=0):
         import torch
         import paper_1705_06965_b300 as G
         import workloads
@@ -241,6 +241,7 @@ class Rig:
         self.c1_stage_bytes = max(2 * C1_GROUPS * C1_CHUNK, 2 * SCAN_GROUPS * SCAN_CHUNK if need_scan else 0)
         self.c3_stage_bytes = C3_CTAS * (C3_CHUNK + 64) * 2 if need_c3 else 0
         self.ctx = G.Context(device=local, service_threads=st_threads, coalesce_max=coalesce_max, poll_max_ns=poll_max_ns,
+                             n_slots=n_slots,
                              staging_bytes=max(SIZES) * 64 + self.c1_stage_bytes + self.c3_stage_bytes + (4 << 20),
                              deadline_ns=10_000_000_000)
         self.c2_stage = self.ctx.staging(max(SIZES) * 64)
@@ -316,14 +317,15 @@ def sweep_step(rig, note=None):
 
 def tune_step(args, local, rank):
     """Autotune the context knobs of the timed step (service threads, batch
-    size); cached per machine."""
+    size, slot-area size: 0 = the default of 2048 slots per SM); cached per
+    machine."""
     from paper_1705_06965_b300 import autotune
     tuner = autotune.Autotuner()
     key = tuner.key("bench-step", sizes=len(SIZES), combos=len(COMBOS))
 
     def run(cfg):
         rig = Rig(args, local, rank, need_scan=False, need_c3=False, service_threads=cfg["service_threads"],
-                  coalesce_max=cfg["coalesce_max"], poll_max_ns=cfg["poll_max_ns"])
+                  coalesce_max=cfg["coalesce_max"], poll_max_ns=cfg["poll_max_ns"], n_slots=cfg["n_slots"])
         try:
             sweep_step(rig)
             return rig.timed(lambda: sweep_step(rig)) * 1e-3
@@ -331,7 +333,7 @@ def tune_step(args, local, rank):
             rig.close()
 
     best, table = tuner.tune(key, autotune.grid(service_threads=(1, 2, 4), coalesce_max=(64, 256),
-                                                poll_max_ns=(2048,)), run, repeats=2)
+                                                poll_max_ns=(2048,), n_slots=(0, 32768)), run, repeats=2)
     return best, table
 
 
@@ -406,22 +408,25 @@ def profile_extras(args, rig, local, rank, link):
     from paper_1705_06965_b300 import autotune
     G = rig.G
     out = {}
-    # pread + histogram over 1 GiB
+    # pread + histogram over 1 GiB: each form (work-group plain, work-group
+    # batched, warp) at its own autotuned setting
     best = autotune.tune_scan(local, rig.fd_scan, SCAN_BYTES)
-    with G.Context(device=local, service_threads=best["service_threads"],
-                   staging_bytes=2 * best["groups"] * best["chunk"] + (1 << 20)) as ctx:
-        sb = 2 * best["groups"] * best["chunk"]
-        st = ctx.staging(sb)
-        res = {}
-        for form in (G.FORM_PLAIN, G.FORM_BATCHED):
+    per_form = best.get("by_form") or {str(best["form"]): best}
+    sb = max(c["groups"] * c["chunk"] * (32 if c["form"] == G.FORM_WARP else 2) for c in per_form.values())
+    res = {}
+    names = {G.FORM_PLAIN: "plain", G.FORM_BATCHED: "batched", G.FORM_WARP: "warp"}
+    for f, cfg in sorted(per_form.items()):
+        with G.Context(device=local, service_threads=cfg["service_threads"], staging_bytes=sb + (1 << 20)) as ctx:
+            st = ctx.staging(sb)
             fn = lambda: ctx.c1_histogram(rig.fd_scan, SCAN_BYTES, rig.hist[0].data_ptr(), st, sb,  # noqa: E731
-                                          chunk=best["chunk"], groups=best["groups"], threads=1024, form=form)
+                                          chunk=cfg["chunk"], groups=cfg["groups"], threads=1024, form=cfg["form"])
             fn()
             ms = min(rig.timed(fn) for _ in range(3))
             gbs = SCAN_BYTES / (ms * 1e-3) / 1e9
-            res["plain" if form == G.FORM_PLAIN else "batched"] = {
-                "GB_per_s": round(gbs, 2), "frac_of_host_link_h2d": round(gbs / link["h2d"], 4), "ms": round(ms, 2)}
-        out["pread_scan_1GiB"] = {"autotuned": best, **res}
+            res[names[cfg["form"]]] = {"GB_per_s": round(gbs, 2), "frac_of_host_link_h2d": round(gbs / link["h2d"], 4),
+                                       "ms": round(ms, 2), "chunk": cfg["chunk"], "groups": cfg["groups"],
+                                       "service_threads": cfg["service_threads"]}
+    out["pread_scan_1GiB"] = {"autotuned": {k: v for k, v in best.items() if k != "by_form"}, **res}
     # C3 wordcount over the full corpus
     c = workloads.corpus(workloads.C3_FULL)
     fds = [os.open(p, os.O_RDONLY) for p in c.paths]
@@ -688,10 +693,10 @@ def run_genesys(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     step_cfg, step_table = tune_step(args, local, rank) if args.autotune else (
-        {"service_threads": args.service_threads, "coalesce_max": args.coalesce_max, "poll_max_ns": args.poll_max_ns},
-        [])
+        {"service_threads": args.service_threads, "coalesce_max": args.coalesce_max, "poll_max_ns": args.poll_max_ns,
+         "n_slots": 0}, [])
     rig = Rig(args, local, rank, service_threads=step_cfg["service_threads"], coalesce_max=step_cfg["coalesce_max"],
-              poll_max_ns=step_cfg["poll_max_ns"])
+              poll_max_ns=step_cfg["poll_max_ns"], n_slots=step_cfg.get("n_slots", 0))
     G, ctx, dev = rig.G, rig.ctx, rig.dev
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     kernel_ms = {}
@@ -832,6 +837,7 @@ def run_genesys(args):
                    "threads": SIZES, "combinations": len(COMBOS), "kernels_per_step": len(SIZES) * len(COMBOS) + 2,
                    "syscalls_per_step": calls_step, "service_threads": step_cfg["service_threads"],
                    "coalesce_max": step_cfg["coalesce_max"], "poll_max_ns": step_cfg["poll_max_ns"],
+                   "n_slots": step_cfg.get("n_slots", 0) or "2048 per SM",
                    "l2": "256 MiB device buffer written between timed steps (L2 flush)",
                    "parallelism": f"replicas x{world}"},
         "requests_per_s": round(job_value(world, (sum(SIZES) * len(COMBOS) + c1_calls) * args.steps, tot_ms * 1e-3), 1),

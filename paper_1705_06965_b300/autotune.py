@@ -88,8 +88,10 @@ def _timed(torch, fn) -> float:
 
 def tune_scan(device: int, fd: int, nbytes: int, tuner: Autotuner | None = None, force: bool = False,
               service_threads=(4, 8, 12), chunks=(128 << 10, 256 << 10, 512 << 10, 1 << 20),
-              groups=(148, 296), forms=(0, 1)):
-    """pread + histogram scan: service threads x chunk x groups x form."""
+              groups=(148, 296), forms=(0, 1, 2), warp_chunks=(16 << 10, 64 << 10)):
+    """pread + histogram scan: service threads x chunk x groups x form, where
+    the form sets the invocation granularity (work-group plain or batched,
+    or warp, which reads smaller chunks: `warp_chunks`)."""
     import torch
     import paper_1705_06965_b300 as G
     tuner = tuner or Autotuner()
@@ -99,10 +101,12 @@ def tune_scan(device: int, fd: int, nbytes: int, tuner: Autotuner | None = None,
         return hit
     hist = torch.zeros(256, dtype=torch.int32, device=f"cuda:{device}")
     table_all, best, best_t = [], None, None
+    cands = [c for c in grid(chunk=chunks, groups=groups, form=[f for f in forms if f != 2])]
+    if 2 in forms:
+        cands += grid(chunk=warp_chunks, groups=groups, form=(2,))
+    stage_bytes = max(c["groups"] * c["chunk"] * (32 if c["form"] == 2 else 2) for c in cands)
     for st in service_threads:
-        with G.Context(device=device, service_threads=st,
-                       staging_bytes=2 * max(groups) * max(chunks) + (1 << 20)) as ctx:
-            stage_bytes = 2 * max(groups) * max(chunks)
+        with G.Context(device=device, service_threads=st, staging_bytes=stage_bytes + (1 << 20)) as ctx:
             stage = ctx.staging(stage_bytes)
 
             def run(cfg):
@@ -111,12 +115,19 @@ def tune_scan(device: int, fd: int, nbytes: int, tuner: Autotuner | None = None,
                 fn()
                 return _timed(torch, fn)
 
-            for cfg in grid(chunk=chunks, groups=groups, form=forms):
+            for cfg in cands:
                 t = min(run(cfg) for _ in range(2))
                 c = dict(cfg, service_threads=st)
                 table_all.append((c, t))
                 if best_t is None or t < best_t:
                     best, best_t = c, t
+    # the best setting of each form too, so that callers can compare forms
+    by_form = {}
+    for c, t in table_all:
+        f = str(c["form"])
+        if f not in by_form or t < by_form[f][1]:
+            by_form[f] = (c, t)
+    best = dict(best, by_form={f: c for f, (c, _) in by_form.items()})
     tuner.cache[key] = {"best": best, "table": table_all, "when": time.time()}
     tuner.save()
     return best

@@ -68,6 +68,23 @@ __device__ __forceinline__ void hist_bytes(const uint8_t *buf, uint64_t n, uint3
   for (uint64_t i = (n16 << 4) + threadIdx.x; i < n; i += blockDim.x) atomicAdd(&my[buf[i]], 1u);
 }
 
+// The same for one warp: lanes stride the buffer, four loads in flight each.
+__device__ __forceinline__ void hist_bytes_warp(const uint8_t *buf, uint64_t n, uint32_t *my, uint32_t lane) {
+  const uint4 *v = reinterpret_cast<const uint4 *>(buf);
+  const uint64_t n16 = n >> 4;
+#pragma unroll 4
+  for (uint64_t i = lane; i < n16; i += 32) {
+    const uint4 x = v[i];
+    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+      for (int b = 0; b < 4; ++b) atomicAdd(&my[(w[k] >> (8 * b)) & 0xFFu], 1u);
+    }
+  }
+  for (uint64_t i = (n16 << 4) + lane; i < n; i += 32) atomicAdd(&my[buf[i]], 1u);
+}
+
 __device__ __forceinline__ void hist_flush(uint32_t *sh, uint32_t *hist_out) {
   __syncthreads();
   const uint32_t nw = blockDim.x >> 5;
@@ -94,6 +111,31 @@ __global__ void __launch_bounds__(1024) c1_plain_kernel(genesys_dev g, int fd, u
     const int64_t r = call<GROUP, STRONG, BLOCKING>(g, SYS_pread64, (uint64_t)fd, (uint64_t)buf, len, off);
     if (r <= 0) break;  // r is the same in every thread (broadcast after the call)
     hist_bytes(buf, (uint64_t)r < len ? (uint64_t)r : len, my);
+  }
+  hist_flush(sh, hist_out);
+}
+
+// Warp form: warp grain, strong ordering, blocking.  Every warp of the grid
+// reads on its own: global warp w reads chunks w, w + W, ... (W warps in the
+// grid) into its own staging piece and counts them into its own shared-memory
+// histogram copy, with no block-wide barrier between chunks.
+__global__ void __launch_bounds__(1024) c1_warp_kernel(genesys_dev g, int fd, uint64_t file_bytes, uint32_t chunk,
+                                                       uint8_t *staging, uint32_t *hist_out) {
+  extern __shared__ uint32_t sh[];
+  for (uint32_t i = threadIdx.x; i < (blockDim.x >> 5) * 256; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint32_t *my = sh + wib * 256;
+  const uint64_t n_warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+  uint8_t *buf = staging + gw * chunk;
+  const uint64_t n_chunks = (file_bytes + chunk - 1) / chunk;
+  for (uint64_t c = gw; c < n_chunks; c += n_warps) {  // warp-uniform loop
+    const uint64_t off = c * chunk;
+    const uint64_t len = file_bytes - off < chunk ? file_bytes - off : chunk;
+    const int64_t r = call<WARP, STRONG, BLOCKING>(g, SYS_pread64, (uint64_t)fd, (uint64_t)buf, len, off);
+    if (r <= 0) break;  // r is the same in every lane (broadcast after the call)
+    hist_bytes_warp(buf, (uint64_t)r < len ? (uint64_t)r : len, my, lane);
   }
   hist_flush(sh, hist_out);
 }
@@ -308,7 +350,9 @@ int genesys_c1_histogram(genesys_ctx *c, int fd, uint64_t file_bytes, uint64_t c
   if (chunk == 0 || chunk % 16 || chunk > (1u << 30)) return set_err(GENESYS_EINVAL, "chunk must be a multiple of 16");
   if (groups == 0 || threads < 32 || threads > 1024 || threads % 32) return set_err(GENESYS_EINVAL, "bad launch shape");
   if ((uintptr_t)staging % 16) return set_err(GENESYS_EINVAL, "staging must be 16-byte aligned");
-  const uint64_t need = (uint64_t)groups * chunk * (form == GENESYS_FORM_BATCHED ? 2 : 1);
+  if (form > GENESYS_FORM_WARP) return set_err(GENESYS_EINVAL, "form: GENESYS_FORM_PLAIN, _BATCHED or _WARP");
+  const uint64_t need = (uint64_t)groups * chunk *
+                        (form == GENESYS_FORM_BATCHED ? 2 : form == GENESYS_FORM_WARP ? threads / 32 : 1);
   if (staging_bytes < need) return set_err(GENESYS_EINVAL, "staging too small");
   if (file_bytes == 0) return 0;
   genesys_dev g;
@@ -322,6 +366,8 @@ int genesys_c1_histogram(genesys_ctx *c, int fd, uint64_t file_bytes, uint64_t c
   if (form == GENESYS_FORM_BATCHED)
     return run(c, (const void *)&c1_batched_kernel, groups, threads, smem, args,
                GENESYS_GRAN_GROUP | GENESYS_LAUNCH_RELAXED | GENESYS_LAUNCH_NONBLOCKING, stream);
+  if (form == GENESYS_FORM_WARP)
+    return run(c, (const void *)&c1_warp_kernel, groups, threads, smem, args, GENESYS_GRAN_WARP, stream);
   return run(c, (const void *)&c1_plain_kernel, groups, threads, smem, args, GENESYS_GRAN_GROUP, stream);
 }
 
