@@ -526,8 +526,8 @@ def study_fig7(G, rig, local, rank, sizes=(256 << 10, 1 << 20, 4 << 20, 16 << 20
 
 def serve_c5(G, local, rank):
     """C5: the 10,000-request trace served with continuous admission (up to 64
-    kernels in flight, graph relaunch), and its first 1,000 requests both
-    served and in the plain one-at-a-time form."""
+    kernels in flight, graph relaunch, autotuned call granularity), and its
+    first 1,000 requests both served and in the plain one-at-a-time form."""
     import numpy as np
     import workloads
     tr = workloads.c5_trace(workloads.C5_FULL)
@@ -552,12 +552,19 @@ def serve_c5(G, local, rank):
                              "p99_ms": round(float(np.percentile(lat, 99)) / 1e6, 3),
                              "makespan_s": round(span, 3), "wall_s": round(wall, 3),
                              "max_inflight": st["max_inflight"], "graph_launches": st["graph_launches"]}
+            from paper_1705_06965_b300 import autotune
+            ofd = os.open(os.path.join(d, "tune.bin"), os.O_CREAT | os.O_RDWR, 0o644)
+            try:
+                tuned = autotune.tune_serve(local, ctx, tr, in_fds, ofd)
+            finally:
+                os.close(ofd)
+            out["autotuned"] = tuned
             first = tr.subset(np.arange(1000))
             r_plain, out["plain_first1000"] = run(first, max_inflight=1, use_graphs=0)
-            r_served, out["served_first1000"] = run(first, max_inflight=64)
+            r_served, out["served_first1000"] = run(first, max_inflight=64, **tuned)
             m = np.arange(8)[None, :] < first.n_ops[:, None]
             out["first1000_alone_equals_mix"] = bool(np.array_equal(r_plain[m], r_served[m]))
-            _, out["served_full"] = run(tr, max_inflight=64)
+            _, out["served_full"] = run(tr, max_inflight=64, **tuned)
     finally:
         for fd in in_fds:
             os.close(fd)

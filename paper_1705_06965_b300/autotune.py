@@ -191,3 +191,25 @@ def tune_context(device: int, step: Callable, tuner: Autotuner | None = None, fo
     tuner.cache[key] = {"best": best, "table": table_all, "when": time.time()}
     tuner.save()
     return best
+
+
+def tune_serve(device: int, ctx, trace, in_fds, out_fd: int, tuner: Autotuner | None = None, force: bool = False,
+               min_parts=(4096, 16384, 65536), block_threads=(256, 1024), n_requests: int = 300):
+    """C5 serving: the granularity of the request kernels' pread/pwrite calls
+    (min_part: bytes per work-group call) x threads per block, measured as the
+    makespan of the trace's first n_requests served back to back."""
+    import numpy as np
+    tuner = tuner or Autotuner()
+    key = tuner.key("serve", requests=n_requests, min_parts=len(min_parts), block_threads=len(block_threads))
+    hit = None if force else tuner.lookup(key)
+    if hit:
+        return hit
+    sub = trace.subset(np.arange(min(n_requests, len(trace))))
+
+    def run(cfg):
+        _, _, st = ctx.c5_serve(sub.arrival_ns, sub.threads, sub.n_ops, sub.ops, in_fds, out_fd, honor_arrivals=0,
+                                **cfg)
+        return st["makespan_ns"] * 1e-9
+
+    best, _ = tuner.tune(key, grid(min_part=min_parts, block_threads=block_threads), run, repeats=1, force=True)
+    return best
