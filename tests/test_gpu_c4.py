@@ -60,3 +60,23 @@ def test_c4_replies_bit_exact(G, ctx, n_sockets, batch, rate):
         expect = (workloads.stream_bytes(int(tr.vseed[sets[-1]]), int(tr.vlen[sets[-1]])) if len(sets)
                   else tr.value0(k))
         assert v == expect
+
+
+def test_c4_full_table_replies_bit_exact(G, ctx):
+    """The benchmark's configuration: the 1 M-key table in HBM, 32 sockets,
+    batches of 64, 100 k requests at 200 k/s offered; every reply equals the
+    oracle's replay in client sequence order."""
+    p = dict(workloads.C4_FULL, n_requests=100_000, rate_per_s=200_000.0)
+    tr = workloads.kv_trace(p)
+    want = oracle.c4_replay(tr)
+    reqs, off = workloads.kv_request_bytes(tr)
+    port = _port() + 101
+    srv = G.KVServer(ctx, tr.keys, tr.vlen0, tr.vseed0, n_sockets=32, batch=64, port_base=port)
+    try:
+        reps, lat, st = G.kv_client(reqs, off, tr.arrival_ns, port, 32)
+    finally:
+        served = srv.stop()
+    assert st["rc"] == 0 and st["received"] == len(tr), st
+    bad = [j for j in range(len(tr)) if reps[j] != want[j]]
+    assert not bad, (len(bad), bad[:5])
+    assert served == len(tr)
