@@ -52,6 +52,10 @@ struct C3Queries {
 
 int set_err(int code, const char *msg) { return genesys_internal_error(code, msg); }
 
+// Shared-memory tile of a block: 64 bytes per thread (32 at 1024 threads),
+// within the 48 KiB a launch gets without opting in.
+inline uint32_t c3_tile_bytes(uint32_t threads) { return threads * 16 * (threads > 512 ? 2 : 4); }
+
 __device__ __forceinline__ bool is_sep(uint8_t c) { return c == ' ' || c == '\n'; }
 
 __device__ __forceinline__ uint32_t qhash(uint64_t w0, uint64_t w1, uint32_t len) {
@@ -96,9 +100,70 @@ __device__ void c3_prologue(C3Smem &S, const C3Queries *Q) {
   __syncthreads();
 }
 
+// Separator bits of four bytes (bit i set when byte i is ' ' or '\n'): an
+// exact zero-byte test on x ^ ' ' and x ^ '\n', then the four high bits
+// gathered into the low nibble.
+__device__ __forceinline__ uint32_t sep_bits4(uint32_t x) {
+  const uint32_t t1 = x ^ 0x20202020u, t2 = x ^ 0x0A0A0A0Au;
+  const uint32_t z1 = ~(((t1 & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t1 | 0x7F7F7F7Fu);
+  const uint32_t z2 = ~(((t2 & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t2 | 0x7F7F7F7Fu);
+  const uint32_t m = (z1 | z2) >> 7;        // 0 or 1 in bits 0, 8, 16, 24
+  return (m * 0x01020408u) >> 24;            // bits 0..3
+}
+
+// Count the tokens that start at the 16 positions p0 .. p0 + 15 of an item,
+// whose bytes b[p0 - 1] .. b[p0 + 46] are tile[base] .. tile[base + 47]: three
+// 16-byte shared loads become a 48-bit separator mask (positions at or past
+// `avail`, and b[-1] at the start of a file, count as separators).  Token
+// starts are the non-separators after a separator; a token's length is the
+// distance to the next separator bit, so only tokens of a query's length
+// range are assembled byte by byte and looked up in the query hash table.
+__device__ __noinline__ void c3_window(C3Smem &S, const uint8_t *tile, uint32_t base, uint32_t p0, uint32_t len,
+                                       uint64_t avail, uint64_t off) {
+  uint64_t sep = 0;  // bit j: window byte j (= b[p0 - 1 + j]) is a separator
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    const uint4 x = *reinterpret_cast<const uint4 *>(tile + base + 16 * v);
+    const uint64_t bits = sep_bits4(x.x) | (sep_bits4(x.y) << 4) | (sep_bits4(x.z) << 8) | (sep_bits4(x.w) << 12);
+    sep |= bits << (16 * v);
+  }
+  const uint64_t valid = avail - p0 + 1;  // window bytes before `avail` (>= 2, as p0 < len <= avail)
+  if (valid < 48) sep |= ~0ull << valid;
+  sep |= ~0ull << 48;
+  if (p0 == 0 && off == 0) sep |= 1ull;  // the start of a file
+  // token starts among window bytes 1 .. min(16, len - p0)
+  const uint32_t last = len - p0 < 16 ? len - p0 : 16;
+  uint64_t starts = ~sep & (sep << 1) & (((2ull << last) - 1) & ~1ull);
+  while (starts) {
+    const int j = __ffsll((long long)starts) - 1;
+    starts &= starts - 1;
+    const uint32_t L = (uint32_t)(__ffsll((long long)(sep >> j)) - 1);  // run of non-separators
+    if (L > (uint32_t)kHalo || L < S.minlen) continue;
+    const uint8_t *tok = tile + base + j;
+    uint64_t w0 = 0, w1 = 0;
+    for (uint32_t q = 0; q < L; ++q) {
+      const uint64_t c = tok[q];
+      if (q < 8) w0 |= c << (8 * q); else w1 |= c << (8 * (q - 8));
+    }
+    uint32_t h = qhash(w0, w1, L);
+    for (int probe = 0; probe < kHash; ++probe) {
+      const int qi = S.htab[h];
+      if (qi < 0) break;
+      if (S.qlen[qi] == L && S.qw[qi][0] == w0 && S.qw[qi][1] == w1) {
+        atomicAdd(&S.cnt[qi], 1ull);
+        break;
+      }
+      h = (h + 1) & (kHash - 1);
+    }
+  }
+}
+
 // Count the tokens that start in [0, len) of one item.  b[j] = buf[1 + j]
 // holds file byte off + j for j in [-1, avail); b[-1] is meaningful only when
-// off > 0.  tile: dynamic shared memory of tile_bytes + 48.
+// off > 0.  tile: dynamic shared memory of tile_bytes + 48.  A tile is
+// several 16-byte loads per thread, all in flight together (the bytes cross
+// the host link: one load per round trip would leave the block waiting at the
+// barrier); thread t then owns the 16-position windows t, t + threads, ...
 __device__ void c3_scan(C3Smem &S, uint8_t *tile, uint32_t tile_bytes, const uint8_t *buf, uint64_t buf_cap,
                         uint64_t off, uint32_t len, uint64_t avail) {
   if (avail < len) len = (uint32_t)avail;
@@ -109,33 +174,8 @@ __device__ void c3_scan(C3Smem &S, uint8_t *tile, uint32_t tile_bytes, const uin
         *reinterpret_cast<uint4 *>(tile + i) = *reinterpret_cast<const uint4 *>(buf + t0 + i);
     }
     __syncthreads();
-    const uint32_t base = threadIdx.x * 16;
-    for (uint32_t k = 0; k < 16; ++k) {
-      const uint32_t p = t0 + base + k;  // position within the item
-      if (base + k >= tile_bytes || p >= len) break;
-      const uint32_t si = base + k + 1;  // tile index of b[p]
-      if (is_sep(tile[si])) continue;
-      const bool start = (p == 0) ? (off == 0 || is_sep(tile[si - 1])) : is_sep(tile[si - 1]);
-      if (!start) continue;
-      uint32_t L = 0;
-      while (L <= (uint32_t)kHalo && p + L < avail && !is_sep(tile[si + L])) ++L;
-      if (L > (uint32_t)kHalo || L < S.minlen) continue;
-      uint64_t w0 = 0, w1 = 0;
-      for (uint32_t q = 0; q < L; ++q) {
-        const uint64_t c = tile[si + q];
-        if (q < 8) w0 |= c << (8 * q); else w1 |= c << (8 * (q - 8));
-      }
-      uint32_t h = qhash(w0, w1, L);
-      for (int probe = 0; probe < kHash; ++probe) {
-        const int qi = S.htab[h];
-        if (qi < 0) break;
-        if (S.qlen[qi] == L && S.qw[qi][0] == w0 && S.qw[qi][1] == w1) {
-          atomicAdd(&S.cnt[qi], 1ull);
-          break;
-        }
-        h = (h + 1) & (kHash - 1);
-      }
-    }
+    for (uint32_t base = threadIdx.x * 16; base < tile_bytes && t0 + base < len; base += blockDim.x * 16)
+      c3_window(S, tile, base, t0 + base, len, avail, off);
     __syncthreads();
   }
 }
@@ -167,7 +207,7 @@ __device__ void c3_flush(C3Smem &S, uint32_t nq, unsigned long long *counts) {
 
 // Plain form: each block pops an item, issues a blocking, strongly ordered
 // work-group-grain pread, scans it, repeats.
-__global__ void __launch_bounds__(1024) c3_plain_kernel(genesys_dev g, const C3Item *items, uint32_t n_items,
+__global__ void __launch_bounds__(1024, 1) c3_plain_kernel(genesys_dev g, const C3Item *items, uint32_t n_items,
                                                         uint32_t *head, const C3Queries *Q, uint8_t *staging,
                                                         uint64_t buf_bytes, uint32_t tile_bytes,
                                                         unsigned long long *counts) {
@@ -192,7 +232,7 @@ __global__ void __launch_bounds__(1024) c3_plain_kernel(genesys_dev g, const C3I
 }
 
 // Batched form: double-buffered, relaxed non-blocking preads (tickets).
-__global__ void __launch_bounds__(1024) c3_batched_kernel(genesys_dev g, const C3Item *items, uint32_t n_items,
+__global__ void __launch_bounds__(1024, 1) c3_batched_kernel(genesys_dev g, const C3Item *items, uint32_t n_items,
                                                           uint32_t *head, const C3Queries *Q, uint8_t *staging,
                                                           uint64_t buf_bytes, uint32_t tile_bytes,
                                                           unsigned long long *counts) {
@@ -313,7 +353,7 @@ int genesys_c3_wordcount(genesys_ctx *c, const int32_t *fds, const uint64_t *fil
   const C3Queries *d_q = (const C3Queries *)((uint8_t *)scratch + q_off);
   uint8_t *st = (uint8_t *)staging;
   uint64_t bb = buf_bytes;
-  uint32_t tile_bytes = threads * 16;
+  uint32_t tile_bytes = c3_tile_bytes(threads);
   void *args[] = {&g, &d_items, &n_items, &head, &d_q, &st, &bb, &tile_bytes, &counts_dev};
   const size_t smem = tile_bytes + 48;
   const void *k = form == GENESYS_FORM_BATCHED ? (const void *)&c3_batched_kernel : (const void *)&c3_plain_kernel;
@@ -453,7 +493,7 @@ extern "C" int genesys_c3_wordcount_noalloc(genesys_ctx *c, const int32_t *fds, 
   const C3Queries *d_q = (const C3Queries *)(scratch + kStaticQOff);
   uint8_t *st = (uint8_t *)staging;
   uint64_t bb = buf_bytes;
-  uint32_t tile_bytes = threads * 16;
+  uint32_t tile_bytes = c3_tile_bytes(threads);
   void *args[] = {&g, &d_items, &n, &head, &d_q, &st, &bb, &tile_bytes, &counts_dev};
   const size_t smem = tile_bytes + 48;
   const void *k = form == GENESYS_FORM_BATCHED ? (const void *)&c3_batched_kernel : (const void *)&c3_plain_kernel;
