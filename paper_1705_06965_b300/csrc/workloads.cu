@@ -50,12 +50,13 @@ int run(genesys_ctx *c, const void *kernel, uint32_t grid, uint32_t block, size_
 
 // ------------------------------------------------------------------- C1
 // Byte histogram of `n` bytes at `buf` (host-mapped staging, 16-byte aligned)
-// into the calling warp's shared-memory copy.  16-byte vector loads, one per
-// thread per step, so a block streams the chunk over the host link in as few
-// round trips as its width allows.
+// into the calling warp's shared-memory copy.  16-byte vector loads, up to
+// four in flight per thread, so a block streams the chunk over the host link
+// in few round trips.
 __device__ __forceinline__ void hist_bytes(const uint8_t *buf, uint64_t n, uint32_t *my) {
   const uint4 *v = reinterpret_cast<const uint4 *>(buf);
   const uint64_t n16 = n >> 4;
+#pragma unroll 4
   for (uint64_t i = threadIdx.x; i < n16; i += blockDim.x) {
     const uint4 x = v[i];
     const uint32_t w[4] = {x.x, x.y, x.z, x.w};
@@ -97,7 +98,7 @@ __device__ __forceinline__ void hist_flush(uint32_t *sh, uint32_t *hist_out) {
 
 // Plain form: work-group grain, strong ordering, blocking (the combination
 // the paper's microbenchmarks start from).  Block b reads chunks b, b+G, ...
-__global__ void __launch_bounds__(1024) c1_plain_kernel(genesys_dev g, int fd, uint64_t file_bytes, uint32_t chunk,
+__global__ void __launch_bounds__(1024, 1) c1_plain_kernel(genesys_dev g, int fd, uint64_t file_bytes, uint32_t chunk,
                                                         uint8_t *staging, uint32_t *hist_out) {
   extern __shared__ uint32_t sh[];
   for (uint32_t i = threadIdx.x; i < (blockDim.x >> 5) * 256; i += blockDim.x) sh[i] = 0;
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(1024) c1_plain_kernel(genesys_dev g, int fd, u
 // reads on its own: global warp w reads chunks w, w + W, ... (W warps in the
 // grid) into its own staging piece and counts them into its own shared-memory
 // histogram copy, with no block-wide barrier between chunks.
-__global__ void __launch_bounds__(1024) c1_warp_kernel(genesys_dev g, int fd, uint64_t file_bytes, uint32_t chunk,
+__global__ void __launch_bounds__(1024, 1) c1_warp_kernel(genesys_dev g, int fd, uint64_t file_bytes, uint32_t chunk,
                                                        uint8_t *staging, uint32_t *hist_out) {
   extern __shared__ uint32_t sh[];
   for (uint32_t i = threadIdx.x; i < (blockDim.x >> 5) * 256; i += blockDim.x) sh[i] = 0;
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(1024) c1_warp_kernel(genesys_dev g, int fd, ui
 // Batched form: relaxed, non-blocking preads double-buffered per block - the
 // read of chunk k+1 is in flight while chunk k is scanned (Sec. 4.1: weak
 // ordering with non-blocking prefetching reads).
-__global__ void __launch_bounds__(1024) c1_batched_kernel(genesys_dev g, int fd, uint64_t file_bytes, uint32_t chunk,
+__global__ void __launch_bounds__(1024, 1) c1_batched_kernel(genesys_dev g, int fd, uint64_t file_bytes, uint32_t chunk,
                                                           uint8_t *staging, uint32_t *hist_out) {
   extern __shared__ uint32_t sh[];
   __shared__ int64_t r_s;
