@@ -168,22 +168,40 @@ def host_pwrite_peak(fd, buf, nbytes, repeats=3):
     return best
 
 
-def host_link_peak(torch):
-    """Pinned cudaMemcpy H2D / D2H bandwidth at 256 MiB (best of 6), GB/s."""
-    n = 256 << 20
+def hbm_peak() -> float:
+    """Measured HBM copy bandwidth of this GPU model (GB/s), from the peaks file
+    beside this script, else the nominal 7,700 GB/s.  The scans read HBM only
+    for their histograms and counters: their fraction of it is reported for
+    completeness."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 7700.0
+
+
+def host_link_peak(torch, sizes=(4 << 10, 64 << 10, 1 << 20, 16 << 20, 64 << 20, 256 << 20, 1 << 30)):
+    """Pinned cudaMemcpy sweep, H2D and D2H, best of 6 per size (GB/s); the
+    ceiling is the best at >= 64 MiB.  Returns {"h2d": .., "d2h": .., "sweep":
+    {direction: {bytes: GB/s}}}."""
+    n = max(sizes)
     h = torch.empty(n, dtype=torch.uint8, pin_memory=True)
     d = torch.empty(n, dtype=torch.uint8, device="cuda")
-    out = {}
+    out = {"sweep": {}}
     for name, (dst, src) in {"h2d": (d, h), "d2h": (h, d)}.items():
-        best = 0.0
-        for _ in range(6):
-            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s.record()
-            dst.copy_(src, non_blocking=True)
-            e.record()
-            e.synchronize()
-            best = max(best, n / (s.elapsed_time(e) * 1e-3) / 1e9)
-        out[name] = round(best, 2)
+        row = {}
+        for size in sizes:
+            best = 0.0
+            for _ in range(6):
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.record()
+                dst[:size].copy_(src[:size], non_blocking=True)
+                e.record()
+                e.synchronize()
+                best = max(best, size / (s.elapsed_time(e) * 1e-3) / 1e9)
+            row[str(size)] = round(best, 2)
+        out["sweep"][name] = row
+        out[name] = max(v for k, v in row.items() if int(k) >= 64 << 20)
     del h, d
     return out
 
@@ -424,6 +442,7 @@ def profile_extras(args, rig, local, rank, link):
             ms = min(rig.timed(fn) for _ in range(3))
             gbs = SCAN_BYTES / (ms * 1e-3) / 1e9
             res[names[cfg["form"]]] = {"GB_per_s": round(gbs, 2), "frac_of_host_link_h2d": round(gbs / link["h2d"], 4),
+                                       "frac_of_hbm_peak": round(gbs / hbm_peak(), 5),
                                        "ms": round(ms, 2), "chunk": cfg["chunk"], "groups": cfg["groups"],
                                        "service_threads": cfg["service_threads"]}
     out["pread_scan_1GiB"] = {"autotuned": {k: v for k, v in best.items() if k != "by_form"}, **res}
@@ -448,6 +467,7 @@ def profile_extras(args, rig, local, rank, link):
                 gbs = c.total_bytes / (ms * 1e-3) / 1e9
                 res["plain" if form == G.FORM_PLAIN else "batched"] = {
                     "GB_per_s": round(gbs, 2), "frac_of_host_link_h2d": round(gbs / link["h2d"], 4),
+                    "frac_of_hbm_peak": round(gbs / hbm_peak(), 5),
                     "ms": round(ms, 2), "counts_equal_ground_truth": ok}
             out["wordcount_c3"] = {"autotuned": best, "corpus_bytes": c.total_bytes, **res}
     finally:
@@ -802,6 +822,7 @@ def run_genesys(args):
                        "peak_source": "one host thread pwrite of the same 64 MiB from the same pinned buffer to the "
                                       "same tmpfs file, best of 3 (measured)"}
     link = host_link_peak(torch)
+    link["round_trip_ns"] = G.link_pingpong(local, rounds=20000)  # GPU <-> host flag, the floor of a blocking call
     extras = profile_extras(args, rig, local, rank, link) if args.extras else {}
     # dominant kernel of the timed region and its host-link roofline
     tot = {k: sum(v) for k, v in kernel_ms.items()}
@@ -825,7 +846,7 @@ def run_genesys(args):
     peak = link["d2h"] if dom.startswith("c2") else link["h2d"]
     roofline = {"bound": "host_link", "kernel": dom, "achieved": round(achieved, 3), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 5), "traffic": load_traffic(dom, units),
-                "peak_source": "pinned cudaMemcpy 256 MiB in this run (of measured)",
+                "peak_source": "pinned cudaMemcpy sweep in this run, best at >= 64 MiB (of measured)",
                 "alg_bytes_per_launch": int(alg_bytes), "avg_launch_ms": round(avg_ms, 4),
                 "share_of_timed_device_time": round(tot[dom] / sum(tot.values()), 4),
                 "service": service_roofline, "coarse": coarse_roofline}

@@ -465,6 +465,14 @@ int genesys_visibility_probe(genesys_ctx *ctx, uint64_t n_threads, uint32_t gran
                              uint32_t order_relaxed, uint64_t seed, uint64_t *probe,
                              unsigned long long *violations_dev, void *stream);
 
+/* Host-link round trip (the latency floor of a blocking GPU system call,
+ * Sec. 5: the GPU publishes a request and waits for the CPU's answer): one GPU
+ * thread on `device` stores r to a flag in pinned host-mapped memory and waits
+ * for a host thread to store r to a second flag, r = 1 .. rounds.
+ * *ns_per_round = GPU-timed nanoseconds per round trip.  Every wait, on both
+ * sides, ends after timeout_ns (GENESYS_ETIMEDOUT); no context is needed. */
+int genesys_link_pingpong(int device, uint32_t rounds, uint64_t timeout_ns, uint64_t *ns_per_round);
+
 #ifdef __cplusplus
 }
 #endif

@@ -44,7 +44,7 @@ EXPORTS = [
     "genesys_c3_wordcount", "genesys_c3_wordcount_noalloc", "genesys_serve_config_default", "genesys_c5_serve",
     "genesys_reclaim", "genesys_mmap_reserve", "genesys_kv_start", "genesys_kv_stop", "genesys_kv_value",
     "genesys_kv_client", "genesys_c6_permute", "genesys_gpu_call", "genesys_echo_start", "genesys_echo_stop",
-    "genesys_echo_client", "genesys_service_probe",
+    "genesys_echo_client", "genesys_service_probe", "genesys_link_pingpong",
 ]
 
 
@@ -148,6 +148,7 @@ def lib() -> ctypes.CDLL:
         "genesys_kv_client": (ctypes.c_int, [vp, vp, u64, vp, ctypes.c_uint16, u32, u64, vp, vp, vp, vp]),
         "genesys_c5_serve": (ctypes.c_int, [vp, vp, u32, vp, u32, ctypes.c_int32, ctypes.POINTER(ServeConfig), vp, vp,
                                             ctypes.POINTER(ServeStats)]),
+        "genesys_link_pingpong": (ctypes.c_int, [ctypes.c_int, u32, u64, ctypes.POINTER(u64)]),
         "genesys_service_probe": (ctypes.c_int, [vp, ctypes.c_int, vp, u32, u64, ctypes.POINTER(u64)]),
         "genesys_echo_start": (ctypes.c_int, [vp, u32, u32, u32, u32, u32, ctypes.c_uint16, u64, ctypes.POINTER(vp)]),
         "genesys_echo_stop": (ctypes.c_int, [vp, u64, vp]),
@@ -457,6 +458,14 @@ class EchoServer:
             h, self._h = self._h, None
             _check(lib().genesys_echo_stop(h, timeout_ns, st.ctypes.data), "genesys_echo_stop")
         return {"packets": int(st[0]), "bytes": int(st[1])}
+
+
+def link_pingpong(device: int = 0, rounds: int = 2000, timeout_ns: int = 2_000_000_000) -> float:
+    """Host-link flag round trip between a GPU thread and a host thread
+    (genesys_link_pingpong); returns nanoseconds per round trip."""
+    ns = ctypes.c_uint64()
+    _check(lib().genesys_link_pingpong(device, rounds, timeout_ns, ctypes.byref(ns)), "genesys_link_pingpong")
+    return float(ns.value)
 
 
 def echo_client(port_base: int, n_sockets: int, packet_bytes: int, n_packets: int, window: int = 4,

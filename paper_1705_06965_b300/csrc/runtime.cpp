@@ -117,8 +117,9 @@ struct Batch {
   std::vector<int32_t> next;       // run that continues this one in its file, or -1
   std::vector<uint8_t> has_pred;
   std::vector<uint32_t> hidx, hgen;  // open-addressing table: (call, fd, offset) -> run
+  std::vector<uint32_t> slot_ids;    // slots of the ready ring entries
   uint32_t gen = 0;
-  explicit Batch(size_t n) : req(n), ptr(n), run(n + 1), next(n), has_pred(n) {
+  explicit Batch(size_t n) : req(n), ptr(n), run(n + 1), next(n), has_pred(n), slot_ids(n) {
     size_t cap = 16;
     while (cap < 2 * n) cap <<= 1;
     hidx.assign(cap, 0);
@@ -523,8 +524,8 @@ size_t poll_ring(genesys_ctx *c, uint32_t ri, Batch &b) {
   uint32_t s;
   // take the ready entries first and prefetch their slots (written by the GPU,
   // so their lines are not in the CPU's caches), then read the slots
-  uint32_t slots[1024];
-  const size_t cap_n = std::min<size_t>(maxb, 1024);
+  uint32_t *slots = b.slot_ids.data();
+  const size_t cap_n = maxb;
   while (n < cap_n && entry_ready(ring, mask, h + n, &s)) {
     slots[n] = s;
     __builtin_prefetch(&c->slots[s], 0, 0);

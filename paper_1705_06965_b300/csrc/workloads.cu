@@ -6,8 +6,13 @@
 //   C2  Sec. 4.1 / Sec. 6 pwrite at work-item / warp / work-group / kernel grain
 //   C6  Sec. 6 / Fig. 6   block permutation + work-group pwrite, 4 ordering x blocking modes
 //   probe Sec. 4.1        strong ordering: stores before the call are complete
+//   ping-pong             host-link round trip of a flag (the floor of a blocking call)
 #include <cuda_runtime.h>
 #include <stdio.h>
+#include <string.h>
+#include <time.h>
+
+#include <thread>
 
 #include "genesys.h"
 #include "genesys_device.cuh"
@@ -27,6 +32,12 @@ __device__ __forceinline__ uint64_t sm64_at(uint64_t seed, uint64_t i) {
 }
 
 int set_err(int code, const char *msg) { return genesys_internal_error(code, msg); }
+
+inline uint64_t host_now_ns() {
+  timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
+}
 
 // Launch through the runtime (legality checks, kernel-grain state reset,
 // synchronise + drain), then turn device-side failures into GENESYS_EDEVICE.
@@ -339,6 +350,28 @@ const void *vis_ptr() {
   return reinterpret_cast<const void *>(&visibility_kernel<G, O, R>);
 }
 
+// Host-link round trip: one GPU thread stores `r` to `ping` (host-mapped) and
+// waits for the host to store `r` to `pong`, for r = 1 .. rounds; the wait is
+// bounded by deadline_ns.  out[0] = elapsed ns, out[1] = rounds completed,
+// out[2] = 1 if the deadline ended it.
+__global__ void pingpong_kernel(uint64_t *ping, const uint64_t *pong, uint32_t rounds, uint64_t deadline_ns,
+                                unsigned long long *out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const uint64_t t0 = now_ns();
+  uint32_t done = 0;
+  bool late = false;
+  for (uint32_t r = 1; r <= rounds && !late; ++r) {
+    st_release_sys(ping, r);
+    while (ld_acquire_sys(pong) != r) {
+      if (now_ns() - t0 > deadline_ns) { late = true; break; }
+    }
+    if (!late) done = r;
+  }
+  out[0] = now_ns() - t0;
+  out[1] = done;
+  out[2] = late ? 1ull : 0ull;
+}
+
 }  // namespace
 
 extern "C" {
@@ -472,6 +505,54 @@ int genesys_visibility_probe(genesys_ctx *c, uint64_t n, uint32_t gran, uint32_t
   void *args[] = {&g, &n, &seed, &probe, &viol};
   const uint32_t flags = gran | (relaxed ? GENESYS_LAUNCH_RELAXED : 0);
   return run(c, k, (uint32_t)blocks, bt, 0, args, flags, stream);
+}
+
+// Round-trip latency of a flag between a GPU thread and a host thread over
+// the host link (the floor under any blocking GPU system call).
+int genesys_link_pingpong(int device, uint32_t rounds, uint64_t timeout_ns, uint64_t *ns_per_round) {
+  if (!ns_per_round || rounds == 0) return set_err(GENESYS_EINVAL, "NULL argument or zero rounds");
+  if (cudaSetDevice(device) != cudaSuccess) return set_err(GENESYS_ECUDA, "cudaSetDevice");
+  uint64_t *flags = nullptr;  // ping in line 0, pong in line 1 (separate 64-byte lines)
+  if (cudaHostAlloc((void **)&flags, 128, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess)
+    return set_err(GENESYS_ECUDA, "cudaHostAlloc");
+  memset(flags, 0, 128);
+  uint64_t *d_flags = nullptr;
+  unsigned long long *d_out = nullptr;
+  cudaStream_t st = nullptr;
+  int rc = 0;
+  if (cudaHostGetDevicePointer((void **)&d_flags, flags, 0) != cudaSuccess ||
+      cudaMalloc((void **)&d_out, 3 * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    rc = set_err(GENESYS_ECUDA, "pingpong set-up");
+  }
+  bool host_late = false;
+  if (rc == 0) {
+    volatile uint64_t *ping = flags, *pong = flags + 8;
+    std::thread echo([&] {
+      const uint64_t until = host_now_ns() + timeout_ns + 1000000000ull;
+      for (uint32_t r = 1; r <= rounds; ++r) {
+        while (__atomic_load_n(ping, __ATOMIC_ACQUIRE) != r) {
+          if (host_now_ns() > until) { host_late = true; return; }
+          __builtin_ia32_pause();
+        }
+        __atomic_store_n(pong, (uint64_t)r, __ATOMIC_RELEASE);
+      }
+    });
+    pingpong_kernel<<<1, 32, 0, st>>>(d_flags, d_flags + 8, rounds, timeout_ns, d_out);
+    const cudaError_t e = cudaStreamSynchronize(st);
+    echo.join();
+    unsigned long long out[3] = {0, 0, 0};
+    if (e != cudaSuccess || cudaMemcpy(out, d_out, sizeof out, cudaMemcpyDeviceToHost) != cudaSuccess)
+      rc = set_err(GENESYS_ECUDA, "pingpong kernel");
+    else if (out[2] || host_late || out[1] != rounds)
+      rc = set_err(GENESYS_ETIMEDOUT, "pingpong: rounds did not complete within the timeout");
+    else
+      *ns_per_round = out[0] / rounds;
+  }
+  if (st) cudaStreamDestroy(st);
+  if (d_out) cudaFree(d_out);
+  cudaFreeHost(flags);
+  return rc;
 }
 
 }  // extern "C"

@@ -59,3 +59,12 @@ def test_madvise_and_getpid_from_gpu(G, ctx):
     assert ctx.gpu_call(SYS_madvise, [page, 4096, 12345]) == -errno.EINVAL
     assert ctx.gpu_call(SYS_getpid) == os.getpid()
     assert ctx.gpu_call(200) == -errno.ENOSYS                               # not in the supported set
+
+
+def test_link_pingpong_round_trip():
+    """The host-link round trip under every blocking call: a GPU thread and a
+    host thread exchange 2,000 flags; the time per round trip is positive and
+    below the 10 us a PCIe round trip plus a polling host stays well under."""
+    import paper_1705_06965_b300 as G
+    ns = G.link_pingpong(0, rounds=2000)
+    assert 100 < ns < 10_000, ns
