@@ -192,3 +192,34 @@ def test_c2_small_slot_area_and_coalescing_window(G, tmp_path, n_slots, threads,
             assert got == open(want_path, "rb").read(), (gran, relaxed, nb)
         st = c.stats()
         assert st["failed"] == 0
+
+
+def test_service_probe_leaves_the_context_usable(G, tmp_path):
+    """genesys_service_probe publishes work-item pwrites from the host into
+    the same slot area and rewrites the device-side claim state: kernels on
+    the context afterwards still claim, complete and write exactly."""
+    with G.Context(device=0, service_threads=2, n_slots=4096, staging_bytes=(1 << 20) * 64 + (1 << 20),
+                   deadline_ns=5_000_000_000) as c:
+        n = 1 << 14
+        st = c.staging(n * 64 * 2)
+        view = c.host_view(st, n * 64)
+        view[:] = np.frombuffer(workloads.stream_bytes(5, n * 64), np.uint8)
+        p = str(tmp_path / "probe.bin")
+        fd = os.open(p, os.O_CREAT | os.O_TRUNC | os.O_RDWR, 0o644)
+        try:
+            rate = c.service_probe(fd, st, 64, n)   # 4 rounds of the 4096-slot area
+            assert rate > 0
+        finally:
+            os.close(fd)
+        assert open(p, "rb").read() == workloads.stream_bytes(5, n * 64)
+        for gran, bt in ((0, 256), (1, 256), (2, 64)):
+            want_path = str(tmp_path / f"want_{gran}.bin")
+            oracle.c2_pwrite(want_path, 20000, {0: 1, 1: 32, 2: bt}[gran])
+            q = str(tmp_path / f"after_{gran}.bin")
+            fd = os.open(q, os.O_CREAT | os.O_TRUNC | os.O_WRONLY, 0o644)
+            try:
+                c.c2_pwrite(fd, 20000, gran, bt, False, False, workloads.SEED_C2, st + n * 64, 20000 * 64)
+            finally:
+                os.close(fd)
+            assert open(q, "rb").read() == open(want_path, "rb").read()
+        assert c.status() == [0] * G.ST_WORDS
