@@ -282,3 +282,22 @@ def test_one_batch_of_neighbours_becomes_one_call(tmp_path, pattern):
     assert done == n and st["requests"] == n and st["failed"] == 0
     assert st["os_calls"] == 1, st
     assert open(p, "rb").read() == want
+
+
+def test_c_abi_from_plain_c(tmp_path):
+    """The boundary is a C ABI: a plain C program compiled against
+    include/genesys.h and linked with libgenesys.so runs the request protocol
+    in a host-only context (no Python in the loop)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.dirname(G.LIB_PATH)
+    exe = str(tmp_path / "host_only_client")
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-I", os.path.join(root, "include"),
+                           os.path.join(root, "tests", "c_abi", "host_only_client.c"), "-o", exe,
+                           G.LIB_PATH, "-Wl,-rpath," + pkg])
+    out = subprocess.run([exe, str(tmp_path / "scratch.bin")], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr + out.stdout
+    assert out.stdout.startswith("ok requests=66")
