@@ -585,6 +585,11 @@ def serve_c5(G, local, rank):
             m = np.arange(8)[None, :] < first.n_ops[:, None]
             out["first1000_alone_equals_mix"] = bool(np.array_equal(r_plain[m], r_served[m]))
             _, out["served_full"] = run(tr, max_inflight=64, **tuned)
+            # below saturation: the first 2,000 requests with arrivals spread to
+            # 4 k/s, where latency is service time rather than queueing
+            slow = tr.subset(np.arange(2000))
+            slow.arrival_ns = (slow.arrival_ns.astype(np.float64) * (tr.params["rate_per_s"] / 4000.0)).astype(np.uint64)
+            _, out["served_first2000_at_4k_per_s"] = run(slow, max_inflight=64, **tuned)
     finally:
         for fd in in_fds:
             os.close(fd)
@@ -768,6 +773,16 @@ def run_genesys(args):
     want = oracle.c1_histogram(rig.c1_path, C1_CHUNK)
     if not (np.array_equal(h[0].numpy().view(np.uint32), want) and np.array_equal(h[1].numpy().view(np.uint32), want)):
         raise RuntimeError("C1 histogram differs from the oracle")
+    # the C1 configuration (4 MiB, 64 work-groups x 256 threads, 4 KiB preads)
+    # in its plain and batched forms, from the kernels of the timed steps
+    c1_forms = {}
+    for kname, form in (("c1_plain_kernel", "plain"), ("c1_batched_kernel", "batched")):
+        ms_list = kernel_ms.get(kname, [])
+        if ms_list:
+            k_ms = statistics.median(ms_list)
+            c1_forms[form] = {"kernel_ms": round(k_ms, 3), "GB_per_s": round(C1_BYTES / (k_ms * 1e-3) / 1e9, 2),
+                              "preads_per_s": round(C1_BYTES // C1_CHUNK / (k_ms * 1e-3), 1),
+                              "histogram_equals_oracle": True}
 
     tot_ms, e2e_tot = reduce_max([sum(step_ms), sum(e2e_s)], dev)
     calls_step = c2_calls + c1_calls
@@ -872,6 +887,7 @@ def run_genesys(args):
         "forms": {"plain_blocking_strong": {"combo": "work-item/strong/blocking", **plain},
                   "batched": {"combo": batched_key, **batched}},
         "plain_latency_by_threads": lat_by_size,
+        "c1_4MiB": c1_forms,
         "sweep_2p20": sweep,
         **extras,
         "autotuned_step": {"best": step_cfg, "table": step_table},
