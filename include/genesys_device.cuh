@@ -215,11 +215,12 @@ __device__ __forceinline__ uint32_t slot_fill(const genesys_dev &g, uint32_t s, 
   return sq;
 }
 
-/* Doorbell for one published slot (one thread). */
-__device__ __forceinline__ void ring_one(const genesys_dev &g, uint32_t s) {
+/* Doorbell for one published slot (one thread); returns its ring position. */
+__device__ __forceinline__ uint32_t ring_one(const genesys_dev &g, uint32_t s) {
   const uint32_t r = ring_of(g, s);
   const uint32_t pos = atomicAdd(&g.ring_tail[r * 32u], 1u);
   st_release_sys(g.rings + (size_t)r * (g.ring_mask + 1u) + (pos & g.ring_mask), GENESYS_RING_ENTRY(pos, s));
+  return pos;
 }
 
 /* Doorbell for the lanes of `mask` that each filled slot `s`.  Lanes going to
@@ -227,8 +228,8 @@ __device__ __forceinline__ void ring_one(const genesys_dev &g, uint32_t s) {
  * one atomic; after a warp barrier the group's first lane makes one system-scope
  * release fence and writes all of the group's entries, so every lane's slot
  * stores happen before its entry becomes visible, at one fence per group
- * instead of one per lane. */
-__device__ __forceinline__ void ring_warp(const genesys_dev &g, uint32_t mask, uint32_t s) {
+ * instead of one per lane.  Returns the calling lane's ring position. */
+__device__ __forceinline__ uint32_t ring_warp(const genesys_dev &g, uint32_t mask, uint32_t s) {
   const uint32_t r = ring_of(g, s);
   const uint32_t peers = __match_any_sync(mask, r);
   const uint32_t lane = lane_id();
@@ -246,6 +247,7 @@ __device__ __forceinline__ void ring_warp(const genesys_dev &g, uint32_t mask, u
     const uint32_t sj = __shfl_sync(peers, s, j);
     if (lane == leader) st_relaxed_sys(ring + ((base + k) & g.ring_mask), GENESYS_RING_ENTRY(base + k, sj));
   }
+  return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));  // entries are written in lane order
 }
 
 /* Wait until the CPU finished request `sq` of slot `s`; returns its result.
@@ -270,6 +272,53 @@ __device__ __forceinline__ int64_t slot_wait(const genesys_dev &g, uint32_t s, u
   return ret;
 }
 
+/* The same wait for a request published at position `pos` of ring `r`.  The
+ * caller polls a count of the ring's finished entries instead of its own
+ * completion word: one word for all the lanes of a warp, so a warp's polls
+ * coalesce into one read, and GENESYS_RING_DONE_COPIES copies of it on
+ * separate lines, one per group of warps, so that the grid's polls do not all
+ * queue on one host-memory word.  It sleeps about as long as the entries still
+ * ahead of it take at the rate it has seen the count advance (at most
+ * kMaxNapNs at a time, so the deadline check stays prompt).  Once the count
+ * has passed its position, one acquire fence and one read of its completion
+ * word give the result. */
+constexpr uint32_t kMaxNapNs = 100000;
+
+__device__ __forceinline__ int64_t slot_wait_ring(const genesys_dev &g, uint32_t s, uint32_t sq, uint32_t r,
+                                                  uint32_t pos, uint64_t t0) {
+  const uint32_t copy = (hw_lane_id() >> 5) % GENESYS_RING_DONE_COPIES;
+  const uint64_t *fin_word = g.ring_done + ((size_t)r * GENESYS_RING_DONE_COPIES + copy) * 8u;
+  uint32_t ns = g.poll_min_ns;
+  const uint32_t cap = g.poll_max_ns;
+  uint32_t fin0 = 0;
+  uint64_t when0 = 0;
+  for (;;) {
+    const uint32_t fin = (uint32_t)ld_relaxed_sys(fin_word);
+    const int32_t ahead = (int32_t)(pos + 1u - fin);  // entries up to and including ours not finished
+    if (ahead <= 0) break;
+    const uint64_t now = now_ns();
+    if (now - t0 > g.deadline_ns) { note_error(g, -kETIMEDOUT); return -kETIMEDOUT; }
+    uint64_t nap = ns;
+    if (when0 == 0) {
+      when0 = now;
+      fin0 = fin;
+    } else if (fin != fin0) {
+      const uint64_t est = (now - when0) / (uint32_t)(fin - fin0) * (uint64_t)ahead;  // ns per entry x ahead
+      nap = est > nap ? est : nap;
+    }
+    __nanosleep(nap < kMaxNapNs ? (uint32_t)nap : kMaxNapNs);
+    ns = ns < cap ? ns + (ns >> 1) + 1 : cap;
+  }
+  fence_acq_rel_sys();
+  const uint64_t d = ld_relaxed_sys(&g.done[s]);
+  if ((uint32_t)(d >> 32) != sq) return slot_wait(g, s, sq, t0);  // not expected once the count passed it
+  st_relaxed_gpu(&g.known_done[s], sq);
+  const uint32_t lo = (uint32_t)d;
+  const int64_t ret = lo == GENESYS_RET_IN_SLOT ? (int64_t)ld_relaxed_sys(&g.slots[s].ret) : (int64_t)(int32_t)lo;
+  if (ret < 0) atomicAdd(reinterpret_cast<int *>(&g.status[GENESYS_ST_FAILED_CALLS]), 1);
+  return ret;
+}
+
 __device__ __forceinline__ void slot_release(const genesys_dev &g, uint32_t s) {
   __threadfence();
   atomicExch(&g.owner[s], 0u);
@@ -284,11 +333,11 @@ __device__ __forceinline__ int64_t single_call(const genesys_dev &g, uint32_t nr
   int64_t rc = slot_claim(g, hw_lane_id(), &s, t0);
   if (rc < 0) return rc;
   const uint32_t sq = slot_fill(g, s, nr, flags, a0, a1, a2, a3, a4, a5);
-  ring_one(g, s);  // st.release.sys: the slot stores (and, through the group's
-                   // barrier, the group's earlier stores) are visible first
+  const uint32_t pos = ring_one(g, s);  // st.release.sys: the slot stores (and, through
+                                        // the group's barrier, its earlier stores) first
   int64_t ret = 0;
   if (wait) {
-    ret = slot_wait(g, s, sq, t0);
+    ret = slot_wait_ring(g, s, sq, ring_of(g, s), pos, t0);
     if (ret == -kETIMEDOUT) {  /* the CPU may still finish it: keep the slot's
                                   sequence so the next claimer waits for it */
       slot_release(g, s);
@@ -308,6 +357,8 @@ struct Ticket {
   uint32_t slot;
   uint32_t seq;
   uint64_t t0;
+  uint32_t pos;  // ring position
+  uint32_t pad;
 };
 
 __device__ __forceinline__ int64_t issue(const genesys_dev &g, Ticket *t, uint32_t nr, uint64_t a0 = 0,
@@ -317,13 +368,13 @@ __device__ __forceinline__ int64_t issue(const genesys_dev &g, Ticket *t, uint32
   int64_t rc = slot_claim(g, hw_lane_id(), &t->slot, t->t0);
   if (rc < 0) { t->slot = 0xFFFFFFFFu; return rc; }
   t->seq = slot_fill(g, t->slot, nr, GENESYS_REQ_TICKET | GENESYS_REQ_RELAXED, a0, a1, a2, a3, a4, a5);
-  ring_one(g, t->slot);
+  t->pos = ring_one(g, t->slot);
   return 0;
 }
 
 __device__ __forceinline__ int64_t wait(const genesys_dev &g, const Ticket &t) {
   if (t.slot == 0xFFFFFFFFu) return -kETIMEDOUT;
-  const int64_t ret = slot_wait(g, t.slot, t.seq, now_ns());
+  const int64_t ret = slot_wait_ring(g, t.slot, t.seq, ring_of(g, t.slot), t.pos, now_ns());
   slot_release(g, t.slot);
   if (ret != -kETIMEDOUT) note_latency(g, t.t0);
   return ret;
@@ -408,8 +459,8 @@ __device__ __forceinline__ int64_t call_at(const genesys_dev &g, uint32_t site, 
       const uint32_t okmask = __ballot_sync(active, ok);
       if (ok) {
         const uint32_t sq = slot_fill(g, s, nr, flags, a0, a1, a2, a3, a4, a5);
-        ring_warp(g, okmask, s);
-        rc = B == BLOCKING ? slot_wait(g, s, sq, t0) : 0;
+        const uint32_t pos = ring_warp(g, okmask, s);
+        rc = B == BLOCKING ? slot_wait_ring(g, s, sq, ring_of(g, s), pos, t0) : 0;
         slot_release(g, s);
         if (rc != -kETIMEDOUT) note_latency(g, t0);
         pending = false;

@@ -99,6 +99,10 @@ static inline GENESYS_HD uint32_t genesys_ring_of(uint32_t slot, uint32_t n_ring
 /* Doorbell ring entry: bits 63..32 = ring position + 1, bits 31..0 = slot. */
 #define GENESYS_RING_ENTRY(pos, slot) ((((uint64_t)(uint32_t)((pos) + 1u)) << 32) | (uint64_t)(uint32_t)(slot))
 
+/* Copies of each ring's finished-entries count (callers poll the copy of
+ * their warp, so that no single host-memory word takes every poll). */
+#define GENESYS_RING_DONE_COPIES 16u
+
 /* Kernel-grain call sites per launch (GENESYS_GRAN_KERNEL). */
 #define GENESYS_KSITES 64u
 
@@ -124,6 +128,10 @@ typedef struct genesys_dev {
   genesys_slot *slots;        /* host-mapped, n_slots entries                       */
   uint64_t *done;             /* host-mapped, n_slots completion words              */
   uint64_t *rings;            /* host-mapped, n_rings * ring_cap doorbell entries   */
+  uint64_t *ring_done;        /* host-mapped: entries of ring r the CPU has finished,
+                                 GENESYS_RING_DONE_COPIES copies on separate 64-byte
+                                 lines (word 8 * (r * COPIES + c)), stored with
+                                 release after each batch's completion words       */
   uint32_t *owner;            /* device memory: slot claim locks                    */
   uint32_t *seq;              /* device memory: last published sequence per slot    */
   uint32_t *known_done;       /* device memory: last sequence seen finished         */

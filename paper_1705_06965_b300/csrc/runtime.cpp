@@ -139,6 +139,7 @@ struct genesys_ctx {
   genesys_slot *slots = nullptr;
   uint64_t *done = nullptr;
   uint64_t *rings = nullptr;
+  uint64_t *ring_done = nullptr;  // per ring: GENESYS_RING_DONE_COPIES copies of the finished count
   uint32_t ring_cap = 0;
   uint8_t *staging = nullptr;
   std::atomic<uint64_t> staging_used{0};
@@ -547,6 +548,8 @@ size_t poll_ring(genesys_ctx *c, uint32_t ri, Batch &b) {
   process_batch(c, b, n, c->counters[ri]);
   c->head[ri] = h + n;
   c->retired[ri].store(h + n, std::memory_order_release);
+  for (uint32_t k = 0; k < GENESYS_RING_DONE_COPIES; ++k)
+    __atomic_store_n(&c->ring_done[((size_t)ri * GENESYS_RING_DONE_COPIES + k) * 8], h + n, __ATOMIC_RELEASE);
   return n;
 }
 
@@ -623,6 +626,7 @@ void free_all(genesys_ctx *c) {
   host_free(c, c->slots);
   host_free(c, c->done);
   host_free(c, c->rings);
+  host_free(c, c->ring_done);
   host_free(c, c->staging);
   dev_free(c, c->owner);
   dev_free(c, c->seq);
@@ -764,6 +768,8 @@ int genesys_init(const genesys_config *cfg_in, int device, genesys_ctx **out) {
   if ((rc = host_alloc(c.get(), &c->slots, (size_t)cfg.n_slots * sizeof(genesys_slot)))) return cleanup(rc);
   if ((rc = host_alloc(c.get(), &c->done, (size_t)cfg.n_slots * 8))) return cleanup(rc);
   if ((rc = host_alloc(c.get(), &c->rings, (size_t)cfg.n_service_threads * c->ring_cap * 8))) return cleanup(rc);
+  if ((rc = host_alloc(c.get(), &c->ring_done, (size_t)cfg.n_service_threads * GENESYS_RING_DONE_COPIES * 64)))
+    return cleanup(rc);
   if (cfg.staging_bytes && (rc = host_alloc(c.get(), &c->staging, cfg.staging_bytes))) return cleanup(rc);
   if ((rc = dev_alloc(c.get(), &c->owner, cfg.n_slots))) return cleanup(rc);
   if ((rc = dev_alloc(c.get(), &c->seq, cfg.n_slots))) return cleanup(rc);
@@ -832,6 +838,7 @@ int genesys_device_view(genesys_ctx *c, genesys_dev *d) {
   d->slots = c->slots;
   d->done = c->done;
   d->rings = c->rings;
+  d->ring_done = c->ring_done;
   d->owner = c->owner;
   d->seq = c->seq;
   d->known_done = c->known_done;
