@@ -431,12 +431,13 @@ def profile_extras(args, rig, local, rank, link):
     G = rig.G
     out = {}
     # pread + histogram over 1 GiB: each form (work-group plain, work-group
-    # batched, warp) at its own autotuned setting
+    # batched, warp, work-group with an HBM landing copy) at its own autotuned
+    # setting
     best = autotune.tune_scan(local, rig.fd_scan, SCAN_BYTES)
     per_form = best.get("by_form") or {str(best["form"]): best}
     sb = max(c["groups"] * c["chunk"] * (32 if c["form"] == G.FORM_WARP else 2) for c in per_form.values())
     res = {}
-    names = {G.FORM_PLAIN: "plain", G.FORM_BATCHED: "batched", G.FORM_WARP: "warp"}
+    names = {G.FORM_PLAIN: "plain", G.FORM_BATCHED: "batched", G.FORM_WARP: "warp", G.FORM_HBM: "hbm_landing"}
     for f, cfg in sorted(per_form.items()):
         with G.Context(device=local, service_threads=cfg["service_threads"], staging_bytes=sb + (1 << 20)) as ctx:
             st = ctx.staging(sb)

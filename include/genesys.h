@@ -202,15 +202,19 @@ int genesys_emulate_call(genesys_ctx *ctx, uint32_t nr, const uint64_t args[6], 
 #define GENESYS_FORM_PLAIN   0u  /* work-group grain, strong ordering, blocking      */
 #define GENESYS_FORM_BATCHED 1u  /* relaxed, non-blocking, double-buffered prefetch  */
 #define GENESYS_FORM_WARP    2u  /* warp grain, strong ordering, blocking (C1)       */
+#define GENESYS_FORM_HBM     3u  /* plain, each chunk copied to HBM and scanned there (C1) */
 
 /* C1, Sec. 6 pread microbenchmark (Fig. 5): `groups` thread blocks of `threads`
  * threads read `file_bytes` bytes of `fd` with pread in `chunk`-byte pieces
  * (chunk i by block i mod groups) at work-group granularity and build a
  * 256-bin byte histogram, added into hist_dev[256] (device pointer, uint32).
  * form GENESYS_FORM_WARP reads at warp granularity instead: chunk i by warp
- * i mod (groups * threads / 32).  staging: host-mapped, >= groups * chunk *
- * (BATCHED: 2, WARP: threads / 32, PLAIN: 1) bytes, 16-byte aligned; chunk a
- * multiple of 16, threads a multiple of 32; another form is GENESYS_EINVAL. */
+ * i mod (groups * threads / 32); GENESYS_FORM_HBM is the plain form with each
+ * chunk moved from staging into an HBM landing buffer (the context's device
+ * scratch, groups * chunk bytes) and counted there.  staging: host-mapped,
+ * >= groups * chunk * (BATCHED: 2, WARP: threads / 32, PLAIN and HBM: 1)
+ * bytes, 16-byte aligned; chunk a multiple of 16, threads a multiple of 32;
+ * another form is GENESYS_EINVAL. */
 int genesys_c1_histogram(genesys_ctx *ctx, int fd, uint64_t file_bytes, uint64_t chunk, uint32_t groups,
                          uint32_t threads, uint32_t form, void *staging, uint64_t staging_bytes,
                          uint32_t *hist_dev, void *stream);

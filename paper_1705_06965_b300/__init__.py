@@ -30,7 +30,7 @@ GRAN_ITEM, GRAN_WARP, GRAN_GROUP, GRAN_KERNEL = 0, 1, 2, 3
 GRAN_NAMES = {GRAN_ITEM: "work-item", GRAN_WARP: "warp", GRAN_GROUP: "work-group", GRAN_KERNEL: "kernel"}
 REQ_BLOCKING, REQ_RELAXED, REQ_TICKET = 0x1, 0x8, 0x10
 INIT_HOST_ONLY, INIT_NO_THREADS, INIT_ANY_SYSCALL = 0x1, 0x2, 0x4
-FORM_PLAIN, FORM_BATCHED, FORM_WARP = 0, 1, 2
+FORM_PLAIN, FORM_BATCHED, FORM_WARP, FORM_HBM = 0, 1, 2, 3
 ST_FIRST_ERROR, ST_TIMEOUTS, ST_FAILED_CALLS, ST_BAD_ARGS, ST_WORDS = 0, 1, 2, 3, 8
 
 EINVAL, ENOMEM, ETIMEDOUT, ENODEV, EDEVICE, ECUDA = -22, -12, -110, -19, -1001, -1000

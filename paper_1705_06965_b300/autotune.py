@@ -88,10 +88,11 @@ def _timed(torch, fn) -> float:
 
 def tune_scan(device: int, fd: int, nbytes: int, tuner: Autotuner | None = None, force: bool = False,
               service_threads=(4, 8, 12), chunks=(128 << 10, 256 << 10, 512 << 10, 1 << 20),
-              groups=(148, 296), forms=(0, 1, 2), warp_chunks=(16 << 10, 64 << 10)):
+              groups=(148, 296), forms=(0, 1, 2, 3), warp_chunks=(16 << 10, 64 << 10)):
     """pread + histogram scan: service threads x chunk x groups x form, where
     the form sets the invocation granularity (work-group plain or batched,
-    or warp, which reads smaller chunks: `warp_chunks`)."""
+    or warp, which reads smaller chunks: `warp_chunks`) and where the chunk
+    is counted (staging, or an HBM copy: form 3)."""
     import torch
     import paper_1705_06965_b300 as G
     tuner = tuner or Autotuner()

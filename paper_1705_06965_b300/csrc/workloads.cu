@@ -127,6 +127,35 @@ __global__ void __launch_bounds__(1024, 1) c1_plain_kernel(genesys_dev g, int fd
   hist_flush(sh, hist_out);
 }
 
+// HBM form: as the plain form, but the block first moves each chunk from
+// staging into its own landing buffer in HBM (16-byte loads over the host
+// link, stores to HBM) and builds the histogram from the HBM copy.
+__global__ void __launch_bounds__(1024, 1) c1_hbm_kernel(genesys_dev g, int fd, uint64_t file_bytes, uint32_t chunk,
+                                                        uint8_t *staging, uint32_t *hist_out, uint8_t *landing) {
+  extern __shared__ uint32_t sh[];
+  for (uint32_t i = threadIdx.x; i < (blockDim.x >> 5) * 256; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  uint32_t *my = sh + (threadIdx.x >> 5) * 256;
+  uint8_t *buf = staging + (size_t)blockIdx.x * chunk;
+  uint8_t *land = landing + (size_t)blockIdx.x * chunk;
+  const uint64_t n_chunks = (file_bytes + chunk - 1) / chunk;
+  for (uint64_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+    const uint64_t off = c * chunk;
+    const uint64_t len = file_bytes - off < chunk ? file_bytes - off : chunk;
+    const int64_t r = call<GROUP, STRONG, BLOCKING>(g, SYS_pread64, (uint64_t)fd, (uint64_t)buf, len, off);
+    if (r <= 0) break;  // r is the same in every thread (broadcast after the call)
+    const uint64_t n = (uint64_t)r < len ? (uint64_t)r : len;
+    const uint4 *src = reinterpret_cast<const uint4 *>(buf);
+    uint4 *dst = reinterpret_cast<uint4 *>(land);
+#pragma unroll 4
+    for (uint64_t i = threadIdx.x; i < (n + 15) / 16; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    hist_bytes(land, n, my);
+    __syncthreads();  // the landing buffer is rewritten by the next chunk
+  }
+  hist_flush(sh, hist_out);
+}
+
 // Warp form: warp grain, strong ordering, blocking.  Every warp of the grid
 // reads on its own: global warp w reads chunks w, w + W, ... (W warps in the
 // grid) into its own staging piece and counts them into its own shared-memory
@@ -384,7 +413,7 @@ int genesys_c1_histogram(genesys_ctx *c, int fd, uint64_t file_bytes, uint64_t c
   if (chunk == 0 || chunk % 16 || chunk > (1u << 30)) return set_err(GENESYS_EINVAL, "chunk must be a multiple of 16");
   if (groups == 0 || threads < 32 || threads > 1024 || threads % 32) return set_err(GENESYS_EINVAL, "bad launch shape");
   if ((uintptr_t)staging % 16) return set_err(GENESYS_EINVAL, "staging must be 16-byte aligned");
-  if (form > GENESYS_FORM_WARP) return set_err(GENESYS_EINVAL, "form: GENESYS_FORM_PLAIN, _BATCHED or _WARP");
+  if (form > GENESYS_FORM_HBM) return set_err(GENESYS_EINVAL, "form: GENESYS_FORM_PLAIN, _BATCHED, _WARP or _HBM");
   const uint64_t need = (uint64_t)groups * chunk *
                         (form == GENESYS_FORM_BATCHED ? 2 : form == GENESYS_FORM_WARP ? threads / 32 : 1);
   if (staging_bytes < need) return set_err(GENESYS_EINVAL, "staging too small");
@@ -402,6 +431,14 @@ int genesys_c1_histogram(genesys_ctx *c, int fd, uint64_t file_bytes, uint64_t c
                GENESYS_GRAN_GROUP | GENESYS_LAUNCH_RELAXED | GENESYS_LAUNCH_NONBLOCKING, stream);
   if (form == GENESYS_FORM_WARP)
     return run(c, (const void *)&c1_warp_kernel, groups, threads, smem, args, GENESYS_GRAN_WARP, stream);
+  if (form == GENESYS_FORM_HBM) {
+    void *landing = nullptr;  // the context's device scratch: one chunk per block
+    const int rc = genesys_internal_scratch(c, (size_t)groups * chunk, &landing);
+    if (rc) return rc;
+    uint8_t *land = (uint8_t *)landing;
+    void *hargs[] = {&g, &fd, &file_bytes, &ch, &st, &hist_dev, &land};
+    return run(c, (const void *)&c1_hbm_kernel, groups, threads, smem, hargs, GENESYS_GRAN_GROUP, stream);
+  }
   return run(c, (const void *)&c1_plain_kernel, groups, threads, smem, args, GENESYS_GRAN_GROUP, stream);
 }
 

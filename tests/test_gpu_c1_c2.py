@@ -47,7 +47,7 @@ def _c1(ctx, G, path, nbytes, chunk, groups, threads, form):
     return hist.cpu().numpy().view(np.uint32)
 
 
-@pytest.mark.parametrize("form", [0, 1, 2])
+@pytest.mark.parametrize("form", [0, 1, 2, 3])
 def test_c1_full_config_bit_exact(ctx, G, form):
     """The C1 configuration: 4 MiB, 64 work-groups x 256 threads, 4 KiB preads."""
     p = workloads.c1_file()
@@ -64,7 +64,7 @@ def test_c1_full_config_bit_exact(ctx, G, form):
     ((1 << 20) + 123, 65536, 148, 1024),
     (6 << 20, 1 << 20, 5, 512),
 ])
-@pytest.mark.parametrize("form", [0, 1, 2])
+@pytest.mark.parametrize("form", [0, 1, 2, 3])
 def test_c1_shapes(ctx, G, tmp_path, nbytes, chunk, groups, threads, form):
     p = workloads.c1_file(str(tmp_path / "c1.bin"), nbytes, seed=nbytes)
     want = oracle.c1_histogram(p, chunk)
@@ -81,7 +81,7 @@ def test_c1_empty_and_errors(ctx, G, tmp_path):
         ctx.c1_histogram(3, 4096, hist.data_ptr(), st, 4096, chunk=4008, groups=1, threads=64)
     assert e.value.code == G.EINVAL        # chunk not a multiple of 16
     with pytest.raises(G.GenesysError) as e:
-        ctx.c1_histogram(3, 4096, hist.data_ptr(), st, 4096, chunk=4096, groups=1, threads=64, form=3)
+        ctx.c1_histogram(3, 4096, hist.data_ptr(), st, 4096, chunk=4096, groups=1, threads=64, form=4)
     assert e.value.code == G.EINVAL        # no such form
     with pytest.raises(G.GenesysError) as e:  # warp form: one chunk per warp in staging
         ctx.c1_histogram(3, 4096, hist.data_ptr(), st, 4096, chunk=4096, groups=1, threads=64, form=G.FORM_WARP)
