@@ -798,6 +798,7 @@ int genesys_drain(genesys_ctx *c, uint64_t timeout_ns) {
   std::vector<uint32_t> tails(c->cfg.n_service_threads);
   int rc = read_tails(c, tails);
   if (rc) return rc;
+  std::unique_ptr<Batch> batch;  // NO_THREADS mode: the caller services the rings
   const uint64_t until = mono_ns() + timeout_ns;
   for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) {
     for (;;) {
@@ -806,8 +807,8 @@ int genesys_drain(genesys_ctx *c, uint64_t timeout_ns) {
       if ((int32_t)(got - tails[r]) >= 0) break;
       if (c->cfg.flags & GENESYS_INIT_NO_THREADS) {
         std::lock_guard<std::mutex> g(c->svc_mu);
-        Batch batch(std::max<uint32_t>(1, c->cfg.coalesce_max));
-        poll_ring(c, r, batch);
+        if (!batch) batch.reset(new Batch(std::max<uint32_t>(1, c->cfg.coalesce_max)));
+        poll_ring(c, r, *batch);
       } else {
         std::this_thread::sleep_for(std::chrono::microseconds(5));
       }
