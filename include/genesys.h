@@ -185,6 +185,15 @@ int genesys_staging_reset(genesys_ctx *ctx);
 /* Message of the calling thread's last failure. */
 const char *genesys_last_error(void);
 
+/* Failure handling on the host: stop the service thread of doorbell ring
+ * `ring` (it finishes the batch it holds), leave the ring unserved for
+ * pause_ns, then start a new thread that continues from the same ring
+ * position.  Requests published meanwhile wait in the ring; a caller whose
+ * wait passes device_deadline_ns gives up with -ETIMEDOUT, and its request is
+ * still carried out later.  GENESYS_EINVAL without service threads or for a
+ * bad ring.  Blocks for pause_ns. */
+int genesys_service_restart(genesys_ctx *ctx, uint32_t ring, uint64_t pause_ns);
+
 /* GENESYS_INIT_HOST_ONLY contexts: make one call through the full protocol
  * from a CPU thread standing in for a GPU lane (claim a slot, marshal,
  * publish, ring the doorbell, wait if GENESYS_REQ_BLOCKING is in flags).

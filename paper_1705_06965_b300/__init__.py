@@ -44,7 +44,7 @@ EXPORTS = [
     "genesys_c3_wordcount", "genesys_c3_wordcount_noalloc", "genesys_serve_config_default", "genesys_c5_serve",
     "genesys_reclaim", "genesys_mmap_reserve", "genesys_kv_start", "genesys_kv_stop", "genesys_kv_value",
     "genesys_kv_client", "genesys_c6_permute", "genesys_gpu_call", "genesys_echo_start", "genesys_echo_stop",
-    "genesys_echo_client", "genesys_service_probe", "genesys_link_pingpong",
+    "genesys_echo_client", "genesys_service_probe", "genesys_link_pingpong", "genesys_service_restart",
 ]
 
 
@@ -148,6 +148,7 @@ def lib() -> ctypes.CDLL:
         "genesys_kv_client": (ctypes.c_int, [vp, vp, u64, vp, ctypes.c_uint16, u32, u64, vp, vp, vp, vp]),
         "genesys_c5_serve": (ctypes.c_int, [vp, vp, u32, vp, u32, ctypes.c_int32, ctypes.POINTER(ServeConfig), vp, vp,
                                             ctypes.POINTER(ServeStats)]),
+        "genesys_service_restart": (ctypes.c_int, [vp, u32, u64]),
         "genesys_link_pingpong": (ctypes.c_int, [ctypes.c_int, u32, u64, ctypes.POINTER(u64)]),
         "genesys_service_probe": (ctypes.c_int, [vp, ctypes.c_int, vp, u32, u64, ctypes.POINTER(u64)]),
         "genesys_echo_start": (ctypes.c_int, [vp, u32, u32, u32, u32, u32, ctypes.c_uint16, u64, ctypes.POINTER(vp)]),
@@ -277,6 +278,11 @@ class Context:
 
     def stats_reset(self) -> None:
         _check(lib().genesys_stats_reset(self.handle), "genesys_stats_reset")
+
+    def service_restart(self, ring: int, pause_ns: int = 0) -> None:
+        """Stop the service thread of `ring`, leave the ring unserved for
+        pause_ns, start a new one (genesys_service_restart)."""
+        _check(lib().genesys_service_restart(self.handle, ring, pause_ns), "genesys_service_restart")
 
     def service_probe(self, fd: int, payload: int, bytes_per_call: int, n_calls: int) -> float:
         """Service-thread ceiling for work-item pwrites (genesys_service_probe):

@@ -155,6 +155,8 @@ struct genesys_ctx {
   // service side
   std::vector<std::thread> threads;
   std::atomic<bool> stop{false};
+  std::unique_ptr<std::atomic<bool>[]> ring_stop;  // per ring: its thread should leave
+  std::mutex restart_mu;
   std::vector<uint64_t> head;                       // per ring, touched by its thread only
   std::unique_ptr<std::atomic<uint64_t>[]> retired;  // per ring: positions fully processed
   std::unique_ptr<Counters[]> counters;             // per ring
@@ -564,7 +566,7 @@ void service_main(genesys_ctx *c, uint32_t ri) {
   Batch batch(std::max<uint32_t>(1, c->cfg.coalesce_max));
   uint64_t last_work = mono_ns();
   uint32_t idle_polls = 0;
-  while (!c->stop.load(std::memory_order_relaxed)) {
+  while (!c->stop.load(std::memory_order_relaxed) && !c->ring_stop[ri].load(std::memory_order_relaxed)) {
     if (poll_ring(c, ri, batch)) {
       last_work = 0;
       idle_polls = 0;
@@ -786,6 +788,8 @@ int genesys_init(const genesys_config *cfg_in, int device, genesys_ctx **out) {
   c->retired.reset(new std::atomic<uint64_t>[nr]);
   for (uint32_t r = 0; r < nr; ++r) c->retired[r].store(0);
   c->counters.reset(new Counters[nr]);
+  c->ring_stop.reset(new std::atomic<bool>[nr]);
+  for (uint32_t r = 0; r < nr; ++r) c->ring_stop[r].store(false);
   if (!(cfg.flags & GENESYS_INIT_NO_THREADS)) {
     for (uint32_t r = 0; r < nr; ++r) c->threads.emplace_back(service_main, c.get(), r);
   }
@@ -819,15 +823,32 @@ int genesys_drain(genesys_ctx *c, uint64_t timeout_ns) {
   return 0;
 }
 
+int genesys_service_restart(genesys_ctx *c, uint32_t ring, uint64_t pause_ns) {
+  if (!c) return fail(GENESYS_EINVAL, "ctx is NULL");
+  if (c->threads.empty()) return fail(GENESYS_EINVAL, "the context has no service threads");
+  if (ring >= c->cfg.n_service_threads) return fail(GENESYS_EINVAL, "no ring %u", ring);
+  std::lock_guard<std::mutex> g(c->restart_mu);
+  // the thread finishes the batch it has and leaves; its ring position (head)
+  // stays with the context, so the new thread continues where it stopped
+  c->ring_stop[ring].store(true);
+  c->threads[ring].join();
+  if (pause_ns) std::this_thread::sleep_for(std::chrono::nanoseconds(pause_ns));
+  c->ring_stop[ring].store(false);
+  c->threads[ring] = std::thread(service_main, c, ring);
+  return 0;
+}
+
 int genesys_shutdown(genesys_ctx *c) {
   if (!c) return 0;
   int rc = 0;
+  std::unique_lock<std::mutex> restarting(c->restart_mu);  // no thread is being replaced meanwhile
   if (!c->threads.empty()) {
     rc = genesys_drain(c, 1000000000ull);
     c->stop.store(true);
     for (auto &t : c->threads) t.join();
     c->threads.clear();
   }
+  restarting.unlock();
   free_all(c);
   delete c;
   return rc;

@@ -10,6 +10,7 @@ import errno
 import os
 import re
 import threading
+import time
 
 import numpy as np
 import pytest
@@ -301,3 +302,64 @@ def test_c_abi_from_plain_c(tmp_path):
     out = subprocess.run([exe, str(tmp_path / "scratch.bin")], capture_output=True, text=True, timeout=60)
     assert out.returncode == 0, out.stderr + out.stdout
     assert out.stdout.startswith("ok requests=66")
+
+
+def test_service_thread_restart_loses_no_request():
+    """A service thread is stopped and restarted while emulated callers keep
+    calling: requests published meanwhile wait in the ring and are carried out
+    by the new thread, each exactly once (every NOP returns its own argument
+    and the request count matches)."""
+    with _ctx(n_slots=256, service_threads=2, deadline_ns=5_000_000_000) as c:
+        errs, done = [], []
+        stop = threading.Event()
+
+        def lane(k):
+            i = 0
+            while not stop.is_set() or i < 200:
+                v = k * 1_000_000 + i
+                if c.emulate_call(G.NR_NOP, [v]) != v:
+                    errs.append(v)
+                i += 1
+            done.append(i)
+
+        th = [threading.Thread(target=lane, args=(k,)) for k in range(4)]
+        [t.start() for t in th]
+        for ring in (0, 1, 0):
+            c.service_restart(ring, pause_ns=30_000_000)
+        stop.set()
+        [t.join() for t in th]
+        c.drain()
+        assert not errs
+        assert c.stats()["requests"] == sum(done)
+
+
+def test_service_pause_past_the_deadline_times_out_then_recovers():
+    with _ctx(n_slots=64, service_threads=1, deadline_ns=50_000_000) as c:
+        out = {}
+
+        def caller():
+            try:
+                out["r"] = c.emulate_call(G.NR_NOP, [3])
+            except G.GenesysError as e:
+                out["e"] = e.code
+
+        t = threading.Thread(target=caller)
+        restart = threading.Thread(target=c.service_restart, args=(0, 300_000_000))
+        restart.start()
+        time.sleep(0.05)            # the ring is unserved now
+        t.start()
+        t.join()
+        restart.join()
+        assert out.get("e") == G.ETIMEDOUT
+        c.drain()                   # the late request is still carried out
+        assert c.emulate_call(G.NR_NOP, [4]) == 4
+        assert c.stats()["requests"] == 2
+
+
+def test_service_restart_rejects_bad_use():
+    with _ctx(no_threads=True) as c:
+        with pytest.raises(G.GenesysError):
+            c.service_restart(0)
+    with _ctx(service_threads=2) as c:
+        with pytest.raises(G.GenesysError):
+            c.service_restart(2)
