@@ -2,6 +2,7 @@
 (nobody services the call) returns an error status the host reads, and the
 context stays usable.  Failures are made on the host side only."""
 import errno
+import os
 import threading
 
 import pytest
@@ -51,3 +52,35 @@ def test_failed_syscall_is_a_result_not_a_fault(G):
     with G.Context(device=0, service_threads=1, staging_bytes=1 << 20) as ctx:
         assert ctx.gpu_call(17, [987654, 0, 16, 0]) == -errno.EBADF   # pread on a closed fd
         assert ctx.status()[G.ST_FAILED_CALLS] >= 0
+
+
+def test_service_thread_restart_during_a_kernel(G, tmp_path):
+    """A service thread is stopped and restarted (20 ms unserved) while a
+    work-item-grain pwrite kernel runs: its calls wait, complete after the
+    restart, and the file is exact."""
+    import oracle
+    import workloads
+    n = 1 << 18
+    with G.Context(device=0, service_threads=2, staging_bytes=n * 64 + (1 << 20), deadline_ns=5_000_000_000) as ctx:
+        st = ctx.staging(n * 64)
+        p = str(tmp_path / "r.bin")
+        fd = os.open(p, os.O_CREAT | os.O_TRUNC | os.O_WRONLY, 0o644)
+        err = []
+
+        def run():
+            try:
+                ctx.c2_pwrite(fd, n, G.GRAN_ITEM, 256, False, False, workloads.SEED_C2, st, n * 64)
+            except Exception as e:  # reported below
+                err.append(e)
+
+        t = threading.Thread(target=run)
+        t.start()
+        for ring in (0, 1):
+            ctx.service_restart(ring, pause_ns=20_000_000)
+        t.join()
+        os.close(fd)
+        assert not err, err
+        want = str(tmp_path / "w.bin")
+        oracle.c2_pwrite(want, n, 1)
+        assert open(p, "rb").read() == open(want, "rb").read()
+        assert ctx.status() == [0] * G.ST_WORDS
