@@ -32,6 +32,12 @@
  *
  * Pointer arguments must be addresses the host can use: pinned host-mapped
  * memory (genesys_staging), or memory the GPU obtained through mmap.
+ *
+ * Checked builds (GENESYS_DEVICE_CHECKS defined) test the indices this file
+ * and the workload kernels compute (slot, ring, buffer offsets) before using
+ * them; a failed check counts in dev.status[GENESYS_ST_BAD_ARGS], records
+ * -EINVAL as the first error and skips the access, so a bug shows as a status
+ * word instead of a fault.
  */
 #ifndef GENESYS_DEVICE_CUH
 #define GENESYS_DEVICE_CUH
@@ -131,6 +137,20 @@ __device__ __forceinline__ void note_error(const genesys_dev &g, int64_t code) {
   if (code == -kETIMEDOUT) atomicAdd(reinterpret_cast<int *>(&g.status[GENESYS_ST_TIMEOUTS]), 1);
 }
 
+/* Checked builds: true if `ok`, else count the failure and return false. */
+__device__ __forceinline__ bool dcheck(const genesys_dev &g, bool ok) {
+#ifdef GENESYS_DEVICE_CHECKS
+  if (!ok) {
+    atomicAdd(reinterpret_cast<int *>(&g.status[GENESYS_ST_BAD_ARGS]), 1);
+    atomicCAS(reinterpret_cast<int *>(&g.status[GENESYS_ST_FIRST_ERROR]), 0, -22);
+  }
+  return ok;
+#else
+  (void)g;
+  return true || ok;
+#endif
+}
+
 __device__ __forceinline__ void note_latency(const genesys_dev &g, uint64_t t0) {
   if (g.lat_cap == 0) return;
   uint32_t i = atomicAdd(g.lat_count, 1u);
@@ -156,6 +176,7 @@ __device__ __forceinline__ int64_t slot_try_claim(const genesys_dev &g, uint32_t
                                                   uint64_t t0) {
   uint32_t s = hint % g.n_slots;
   for (uint32_t probe = 0; probe < 32; ++probe) {
+    if (!dcheck(g, s < g.n_slots)) return -kETIMEDOUT;
     if (atomicCAS(&g.owner[s], 0u, 1u) == 0u) {
       __threadfence();
       const uint32_t sq = ld_relaxed_gpu(&g.seq[s]);
@@ -218,6 +239,7 @@ __device__ __forceinline__ uint32_t slot_fill(const genesys_dev &g, uint32_t s, 
 /* Doorbell for one published slot (one thread); returns its ring position. */
 __device__ __forceinline__ uint32_t ring_one(const genesys_dev &g, uint32_t s) {
   const uint32_t r = ring_of(g, s);
+  if (!dcheck(g, r < g.n_rings && s < g.n_slots)) return 0;
   const uint32_t pos = atomicAdd(&g.ring_tail[r * 32u], 1u);
   st_release_sys(g.rings + (size_t)r * (g.ring_mask + 1u) + (pos & g.ring_mask), GENESYS_RING_ENTRY(pos, s));
   return pos;
@@ -231,6 +253,7 @@ __device__ __forceinline__ uint32_t ring_one(const genesys_dev &g, uint32_t s) {
  * instead of one per lane.  Returns the calling lane's ring position. */
 __device__ __forceinline__ uint32_t ring_warp(const genesys_dev &g, uint32_t mask, uint32_t s) {
   const uint32_t r = ring_of(g, s);
+  dcheck(g, r < g.n_rings && s < g.n_slots);
   const uint32_t peers = __match_any_sync(mask, r);
   const uint32_t lane = lane_id();
   const uint32_t leader = __ffs(peers) - 1;
@@ -287,6 +310,7 @@ constexpr uint32_t kMaxNapNs = 100000;
 __device__ __forceinline__ int64_t slot_wait_ring(const genesys_dev &g, uint32_t s, uint32_t sq, uint32_t r,
                                                   uint32_t pos, uint64_t t0) {
   const uint32_t copy = (hw_lane_id() >> 5) % GENESYS_RING_DONE_COPIES;
+  if (!dcheck(g, r < g.n_rings && s < g.n_slots)) return -kETIMEDOUT;
   const uint64_t *fin_word = g.ring_done + ((size_t)r * GENESYS_RING_DONE_COPIES + copy) * 8u;
   uint32_t ns = g.poll_min_ns;
   const uint32_t cap = g.poll_max_ns;

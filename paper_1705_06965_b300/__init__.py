@@ -18,7 +18,9 @@ from typing import Optional
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libgenesys.so")
+# GENESYS_LIBRARY=checked selects the build with device-side index checks
+LIB_PATH = os.path.join(_PKG, "libgenesys_checked.so" if os.environ.get("GENESYS_LIBRARY") == "checked"
+                        else "libgenesys.so")
 
 # x86-64 system call numbers (<asm/unistd_64.h>)
 SYS_read, SYS_write, SYS_close, SYS_mmap, SYS_munmap = 0, 1, 3, 9, 11

@@ -1,6 +1,11 @@
 """Build libgenesys.so (runtime + sm_103a kernels) in-tree with nvcc.
 
-    python -m paper_1705_06965_b300.build
+    python -m paper_1705_06965_b300.build                  # libgenesys.so
+    python -m paper_1705_06965_b300.build --device-checks  # libgenesys_checked.so
+
+The checked library compiles the device-side index checks
+(GENESYS_DEVICE_CHECKS: a failed check is counted in a status word instead of
+faulting); the binding loads it when GENESYS_LIBRARY=checked.
 """
 from __future__ import annotations
 
@@ -13,6 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libgenesys.so")
+LIB_CHECKED = os.path.join(PKG, "libgenesys_checked.so")
 
 SOURCES = ["runtime.cpp", "workloads.cu", "wordcount.cu", "serve.cu", "kv.cu", "echo.cu"]
 HEADERS = [os.path.join(INCLUDE, h) for h in ("genesys.h", "genesys_layout.h", "genesys_device.cuh")] + [
@@ -35,24 +41,28 @@ def command(out: str = LIB, extra: list[str] | None = None) -> list[str]:
             *(extra or [])]
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+def stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, s) for s in SOURCES] + HEADERS
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if force or stale():
-        cmd = command(extra=["-Xptxas", "-v"] if verbose else None)
-        r = subprocess.run(cmd, capture_output=True, text=True)
+def build(force: bool = False, verbose: bool = False, device_checks: bool = False) -> str:
+    lib = LIB_CHECKED if device_checks else LIB
+    if force or stale(lib):
+        extra = ["-Xptxas", "-v"] if verbose else []
+        if device_checks:
+            extra.append("-DGENESYS_DEVICE_CHECKS")
+        r = subprocess.run(command(lib, extra), capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
         if verbose:
             print(r.stdout + r.stderr)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                device_checks="--device-checks" in sys.argv))

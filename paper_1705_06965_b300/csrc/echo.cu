@@ -73,8 +73,8 @@ inline void set_buffers(int fd) {
 // with the whole block: the 16-byte chunks of all messages are spread over
 // the threads, four loads in flight per thread.  Receive buffers are read
 // with ld.global.cv (the host rewrote them since the last batch).
-__device__ void copy_messages(const uint8_t *src, uint8_t *dst, uint32_t stride, const uint32_t *len, uint32_t n,
-                              uint32_t *prefix /* smem, kMaxBatch + 1 */) {
+__device__ void copy_messages(const genesys_dev &g, const uint8_t *src, uint8_t *dst, uint32_t stride,
+                              const uint32_t *len, uint32_t n, uint32_t *prefix /* smem, kMaxBatch + 1 */) {
   if (threadIdx.x == 0) {
     uint32_t c = 0;
     for (uint32_t i = 0; i < n; ++i) { prefix[i] = c; c += (len[i] + 15) >> 4; }
@@ -94,6 +94,7 @@ __device__ void copy_messages(const uint8_t *src, uint8_t *dst, uint32_t stride,
         uint32_t lo = 0, hi = n;  // message m with prefix[m] <= c < prefix[m + 1]
         while (hi - lo > 1) { const uint32_t mid = (lo + hi) >> 1; if (prefix[mid] <= c) lo = mid; else hi = mid; }
         at[u] = lo * stride + ((c - prefix[lo]) << 4);
+        if (!dcheck(g, lo < n && ((c - prefix[lo]) << 4) + 16 <= stride)) { at[u] = ~0u; continue; }
         v[u] = __ldcv(reinterpret_cast<const uint4 *>(src + at[u]));
       }
     }
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(1024) echo_server_kernel(genesys_dev g, const 
     // a GENESYS_ECHO_STOP_BYTES datagram is the last one its socket gets
     const bool stop = s_len[m - 1] == GENESYS_ECHO_STOP_BYTES;
     const uint32_t echo = stop ? m - 1 : m;
-    copy_messages(rbuf, sbuf, stride, s_len, echo, s_prefix);
+    copy_messages(g, rbuf, sbuf, stride, s_len, echo, s_prefix);
     if (kBatch) {
       for (uint32_t i = threadIdx.x; i < echo; i += blockDim.x) {
         H->siov[i].iov_len = s_len[i];

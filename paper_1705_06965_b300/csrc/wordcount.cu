@@ -119,7 +119,8 @@ __device__ __forceinline__ uint32_t sep_bits4(uint32_t x) {
 // distance to the next separator bit, so only tokens of a query's length
 // range are assembled byte by byte and looked up in the query hash table.
 __device__ __noinline__ void c3_window(C3Smem &S, const uint8_t *tile, uint32_t base, uint32_t p0, uint32_t len,
-                                       uint64_t avail, uint64_t off) {
+                                       uint64_t avail, uint64_t off, uint32_t tile_bytes, const genesys_dev &g) {
+  if (!dcheck(g, base + 48 <= tile_bytes + 48 && (base & 15) == 0)) return;
   uint64_t sep = 0;  // bit j: window byte j (= b[p0 - 1 + j]) is a separator
 #pragma unroll
   for (int v = 0; v < 3; ++v) {
@@ -164,8 +165,8 @@ __device__ __noinline__ void c3_window(C3Smem &S, const uint8_t *tile, uint32_t 
 // several 16-byte loads per thread, all in flight together (the bytes cross
 // the host link: one load per round trip would leave the block waiting at the
 // barrier); thread t then owns the 16-position windows t, t + threads, ...
-__device__ void c3_scan(C3Smem &S, uint8_t *tile, uint32_t tile_bytes, const uint8_t *buf, uint64_t buf_cap,
-                        uint64_t off, uint32_t len, uint64_t avail) {
+__device__ void c3_scan(const genesys_dev &g, C3Smem &S, uint8_t *tile, uint32_t tile_bytes, const uint8_t *buf,
+                        uint64_t buf_cap, uint64_t off, uint32_t len, uint64_t avail) {
   if (avail < len) len = (uint32_t)avail;
   const uint32_t span = tile_bytes + 32;  // s[i] = b[t0 + i - 1], i < span
   for (uint32_t t0 = 0; t0 < len; t0 += tile_bytes) {
@@ -175,7 +176,7 @@ __device__ void c3_scan(C3Smem &S, uint8_t *tile, uint32_t tile_bytes, const uin
     }
     __syncthreads();
     for (uint32_t base = threadIdx.x * 16; base < tile_bytes && t0 + base < len; base += blockDim.x * 16)
-      c3_window(S, tile, base, t0 + base, len, avail, off);
+      c3_window(S, tile, base, t0 + base, len, avail, off, tile_bytes, g);
     __syncthreads();
   }
 }
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(1024, 1) c3_plain_kernel(genesys_dev g, const 
     c3_read_args(it, buf, &dst, &n, &foff);
     const int64_t r = call<GROUP, STRONG, BLOCKING>(g, SYS_pread64, (uint64_t)it.fd, dst, n, foff);
     if (r < 0) break;
-    c3_scan(S, tile, tile_bytes, buf, buf_bytes, it.off, it.len, c3_avail(it, r));
+    c3_scan(g, S, tile, tile_bytes, buf, buf_bytes, it.off, it.len, c3_avail(it, r));
     __syncthreads();  // S.item is rewritten by the next pop
   }
   c3_flush(S, Q->nq, counts);
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(1024, 1) c3_batched_kernel(genesys_dev g, cons
     const int64_t r = S.r;
     if (idx >= n_items || r < 0) break;
     const C3Item it = items[idx];
-    c3_scan(S, tile, tile_bytes, bufs[k & 1], buf_bytes, it.off, it.len, c3_avail(it, r));
+    c3_scan(g, S, tile, tile_bytes, bufs[k & 1], buf_bytes, it.off, it.len, c3_avail(it, r));
     __syncthreads();  // buffer k&1 is free for the prefetch two items ahead; S is rewritten next
   }
   c3_flush(S, Q->nq, counts);
