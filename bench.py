@@ -172,6 +172,49 @@ def host_pwrite_peak(fd, buf, nbytes, repeats=3, chunks=(256 << 10, 1 << 20, 4 <
     return best, best_chunk
 
 
+def host_probes(torch, local, scan_path):
+    """What the design depends on, measured on this machine: the host CPU, SM
+    count, whether the GPU has native atomics on host memory (the protocol
+    never needs them), and tmpfs pread GB/s by thread count (1 MiB preads of
+    the 1 GiB scan file)."""
+    import platform
+    import threading
+    import numpy as np
+    out = {"machine": platform.machine(), "host_cpus": os.cpu_count(),
+           "sm_count": torch.cuda.get_device_properties(local).multi_processor_count}
+    try:
+        with open("/proc/cpuinfo") as f:
+            out["cpu_model"] = next((ln.split(":", 1)[1].strip() for ln in f if ln.startswith("model name")), None)
+    except OSError:
+        pass
+    try:
+        from cuda.bindings import runtime as rt
+        err, v = rt.cudaDeviceGetAttribute(rt.cudaDeviceAttr.cudaDevAttrHostNativeAtomicSupported, local)
+        out["host_native_atomics"] = int(v) if err == rt.cudaError_t.cudaSuccess else None
+    except Exception:  # cuda-bindings missing: the probe is informational
+        out["host_native_atomics"] = None
+    if scan_path:
+        size = os.path.getsize(scan_path)
+        chunk = 1 << 20
+        rates = {}
+        for n_threads in (1, 4, 12):
+            fd = os.open(scan_path, os.O_RDONLY)
+            bufs = [np.empty(chunk, np.uint8) for _ in range(n_threads)]
+
+            def reader(t):
+                for off in range(t * chunk, size, n_threads * chunk):
+                    os.preadv(fd, [bufs[t]], off)
+
+            t0 = time.perf_counter()
+            th = [threading.Thread(target=reader, args=(t,)) for t in range(n_threads)]
+            [x.start() for x in th]
+            [x.join() for x in th]
+            rates[str(n_threads)] = round(size / (time.perf_counter() - t0) / 1e9, 2)
+            os.close(fd)
+        out["tmpfs_pread_GB_per_s_by_threads"] = rates
+    return out
+
+
 def hbm_peak() -> float:
     """Measured HBM copy bandwidth of this GPU model (GB/s), from the peaks file
     beside this script, else the nominal 7,700 GB/s.  The scans read HBM only
@@ -844,6 +887,7 @@ def run_genesys(args):
                                       f"{host_chunk >> 10} KiB calls; measured)"}
     link = host_link_peak(torch)
     link["round_trip_ns"] = G.link_pingpong(local, rounds=20000)  # GPU <-> host flag, the floor of a blocking call
+    probes = host_probes(torch, local, rig.scan_path)
     extras = profile_extras(args, rig, local, rank, link) if args.extras else {}
     # dominant kernel of the timed region and its host-link roofline
     tot = {k: sum(v) for k, v in kernel_ms.items()}
@@ -898,6 +942,7 @@ def run_genesys(args):
         **extras,
         "autotuned_step": {"best": step_cfg, "table": step_table},
         "host_link_GB_per_s": link,
+        "probes": probes,
         "service": {k: stats[k] for k in ("requests", "os_calls", "batches", "bytes", "failed", "busy_ns")},
         "roofline": roofline,
         "cpu_baseline": cpu,
