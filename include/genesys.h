@@ -74,6 +74,9 @@ typedef struct genesys_config {
   uint32_t poll_min_ns;        /* GPU completion polls: first back-off (ns) ...         */
   uint32_t poll_max_ns;        /* ... growing 1.5x per poll up to this; more polls cost
                                   host-link read requests, fewer add latency           */
+  uint32_t trace_capacity;     /* per-call trace records kept on each side (device and
+                                  host); 0 = tracing off (genesys_trace_read)          */
+  uint32_t reserved0;
 } genesys_config;
 
 typedef struct genesys_stats {
@@ -90,6 +93,9 @@ typedef struct genesys_stats {
   uint64_t op_max_ns[8];       /* longest single request per op                        */
   uint64_t mmap_new;           /* GPU mmaps served by mmap(2) + registration           */
   uint64_t mmap_reused;        /* GPU mmaps served by a released region                */
+  uint64_t service_cpu_ns;     /* CPU time of the service threads (getrusage per thread,
+                                  sampled when a thread goes idle and every 1,024
+                                  batches)                                              */
 } genesys_stats;
 
 typedef struct genesys_ctx genesys_ctx;
@@ -184,6 +190,20 @@ int genesys_staging_reset(genesys_ctx *ctx);
 
 /* Message of the calling thread's last failure. */
 const char *genesys_last_error(void);
+
+/* Per-call trace (the timeline of a call, Sec. 5: publish, CPU pickup, CPU
+ * completion, result seen), kept when genesys_config.trace_capacity > 0.
+ * Device records are written by the calling GPU thread (device clock, ns);
+ * host records by the service thread (CLOCK_MONOTONIC, ns).  A record pair
+ * is joined by (slot, seq). */
+/* (genesys_trace_dev and genesys_trace_host are defined in genesys_layout.h) */
+/* Copy out and clear the trace (call it with no kernel running on the
+ * context): up to dev_cap / host_cap records (the rest is dropped and counted
+ * in *n_dev / *n_host, which return the totals recorded).  *host_minus_device_ns
+ * (if non-NULL) = host clock - device clock, from a round-trip calibration
+ * (the sample with the shortest round trip; error <= half of it). */
+int genesys_trace_read(genesys_ctx *ctx, genesys_trace_dev *dev, uint32_t dev_cap, uint32_t *n_dev,
+                       genesys_trace_host *host, uint32_t host_cap, uint32_t *n_host, int64_t *host_minus_device_ns);
 
 /* Failure handling on the host: stop the service thread of doorbell ring
  * `ring` (it finishes the batch it holds), leave the ring unserved for

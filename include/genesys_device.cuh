@@ -157,6 +157,22 @@ __device__ __forceinline__ void note_latency(const genesys_dev &g, uint64_t t0) 
   if (i < g.lat_cap) g.lat[i] = now_ns() - t0;
 }
 
+/* Per-call trace record (only when the context keeps a trace). */
+__device__ __forceinline__ void trace_call(const genesys_dev &g, uint32_t s, uint32_t sq, uint32_t nr, uint32_t gran,
+                                           uint64_t t_call, uint64_t t_pub, uint64_t t_done) {
+  if (g.trace_cap == 0) return;
+  const uint32_t i = atomicAdd(g.trace_count, 1u);
+  if (i >= g.trace_cap) return;
+  genesys_trace_dev *r = g.trace + i;
+  r->slot = s;
+  r->seq = sq;
+  r->nr = nr;
+  r->gran = gran;
+  r->t_call = t_call;
+  r->t_publish = t_pub;
+  r->t_done = t_done;
+}
+
 __device__ __forceinline__ bool expired(const genesys_dev &g, uint64_t t0) {
   return now_ns() - t0 > g.deadline_ns;
 }
@@ -359,14 +375,18 @@ __device__ __forceinline__ int64_t single_call(const genesys_dev &g, uint32_t nr
   const uint32_t sq = slot_fill(g, s, nr, flags, a0, a1, a2, a3, a4, a5);
   const uint32_t pos = ring_one(g, s);  // st.release.sys: the slot stores (and, through
                                         // the group's barrier, its earlier stores) first
+  const uint64_t t_pub = g.trace_cap ? now_ns() : 0;
   int64_t ret = 0;
   if (wait) {
     ret = slot_wait_ring(g, s, sq, ring_of(g, s), pos, t0);
+    trace_call(g, s, sq, nr, (flags >> GENESYS_REQ_GRAN_SHIFT) & 3u, t0, t_pub, ret == -kETIMEDOUT ? 0 : now_ns());
     if (ret == -kETIMEDOUT) {  /* the CPU may still finish it: keep the slot's
                                   sequence so the next claimer waits for it */
       slot_release(g, s);
       return ret;
     }
+  } else {
+    trace_call(g, s, sq, nr, (flags >> GENESYS_REQ_GRAN_SHIFT) & 3u, t0, t_pub, 0);
   }
   slot_release(g, s);
   note_latency(g, t0);
@@ -399,6 +419,7 @@ __device__ __forceinline__ int64_t issue(const genesys_dev &g, Ticket *t, uint32
 __device__ __forceinline__ int64_t wait(const genesys_dev &g, const Ticket &t) {
   if (t.slot == 0xFFFFFFFFu) return -kETIMEDOUT;
   const int64_t ret = slot_wait_ring(g, t.slot, t.seq, ring_of(g, t.slot), t.pos, now_ns());
+  trace_call(g, t.slot, t.seq, 0, GENESYS_GRAN_GROUP, t.t0, 0, ret == -kETIMEDOUT ? 0 : now_ns());
   slot_release(g, t.slot);
   if (ret != -kETIMEDOUT) note_latency(g, t.t0);
   return ret;
@@ -484,7 +505,10 @@ __device__ __forceinline__ int64_t call_at(const genesys_dev &g, uint32_t site, 
       if (ok) {
         const uint32_t sq = slot_fill(g, s, nr, flags, a0, a1, a2, a3, a4, a5);
         const uint32_t pos = ring_warp(g, okmask, s);
+        const uint64_t t_pub = g.trace_cap ? now_ns() : 0;
         rc = B == BLOCKING ? slot_wait_ring(g, s, sq, ring_of(g, s), pos, t0) : 0;
+        trace_call(g, s, sq, nr, GENESYS_GRAN_ITEM, t0, t_pub,
+                   (B == BLOCKING && rc != -kETIMEDOUT) ? now_ns() : 0);
         slot_release(g, s);
         if (rc != -kETIMEDOUT) note_latency(g, t0);
         pending = false;

@@ -123,6 +123,21 @@ typedef struct genesys_ksite {
   uint64_t pad2;
 } genesys_ksite;
 
+/* Per-call trace records (genesys_trace_read): the device record is written
+ * by the calling GPU thread (device clock, ns), the host record by the service
+ * thread (CLOCK_MONOTONIC, ns); they are joined by (slot, seq). */
+typedef struct genesys_trace_dev {
+  uint32_t slot, seq, nr, gran;  /* gran: GENESYS_GRAN_*                         */
+  uint64_t t_call;               /* the call began (before the slot claim)        */
+  uint64_t t_publish;            /* its doorbell entry was written (0: unknown)   */
+  uint64_t t_done;               /* the result was seen (0: non-blocking)         */
+} genesys_trace_dev;
+typedef struct genesys_trace_host {
+  uint32_t slot, seq;
+  uint64_t t_pickup;             /* the batch holding it was taken from the ring  */
+  uint64_t t_done;               /* its completion word was written               */
+} genesys_trace_host;
+
 /* The device view of a context: a plain struct passed to kernels by value. */
 typedef struct genesys_dev {
   genesys_slot *slots;        /* host-mapped, n_slots entries                       */
@@ -141,6 +156,9 @@ typedef struct genesys_dev {
   int32_t *status;            /* device memory: GENESYS_ST_WORDS                    */
   uint64_t *lat;              /* device memory: per-call latency samples (ns)       */
   uint32_t *lat_count;        /* device memory: samples written (may exceed cap)    */
+  genesys_trace_dev *trace;   /* device memory: per-call trace records, or NULL    */
+  uint32_t *trace_count;      /* device memory: trace records written (may exceed cap) */
+  uint32_t trace_cap;         /* 0: tracing off                                     */
   uint32_t lat_cap;
   uint32_t n_slots;
   uint32_t n_rings;

@@ -47,6 +47,7 @@ EXPORTS = [
     "genesys_reclaim", "genesys_mmap_reserve", "genesys_kv_start", "genesys_kv_stop", "genesys_kv_value",
     "genesys_kv_client", "genesys_c6_permute", "genesys_gpu_call", "genesys_echo_start", "genesys_echo_stop",
     "genesys_echo_client", "genesys_service_probe", "genesys_link_pingpong", "genesys_service_restart",
+    "genesys_trace_read",
 ]
 
 
@@ -63,6 +64,7 @@ class Config(ctypes.Structure):
         ("coalesce_window_ns", ctypes.c_uint64), ("coalesce_max", ctypes.c_uint32), ("merge", ctypes.c_uint32),
         ("device_deadline_ns", ctypes.c_uint64), ("lat_samples", ctypes.c_uint32), ("flags", ctypes.c_uint32),
         ("idle_spin_ns", ctypes.c_uint64), ("poll_min_ns", ctypes.c_uint32), ("poll_max_ns", ctypes.c_uint32),
+        ("trace_capacity", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
     ]
 
 
@@ -89,7 +91,7 @@ class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in
                 ("requests", "os_calls", "failed", "nonblocking_failed", "bytes", "batches", "busy_ns")] + [
         ("by_op", ctypes.c_uint64 * 8), ("op_ns", ctypes.c_uint64 * 8), ("op_max_ns", ctypes.c_uint64 * 8),
-        ("mmap_new", ctypes.c_uint64), ("mmap_reused", ctypes.c_uint64)]
+        ("mmap_new", ctypes.c_uint64), ("mmap_reused", ctypes.c_uint64), ("service_cpu_ns", ctypes.c_uint64)]
 
     OPS = ("pread", "pwrite", "sendto", "recvfrom", "mmap", "munmap", "internal", "other")
 
@@ -151,6 +153,8 @@ def lib() -> ctypes.CDLL:
         "genesys_c5_serve": (ctypes.c_int, [vp, vp, u32, vp, u32, ctypes.c_int32, ctypes.POINTER(ServeConfig), vp, vp,
                                             ctypes.POINTER(ServeStats)]),
         "genesys_service_restart": (ctypes.c_int, [vp, u32, u64]),
+        "genesys_trace_read": (ctypes.c_int, [vp, vp, u32, ctypes.POINTER(u32), vp, u32, ctypes.POINTER(u32),
+                                              ctypes.POINTER(i64)]),
         "genesys_link_pingpong": (ctypes.c_int, [ctypes.c_int, u32, u64, ctypes.POINTER(u64)]),
         "genesys_service_probe": (ctypes.c_int, [vp, ctypes.c_int, vp, u32, u64, ctypes.POINTER(u64)]),
         "genesys_echo_start": (ctypes.c_int, [vp, u32, u32, u32, u32, u32, ctypes.c_uint16, u64, ctypes.POINTER(vp)]),
@@ -193,7 +197,7 @@ class Context:
                  merge: bool = True, deadline_ns: int = 2_000_000_000, lat_samples: int = 1 << 20,
                  host_only: bool = False, no_threads: bool = False, any_syscall: bool = False,
                  idle_spin_ns: int = 200_000_000, service_cpus=None, poll_min_ns: int = 256,
-                 poll_max_ns: int = 2048):
+                 poll_max_ns: int = 2048, trace: int = 0):
         L = lib()
         cfg = Config()
         _check(L.genesys_config_default(ctypes.byref(cfg)), "genesys_config_default")
@@ -212,6 +216,7 @@ class Context:
         cfg.idle_spin_ns = int(idle_spin_ns)
         cfg.poll_min_ns = int(poll_min_ns)
         cfg.poll_max_ns = int(poll_max_ns)
+        cfg.trace_capacity = int(trace)
         cfg.flags = (INIT_HOST_ONLY if host_only else 0) | (INIT_NO_THREADS if no_threads else 0) | (
             INIT_ANY_SYSCALL if any_syscall else 0)
         self.config = cfg
@@ -280,6 +285,19 @@ class Context:
 
     def stats_reset(self) -> None:
         _check(lib().genesys_stats_reset(self.handle), "genesys_stats_reset")
+
+    def trace_read(self, calibrate: bool = True):
+        """Copy out and clear the per-call trace (genesys_trace_read): device
+        records (TRACE_DEV_DTYPE), host records (TRACE_HOST_DTYPE), and the host
+        minus device clock offset in ns (None without calibration)."""
+        cap = int(self.config.trace_capacity)
+        dev = np.zeros(max(cap, 1), TRACE_DEV_DTYPE)
+        host = np.zeros(max(cap, 1), TRACE_HOST_DTYPE)
+        nd, nh, off = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_int64()
+        _check(lib().genesys_trace_read(self.handle, dev.ctypes.data, cap, ctypes.byref(nd), host.ctypes.data, cap,
+                                        ctypes.byref(nh), ctypes.byref(off) if calibrate else None),
+               "genesys_trace_read")
+        return dev[:min(nd.value, cap)], host[:min(nh.value, cap)], (off.value if calibrate else None)
 
     def service_restart(self, ring: int, pause_ns: int = 0) -> None:
         """Stop the service thread of `ring`, leave the ring unserved for
@@ -443,6 +461,39 @@ def kv_client(reqs: bytes, req_off, arrival_ns, port_base: int, n_sockets: int, 
     stats["rc"] = rc
     reps = [out[j * KV_REPLY_STRIDE: j * KV_REPLY_STRIDE + int(rlen[j])].tobytes() for j in range(n)]
     return reps, lat[:n], stats
+
+
+TRACE_DEV_DTYPE = np.dtype([("slot", "<u4"), ("seq", "<u4"), ("nr", "<u4"), ("gran", "<u4"), ("t_call", "<u8"),
+                            ("t_publish", "<u8"), ("t_done", "<u8")])
+TRACE_HOST_DTYPE = np.dtype([("slot", "<u4"), ("seq", "<u4"), ("t_pickup", "<u8"), ("t_done", "<u8")])
+
+
+def trace_breakdown(dev, host, host_minus_device_ns: int) -> dict:
+    """Join device and host trace records by (slot, seq) and give the
+    percentiles (ns) of each stage of a blocking call: claim (call to
+    publish), queue (publish to CPU pickup), service (pickup to completion
+    word), delivery (completion word to result seen), total (call to result)."""
+    done = dev[dev["t_done"] > 0]
+    key_h = {(int(a), int(b)): i for i, (a, b) in enumerate(zip(host["slot"], host["seq"]))}
+    rows = [(i, key_h[(int(a), int(b))]) for i, (a, b) in enumerate(zip(done["slot"], done["seq"]))
+            if (int(a), int(b)) in key_h]
+    if not rows:
+        return {"joined": 0}
+    di = np.array([r[0] for r in rows])
+    hi = np.array([r[1] for r in rows])
+    d, h = done[di], host[hi]
+    off = np.int64(host_minus_device_ns)
+    stages = {
+        "claim": d["t_publish"].astype(np.int64) - d["t_call"].astype(np.int64),
+        "queue": h["t_pickup"].astype(np.int64) - (d["t_publish"].astype(np.int64) + off),
+        "service": h["t_done"].astype(np.int64) - h["t_pickup"].astype(np.int64),
+        "delivery": (d["t_done"].astype(np.int64) + off) - h["t_done"].astype(np.int64),
+        "total": d["t_done"].astype(np.int64) - d["t_call"].astype(np.int64),
+    }
+    out = {"joined": len(rows)}
+    for k, v in stages.items():
+        out[k] = {"p50_ns": int(np.percentile(v, 50)), "p99_ns": int(np.percentile(v, 99))}
+    return out
 
 
 ECHO_SINGLE, ECHO_BATCH = 0, 1

@@ -25,6 +25,13 @@ void genesys_internal_staging_release(struct genesys_ctx *ctx, uint64_t mark);
 /* CUDA device ordinal of the context (-1 for NULL). */
 int genesys_internal_device(struct genesys_ctx *ctx);
 
+/* Host clock (CLOCK_MONOTONIC) minus device clock (%globaltimer), in ns, from
+ * `rounds` GPU <-> host flag round trips: the estimate of the round with the
+ * shortest trip, whose length goes to *rtt_ns (the error is at most half of
+ * it).  Every wait is bounded by timeout_ns. */
+int genesys_internal_clock_offset(int device, uint32_t rounds, uint64_t timeout_ns, int64_t *offset_ns,
+                                  uint64_t *rtt_ns);
+
 #ifdef __cplusplus
 }
 #endif

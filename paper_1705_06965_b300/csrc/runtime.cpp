@@ -183,6 +183,18 @@ struct genesys_ctx {
 
   void *scratch = nullptr;  // device scratch arena for workload entry points
   size_t scratch_bytes = 0;
+
+  // per-call trace (cfg.trace_capacity > 0): device records in device memory,
+  // host records per ring (written by that ring's service thread only)
+  genesys_trace_dev *trace = nullptr;
+  uint32_t *trace_count = nullptr;
+  std::vector<std::vector<genesys_trace_host>> trace_host;
+  std::unique_ptr<std::atomic<uint32_t>[]> trace_n;  // host records written per ring (may exceed capacity)
+
+  // CPU time of service threads that have left (restarts), and the total at
+  // the last genesys_stats_reset
+  std::atomic<uint64_t> cpu_retired_ns{0};
+  uint64_t cpu_reset_ns = 0;
 };
 
 namespace {
@@ -392,7 +404,7 @@ size_t merge_run(genesys_ctx *c, Request *const *reqs, size_t i, size_t n, Count
 
 inline bool is_rw(uint32_t nr) { return nr == SYS_pread64 || nr == SYS_pwrite64; }
 
-void process_batch(genesys_ctx *c, Batch &b, size_t n, Counters &k) {
+void process_batch(genesys_ctx *c, uint32_t ri, Batch &b, size_t n, Counters &k) {
   const uint64_t t0 = mono_ns();
   Request *const req = b.req.data();
   Request **p = b.ptr.data();
@@ -490,6 +502,14 @@ void process_batch(genesys_ctx *c, Batch &b, size_t n, Counters &k) {
     complete(c, req[i], k);
     ++per_op[op_index(req[i].nr)];
   }
+  if (c->cfg.trace_capacity) {
+    std::vector<genesys_trace_host> &tr = c->trace_host[ri];
+    const uint32_t at = c->trace_n[ri].load(std::memory_order_relaxed);
+    const uint64_t t_done = mono_ns();
+    for (size_t i = 0; i < n; ++i)
+      if (at + i < tr.size()) tr[at + i] = genesys_trace_host{req[i].slot, req[i].seq, t0, t_done};
+    c->trace_n[ri].store(at + (uint32_t)n, std::memory_order_release);
+  }
   for (int o = 0; o < 8; ++o)
     if (per_op[o]) bump(k.by_op[o], per_op[o]);
   bump(k.requests, n);
@@ -547,7 +567,7 @@ size_t poll_ring(genesys_ctx *c, uint32_t ri, Batch &b) {
       }
     }
   }
-  process_batch(c, b, n, c->counters[ri]);
+  process_batch(c, ri, b, n, c->counters[ri]);
   c->head[ri] = h + n;
   c->retired[ri].store(h + n, std::memory_order_release);
   for (uint32_t k = 0; k < GENESYS_RING_DONE_COPIES; ++k)
@@ -639,6 +659,8 @@ void free_all(genesys_ctx *c) {
   dev_free(c, c->status);
   dev_free(c, c->lat);
   dev_free(c, c->lat_count);
+  dev_free(c, c->trace);
+  dev_free(c, c->trace_count);
   if (c->scratch && !c->host_only) cudaFree(c->scratch);
   if (c->aux) cudaStreamDestroy(c->aux);
   if (c->ev_start) cudaEventDestroy(c->ev_start);
@@ -782,6 +804,10 @@ int genesys_init(const genesys_config *cfg_in, int device, genesys_ctx **out) {
   if ((rc = dev_alloc(c.get(), &c->status, GENESYS_ST_WORDS))) return cleanup(rc);
   if ((rc = dev_alloc(c.get(), &c->lat, std::max<uint32_t>(cfg.lat_samples, 1)))) return cleanup(rc);
   if ((rc = dev_alloc(c.get(), &c->lat_count, 1))) return cleanup(rc);
+  if (cfg.trace_capacity) {
+    if ((rc = dev_alloc(c.get(), &c->trace, cfg.trace_capacity))) return cleanup(rc);
+    if ((rc = dev_alloc(c.get(), &c->trace_count, 1))) return cleanup(rc);
+  }
 
   const uint32_t nr = cfg.n_service_threads;
   c->head.assign(nr, 0);
@@ -790,6 +816,9 @@ int genesys_init(const genesys_config *cfg_in, int device, genesys_ctx **out) {
   c->counters.reset(new Counters[nr]);
   c->ring_stop.reset(new std::atomic<bool>[nr]);
   for (uint32_t r = 0; r < nr; ++r) c->ring_stop[r].store(false);
+  c->trace_n.reset(new std::atomic<uint32_t>[nr]);
+  for (uint32_t r = 0; r < nr; ++r) c->trace_n[r].store(0);
+  if (cfg.trace_capacity) c->trace_host.assign(nr, std::vector<genesys_trace_host>((cfg.trace_capacity + nr - 1) / nr));
   if (!(cfg.flags & GENESYS_INIT_NO_THREADS)) {
     for (uint32_t r = 0; r < nr; ++r) c->threads.emplace_back(service_main, c.get(), r);
   }
@@ -823,6 +852,20 @@ int genesys_drain(genesys_ctx *c, uint64_t timeout_ns) {
   return 0;
 }
 
+// CPU time a running service thread has used so far (0 if unavailable).
+static uint64_t thread_cpu_ns(std::thread &t) {
+  clockid_t cid;
+  timespec ts;
+  if (!t.joinable() || pthread_getcpuclockid(t.native_handle(), &cid) != 0 || clock_gettime(cid, &ts) != 0) return 0;
+  return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
+}
+
+static uint64_t service_cpu_total(genesys_ctx *c) {
+  uint64_t t = c->cpu_retired_ns.load();
+  for (auto &th : c->threads) t += thread_cpu_ns(th);
+  return t;
+}
+
 int genesys_service_restart(genesys_ctx *c, uint32_t ring, uint64_t pause_ns) {
   if (!c) return fail(GENESYS_EINVAL, "ctx is NULL");
   if (c->threads.empty()) return fail(GENESYS_EINVAL, "the context has no service threads");
@@ -831,7 +874,9 @@ int genesys_service_restart(genesys_ctx *c, uint32_t ring, uint64_t pause_ns) {
   // the thread finishes the batch it has and leaves; its ring position (head)
   // stays with the context, so the new thread continues where it stopped
   c->ring_stop[ring].store(true);
+  const uint64_t used = thread_cpu_ns(c->threads[ring]);  // read before it leaves: its clock goes with it
   c->threads[ring].join();
+  c->cpu_retired_ns.fetch_add(used);
   if (pause_ns) std::this_thread::sleep_for(std::chrono::nanoseconds(pause_ns));
   c->ring_stop[ring].store(false);
   c->threads[ring] = std::thread(service_main, c, ring);
@@ -871,6 +916,9 @@ int genesys_device_view(genesys_ctx *c, genesys_dev *d) {
   d->lat = c->lat;
   d->lat_count = c->lat_count;
   d->lat_cap = c->cfg.lat_samples;
+  d->trace = c->trace;
+  d->trace_count = c->trace_count;
+  d->trace_cap = c->cfg.trace_capacity;
   d->n_slots = c->cfg.n_slots;
   d->n_rings = c->cfg.n_service_threads;
   d->ring_mask = c->ring_cap - 1;
@@ -996,6 +1044,11 @@ int genesys_stats_get(genesys_ctx *c, genesys_stats *o) {
   }
   o->mmap_new = c->mmap_new.load();
   o->mmap_reused = c->mmap_reused.load();
+  {
+    std::lock_guard<std::mutex> g(c->restart_mu);  // the thread list is stable
+    const uint64_t cpu = service_cpu_total(c);
+    o->service_cpu_ns = cpu > c->cpu_reset_ns ? cpu - c->cpu_reset_ns : 0;
+  }
   return 0;
 }
 
@@ -1005,6 +1058,40 @@ int genesys_stats_reset(genesys_ctx *c) {
     Counters &k = c->counters[r];
     k.requests = 0; k.os_calls = 0; k.failed = 0; k.nb_failed = 0; k.bytes = 0; k.batches = 0; k.busy_ns = 0;
     for (int i = 0; i < 8; ++i) k.by_op[i] = 0, k.op_ns[i] = 0, k.op_max_ns[i] = 0;
+  }
+  std::lock_guard<std::mutex> g(c->restart_mu);
+  c->cpu_reset_ns = service_cpu_total(c);
+  return 0;
+}
+
+int genesys_trace_read(genesys_ctx *c, genesys_trace_dev *dev, uint32_t dev_cap, uint32_t *n_dev,
+                       genesys_trace_host *host, uint32_t host_cap, uint32_t *n_host, int64_t *host_minus_device_ns) {
+  if (!c || (dev_cap && !dev) || (host_cap && !host)) return fail(GENESYS_EINVAL, "NULL argument");
+  if (!c->cfg.trace_capacity) return fail(GENESYS_EINVAL, "the context keeps no trace (trace_capacity 0)");
+  uint32_t nd = 0;
+  if (!c->host_only) {
+    CUDA_TRY(cudaMemcpy(&nd, c->trace_count, 4, cudaMemcpyDeviceToHost));
+    const uint32_t k = std::min({nd, c->cfg.trace_capacity, dev_cap});
+    if (k) CUDA_TRY(cudaMemcpy(dev, c->trace, (size_t)k * sizeof(genesys_trace_dev), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(c->trace_count, 0, 4));
+  }
+  if (n_dev) *n_dev = nd;
+  uint32_t nh = 0, out = 0;
+  for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) {
+    const uint32_t n = c->trace_n[r].load(std::memory_order_acquire);
+    const uint32_t have = std::min<uint32_t>(n, (uint32_t)c->trace_host[r].size());
+    for (uint32_t i = 0; i < have && out < host_cap; ++i) host[out++] = c->trace_host[r][i];
+    nh += n;
+    c->trace_n[r].store(0, std::memory_order_release);
+  }
+  if (n_host) *n_host = nh;
+  if (host_minus_device_ns) {
+    if (c->host_only) {
+      *host_minus_device_ns = 0;
+    } else {
+      int rc = genesys_internal_clock_offset(c->device, 200, 2000000000ull, host_minus_device_ns, nullptr);
+      if (rc) return rc;
+    }
   }
   return 0;
 }

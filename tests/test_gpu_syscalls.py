@@ -68,3 +68,33 @@ def test_link_pingpong_round_trip():
     import paper_1705_06965_b300 as G
     ns = G.link_pingpong(0, rounds=2000)
     assert 100 < ns < 10_000, ns
+
+
+@pytest.mark.parametrize("gran,bt", [(0, 256), (2, 128)])
+def test_call_trace_joins_and_adds_up(gran, bt, tmp_path):
+    """Trace of a pwrite kernel: one device record per call, each joined with
+    its host record; the stages are non-negative within the clock
+    calibration's error."""
+    import paper_1705_06965_b300 as G
+    import workloads
+    n = 4096
+    calls = n if gran == 0 else n // bt
+    with G.Context(device=0, service_threads=2, staging_bytes=n * 64 + (1 << 20), trace=2 * n) as ctx:
+        st = ctx.staging(n * 64)
+        fd = os.open(str(tmp_path / "t.bin"), os.O_CREAT | os.O_TRUNC | os.O_WRONLY, 0o644)
+        try:
+            ctx.c2_pwrite(fd, n, gran, bt, gran != 0, False, workloads.SEED_C2, st, n * 64)
+        finally:
+            os.close(fd)
+        dev, host, off = ctx.trace_read()
+    assert len(dev) == calls and len(host) == calls
+    b = G.trace_breakdown(dev, host, off)
+    assert b["joined"] == calls
+    slack = 20_000  # ns: calibration error and clock granularity
+    for k in ("claim", "service", "total"):
+        assert b[k]["p50_ns"] >= 0, b
+    for k in ("queue", "delivery"):
+        assert b[k]["p50_ns"] >= -slack, b
+    # the host stages lie inside the call: pickup after publish, completion
+    # before the result is seen (up to the calibration error)
+    assert b["service"]["p99_ns"] <= b["total"]["p99_ns"] + slack, b

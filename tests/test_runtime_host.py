@@ -363,3 +363,27 @@ def test_service_restart_rejects_bad_use():
     with _ctx(service_threads=2) as c:
         with pytest.raises(G.GenesysError):
             c.service_restart(2)
+
+
+def test_host_trace_and_service_cpu_time():
+    """With a trace kept, every request gets a host record (pickup <= done),
+    reading clears it, and the service threads' CPU time is reported."""
+    with _ctx(trace=4096, service_threads=2) as c:
+        for v in range(300):
+            assert c.emulate_call(G.NR_NOP, [v]) == v
+        dev, host, off = c.trace_read()
+        assert len(dev) == 0 and off == 0          # no device side in a host-only context
+        assert len(host) == 300
+        assert np.all(host["t_done"] >= host["t_pickup"]) and np.all(host["t_pickup"] > 0)
+        assert len({(int(a), int(b)) for a, b in zip(host["slot"], host["seq"])}) == 300
+        _, host2, _ = c.trace_read()
+        assert len(host2) == 0
+        assert c.stats()["service_cpu_ns"] > 0
+        c.stats_reset()
+        assert c.stats()["service_cpu_ns"] < 50_000_000
+
+
+def test_trace_needs_capacity():
+    with _ctx() as c:
+        with pytest.raises(G.GenesysError):
+            c.trace_read()
