@@ -520,6 +520,28 @@ def profile_extras(args, rig, local, rank, link):
     out["fig6_block_permutation"] = study_fig6(G, rig, local)
     out["fig7_coalescing"] = study_fig7(G, rig, local, rank)
     out["fig10_echo"] = study_fig10(G, local, rank)
+    out["call_timeline"] = trace_timeline(G, rig, local)
+    return out
+
+
+def trace_timeline(G, rig, local, n=1 << 16):
+    """Where a blocking call's time goes (per-call trace, clocks aligned by
+    round trips): claim (call to publish), queue (publish to CPU pickup),
+    service (pickup to completion word), delivery (completion word to result
+    seen), at work-item and work-group (256) grain for 2^16 threads."""
+    import workloads
+    out = {}
+    for name, gran, bt in (("work-item", G.GRAN_ITEM, 256), ("work-group-256", G.GRAN_GROUP, 256)):
+        with G.Context(device=local, service_threads=2, coalesce_max=256, staging_bytes=n * 64 + (1 << 20),
+                       trace=2 * n) as ctx:
+            st = ctx.staging(n * 64)
+            ctx.c2_pwrite(rig.fds[n], n, gran, bt, False, False, workloads.SEED_C2, st, n * 64)
+            ctx.trace_read(calibrate=False)
+            ctx.c2_pwrite(rig.fds[n], n, gran, bt, False, False, workloads.SEED_C2, st, n * 64)
+            dev, host, off = ctx.trace_read()
+            b = G.trace_breakdown(dev, host, off)
+            b["service_cpu_ms"] = round(ctx.stats()["service_cpu_ns"] / 1e6, 1)
+            out[name] = b
     return out
 
 
