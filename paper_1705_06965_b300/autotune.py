@@ -72,6 +72,14 @@ class Autotuner:
         return best, table
 
 
+def _fit_threads(candidates) -> tuple:
+    """Service-thread counts that leave two host cores for the calling thread
+    and the GPU driver (the smallest candidate is always kept)."""
+    room = max(1, (os.cpu_count() or 1) - 2)
+    fit = tuple(t for t in candidates if t <= room)
+    return fit or (min(candidates),)
+
+
 def grid(**axes) -> list[dict]:
     names = list(axes)
     return [dict(zip(names, vals)) for vals in itertools.product(*(axes[n] for n in names))]
@@ -87,7 +95,7 @@ def _timed(torch, fn) -> float:
 
 
 def tune_scan(device: int, fd: int, nbytes: int, tuner: Autotuner | None = None, force: bool = False,
-              service_threads=(4, 8, 12), chunks=(128 << 10, 256 << 10, 512 << 10, 1 << 20),
+              service_threads=(8, 12, 14), chunks=(128 << 10, 256 << 10, 512 << 10, 1 << 20),
               groups=(148, 296), forms=(0, 1, 2, 3), warp_chunks=(16 << 10, 64 << 10)):
     """pread + histogram scan: service threads x chunk x groups x form, where
     the form sets the invocation granularity (work-group plain or batched,
@@ -96,6 +104,7 @@ def tune_scan(device: int, fd: int, nbytes: int, tuner: Autotuner | None = None,
     import torch
     import paper_1705_06965_b300 as G
     tuner = tuner or Autotuner()
+    service_threads = _fit_threads(service_threads)
     key = tuner.key("scan", nbytes=nbytes)
     hit = None if force else tuner.lookup(key)
     if hit:
@@ -135,12 +144,13 @@ def tune_scan(device: int, fd: int, nbytes: int, tuner: Autotuner | None = None,
 
 
 def tune_wordcount(device: int, fds, sizes, queries, tuner: Autotuner | None = None, force: bool = False,
-                   service_threads=(4, 8, 12), chunks=(256 << 10, 1 << 20), ctas=(148, 296), forms=(0, 1)):
+                   service_threads=(8, 12, 14), chunks=(256 << 10, 1 << 20), ctas=(148, 296), forms=(0, 1)):
     """C3 wordcount: service threads x chunk x persistent blocks x form."""
     import numpy as np
     import torch
     import paper_1705_06965_b300 as G
     tuner = tuner or Autotuner()
+    service_threads = _fit_threads(service_threads)
     total = int(np.asarray(sizes, np.uint64).sum())
     key = tuner.key("wordcount", files=len(sizes), bytes=total)
     hit = None if force else tuner.lookup(key)
