@@ -243,7 +243,9 @@ int genesys_emulate_call(genesys_ctx *ctx, uint32_t nr, const uint64_t args[6], 
  * scratch, groups * chunk bytes) and counted there.  staging: host-mapped,
  * >= groups * chunk * (BATCHED: 2, WARP: threads / 32, PLAIN and HBM: 1)
  * bytes, 16-byte aligned; chunk a multiple of 16, threads a multiple of 32;
- * another form is GENESYS_EINVAL. */
+ * another form is GENESYS_EINVAL.  The batched form keeps up to
+ * min(4, staging_bytes / (groups * chunk)) reads in flight per block (at
+ * least 2; fewer if the slot area cannot hold that many per block). */
 int genesys_c1_histogram(genesys_ctx *ctx, int fd, uint64_t file_bytes, uint64_t chunk, uint32_t groups,
                          uint32_t threads, uint32_t form, void *staging, uint64_t staging_bytes,
                          uint32_t *hist_dev, void *stream);

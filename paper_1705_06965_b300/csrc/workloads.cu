@@ -12,6 +12,7 @@
 #include <string.h>
 #include <time.h>
 
+#include <algorithm>
 #include <thread>
 #include <vector>
 
@@ -185,43 +186,40 @@ __global__ void __launch_bounds__(1024, 1) c1_warp_kernel(genesys_dev g, int fd,
 // Batched form: relaxed, non-blocking preads double-buffered per block - the
 // read of chunk k+1 is in flight while chunk k is scanned (Sec. 4.1: weak
 // ordering with non-blocking prefetching reads).
+template <int D>
 __global__ void __launch_bounds__(1024, 1) c1_batched_kernel(genesys_dev g, int fd, uint64_t file_bytes, uint32_t chunk,
                                                           uint8_t *staging, uint32_t *hist_out) {
   extern __shared__ uint32_t sh[];
   __shared__ int64_t r_s;
   for (uint32_t i = threadIdx.x; i < (blockDim.x >> 5) * 256; i += blockDim.x) sh[i] = 0;
   uint32_t *my = sh + (threadIdx.x >> 5) * 256;
-  uint8_t *bufs[2] = {staging + (size_t)(2 * blockIdx.x) * chunk, staging + (size_t)(2 * blockIdx.x + 1) * chunk};
+  uint8_t *base = staging + (size_t)D * blockIdx.x * chunk;  // D buffers of this block
   const uint64_t n_chunks = (file_bytes + chunk - 1) / chunk;
+  const uint64_t n_mine = blockIdx.x < n_chunks ? (n_chunks - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   const bool leader = threadIdx.x == 0;
-  Ticket cur{0xFFFFFFFFu, 0, 0}, nxt{0xFFFFFFFFu, 0, 0};
-  auto issue_chunk = [&](Ticket *t, uint64_t c, uint8_t *buf) {
-    const uint64_t off = c * chunk;
+  Ticket t[D];  // the k-th chunk of this block uses ticket and buffer k % D
+  auto issue_chunk = [&](uint64_t k) {
+    const uint64_t off = (blockIdx.x + k * gridDim.x) * (uint64_t)chunk;
     const uint64_t len = file_bytes - off < chunk ? file_bytes - off : chunk;
-    issue(g, t, SYS_pread64, (uint64_t)fd, (uint64_t)buf, len, off);
+    issue(g, &t[k % D], SYS_pread64, (uint64_t)fd, (uint64_t)(base + (k % D) * (uint64_t)chunk), len, off);
   };
-  uint64_t c = blockIdx.x;
-  if (leader && c < n_chunks) issue_chunk(&cur, c, bufs[0]);
+  uint64_t issued = 0;
+  if (leader)
+    for (; issued < D && issued < n_mine; ++issued) issue_chunk(issued);
   __syncthreads();
-  for (uint32_t k = 0; c < n_chunks; c += gridDim.x, ++k) {
+  for (uint64_t k = 0; k < n_mine; ++k) {
     if (leader) {
-      const uint64_t cn = c + gridDim.x;
-      bool has_next = cn < n_chunks;
-      if (has_next) issue_chunk(&nxt, cn, bufs[(k + 1) & 1]);
-      int64_t r = wait(g, cur);
-      if (r <= 0 && has_next) {  // stop early: collect the prefetch so its slot is released
-        wait(g, nxt);
-        has_next = false;
-      }
-      cur = nxt;
-      nxt = Ticket{0xFFFFFFFFu, 0, 0};
+      const int64_t r = wait(g, t[k % D]);
+      if (r <= 0)  // stop early: collect the reads still in flight so that their slots are released
+        for (uint64_t j = k + 1; j < issued; ++j) wait(g, t[j % D]);
       r_s = r;
     }
     __syncthreads();  // consumer: barrier after the read completes
     const int64_t r = r_s;
     if (r <= 0) break;
-    hist_bytes(bufs[k & 1], (uint64_t)r < chunk ? (uint64_t)r : chunk, my);
-    __syncthreads();  // buffer k&1 is free for the prefetch two chunks ahead
+    hist_bytes(base + (k % D) * (uint64_t)chunk, (uint64_t)r < chunk ? (uint64_t)r : chunk, my);
+    __syncthreads();  // buffer k % D is free again
+    if (leader && issued < n_mine) issue_chunk(issued++);
   }
   hist_flush(sh, hist_out);
 }
@@ -436,18 +434,25 @@ int genesys_c1_histogram(genesys_ctx *c, int fd, uint64_t file_bytes, uint64_t c
   const uint64_t need = (uint64_t)groups * chunk *
                         (form == GENESYS_FORM_BATCHED ? 2 : form == GENESYS_FORM_WARP ? threads / 32 : 1);
   if (staging_bytes < need) return set_err(GENESYS_EINVAL, "staging too small");
+  // the batched form keeps as many reads in flight per block as the staging
+  // holds buffers for (2..4)
+  uint32_t depth = (uint32_t)std::min<uint64_t>(4, staging_bytes / ((uint64_t)groups * chunk));
   if (file_bytes == 0) return 0;
   genesys_dev g;
   genesys_device_view(c, &g);
   if (form == GENESYS_FORM_BATCHED && g.n_slots < 2ull * groups)
     return set_err(GENESYS_EINVAL, "the batched form holds two slots per block: n_slots must be >= 2 * groups");
+  while (depth > 2 && g.n_slots < (uint64_t)depth * groups) --depth;
   uint32_t ch = (uint32_t)chunk;
   uint8_t *st = (uint8_t *)staging;
   void *args[] = {&g, &fd, &file_bytes, &ch, &st, &hist_dev};
   const size_t smem = (size_t)(threads / 32) * 256 * 4;
-  if (form == GENESYS_FORM_BATCHED)
-    return run(c, (const void *)&c1_batched_kernel, groups, threads, smem, args,
+  if (form == GENESYS_FORM_BATCHED) {
+    const void *k = depth >= 4 ? (const void *)&c1_batched_kernel<4>
+                  : depth == 3 ? (const void *)&c1_batched_kernel<3> : (const void *)&c1_batched_kernel<2>;
+    return run(c, k, groups, threads, smem, args,
                GENESYS_GRAN_GROUP | GENESYS_LAUNCH_RELAXED | GENESYS_LAUNCH_NONBLOCKING, stream);
+  }
   if (form == GENESYS_FORM_WARP)
     return run(c, (const void *)&c1_warp_kernel, groups, threads, smem, args, GENESYS_GRAN_WARP, stream);
   if (form == GENESYS_FORM_HBM) {

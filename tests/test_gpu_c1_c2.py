@@ -223,3 +223,24 @@ def test_service_probe_leaves_the_context_usable(G, tmp_path):
                 os.close(fd)
             assert open(q, "rb").read() == open(want_path, "rb").read()
         assert c.status() == [0] * G.ST_WORDS
+
+
+@pytest.mark.parametrize("factor", [2, 3, 4, 8])
+@pytest.mark.parametrize("nbytes,chunk,groups", [((1 << 20) + 123, 4096, 16), (4096 * 5 + 9, 4096, 4)])
+def test_c1_batched_read_depths(ctx, G, tmp_path, factor, nbytes, chunk, groups):
+    """The batched form keeps as many reads in flight per block as the staging
+    holds (2..4): ragged files, fewer chunks than buffers, all equal the oracle."""
+    p = workloads.c1_file(str(tmp_path / "d.bin"), nbytes, seed=factor)
+    want = oracle.c1_histogram(p, chunk)
+    hist = torch.zeros(256, dtype=torch.int32, device="cuda")
+    ctx.staging_reset()
+    need = groups * chunk * factor
+    st = ctx.staging(need)
+    fd = os.open(p, os.O_RDONLY)
+    try:
+        ctx.c1_histogram(fd, nbytes, hist.data_ptr(), st, need, chunk=chunk, groups=groups, threads=256,
+                         form=G.FORM_BATCHED)
+    finally:
+        os.close(fd)
+    assert np.array_equal(hist.cpu().numpy().view(np.uint32), want)
+    assert ctx.status() == [0] * G.ST_WORDS
