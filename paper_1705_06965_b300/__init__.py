@@ -491,8 +491,12 @@ def trace_breakdown(dev, host, host_minus_device_ns: int) -> dict:
         "total": d["t_done"].astype(np.int64) - d["t_call"].astype(np.int64),
     }
     out = {"joined": len(rows)}
+    known = d["t_publish"] > 0  # collected tickets do not record when they were published
     for k, v in stages.items():
-        out[k] = {"p50_ns": int(np.percentile(v, 50)), "p99_ns": int(np.percentile(v, 99))}
+        if k in ("claim", "queue"):
+            v = v[known]
+        if len(v):
+            out[k] = {"p50_ns": int(np.percentile(v, 50)), "p99_ns": int(np.percentile(v, 99))}
     return out
 
 
