@@ -387,3 +387,18 @@ def test_trace_needs_capacity():
     with _ctx() as c:
         with pytest.raises(G.GenesysError):
             c.trace_read()
+
+
+def test_trace_breakdown_joins_and_skips_unknown_publish_times():
+    dev = np.zeros(3, G.TRACE_DEV_DTYPE)
+    host = np.zeros(2, G.TRACE_HOST_DTYPE)
+    dev["slot"], dev["seq"] = [1, 2, 3], [7, 7, 7]
+    dev["t_call"], dev["t_publish"], dev["t_done"] = [100, 100, 100], [150, 0, 150], [400, 500, 0]
+    host["slot"], host["seq"] = [1, 2], [7, 7]
+    host["t_pickup"], host["t_done"] = [1200, 1210], [1300, 1310]
+    b = G.trace_breakdown(dev, host, 1000)          # host clock = device clock + 1000 ns
+    assert b["joined"] == 2                          # slot 3 is non-blocking (no t_done) and has no host record
+    assert b["claim"] == {"p50_ns": 50, "p99_ns": 50}   # only the record with a publish time
+    assert b["queue"]["p50_ns"] == 1200 - (150 + 1000)
+    assert b["service"]["p50_ns"] == 100
+    assert b["total"]["p99_ns"] <= 400
