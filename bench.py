@@ -105,7 +105,10 @@ class ClockSampler:
     def __init__(self, gpu: int):
         self.gpu = gpu
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{gpu}.csv")
+        import tempfile
+        # the raw samples: GENESYS_CLOCKS_DIR if set, else the temporary directory
+        d = os.environ.get("GENESYS_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"genesys_clocks_{os.getpid()}_{gpu}.csv")
 
     def __enter__(self):
         try:
