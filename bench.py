@@ -176,7 +176,7 @@ def host_pwrite_peak(fd, buf, nbytes, repeats=3, chunks=(256 << 10, 1 << 20, 4 <
 
 
 def host_probes(torch, local, scan_path):
-    """What the design depends on, measured on this box: the host CPU, SM
+    """What the design depends on, measured on this machine: the host CPU, SM
     count, whether the GPU has native atomics on host memory (the protocol
     never needs them), and one host thread's tmpfs pread GB/s (1 MiB preads of
     the 1 GiB scan file into a reused buffer: the per-thread copy rate that

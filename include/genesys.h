@@ -165,10 +165,10 @@ int genesys_reclaim(genesys_ctx *ctx);
 
 /* Map (mmap(2), anonymous) and register n regions of the given sizes (rounded
  * up to pages) ahead of time, into the pool GPU mmaps are served from.
- * cudaHostRegister can stall while the GPU is busy with other kernels (on the
- * B300 test box a registration waited tens of seconds behind a stream of
- * kernels), and a kernel waiting for its mmap keeps the GPU busy: reserving
- * before the kernels start keeps registration off the path. */
+ * cudaHostRegister can stall while the GPU is busy with other kernels (on a
+ * B300 a registration waited tens of seconds behind a stream of kernels), and
+ * a kernel waiting for its mmap keeps the GPU busy: reserving before the
+ * kernels start keeps registration off the path. */
 int genesys_mmap_reserve(genesys_ctx *ctx, const uint64_t *sizes, uint32_t n);
 
 int genesys_stats_get(genesys_ctx *ctx, genesys_stats *out);
