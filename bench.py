@@ -742,7 +742,7 @@ def cpu_baseline_c4(tr, reqs, off, port, rates):
             "saturation_req_per_s": max((v["achieved_req_per_s"] for v in res.values()), default=None)}
 
 
-def study_fig10(G, local, rank, sizes=(64, 256, 1024, 4096, 16384, 65504), n_sockets=8):
+def study_fig10(G, local, rank, sizes=(64, 256, 1024, 4096, 16384, 65504), n_sockets=32):
     """Sec. 7.3 / Fig. 10: bandwidth of a UDP echo server versus packet size,
     with the packets processed on the GPU (recvfrom/sendto at work-group
     grain, and the recvmmsg/sendmmsg batch form) and on the CPU (the
