@@ -252,6 +252,8 @@ class Context:
 
     # -- staging arena (pinned, host-mapped: one address valid on both sides)
     def staging(self, nbytes: int) -> int:
+        """Address of nbytes of the context's pinned host-mapped staging arena
+        (usable by the host and by GPU code until staging_reset or close)."""
         p = lib().genesys_staging(self.handle, nbytes)
         if not p:
             raise GenesysError(ENOMEM, "genesys_staging", last_error())
@@ -262,7 +264,9 @@ class Context:
 
     @staticmethod
     def host_view(addr: int, nbytes: int, dtype=np.uint8) -> np.ndarray:
-        """numpy view (host side) of staging memory at `addr`."""
+        """numpy view (host side) of staging memory at `addr`.  It does not
+        keep the memory alive: it is valid only while its context is open
+        (reading it after close() reads freed memory)."""
         buf = (ctypes.c_uint8 * nbytes).from_address(addr)
         return np.frombuffer(buf, dtype=dtype)
 

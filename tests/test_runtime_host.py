@@ -402,3 +402,70 @@ def test_trace_breakdown_joins_and_skips_unknown_publish_times():
     assert b["queue"]["p50_ns"] == 1200 - (150 + 1000)
     assert b["service"]["p50_ns"] == 100
     assert b["total"]["p99_ns"] <= 400
+
+
+def test_merged_preads_split_a_short_read_correctly(tmp_path):
+    """Coalescing must not change any call's result (Sec. 4.2): eight 64-byte
+    preads that continue each other merge into one Linux call; the file ends
+    inside the fifth, so the results are 64, 64, 64, 64, 16, 0, 0, 0 - what
+    each call alone would have returned - and the bytes land where each asked."""
+    p = str(tmp_path / "short.bin")
+    data = workloads.stream_bytes(21, 4 * 64 + 16)
+    open(p, "wb").write(data)
+    with _ctx(no_threads=True, service_threads=1, n_slots=64, coalesce_max=64) as c:
+        buf = c.staging(8 * 64)
+        view = c.host_view(buf, 8 * 64)
+        view[:] = 0xAA
+        fd = os.open(p, os.O_RDONLY)
+        try:
+            threads, results = [], [None] * 8
+
+            def call(i):
+                results[i] = c.emulate_call(G.SYS_pread64, [fd, buf + 64 * i, 64, 64 * i])
+
+            for i in range(8):
+                t = threading.Thread(target=call, args=(i,))
+                t.start()
+                threads.append(t)
+            time.sleep(0.2)        # all eight published before the one service pass
+            served = 0
+            for _ in range(200):
+                served += c.service(1_000_000)
+                if served >= 8:
+                    break
+            [t.join() for t in threads]
+            st = c.stats()
+            got = bytes(view)  # staging memory lives as long as the context
+        finally:
+            os.close(fd)
+    assert results == [64, 64, 64, 64, 16, 0, 0, 0], results
+    assert st["os_calls"] == 1, st
+    assert got[:4 * 64 + 16] == data
+    assert got[4 * 64 + 16:] == b"\xaa" * (8 * 64 - 4 * 64 - 16)
+
+
+def test_merged_pwrites_with_scattered_buffers_use_one_vector_call(tmp_path):
+    """Neighbouring file ranges whose buffers are not neighbours merge into one
+    pwritev; the file is right."""
+    p = str(tmp_path / "v.bin")
+    n = 16
+    pieces = [workloads.stream_bytes(100 + i, 64) for i in range(n)]
+    with _ctx(no_threads=True, service_threads=1, n_slots=64, coalesce_max=64) as c:
+        buf = c.staging(n * 64)
+        view = c.host_view(buf, n * 64)
+        for i in range(n):  # piece i sits in buffer slot n-1-i
+            view[(n - 1 - i) * 64:(n - i) * 64] = np.frombuffer(pieces[i], np.uint8)
+        fd = os.open(p, os.O_CREAT | os.O_TRUNC | os.O_RDWR, 0o644)
+        try:
+            for i in range(n):
+                assert c.emulate_call(G.SYS_pwrite64, [fd, buf + (n - 1 - i) * 64, 64, 64 * i], flags=0) == 0
+            served = 0
+            for _ in range(100):
+                served += c.service(1_000_000)
+                if served >= n:
+                    break
+            st = c.stats()
+        finally:
+            os.close(fd)
+    assert st["requests"] == n and st["os_calls"] == 1 and st["failed"] == 0
+    assert open(p, "rb").read() == b"".join(pieces)
