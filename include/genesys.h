@@ -205,6 +205,18 @@ const char *genesys_last_error(void);
 int genesys_trace_read(genesys_ctx *ctx, genesys_trace_dev *dev, uint32_t dev_cap, uint32_t *n_dev,
                        genesys_trace_host *host, uint32_t host_cap, uint32_t *n_host, int64_t *host_minus_device_ns);
 
+/* Size in bytes of a structure of this interface, so that a binding built
+ * against another version of this header can refuse to run instead of
+ * misreading memory: which = GENESYS_SIZEOF_*; 0 for an unknown value. */
+#define GENESYS_SIZEOF_CONFIG       0
+#define GENESYS_SIZEOF_STATS        1
+#define GENESYS_SIZEOF_SERVE_CONFIG 2
+#define GENESYS_SIZEOF_SERVE_STATS  3
+#define GENESYS_SIZEOF_TRACE_DEV    4
+#define GENESYS_SIZEOF_TRACE_HOST   5
+#define GENESYS_SIZEOF_C5_REQUEST   6
+uint32_t genesys_sizeof(int which);
+
 /* Failure handling on the host: stop the service thread of doorbell ring
  * `ring` (it finishes the batch it holds), leave the ring unserved for
  * pause_ns, then start a new thread that continues from the same ring

@@ -47,7 +47,7 @@ EXPORTS = [
     "genesys_reclaim", "genesys_mmap_reserve", "genesys_kv_start", "genesys_kv_stop", "genesys_kv_value",
     "genesys_kv_client", "genesys_c6_permute", "genesys_gpu_call", "genesys_echo_start", "genesys_echo_stop",
     "genesys_echo_client", "genesys_service_probe", "genesys_link_pingpong", "genesys_service_restart",
-    "genesys_trace_read",
+    "genesys_trace_read", "genesys_sizeof",
 ]
 
 
@@ -153,6 +153,7 @@ def lib() -> ctypes.CDLL:
         "genesys_c5_serve": (ctypes.c_int, [vp, vp, u32, vp, u32, ctypes.c_int32, ctypes.POINTER(ServeConfig), vp, vp,
                                             ctypes.POINTER(ServeStats)]),
         "genesys_service_restart": (ctypes.c_int, [vp, u32, u64]),
+        "genesys_sizeof": (u32, [ctypes.c_int]),
         "genesys_trace_read": (ctypes.c_int, [vp, vp, u32, ctypes.POINTER(u32), vp, u32, ctypes.POINTER(u32),
                                               ctypes.POINTER(i64)]),
         "genesys_link_pingpong": (ctypes.c_int, [ctypes.c_int, u32, u64, ctypes.POINTER(u64)]),
@@ -164,8 +165,21 @@ def lib() -> ctypes.CDLL:
     for name, (res, args) in sig.items():
         f = getattr(L, name)
         f.restype, f.argtypes = res, args
+    _check_layouts(L)
     _lib = L
     return L
+
+
+def _check_layouts(L) -> None:
+    """Refuse a library built from another version of the headers: every
+    structure this binding mirrors must have the library's size."""
+    mine = {0: ctypes.sizeof(Config), 1: ctypes.sizeof(Stats), 2: ctypes.sizeof(ServeConfig),
+            3: ctypes.sizeof(ServeStats), 4: TRACE_DEV_DTYPE.itemsize, 5: TRACE_HOST_DTYPE.itemsize,
+            6: C5_REQ_DTYPE.itemsize}
+    bad = {k: (v, int(L.genesys_sizeof(k))) for k, v in mine.items() if int(L.genesys_sizeof(k)) != v}
+    if bad:
+        raise ImportError(f"{LIB_PATH} was built from other headers than this binding (struct sizes "
+                          f"binding/library: {bad}); rebuild it with `python -m paper_1705_06965_b300.build --force`")
 
 
 def last_error() -> str:

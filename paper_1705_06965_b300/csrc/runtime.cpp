@@ -866,6 +866,19 @@ static uint64_t service_cpu_total(genesys_ctx *c) {
   return t;
 }
 
+uint32_t genesys_sizeof(int which) {
+  switch (which) {
+    case GENESYS_SIZEOF_CONFIG: return sizeof(genesys_config);
+    case GENESYS_SIZEOF_STATS: return sizeof(genesys_stats);
+    case GENESYS_SIZEOF_SERVE_CONFIG: return sizeof(genesys_serve_config);
+    case GENESYS_SIZEOF_SERVE_STATS: return sizeof(genesys_serve_stats);
+    case GENESYS_SIZEOF_TRACE_DEV: return sizeof(genesys_trace_dev);
+    case GENESYS_SIZEOF_TRACE_HOST: return sizeof(genesys_trace_host);
+    case GENESYS_SIZEOF_C5_REQUEST: return sizeof(genesys_c5_request);
+    default: return 0;
+  }
+}
+
 int genesys_service_restart(genesys_ctx *c, uint32_t ring, uint64_t pause_ns) {
   if (!c) return fail(GENESYS_EINVAL, "ctx is NULL");
   if (c->threads.empty()) return fail(GENESYS_EINVAL, "the context has no service threads");

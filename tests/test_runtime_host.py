@@ -7,6 +7,7 @@ them.  Failures are made on the host: bad file descriptors, unsupported calls,
 a stalled service (nobody polls) that makes the caller's deadline fire.
 """
 import errno
+import ctypes
 import os
 import re
 import threading
@@ -27,7 +28,7 @@ def test_library_exports_every_declared_symbol():
     for h in os.listdir(INCLUDE):
         if h.endswith(".h"):
             txt = open(os.path.join(INCLUDE, h)).read()
-            declared |= set(re.findall(r"^(?:int|void|const char)\b[^;(]*?\b(genesys_\w+)\s*\(", txt, re.M))
+            declared |= set(re.findall(r"^(?:int|void|const char|uint32_t|uint64_t)\b[^;(]*?\b(genesys_\w+)\s*\(", txt, re.M))
     assert declared, "no declarations found"
     assert declared == set(G.EXPORTS), declared ^ set(G.EXPORTS)
     for name in declared:
@@ -469,3 +470,12 @@ def test_merged_pwrites_with_scattered_buffers_use_one_vector_call(tmp_path):
             os.close(fd)
     assert st["requests"] == n and st["os_calls"] == 1 and st["failed"] == 0
     assert open(p, "rb").read() == b"".join(pieces)
+
+
+def test_binding_and_library_agree_on_struct_sizes():
+    L = G.lib()  # loading already refuses a mismatch; check the values and the unknown case
+    assert int(L.genesys_sizeof(0)) == ctypes.sizeof(G.Config)
+    assert int(L.genesys_sizeof(1)) == ctypes.sizeof(G.Stats)
+    assert int(L.genesys_sizeof(4)) == G.TRACE_DEV_DTYPE.itemsize == 40
+    assert int(L.genesys_sizeof(5)) == G.TRACE_HOST_DTYPE.itemsize == 24
+    assert int(L.genesys_sizeof(99)) == 0
