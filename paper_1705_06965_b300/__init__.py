@@ -486,6 +486,20 @@ TRACE_DEV_DTYPE = np.dtype([("slot", "<u4"), ("seq", "<u4"), ("nr", "<u4"), ("gr
 TRACE_HOST_DTYPE = np.dtype([("slot", "<u4"), ("seq", "<u4"), ("t_pickup", "<u8"), ("t_done", "<u8")])
 
 
+def latency_by_gran(dev) -> dict:
+    """Per invocation granularity: blocking calls traced, and their call-to-
+    result time p50/p99 (ns), from device trace records alone."""
+    out = {}
+    done = dev[dev["t_done"] > 0]
+    for g, name in GRAN_NAMES.items():
+        sel = done[done["gran"] == g]
+        if len(sel):
+            t = sel["t_done"].astype(np.int64) - sel["t_call"].astype(np.int64)
+            out[name] = {"calls": int(len(sel)), "p50_ns": int(np.percentile(t, 50)),
+                         "p99_ns": int(np.percentile(t, 99))}
+    return out
+
+
 def trace_breakdown(dev, host, host_minus_device_ns: int) -> dict:
     """Join device and host trace records by (slot, seq) and give the
     percentiles (ns) of each stage of a blocking call: claim (call to
@@ -508,7 +522,7 @@ def trace_breakdown(dev, host, host_minus_device_ns: int) -> dict:
         "delivery": (d["t_done"].astype(np.int64) + off) - h["t_done"].astype(np.int64),
         "total": d["t_done"].astype(np.int64) - d["t_call"].astype(np.int64),
     }
-    out = {"joined": len(rows)}
+    out = {"joined": len(rows), "by_gran": latency_by_gran(dev)}
     known = d["t_publish"] > 0  # collected tickets do not record when they were published
     for k, v in stages.items():
         if k in ("claim", "queue"):

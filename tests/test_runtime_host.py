@@ -403,6 +403,10 @@ def test_trace_breakdown_joins_and_skips_unknown_publish_times():
     assert b["queue"]["p50_ns"] == 1200 - (150 + 1000)
     assert b["service"]["p50_ns"] == 100
     assert b["total"]["p99_ns"] <= 400
+    dev["gran"] = [0, 2, 2]
+    by = G.latency_by_gran(dev)
+    assert by == {"work-item": {"calls": 1, "p50_ns": 300, "p99_ns": 300},
+                  "work-group": {"calls": 1, "p50_ns": 400, "p99_ns": 400}}
 
 
 def test_merged_preads_split_a_short_read_correctly(tmp_path):
