@@ -93,9 +93,12 @@ typedef struct genesys_stats {
   uint64_t op_max_ns[8];       /* longest single request per op                        */
   uint64_t mmap_new;           /* GPU mmaps served by mmap(2) + registration           */
   uint64_t mmap_reused;        /* GPU mmaps served by a released region                */
-  uint64_t service_cpu_ns;     /* CPU time of the service threads (getrusage per thread,
-                                  sampled when a thread goes idle and every 1,024
-                                  batches)                                              */
+  uint64_t service_cpu_ns;     /* CPU time of the service threads (their per-thread CPU
+                                  clocks)                                              */
+  uint64_t protocol_errors;    /* checked builds (GENESYS_DEVICE_CHECKS): requests whose
+                                  sequence number was not the slot's previous one + 1,
+                                  or whose ring entry named a slot out of range; always
+                                  0 in other builds                                    */
 } genesys_stats;
 
 typedef struct genesys_ctx genesys_ctx;

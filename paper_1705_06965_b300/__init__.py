@@ -91,7 +91,8 @@ class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in
                 ("requests", "os_calls", "failed", "nonblocking_failed", "bytes", "batches", "busy_ns")] + [
         ("by_op", ctypes.c_uint64 * 8), ("op_ns", ctypes.c_uint64 * 8), ("op_max_ns", ctypes.c_uint64 * 8),
-        ("mmap_new", ctypes.c_uint64), ("mmap_reused", ctypes.c_uint64), ("service_cpu_ns", ctypes.c_uint64)]
+        ("mmap_new", ctypes.c_uint64), ("mmap_reused", ctypes.c_uint64), ("service_cpu_ns", ctypes.c_uint64),
+        ("protocol_errors", ctypes.c_uint64)]
 
     OPS = ("pread", "pwrite", "sendto", "recvfrom", "mmap", "munmap", "internal", "other")
 

@@ -195,6 +195,11 @@ struct genesys_ctx {
   // the last genesys_stats_reset
   std::atomic<uint64_t> cpu_retired_ns{0};
   uint64_t cpu_reset_ns = 0;
+
+  // checked builds: the last sequence number the service saw per slot (each
+  // slot's requests go through one ring, so one thread writes each entry)
+  std::vector<uint32_t> last_seq;
+  std::atomic<uint64_t> protocol_errors{0};
 };
 
 namespace {
@@ -525,10 +530,22 @@ inline bool entry_ready(const uint64_t *ring, uint32_t mask, uint64_t pos, uint3
 }
 
 inline void read_request(genesys_ctx *c, uint32_t s, Request *r) {
+#ifdef GENESYS_DEVICE_CHECKS
+  if (s >= c->cfg.n_slots) {  // a doorbell entry naming no slot: count it and serve slot 0's request instead
+    c->protocol_errors.fetch_add(1);
+    s = 0;
+  }
+#endif
   const genesys_slot *sl = &c->slots[s];
   const uint64_t req = __atomic_load_n(&sl->req, __ATOMIC_ACQUIRE);
   r->slot = s;
   r->seq = (uint32_t)(req >> 32);
+#ifdef GENESYS_DEVICE_CHECKS
+  // a slot's requests are numbered 1, 2, 3, ... and each waits for the one
+  // before it, so the service must see them in that order
+  if (r->seq != c->last_seq[s] + 1u) c->protocol_errors.fetch_add(1);
+  c->last_seq[s] = r->seq;
+#endif
   r->nr = (uint32_t)(req >> 16) & 0xFFFFu;
   r->flags = (uint32_t)req & 0xFFFFu;
   for (int i = 0; i < 6; ++i) r->a[i] = __atomic_load_n(&sl->args[i], __ATOMIC_RELAXED);
@@ -816,6 +833,9 @@ int genesys_init(const genesys_config *cfg_in, int device, genesys_ctx **out) {
   c->counters.reset(new Counters[nr]);
   c->ring_stop.reset(new std::atomic<bool>[nr]);
   for (uint32_t r = 0; r < nr; ++r) c->ring_stop[r].store(false);
+#ifdef GENESYS_DEVICE_CHECKS
+  c->last_seq.assign(cfg.n_slots, 0);
+#endif
   c->trace_n.reset(new std::atomic<uint32_t>[nr]);
   for (uint32_t r = 0; r < nr; ++r) c->trace_n[r].store(0);
   if (cfg.trace_capacity) c->trace_host.assign(nr, std::vector<genesys_trace_host>((cfg.trace_capacity + nr - 1) / nr));
@@ -1062,6 +1082,7 @@ int genesys_stats_get(genesys_ctx *c, genesys_stats *o) {
     const uint64_t cpu = service_cpu_total(c);
     o->service_cpu_ns = cpu > c->cpu_reset_ns ? cpu - c->cpu_reset_ns : 0;
   }
+  o->protocol_errors = c->protocol_errors.load();
   return 0;
 }
 

@@ -54,6 +54,7 @@ def main(tmp: str) -> None:
             os.close(fd)
         assert np.array_equal(counts.cpu().numpy().astype(np.uint64), c.truth_total())
         assert ctx.status() == [0] * G.ST_WORDS, ctx.status()
+        assert ctx.stats()["protocol_errors"] == 0
     print("checked ok")
 
 

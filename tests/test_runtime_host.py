@@ -483,3 +483,31 @@ def test_binding_and_library_agree_on_struct_sizes():
     assert int(L.genesys_sizeof(4)) == G.TRACE_DEV_DTYPE.itemsize == 40
     assert int(L.genesys_sizeof(5)) == G.TRACE_HOST_DTYPE.itemsize == 24
     assert int(L.genesys_sizeof(99)) == 0
+
+
+def test_checked_build_host_protocol_checker(tmp_path):
+    """The checked build also checks, on the host, that every slot's requests
+    reach the service numbered 1, 2, 3, ...: concurrent emulated callers over
+    a small slot area (every slot reused many times) give no protocol error."""
+    import subprocess
+    import sys
+    from paper_1705_06965_b300 import build
+    build.build(device_checks=True)
+    code = (
+        "import threading, paper_1705_06965_b300 as G\n"
+        "assert G.LIB_PATH.endswith('libgenesys_checked.so')\n"
+        "c = G.Context(host_only=True, service_threads=2, n_slots=64, staging_bytes=1 << 20)\n"
+        "errs = []\n"
+        "def lane(k):\n"
+        "    for i in range(500):\n"
+        "        if c.emulate_call(G.NR_NOP, [k * 10000 + i]) != k * 10000 + i: errs.append(i)\n"
+        "th = [threading.Thread(target=lane, args=(k,)) for k in range(6)]\n"
+        "[t.start() for t in th]; [t.join() for t in th]\n"
+        "st = c.stats(); c.close()\n"
+        "assert not errs and st['requests'] == 3000, (errs[:3], st['requests'])\n"
+        "assert st['protocol_errors'] == 0, st['protocol_errors']\n"
+        "print('ok')\n")
+    env = dict(os.environ, GENESYS_LIBRARY="checked")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
