@@ -511,3 +511,56 @@ def test_checked_build_host_protocol_checker(tmp_path):
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     r = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
+
+
+def test_every_entry_point_rejects_null_arguments():
+    """The C ABI returns GENESYS_EINVAL for NULL contexts and pointers - no
+    entry point touches CUDA or dereferences anything before checking
+    (genesys_shutdown(NULL) is a no-op returning 0)."""
+    L = G.lib()
+    res = {}
+    def t(name, *args):
+        f = getattr(L, name)
+        try:
+            res[name] = f(*args)
+        except Exception as e:
+            res[name] = repr(e)
+    t("genesys_config_default", None)
+    t("genesys_init", None, 0, None)
+    t("genesys_shutdown", None)
+    t("genesys_device_view", None, None)
+    t("genesys_launch", None, None, None, None, 0, None, 0, None)
+    t("genesys_service", None, 0)
+    t("genesys_drain", None, 0)
+    t("genesys_stats_get", None, None)
+    t("genesys_stats_reset", None)
+    t("genesys_status", None, None, 0)
+    t("genesys_latency", None, None, 0, None, 0)
+    t("genesys_staging_reset", None)
+    t("genesys_emulate_call", None, 0, None, 0, None)
+    t("genesys_c1_histogram", None, 0, 0, 0, 0, 0, 0, None, 0, None, None)
+    t("genesys_c2_pwrite", None, 0, 0, 0, 0, 0, 0, 0, None, 0, None)
+    t("genesys_visibility_probe", None, 0, 0, 0, 0, 0, None, None, None)
+    t("genesys_last_launch_ms", None, None)
+    t("genesys_c3_wordcount", None, None, None, 0, None, None, 0, 0, 0, 0, 0, None, 0, None, None)
+    t("genesys_c3_wordcount_noalloc", None, None, None, 0, None, None, 0, 0, 0, 0, 0, None, 0, None, None)
+    t("genesys_serve_config_default", None)
+    t("genesys_reclaim", None)
+    t("genesys_mmap_reserve", None, None, 0)
+    t("genesys_kv_start", None, None, None, None, 0, 0, 0, 0, 0, 0, None)
+    t("genesys_kv_stop", None, 0, None)
+    t("genesys_kv_value", None, 0, None)
+    t("genesys_kv_client", None, None, 0, None, 0, 0, 0, None, None, None, None)
+    t("genesys_c6_permute", None, 0, None, None, 0, 0, 0, 0, None, 0, None)
+    t("genesys_gpu_call", None, 0, None, 0, 0, None, None)
+    t("genesys_echo_start", None, 0, 0, 0, 0, 0, 0, 0, None)
+    t("genesys_echo_stop", None, 0, None)
+    t("genesys_echo_client", 0, 0, 0, 0, 0, 0, 0, 0, 0, None)
+    t("genesys_service_probe", None, 0, None, 0, 0, None)
+    t("genesys_link_pingpong", 0, 0, 0, None)
+    t("genesys_service_restart", None, 0, 0)
+    t("genesys_trace_read", None, None, 0, None, None, 0, None, None)
+    t("genesys_c5_serve", None, None, 0, None, 0, 0, None, None, None, None)
+    assert res.pop("genesys_shutdown") == 0
+    assert all(v == G.EINVAL for v in res.values()), res
+    assert len(res) >= 35
