@@ -942,10 +942,7 @@ def run_genesys(args):
         "value": round(value, 1), "unit": "syscalls/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(tot_ms / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": "C2 invocation microbenchmark sweep: 2^10..2^20 threads x {work-item, warp, "
-                               "work-group 64/256/1024, kernel} x {strong, relaxed} x {blocking, non-blocking}, "
-                               "64-byte pwrite per thread to a tmpfs file at gid*64; then C1 (4 MiB file, 4 KiB "
-                               "preads, 64 work-groups x 256 threads, 256-bin histogram, plain and batched)",
+        "config": {"workload": WORKLOAD,
                    "threads": SIZES, "combinations": len(COMBOS), "kernels_per_step": len(SIZES) * len(COMBOS) + 2,
                    "syscalls_per_step": calls_step, "service_threads": step_cfg["service_threads"],
                    "coalesce_max": step_cfg["coalesce_max"], "poll_max_ns": step_cfg["poll_max_ns"],
@@ -1011,6 +1008,12 @@ def cpu_baseline_sample(budget_s=20.0):
             "host_cpus": os.cpu_count()}
 
 
+WORKLOAD = ("C2 invocation microbenchmark sweep: 2^10..2^20 threads x {work-item, warp, work-group 64/256/1024, "
+            "kernel} x {strong, relaxed} x {blocking, non-blocking}, 64-byte pwrite per thread to a tmpfs file at "
+            "gid*64; then C1 (4 MiB file, 4 KiB preads, 64 work-groups x 256 threads, 256-bin histogram, plain and "
+            "batched)")
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -1029,8 +1032,8 @@ def run_reference(args):
             "value": round(v, 1), "unit": "syscalls/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(tot_s * 1e3 / args.steps, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": "same sweep and pread pass, issued by the sequential CPU oracle",
-                       "syscalls_per_step": sum(step_calls())},
+            "config": {"workload": WORKLOAD, "issued_by": "the sequential CPU oracle (one host thread)",
+                       "threads": SIZES, "combinations": len(COMBOS), "syscalls_per_step": sum(step_calls())},
             "cpu_baseline": {"value": round(v, 1), "unit": "syscalls/s", "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} full steps"},
             "e2e": {"value": round(v, 1), "unit": "syscalls/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
