@@ -220,6 +220,14 @@ int genesys_trace_read(genesys_ctx *ctx, genesys_trace_dev *dev, uint32_t dev_ca
 #define GENESYS_SIZEOF_C5_REQUEST   6
 uint32_t genesys_sizeof(int which);
 
+/* Failure detection on the host (a watchdog's probe): *stalled_mask gets bit r
+ * set for every doorbell ring r (r < 64) that has requests waiting but whose
+ * service has finished no batch for stall_ns (a stopped, paused or stuck
+ * service thread, or a NO_THREADS context nobody services); *pending (if
+ * non-NULL) = requests published and not yet finished over all rings.  Cheap
+ * enough to call periodically while kernels run. */
+int genesys_service_health(genesys_ctx *ctx, uint64_t stall_ns, uint64_t *stalled_mask, uint64_t *pending);
+
 /* Failure handling on the host: stop the service thread of doorbell ring
  * `ring` (it finishes the batch it holds), leave the ring unserved for
  * pause_ns, then start a new thread that continues from the same ring

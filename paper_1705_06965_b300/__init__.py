@@ -47,7 +47,7 @@ EXPORTS = [
     "genesys_reclaim", "genesys_mmap_reserve", "genesys_kv_start", "genesys_kv_stop", "genesys_kv_value",
     "genesys_kv_client", "genesys_c6_permute", "genesys_gpu_call", "genesys_echo_start", "genesys_echo_stop",
     "genesys_echo_client", "genesys_service_probe", "genesys_link_pingpong", "genesys_service_restart",
-    "genesys_trace_read", "genesys_sizeof",
+    "genesys_trace_read", "genesys_sizeof", "genesys_service_health",
 ]
 
 
@@ -155,6 +155,7 @@ def lib() -> ctypes.CDLL:
                                             ctypes.POINTER(ServeStats)]),
         "genesys_service_restart": (ctypes.c_int, [vp, u32, u64]),
         "genesys_sizeof": (u32, [ctypes.c_int]),
+        "genesys_service_health": (ctypes.c_int, [vp, u64, ctypes.POINTER(u64), ctypes.POINTER(u64)]),
         "genesys_trace_read": (ctypes.c_int, [vp, vp, u32, ctypes.POINTER(u32), vp, u32, ctypes.POINTER(u32),
                                               ctypes.POINTER(i64)]),
         "genesys_link_pingpong": (ctypes.c_int, [ctypes.c_int, u32, u64, ctypes.POINTER(u64)]),
@@ -317,6 +318,14 @@ class Context:
                                         ctypes.byref(nh), ctypes.byref(off) if calibrate else None),
                "genesys_trace_read")
         return dev[:min(nd.value, cap)], host[:min(nh.value, cap)], (off.value if calibrate else None)
+
+    def service_health(self, stall_ns: int = 100_000_000) -> tuple:
+        """(rings stalled for stall_ns with requests waiting, requests pending)
+        (genesys_service_health)."""
+        mask, pend = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().genesys_service_health(self.handle, stall_ns, ctypes.byref(mask), ctypes.byref(pend)),
+               "genesys_service_health")
+        return [r for r in range(64) if mask.value >> r & 1], int(pend.value)
 
     def service_restart(self, ring: int, pause_ns: int = 0) -> None:
         """Stop the service thread of `ring`, leave the ring unserved for

@@ -100,6 +100,7 @@ struct alignas(64) Counters {
   std::atomic<uint64_t> requests{0}, os_calls{0}, failed{0}, nb_failed{0}, bytes{0}, batches{0}, busy_ns{0};
   std::atomic<uint64_t> by_op[8] = {};
   std::atomic<uint64_t> op_ns[8] = {}, op_max_ns[8] = {};
+  std::atomic<uint64_t> last_batch_ns{0};  // when the ring's last batch was finished
 };
 
 struct Request {
@@ -200,6 +201,7 @@ struct genesys_ctx {
   // slot's requests go through one ring, so one thread writes each entry)
   std::vector<uint32_t> last_seq;
   std::atomic<uint64_t> protocol_errors{0};
+  uint64_t created_ns = 0;
 };
 
 namespace {
@@ -519,6 +521,7 @@ void process_batch(genesys_ctx *c, uint32_t ri, Batch &b, size_t n, Counters &k)
     if (per_op[o]) bump(k.by_op[o], per_op[o]);
   bump(k.requests, n);
   bump(k.batches, 1);
+  k.last_batch_ns.store(mono_ns(), std::memory_order_relaxed);
   bump(k.busy_ns, mono_ns() - t0);
 }
 
@@ -836,6 +839,7 @@ int genesys_init(const genesys_config *cfg_in, int device, genesys_ctx **out) {
 #ifdef GENESYS_DEVICE_CHECKS
   c->last_seq.assign(cfg.n_slots, 0);
 #endif
+  c->created_ns = mono_ns();
   c->trace_n.reset(new std::atomic<uint32_t>[nr]);
   for (uint32_t r = 0; r < nr; ++r) c->trace_n[r].store(0);
   if (cfg.trace_capacity) c->trace_host.assign(nr, std::vector<genesys_trace_host>((cfg.trace_capacity + nr - 1) / nr));
@@ -897,6 +901,25 @@ uint32_t genesys_sizeof(int which) {
     case GENESYS_SIZEOF_C5_REQUEST: return sizeof(genesys_c5_request);
     default: return 0;
   }
+}
+
+int genesys_service_health(genesys_ctx *c, uint64_t stall_ns, uint64_t *stalled_mask, uint64_t *pending) {
+  if (!c || !stalled_mask) return fail(GENESYS_EINVAL, "NULL argument");
+  std::vector<uint32_t> tails(c->cfg.n_service_threads);
+  int rc = read_tails(c, tails);
+  if (rc) return rc;
+  const uint64_t now = mono_ns();
+  uint64_t mask = 0, total = 0;
+  for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) {
+    // positions are 32-bit on the device: the distance modulo 2^32
+    const uint32_t waiting = tails[r] - (uint32_t)c->retired[r].load(std::memory_order_acquire);
+    total += waiting;
+    const uint64_t last = c->counters[r].last_batch_ns.load(std::memory_order_relaxed);
+    if (waiting && now - std::max(last, c->created_ns) > stall_ns && r < 64) mask |= 1ull << r;
+  }
+  *stalled_mask = mask;
+  if (pending) *pending = total;
+  return 0;
 }
 
 int genesys_service_restart(genesys_ctx *c, uint32_t ring, uint64_t pause_ns) {

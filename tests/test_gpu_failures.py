@@ -77,6 +77,10 @@ def test_service_thread_restart_during_a_kernel(G, tmp_path):
         t.start()
         for ring in (0, 1):
             ctx.service_restart(ring, pause_ns=20_000_000)
+        # the watchdog probe works while the kernel runs (reads the rings'
+        # producer positions on a non-blocking stream)
+        stalled, pending = ctx.service_health(1_000_000_000)
+        assert stalled == [] and pending >= 0
         t.join()
         os.close(fd)
         assert not err, err

@@ -564,3 +564,37 @@ def test_every_entry_point_rejects_null_arguments():
     assert res.pop("genesys_shutdown") == 0
     assert all(v == G.EINVAL for v in res.values()), res
     assert len(res) >= 35
+
+
+def test_service_health_reports_an_unserved_ring():
+    """The watchdog probe: requests waiting in a ring nobody services for
+    longer than stall_ns are reported; once serviced, the ring is healthy."""
+    with _ctx(no_threads=True, service_threads=2, n_slots=512) as c:
+        assert c.service_health(1_000_000) == ([], 0)
+        for v in range(40):
+            assert c.emulate_call(G.NR_NOP, [v], flags=0) == 0    # non-blocking: published, not served
+        time.sleep(0.02)
+        stalled, pending = c.service_health(10_000_000)
+        assert pending == 40 and stalled, (stalled, pending)
+        n = 0
+        for _ in range(100):
+            n += c.service(1_000_000)
+            if n == 40:
+                break
+        assert c.service_health(10_000_000) == ([], 0)
+
+
+def test_service_health_sees_a_paused_thread():
+    with _ctx(service_threads=1, n_slots=64, deadline_ns=5_000_000_000) as c:
+        assert c.emulate_call(G.NR_NOP, [1]) == 1
+        restart = threading.Thread(target=c.service_restart, args=(0, 300_000_000))
+        restart.start()
+        time.sleep(0.05)
+        caller = threading.Thread(target=c.emulate_call, args=(G.NR_NOP, [2]))
+        caller.start()
+        time.sleep(0.1)
+        stalled, pending = c.service_health(50_000_000)
+        assert stalled == [0] and pending == 1
+        restart.join()
+        caller.join()
+        assert c.service_health(50_000_000) == ([], 0)
