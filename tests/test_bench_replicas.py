@@ -47,3 +47,25 @@ def test_single_process_is_identity():
     import bench
     assert bench.reduce_max([4.0, 5.0]) == [4.0, 5.0]
     assert bench.job_value(1, 10.0, 2.0) == 5.0
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    """Under torchrun the reference arm (the CPU oracle) runs on rank 0 alone;
+    the other ranks exit without work or output."""
+    import argparse
+    import bench
+    calls = []
+    monkeypatch.setattr(bench, "oracle_step", lambda d: calls.append(d) or (10, 0.5, None))
+    args = argparse.Namespace(steps=2, warmup=1)
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    bench.run_reference(args)
+    assert calls == [] and capsys.readouterr().out == ""
+    monkeypatch.setenv("RANK", "0")
+    bench.run_reference(args)
+    out = capsys.readouterr().out
+    import json
+    line = json.loads(out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and len(calls) == 3
+    assert line["value"] == 10 / 0.5 and line["e2e"]["h2d_bytes_per_step"] == 0
+    assert line["config"]["workload"] == bench.WORKLOAD
