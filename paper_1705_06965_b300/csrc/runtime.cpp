@@ -911,8 +911,11 @@ int genesys_service_health(genesys_ctx *c, uint64_t stall_ns, uint64_t *stalled_
   const uint64_t now = mono_ns();
   uint64_t mask = 0, total = 0;
   for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) {
-    // positions are 32-bit on the device: the distance modulo 2^32
-    const uint32_t waiting = tails[r] - (uint32_t)c->retired[r].load(std::memory_order_acquire);
+    // positions are 32-bit on the device: the distance modulo 2^32; the
+    // service may have passed the tails read above (requests published and
+    // finished since), which counts as nothing waiting
+    const int32_t d = (int32_t)(tails[r] - (uint32_t)c->retired[r].load(std::memory_order_acquire));
+    const uint32_t waiting = d > 0 ? (uint32_t)d : 0u;
     total += waiting;
     const uint64_t last = c->counters[r].last_batch_ns.load(std::memory_order_relaxed);
     if (waiting && now - std::max(last, c->created_ns) > stall_ns && r < 64) mask |= 1ull << r;
