@@ -598,3 +598,19 @@ def test_service_health_sees_a_paused_thread():
         restart.join()
         caller.join()
         assert c.service_health(50_000_000) == ([], 0)
+
+
+def test_a_user_kernel_compiles_against_the_headers(tmp_path):
+    """The device header is usable from a user's own kernel: the README's
+    example compiles for sm_103a with nothing but include/ (not run here)."""
+    import shutil
+    import subprocess
+    from paper_1705_06965_b300 import build
+    nvcc = build.nvcc()
+    if shutil.which(nvcc) is None and not os.path.exists(nvcc):
+        pytest.skip("no nvcc")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([nvcc, *build.ARCH, "-std=c++17", "-c", "-I", os.path.join(root, "include"),
+                        os.path.join(root, "tests", "c_abi", "user_kernel.cu"), "-o", str(tmp_path / "u.o")],
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
