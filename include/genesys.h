@@ -43,6 +43,10 @@ extern "C" {
 #define GENESYS_ENODEV    (-19)   /* no usable CUDA device                           */
 #define GENESYS_EDEVICE   (-1001) /* the GPU reported failed or timed-out calls     */
 #define GENESYS_ECUDA     (-1000) /* a CUDA runtime call failed                      */
+/* Every entry point returns one of these codes (0 on success) and records a
+ * message for genesys_last_error.  No C++ exception leaves the library: a host
+ * allocation that fails, or a thread that cannot start, becomes
+ * GENESYS_ENOMEM, and whatever the call had set up is given back. */
 
 /* ------------------------------------------------------------ configuration */
 #define GENESYS_INIT_HOST_ONLY   0x1u /* no GPU: host memory only; requests come from

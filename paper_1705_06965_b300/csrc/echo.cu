@@ -218,105 +218,109 @@ struct genesys_echo_server {
 extern "C" int genesys_echo_start(genesys_ctx *c, uint32_t n_sockets, uint32_t max_packet, uint32_t form,
                                   uint32_t batch, uint32_t threads, uint16_t port_base, uint64_t idle_timeout_ns,
                                   genesys_echo_server **out) {
-  if (!c || !out) return set_err(GENESYS_EINVAL, "NULL argument");
-  if (n_sockets == 0 || n_sockets > 1024 || max_packet < kHeader || max_packet > GENESYS_ECHO_PACKET_MAX ||
-      form > GENESYS_ECHO_BATCH || threads < 32 || threads > 1024 || threads % 32)
-    return set_err(GENESYS_EINVAL, "n_sockets 1..1024, max_packet 8..GENESYS_ECHO_PACKET_MAX, form SINGLE/BATCH, "
-                                   "threads 32..1024 (multiple of 32)");
-  if (form == GENESYS_ECHO_SINGLE) batch = 1;
-  if (batch == 0 || batch > kMaxBatch) return set_err(GENESYS_EINVAL, "batch 1..GENESYS_ECHO_MAX_BATCH");
-  const uint32_t stride = (max_packet + 255) & ~255u;
-  const uint64_t area_bytes = kHeadersBytes + 2ull * batch * stride;
-  auto s = new genesys_echo_server();
-  s->ctx = c;
-  auto fail_cleanup = [&](int code, const char *msg) {
-    for (int fd : s->socks) close(fd);
-    if (s->dmem) cudaFree(s->dmem);
-    if (s->stream) cudaStreamDestroy(s->stream);
-    if (s->ctl) cudaStreamDestroy(s->ctl);
-    genesys_internal_staging_release(c, s->staging_mark);
-    delete s;
-    return set_err(code, msg);
-  };
-  s->staging_mark = genesys_internal_staging_mark(c);
-  for (uint32_t w = 0; w < n_sockets; ++w) {
-    int fd = socket(AF_INET, SOCK_DGRAM, 0);
-    if (fd < 0) return fail_cleanup(GENESYS_EINVAL, "socket failed");
-    s->socks.push_back(fd);
-    set_buffers(fd);
-    sockaddr_in a{};
-    a.sin_family = AF_INET;
-    a.sin_port = htons((uint16_t)(port_base + w));
-    a.sin_addr.s_addr = htonl(INADDR_LOOPBACK);
-    if (bind(fd, (sockaddr *)&a, sizeof a) != 0) return fail_cleanup(GENESYS_EINVAL, "bind failed (port in use?)");
-  }
-  const int dev = genesys_internal_device(c);
-  if (cudaSetDevice(dev) != cudaSuccess) return fail_cleanup(GENESYS_ECUDA, "cudaSetDevice");
-  const size_t o_stop = (4ull * n_sockets + 15) & ~size_t(15), o_cnt = o_stop + 16, bytes = o_cnt + 16;
-  if (cudaMalloc(&s->dmem, bytes) != cudaSuccess) return fail_cleanup(GENESYS_ENOMEM, "device memory");
-  uint8_t *d = (uint8_t *)s->dmem;
-  std::vector<int32_t> fds(s->socks.begin(), s->socks.end());
-  if (cudaMemset(d, 0, bytes) != cudaSuccess ||
-      cudaMemcpy(d, fds.data(), 4ull * n_sockets, cudaMemcpyHostToDevice) != cudaSuccess)
-    return fail_cleanup(GENESYS_ECUDA, "upload");
-  s->d_stop = (int32_t *)(d + o_stop);
-  s->d_counters = (unsigned long long *)(d + o_cnt);
-  uint8_t *areas = (uint8_t *)genesys_staging(c, area_bytes * n_sockets);
-  if (!areas) return fail_cleanup(GENESYS_ENOMEM, "staging arena too small for the echo buffers");
-  if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s->ctl, cudaStreamNonBlocking) != cudaSuccess)
-    return fail_cleanup(GENESYS_ECUDA, "streams");
-  genesys_dev g;
-  genesys_device_view(c, &g);
-  const int32_t *d_fds = (const int32_t *)d;
-  uint64_t ab = area_bytes;
-  uint32_t bt = batch, st = stride;
-  volatile int32_t *stop = s->d_stop;
-  uint64_t idle = idle_timeout_ns ? idle_timeout_ns : 10000000000ull;
-  unsigned long long *cnt = s->d_counters;
-  void *args[] = {&g, &d_fds, &areas, &ab, &bt, &st, &stop, &idle, &cnt};
-  const uint32_t g3[3] = {n_sockets, 1, 1}, b3[3] = {threads, 1, 1};
-  const void *k = form == GENESYS_ECHO_BATCH ? (const void *)&echo_server_kernel<true>
-                                             : (const void *)&echo_server_kernel<false>;
-  const int rc = genesys_launch(c, k, g3, b3, 0, args, GENESYS_GRAN_GROUP | GENESYS_LAUNCH_RELAXED, s->stream);
-  if (rc) return fail_cleanup(rc, genesys_last_error());
-  s->running = true;
-  *out = s;
-  return 0;
+  return genesys_guard("genesys_echo_start", [&]() -> int {
+    if (!c || !out) return set_err(GENESYS_EINVAL, "NULL argument");
+    if (n_sockets == 0 || n_sockets > 1024 || max_packet < kHeader || max_packet > GENESYS_ECHO_PACKET_MAX ||
+        form > GENESYS_ECHO_BATCH || threads < 32 || threads > 1024 || threads % 32)
+      return set_err(GENESYS_EINVAL, "n_sockets 1..1024, max_packet 8..GENESYS_ECHO_PACKET_MAX, form SINGLE/BATCH, "
+                                     "threads 32..1024 (multiple of 32)");
+    if (form == GENESYS_ECHO_SINGLE) batch = 1;
+    if (batch == 0 || batch > kMaxBatch) return set_err(GENESYS_EINVAL, "batch 1..GENESYS_ECHO_MAX_BATCH");
+    const uint32_t stride = (max_packet + 255) & ~255u;
+    const uint64_t area_bytes = kHeadersBytes + 2ull * batch * stride;
+    auto s = new genesys_echo_server();
+    s->ctx = c;
+    auto fail_cleanup = [&](int code, const char *msg) {
+      for (int fd : s->socks) close(fd);
+      if (s->dmem) cudaFree(s->dmem);
+      if (s->stream) cudaStreamDestroy(s->stream);
+      if (s->ctl) cudaStreamDestroy(s->ctl);
+      genesys_internal_staging_release(c, s->staging_mark);
+      delete s;
+      return set_err(code, msg);
+    };
+    s->staging_mark = genesys_internal_staging_mark(c);
+    for (uint32_t w = 0; w < n_sockets; ++w) {
+      int fd = socket(AF_INET, SOCK_DGRAM, 0);
+      if (fd < 0) return fail_cleanup(GENESYS_EINVAL, "socket failed");
+      s->socks.push_back(fd);
+      set_buffers(fd);
+      sockaddr_in a{};
+      a.sin_family = AF_INET;
+      a.sin_port = htons((uint16_t)(port_base + w));
+      a.sin_addr.s_addr = htonl(INADDR_LOOPBACK);
+      if (bind(fd, (sockaddr *)&a, sizeof a) != 0) return fail_cleanup(GENESYS_EINVAL, "bind failed (port in use?)");
+    }
+    const int dev = genesys_internal_device(c);
+    if (cudaSetDevice(dev) != cudaSuccess) return fail_cleanup(GENESYS_ECUDA, "cudaSetDevice");
+    const size_t o_stop = (4ull * n_sockets + 15) & ~size_t(15), o_cnt = o_stop + 16, bytes = o_cnt + 16;
+    if (cudaMalloc(&s->dmem, bytes) != cudaSuccess) return fail_cleanup(GENESYS_ENOMEM, "device memory");
+    uint8_t *d = (uint8_t *)s->dmem;
+    std::vector<int32_t> fds(s->socks.begin(), s->socks.end());
+    if (cudaMemset(d, 0, bytes) != cudaSuccess ||
+        cudaMemcpy(d, fds.data(), 4ull * n_sockets, cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail_cleanup(GENESYS_ECUDA, "upload");
+    s->d_stop = (int32_t *)(d + o_stop);
+    s->d_counters = (unsigned long long *)(d + o_cnt);
+    uint8_t *areas = (uint8_t *)genesys_staging(c, area_bytes * n_sockets);
+    if (!areas) return fail_cleanup(GENESYS_ENOMEM, "staging arena too small for the echo buffers");
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->ctl, cudaStreamNonBlocking) != cudaSuccess)
+      return fail_cleanup(GENESYS_ECUDA, "streams");
+    genesys_dev g;
+    genesys_device_view(c, &g);
+    const int32_t *d_fds = (const int32_t *)d;
+    uint64_t ab = area_bytes;
+    uint32_t bt = batch, st = stride;
+    volatile int32_t *stop = s->d_stop;
+    uint64_t idle = idle_timeout_ns ? idle_timeout_ns : 10000000000ull;
+    unsigned long long *cnt = s->d_counters;
+    void *args[] = {&g, &d_fds, &areas, &ab, &bt, &st, &stop, &idle, &cnt};
+    const uint32_t g3[3] = {n_sockets, 1, 1}, b3[3] = {threads, 1, 1};
+    const void *k = form == GENESYS_ECHO_BATCH ? (const void *)&echo_server_kernel<true>
+                                               : (const void *)&echo_server_kernel<false>;
+    const int rc = genesys_launch(c, k, g3, b3, 0, args, GENESYS_GRAN_GROUP | GENESYS_LAUNCH_RELAXED, s->stream);
+    if (rc) return fail_cleanup(rc, genesys_last_error());
+    s->running = true;
+    *out = s;
+    return 0;
+  });
 }
 
 extern "C" int genesys_echo_stop(genesys_echo_server *s, uint64_t timeout_ns, uint64_t *stats) {
-  if (!s) return set_err(GENESYS_EINVAL, "NULL server");
-  int rc = 0;
-  if (s->running) {
-    const int32_t one = 1;
-    cudaMemcpyAsync(s->d_stop, &one, 4, cudaMemcpyHostToDevice, s->ctl);
-    cudaStreamSynchronize(s->ctl);
-    const uint64_t until = mono_ns() + timeout_ns;
-    while (cudaStreamQuery(s->stream) == cudaErrorNotReady) {
-      if (mono_ns() > until) { rc = set_err(GENESYS_ETIMEDOUT, "echo server did not stop"); break; }
-      std::this_thread::sleep_for(std::chrono::microseconds(100));
+  return genesys_guard("genesys_echo_stop", [&]() -> int {
+    if (!s) return set_err(GENESYS_EINVAL, "NULL server");
+    int rc = 0;
+    if (s->running) {
+      const int32_t one = 1;
+      cudaMemcpyAsync(s->d_stop, &one, 4, cudaMemcpyHostToDevice, s->ctl);
+      cudaStreamSynchronize(s->ctl);
+      const uint64_t until = mono_ns() + timeout_ns;
+      while (cudaStreamQuery(s->stream) == cudaErrorNotReady) {
+        if (mono_ns() > until) { rc = set_err(GENESYS_ETIMEDOUT, "echo server did not stop"); break; }
+        std::this_thread::sleep_for(std::chrono::microseconds(100));
+      }
+      if (rc == 0) {
+        cudaStreamSynchronize(s->stream);
+        rc = genesys_drain(s->ctx, timeout_ns);
+      }
+      s->running = false;
     }
-    if (rc == 0) {
-      cudaStreamSynchronize(s->stream);
-      rc = genesys_drain(s->ctx, timeout_ns);
+    if (stats) {
+      unsigned long long v[2] = {0, 0};
+      cudaMemcpy(v, s->d_counters, sizeof v, cudaMemcpyDeviceToHost);
+      stats[0] = v[0];
+      stats[1] = v[1];
     }
-    s->running = false;
-  }
-  if (stats) {
-    unsigned long long v[2] = {0, 0};
-    cudaMemcpy(v, s->d_counters, sizeof v, cudaMemcpyDeviceToHost);
-    stats[0] = v[0];
-    stats[1] = v[1];
-  }
-  if (rc) return rc;  // the kernel may still run: keep its memory
-  for (int fd : s->socks) close(fd);
-  cudaFree(s->dmem);
-  cudaStreamDestroy(s->stream);
-  cudaStreamDestroy(s->ctl);
-  genesys_internal_staging_release(s->ctx, s->staging_mark);
-  delete s;
-  return 0;
+    if (rc) return rc;  // the kernel may still run: keep its memory
+    for (int fd : s->socks) close(fd);
+    cudaFree(s->dmem);
+    cudaStreamDestroy(s->stream);
+    cudaStreamDestroy(s->ctl);
+    genesys_internal_staging_release(s->ctx, s->staging_mark);
+    delete s;
+    return 0;
+  });
 }
 
 // ---------------------------------------------------------------- client
@@ -465,45 +469,48 @@ void echo_client_thread(uint32_t t, uint32_t n_threads, uint16_t port_base, uint
 extern "C" int genesys_echo_client(uint16_t port_base, uint32_t n_sockets, uint32_t packet_bytes, uint64_t n_packets,
                                    uint32_t window, uint32_t n_threads, uint64_t seed, uint64_t stall_ns,
                                    uint32_t send_stop, uint64_t *stats) {
-  if (!stats || n_sockets == 0 || packet_bytes < kHeader || packet_bytes > GENESYS_ECHO_PACKET_MAX || window == 0 ||
-      n_threads == 0)
-    return set_err(GENESYS_EINVAL, "bad argument");
-  n_threads = std::min(n_threads, n_sockets);
-  std::vector<EchoTally> tally(n_threads);
-  std::vector<std::thread> th;
-  for (uint32_t t = 0; t < n_threads; ++t) {
-    const uint64_t quota = n_packets / n_threads + (t < n_packets % n_threads ? 1 : 0);
-    th.emplace_back(echo_client_thread, t, n_threads, port_base, n_sockets, packet_bytes, quota, window, seed,
-                    stall_ns ? stall_ns : 200000000ull, &tally[t]);
-  }
-  for (auto &x : th) x.join();
-  EchoTally S;
-  for (auto &T : tally) {
-    S.sent += T.sent; S.echoed += T.echoed; S.bad += T.bad; S.lost += T.lost; S.bytes += T.bytes;
-    S.send_err += T.send_err;
-    S.first = std::min(S.first, T.first);
-    S.last = std::max(S.last, T.last);
-  }
-  if (send_stop) {
-    int fd = socket(AF_INET, SOCK_DGRAM, 0);
-    if (fd >= 0) {
-      for (uint32_t w = 0; w < n_sockets; ++w) {
-        const uint8_t stop[GENESYS_ECHO_STOP_BYTES] = {0};
-        sockaddr_in to{};
-        to.sin_family = AF_INET;
-        to.sin_port = htons((uint16_t)(port_base + w));
-        to.sin_addr.s_addr = htonl(INADDR_LOOPBACK);
-        sendto(fd, stop, sizeof stop, 0, (sockaddr *)&to, sizeof to);
-      }
-      close(fd);
+  return genesys_guard("genesys_echo_client", [&]() -> int {
+    if (!stats || n_sockets == 0 || packet_bytes < kHeader || packet_bytes > GENESYS_ECHO_PACKET_MAX || window == 0 ||
+        n_threads == 0)
+      return set_err(GENESYS_EINVAL, "bad argument");
+    n_threads = std::min(n_threads, n_sockets);
+    std::vector<EchoTally> tally(n_threads);
+    std::vector<std::thread> th;
+    genesys_joiner join_all{th};
+    for (uint32_t t = 0; t < n_threads; ++t) {
+      const uint64_t quota = n_packets / n_threads + (t < n_packets % n_threads ? 1 : 0);
+      th.emplace_back(echo_client_thread, t, n_threads, port_base, n_sockets, packet_bytes, quota, window, seed,
+                      stall_ns ? stall_ns : 200000000ull, &tally[t]);
     }
-  }
-  stats[0] = S.sent;
-  stats[1] = S.echoed;
-  stats[2] = S.bad;
-  stats[3] = S.lost;
-  stats[4] = S.last > S.first ? S.last - S.first : 0;
-  stats[5] = S.bytes;
-  stats[6] = S.send_err;
-  return 0;
+    for (auto &x : th) x.join();
+    EchoTally S;
+    for (auto &T : tally) {
+      S.sent += T.sent; S.echoed += T.echoed; S.bad += T.bad; S.lost += T.lost; S.bytes += T.bytes;
+      S.send_err += T.send_err;
+      S.first = std::min(S.first, T.first);
+      S.last = std::max(S.last, T.last);
+    }
+    if (send_stop) {
+      int fd = socket(AF_INET, SOCK_DGRAM, 0);
+      if (fd >= 0) {
+        for (uint32_t w = 0; w < n_sockets; ++w) {
+          const uint8_t stop[GENESYS_ECHO_STOP_BYTES] = {0};
+          sockaddr_in to{};
+          to.sin_family = AF_INET;
+          to.sin_port = htons((uint16_t)(port_base + w));
+          to.sin_addr.s_addr = htonl(INADDR_LOOPBACK);
+          sendto(fd, stop, sizeof stop, 0, (sockaddr *)&to, sizeof to);
+        }
+        close(fd);
+      }
+    }
+    stats[0] = S.sent;
+    stats[1] = S.echoed;
+    stats[2] = S.bad;
+    stats[3] = S.lost;
+    stats[4] = S.last > S.first ? S.last - S.first : 0;
+    stats[5] = S.bytes;
+    stats[6] = S.send_err;
+    return 0;
+  });
 }

@@ -3,6 +3,8 @@
 
 #include <stddef.h>
 
+#include "genesys.h"
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -34,4 +36,50 @@ int genesys_internal_clock_offset(int device, uint32_t rounds, uint64_t timeout_
 
 #ifdef __cplusplus
 }
+
+#include <stdio.h>
+
+#include <exception>
+#include <new>
+#include <system_error>
+#include <thread>
+#include <vector>
+
+/* C++ exceptions must not cross the C ABI (a ctypes or C caller would be
+ * terminated): an entry point whose body allocates host containers or starts
+ * threads runs it through genesys_guard, which turns an exception into an
+ * error code and a message.  bad_alloc and system_error (a thread that cannot
+ * start) become GENESYS_ENOMEM, anything else GENESYS_EINVAL.  The message is
+ * formatted into a fixed buffer: no allocation while handling. */
+template <class Body>
+static inline int genesys_guard(const char *where, Body &&body) noexcept {
+  char msg[256];
+  try {
+    return body();
+  } catch (const std::bad_alloc &) {
+    snprintf(msg, sizeof msg, "%s: out of host memory", where);
+    return genesys_internal_error(GENESYS_ENOMEM, msg);
+  } catch (const std::system_error &e) {
+    snprintf(msg, sizeof msg, "%s: %s", where, e.what());
+    return genesys_internal_error(GENESYS_ENOMEM, msg);
+  } catch (const std::exception &e) {
+    snprintf(msg, sizeof msg, "%s: %s", where, e.what());
+    return genesys_internal_error(GENESYS_EINVAL, msg);
+  } catch (...) {
+    snprintf(msg, sizeof msg, "%s: unexpected exception", where);
+    return genesys_internal_error(GENESYS_EINVAL, msg);
+  }
+}
+
+/* Joins the threads of `th` that are still joinable when it goes out of
+ * scope, also when an exception or an early return leaves the scope:
+ * destroying a joinable std::thread would terminate the process.  Every wait
+ * of those threads is bounded, so the joins end. */
+struct genesys_joiner {
+  std::vector<std::thread> &th;
+  ~genesys_joiner() {
+    for (auto &t : th)
+      if (t.joinable()) t.join();
+  }
+};
 #endif

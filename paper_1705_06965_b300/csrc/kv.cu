@@ -279,136 +279,142 @@ struct genesys_kv_server {
 extern "C" int genesys_kv_start(genesys_ctx *c, const uint8_t *keys, const uint16_t *vlen0, const uint64_t *vseed0,
                                 uint32_t n_keys, uint32_t n_sockets, uint32_t batch, uint32_t threads,
                                 uint16_t port_base, uint64_t idle_timeout_ns, genesys_kv_server **out) {
-  if (!c || !keys || !vlen0 || !vseed0 || !out || n_keys == 0) return set_err(GENESYS_EINVAL, "NULL argument");
-  if (n_sockets == 0 || n_sockets > 1024 || batch == 0 || batch > kMaxBatch || threads < 32 || threads > 1024 ||
-      threads % 32)
-    return set_err(GENESYS_EINVAL, "n_sockets 1..1024, batch 1..64, threads 32..1024 (multiple of 32)");
-  for (uint32_t i = 0; i < n_keys; ++i)
-    if (vlen0[i] > kVal) return set_err(GENESYS_EINVAL, "value longer than GENESYS_KV_VALUE_MAX");
-  auto s = new genesys_kv_server();
-  s->ctx = c;
-  s->n_sockets = n_sockets;
-  s->batch = batch;
-  s->n_keys = n_keys;
-  auto fail_cleanup = [&](int code, const char *msg) {
-    for (int fd : s->socks) close(fd);
-    if (s->dmem) cudaFree(s->dmem);
-    if (s->stream) cudaStreamDestroy(s->stream);
-    if (s->ctl) cudaStreamDestroy(s->ctl);
-    genesys_internal_staging_release(c, s->staging_mark);
-    delete s;
-    return set_err(code, msg);
-  };
-  // sockets: 127.0.0.1:port_base + w, large receive buffers
-  for (uint32_t w = 0; w < n_sockets; ++w) {
-    int fd = socket(AF_INET, SOCK_DGRAM, 0);
-    if (fd < 0) return fail_cleanup(GENESYS_EINVAL, "socket failed");
-    s->socks.push_back(fd);
-    int buf = 64 << 20;
-    setsockopt(fd, SOL_SOCKET, SO_RCVBUF, &buf, sizeof buf);
-    setsockopt(fd, SOL_SOCKET, SO_SNDBUF, &buf, sizeof buf);
-    sockaddr_in a{};
-    a.sin_family = AF_INET;
-    a.sin_port = htons((uint16_t)(port_base + w));
-    a.sin_addr.s_addr = htonl(INADDR_LOOPBACK);
-    if (bind(fd, (sockaddr *)&a, sizeof a) != 0) return fail_cleanup(GENESYS_EINVAL, "bind failed (port in use?)");
-  }
-  const int dev = genesys_internal_device(c);
-  if (cudaSetDevice(dev) != cudaSuccess) return fail_cleanup(GENESYS_ECUDA, "cudaSetDevice");
-  uint32_t index_size = 1;
-  while (index_size < 2 * n_keys) index_size <<= 1;
-  // device memory: fds | stop | served | index | keys | vals | vlens | vlen0 | vseed0
-  size_t off = 0;
-  auto take = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) & ~size_t(255); return o; };
-  const size_t o_fds = take(4 * n_sockets), o_stop = take(4), o_served = take(8), o_index = take(4ull * index_size),
-               o_keys = take(16ull * n_keys), o_vals = take((size_t)kVal * n_keys), o_vlens = take(2ull * n_keys),
-               o_vlen0 = take(2ull * n_keys), o_vseed0 = take(8ull * n_keys);
-  if (cudaMalloc(&s->dmem, off) != cudaSuccess) return fail_cleanup(GENESYS_ENOMEM, "device memory for the table");
-  uint8_t *d = (uint8_t *)s->dmem;
-  std::vector<int32_t> fds(s->socks.begin(), s->socks.end());
-  if (cudaMemset(d, 0, o_keys) != cudaSuccess ||
-      cudaMemcpy(d + o_fds, fds.data(), 4 * n_sockets, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(d + o_keys, keys, 16ull * n_keys, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(d + o_vlen0, vlen0, 2ull * n_keys, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(d + o_vseed0, vseed0, 8ull * n_keys, cudaMemcpyHostToDevice) != cudaSuccess)
-    return fail_cleanup(GENESYS_ECUDA, "upload of the table");
-  s->d_stop = (int32_t *)(d + o_stop);
-  s->d_served = (unsigned long long *)(d + o_served);
-  s->d_vals = d + o_vals;
-  s->d_vlens = (uint16_t *)(d + o_vlens);
-  kv_build_kernel<<<n_keys, 128>>>(d + o_keys, (const uint16_t *)(d + o_vlen0), (const uint64_t *)(d + o_vseed0),
-                                   n_keys, (uint32_t *)(d + o_index), index_size - 1, d + o_vals, s->d_vlens);
-  if (cudaDeviceSynchronize() != cudaSuccess) return fail_cleanup(GENESYS_ECUDA, "table build");
-  // staging: one message area per block
-  s->staging_mark = genesys_internal_staging_mark(c);
-  KvBlockArea *areas = (KvBlockArea *)genesys_staging(c, sizeof(KvBlockArea) * n_sockets);
-  if (!areas) return fail_cleanup(GENESYS_ENOMEM, "staging arena too small for the message areas");
-  if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s->ctl, cudaStreamNonBlocking) != cudaSuccess)
-    return fail_cleanup(GENESYS_ECUDA, "streams");
-  genesys_dev g;
-  genesys_device_view(c, &g);
-  const int32_t *d_fds = (const int32_t *)(d + o_fds);
-  const uint8_t *d_keys = d + o_keys;
-  const uint32_t *d_index = (const uint32_t *)(d + o_index);
-  uint32_t imask = index_size - 1, bt = batch;
-  uint8_t *vals = s->d_vals;
-  uint16_t *vl = s->d_vlens;
-  volatile int32_t *stop = s->d_stop;
-  uint64_t idle = idle_timeout_ns ? idle_timeout_ns : 10000000000ull;
-  unsigned long long *served = s->d_served;
-  void *args[] = {&g, &d_fds, &areas, &bt, &d_keys, &d_index, &imask, &vals, &vl, &stop, &idle, &served};
-  const uint32_t g3[3] = {n_sockets, 1, 1}, b3[3] = {threads, 1, 1};
-  int rc = genesys_launch(c, (const void *)&kv_server_kernel, g3, b3, 0, args,
-                          GENESYS_GRAN_GROUP | GENESYS_LAUNCH_RELAXED, s->stream);
-  if (rc) return fail_cleanup(rc, genesys_last_error());
-  s->running = true;
-  *out = s;
-  return 0;
+  return genesys_guard("genesys_kv_start", [&]() -> int {
+    if (!c || !keys || !vlen0 || !vseed0 || !out || n_keys == 0) return set_err(GENESYS_EINVAL, "NULL argument");
+    if (n_sockets == 0 || n_sockets > 1024 || batch == 0 || batch > kMaxBatch || threads < 32 || threads > 1024 ||
+        threads % 32)
+      return set_err(GENESYS_EINVAL, "n_sockets 1..1024, batch 1..64, threads 32..1024 (multiple of 32)");
+    for (uint32_t i = 0; i < n_keys; ++i)
+      if (vlen0[i] > kVal) return set_err(GENESYS_EINVAL, "value longer than GENESYS_KV_VALUE_MAX");
+    auto s = new genesys_kv_server();
+    s->ctx = c;
+    s->n_sockets = n_sockets;
+    s->batch = batch;
+    s->n_keys = n_keys;
+    auto fail_cleanup = [&](int code, const char *msg) {
+      for (int fd : s->socks) close(fd);
+      if (s->dmem) cudaFree(s->dmem);
+      if (s->stream) cudaStreamDestroy(s->stream);
+      if (s->ctl) cudaStreamDestroy(s->ctl);
+      genesys_internal_staging_release(c, s->staging_mark);
+      delete s;
+      return set_err(code, msg);
+    };
+    // sockets: 127.0.0.1:port_base + w, large receive buffers
+    for (uint32_t w = 0; w < n_sockets; ++w) {
+      int fd = socket(AF_INET, SOCK_DGRAM, 0);
+      if (fd < 0) return fail_cleanup(GENESYS_EINVAL, "socket failed");
+      s->socks.push_back(fd);
+      int buf = 64 << 20;
+      setsockopt(fd, SOL_SOCKET, SO_RCVBUF, &buf, sizeof buf);
+      setsockopt(fd, SOL_SOCKET, SO_SNDBUF, &buf, sizeof buf);
+      sockaddr_in a{};
+      a.sin_family = AF_INET;
+      a.sin_port = htons((uint16_t)(port_base + w));
+      a.sin_addr.s_addr = htonl(INADDR_LOOPBACK);
+      if (bind(fd, (sockaddr *)&a, sizeof a) != 0) return fail_cleanup(GENESYS_EINVAL, "bind failed (port in use?)");
+    }
+    const int dev = genesys_internal_device(c);
+    if (cudaSetDevice(dev) != cudaSuccess) return fail_cleanup(GENESYS_ECUDA, "cudaSetDevice");
+    uint32_t index_size = 1;
+    while (index_size < 2 * n_keys) index_size <<= 1;
+    // device memory: fds | stop | served | index | keys | vals | vlens | vlen0 | vseed0
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) & ~size_t(255); return o; };
+    const size_t o_fds = take(4 * n_sockets), o_stop = take(4), o_served = take(8), o_index = take(4ull * index_size),
+                 o_keys = take(16ull * n_keys), o_vals = take((size_t)kVal * n_keys), o_vlens = take(2ull * n_keys),
+                 o_vlen0 = take(2ull * n_keys), o_vseed0 = take(8ull * n_keys);
+    if (cudaMalloc(&s->dmem, off) != cudaSuccess) return fail_cleanup(GENESYS_ENOMEM, "device memory for the table");
+    uint8_t *d = (uint8_t *)s->dmem;
+    std::vector<int32_t> fds(s->socks.begin(), s->socks.end());
+    if (cudaMemset(d, 0, o_keys) != cudaSuccess ||
+        cudaMemcpy(d + o_fds, fds.data(), 4 * n_sockets, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d + o_keys, keys, 16ull * n_keys, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d + o_vlen0, vlen0, 2ull * n_keys, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d + o_vseed0, vseed0, 8ull * n_keys, cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail_cleanup(GENESYS_ECUDA, "upload of the table");
+    s->d_stop = (int32_t *)(d + o_stop);
+    s->d_served = (unsigned long long *)(d + o_served);
+    s->d_vals = d + o_vals;
+    s->d_vlens = (uint16_t *)(d + o_vlens);
+    kv_build_kernel<<<n_keys, 128>>>(d + o_keys, (const uint16_t *)(d + o_vlen0), (const uint64_t *)(d + o_vseed0),
+                                     n_keys, (uint32_t *)(d + o_index), index_size - 1, d + o_vals, s->d_vlens);
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail_cleanup(GENESYS_ECUDA, "table build");
+    // staging: one message area per block
+    s->staging_mark = genesys_internal_staging_mark(c);
+    KvBlockArea *areas = (KvBlockArea *)genesys_staging(c, sizeof(KvBlockArea) * n_sockets);
+    if (!areas) return fail_cleanup(GENESYS_ENOMEM, "staging arena too small for the message areas");
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->ctl, cudaStreamNonBlocking) != cudaSuccess)
+      return fail_cleanup(GENESYS_ECUDA, "streams");
+    genesys_dev g;
+    genesys_device_view(c, &g);
+    const int32_t *d_fds = (const int32_t *)(d + o_fds);
+    const uint8_t *d_keys = d + o_keys;
+    const uint32_t *d_index = (const uint32_t *)(d + o_index);
+    uint32_t imask = index_size - 1, bt = batch;
+    uint8_t *vals = s->d_vals;
+    uint16_t *vl = s->d_vlens;
+    volatile int32_t *stop = s->d_stop;
+    uint64_t idle = idle_timeout_ns ? idle_timeout_ns : 10000000000ull;
+    unsigned long long *served = s->d_served;
+    void *args[] = {&g, &d_fds, &areas, &bt, &d_keys, &d_index, &imask, &vals, &vl, &stop, &idle, &served};
+    const uint32_t g3[3] = {n_sockets, 1, 1}, b3[3] = {threads, 1, 1};
+    int rc = genesys_launch(c, (const void *)&kv_server_kernel, g3, b3, 0, args,
+                            GENESYS_GRAN_GROUP | GENESYS_LAUNCH_RELAXED, s->stream);
+    if (rc) return fail_cleanup(rc, genesys_last_error());
+    s->running = true;
+    *out = s;
+    return 0;
+  });
 }
 
 extern "C" int genesys_kv_stop(genesys_kv_server *s, uint64_t timeout_ns, uint64_t *served) {
-  if (!s) return set_err(GENESYS_EINVAL, "NULL server");
-  int rc = 0;
-  if (s->running) {
-    // ask the blocks to leave once idle (they also leave on a STOP message)
-    const int32_t one = 1;
-    cudaMemcpyAsync(s->d_stop, &one, 4, cudaMemcpyHostToDevice, s->ctl);
-    cudaStreamSynchronize(s->ctl);
-    const uint64_t until = mono_ns() + timeout_ns;
-    while (cudaStreamQuery(s->stream) == cudaErrorNotReady) {
-      if (mono_ns() > until) { rc = set_err(GENESYS_ETIMEDOUT, "kv server did not stop"); break; }
-      std::this_thread::sleep_for(std::chrono::microseconds(100));
+  return genesys_guard("genesys_kv_stop", [&]() -> int {
+    if (!s) return set_err(GENESYS_EINVAL, "NULL server");
+    int rc = 0;
+    if (s->running) {
+      // ask the blocks to leave once idle (they also leave on a STOP message)
+      const int32_t one = 1;
+      cudaMemcpyAsync(s->d_stop, &one, 4, cudaMemcpyHostToDevice, s->ctl);
+      cudaStreamSynchronize(s->ctl);
+      const uint64_t until = mono_ns() + timeout_ns;
+      while (cudaStreamQuery(s->stream) == cudaErrorNotReady) {
+        if (mono_ns() > until) { rc = set_err(GENESYS_ETIMEDOUT, "kv server did not stop"); break; }
+        std::this_thread::sleep_for(std::chrono::microseconds(100));
+      }
+      if (rc == 0) {
+        cudaStreamSynchronize(s->stream);
+        rc = genesys_drain(s->ctx, timeout_ns);
+      }
+      s->running = false;
     }
-    if (rc == 0) {
-      cudaStreamSynchronize(s->stream);
-      rc = genesys_drain(s->ctx, timeout_ns);
+    if (served) {
+      unsigned long long v = 0;
+      cudaMemcpy(&v, s->d_served, 8, cudaMemcpyDeviceToHost);
+      *served = v;
     }
-    s->running = false;
-  }
-  if (served) {
-    unsigned long long v = 0;
-    cudaMemcpy(&v, s->d_served, 8, cudaMemcpyDeviceToHost);
-    *served = v;
-  }
-  if (rc) return rc;  // the kernel may still run: keep its memory
-  for (int fd : s->socks) close(fd);
-  cudaFree(s->dmem);
-  cudaStreamDestroy(s->stream);
-  cudaStreamDestroy(s->ctl);
-  genesys_internal_staging_release(s->ctx, s->staging_mark);
-  delete s;
-  return 0;
+    if (rc) return rc;  // the kernel may still run: keep its memory
+    for (int fd : s->socks) close(fd);
+    cudaFree(s->dmem);
+    cudaStreamDestroy(s->stream);
+    cudaStreamDestroy(s->ctl);
+    genesys_internal_staging_release(s->ctx, s->staging_mark);
+    delete s;
+    return 0;
+  });
 }
 
 // Copy the current value of key `k` (for checks): returns its length.
 extern "C" int genesys_kv_value(genesys_kv_server *s, uint32_t k, uint8_t *out) {
-  if (!s || !out || k >= s->n_keys) return set_err(GENESYS_EINVAL, "bad argument");
-  uint16_t len = 0;
-  if (cudaMemcpy(&len, s->d_vlens + k, 2, cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemcpy(out, s->d_vals + (size_t)k * kVal, len, cudaMemcpyDeviceToHost) != cudaSuccess)
-    return set_err(GENESYS_ECUDA, "copy");
-  return len;
+  return genesys_guard("genesys_kv_value", [&]() -> int {
+    if (!s || !out || k >= s->n_keys) return set_err(GENESYS_EINVAL, "bad argument");
+    uint16_t len = 0;
+    if (cudaMemcpy(&len, s->d_vlens + k, 2, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(out, s->d_vals + (size_t)k * kVal, len, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return set_err(GENESYS_ECUDA, "copy");
+    return len;
+  });
 }
 
 // ---------------------------------------------------------------- client
@@ -507,77 +513,80 @@ void kv_client_thread(int fd, const std::vector<uint64_t> &mine, const uint8_t *
 extern "C" int genesys_kv_client(const uint8_t *reqs, const uint64_t *req_off, uint64_t n, const uint64_t *arrival_ns,
                                  uint16_t port_base, uint32_t n_sockets, uint64_t timeout_ns, uint8_t *replies,
                                  uint32_t *reply_len, uint64_t *latency_ns, uint64_t *stats) {
-  if (!reqs || !req_off || !arrival_ns || !replies || !reply_len || !latency_ns || n_sockets == 0)
-    return set_err(GENESYS_EINVAL, "NULL argument");
-  const uint32_t n_threads = std::min<uint32_t>(n_sockets, 4);
-  std::vector<int> fds;
-  for (uint32_t w = 0; w < n_threads; ++w) {
-    int fd = socket(AF_INET, SOCK_DGRAM, 0);
-    if (fd < 0) break;
-    int want = 64 << 20;
-    if (setsockopt(fd, SOL_SOCKET, SO_RCVBUFFORCE, &want, sizeof want) != 0)
-      setsockopt(fd, SOL_SOCKET, SO_RCVBUF, &want, sizeof want);
-    if (setsockopt(fd, SOL_SOCKET, SO_SNDBUFFORCE, &want, sizeof want) != 0)
-      setsockopt(fd, SOL_SOCKET, SO_SNDBUF, &want, sizeof want);
-    sockaddr_in me{};
-    me.sin_family = AF_INET;
-    me.sin_addr.s_addr = htonl(INADDR_LOOPBACK);
-    if (bind(fd, (sockaddr *)&me, sizeof me) != 0) { close(fd); break; }
-    fds.push_back(fd);
-  }
-  if (fds.size() != n_threads) {
-    for (int fd : fds) close(fd);
-    return set_err(GENESYS_EINVAL, "client socket or bind failed");
-  }
-  std::vector<uint64_t> t_send(n, 0);
-  memset(reply_len, 0, sizeof(uint32_t) * n);
-  std::vector<std::vector<uint64_t>> owned(n_threads);
-  for (uint64_t j = 0; j < n; ++j) {
-    uint32_t k0;
-    memcpy(&k0, reqs + req_off[j] + 8, 4);
-    owned[(k0 % n_sockets) % n_threads].push_back(j);
-  }
-  std::vector<KvClientTally> tally(n_threads);
-  const uint64_t t0 = mono_ns() + 2000000;  // start in 2 ms, once the threads run
-  const uint64_t deadline = t0 + (n ? arrival_ns[n - 1] : 0) + timeout_ns;
-  std::vector<std::thread> th;
-  for (uint32_t w = 0; w < n_threads; ++w)
-    th.emplace_back(kv_client_thread, fds[w], std::cref(owned[w]), reqs, req_off, n, arrival_ns, t0, port_base,
-                    n_sockets, deadline, replies, reply_len, latency_ns, t_send.data(), &tally[w]);
-  for (auto &t : th) t.join();
-  // STOP to every socket (no reply)
-  for (uint32_t w = 0; w < n_sockets; ++w) {
-    uint8_t stop[24] = {GENESYS_KV_STOP};
-    sockaddr_in to{};
-    to.sin_family = AF_INET;
-    to.sin_port = htons((uint16_t)(port_base + w));
-    to.sin_addr.s_addr = htonl(INADDR_LOOPBACK);
-    sendto(fds[0], stop, sizeof stop, 0, (sockaddr *)&to, sizeof to);
-  }
-  for (int fd : fds) close(fd);
-  KvClientTally S;
-  for (auto &T : tally) {
-    S.received += T.received;
-    S.dup += T.dup;
-    S.bad += T.bad;
-    S.send_err += T.send_err;
-    S.late_max = std::max(S.late_max, T.late_max);
-    S.timed_out |= T.timed_out;
-  }
-  if (stats) {
-    stats[0] = S.received;
-    stats[1] = S.dup;
-    stats[2] = S.bad;
-    stats[3] = S.send_err;
-    stats[4] = S.late_max;
-    uint64_t first = ~0ull, last = 0;
-    for (uint64_t j = 0; j < n; ++j) {
-      if (!reply_len[j]) continue;
-      first = std::min(first, t_send[j]);
-      last = std::max(last, t_send[j] + latency_ns[j]);
+  return genesys_guard("genesys_kv_client", [&]() -> int {
+    if (!reqs || !req_off || !arrival_ns || !replies || !reply_len || !latency_ns || n_sockets == 0)
+      return set_err(GENESYS_EINVAL, "NULL argument");
+    const uint32_t n_threads = std::min<uint32_t>(n_sockets, 4);
+    std::vector<uint64_t> t_send(n, 0);  // before any socket is opened: this may throw
+    std::vector<int> fds;
+    for (uint32_t w = 0; w < n_threads; ++w) {
+      int fd = socket(AF_INET, SOCK_DGRAM, 0);
+      if (fd < 0) break;
+      int want = 64 << 20;
+      if (setsockopt(fd, SOL_SOCKET, SO_RCVBUFFORCE, &want, sizeof want) != 0)
+        setsockopt(fd, SOL_SOCKET, SO_RCVBUF, &want, sizeof want);
+      if (setsockopt(fd, SOL_SOCKET, SO_SNDBUFFORCE, &want, sizeof want) != 0)
+        setsockopt(fd, SOL_SOCKET, SO_SNDBUF, &want, sizeof want);
+      sockaddr_in me{};
+      me.sin_family = AF_INET;
+      me.sin_addr.s_addr = htonl(INADDR_LOOPBACK);
+      if (bind(fd, (sockaddr *)&me, sizeof me) != 0) { close(fd); break; }
+      fds.push_back(fd);
     }
-    stats[5] = last > first ? last - first : 0;  // first send to last reply
-  }
-  if (S.timed_out) return set_err(GENESYS_ETIMEDOUT, "kv client: replies missing at the deadline");
-  return 0;
+    if (fds.size() != n_threads) {
+      for (int fd : fds) close(fd);
+      return set_err(GENESYS_EINVAL, "client socket or bind failed");
+    }
+    memset(reply_len, 0, sizeof(uint32_t) * n);
+    std::vector<std::vector<uint64_t>> owned(n_threads);
+    for (uint64_t j = 0; j < n; ++j) {
+      uint32_t k0;
+      memcpy(&k0, reqs + req_off[j] + 8, 4);
+      owned[(k0 % n_sockets) % n_threads].push_back(j);
+    }
+    std::vector<KvClientTally> tally(n_threads);
+    const uint64_t t0 = mono_ns() + 2000000;  // start in 2 ms, once the threads run
+    const uint64_t deadline = t0 + (n ? arrival_ns[n - 1] : 0) + timeout_ns;
+    std::vector<std::thread> th;
+    genesys_joiner join_all{th};
+    for (uint32_t w = 0; w < n_threads; ++w)
+      th.emplace_back(kv_client_thread, fds[w], std::cref(owned[w]), reqs, req_off, n, arrival_ns, t0, port_base,
+                      n_sockets, deadline, replies, reply_len, latency_ns, t_send.data(), &tally[w]);
+    for (auto &t : th) t.join();
+    // STOP to every socket (no reply)
+    for (uint32_t w = 0; w < n_sockets; ++w) {
+      uint8_t stop[24] = {GENESYS_KV_STOP};
+      sockaddr_in to{};
+      to.sin_family = AF_INET;
+      to.sin_port = htons((uint16_t)(port_base + w));
+      to.sin_addr.s_addr = htonl(INADDR_LOOPBACK);
+      sendto(fds[0], stop, sizeof stop, 0, (sockaddr *)&to, sizeof to);
+    }
+    for (int fd : fds) close(fd);
+    KvClientTally S;
+    for (auto &T : tally) {
+      S.received += T.received;
+      S.dup += T.dup;
+      S.bad += T.bad;
+      S.send_err += T.send_err;
+      S.late_max = std::max(S.late_max, T.late_max);
+      S.timed_out |= T.timed_out;
+    }
+    if (stats) {
+      stats[0] = S.received;
+      stats[1] = S.dup;
+      stats[2] = S.bad;
+      stats[3] = S.send_err;
+      stats[4] = S.late_max;
+      uint64_t first = ~0ull, last = 0;
+      for (uint64_t j = 0; j < n; ++j) {
+        if (!reply_len[j]) continue;
+        first = std::min(first, t_send[j]);
+        last = std::max(last, t_send[j] + latency_ns[j]);
+      }
+      stats[5] = last > first ? last - first : 0;  // first send to last reply
+    }
+    if (S.timed_out) return set_err(GENESYS_ETIMEDOUT, "kv client: replies missing at the deadline");
+    return 0;
+  });
 }

@@ -757,123 +757,141 @@ int genesys_config_default(genesys_config *cfg) {
 }
 
 int genesys_init(const genesys_config *cfg_in, int device, genesys_ctx **out) {
-  if (!out) return fail(GENESYS_EINVAL, "out is NULL");
-  *out = nullptr;
-  genesys_config cfg;
-  if (cfg_in) cfg = *cfg_in; else genesys_config_default(&cfg);
-  if (cfg.n_service_threads == 0 || cfg.n_service_threads > 256)
-    return fail(GENESYS_EINVAL, "n_service_threads must be 1..256");
-  if (cfg.coalesce_max == 0) cfg.coalesce_max = 1;
-  if (cfg.device_deadline_ns == 0) return fail(GENESYS_EINVAL, "device_deadline_ns must be > 0");
-  if (cfg.poll_min_ns == 0) cfg.poll_min_ns = 256;
-  if (cfg.poll_max_ns < cfg.poll_min_ns) cfg.poll_max_ns = cfg.poll_min_ns;
-  if (cfg.poll_max_ns > 1000000) return fail(GENESYS_EINVAL, "poll_max_ns above 1 ms");
+  return genesys_guard("genesys_init", [&]() -> int {
+    if (!out) return fail(GENESYS_EINVAL, "out is NULL");
+    *out = nullptr;
+    genesys_config cfg;
+    if (cfg_in) cfg = *cfg_in; else genesys_config_default(&cfg);
+    if (cfg.n_service_threads == 0 || cfg.n_service_threads > 256)
+      return fail(GENESYS_EINVAL, "n_service_threads must be 1..256");
+    if (cfg.coalesce_max == 0) cfg.coalesce_max = 1;
+    if (cfg.device_deadline_ns == 0) return fail(GENESYS_EINVAL, "device_deadline_ns must be > 0");
+    if (cfg.poll_min_ns == 0) cfg.poll_min_ns = 256;
+    if (cfg.poll_max_ns < cfg.poll_min_ns) cfg.poll_max_ns = cfg.poll_min_ns;
+    if (cfg.poll_max_ns > 1000000) return fail(GENESYS_EINVAL, "poll_max_ns above 1 ms");
 
-  auto c = std::make_unique<genesys_ctx>();
-  c->host_only = (cfg.flags & GENESYS_INIT_HOST_ONLY) != 0;
-  c->device = device;
-  if (!c->host_only) {
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
-      cudaGetLastError();
-      return fail(GENESYS_ENODEV, "no CUDA device");
+    auto c = std::make_unique<genesys_ctx>();
+    // whatever was set up is given back on every failure path (an early
+    // return or an exception) until the context is handed out
+    struct FreeOnFail {
+      genesys_ctx *c;
+      bool armed = true;
+      ~FreeOnFail() { if (armed) free_all(c); }
+    } free_on_fail{c.get()};
+    c->host_only = (cfg.flags & GENESYS_INIT_HOST_ONLY) != 0;
+    c->device = device;
+    if (!c->host_only) {
+      int ndev = 0;
+      if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(GENESYS_ENODEV, "no CUDA device");
+      }
+      if (device < 0 || device >= ndev) return fail(GENESYS_EINVAL, "device %d out of range", device);
+      CUDA_TRY(cudaSetDevice(device));
+      int sms = 0, mapped = 0;
+      CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+      CUDA_TRY(cudaDeviceGetAttribute(&mapped, cudaDevAttrCanMapHostMemory, device));
+      if (!mapped) return fail(GENESYS_ENODEV, "device cannot map host memory");
+      c->n_sms = (uint32_t)sms;
+      CUDA_TRY(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+      CUDA_TRY(cudaEventCreate(&c->ev_start));
+      CUDA_TRY(cudaEventCreate(&c->ev_end));
+    } else {
+      c->n_sms = 0;
     }
-    if (device < 0 || device >= ndev) return fail(GENESYS_EINVAL, "device %d out of range", device);
-    CUDA_TRY(cudaSetDevice(device));
-    int sms = 0, mapped = 0;
-    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
-    CUDA_TRY(cudaDeviceGetAttribute(&mapped, cudaDevAttrCanMapHostMemory, device));
-    if (!mapped) return fail(GENESYS_ENODEV, "device cannot map host memory");
-    c->n_sms = (uint32_t)sms;
-    CUDA_TRY(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
-    CUDA_TRY(cudaEventCreate(&c->ev_start));
-    CUDA_TRY(cudaEventCreate(&c->ev_end));
-  } else {
-    c->n_sms = 0;
-  }
-  if (cfg.n_slots == 0) cfg.n_slots = c->host_only ? 65536u : c->n_sms * 2048u;
-  if (cfg.n_slots < 32) cfg.n_slots = 32;
-  c->cfg = cfg;
+    if (cfg.n_slots == 0) cfg.n_slots = c->host_only ? 65536u : c->n_sms * 2048u;
+    if (cfg.n_slots < 32) cfg.n_slots = 32;
+    c->cfg = cfg;
 
-  // doorbell rings: ring r receives the slots s with genesys_ring_of(s) == r,
-  // each with at most one request outstanding - so a ring whose capacity is
-  // the largest number of slots that map to one ring can never overflow.
-  {
-    std::vector<uint64_t> per(cfg.n_service_threads, 0);
-    const uint32_t gsz = 1u << GENESYS_RING_GROUP_SHIFT;
-    for (uint64_t s0 = 0; s0 < cfg.n_slots; s0 += gsz)
-      per[genesys_ring_of((uint32_t)s0, cfg.n_service_threads)] += std::min<uint64_t>(gsz, cfg.n_slots - s0);
-    const uint64_t most = *std::max_element(per.begin(), per.end());
-    c->ring_cap = (uint32_t)next_pow2(std::max<uint64_t>(most, 64));
-  }
+    // doorbell rings: ring r receives the slots s with genesys_ring_of(s) == r,
+    // each with at most one request outstanding - so a ring whose capacity is
+    // the largest number of slots that map to one ring can never overflow.
+    {
+      std::vector<uint64_t> per(cfg.n_service_threads, 0);
+      const uint32_t gsz = 1u << GENESYS_RING_GROUP_SHIFT;
+      for (uint64_t s0 = 0; s0 < cfg.n_slots; s0 += gsz)
+        per[genesys_ring_of((uint32_t)s0, cfg.n_service_threads)] += std::min<uint64_t>(gsz, cfg.n_slots - s0);
+      const uint64_t most = *std::max_element(per.begin(), per.end());
+      c->ring_cap = (uint32_t)next_pow2(std::max<uint64_t>(most, 64));
+    }
 
-  int rc;
-  auto cleanup = [&](int code) { free_all(c.get()); return code; };
-  if ((rc = host_alloc(c.get(), &c->slots, (size_t)cfg.n_slots * sizeof(genesys_slot)))) return cleanup(rc);
-  if ((rc = host_alloc(c.get(), &c->done, (size_t)cfg.n_slots * 8))) return cleanup(rc);
-  if ((rc = host_alloc(c.get(), &c->rings, (size_t)cfg.n_service_threads * c->ring_cap * 8))) return cleanup(rc);
-  if ((rc = host_alloc(c.get(), &c->ring_done, (size_t)cfg.n_service_threads * GENESYS_RING_DONE_COPIES * 64)))
-    return cleanup(rc);
-  if (cfg.staging_bytes && (rc = host_alloc(c.get(), &c->staging, cfg.staging_bytes))) return cleanup(rc);
-  if ((rc = dev_alloc(c.get(), &c->owner, cfg.n_slots))) return cleanup(rc);
-  if ((rc = dev_alloc(c.get(), &c->seq, cfg.n_slots))) return cleanup(rc);
-  if ((rc = dev_alloc(c.get(), &c->known_done, cfg.n_slots))) return cleanup(rc);
-  if ((rc = dev_alloc(c.get(), &c->ring_tail, (size_t)cfg.n_service_threads * 32))) return cleanup(rc);
-  if ((rc = dev_alloc(c.get(), &c->ksite, GENESYS_KSITES))) return cleanup(rc);
-  if ((rc = dev_alloc(c.get(), &c->grid_bar, 64))) return cleanup(rc);
-  if ((rc = dev_alloc(c.get(), &c->status, GENESYS_ST_WORDS))) return cleanup(rc);
-  if ((rc = dev_alloc(c.get(), &c->lat, std::max<uint32_t>(cfg.lat_samples, 1)))) return cleanup(rc);
-  if ((rc = dev_alloc(c.get(), &c->lat_count, 1))) return cleanup(rc);
-  if (cfg.trace_capacity) {
-    if ((rc = dev_alloc(c.get(), &c->trace, cfg.trace_capacity))) return cleanup(rc);
-    if ((rc = dev_alloc(c.get(), &c->trace_count, 1))) return cleanup(rc);
-  }
+    int rc;
+    if ((rc = host_alloc(c.get(), &c->slots, (size_t)cfg.n_slots * sizeof(genesys_slot)))) return rc;
+    if ((rc = host_alloc(c.get(), &c->done, (size_t)cfg.n_slots * 8))) return rc;
+    if ((rc = host_alloc(c.get(), &c->rings, (size_t)cfg.n_service_threads * c->ring_cap * 8))) return rc;
+    if ((rc = host_alloc(c.get(), &c->ring_done, (size_t)cfg.n_service_threads * GENESYS_RING_DONE_COPIES * 64)))
+      return rc;
+    if (cfg.staging_bytes && (rc = host_alloc(c.get(), &c->staging, cfg.staging_bytes))) return rc;
+    if ((rc = dev_alloc(c.get(), &c->owner, cfg.n_slots))) return rc;
+    if ((rc = dev_alloc(c.get(), &c->seq, cfg.n_slots))) return rc;
+    if ((rc = dev_alloc(c.get(), &c->known_done, cfg.n_slots))) return rc;
+    if ((rc = dev_alloc(c.get(), &c->ring_tail, (size_t)cfg.n_service_threads * 32))) return rc;
+    if ((rc = dev_alloc(c.get(), &c->ksite, GENESYS_KSITES))) return rc;
+    if ((rc = dev_alloc(c.get(), &c->grid_bar, 64))) return rc;
+    if ((rc = dev_alloc(c.get(), &c->status, GENESYS_ST_WORDS))) return rc;
+    if ((rc = dev_alloc(c.get(), &c->lat, std::max<uint32_t>(cfg.lat_samples, 1)))) return rc;
+    if ((rc = dev_alloc(c.get(), &c->lat_count, 1))) return rc;
+    if (cfg.trace_capacity) {
+      if ((rc = dev_alloc(c.get(), &c->trace, cfg.trace_capacity))) return rc;
+      if ((rc = dev_alloc(c.get(), &c->trace_count, 1))) return rc;
+    }
 
-  const uint32_t nr = cfg.n_service_threads;
-  c->head.assign(nr, 0);
-  c->retired.reset(new std::atomic<uint64_t>[nr]);
-  for (uint32_t r = 0; r < nr; ++r) c->retired[r].store(0);
-  c->counters.reset(new Counters[nr]);
-  c->ring_stop.reset(new std::atomic<bool>[nr]);
-  for (uint32_t r = 0; r < nr; ++r) c->ring_stop[r].store(false);
-#ifdef GENESYS_DEVICE_CHECKS
-  c->last_seq.assign(cfg.n_slots, 0);
-#endif
-  c->created_ns = mono_ns();
-  c->trace_n.reset(new std::atomic<uint32_t>[nr]);
-  for (uint32_t r = 0; r < nr; ++r) c->trace_n[r].store(0);
-  if (cfg.trace_capacity) c->trace_host.assign(nr, std::vector<genesys_trace_host>((cfg.trace_capacity + nr - 1) / nr));
-  if (!(cfg.flags & GENESYS_INIT_NO_THREADS)) {
-    for (uint32_t r = 0; r < nr; ++r) c->threads.emplace_back(service_main, c.get(), r);
-  }
-  *out = c.release();
-  return 0;
+    const uint32_t nr = cfg.n_service_threads;
+    c->head.assign(nr, 0);
+    c->retired.reset(new std::atomic<uint64_t>[nr]);
+    for (uint32_t r = 0; r < nr; ++r) c->retired[r].store(0);
+    c->counters.reset(new Counters[nr]);
+    c->ring_stop.reset(new std::atomic<bool>[nr]);
+    for (uint32_t r = 0; r < nr; ++r) c->ring_stop[r].store(false);
+  #ifdef GENESYS_DEVICE_CHECKS
+    c->last_seq.assign(cfg.n_slots, 0);
+  #endif
+    c->created_ns = mono_ns();
+    c->trace_n.reset(new std::atomic<uint32_t>[nr]);
+    for (uint32_t r = 0; r < nr; ++r) c->trace_n[r].store(0);
+    if (cfg.trace_capacity) c->trace_host.assign(nr, std::vector<genesys_trace_host>((cfg.trace_capacity + nr - 1) / nr));
+    if (!(cfg.flags & GENESYS_INIT_NO_THREADS)) {
+      try {
+        for (uint32_t r = 0; r < nr; ++r) c->threads.emplace_back(service_main, c.get(), r);
+      } catch (...) {  // a thread could not start: stop the ones that did
+        c->stop.store(true);
+        for (auto &t : c->threads) t.join();
+        c->threads.clear();
+        throw;
+      }
+    }
+    free_on_fail.armed = false;
+    *out = c.release();
+    return 0;
+  });
 }
 
 int genesys_drain(genesys_ctx *c, uint64_t timeout_ns) {
-  if (!c) return fail(GENESYS_EINVAL, "ctx is NULL");
-  std::vector<uint32_t> tails(c->cfg.n_service_threads);
-  int rc = read_tails(c, tails);
-  if (rc) return rc;
-  std::unique_ptr<Batch> batch;  // NO_THREADS mode: the caller services the rings
-  const uint64_t until = mono_ns() + timeout_ns;
-  for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) {
-    for (;;) {
-      // positions are 32-bit on the device: compare modulo 2^32
-      const uint32_t got = (uint32_t)c->retired[r].load(std::memory_order_acquire);
-      if ((int32_t)(got - tails[r]) >= 0) break;
-      if (c->cfg.flags & GENESYS_INIT_NO_THREADS) {
-        std::lock_guard<std::mutex> g(c->svc_mu);
-        if (!batch) batch.reset(new Batch(std::max<uint32_t>(1, c->cfg.coalesce_max)));
-        poll_ring(c, r, *batch);
-      } else {
-        std::this_thread::sleep_for(std::chrono::microseconds(5));
+  return genesys_guard("genesys_drain", [&]() -> int {
+    if (!c) return fail(GENESYS_EINVAL, "ctx is NULL");
+    std::vector<uint32_t> tails(c->cfg.n_service_threads);
+    int rc = read_tails(c, tails);
+    if (rc) return rc;
+    std::unique_ptr<Batch> batch;  // NO_THREADS mode: the caller services the rings
+    const uint64_t until = mono_ns() + timeout_ns;
+    for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) {
+      for (;;) {
+        // positions are 32-bit on the device: compare modulo 2^32
+        const uint32_t got = (uint32_t)c->retired[r].load(std::memory_order_acquire);
+        if ((int32_t)(got - tails[r]) >= 0) break;
+        if (c->cfg.flags & GENESYS_INIT_NO_THREADS) {
+          std::lock_guard<std::mutex> g(c->svc_mu);
+          if (!batch) batch.reset(new Batch(std::max<uint32_t>(1, c->cfg.coalesce_max)));
+          poll_ring(c, r, *batch);
+        } else {
+          std::this_thread::sleep_for(std::chrono::microseconds(5));
+        }
+        if (mono_ns() > until)
+          return fail(GENESYS_ETIMEDOUT, "drain: ring %u retired %u of %u requests", r, got, tails[r]);
       }
-      if (mono_ns() > until)
-        return fail(GENESYS_ETIMEDOUT, "drain: ring %u retired %u of %u requests", r, got, tails[r]);
     }
-  }
-  return 0;
+    return 0;
+  });
 }
 
 // CPU time a running service thread has used so far (0 if unavailable).
@@ -904,42 +922,46 @@ uint32_t genesys_sizeof(int which) {
 }
 
 int genesys_service_health(genesys_ctx *c, uint64_t stall_ns, uint64_t *stalled_mask, uint64_t *pending) {
-  if (!c || !stalled_mask) return fail(GENESYS_EINVAL, "NULL argument");
-  std::vector<uint32_t> tails(c->cfg.n_service_threads);
-  int rc = read_tails(c, tails);
-  if (rc) return rc;
-  const uint64_t now = mono_ns();
-  uint64_t mask = 0, total = 0;
-  for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) {
-    // positions are 32-bit on the device: the distance modulo 2^32; the
-    // service may have passed the tails read above (requests published and
-    // finished since), which counts as nothing waiting
-    const int32_t d = (int32_t)(tails[r] - (uint32_t)c->retired[r].load(std::memory_order_acquire));
-    const uint32_t waiting = d > 0 ? (uint32_t)d : 0u;
-    total += waiting;
-    const uint64_t last = c->counters[r].last_batch_ns.load(std::memory_order_relaxed);
-    if (waiting && now - std::max(last, c->created_ns) > stall_ns && r < 64) mask |= 1ull << r;
-  }
-  *stalled_mask = mask;
-  if (pending) *pending = total;
-  return 0;
+  return genesys_guard("genesys_service_health", [&]() -> int {
+    if (!c || !stalled_mask) return fail(GENESYS_EINVAL, "NULL argument");
+    std::vector<uint32_t> tails(c->cfg.n_service_threads);
+    int rc = read_tails(c, tails);
+    if (rc) return rc;
+    const uint64_t now = mono_ns();
+    uint64_t mask = 0, total = 0;
+    for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) {
+      // positions are 32-bit on the device: the distance modulo 2^32; the
+      // service may have passed the tails read above (requests published and
+      // finished since), which counts as nothing waiting
+      const int32_t d = (int32_t)(tails[r] - (uint32_t)c->retired[r].load(std::memory_order_acquire));
+      const uint32_t waiting = d > 0 ? (uint32_t)d : 0u;
+      total += waiting;
+      const uint64_t last = c->counters[r].last_batch_ns.load(std::memory_order_relaxed);
+      if (waiting && now - std::max(last, c->created_ns) > stall_ns && r < 64) mask |= 1ull << r;
+    }
+    *stalled_mask = mask;
+    if (pending) *pending = total;
+    return 0;
+  });
 }
 
 int genesys_service_restart(genesys_ctx *c, uint32_t ring, uint64_t pause_ns) {
-  if (!c) return fail(GENESYS_EINVAL, "ctx is NULL");
-  if (c->threads.empty()) return fail(GENESYS_EINVAL, "the context has no service threads");
-  if (ring >= c->cfg.n_service_threads) return fail(GENESYS_EINVAL, "no ring %u", ring);
-  std::lock_guard<std::mutex> g(c->restart_mu);
-  // the thread finishes the batch it has and leaves; its ring position (head)
-  // stays with the context, so the new thread continues where it stopped
-  c->ring_stop[ring].store(true);
-  const uint64_t used = thread_cpu_ns(c->threads[ring]);  // read before it leaves: its clock goes with it
-  c->threads[ring].join();
-  c->cpu_retired_ns.fetch_add(used);
-  if (pause_ns) std::this_thread::sleep_for(std::chrono::nanoseconds(pause_ns));
-  c->ring_stop[ring].store(false);
-  c->threads[ring] = std::thread(service_main, c, ring);
-  return 0;
+  return genesys_guard("genesys_service_restart", [&]() -> int {
+    if (!c) return fail(GENESYS_EINVAL, "ctx is NULL");
+    if (c->threads.empty()) return fail(GENESYS_EINVAL, "the context has no service threads");
+    if (ring >= c->cfg.n_service_threads) return fail(GENESYS_EINVAL, "no ring %u", ring);
+    std::lock_guard<std::mutex> g(c->restart_mu);
+    // the thread finishes the batch it has and leaves; its ring position (head)
+    // stays with the context, so the new thread continues where it stopped
+    c->ring_stop[ring].store(true);
+    const uint64_t used = thread_cpu_ns(c->threads[ring]);  // read before it leaves: its clock goes with it
+    c->threads[ring].join();
+    c->cpu_retired_ns.fetch_add(used);
+    if (pause_ns) std::this_thread::sleep_for(std::chrono::nanoseconds(pause_ns));
+    c->ring_stop[ring].store(false);
+    c->threads[ring] = std::thread(service_main, c, ring);
+    return 0;
+  });
 }
 
 int genesys_shutdown(genesys_ctx *c) {
@@ -1034,47 +1056,51 @@ int genesys_last_launch_ms(genesys_ctx *c, float *ms) {
 }
 
 int genesys_service(genesys_ctx *c, uint64_t timeout_ns) {
-  if (!c) return fail(GENESYS_EINVAL, "ctx is NULL");
-  const uint64_t until = mono_ns() + timeout_ns;
-  if (c->cfg.flags & GENESYS_INIT_NO_THREADS) {
-    std::lock_guard<std::mutex> g(c->svc_mu);
-    Batch batch(std::max<uint32_t>(1, c->cfg.coalesce_max));
-    int total = 0;
-    do {
-      size_t n = 0;
-      for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) n += poll_ring(c, r, batch);
-      total += (int)n;
-      if (n == 0) cpu_relax();
-    } while (mono_ns() < until);
-    return total;
-  }
-  return genesys_drain(c, timeout_ns);
+  return genesys_guard("genesys_service", [&]() -> int {
+    if (!c) return fail(GENESYS_EINVAL, "ctx is NULL");
+    const uint64_t until = mono_ns() + timeout_ns;
+    if (c->cfg.flags & GENESYS_INIT_NO_THREADS) {
+      std::lock_guard<std::mutex> g(c->svc_mu);
+      Batch batch(std::max<uint32_t>(1, c->cfg.coalesce_max));
+      int total = 0;
+      do {
+        size_t n = 0;
+        for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) n += poll_ring(c, r, batch);
+        total += (int)n;
+        if (n == 0) cpu_relax();
+      } while (mono_ns() < until);
+      return total;
+    }
+    return genesys_drain(c, timeout_ns);
+  });
 }
 
 int genesys_mmap_reserve(genesys_ctx *c, const uint64_t *sizes, uint32_t n) {
-  if (!c || (!sizes && n)) return fail(GENESYS_EINVAL, "NULL argument");
-  if (c->host_only) return fail(GENESYS_EINVAL, "host-only context");
-  for (uint32_t i = 0; i < n; ++i) {
-    const size_t len = (size_t)((sizes[i] + 4095) & ~uint64_t(4095));
-    if (len == 0) continue;
-    void *p = mmap(nullptr, len, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
-    if (p == MAP_FAILED) return fail(GENESYS_ENOMEM, "mmap of %zu bytes failed", len);
-    if (cudaHostRegister(p, len, cudaHostRegisterMapped | cudaHostRegisterPortable) != cudaSuccess) {
-      cudaGetLastError();
-      munmap(p, len);
-      return fail(GENESYS_ECUDA, "cudaHostRegister of %zu bytes failed", len);
+  return genesys_guard("genesys_mmap_reserve", [&]() -> int {
+    if (!c || (!sizes && n)) return fail(GENESYS_EINVAL, "NULL argument");
+    if (c->host_only) return fail(GENESYS_EINVAL, "host-only context");
+    for (uint32_t i = 0; i < n; ++i) {
+      const size_t len = (size_t)((sizes[i] + 4095) & ~uint64_t(4095));
+      if (len == 0) continue;
+      void *p = mmap(nullptr, len, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+      if (p == MAP_FAILED) return fail(GENESYS_ENOMEM, "mmap of %zu bytes failed", len);
+      if (cudaHostRegister(p, len, cudaHostRegisterMapped | cudaHostRegisterPortable) != cudaSuccess) {
+        cudaGetLastError();
+        munmap(p, len);
+        return fail(GENESYS_ECUDA, "cudaHostRegister of %zu bytes failed", len);
+      }
+      void *d = nullptr;
+      if (cudaHostGetDevicePointer(&d, p, 0) != cudaSuccess) {
+        cudaGetLastError();
+        cudaHostUnregister(p);
+        munmap(p, len);
+        return fail(GENESYS_ECUDA, "cudaHostGetDevicePointer failed");
+      }
+      std::lock_guard<std::mutex> g(c->map_mu);
+      c->released.emplace(len, std::make_pair((uintptr_t)d, genesys_ctx::Mapping{p, len, len}));
     }
-    void *d = nullptr;
-    if (cudaHostGetDevicePointer(&d, p, 0) != cudaSuccess) {
-      cudaGetLastError();
-      cudaHostUnregister(p);
-      munmap(p, len);
-      return fail(GENESYS_ECUDA, "cudaHostGetDevicePointer failed");
-    }
-    std::lock_guard<std::mutex> g(c->map_mu);
-    c->released.emplace(len, std::make_pair((uintptr_t)d, genesys_ctx::Mapping{p, len, len}));
-  }
-  return 0;
+    return 0;
+  });
 }
 
 int genesys_reclaim(genesys_ctx *c) {
@@ -1084,32 +1110,34 @@ int genesys_reclaim(genesys_ctx *c) {
 }
 
 int genesys_stats_get(genesys_ctx *c, genesys_stats *o) {
-  if (!c || !o) return fail(GENESYS_EINVAL, "NULL argument");
-  memset(o, 0, sizeof *o);
-  for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) {
-    Counters &k = c->counters[r];
-    o->requests += k.requests.load();
-    o->os_calls += k.os_calls.load();
-    o->failed += k.failed.load();
-    o->nonblocking_failed += k.nb_failed.load();
-    o->bytes += k.bytes.load();
-    o->batches += k.batches.load();
-    o->busy_ns += k.busy_ns.load();
-    for (int i = 0; i < 8; ++i) {
-      o->by_op[i] += k.by_op[i].load();
-      o->op_ns[i] += k.op_ns[i].load();
-      o->op_max_ns[i] = std::max<uint64_t>(o->op_max_ns[i], k.op_max_ns[i].load());
+  return genesys_guard("genesys_stats_get", [&]() -> int {
+    if (!c || !o) return fail(GENESYS_EINVAL, "NULL argument");
+    memset(o, 0, sizeof *o);
+    for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) {
+      Counters &k = c->counters[r];
+      o->requests += k.requests.load();
+      o->os_calls += k.os_calls.load();
+      o->failed += k.failed.load();
+      o->nonblocking_failed += k.nb_failed.load();
+      o->bytes += k.bytes.load();
+      o->batches += k.batches.load();
+      o->busy_ns += k.busy_ns.load();
+      for (int i = 0; i < 8; ++i) {
+        o->by_op[i] += k.by_op[i].load();
+        o->op_ns[i] += k.op_ns[i].load();
+        o->op_max_ns[i] = std::max<uint64_t>(o->op_max_ns[i], k.op_max_ns[i].load());
+      }
     }
-  }
-  o->mmap_new = c->mmap_new.load();
-  o->mmap_reused = c->mmap_reused.load();
-  {
-    std::lock_guard<std::mutex> g(c->restart_mu);  // the thread list is stable
-    const uint64_t cpu = service_cpu_total(c);
-    o->service_cpu_ns = cpu > c->cpu_reset_ns ? cpu - c->cpu_reset_ns : 0;
-  }
-  o->protocol_errors = c->protocol_errors.load();
-  return 0;
+    o->mmap_new = c->mmap_new.load();
+    o->mmap_reused = c->mmap_reused.load();
+    {
+      std::lock_guard<std::mutex> g(c->restart_mu);  // the thread list is stable
+      const uint64_t cpu = service_cpu_total(c);
+      o->service_cpu_ns = cpu > c->cpu_reset_ns ? cpu - c->cpu_reset_ns : 0;
+    }
+    o->protocol_errors = c->protocol_errors.load();
+    return 0;
+  });
 }
 
 int genesys_stats_reset(genesys_ctx *c) {
@@ -1126,34 +1154,36 @@ int genesys_stats_reset(genesys_ctx *c) {
 
 int genesys_trace_read(genesys_ctx *c, genesys_trace_dev *dev, uint32_t dev_cap, uint32_t *n_dev,
                        genesys_trace_host *host, uint32_t host_cap, uint32_t *n_host, int64_t *host_minus_device_ns) {
-  if (!c || (dev_cap && !dev) || (host_cap && !host)) return fail(GENESYS_EINVAL, "NULL argument");
-  if (!c->cfg.trace_capacity) return fail(GENESYS_EINVAL, "the context keeps no trace (trace_capacity 0)");
-  uint32_t nd = 0;
-  if (!c->host_only) {
-    CUDA_TRY(cudaMemcpy(&nd, c->trace_count, 4, cudaMemcpyDeviceToHost));
-    const uint32_t k = std::min({nd, c->cfg.trace_capacity, dev_cap});
-    if (k) CUDA_TRY(cudaMemcpy(dev, c->trace, (size_t)k * sizeof(genesys_trace_dev), cudaMemcpyDeviceToHost));
-    CUDA_TRY(cudaMemset(c->trace_count, 0, 4));
-  }
-  if (n_dev) *n_dev = nd;
-  uint32_t nh = 0, out = 0;
-  for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) {
-    const uint32_t n = c->trace_n[r].load(std::memory_order_acquire);
-    const uint32_t have = std::min<uint32_t>(n, (uint32_t)c->trace_host[r].size());
-    for (uint32_t i = 0; i < have && out < host_cap; ++i) host[out++] = c->trace_host[r][i];
-    nh += n;
-    c->trace_n[r].store(0, std::memory_order_release);
-  }
-  if (n_host) *n_host = nh;
-  if (host_minus_device_ns) {
-    if (c->host_only) {
-      *host_minus_device_ns = 0;
-    } else {
-      int rc = genesys_internal_clock_offset(c->device, 200, 2000000000ull, host_minus_device_ns, nullptr);
-      if (rc) return rc;
+  return genesys_guard("genesys_trace_read", [&]() -> int {
+    if (!c || (dev_cap && !dev) || (host_cap && !host)) return fail(GENESYS_EINVAL, "NULL argument");
+    if (!c->cfg.trace_capacity) return fail(GENESYS_EINVAL, "the context keeps no trace (trace_capacity 0)");
+    uint32_t nd = 0;
+    if (!c->host_only) {
+      CUDA_TRY(cudaMemcpy(&nd, c->trace_count, 4, cudaMemcpyDeviceToHost));
+      const uint32_t k = std::min({nd, c->cfg.trace_capacity, dev_cap});
+      if (k) CUDA_TRY(cudaMemcpy(dev, c->trace, (size_t)k * sizeof(genesys_trace_dev), cudaMemcpyDeviceToHost));
+      CUDA_TRY(cudaMemset(c->trace_count, 0, 4));
     }
-  }
-  return 0;
+    if (n_dev) *n_dev = nd;
+    uint32_t nh = 0, out = 0;
+    for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) {
+      const uint32_t n = c->trace_n[r].load(std::memory_order_acquire);
+      const uint32_t have = std::min<uint32_t>(n, (uint32_t)c->trace_host[r].size());
+      for (uint32_t i = 0; i < have && out < host_cap; ++i) host[out++] = c->trace_host[r][i];
+      nh += n;
+      c->trace_n[r].store(0, std::memory_order_release);
+    }
+    if (n_host) *n_host = nh;
+    if (host_minus_device_ns) {
+      if (c->host_only) {
+        *host_minus_device_ns = 0;
+      } else {
+        int rc = genesys_internal_clock_offset(c->device, 200, 2000000000ull, host_minus_device_ns, nullptr);
+        if (rc) return rc;
+      }
+    }
+    return 0;
+  });
 }
 
 int genesys_status(genesys_ctx *c, int32_t out[GENESYS_ST_WORDS], int clear) {
@@ -1170,26 +1200,28 @@ int genesys_status(genesys_ctx *c, int32_t out[GENESYS_ST_WORDS], int clear) {
 }
 
 int genesys_latency(genesys_ctx *c, uint64_t *out, uint32_t cap, uint32_t *n_out, int clear) {
-  if (!c || !n_out) return fail(GENESYS_EINVAL, "NULL argument");
-  uint32_t n = 0;
-  if (c->host_only) {
-    n = *c->lat_count;
-  } else {
-    CUDA_TRY(cudaMemcpyAsync(&n, c->lat_count, 4, cudaMemcpyDeviceToHost, c->aux));
-    CUDA_TRY(cudaStreamSynchronize(c->aux));
-  }
-  *n_out = n;
-  const uint32_t m = std::min(std::min(n, cap), c->cfg.lat_samples);
-  if (out && m) {
-    if (c->host_only) memcpy(out, c->lat, (size_t)m * 8);
-    else CUDA_TRY(cudaMemcpyAsync(out, c->lat, (size_t)m * 8, cudaMemcpyDeviceToHost, c->aux));
-  }
-  if (clear) {
-    if (c->host_only) *c->lat_count = 0;
-    else CUDA_TRY(cudaMemsetAsync(c->lat_count, 0, 4, c->aux));
-  }
-  if (!c->host_only) CUDA_TRY(cudaStreamSynchronize(c->aux));
-  return 0;
+  return genesys_guard("genesys_latency", [&]() -> int {
+    if (!c || !n_out) return fail(GENESYS_EINVAL, "NULL argument");
+    uint32_t n = 0;
+    if (c->host_only) {
+      n = *c->lat_count;
+    } else {
+      CUDA_TRY(cudaMemcpyAsync(&n, c->lat_count, 4, cudaMemcpyDeviceToHost, c->aux));
+      CUDA_TRY(cudaStreamSynchronize(c->aux));
+    }
+    *n_out = n;
+    const uint32_t m = std::min(std::min(n, cap), c->cfg.lat_samples);
+    if (out && m) {
+      if (c->host_only) memcpy(out, c->lat, (size_t)m * 8);
+      else CUDA_TRY(cudaMemcpyAsync(out, c->lat, (size_t)m * 8, cudaMemcpyDeviceToHost, c->aux));
+    }
+    if (clear) {
+      if (c->host_only) *c->lat_count = 0;
+      else CUDA_TRY(cudaMemsetAsync(c->lat_count, 0, 4, c->aux));
+    }
+    if (!c->host_only) CUDA_TRY(cudaStreamSynchronize(c->aux));
+    return 0;
+  });
 }
 
 void *genesys_staging(genesys_ctx *c, size_t bytes) {
@@ -1224,141 +1256,145 @@ int genesys_staging_reset(genesys_ctx *c) {
 // usable by kernels.  No kernel may be running on the context meanwhile.
 int genesys_service_probe(genesys_ctx *c, int fd, const void *payload, uint32_t bytes_per_call, uint64_t n_calls,
                           uint64_t *elapsed_ns) {
-  if (!c || !payload || !elapsed_ns || bytes_per_call == 0) return fail(GENESYS_EINVAL, "NULL argument");
-  if (c->threads.empty()) return fail(GENESYS_EINVAL, "genesys_service_probe needs service threads");
-  const uint32_t S = c->cfg.n_slots, R = c->cfg.n_service_threads;
-  std::vector<uint32_t> seq(S), kd(S), owner(S), tails_raw((size_t)R * 32);
-  auto copy = [&](void *dst, const void *src, size_t bytes, cudaMemcpyKind kind) -> int {
-    if (c->host_only) { memcpy(dst, src, bytes); return 0; }
-    CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, kind, c->aux));
-    CUDA_TRY(cudaStreamSynchronize(c->aux));
-    return 0;
-  };
-  int rc;
-  if ((rc = copy(seq.data(), c->seq, 4ull * S, cudaMemcpyDeviceToHost)) ||
-      (rc = copy(kd.data(), c->known_done, 4ull * S, cudaMemcpyDeviceToHost)) ||
-      (rc = copy(owner.data(), c->owner, 4ull * S, cudaMemcpyDeviceToHost)) ||
-      (rc = copy(tails_raw.data(), c->ring_tail, tails_raw.size() * 4, cudaMemcpyDeviceToHost)))
-    return rc;
-  for (uint32_t s = 0; s < S; ++s) {
-    if (owner[s] != 0) return fail(GENESYS_EINVAL, "service probe: slot %u is claimed (a kernel is running?)", s);
-    if ((uint32_t)(__atomic_load_n(&c->done[s], __ATOMIC_ACQUIRE) >> 32) != seq[s])
-      return fail(GENESYS_EINVAL, "service probe: slot %u has a request in flight", s);
-  }
-  const uint64_t deadline = c->cfg.device_deadline_ns;
-  const uint16_t flags = GENESYS_REQ_BLOCKING | (GENESYS_GRAN_ITEM << GENESYS_REQ_GRAN_SHIFT);
-  const uint8_t *base = (const uint8_t *)payload;
-  uint64_t total = 0, bad = 0;
-  for (uint64_t i0 = 0; i0 < n_calls;) {
-    const uint32_t m = (uint32_t)std::min<uint64_t>(S, n_calls - i0);
-    for (uint32_t s = 0; s < m; ++s) {
-      const uint64_t i = i0 + s;
-      genesys_slot *sl = &c->slots[s];
-      const uint64_t a[6] = {(uint64_t)fd, (uint64_t)(uintptr_t)(base + i * bytes_per_call), bytes_per_call,
-                             i * bytes_per_call, 0, 0};
-      for (int k = 0; k < 6; ++k) __atomic_store_n(&sl->args[k], a[k], __ATOMIC_RELAXED);
-      ++seq[s];
-      __atomic_store_n(&sl->req, ((uint64_t)seq[s] << 32) | ((uint64_t)(SYS_pwrite64 & 0xFFFF) << 16) | flags,
-                       __ATOMIC_RELEASE);
+  return genesys_guard("genesys_service_probe", [&]() -> int {
+    if (!c || !payload || !elapsed_ns || bytes_per_call == 0) return fail(GENESYS_EINVAL, "NULL argument");
+    if (c->threads.empty()) return fail(GENESYS_EINVAL, "genesys_service_probe needs service threads");
+    const uint32_t S = c->cfg.n_slots, R = c->cfg.n_service_threads;
+    std::vector<uint32_t> seq(S), kd(S), owner(S), tails_raw((size_t)R * 32);
+    auto copy = [&](void *dst, const void *src, size_t bytes, cudaMemcpyKind kind) -> int {
+      if (c->host_only) { memcpy(dst, src, bytes); return 0; }
+      CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, kind, c->aux));
+      CUDA_TRY(cudaStreamSynchronize(c->aux));
+      return 0;
+    };
+    int rc;
+    if ((rc = copy(seq.data(), c->seq, 4ull * S, cudaMemcpyDeviceToHost)) ||
+        (rc = copy(kd.data(), c->known_done, 4ull * S, cudaMemcpyDeviceToHost)) ||
+        (rc = copy(owner.data(), c->owner, 4ull * S, cudaMemcpyDeviceToHost)) ||
+        (rc = copy(tails_raw.data(), c->ring_tail, tails_raw.size() * 4, cudaMemcpyDeviceToHost)))
+      return rc;
+    for (uint32_t s = 0; s < S; ++s) {
+      if (owner[s] != 0) return fail(GENESYS_EINVAL, "service probe: slot %u is claimed (a kernel is running?)", s);
+      if ((uint32_t)(__atomic_load_n(&c->done[s], __ATOMIC_ACQUIRE) >> 32) != seq[s])
+        return fail(GENESYS_EINVAL, "service probe: slot %u has a request in flight", s);
     }
-    const uint64_t t0 = mono_ns();
-    for (uint32_t s = 0; s < m; ++s) {
-      const uint32_t r = genesys_ring_of(s, R);
-      const uint32_t pos = tails_raw[(size_t)r * 32]++;
-      __atomic_store_n(&c->rings[(size_t)r * c->ring_cap + (pos & (c->ring_cap - 1))], GENESYS_RING_ENTRY(pos, s),
-                       __ATOMIC_RELEASE);
-    }
-    for (uint32_t s = 0; s < m; ++s) {
-      uint64_t d;
-      while ((uint32_t)((d = __atomic_load_n(&c->done[s], __ATOMIC_ACQUIRE)) >> 32) != seq[s]) {
-        if (mono_ns() - t0 > deadline) {
-          rc = fail(GENESYS_ETIMEDOUT, "service probe: slot %u not completed within the deadline", s);
-          break;
-        }
-        cpu_relax();
+    const uint64_t deadline = c->cfg.device_deadline_ns;
+    const uint16_t flags = GENESYS_REQ_BLOCKING | (GENESYS_GRAN_ITEM << GENESYS_REQ_GRAN_SHIFT);
+    const uint8_t *base = (const uint8_t *)payload;
+    uint64_t total = 0, bad = 0;
+    for (uint64_t i0 = 0; i0 < n_calls;) {
+      const uint32_t m = (uint32_t)std::min<uint64_t>(S, n_calls - i0);
+      for (uint32_t s = 0; s < m; ++s) {
+        const uint64_t i = i0 + s;
+        genesys_slot *sl = &c->slots[s];
+        const uint64_t a[6] = {(uint64_t)fd, (uint64_t)(uintptr_t)(base + i * bytes_per_call), bytes_per_call,
+                               i * bytes_per_call, 0, 0};
+        for (int k = 0; k < 6; ++k) __atomic_store_n(&sl->args[k], a[k], __ATOMIC_RELAXED);
+        ++seq[s];
+        __atomic_store_n(&sl->req, ((uint64_t)seq[s] << 32) | ((uint64_t)(SYS_pwrite64 & 0xFFFF) << 16) | flags,
+                         __ATOMIC_RELEASE);
       }
+      const uint64_t t0 = mono_ns();
+      for (uint32_t s = 0; s < m; ++s) {
+        const uint32_t r = genesys_ring_of(s, R);
+        const uint32_t pos = tails_raw[(size_t)r * 32]++;
+        __atomic_store_n(&c->rings[(size_t)r * c->ring_cap + (pos & (c->ring_cap - 1))], GENESYS_RING_ENTRY(pos, s),
+                         __ATOMIC_RELEASE);
+      }
+      for (uint32_t s = 0; s < m; ++s) {
+        uint64_t d;
+        while ((uint32_t)((d = __atomic_load_n(&c->done[s], __ATOMIC_ACQUIRE)) >> 32) != seq[s]) {
+          if (mono_ns() - t0 > deadline) {
+            rc = fail(GENESYS_ETIMEDOUT, "service probe: slot %u not completed within the deadline", s);
+            break;
+          }
+          cpu_relax();
+        }
+        if (rc) break;
+        if ((int32_t)(uint32_t)d != (int32_t)bytes_per_call) ++bad;
+        kd[s] = seq[s];
+      }
+      total += mono_ns() - t0;
       if (rc) break;
-      if ((int32_t)(uint32_t)d != (int32_t)bytes_per_call) ++bad;
-      kd[s] = seq[s];
+      i0 += m;
     }
-    total += mono_ns() - t0;
-    if (rc) break;
-    i0 += m;
-  }
-  // the device-side state the kernels continue from
-  if (c->host_only) {
-    memcpy(c->seq, seq.data(), 4ull * S);
-    memcpy(c->known_done, kd.data(), 4ull * S);
-    for (uint32_t r = 0; r < R; ++r) __atomic_store_n(&c->ring_tail[r * 32], tails_raw[(size_t)r * 32], __ATOMIC_RELEASE);
-  } else {
-    int wrc;
-    if ((wrc = copy(c->seq, seq.data(), 4ull * S, cudaMemcpyHostToDevice)) ||
-        (wrc = copy(c->known_done, kd.data(), 4ull * S, cudaMemcpyHostToDevice)) ||
-        (wrc = copy(c->ring_tail, tails_raw.data(), tails_raw.size() * 4, cudaMemcpyHostToDevice)))
-      return wrc;
-  }
-  if (rc) return rc;
-  *elapsed_ns = total;
-  if (bad) return fail(GENESYS_EINVAL, "service probe: %llu calls returned a short count", (unsigned long long)bad);
-  return 0;
+    // the device-side state the kernels continue from
+    if (c->host_only) {
+      memcpy(c->seq, seq.data(), 4ull * S);
+      memcpy(c->known_done, kd.data(), 4ull * S);
+      for (uint32_t r = 0; r < R; ++r) __atomic_store_n(&c->ring_tail[r * 32], tails_raw[(size_t)r * 32], __ATOMIC_RELEASE);
+    } else {
+      int wrc;
+      if ((wrc = copy(c->seq, seq.data(), 4ull * S, cudaMemcpyHostToDevice)) ||
+          (wrc = copy(c->known_done, kd.data(), 4ull * S, cudaMemcpyHostToDevice)) ||
+          (wrc = copy(c->ring_tail, tails_raw.data(), tails_raw.size() * 4, cudaMemcpyHostToDevice)))
+        return wrc;
+    }
+    if (rc) return rc;
+    *elapsed_ns = total;
+    if (bad) return fail(GENESYS_EINVAL, "service probe: %llu calls returned a short count", (unsigned long long)bad);
+    return 0;
+  });
 }
 
 int genesys_emulate_call(genesys_ctx *c, uint32_t nr, const uint64_t args[6], uint32_t flags, int64_t *ret) {
-  if (!c || !args || !ret) return fail(GENESYS_EINVAL, "NULL argument");
-  if (!c->host_only) return fail(GENESYS_EINVAL, "genesys_emulate_call needs a host-only context");
-  const uint64_t t0 = mono_ns();
-  const uint64_t deadline = c->cfg.device_deadline_ns;
-  static std::atomic<uint32_t> hint_ctr{0};
-  uint32_t s = hint_ctr.fetch_add(1) % c->cfg.n_slots;
-  for (uint32_t probes = 0;; ++probes) {
-    uint32_t expect = 0;
-    if (__atomic_compare_exchange_n(&c->owner[s], &expect, 1u, false, __ATOMIC_ACQUIRE, __ATOMIC_RELAXED)) break;
-    s = (s + 1) % c->cfg.n_slots;
-    if (probes % 64 == 63) {
-      if (mono_ns() - t0 > deadline) return fail(GENESYS_ETIMEDOUT, "no free slot");
-      std::this_thread::yield();
-    }
-  }
-  const uint32_t sq = __atomic_load_n(&c->seq[s], __ATOMIC_RELAXED);
-  if (__atomic_load_n(&c->known_done[s], __ATOMIC_RELAXED) != sq) {
-    while ((uint32_t)(__atomic_load_n(&c->done[s], __ATOMIC_ACQUIRE) >> 32) != sq) {
-      if (mono_ns() - t0 > deadline) {
-        __atomic_store_n(&c->owner[s], 0u, __ATOMIC_RELEASE);
-        return fail(GENESYS_ETIMEDOUT, "slot %u still busy", s);
+  return genesys_guard("genesys_emulate_call", [&]() -> int {
+    if (!c || !args || !ret) return fail(GENESYS_EINVAL, "NULL argument");
+    if (!c->host_only) return fail(GENESYS_EINVAL, "genesys_emulate_call needs a host-only context");
+    const uint64_t t0 = mono_ns();
+    const uint64_t deadline = c->cfg.device_deadline_ns;
+    static std::atomic<uint32_t> hint_ctr{0};
+    uint32_t s = hint_ctr.fetch_add(1) % c->cfg.n_slots;
+    for (uint32_t probes = 0;; ++probes) {
+      uint32_t expect = 0;
+      if (__atomic_compare_exchange_n(&c->owner[s], &expect, 1u, false, __ATOMIC_ACQUIRE, __ATOMIC_RELAXED)) break;
+      s = (s + 1) % c->cfg.n_slots;
+      if (probes % 64 == 63) {
+        if (mono_ns() - t0 > deadline) return fail(GENESYS_ETIMEDOUT, "no free slot");
+        std::this_thread::yield();
       }
-      cpu_relax();
     }
-    __atomic_store_n(&c->known_done[s], sq, __ATOMIC_RELAXED);
-  }
-  const uint32_t nsq = sq + 1;
-  __atomic_store_n(&c->seq[s], nsq, __ATOMIC_RELAXED);
-  genesys_slot *sl = &c->slots[s];
-  for (int i = 0; i < 6; ++i) __atomic_store_n(&sl->args[i], args[i], __ATOMIC_RELAXED);
-  __atomic_store_n(&sl->req, ((uint64_t)nsq << 32) | ((uint64_t)(nr & 0xFFFFu) << 16) | (flags & 0xFFFFu),
-                   __ATOMIC_RELEASE);
-  const uint32_t r = genesys_ring_of(s, c->cfg.n_service_threads);
-  const uint32_t pos = __atomic_fetch_add(&c->ring_tail[r * 32], 1u, __ATOMIC_ACQ_REL);
-  __atomic_store_n(&c->rings[(size_t)r * c->ring_cap + (pos & (c->ring_cap - 1))], GENESYS_RING_ENTRY(pos, s),
-                   __ATOMIC_RELEASE);
-  int64_t result = 0;
-  if (flags & GENESYS_REQ_BLOCKING) {
-    uint64_t d;
-    for (;;) {
-      d = __atomic_load_n(&c->done[s], __ATOMIC_ACQUIRE);
-      if ((uint32_t)(d >> 32) == nsq) break;
-      if (mono_ns() - t0 > deadline) {
-        __atomic_store_n(&c->owner[s], 0u, __ATOMIC_RELEASE);
-        return fail(GENESYS_ETIMEDOUT, "call not completed within the deadline");
+    const uint32_t sq = __atomic_load_n(&c->seq[s], __ATOMIC_RELAXED);
+    if (__atomic_load_n(&c->known_done[s], __ATOMIC_RELAXED) != sq) {
+      while ((uint32_t)(__atomic_load_n(&c->done[s], __ATOMIC_ACQUIRE) >> 32) != sq) {
+        if (mono_ns() - t0 > deadline) {
+          __atomic_store_n(&c->owner[s], 0u, __ATOMIC_RELEASE);
+          return fail(GENESYS_ETIMEDOUT, "slot %u still busy", s);
+        }
+        cpu_relax();
       }
-      if (c->cfg.flags & GENESYS_INIT_NO_THREADS) std::this_thread::yield(); else cpu_relax();
+      __atomic_store_n(&c->known_done[s], sq, __ATOMIC_RELAXED);
     }
-    __atomic_store_n(&c->known_done[s], nsq, __ATOMIC_RELAXED);
-    const uint32_t lo = (uint32_t)d;
-    result = lo == GENESYS_RET_IN_SLOT ? (int64_t)__atomic_load_n(&sl->ret, __ATOMIC_RELAXED) : (int64_t)(int32_t)lo;
-  }
-  __atomic_store_n(&c->owner[s], 0u, __ATOMIC_RELEASE);
-  *ret = result;
-  return 0;
+    const uint32_t nsq = sq + 1;
+    __atomic_store_n(&c->seq[s], nsq, __ATOMIC_RELAXED);
+    genesys_slot *sl = &c->slots[s];
+    for (int i = 0; i < 6; ++i) __atomic_store_n(&sl->args[i], args[i], __ATOMIC_RELAXED);
+    __atomic_store_n(&sl->req, ((uint64_t)nsq << 32) | ((uint64_t)(nr & 0xFFFFu) << 16) | (flags & 0xFFFFu),
+                     __ATOMIC_RELEASE);
+    const uint32_t r = genesys_ring_of(s, c->cfg.n_service_threads);
+    const uint32_t pos = __atomic_fetch_add(&c->ring_tail[r * 32], 1u, __ATOMIC_ACQ_REL);
+    __atomic_store_n(&c->rings[(size_t)r * c->ring_cap + (pos & (c->ring_cap - 1))], GENESYS_RING_ENTRY(pos, s),
+                     __ATOMIC_RELEASE);
+    int64_t result = 0;
+    if (flags & GENESYS_REQ_BLOCKING) {
+      uint64_t d;
+      for (;;) {
+        d = __atomic_load_n(&c->done[s], __ATOMIC_ACQUIRE);
+        if ((uint32_t)(d >> 32) == nsq) break;
+        if (mono_ns() - t0 > deadline) {
+          __atomic_store_n(&c->owner[s], 0u, __ATOMIC_RELEASE);
+          return fail(GENESYS_ETIMEDOUT, "call not completed within the deadline");
+        }
+        if (c->cfg.flags & GENESYS_INIT_NO_THREADS) std::this_thread::yield(); else cpu_relax();
+      }
+      __atomic_store_n(&c->known_done[s], nsq, __ATOMIC_RELAXED);
+      const uint32_t lo = (uint32_t)d;
+      result = lo == GENESYS_RET_IN_SLOT ? (int64_t)__atomic_load_n(&sl->ret, __ATOMIC_RELAXED) : (int64_t)(int32_t)lo;
+    }
+    __atomic_store_n(&c->owner[s], 0u, __ATOMIC_RELEASE);
+    *ret = result;
+    return 0;
+  });
 }
 
 }  // extern "C"

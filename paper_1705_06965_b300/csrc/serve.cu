@@ -303,260 +303,262 @@ extern "C" int genesys_serve_config_default(genesys_serve_config *cfg) {
 extern "C" int genesys_c5_serve(genesys_ctx *c, const genesys_c5_request *reqs, uint32_t n_req, const int32_t *in_fds,
                                 uint32_t n_in, int32_t out_fd, const genesys_serve_config *cfg_in, uint64_t *results,
                                 uint64_t *latency_ns, genesys_serve_stats *stats) {
-  if (!c || (!reqs && n_req) || !in_fds || !results || !latency_ns) return set_err(GENESYS_EINVAL, "NULL argument");
-  genesys_serve_config cfg;
-  if (cfg_in) cfg = *cfg_in; else genesys_serve_config_default(&cfg);
-  const uint32_t bt = cfg.block_threads;
-  if (bt < 32 || bt > 1024 || bt % 32) return set_err(GENESYS_EINVAL, "block_threads: 32..1024, multiple of 32");
-  if (cfg.max_inflight == 0 || cfg.n_streams == 0 || cfg.min_part < 16)
-    return set_err(GENESYS_EINVAL, "max_inflight, n_streams >= 1; min_part >= 16");
-  if (out_fd < 0 || n_in == 0) return set_err(GENESYS_EINVAL, "bad file descriptors");
-  for (uint32_t r = 0; r < n_req; ++r) {
-    if (reqs[r].threads == 0 || reqs[r].n_ops > GENESYS_C5_MAX_OPS) return set_err(GENESYS_EINVAL, "bad request");
-    for (uint32_t k = 0; k < reqs[r].n_ops; ++k) {
-      const genesys_c5_op &op = reqs[r].ops[k];
-      if (op.kind > GENESYS_C5_MMAP || op.len == 0 || (op.kind == GENESYS_C5_PREAD && op.file >= n_in) ||
-          (op.kind == GENESYS_C5_MMAP && op.len % 16))
-        return set_err(GENESYS_EINVAL, "bad operation");
+  return genesys_guard("genesys_c5_serve", [&]() -> int {
+    if (!c || (!reqs && n_req) || !in_fds || !results || !latency_ns) return set_err(GENESYS_EINVAL, "NULL argument");
+    genesys_serve_config cfg;
+    if (cfg_in) cfg = *cfg_in; else genesys_serve_config_default(&cfg);
+    const uint32_t bt = cfg.block_threads;
+    if (bt < 32 || bt > 1024 || bt % 32) return set_err(GENESYS_EINVAL, "block_threads: 32..1024, multiple of 32");
+    if (cfg.max_inflight == 0 || cfg.n_streams == 0 || cfg.min_part < 16)
+      return set_err(GENESYS_EINVAL, "max_inflight, n_streams >= 1; min_part >= 16");
+    if (out_fd < 0 || n_in == 0) return set_err(GENESYS_EINVAL, "bad file descriptors");
+    for (uint32_t r = 0; r < n_req; ++r) {
+      if (reqs[r].threads == 0 || reqs[r].n_ops > GENESYS_C5_MAX_OPS) return set_err(GENESYS_EINVAL, "bad request");
+      for (uint32_t k = 0; k < reqs[r].n_ops; ++k) {
+        const genesys_c5_op &op = reqs[r].ops[k];
+        if (op.kind > GENESYS_C5_MMAP || op.len == 0 || (op.kind == GENESYS_C5_PREAD && op.file >= n_in) ||
+            (op.kind == GENESYS_C5_MMAP && op.len % 16))
+          return set_err(GENESYS_EINVAL, "bad operation");
+      }
+      const Needs nd = needs_of(reqs[r], bt, cfg.min_part, cfg.pread_to_hbm);
+      if (nd.staging > cfg.staging_budget || nd.hbm > cfg.hbm_budget || nd.slots > cfg.slot_budget)
+        return set_err(GENESYS_EINVAL, "a request needs more than the whole budget");
     }
-    const Needs nd = needs_of(reqs[r], bt, cfg.min_part, cfg.pread_to_hbm);
-    if (nd.staging > cfg.staging_budget || nd.hbm > cfg.hbm_budget || nd.slots > cfg.slot_budget)
-      return set_err(GENESYS_EINVAL, "a request needs more than the whole budget");
-  }
-  memset(results, 0, sizeof(uint64_t) * GENESYS_C5_MAX_OPS * n_req);
-  memset(latency_ns, 0, sizeof(uint64_t) * n_req);
-  if (n_req == 0) return 0;
+    memset(results, 0, sizeof(uint64_t) * GENESYS_C5_MAX_OPS * n_req);
+    memset(latency_ns, 0, sizeof(uint64_t) * n_req);
+    if (n_req == 0) return 0;
 
-  genesys_dev g0;
-  genesys_device_view(c, &g0);
-  if (cfg.slot_budget > g0.n_slots) cfg.slot_budget = g0.n_slots;
-  const int dev = genesys_internal_device(c);
-  if (cudaSetDevice(dev) != cudaSuccess) return set_err(GENESYS_ECUDA, "cudaSetDevice");
+    genesys_dev g0;
+    genesys_device_view(c, &g0);
+    if (cfg.slot_budget > g0.n_slots) cfg.slot_budget = g0.n_slots;
+    const int dev = genesys_internal_device(c);
+    if (cudaSetDevice(dev) != cudaSuccess) return set_err(GENESYS_ECUDA, "cudaSetDevice");
 
-  // device state: per launch slot its ops, results (+ error words) and
-  // kernel-grain call records; the input fd table; the HBM landing arena
-  const uint32_t K = cfg.max_inflight;
-  const size_t per_ops = GENESYS_C5_MAX_OPS * sizeof(genesys_c5_op);
-  const size_t per_res = 2 * GENESYS_C5_MAX_OPS * sizeof(unsigned long long);
-  const size_t per_ks = kSitesPerReq * sizeof(genesys_ksite);
-  const size_t per_slot = (per_ops + per_res + per_ks + 255) & ~size_t(255);
-  const size_t fds_off = (size_t)K * per_slot;
-  const size_t land_off = (fds_off + n_in * sizeof(int32_t) + 4095) & ~size_t(4095);
-  void *scratch = nullptr;
-  int rc = genesys_internal_scratch(c, land_off + cfg.hbm_budget + 4096, &scratch);
-  if (rc) return rc;
-  uint8_t *dbase = (uint8_t *)scratch;
-  const uint64_t staging_mark = genesys_internal_staging_mark(c);
-  uint8_t *staging = (uint8_t *)genesys_staging(c, cfg.staging_budget + 4096);
-  if (!staging) return set_err(GENESYS_ENOMEM, "staging arena too small for staging_budget");
-  staging = (uint8_t *)(((uintptr_t)staging + 255) & ~uintptr_t(255));
+    // device state: per launch slot its ops, results (+ error words) and
+    // kernel-grain call records; the input fd table; the HBM landing arena
+    const uint32_t K = cfg.max_inflight;
+    const size_t per_ops = GENESYS_C5_MAX_OPS * sizeof(genesys_c5_op);
+    const size_t per_res = 2 * GENESYS_C5_MAX_OPS * sizeof(unsigned long long);
+    const size_t per_ks = kSitesPerReq * sizeof(genesys_ksite);
+    const size_t per_slot = (per_ops + per_res + per_ks + 255) & ~size_t(255);
+    const size_t fds_off = (size_t)K * per_slot;
+    const size_t land_off = (fds_off + n_in * sizeof(int32_t) + 4095) & ~size_t(4095);
+    void *scratch = nullptr;
+    int rc = genesys_internal_scratch(c, land_off + cfg.hbm_budget + 4096, &scratch);
+    if (rc) return rc;
+    uint8_t *dbase = (uint8_t *)scratch;
+    const uint64_t staging_mark = genesys_internal_staging_mark(c);
+    uint8_t *staging = (uint8_t *)genesys_staging(c, cfg.staging_budget + 4096);
+    if (!staging) return set_err(GENESYS_ENOMEM, "staging arena too small for staging_budget");
+    staging = (uint8_t *)(((uintptr_t)staging + 255) & ~uintptr_t(255));
 
-  std::vector<cudaStream_t> streams(cfg.n_streams);
-  for (auto &s : streams) {
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-      genesys_internal_staging_release(c, staging_mark);
-      return set_err(GENESYS_ECUDA, "stream");
-    }
-  }
-  // pinned host mirrors of each slot's ops and results
-  uint8_t *hmirror = nullptr;
-  if (cudaHostAlloc((void **)&hmirror, (size_t)K * (per_ops + per_res), cudaHostAllocPortable) != cudaSuccess) {
-    for (auto s : streams) cudaStreamDestroy(s);
-    genesys_internal_staging_release(c, staging_mark);
-    return set_err(GENESYS_ECUDA, "pinned mirror");
-  }
-  std::vector<Launch> slots(K);
-  for (auto &L : slots) cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);
-  cudaMemcpy(dbase + fds_off, in_fds, n_in * sizeof(int32_t), cudaMemcpyHostToDevice);
-
-  // GPU mmaps are served from regions mapped and registered now, while no
-  // request kernel runs: per power-of-two size class, as many regions as the
-  // trace has mmaps of that class, at most two per launch slot (blocks of a
-  // request can be one operation apart)
-  {
-    std::map<uint64_t, uint64_t> per_class;
-    for (uint32_t r = 0; r < n_req; ++r)
-      for (uint32_t k = 0; k < reqs[r].n_ops; ++k)
-        if (reqs[r].ops[k].kind == GENESYS_C5_MMAP) {
-          uint64_t cls = 4096;
-          while (cls < reqs[r].ops[k].len) cls <<= 1;
-          per_class[cls] += 1;
-        }
-    std::vector<uint64_t> sizes;
-    for (auto &kv : per_class)
-      for (uint64_t i = 0; i < std::min<uint64_t>(kv.second, 2ull * K); ++i) sizes.push_back(kv.first);
-    if (cfg.reserve_mmaps && !sizes.empty()) {
-      rc = genesys_mmap_reserve(c, sizes.data(), (uint32_t)sizes.size());
-      if (rc) {
-        for (auto s : streams) cudaStreamDestroy(s);
-        cudaFreeHost(hmirror);
+    std::vector<cudaStream_t> streams(cfg.n_streams);
+    for (auto &s : streams) {
+      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
         genesys_internal_staging_release(c, staging_mark);
-        return rc;
+        return set_err(GENESYS_ECUDA, "stream");
       }
     }
-  }
+    // pinned host mirrors of each slot's ops and results
+    uint8_t *hmirror = nullptr;
+    if (cudaHostAlloc((void **)&hmirror, (size_t)K * (per_ops + per_res), cudaHostAllocPortable) != cudaSuccess) {
+      for (auto s : streams) cudaStreamDestroy(s);
+      genesys_internal_staging_release(c, staging_mark);
+      return set_err(GENESYS_ECUDA, "pinned mirror");
+    }
+    std::vector<Launch> slots(K);
+    for (auto &L : slots) cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);
+    cudaMemcpy(dbase + fds_off, in_fds, n_in * sizeof(int32_t), cudaMemcpyHostToDevice);
 
-  RangeAlloc st_alloc(cfg.staging_budget), hbm_alloc(cfg.hbm_budget);
-  uint32_t slots_free = cfg.slot_budget;
-  uint64_t next = 0, retired = 0, launched = 0, calls = 0, admitted_wait_ns = 0;
-  uint64_t max_inflight_seen = 0, inflight = 0, graph_launches = 0;
-  int err = 0;
-  const uint64_t t0 = mono_ns();
-  std::vector<uint64_t> arrival_abs(n_req);
-  for (uint32_t r = 0; r < n_req; ++r) arrival_abs[r] = cfg.honor_arrivals ? t0 + reqs[r].arrival_ns : t0;
+    // GPU mmaps are served from regions mapped and registered now, while no
+    // request kernel runs: per power-of-two size class, as many regions as the
+    // trace has mmaps of that class, at most two per launch slot (blocks of a
+    // request can be one operation apart)
+    {
+      std::map<uint64_t, uint64_t> per_class;
+      for (uint32_t r = 0; r < n_req; ++r)
+        for (uint32_t k = 0; k < reqs[r].n_ops; ++k)
+          if (reqs[r].ops[k].kind == GENESYS_C5_MMAP) {
+            uint64_t cls = 4096;
+            while (cls < reqs[r].ops[k].len) cls <<= 1;
+            per_class[cls] += 1;
+          }
+      std::vector<uint64_t> sizes;
+      for (auto &kv : per_class)
+        for (uint64_t i = 0; i < std::min<uint64_t>(kv.second, 2ull * K); ++i) sizes.push_back(kv.first);
+      if (cfg.reserve_mmaps && !sizes.empty()) {
+        rc = genesys_mmap_reserve(c, sizes.data(), (uint32_t)sizes.size());
+        if (rc) {
+          for (auto s : streams) cudaStreamDestroy(s);
+          cudaFreeHost(hmirror);
+          genesys_internal_staging_release(c, staging_mark);
+          return rc;
+        }
+      }
+    }
 
-  auto launch = [&](uint32_t si, uint32_t r) -> int {
-    Launch &L = slots[si];
-    const genesys_c5_request &q = reqs[r];
-    cudaStream_t s = streams[L.stream];
-    uint8_t *dslot = dbase + (size_t)si * per_slot;
-    genesys_c5_op *d_ops = (genesys_c5_op *)dslot;
-    unsigned long long *d_res = (unsigned long long *)(dslot + per_ops);
-    genesys_ksite *d_ks = (genesys_ksite *)(dslot + per_ops + per_res);
-    uint8_t *h = hmirror + (size_t)si * (per_ops + per_res);
-    memcpy(h, q.ops, q.n_ops * sizeof(genesys_c5_op));
-    if (cudaMemcpyAsync(d_ops, h, q.n_ops * sizeof(genesys_c5_op), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(d_res, 0, per_res + per_ks, s) != cudaSuccess)
-      return -1;
-    genesys_dev g = g0;
-    g.ksite = d_ks;
-    const int32_t *d_fds = (const int32_t *)(dbase + fds_off);
-    uint8_t *st = staging + L.st_off;
-    uint8_t *land = dbase + land_off + L.hbm_off;
-    uint32_t nops = q.n_ops, mp = cfg.min_part, p2h = cfg.pread_to_hbm;
-    int32_t ofd = out_fd;
-    void *args[] = {&g, &d_ops, &nops, &d_fds, &ofd, &st, &land, &d_res, &mp, &p2h};
-    const dim3 grid(L.need.blocks), block(bt);
-    if (cfg.use_graphs) {
-      cudaKernelNodeParams kp{};
-      kp.func = (void *)&c5_request_kernel;
-      kp.gridDim = grid;
-      kp.blockDim = block;
-      kp.sharedMemBytes = 0;
-      kp.kernelParams = args;
-      if (!L.exec) {
-        // one single-kernel graph per launch slot, instantiated once; later
-        // requests on the slot only update the node's parameters
-        if (cudaGraphCreate(&L.graph, 0) != cudaSuccess) return -1;
-        if (cudaGraphAddKernelNode(&L.node, L.graph, nullptr, 0, &kp) != cudaSuccess) return -1;
-        if (cudaGraphInstantiate(&L.exec, L.graph, 0) != cudaSuccess) return -1;
-      } else if (cudaGraphExecKernelNodeSetParams(L.exec, L.node, &kp) != cudaSuccess) {
+    RangeAlloc st_alloc(cfg.staging_budget), hbm_alloc(cfg.hbm_budget);
+    uint32_t slots_free = cfg.slot_budget;
+    uint64_t next = 0, retired = 0, launched = 0, calls = 0, admitted_wait_ns = 0;
+    uint64_t max_inflight_seen = 0, inflight = 0, graph_launches = 0;
+    int err = 0;
+    const uint64_t t0 = mono_ns();
+    std::vector<uint64_t> arrival_abs(n_req);
+    for (uint32_t r = 0; r < n_req; ++r) arrival_abs[r] = cfg.honor_arrivals ? t0 + reqs[r].arrival_ns : t0;
+
+    auto launch = [&](uint32_t si, uint32_t r) -> int {
+      Launch &L = slots[si];
+      const genesys_c5_request &q = reqs[r];
+      cudaStream_t s = streams[L.stream];
+      uint8_t *dslot = dbase + (size_t)si * per_slot;
+      genesys_c5_op *d_ops = (genesys_c5_op *)dslot;
+      unsigned long long *d_res = (unsigned long long *)(dslot + per_ops);
+      genesys_ksite *d_ks = (genesys_ksite *)(dslot + per_ops + per_res);
+      uint8_t *h = hmirror + (size_t)si * (per_ops + per_res);
+      memcpy(h, q.ops, q.n_ops * sizeof(genesys_c5_op));
+      if (cudaMemcpyAsync(d_ops, h, q.n_ops * sizeof(genesys_c5_op), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+          cudaMemsetAsync(d_res, 0, per_res + per_ks, s) != cudaSuccess)
+        return -1;
+      genesys_dev g = g0;
+      g.ksite = d_ks;
+      const int32_t *d_fds = (const int32_t *)(dbase + fds_off);
+      uint8_t *st = staging + L.st_off;
+      uint8_t *land = dbase + land_off + L.hbm_off;
+      uint32_t nops = q.n_ops, mp = cfg.min_part, p2h = cfg.pread_to_hbm;
+      int32_t ofd = out_fd;
+      void *args[] = {&g, &d_ops, &nops, &d_fds, &ofd, &st, &land, &d_res, &mp, &p2h};
+      const dim3 grid(L.need.blocks), block(bt);
+      if (cfg.use_graphs) {
+        cudaKernelNodeParams kp{};
+        kp.func = (void *)&c5_request_kernel;
+        kp.gridDim = grid;
+        kp.blockDim = block;
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = args;
+        if (!L.exec) {
+          // one single-kernel graph per launch slot, instantiated once; later
+          // requests on the slot only update the node's parameters
+          if (cudaGraphCreate(&L.graph, 0) != cudaSuccess) return -1;
+          if (cudaGraphAddKernelNode(&L.node, L.graph, nullptr, 0, &kp) != cudaSuccess) return -1;
+          if (cudaGraphInstantiate(&L.exec, L.graph, 0) != cudaSuccess) return -1;
+        } else if (cudaGraphExecKernelNodeSetParams(L.exec, L.node, &kp) != cudaSuccess) {
+          return -1;
+        }
+        if (cudaGraphLaunch(L.exec, s) != cudaSuccess) return -1;
+        ++graph_launches;
+      } else if (cudaLaunchKernel((const void *)&c5_request_kernel, grid, block, args, 0, s) != cudaSuccess) {
         return -1;
       }
-      if (cudaGraphLaunch(L.exec, s) != cudaSuccess) return -1;
-      ++graph_launches;
-    } else if (cudaLaunchKernel((const void *)&c5_request_kernel, grid, block, args, 0, s) != cudaSuccess) {
-      return -1;
-    }
-    if (cudaMemcpyAsync(h + per_ops, d_res, per_res, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaEventRecord(L.done, s) != cudaSuccess)
-      return -1;
-    return 0;
-  };
+      if (cudaMemcpyAsync(h + per_ops, d_res, per_res, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaEventRecord(L.done, s) != cudaSuccess)
+        return -1;
+      return 0;
+    };
 
-  const uint64_t deadline = t0 + cfg.timeout_ns;
-  while (retired < n_req && !err) {
-    bool progress = false;
-    // retire finished requests
-    for (uint32_t si = 0; si < K; ++si) {
-      Launch &L = slots[si];
-      if (!L.busy) continue;
-      const cudaError_t q = cudaEventQuery(L.done);
-      if (q == cudaErrorNotReady) continue;
-      if (q != cudaSuccess) { err = GENESYS_ECUDA; break; }
-      const uint64_t now = mono_ns();
-      latency_ns[L.req] = now - arrival_abs[L.req];
-      const uint64_t *hr = (const uint64_t *)(hmirror + (size_t)si * (per_ops + per_res) + per_ops);
-      for (uint32_t k = 0; k < GENESYS_C5_MAX_OPS; ++k)
-        results[(size_t)L.req * GENESYS_C5_MAX_OPS + k] = hr[GENESYS_C5_MAX_OPS + k] ? hr[GENESYS_C5_MAX_OPS + k]
-                                                                                     : hr[k];
-      st_alloc.release(L.st_off, L.need.staging);
-      hbm_alloc.release(L.hbm_off, L.need.hbm);
-      slots_free += L.need.slots;
-      L.busy = false;
-      --inflight;
-      ++retired;
-      progress = true;
-    }
-    // admit arrived requests, in arrival order, while budgets allow
-    while (next < n_req && !err) {
-      const uint64_t now = mono_ns();
-      if (arrival_abs[next] > now) break;
-      uint32_t si = 0;
-      while (si < K && slots[si].busy) ++si;
-      if (si == K) break;
-      const Needs nd = needs_of(reqs[next], bt, cfg.min_part, cfg.pread_to_hbm);
-      if (nd.slots > slots_free) break;
-      uint64_t so = 0, ho = 0;
-      if (!st_alloc.alloc(nd.staging, &so)) break;
-      if (!hbm_alloc.alloc(nd.hbm, &ho)) { st_alloc.release(so, nd.staging); break; }
-      Launch &L = slots[si];
-      L.busy = true;
-      L.req = (uint32_t)next;
-      L.need = nd;
-      L.st_off = so;
-      L.hbm_off = ho;
-      // launch slot si owns stream si mod n_streams: with as many streams as
-      // launch slots a request never queues behind another on its stream
-      L.stream = (int)(si % cfg.n_streams);
-      slots_free -= nd.slots;
-      admitted_wait_ns += now - arrival_abs[next];
-      if (launch(si, (uint32_t)next) != 0) { err = GENESYS_ECUDA; break; }
-      ++launched;
-      ++inflight;
-      max_inflight_seen = std::max(max_inflight_seen, inflight);
-      for (uint32_t k = 0; k < reqs[next].n_ops; ++k) {
-        const genesys_c5_op &op = reqs[next].ops[k];
-        if (op.kind == GENESYS_C5_MMAP) { calls += 2; continue; }
-        uint64_t p = (op.len + cfg.min_part - 1) / cfg.min_part;
-        p = std::min<uint64_t>(std::min<uint64_t>(p ? p : 1, nd.blocks), GENESYS_C5_MAX_PARTS);
-        const uint64_t sh = ((op.len + p - 1) / p + 15) & ~uint64_t(15);
-        calls += (op.len + sh - 1) / sh;
+    const uint64_t deadline = t0 + cfg.timeout_ns;
+    while (retired < n_req && !err) {
+      bool progress = false;
+      // retire finished requests
+      for (uint32_t si = 0; si < K; ++si) {
+        Launch &L = slots[si];
+        if (!L.busy) continue;
+        const cudaError_t q = cudaEventQuery(L.done);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) { err = GENESYS_ECUDA; break; }
+        const uint64_t now = mono_ns();
+        latency_ns[L.req] = now - arrival_abs[L.req];
+        const uint64_t *hr = (const uint64_t *)(hmirror + (size_t)si * (per_ops + per_res) + per_ops);
+        for (uint32_t k = 0; k < GENESYS_C5_MAX_OPS; ++k)
+          results[(size_t)L.req * GENESYS_C5_MAX_OPS + k] = hr[GENESYS_C5_MAX_OPS + k] ? hr[GENESYS_C5_MAX_OPS + k]
+                                                                                       : hr[k];
+        st_alloc.release(L.st_off, L.need.staging);
+        hbm_alloc.release(L.hbm_off, L.need.hbm);
+        slots_free += L.need.slots;
+        L.busy = false;
+        --inflight;
+        ++retired;
+        progress = true;
       }
-      ++next;
-      progress = true;
+      // admit arrived requests, in arrival order, while budgets allow
+      while (next < n_req && !err) {
+        const uint64_t now = mono_ns();
+        if (arrival_abs[next] > now) break;
+        uint32_t si = 0;
+        while (si < K && slots[si].busy) ++si;
+        if (si == K) break;
+        const Needs nd = needs_of(reqs[next], bt, cfg.min_part, cfg.pread_to_hbm);
+        if (nd.slots > slots_free) break;
+        uint64_t so = 0, ho = 0;
+        if (!st_alloc.alloc(nd.staging, &so)) break;
+        if (!hbm_alloc.alloc(nd.hbm, &ho)) { st_alloc.release(so, nd.staging); break; }
+        Launch &L = slots[si];
+        L.busy = true;
+        L.req = (uint32_t)next;
+        L.need = nd;
+        L.st_off = so;
+        L.hbm_off = ho;
+        // launch slot si owns stream si mod n_streams: with as many streams as
+        // launch slots a request never queues behind another on its stream
+        L.stream = (int)(si % cfg.n_streams);
+        slots_free -= nd.slots;
+        admitted_wait_ns += now - arrival_abs[next];
+        if (launch(si, (uint32_t)next) != 0) { err = GENESYS_ECUDA; break; }
+        ++launched;
+        ++inflight;
+        max_inflight_seen = std::max(max_inflight_seen, inflight);
+        for (uint32_t k = 0; k < reqs[next].n_ops; ++k) {
+          const genesys_c5_op &op = reqs[next].ops[k];
+          if (op.kind == GENESYS_C5_MMAP) { calls += 2; continue; }
+          uint64_t p = (op.len + cfg.min_part - 1) / cfg.min_part;
+          p = std::min<uint64_t>(std::min<uint64_t>(p ? p : 1, nd.blocks), GENESYS_C5_MAX_PARTS);
+          const uint64_t sh = ((op.len + p - 1) / p + 15) & ~uint64_t(15);
+          calls += (op.len + sh - 1) / sh;
+        }
+        ++next;
+        progress = true;
+      }
+      if (!progress) {
+        if (mono_ns() > deadline) { err = GENESYS_ETIMEDOUT; break; }
+        // nap between event polls: back-to-back cudaEventQuery calls contend
+        // with the service threads' CUDA calls
+        timespec ts{0, 2000};
+        nanosleep(&ts, nullptr);
+      }
     }
-    if (!progress) {
-      if (mono_ns() > deadline) { err = GENESYS_ETIMEDOUT; break; }
-      // nap between event polls: back-to-back cudaEventQuery calls contend
-      // with the service threads' CUDA calls
-      timespec ts{0, 2000};
-      nanosleep(&ts, nullptr);
+    const uint64_t t_end = mono_ns();
+    // on failure: wait for what was launched before freeing its resources
+    for (auto s : streams) cudaStreamSynchronize(s);
+    int drc = genesys_drain(c, 10ull * g0.deadline_ns);
+    genesys_reclaim(c);  // no request kernel runs any more: unpin released regions
+    for (auto &L : slots) {
+      if (L.exec) cudaGraphExecDestroy(L.exec);
+      if (L.graph) cudaGraphDestroy(L.graph);
+      cudaEventDestroy(L.done);
     }
-  }
-  const uint64_t t_end = mono_ns();
-  // on failure: wait for what was launched before freeing its resources
-  for (auto s : streams) cudaStreamSynchronize(s);
-  int drc = genesys_drain(c, 10ull * g0.deadline_ns);
-  genesys_reclaim(c);  // no request kernel runs any more: unpin released regions
-  for (auto &L : slots) {
-    if (L.exec) cudaGraphExecDestroy(L.exec);
-    if (L.graph) cudaGraphDestroy(L.graph);
-    cudaEventDestroy(L.done);
-  }
-  for (auto s : streams) cudaStreamDestroy(s);
-  cudaFreeHost(hmirror);
-  genesys_internal_staging_release(c, staging_mark);
-  if (stats) {
-    memset(stats, 0, sizeof *stats);
-    stats->requests = retired;
-    stats->syscalls = calls;
-    stats->makespan_ns = t_end - t0;
-    stats->max_inflight = max_inflight_seen;
-    stats->admission_wait_ns = admitted_wait_ns;
-    stats->graph_launches = graph_launches;
-  }
-  if (err == GENESYS_ETIMEDOUT) return set_err(err, "serve: trace did not finish within timeout_ns");
-  if (err) return set_err(err, "serve: a CUDA call failed");
-  if (drc) return drc;
-  int32_t stw[GENESYS_ST_WORDS];
-  rc = genesys_status(c, stw, 1);
-  if (rc) return rc;
-  if (stw[GENESYS_ST_TIMEOUTS] || stw[GENESYS_ST_FIRST_ERROR]) {
-    char msg[160];
-    snprintf(msg, sizeof msg, "serve: device-side calls failed: first error %d, %d timeouts",
-             stw[GENESYS_ST_FIRST_ERROR], stw[GENESYS_ST_TIMEOUTS]);
-    return set_err(GENESYS_EDEVICE, msg);
-  }
-  return 0;
+    for (auto s : streams) cudaStreamDestroy(s);
+    cudaFreeHost(hmirror);
+    genesys_internal_staging_release(c, staging_mark);
+    if (stats) {
+      memset(stats, 0, sizeof *stats);
+      stats->requests = retired;
+      stats->syscalls = calls;
+      stats->makespan_ns = t_end - t0;
+      stats->max_inflight = max_inflight_seen;
+      stats->admission_wait_ns = admitted_wait_ns;
+      stats->graph_launches = graph_launches;
+    }
+    if (err == GENESYS_ETIMEDOUT) return set_err(err, "serve: trace did not finish within timeout_ns");
+    if (err) return set_err(err, "serve: a CUDA call failed");
+    if (drc) return drc;
+    int32_t stw[GENESYS_ST_WORDS];
+    rc = genesys_status(c, stw, 1);
+    if (rc) return rc;
+    if (stw[GENESYS_ST_TIMEOUTS] || stw[GENESYS_ST_FIRST_ERROR]) {
+      char msg[160];
+      snprintf(msg, sizeof msg, "serve: device-side calls failed: first error %d, %d timeouts",
+               stw[GENESYS_ST_FIRST_ERROR], stw[GENESYS_ST_TIMEOUTS]);
+      return set_err(GENESYS_EDEVICE, msg);
+    }
+    return 0;
+  });
 }

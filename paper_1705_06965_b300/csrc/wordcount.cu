@@ -293,87 +293,89 @@ int genesys_c3_wordcount(genesys_ctx *c, const int32_t *fds, const uint64_t *fil
                          const uint8_t *queries16, const uint8_t *qlen, uint32_t nq, uint64_t chunk, uint32_t ctas,
                          uint32_t threads, uint32_t form, void *staging, uint64_t staging_bytes,
                          unsigned long long *counts_dev, void *stream) {
-  if (!c || !fds || !file_bytes || !queries16 || !qlen || !staging || !counts_dev)
-    return set_err(GENESYS_EINVAL, "NULL argument");
-  if (nq == 0 || nq > (uint32_t)kMaxQ) return set_err(GENESYS_EINVAL, "1..64 queries");
-  for (uint32_t q = 0; q < nq; ++q)
-    if (qlen[q] == 0 || qlen[q] > kHalo) return set_err(GENESYS_EINVAL, "query length must be 1..16");
-  if (chunk < 64 || chunk % 16 || chunk > (1u << 30)) return set_err(GENESYS_EINVAL, "chunk: multiple of 16, >= 64");
-  if (ctas == 0 || threads < 32 || threads > 1024 || threads % 32) return set_err(GENESYS_EINVAL, "bad launch shape");
-  if ((uintptr_t)staging % 16) return set_err(GENESYS_EINVAL, "staging must be 16-byte aligned");
-  const uint64_t buf_bytes = chunk + 64;
-  const uint64_t need = (uint64_t)ctas * buf_bytes * (form == GENESYS_FORM_BATCHED ? 2 : 1);
-  if (staging_bytes < need) return set_err(GENESYS_EINVAL, "staging too small: ctas * (chunk + 64) per buffer");
+  return genesys_guard("genesys_c3_wordcount", [&]() -> int {
+    if (!c || !fds || !file_bytes || !queries16 || !qlen || !staging || !counts_dev)
+      return set_err(GENESYS_EINVAL, "NULL argument");
+    if (nq == 0 || nq > (uint32_t)kMaxQ) return set_err(GENESYS_EINVAL, "1..64 queries");
+    for (uint32_t q = 0; q < nq; ++q)
+      if (qlen[q] == 0 || qlen[q] > kHalo) return set_err(GENESYS_EINVAL, "query length must be 1..16");
+    if (chunk < 64 || chunk % 16 || chunk > (1u << 30)) return set_err(GENESYS_EINVAL, "chunk: multiple of 16, >= 64");
+    if (ctas == 0 || threads < 32 || threads > 1024 || threads % 32) return set_err(GENESYS_EINVAL, "bad launch shape");
+    if ((uintptr_t)staging % 16) return set_err(GENESYS_EINVAL, "staging must be 16-byte aligned");
+    const uint64_t buf_bytes = chunk + 64;
+    const uint64_t need = (uint64_t)ctas * buf_bytes * (form == GENESYS_FORM_BATCHED ? 2 : 1);
+    if (staging_bytes < need) return set_err(GENESYS_EINVAL, "staging too small: ctas * (chunk + 64) per buffer");
 
-  // work items: (file, chunk) pairs in file order
-  std::vector<C3Item> items;
-  for (uint32_t f = 0; f < n_files; ++f) {
-    if (fds[f] < 0) return set_err(GENESYS_EINVAL, "bad fd");
-    for (uint64_t off = 0; off < file_bytes[f]; off += chunk) {
-      C3Item it{};
-      it.fd = fds[f];
-      it.len = (uint32_t)(file_bytes[f] - off < chunk ? file_bytes[f] - off : chunk);
-      it.off = off;
-      it.fsize = file_bytes[f];
-      items.push_back(it);
+    // work items: (file, chunk) pairs in file order
+    std::vector<C3Item> items;
+    for (uint32_t f = 0; f < n_files; ++f) {
+      if (fds[f] < 0) return set_err(GENESYS_EINVAL, "bad fd");
+      for (uint64_t off = 0; off < file_bytes[f]; off += chunk) {
+        C3Item it{};
+        it.fd = fds[f];
+        it.len = (uint32_t)(file_bytes[f] - off < chunk ? file_bytes[f] - off : chunk);
+        it.off = off;
+        it.fsize = file_bytes[f];
+        items.push_back(it);
+      }
     }
-  }
-  if (items.empty()) return 0;
-  if (items.size() > 0xFFFFFFF0ull) return set_err(GENESYS_EINVAL, "too many work items");
-  C3Queries q{};
-  q.nq = nq;
-  for (uint32_t i = 0; i < nq; ++i) {
-    uint8_t tmp[16] = {0};
-    memcpy(tmp, queries16 + 16 * i, qlen[i]);
-    memcpy(&q.w[i][0], tmp, 8);
-    memcpy(&q.w[i][1], tmp + 8, 8);
-    q.len[i] = qlen[i];
-  }
-  // device scratch: [head u32 | pad to 256][queries][items]
-  const size_t q_off = 256, items_off = (q_off + sizeof(C3Queries) + 255) & ~size_t(255);
-  const size_t bytes = items_off + items.size() * sizeof(C3Item);
-  void *scratch = nullptr;
-  int rc = genesys_internal_scratch(c, bytes, &scratch);
-  if (rc) return rc;
-  cudaStream_t s = (cudaStream_t)stream;
-  std::vector<uint8_t> pack(items_off, 0);
-  memcpy(pack.data() + q_off, &q, sizeof q);
-  if (cudaMemcpyAsync(scratch, pack.data(), pack.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync((uint8_t *)scratch + items_off, items.data(), items.size() * sizeof(C3Item),
-                      cudaMemcpyHostToDevice, s) != cudaSuccess) {
-    cudaGetLastError();
-    return set_err(GENESYS_ECUDA, "upload of work items failed");
-  }
-  genesys_dev g;
-  genesys_device_view(c, &g);
-  if (form == GENESYS_FORM_BATCHED && g.n_slots < 2ull * ctas)
-    return set_err(GENESYS_EINVAL, "the batched form holds two slots per block: n_slots must be >= 2 * ctas");
-  const C3Item *d_items = (const C3Item *)((uint8_t *)scratch + items_off);
-  uint32_t n_items = (uint32_t)items.size();
-  uint32_t *head = (uint32_t *)scratch;
-  const C3Queries *d_q = (const C3Queries *)((uint8_t *)scratch + q_off);
-  uint8_t *st = (uint8_t *)staging;
-  uint64_t bb = buf_bytes;
-  uint32_t tile_bytes = c3_tile_bytes(threads);
-  void *args[] = {&g, &d_items, &n_items, &head, &d_q, &st, &bb, &tile_bytes, &counts_dev};
-  const size_t smem = tile_bytes + 48;
-  const void *k = form == GENESYS_FORM_BATCHED ? (const void *)&c3_batched_kernel : (const void *)&c3_plain_kernel;
-  const uint32_t flags = form == GENESYS_FORM_BATCHED
-                             ? (GENESYS_GRAN_GROUP | GENESYS_LAUNCH_RELAXED | GENESYS_LAUNCH_NONBLOCKING)
-                             : GENESYS_GRAN_GROUP;
-  const uint32_t g3[3] = {ctas, 1, 1}, b3[3] = {threads, 1, 1};
-  rc = genesys_launch(c, k, g3, b3, smem, args, flags | GENESYS_LAUNCH_SYNC, stream);
-  if (rc) return rc;
-  int32_t stw[GENESYS_ST_WORDS];
-  rc = genesys_status(c, stw, 1);
-  if (rc) return rc;
-  if (stw[GENESYS_ST_TIMEOUTS] || stw[GENESYS_ST_FAILED_CALLS] || stw[GENESYS_ST_FIRST_ERROR]) {
-    char msg[160];
-    snprintf(msg, sizeof msg, "device-side calls failed: first error %d, %d timeouts, %d failed calls",
-             stw[GENESYS_ST_FIRST_ERROR], stw[GENESYS_ST_TIMEOUTS], stw[GENESYS_ST_FAILED_CALLS]);
-    return set_err(GENESYS_EDEVICE, msg);
-  }
-  return 0;
+    if (items.empty()) return 0;
+    if (items.size() > 0xFFFFFFF0ull) return set_err(GENESYS_EINVAL, "too many work items");
+    C3Queries q{};
+    q.nq = nq;
+    for (uint32_t i = 0; i < nq; ++i) {
+      uint8_t tmp[16] = {0};
+      memcpy(tmp, queries16 + 16 * i, qlen[i]);
+      memcpy(&q.w[i][0], tmp, 8);
+      memcpy(&q.w[i][1], tmp + 8, 8);
+      q.len[i] = qlen[i];
+    }
+    // device scratch: [head u32 | pad to 256][queries][items]
+    const size_t q_off = 256, items_off = (q_off + sizeof(C3Queries) + 255) & ~size_t(255);
+    const size_t bytes = items_off + items.size() * sizeof(C3Item);
+    void *scratch = nullptr;
+    int rc = genesys_internal_scratch(c, bytes, &scratch);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<uint8_t> pack(items_off, 0);
+    memcpy(pack.data() + q_off, &q, sizeof q);
+    if (cudaMemcpyAsync(scratch, pack.data(), pack.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync((uint8_t *)scratch + items_off, items.data(), items.size() * sizeof(C3Item),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(GENESYS_ECUDA, "upload of work items failed");
+    }
+    genesys_dev g;
+    genesys_device_view(c, &g);
+    if (form == GENESYS_FORM_BATCHED && g.n_slots < 2ull * ctas)
+      return set_err(GENESYS_EINVAL, "the batched form holds two slots per block: n_slots must be >= 2 * ctas");
+    const C3Item *d_items = (const C3Item *)((uint8_t *)scratch + items_off);
+    uint32_t n_items = (uint32_t)items.size();
+    uint32_t *head = (uint32_t *)scratch;
+    const C3Queries *d_q = (const C3Queries *)((uint8_t *)scratch + q_off);
+    uint8_t *st = (uint8_t *)staging;
+    uint64_t bb = buf_bytes;
+    uint32_t tile_bytes = c3_tile_bytes(threads);
+    void *args[] = {&g, &d_items, &n_items, &head, &d_q, &st, &bb, &tile_bytes, &counts_dev};
+    const size_t smem = tile_bytes + 48;
+    const void *k = form == GENESYS_FORM_BATCHED ? (const void *)&c3_batched_kernel : (const void *)&c3_plain_kernel;
+    const uint32_t flags = form == GENESYS_FORM_BATCHED
+                               ? (GENESYS_GRAN_GROUP | GENESYS_LAUNCH_RELAXED | GENESYS_LAUNCH_NONBLOCKING)
+                               : GENESYS_GRAN_GROUP;
+    const uint32_t g3[3] = {ctas, 1, 1}, b3[3] = {threads, 1, 1};
+    rc = genesys_launch(c, k, g3, b3, smem, args, flags | GENESYS_LAUNCH_SYNC, stream);
+    if (rc) return rc;
+    int32_t stw[GENESYS_ST_WORDS];
+    rc = genesys_status(c, stw, 1);
+    if (rc) return rc;
+    if (stw[GENESYS_ST_TIMEOUTS] || stw[GENESYS_ST_FAILED_CALLS] || stw[GENESYS_ST_FIRST_ERROR]) {
+      char msg[160];
+      snprintf(msg, sizeof msg, "device-side calls failed: first error %d, %d timeouts, %d failed calls",
+               stw[GENESYS_ST_FIRST_ERROR], stw[GENESYS_ST_TIMEOUTS], stw[GENESYS_ST_FAILED_CALLS]);
+      return set_err(GENESYS_EDEVICE, msg);
+    }
+    return 0;
+  });
 }
 
 }  // extern "C"

@@ -570,110 +570,114 @@ int genesys_visibility_probe(genesys_ctx *c, uint64_t n, uint32_t gran, uint32_t
 
 int genesys_internal_clock_offset(int device, uint32_t rounds, uint64_t timeout_ns, int64_t *offset_ns,
                                   uint64_t *rtt_ns) {
-  if (!offset_ns || rounds == 0) return set_err(GENESYS_EINVAL, "bad argument");
-  if (cudaSetDevice(device) != cudaSuccess) return set_err(GENESYS_ECUDA, "cudaSetDevice");
-  uint64_t *flags = nullptr;
-  if (cudaHostAlloc((void **)&flags, 128, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess)
-    return set_err(GENESYS_ECUDA, "cudaHostAlloc");
-  memset(flags, 0, 128);
-  uint64_t *d_flags = nullptr;
-  unsigned long long *d_t = nullptr;
-  cudaStream_t st = nullptr;
-  int rc = 0;
-  if (cudaHostGetDevicePointer((void **)&d_flags, flags, 0) != cudaSuccess ||
-      cudaMalloc((void **)&d_t, (2ull * rounds + 1) * sizeof(unsigned long long)) != cudaSuccess ||
-      cudaMemset(d_t, 0, (2ull * rounds + 1) * sizeof(unsigned long long)) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
-    rc = set_err(GENESYS_ECUDA, "clock probe set-up");
-  if (rc == 0) {
-    std::vector<uint64_t> host_t(rounds, 0);
-    bool host_late = false;
-    volatile uint64_t *ping = flags, *pong = flags + 8;
-    std::thread echo([&] {
-      const uint64_t until = host_now_ns() + timeout_ns + 1000000000ull;
-      for (uint32_t r = 1; r <= rounds; ++r) {
-        while (__atomic_load_n(ping, __ATOMIC_ACQUIRE) != r) {
-          if (host_now_ns() > until) { host_late = true; return; }
-          __builtin_ia32_pause();
+  return genesys_guard("genesys_internal_clock_offset", [&]() -> int {
+    if (!offset_ns || rounds == 0) return set_err(GENESYS_EINVAL, "bad argument");
+    if (cudaSetDevice(device) != cudaSuccess) return set_err(GENESYS_ECUDA, "cudaSetDevice");
+    uint64_t *flags = nullptr;
+    if (cudaHostAlloc((void **)&flags, 128, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess)
+      return set_err(GENESYS_ECUDA, "cudaHostAlloc");
+    memset(flags, 0, 128);
+    uint64_t *d_flags = nullptr;
+    unsigned long long *d_t = nullptr;
+    cudaStream_t st = nullptr;
+    int rc = 0;
+    if (cudaHostGetDevicePointer((void **)&d_flags, flags, 0) != cudaSuccess ||
+        cudaMalloc((void **)&d_t, (2ull * rounds + 1) * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(d_t, 0, (2ull * rounds + 1) * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+      rc = set_err(GENESYS_ECUDA, "clock probe set-up");
+    if (rc == 0) {
+      std::vector<uint64_t> host_t(rounds, 0);
+      bool host_late = false;
+      volatile uint64_t *ping = flags, *pong = flags + 8;
+      std::thread echo([&] {
+        const uint64_t until = host_now_ns() + timeout_ns + 1000000000ull;
+        for (uint32_t r = 1; r <= rounds; ++r) {
+          while (__atomic_load_n(ping, __ATOMIC_ACQUIRE) != r) {
+            if (host_now_ns() > until) { host_late = true; return; }
+            __builtin_ia32_pause();
+          }
+          host_t[r - 1] = host_now_ns();
+          __atomic_store_n(pong, (uint64_t)r, __ATOMIC_RELEASE);
         }
-        host_t[r - 1] = host_now_ns();
-        __atomic_store_n(pong, (uint64_t)r, __ATOMIC_RELEASE);
-      }
-    });
-    clock_probe_kernel<<<1, 32, 0, st>>>(d_flags, d_flags + 8, rounds, timeout_ns, d_t, d_t + 2ull * rounds);
-    const cudaError_t e = cudaStreamSynchronize(st);
-    echo.join();
-    std::vector<unsigned long long> t(2ull * rounds + 1);
-    if (e != cudaSuccess || cudaMemcpy(t.data(), d_t, t.size() * sizeof(t[0]), cudaMemcpyDeviceToHost) != cudaSuccess) {
-      rc = set_err(GENESYS_ECUDA, "clock probe kernel");
-    } else if (t[2ull * rounds] || host_late) {
-      rc = set_err(GENESYS_ETIMEDOUT, "clock probe: rounds did not complete within the timeout");
-    } else {
-      uint64_t best = ~0ull;
-      int64_t off = 0;
-      for (uint32_t r = 0; r < rounds; ++r) {
-        const uint64_t a = t[2 * r], b = t[2 * r + 1];
-        if (b - a < best) {
-          best = b - a;
-          off = (int64_t)host_t[r] - (int64_t)(a + (b - a) / 2);
+      });
+      clock_probe_kernel<<<1, 32, 0, st>>>(d_flags, d_flags + 8, rounds, timeout_ns, d_t, d_t + 2ull * rounds);
+      const cudaError_t e = cudaStreamSynchronize(st);
+      echo.join();
+      std::vector<unsigned long long> t(2ull * rounds + 1);
+      if (e != cudaSuccess || cudaMemcpy(t.data(), d_t, t.size() * sizeof(t[0]), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        rc = set_err(GENESYS_ECUDA, "clock probe kernel");
+      } else if (t[2ull * rounds] || host_late) {
+        rc = set_err(GENESYS_ETIMEDOUT, "clock probe: rounds did not complete within the timeout");
+      } else {
+        uint64_t best = ~0ull;
+        int64_t off = 0;
+        for (uint32_t r = 0; r < rounds; ++r) {
+          const uint64_t a = t[2 * r], b = t[2 * r + 1];
+          if (b - a < best) {
+            best = b - a;
+            off = (int64_t)host_t[r] - (int64_t)(a + (b - a) / 2);
+          }
         }
+        *offset_ns = off;
+        if (rtt_ns) *rtt_ns = best;
       }
-      *offset_ns = off;
-      if (rtt_ns) *rtt_ns = best;
     }
-  }
-  if (st) cudaStreamDestroy(st);
-  if (d_t) cudaFree(d_t);
-  cudaFreeHost(flags);
-  return rc;
+    if (st) cudaStreamDestroy(st);
+    if (d_t) cudaFree(d_t);
+    cudaFreeHost(flags);
+    return rc;
+  });
 }
 
 // Round-trip latency of a flag between a GPU thread and a host thread over
 // the host link (the floor under any blocking GPU system call).
 int genesys_link_pingpong(int device, uint32_t rounds, uint64_t timeout_ns, uint64_t *ns_per_round) {
-  if (!ns_per_round || rounds == 0) return set_err(GENESYS_EINVAL, "NULL argument or zero rounds");
-  if (cudaSetDevice(device) != cudaSuccess) return set_err(GENESYS_ECUDA, "cudaSetDevice");
-  uint64_t *flags = nullptr;  // ping in line 0, pong in line 1 (separate 64-byte lines)
-  if (cudaHostAlloc((void **)&flags, 128, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess)
-    return set_err(GENESYS_ECUDA, "cudaHostAlloc");
-  memset(flags, 0, 128);
-  uint64_t *d_flags = nullptr;
-  unsigned long long *d_out = nullptr;
-  cudaStream_t st = nullptr;
-  int rc = 0;
-  if (cudaHostGetDevicePointer((void **)&d_flags, flags, 0) != cudaSuccess ||
-      cudaMalloc((void **)&d_out, 3 * sizeof(unsigned long long)) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
-    rc = set_err(GENESYS_ECUDA, "pingpong set-up");
-  }
-  bool host_late = false;
-  if (rc == 0) {
-    volatile uint64_t *ping = flags, *pong = flags + 8;
-    std::thread echo([&] {
-      const uint64_t until = host_now_ns() + timeout_ns + 1000000000ull;
-      for (uint32_t r = 1; r <= rounds; ++r) {
-        while (__atomic_load_n(ping, __ATOMIC_ACQUIRE) != r) {
-          if (host_now_ns() > until) { host_late = true; return; }
-          __builtin_ia32_pause();
+  return genesys_guard("genesys_link_pingpong", [&]() -> int {
+    if (!ns_per_round || rounds == 0) return set_err(GENESYS_EINVAL, "NULL argument or zero rounds");
+    if (cudaSetDevice(device) != cudaSuccess) return set_err(GENESYS_ECUDA, "cudaSetDevice");
+    uint64_t *flags = nullptr;  // ping in line 0, pong in line 1 (separate 64-byte lines)
+    if (cudaHostAlloc((void **)&flags, 128, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess)
+      return set_err(GENESYS_ECUDA, "cudaHostAlloc");
+    memset(flags, 0, 128);
+    uint64_t *d_flags = nullptr;
+    unsigned long long *d_out = nullptr;
+    cudaStream_t st = nullptr;
+    int rc = 0;
+    if (cudaHostGetDevicePointer((void **)&d_flags, flags, 0) != cudaSuccess ||
+        cudaMalloc((void **)&d_out, 3 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      rc = set_err(GENESYS_ECUDA, "pingpong set-up");
+    }
+    bool host_late = false;
+    if (rc == 0) {
+      volatile uint64_t *ping = flags, *pong = flags + 8;
+      std::thread echo([&] {
+        const uint64_t until = host_now_ns() + timeout_ns + 1000000000ull;
+        for (uint32_t r = 1; r <= rounds; ++r) {
+          while (__atomic_load_n(ping, __ATOMIC_ACQUIRE) != r) {
+            if (host_now_ns() > until) { host_late = true; return; }
+            __builtin_ia32_pause();
+          }
+          __atomic_store_n(pong, (uint64_t)r, __ATOMIC_RELEASE);
         }
-        __atomic_store_n(pong, (uint64_t)r, __ATOMIC_RELEASE);
-      }
-    });
-    pingpong_kernel<<<1, 32, 0, st>>>(d_flags, d_flags + 8, rounds, timeout_ns, d_out);
-    const cudaError_t e = cudaStreamSynchronize(st);
-    echo.join();
-    unsigned long long out[3] = {0, 0, 0};
-    if (e != cudaSuccess || cudaMemcpy(out, d_out, sizeof out, cudaMemcpyDeviceToHost) != cudaSuccess)
-      rc = set_err(GENESYS_ECUDA, "pingpong kernel");
-    else if (out[2] || host_late || out[1] != rounds)
-      rc = set_err(GENESYS_ETIMEDOUT, "pingpong: rounds did not complete within the timeout");
-    else
-      *ns_per_round = out[0] / rounds;
-  }
-  if (st) cudaStreamDestroy(st);
-  if (d_out) cudaFree(d_out);
-  cudaFreeHost(flags);
-  return rc;
+      });
+      pingpong_kernel<<<1, 32, 0, st>>>(d_flags, d_flags + 8, rounds, timeout_ns, d_out);
+      const cudaError_t e = cudaStreamSynchronize(st);
+      echo.join();
+      unsigned long long out[3] = {0, 0, 0};
+      if (e != cudaSuccess || cudaMemcpy(out, d_out, sizeof out, cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = set_err(GENESYS_ECUDA, "pingpong kernel");
+      else if (out[2] || host_late || out[1] != rounds)
+        rc = set_err(GENESYS_ETIMEDOUT, "pingpong: rounds did not complete within the timeout");
+      else
+        *ns_per_round = out[0] / rounds;
+    }
+    if (st) cudaStreamDestroy(st);
+    if (d_out) cudaFree(d_out);
+    cudaFreeHost(flags);
+    return rc;
+  });
 }
 
 }  // extern "C"

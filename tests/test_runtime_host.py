@@ -614,3 +614,27 @@ def test_a_user_kernel_compiles_against_the_headers(tmp_path):
                         os.path.join(root, "tests", "c_abi", "user_kernel.cu"), "-o", str(tmp_path / "u.o")],
                        capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
+
+
+def _open_fds():
+    return len(os.listdir("/proc/self/fd"))
+
+
+def test_no_cxx_exception_crosses_the_c_abi():
+    """A request count no host vector can hold comes back as an error code
+    (the library catches the C++ exception at the entry point), and the
+    sockets the call would have opened are not leaked."""
+    L = G.lib()
+    reqs = np.zeros(64, np.uint8)
+    off = np.zeros(2, np.uint64)
+    arr = np.zeros(1, np.uint64)
+    out8 = np.zeros(64, np.uint8)
+    rl = np.zeros(1, np.uint32)
+    lat = np.zeros(1, np.uint64)
+    stats = np.zeros(6, np.uint64)
+    before = _open_fds()
+    rc = L.genesys_kv_client(reqs.ctypes.data, off.ctypes.data, 1 << 62, arr.ctypes.data, 47000, 4, 1_000_000,
+                             out8.ctypes.data, rl.ctypes.data, lat.ctypes.data, stats.ctypes.data)
+    assert rc == G.EINVAL
+    assert "genesys_kv_client" in L.genesys_last_error().decode()
+    assert _open_fds() == before
