@@ -42,12 +42,6 @@ constexpr uint32_t kHeader = 8;  // client packet header: lane u32, generation u
 
 int set_err(int code, const char *msg) { return genesys_internal_error(code, msg); }
 
-inline uint64_t mono_ns() {
-  timespec ts;
-  clock_gettime(CLOCK_MONOTONIC, &ts);
-  return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
-}
-
 // Message headers of one block, at the start of its staging area; the receive
 // buffers (batch x stride) and send buffers (batch x stride) follow.
 struct EchoHeaders {
@@ -295,9 +289,9 @@ extern "C" int genesys_echo_stop(genesys_echo_server *s, uint64_t timeout_ns, ui
       const int32_t one = 1;
       cudaMemcpyAsync(s->d_stop, &one, 4, cudaMemcpyHostToDevice, s->ctl);
       cudaStreamSynchronize(s->ctl);
-      const uint64_t until = mono_ns() + timeout_ns;
+      const uint64_t until = genesys_mono_ns() + timeout_ns;
       while (cudaStreamQuery(s->stream) == cudaErrorNotReady) {
-        if (mono_ns() > until) { rc = set_err(GENESYS_ETIMEDOUT, "echo server did not stop"); break; }
+        if (genesys_mono_ns() > until) { rc = set_err(GENESYS_ETIMEDOUT, "echo server did not stop"); break; }
         std::this_thread::sleep_for(std::chrono::microseconds(100));
       }
       if (rc == 0) {
@@ -419,13 +413,13 @@ void echo_client_thread(uint32_t t, uint32_t n_threads, uint16_t port_base, uint
     }
     ns = 0;
   };
-  T.first = mono_ns();
+  T.first = genesys_mono_ns();
   for (uint32_t id = 0; id < lanes.size() && T.sent < quota; ++id) {
     queue(id);
     if (ns == kB) flush();
   }
   flush();
-  uint64_t last_reply = mono_ns();
+  uint64_t last_reply = genesys_mono_ns();
   while (busy) {
     for (int i = 0; i < kB; ++i) {
       riov[i] = {rbuf.data() + (size_t)i * (P + 64), P + 64};
@@ -434,7 +428,7 @@ void echo_client_thread(uint32_t t, uint32_t n_threads, uint16_t port_base, uint
       rh[i].msg_hdr.msg_iovlen = 1;
     }
     const int m = recvmmsg(fd, rh.data(), kB, MSG_DONTWAIT, nullptr);
-    const uint64_t now = mono_ns();
+    const uint64_t now = genesys_mono_ns();
     if (m <= 0) {
       if (now - last_reply > stall_ns) break;
       continue;

@@ -2,8 +2,17 @@
 #pragma once
 
 #include <stddef.h>
+#include <time.h>
 
 #include "genesys.h"
+
+/* Host CLOCK_MONOTONIC in ns: the clock of every host-side deadline and host
+ * timestamp of the library. */
+static inline uint64_t genesys_mono_ns(void) {
+  struct timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
+}
 
 #ifdef __cplusplus
 extern "C" {

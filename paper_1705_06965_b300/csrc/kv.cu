@@ -49,12 +49,6 @@ constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
 
 int set_err(int code, const char *msg) { return genesys_internal_error(code, msg); }
 
-inline uint64_t mono_ns() {
-  timespec ts;
-  clock_gettime(CLOCK_MONOTONIC, &ts);
-  return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
-}
-
 __device__ __forceinline__ uint64_t sm_mix(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
@@ -378,9 +372,9 @@ extern "C" int genesys_kv_stop(genesys_kv_server *s, uint64_t timeout_ns, uint64
       const int32_t one = 1;
       cudaMemcpyAsync(s->d_stop, &one, 4, cudaMemcpyHostToDevice, s->ctl);
       cudaStreamSynchronize(s->ctl);
-      const uint64_t until = mono_ns() + timeout_ns;
+      const uint64_t until = genesys_mono_ns() + timeout_ns;
       while (cudaStreamQuery(s->stream) == cudaErrorNotReady) {
-        if (mono_ns() > until) { rc = set_err(GENESYS_ETIMEDOUT, "kv server did not stop"); break; }
+        if (genesys_mono_ns() > until) { rc = set_err(GENESYS_ETIMEDOUT, "kv server did not stop"); break; }
         std::this_thread::sleep_for(std::chrono::microseconds(100));
       }
       if (rc == 0) {
@@ -454,7 +448,7 @@ void kv_client_thread(int fd, const std::vector<uint64_t> &mine, const uint8_t *
       rh[q].msg_hdr.msg_iovlen = 1;
     }
     const int got = recvmmsg(fd, rh.data(), kB, MSG_DONTWAIT, nullptr);
-    uint64_t now = mono_ns();
+    uint64_t now = genesys_mono_ns();
     for (int q = 0; q < got; ++q) {
       const uint8_t *r = rb.data() + (size_t)q * kRep;
       const uint32_t len = rh[q].msg_len;
@@ -545,7 +539,7 @@ extern "C" int genesys_kv_client(const uint8_t *reqs, const uint64_t *req_off, u
       owned[(k0 % n_sockets) % n_threads].push_back(j);
     }
     std::vector<KvClientTally> tally(n_threads);
-    const uint64_t t0 = mono_ns() + 2000000;  // start in 2 ms, once the threads run
+    const uint64_t t0 = genesys_mono_ns() + 2000000;  // start in 2 ms, once the threads run
     const uint64_t deadline = t0 + (n ? arrival_ns[n - 1] : 0) + timeout_ns;
     std::vector<std::thread> th;
     genesys_joiner join_all{th};

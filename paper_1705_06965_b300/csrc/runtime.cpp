@@ -63,12 +63,6 @@ int fail(int code, const char *fmt, ...) {
     if (e_ != cudaSuccess) return fail(GENESYS_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
   } while (0)
 
-inline uint64_t mono_ns() {
-  timespec ts;
-  clock_gettime(CLOCK_MONOTONIC, &ts);
-  return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
-}
-
 inline void cpu_relax() { __builtin_ia32_pause(); }
 
 inline uint64_t next_pow2(uint64_t x) {
@@ -379,7 +373,7 @@ size_t merge_run(genesys_ctx *c, Request *const *reqs, size_t i, size_t n, Count
   for (size_t t = i; t < j; ++t) total += reqs[t]->a[2];
   int64_t res;
   bump(k.os_calls, 1);
-  const uint64_t e0 = mono_ns();
+  const uint64_t e0 = genesys_mono_ns();
   if (m == 1 || contiguous_buf) {
     void *buf = (void *)reqs[i]->a[1];
     long r = nr == SYS_pread64 ? pread(fd, buf, total, (off_t)off) : pwrite(fd, buf, total, (off_t)off);
@@ -390,7 +384,7 @@ size_t merge_run(genesys_ctx *c, Request *const *reqs, size_t i, size_t n, Count
     long r = nr == SYS_pread64 ? preadv(fd, iov, (int)m, (off_t)off) : pwritev(fd, iov, (int)m, (off_t)off);
     res = sys_ret(r);
   }
-  const uint64_t dt = mono_ns() - e0;
+  const uint64_t dt = genesys_mono_ns() - e0;
   const int oi = nr == SYS_pread64 ? OP_PREAD : OP_PWRITE;
   bump(k.op_ns[oi], dt);
   if (dt > k.op_max_ns[oi].load(std::memory_order_relaxed)) k.op_max_ns[oi].store(dt, std::memory_order_relaxed);
@@ -412,7 +406,7 @@ size_t merge_run(genesys_ctx *c, Request *const *reqs, size_t i, size_t n, Count
 inline bool is_rw(uint32_t nr) { return nr == SYS_pread64 || nr == SYS_pwrite64; }
 
 void process_batch(genesys_ctx *c, uint32_t ri, Batch &b, size_t n, Counters &k) {
-  const uint64_t t0 = mono_ns();
+  const uint64_t t0 = genesys_mono_ns();
   Request *const req = b.req.data();
   Request **p = b.ptr.data();
   for (size_t i = 0; i < n; ++i) p[i] = req + i;
@@ -493,9 +487,9 @@ void process_batch(genesys_ctx *c, uint32_t ri, Batch &b, size_t n, Counters &k)
       i = merge_run(c, p, i, n, k);
       continue;
     }
-    const uint64_t e0 = mono_ns();
+    const uint64_t e0 = genesys_mono_ns();
     r.ret = execute_one(c, r, k);
-    const uint64_t dt = mono_ns() - e0;
+    const uint64_t dt = genesys_mono_ns() - e0;
     const int oi = op_index(r.nr);
     bump(k.op_ns[oi], dt);
     if (dt > k.op_max_ns[oi].load(std::memory_order_relaxed)) k.op_max_ns[oi].store(dt, std::memory_order_relaxed);
@@ -512,7 +506,7 @@ void process_batch(genesys_ctx *c, uint32_t ri, Batch &b, size_t n, Counters &k)
   if (c->cfg.trace_capacity) {
     std::vector<genesys_trace_host> &tr = c->trace_host[ri];
     const uint32_t at = c->trace_n[ri].load(std::memory_order_relaxed);
-    const uint64_t t_done = mono_ns();
+    const uint64_t t_done = genesys_mono_ns();
     for (size_t i = 0; i < n; ++i)
       if (at + i < tr.size()) tr[at + i] = genesys_trace_host{req[i].slot, req[i].seq, t0, t_done};
     c->trace_n[ri].store(at + (uint32_t)n, std::memory_order_release);
@@ -521,8 +515,8 @@ void process_batch(genesys_ctx *c, uint32_t ri, Batch &b, size_t n, Counters &k)
     if (per_op[o]) bump(k.by_op[o], per_op[o]);
   bump(k.requests, n);
   bump(k.batches, 1);
-  k.last_batch_ns.store(mono_ns(), std::memory_order_relaxed);
-  bump(k.busy_ns, mono_ns() - t0);
+  k.last_batch_ns.store(genesys_mono_ns(), std::memory_order_relaxed);
+  bump(k.busy_ns, genesys_mono_ns() - t0);
 }
 
 inline bool entry_ready(const uint64_t *ring, uint32_t mask, uint64_t pos, uint32_t *slot) {
@@ -577,8 +571,8 @@ size_t poll_ring(genesys_ctx *c, uint32_t ri, Batch &b) {
   for (size_t i = 0; i < n; ++i) read_request(c, slots[i], &batch[i]);
   if (n == 0) return 0;
   if (n < maxb && c->cfg.coalesce_window_ns) {
-    const uint64_t until = mono_ns() + c->cfg.coalesce_window_ns;
-    while (n < maxb && mono_ns() < until) {
+    const uint64_t until = genesys_mono_ns() + c->cfg.coalesce_window_ns;
+    while (n < maxb && genesys_mono_ns() < until) {
       if (entry_ready(ring, mask, h + n, &s)) {
         read_request(c, s, &batch[n]);
         ++n;
@@ -604,7 +598,7 @@ void service_main(genesys_ctx *c, uint32_t ri) {
   }
   if (!c->host_only) cudaSetDevice(c->device);
   Batch batch(std::max<uint32_t>(1, c->cfg.coalesce_max));
-  uint64_t last_work = mono_ns();
+  uint64_t last_work = genesys_mono_ns();
   uint32_t idle_polls = 0;
   while (!c->stop.load(std::memory_order_relaxed) && !c->ring_stop[ri].load(std::memory_order_relaxed)) {
     if (poll_ring(c, ri, batch)) {
@@ -614,7 +608,7 @@ void service_main(genesys_ctx *c, uint32_t ri) {
     }
     if (++idle_polls < 64) { cpu_relax(); continue; }
     idle_polls = 0;
-    const uint64_t now = mono_ns();
+    const uint64_t now = genesys_mono_ns();
     if (last_work == 0) last_work = now;
     if (now - last_work < c->cfg.idle_spin_ns) {
       cpu_relax();
@@ -846,7 +840,7 @@ int genesys_init(const genesys_config *cfg_in, int device, genesys_ctx **out) {
   #ifdef GENESYS_DEVICE_CHECKS
     c->last_seq.assign(cfg.n_slots, 0);
   #endif
-    c->created_ns = mono_ns();
+    c->created_ns = genesys_mono_ns();
     c->trace_n.reset(new std::atomic<uint32_t>[nr]);
     for (uint32_t r = 0; r < nr; ++r) c->trace_n[r].store(0);
     if (cfg.trace_capacity) c->trace_host.assign(nr, std::vector<genesys_trace_host>((cfg.trace_capacity + nr - 1) / nr));
@@ -873,7 +867,7 @@ int genesys_drain(genesys_ctx *c, uint64_t timeout_ns) {
     int rc = read_tails(c, tails);
     if (rc) return rc;
     std::unique_ptr<Batch> batch;  // NO_THREADS mode: the caller services the rings
-    const uint64_t until = mono_ns() + timeout_ns;
+    const uint64_t until = genesys_mono_ns() + timeout_ns;
     for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) {
       for (;;) {
         // positions are 32-bit on the device: compare modulo 2^32
@@ -886,7 +880,7 @@ int genesys_drain(genesys_ctx *c, uint64_t timeout_ns) {
         } else {
           std::this_thread::sleep_for(std::chrono::microseconds(5));
         }
-        if (mono_ns() > until)
+        if (genesys_mono_ns() > until)
           return fail(GENESYS_ETIMEDOUT, "drain: ring %u retired %u of %u requests", r, got, tails[r]);
       }
     }
@@ -927,7 +921,7 @@ int genesys_service_health(genesys_ctx *c, uint64_t stall_ns, uint64_t *stalled_
     std::vector<uint32_t> tails(c->cfg.n_service_threads);
     int rc = read_tails(c, tails);
     if (rc) return rc;
-    const uint64_t now = mono_ns();
+    const uint64_t now = genesys_mono_ns();
     uint64_t mask = 0, total = 0;
     for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) {
       // positions are 32-bit on the device: the distance modulo 2^32; the
@@ -1058,7 +1052,7 @@ int genesys_last_launch_ms(genesys_ctx *c, float *ms) {
 int genesys_service(genesys_ctx *c, uint64_t timeout_ns) {
   return genesys_guard("genesys_service", [&]() -> int {
     if (!c) return fail(GENESYS_EINVAL, "ctx is NULL");
-    const uint64_t until = mono_ns() + timeout_ns;
+    const uint64_t until = genesys_mono_ns() + timeout_ns;
     if (c->cfg.flags & GENESYS_INIT_NO_THREADS) {
       std::lock_guard<std::mutex> g(c->svc_mu);
       Batch batch(std::max<uint32_t>(1, c->cfg.coalesce_max));
@@ -1068,7 +1062,7 @@ int genesys_service(genesys_ctx *c, uint64_t timeout_ns) {
         for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) n += poll_ring(c, r, batch);
         total += (int)n;
         if (n == 0) cpu_relax();
-      } while (mono_ns() < until);
+      } while (genesys_mono_ns() < until);
       return total;
     }
     return genesys_drain(c, timeout_ns);
@@ -1294,7 +1288,7 @@ int genesys_service_probe(genesys_ctx *c, int fd, const void *payload, uint32_t 
         __atomic_store_n(&sl->req, ((uint64_t)seq[s] << 32) | ((uint64_t)(SYS_pwrite64 & 0xFFFF) << 16) | flags,
                          __ATOMIC_RELEASE);
       }
-      const uint64_t t0 = mono_ns();
+      const uint64_t t0 = genesys_mono_ns();
       for (uint32_t s = 0; s < m; ++s) {
         const uint32_t r = genesys_ring_of(s, R);
         const uint32_t pos = tails_raw[(size_t)r * 32]++;
@@ -1304,7 +1298,7 @@ int genesys_service_probe(genesys_ctx *c, int fd, const void *payload, uint32_t 
       for (uint32_t s = 0; s < m; ++s) {
         uint64_t d;
         while ((uint32_t)((d = __atomic_load_n(&c->done[s], __ATOMIC_ACQUIRE)) >> 32) != seq[s]) {
-          if (mono_ns() - t0 > deadline) {
+          if (genesys_mono_ns() - t0 > deadline) {
             rc = fail(GENESYS_ETIMEDOUT, "service probe: slot %u not completed within the deadline", s);
             break;
           }
@@ -1314,7 +1308,7 @@ int genesys_service_probe(genesys_ctx *c, int fd, const void *payload, uint32_t 
         if ((int32_t)(uint32_t)d != (int32_t)bytes_per_call) ++bad;
         kd[s] = seq[s];
       }
-      total += mono_ns() - t0;
+      total += genesys_mono_ns() - t0;
       if (rc) break;
       i0 += m;
     }
@@ -1341,7 +1335,7 @@ int genesys_emulate_call(genesys_ctx *c, uint32_t nr, const uint64_t args[6], ui
   return genesys_guard("genesys_emulate_call", [&]() -> int {
     if (!c || !args || !ret) return fail(GENESYS_EINVAL, "NULL argument");
     if (!c->host_only) return fail(GENESYS_EINVAL, "genesys_emulate_call needs a host-only context");
-    const uint64_t t0 = mono_ns();
+    const uint64_t t0 = genesys_mono_ns();
     const uint64_t deadline = c->cfg.device_deadline_ns;
     static std::atomic<uint32_t> hint_ctr{0};
     uint32_t s = hint_ctr.fetch_add(1) % c->cfg.n_slots;
@@ -1350,14 +1344,14 @@ int genesys_emulate_call(genesys_ctx *c, uint32_t nr, const uint64_t args[6], ui
       if (__atomic_compare_exchange_n(&c->owner[s], &expect, 1u, false, __ATOMIC_ACQUIRE, __ATOMIC_RELAXED)) break;
       s = (s + 1) % c->cfg.n_slots;
       if (probes % 64 == 63) {
-        if (mono_ns() - t0 > deadline) return fail(GENESYS_ETIMEDOUT, "no free slot");
+        if (genesys_mono_ns() - t0 > deadline) return fail(GENESYS_ETIMEDOUT, "no free slot");
         std::this_thread::yield();
       }
     }
     const uint32_t sq = __atomic_load_n(&c->seq[s], __ATOMIC_RELAXED);
     if (__atomic_load_n(&c->known_done[s], __ATOMIC_RELAXED) != sq) {
       while ((uint32_t)(__atomic_load_n(&c->done[s], __ATOMIC_ACQUIRE) >> 32) != sq) {
-        if (mono_ns() - t0 > deadline) {
+        if (genesys_mono_ns() - t0 > deadline) {
           __atomic_store_n(&c->owner[s], 0u, __ATOMIC_RELEASE);
           return fail(GENESYS_ETIMEDOUT, "slot %u still busy", s);
         }
@@ -1381,7 +1375,7 @@ int genesys_emulate_call(genesys_ctx *c, uint32_t nr, const uint64_t args[6], ui
       for (;;) {
         d = __atomic_load_n(&c->done[s], __ATOMIC_ACQUIRE);
         if ((uint32_t)(d >> 32) == nsq) break;
-        if (mono_ns() - t0 > deadline) {
+        if (genesys_mono_ns() - t0 > deadline) {
           __atomic_store_n(&c->owner[s], 0u, __ATOMIC_RELEASE);
           return fail(GENESYS_ETIMEDOUT, "call not completed within the deadline");
         }

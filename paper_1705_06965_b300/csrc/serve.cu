@@ -37,12 +37,6 @@ constexpr uint64_t kMapUninitialized = 0x4000000;
 
 int set_err(int code, const char *msg) { return genesys_internal_error(code, msg); }
 
-inline uint64_t mono_ns() {
-  timespec ts;
-  clock_gettime(CLOCK_MONOTONIC, &ts);
-  return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
-}
-
 // splitmix64 output function and counter-based value (Steele, Lea & Flood 2014)
 __device__ __forceinline__ uint64_t sm_mix(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -402,7 +396,7 @@ extern "C" int genesys_c5_serve(genesys_ctx *c, const genesys_c5_request *reqs, 
     uint64_t next = 0, retired = 0, launched = 0, calls = 0, admitted_wait_ns = 0;
     uint64_t max_inflight_seen = 0, inflight = 0, graph_launches = 0;
     int err = 0;
-    const uint64_t t0 = mono_ns();
+    const uint64_t t0 = genesys_mono_ns();
     std::vector<uint64_t> arrival_abs(n_req);
     for (uint32_t r = 0; r < n_req; ++r) arrival_abs[r] = cfg.honor_arrivals ? t0 + reqs[r].arrival_ns : t0;
 
@@ -465,7 +459,7 @@ extern "C" int genesys_c5_serve(genesys_ctx *c, const genesys_c5_request *reqs, 
         const cudaError_t q = cudaEventQuery(L.done);
         if (q == cudaErrorNotReady) continue;
         if (q != cudaSuccess) { err = GENESYS_ECUDA; break; }
-        const uint64_t now = mono_ns();
+        const uint64_t now = genesys_mono_ns();
         latency_ns[L.req] = now - arrival_abs[L.req];
         const uint64_t *hr = (const uint64_t *)(hmirror + (size_t)si * (per_ops + per_res) + per_ops);
         for (uint32_t k = 0; k < GENESYS_C5_MAX_OPS; ++k)
@@ -481,7 +475,7 @@ extern "C" int genesys_c5_serve(genesys_ctx *c, const genesys_c5_request *reqs, 
       }
       // admit arrived requests, in arrival order, while budgets allow
       while (next < n_req && !err) {
-        const uint64_t now = mono_ns();
+        const uint64_t now = genesys_mono_ns();
         if (arrival_abs[next] > now) break;
         uint32_t si = 0;
         while (si < K && slots[si].busy) ++si;
@@ -518,14 +512,14 @@ extern "C" int genesys_c5_serve(genesys_ctx *c, const genesys_c5_request *reqs, 
         progress = true;
       }
       if (!progress) {
-        if (mono_ns() > deadline) { err = GENESYS_ETIMEDOUT; break; }
+        if (genesys_mono_ns() > deadline) { err = GENESYS_ETIMEDOUT; break; }
         // nap between event polls: back-to-back cudaEventQuery calls contend
         // with the service threads' CUDA calls
         timespec ts{0, 2000};
         nanosleep(&ts, nullptr);
       }
     }
-    const uint64_t t_end = mono_ns();
+    const uint64_t t_end = genesys_mono_ns();
     // on failure: wait for what was launched before freeing its resources
     for (auto s : streams) cudaStreamSynchronize(s);
     int drc = genesys_drain(c, 10ull * g0.deadline_ns);

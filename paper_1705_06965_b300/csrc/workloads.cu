@@ -35,12 +35,6 @@ __device__ __forceinline__ uint64_t sm64_at(uint64_t seed, uint64_t i) {
 
 int set_err(int code, const char *msg) { return genesys_internal_error(code, msg); }
 
-inline uint64_t host_now_ns() {
-  timespec ts;
-  clock_gettime(CLOCK_MONOTONIC, &ts);
-  return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
-}
-
 // Launch through the runtime (legality checks, kernel-grain state reset,
 // synchronise + drain), then turn device-side failures into GENESYS_EDEVICE.
 int run(genesys_ctx *c, const void *kernel, uint32_t grid, uint32_t block, size_t smem, void **args, uint32_t flags,
@@ -591,13 +585,13 @@ int genesys_internal_clock_offset(int device, uint32_t rounds, uint64_t timeout_
       bool host_late = false;
       volatile uint64_t *ping = flags, *pong = flags + 8;
       std::thread echo([&] {
-        const uint64_t until = host_now_ns() + timeout_ns + 1000000000ull;
+        const uint64_t until = genesys_mono_ns() + timeout_ns + 1000000000ull;
         for (uint32_t r = 1; r <= rounds; ++r) {
           while (__atomic_load_n(ping, __ATOMIC_ACQUIRE) != r) {
-            if (host_now_ns() > until) { host_late = true; return; }
+            if (genesys_mono_ns() > until) { host_late = true; return; }
             __builtin_ia32_pause();
           }
-          host_t[r - 1] = host_now_ns();
+          host_t[r - 1] = genesys_mono_ns();
           __atomic_store_n(pong, (uint64_t)r, __ATOMIC_RELEASE);
         }
       });
@@ -653,10 +647,10 @@ int genesys_link_pingpong(int device, uint32_t rounds, uint64_t timeout_ns, uint
     if (rc == 0) {
       volatile uint64_t *ping = flags, *pong = flags + 8;
       std::thread echo([&] {
-        const uint64_t until = host_now_ns() + timeout_ns + 1000000000ull;
+        const uint64_t until = genesys_mono_ns() + timeout_ns + 1000000000ull;
         for (uint32_t r = 1; r <= rounds; ++r) {
           while (__atomic_load_n(ping, __ATOMIC_ACQUIRE) != r) {
-            if (host_now_ns() > until) { host_late = true; return; }
+            if (genesys_mono_ns() > until) { host_late = true; return; }
             __builtin_ia32_pause();
           }
           __atomic_store_n(pong, (uint64_t)r, __ATOMIC_RELEASE);
