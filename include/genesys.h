@@ -118,8 +118,12 @@ int genesys_config_default(genesys_config *cfg);
  * service threads.  *out receives the context.  Sec. 5. */
 int genesys_init(const genesys_config *cfg, int device, genesys_ctx **out);
 
-/* Stop the service threads (after draining for up to 1 s) and free everything
- * the context owns.  Idempotent for a NULL context. */
+/* Wait for the device's work in flight (kernels that still make calls keep
+ * being served; every device-side wait is bounded), stop the service threads
+ * after draining for up to 1 s, and free everything the context owns.  Returns
+ * GENESYS_EINVAL and leaves the context untouched while a key-value or echo
+ * server started on it still runs (stop it first); on any other return the
+ * context is gone.  Idempotent for a NULL context. */
 int genesys_shutdown(genesys_ctx *ctx);
 
 /* The device view of the context (plain struct, pass it to kernels by value;
@@ -428,7 +432,9 @@ int genesys_kv_start(genesys_ctx *ctx, const uint8_t *keys, const uint16_t *vlen
                      uint32_t n_keys, uint32_t n_sockets, uint32_t batch, uint32_t threads, uint16_t port_base,
                      uint64_t idle_timeout_ns, genesys_kv_server **out);
 /* Stop the server (bounded by timeout_ns), drain its calls, free it; *served
- * (if non-NULL) = replies sent. */
+ * (if non-NULL) = replies sent.  On an error (GENESYS_ETIMEDOUT: the kernel
+ * has not left, or its calls did not drain) the server is kept and the call
+ * can be repeated; the context cannot be shut down until one succeeds. */
 int genesys_kv_stop(genesys_kv_server *srv, uint64_t timeout_ns, uint64_t *served);
 /* Current value of key k (copied to out, GENESYS_KV_VALUE_MAX bytes room);
  * returns its length. */
@@ -468,7 +474,8 @@ typedef struct genesys_echo_server genesys_echo_server;
 int genesys_echo_start(genesys_ctx *ctx, uint32_t n_sockets, uint32_t max_packet, uint32_t form, uint32_t batch,
                        uint32_t threads, uint16_t port_base, uint64_t idle_timeout_ns, genesys_echo_server **out);
 /* Stop the echo server (bounded by timeout_ns), drain its calls and free it;
- * stats[2] (if non-NULL): datagrams echoed, bytes echoed. */
+ * stats[2] (if non-NULL): datagrams echoed, bytes echoed.  On an error the
+ * server is kept and the call can be repeated, as for genesys_kv_stop. */
 int genesys_echo_stop(genesys_echo_server *srv, uint64_t timeout_ns, uint64_t *stats);
 /* Closed-loop UDP echo load generator on n_threads host threads (each with
  * its own socket and the server sockets s = t, t + n_threads, ...): `window`

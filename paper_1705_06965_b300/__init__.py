@@ -250,9 +250,14 @@ class Context:
         return self._h
 
     def close(self) -> None:
+        """Shut the context down.  Refused (GenesysError, the context stays
+        open) while a KVServer or EchoServer started on it still runs."""
         if getattr(self, "_h", None):
-            h, self._h = self._h, None
-            _check(lib().genesys_shutdown(h), "genesys_shutdown")
+            rc = lib().genesys_shutdown(self._h)
+            if rc == EINVAL:  # refused: nothing was freed
+                raise GenesysError(rc, "genesys_shutdown", last_error())
+            self._h = None
+            _check(rc, "genesys_shutdown")
 
     def __enter__(self):
         return self
@@ -453,6 +458,7 @@ class KVServer:
         self.vlen0 = np.ascontiguousarray(np.asarray(vlen0, np.uint16))
         self.vseed0 = np.ascontiguousarray(np.asarray(vseed0, np.uint64))
         self.n_sockets, self.port_base = n_sockets, port_base
+        self._ctx = ctx  # the server runs on the context: keep it alive
         h = ctypes.c_void_p()
         _check(lib().genesys_kv_start(ctx.handle, self.keys.ctypes.data, self.vlen0.ctypes.data,
                                       self.vseed0.ctypes.data, len(self.vlen0), n_sockets, batch, threads, port_base,
@@ -465,11 +471,19 @@ class KVServer:
         return buf.raw[:n]
 
     def stop(self, timeout_ns: int = 30_000_000_000) -> int:
+        """Stop the server; returns the replies it sent.  On an error the
+        server is kept (its kernel may still run) and stop can be called again."""
         served = ctypes.c_uint64()
         if self._h:
-            h, self._h = self._h, None
-            _check(lib().genesys_kv_stop(h, timeout_ns, ctypes.byref(served)), "genesys_kv_stop")
+            _check(lib().genesys_kv_stop(self._h, timeout_ns, ctypes.byref(served)), "genesys_kv_stop")
+            self._h = None
         return served.value
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.stop()
 
 
 def kv_client(reqs: bytes, req_off, arrival_ns, port_base: int, n_sockets: int, timeout_ns: int = 20_000_000_000):
@@ -552,17 +566,27 @@ class EchoServer:
     def __init__(self, ctx: Context, n_sockets: int = 8, max_packet: int = ECHO_PACKET_MAX, form: int = ECHO_SINGLE,
                  batch: int = 16, threads: int = 256, port_base: int = 45000, idle_timeout_ns: int = 20_000_000_000):
         self.n_sockets, self.port_base = n_sockets, port_base
+        self._ctx = ctx  # the server runs on the context: keep it alive
         h = ctypes.c_void_p()
         _check(lib().genesys_echo_start(ctx.handle, n_sockets, max_packet, form, batch, threads, port_base,
                                         idle_timeout_ns, ctypes.byref(h)), "genesys_echo_start")
         self._h = h
 
     def stop(self, timeout_ns: int = 30_000_000_000) -> dict:
+        """Stop the server; returns its packet and byte counts.  On an error
+        the server is kept (its kernel may still run) and stop can be called
+        again."""
         st = np.zeros(2, np.uint64)
         if self._h:
-            h, self._h = self._h, None
-            _check(lib().genesys_echo_stop(h, timeout_ns, st.ctypes.data), "genesys_echo_stop")
+            _check(lib().genesys_echo_stop(self._h, timeout_ns, st.ctypes.data), "genesys_echo_stop")
+            self._h = None
         return {"packets": int(st[0]), "bytes": int(st[1])}
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.stop()
 
 
 def link_pingpong(device: int = 0, rounds: int = 2000, timeout_ns: int = 2_000_000_000) -> float:

@@ -276,6 +276,7 @@ extern "C" int genesys_echo_start(genesys_ctx *c, uint32_t n_sockets, uint32_t m
     const int rc = genesys_launch(c, k, g3, b3, 0, args, GENESYS_GRAN_GROUP | GENESYS_LAUNCH_RELAXED, s->stream);
     if (rc) return fail_cleanup(rc, genesys_last_error());
     s->running = true;
+    genesys_internal_servers(c, +1);
     *out = s;
     return 0;
   });
@@ -294,19 +295,20 @@ extern "C" int genesys_echo_stop(genesys_echo_server *s, uint64_t timeout_ns, ui
         if (genesys_mono_ns() > until) { rc = set_err(GENESYS_ETIMEDOUT, "echo server did not stop"); break; }
         std::this_thread::sleep_for(std::chrono::microseconds(100));
       }
-      if (rc == 0) {
+      if (rc == 0) {  // the kernel has finished (else it stays running: a later stop waits again)
         cudaStreamSynchronize(s->stream);
-        rc = genesys_drain(s->ctx, timeout_ns);
+        s->running = false;
+        genesys_internal_servers(s->ctx, -1);
       }
-      s->running = false;
     }
+    if (rc == 0) rc = genesys_drain(s->ctx, timeout_ns);  // its last calls, also on a repeated stop
     if (stats) {
       unsigned long long v[2] = {0, 0};
       cudaMemcpy(v, s->d_counters, sizeof v, cudaMemcpyDeviceToHost);
       stats[0] = v[0];
       stats[1] = v[1];
     }
-    if (rc) return rc;  // the kernel may still run: keep its memory
+    if (rc) return rc;  // the kernel may still run (or calls are pending): keep its memory
     for (int fd : s->socks) close(fd);
     cudaFree(s->dmem);
     cudaStreamDestroy(s->stream);

@@ -33,6 +33,11 @@ int genesys_internal_scratch(struct genesys_ctx *ctx, size_t bytes, void **out);
 uint64_t genesys_internal_staging_mark(struct genesys_ctx *ctx);
 void genesys_internal_staging_release(struct genesys_ctx *ctx, uint64_t mark);
 
+/* Count of persistent server kernels (key-value, echo) running on the
+ * context: +1 when one starts, -1 once it has finished.  genesys_shutdown
+ * refuses while it is above 0. */
+void genesys_internal_servers(struct genesys_ctx *ctx, int delta);
+
 /* CUDA device ordinal of the context (-1 for NULL). */
 int genesys_internal_device(struct genesys_ctx *ctx);
 

@@ -358,6 +358,7 @@ extern "C" int genesys_kv_start(genesys_ctx *c, const uint8_t *keys, const uint1
                             GENESYS_GRAN_GROUP | GENESYS_LAUNCH_RELAXED, s->stream);
     if (rc) return fail_cleanup(rc, genesys_last_error());
     s->running = true;
+    genesys_internal_servers(c, +1);
     *out = s;
     return 0;
   });
@@ -377,18 +378,19 @@ extern "C" int genesys_kv_stop(genesys_kv_server *s, uint64_t timeout_ns, uint64
         if (genesys_mono_ns() > until) { rc = set_err(GENESYS_ETIMEDOUT, "kv server did not stop"); break; }
         std::this_thread::sleep_for(std::chrono::microseconds(100));
       }
-      if (rc == 0) {
+      if (rc == 0) {  // the kernel has finished (else it stays running: a later stop waits again)
         cudaStreamSynchronize(s->stream);
-        rc = genesys_drain(s->ctx, timeout_ns);
+        s->running = false;
+        genesys_internal_servers(s->ctx, -1);
       }
-      s->running = false;
     }
+    if (rc == 0) rc = genesys_drain(s->ctx, timeout_ns);  // its last calls, also on a repeated stop
     if (served) {
       unsigned long long v = 0;
       cudaMemcpy(&v, s->d_served, 8, cudaMemcpyDeviceToHost);
       *served = v;
     }
-    if (rc) return rc;  // the kernel may still run: keep its memory
+    if (rc) return rc;  // the kernel may still run (or calls are pending): keep its memory
     for (int fd : s->socks) close(fd);
     cudaFree(s->dmem);
     cudaStreamDestroy(s->stream);

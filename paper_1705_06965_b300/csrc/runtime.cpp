@@ -150,6 +150,7 @@ struct genesys_ctx {
   // service side
   std::vector<std::thread> threads;
   std::atomic<bool> stop{false};
+  std::atomic<int> servers{0};  // persistent server kernels running on the context
   std::unique_ptr<std::atomic<bool>[]> ring_stop;  // per ring: its thread should leave
   std::mutex restart_mu;
   std::vector<uint64_t> head;                       // per ring, touched by its thread only
@@ -709,6 +710,10 @@ int genesys_internal_error(int code, const char *msg) { return fail(code, "%s", 
 
 int genesys_internal_device(genesys_ctx *c) { return c ? c->device : -1; }
 
+void genesys_internal_servers(genesys_ctx *c, int delta) {
+  if (c) c->servers.fetch_add(delta);
+}
+
 uint64_t genesys_internal_staging_mark(genesys_ctx *c) { return c ? c->staging_used.load() : 0; }
 
 void genesys_internal_staging_release(genesys_ctx *c, uint64_t mark) {
@@ -960,10 +965,16 @@ int genesys_service_restart(genesys_ctx *c, uint32_t ring, uint64_t pause_ns) {
 
 int genesys_shutdown(genesys_ctx *c) {
   if (!c) return 0;
+  if (const int n = c->servers.load())
+    return fail(GENESYS_EINVAL, "%d server kernel(s) still run on this context: stop them first", n);
   int rc = 0;
+  // kernels still in flight use the slot area and may wait on calls: let them
+  // finish (every device wait is bounded) while the service threads still run
+  if (!c->host_only && cudaSetDevice(c->device) == cudaSuccess && cudaDeviceSynchronize() != cudaSuccess)
+    rc = fail(GENESYS_ECUDA, "shutdown: %s", cudaGetErrorString(cudaGetLastError()));
   std::unique_lock<std::mutex> restarting(c->restart_mu);  // no thread is being replaced meanwhile
   if (!c->threads.empty()) {
-    rc = genesys_drain(c, 1000000000ull);
+    if (const int d = genesys_drain(c, 1000000000ull)) rc = rc ? rc : d;
     c->stop.store(true);
     for (auto &t : c->threads) t.join();
     c->threads.clear();

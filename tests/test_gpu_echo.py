@@ -68,3 +68,17 @@ def test_echo_rejects_bad_arguments(G, ctx):
         G.EchoServer(ctx, n_sockets=1, max_packet=4, port_base=_port(97))
     with pytest.raises(G.GenesysError):
         G.EchoServer(ctx, n_sockets=1, form=1, batch=G.ECHO_MAX_BATCH + 1, port_base=_port(96))
+
+
+def test_a_context_with_a_running_server_is_not_shut_down(G):
+    """genesys_shutdown refuses (and frees nothing) while a server kernel runs
+    on the context; once the server is stopped the context closes."""
+    c = G.Context(device=0, service_threads=2, staging_bytes=8 << 20)
+    with G.EchoServer(c, n_sockets=1, max_packet=256, form=0, port_base=_port(95)) as srv:
+        with pytest.raises(G.GenesysError):
+            c.close()
+        st = G.echo_client(srv.port_base, 1, 64, 50, window=2, threads=1)   # still served
+        assert st["echoed"] == 50, st
+    c.close()
+    with pytest.raises(RuntimeError):
+        c.handle
