@@ -346,9 +346,11 @@ extern "C" int genesys_c5_serve(genesys_ctx *c, const genesys_c5_request *reqs, 
     if (!staging) return set_err(GENESYS_ENOMEM, "staging arena too small for staging_budget");
     staging = (uint8_t *)(((uintptr_t)staging + 255) & ~uintptr_t(255));
 
-    std::vector<cudaStream_t> streams(cfg.n_streams);
+    std::vector<cudaStream_t> streams(cfg.n_streams, nullptr);
     for (auto &s : streams) {
       if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        for (auto made : streams)
+          if (made) cudaStreamDestroy(made);
         genesys_internal_staging_release(c, staging_mark);
         return set_err(GENESYS_ECUDA, "stream");
       }
@@ -361,7 +363,16 @@ extern "C" int genesys_c5_serve(genesys_ctx *c, const genesys_c5_request *reqs, 
       return set_err(GENESYS_ECUDA, "pinned mirror");
     }
     std::vector<Launch> slots(K);
-    for (auto &L : slots) cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);
+    for (auto &L : slots) {
+      if (cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess) {
+        for (auto &M : slots)
+          if (M.done) cudaEventDestroy(M.done);
+        for (auto s : streams) cudaStreamDestroy(s);
+        cudaFreeHost(hmirror);
+        genesys_internal_staging_release(c, staging_mark);
+        return set_err(GENESYS_ECUDA, "events");
+      }
+    }
     cudaMemcpy(dbase + fds_off, in_fds, n_in * sizeof(int32_t), cudaMemcpyHostToDevice);
 
     // GPU mmaps are served from regions mapped and registered now, while no
@@ -383,6 +394,7 @@ extern "C" int genesys_c5_serve(genesys_ctx *c, const genesys_c5_request *reqs, 
       if (cfg.reserve_mmaps && !sizes.empty()) {
         rc = genesys_mmap_reserve(c, sizes.data(), (uint32_t)sizes.size());
         if (rc) {
+          for (auto &L : slots) cudaEventDestroy(L.done);
           for (auto s : streams) cudaStreamDestroy(s);
           cudaFreeHost(hmirror);
           genesys_internal_staging_release(c, staging_mark);
