@@ -638,3 +638,39 @@ def test_no_cxx_exception_crosses_the_c_abi():
     assert rc == G.EINVAL
     assert "genesys_kv_client" in L.genesys_last_error().decode()
     assert _open_fds() == before
+
+
+_THREADS_CANNOT_START = r'''
+import resource
+import paper_1705_06965_b300 as G
+G.lib()
+vm = [int(l.split()[1]) * 1024 for l in open("/proc/self/status") if l.startswith("VmSize:")][0]
+# room for the context's memory but not for 64 thread stacks
+resource.setrlimit(resource.RLIMIT_AS, (vm + (96 << 20), resource.RLIM_INFINITY))
+try:
+    G.Context(host_only=True, service_threads=64, n_slots=32, staging_bytes=0)
+    print("started")
+except G.GenesysError as e:
+    print("code", e.code)
+resource.setrlimit(resource.RLIMIT_AS, (resource.RLIM_INFINITY, resource.RLIM_INFINITY))
+with G.Context(host_only=True, service_threads=2, n_slots=32, staging_bytes=0) as c:
+    print("after", c.emulate_call(G.SYS_getpid))
+'''
+
+
+def test_service_threads_that_cannot_start_are_an_error_not_an_abort():
+    """genesys_init with an address-space limit that leaves no room for the
+    service threads' stacks: the thread that fails to start becomes
+    GENESYS_ENOMEM (the started ones are stopped and joined, the memory given
+    back), and the process goes on to open a context normally."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _THREADS_CANNOT_START], cwd=root, capture_output=True, text=True,
+                       timeout=120, env=dict(os.environ, PYTHONPATH=root))
+    assert r.returncode == 0, r.stdout + r.stderr
+    out = r.stdout.split("\n")
+    if "started" in out:
+        pytest.skip("the address-space limit did not stop the threads here")
+    assert f"code {G.ENOMEM}" in out, r.stdout
+    assert any(ln.startswith("after ") and int(ln.split()[1]) > 0 for ln in out), r.stdout
