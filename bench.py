@@ -20,6 +20,7 @@ step's calls are all complete inside the timed region).
     python bench.py --only c4          # key-value service rate sweep (+ oracle server)
     python bench.py --only c5          # the served mixed trace
     python bench.py --only fig10       # echo bandwidth versus packet size
+    python bench.py --only f4          # open/write/lseek/read/close/madvise from GPU code
 
 --impl reference times the CPU oracle (a sequential C program issuing the
 same pwrite/pread calls) on the same workload on the host cores.
@@ -407,9 +408,12 @@ def run_only(args):
     rank, local, _ = dist_env()
     torch.cuda.set_device(local)
     kind, _, rest = args.only.partition(":")
-    if kind in ("c4", "c5", "fig10"):
+    if kind in ("c4", "c5", "fig10", "f4"):
         import paper_1705_06965_b300 as G
-        res = {"c4": serve_c4, "c5": serve_c5, "fig10": study_fig10}[kind](G, local, rank)
+        if kind == "f4":
+            res = study_f4(G, local)
+        else:
+            res = {"c4": serve_c4, "c5": serve_c5, "fig10": study_fig10}[kind](G, local, rank)
         print(json.dumps({"only": args.only, kind: res}), flush=True)
         return
     rig = Rig(args, local, rank, need_scan=kind == "c1" and rest.split(":")[-1] != str(C1_BYTES),
@@ -523,7 +527,95 @@ def profile_extras(args, rig, local, rank, link):
     out["fig6_block_permutation"] = study_fig6(G, rig, local)
     out["fig7_coalescing"] = study_fig7(G, rig, local, rank)
     out["fig10_echo"] = study_fig10(G, local, rank)
+    try:
+        out["f4_other_calls"] = study_f4(G, local)
+    except Exception as e:  # reported in the line, never hidden
+        out["f4_other_calls"] = {"error": f"{type(e).__name__}: {e}"}
     out["call_timeline"] = trace_timeline(G, rig, local)
+    return out
+
+
+def study_f4(G, local, n=200, nbytes=4096, warmup=3):
+    """Sec. 5 and Sec. 8.1: the rest of the paper's call set made from GPU
+    code - open, write, lseek, read and close on a file the GPU opened
+    itself (a stateful descriptor), and madvise on host-mapped memory - one
+    call per single-block kernel at work-group grain (128 threads).  Per call:
+    the kernel's device time (claim, publish, service, completion and the
+    barriers around the call) p50/p99 over n rounds; every round writes fresh
+    random bytes and must read back exactly them.  The same calls made by a
+    host thread are timed beside it."""
+    import mmap
+    import tempfile
+    import numpy as np
+    nrs = {"open": 2, "write": 1, "lseek": 8, "read": 0, "close": 3, "madvise": 28}
+    o_flags = os.O_RDWR | os.O_CREAT | os.O_TRUNC
+    tmp = tempfile.mkdtemp(prefix="genesys_f4_")
+    path = os.path.join(tmp, "f4.bin")
+    dev_ms = {k: [] for k in nrs}
+    host_ns = {k: [] for k in nrs}
+    ok = True
+    rng = np.random.default_rng(1705)
+    try:
+        with G.Context(device=local, service_threads=2, staging_bytes=1 << 20) as ctx:
+            pb = path.encode() + b"\0"
+            pbuf = ctx.staging(len(pb))
+            ctx.host_view(pbuf, len(pb))[:] = np.frombuffer(pb, np.uint8)
+            wbuf, rbuf = ctx.staging(nbytes), ctx.staging(nbytes)
+            page = (ctx.staging(2 * 4096) + 4095) & ~4095
+            w, r = ctx.host_view(wbuf, nbytes), ctx.host_view(rbuf, nbytes)
+
+            def call(name, args, keep):
+                ret = ctx.gpu_call(nrs[name], args, G.GRAN_GROUP, 128)
+                if keep:
+                    dev_ms[name].append(ctx.last_launch_ms())
+                return ret
+
+            for i in range(warmup + n):
+                keep = i >= warmup
+                w[:] = rng.integers(0, 256, nbytes, dtype=np.uint8)
+                r[:] = 0
+                fd = call("open", [pbuf, o_flags, 0o644], keep)
+                ok &= fd >= 0
+                ok &= call("write", [fd, wbuf, nbytes], keep) == nbytes
+                ok &= call("lseek", [fd, 0, os.SEEK_SET], keep) == 0
+                ok &= call("read", [fd, rbuf, nbytes], keep) == nbytes
+                ok &= bool(np.array_equal(r, w))
+                ok &= call("close", [fd], keep) == 0
+                ok &= call("madvise", [page, 4096, mmap.MADV_NORMAL], keep) == 0
+            status = ctx.status()
+            ok &= not any(status)
+        # the same calls from a host thread
+        hbuf = bytearray(nbytes)
+        region = mmap.mmap(-1, 4096)
+        for i in range(warmup + n):
+            keep = i >= warmup
+            t = [time.perf_counter_ns()]
+            fd = os.open(path, o_flags, 0o644)
+            t.append(time.perf_counter_ns())
+            os.write(fd, hbuf)
+            t.append(time.perf_counter_ns())
+            os.lseek(fd, 0, os.SEEK_SET)
+            t.append(time.perf_counter_ns())
+            os.readv(fd, [hbuf])
+            t.append(time.perf_counter_ns())
+            os.close(fd)
+            t.append(time.perf_counter_ns())
+            region.madvise(mmap.MADV_NORMAL, 0, 4096)
+            t.append(time.perf_counter_ns())
+            if keep:
+                for k, name in enumerate(nrs):
+                    host_ns[name].append(t[k + 1] - t[k])
+        region.close()
+    finally:
+        if os.path.exists(path):
+            os.unlink(path)
+        os.rmdir(tmp)
+    out = {"rounds": n, "bytes_per_read_write": nbytes, "grain": "work-group (128 threads), one call per kernel",
+           "all_results_correct": bool(ok), "gpu_kernel_us": {}, "host_thread_us": {}}
+    for name in nrs:
+        a = [x * 1e3 for x in dev_ms[name]]
+        out["gpu_kernel_us"][name] = {"p50": round(pctl(a, 50), 2), "p99": round(pctl(a, 99), 2)}
+        out["host_thread_us"][name] = {"p50": round(pctl([x * 1e-3 for x in host_ns[name]], 50), 2)}
     return out
 
 
@@ -1052,7 +1144,7 @@ def main():
     ap.add_argument("--coalesce-max", type=int, default=64, help="--only: service batch size")
     ap.add_argument("--poll-max-ns", type=int, default=2048, help="--only: largest completion-poll back-off")
     ap.add_argument("--only", default=None, help="run one case: c2:<grain>/<order>/<block>:<threads>, "
-                                                 "c1:<plain|batched>:<bytes>, c3:<plain|batched>")
+                                                 "c1:<plain|batched>:<bytes>, c3:<plain|batched>, c4, c5, fig10, f4")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
