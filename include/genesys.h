@@ -127,7 +127,8 @@ int genesys_init(const genesys_config *cfg, int device, genesys_ctx **out);
 int genesys_shutdown(genesys_ctx *ctx);
 
 /* The device view of the context (plain struct, pass it to kernels by value;
- * genesys_device.cuh reads it). */
+ * genesys_device.cuh reads it; genesys_syscall.cuh binds it for the
+ * handle-less genesys_syscall). */
 int genesys_device_view(genesys_ctx *ctx, genesys_dev *out);
 
 /* ------------------------------------------------------------ launching */
@@ -226,6 +227,7 @@ int genesys_trace_read(genesys_ctx *ctx, genesys_trace_dev *dev, uint32_t dev_ca
 #define GENESYS_SIZEOF_TRACE_DEV    4
 #define GENESYS_SIZEOF_TRACE_HOST   5
 #define GENESYS_SIZEOF_C5_REQUEST   6
+#define GENESYS_SIZEOF_DEV          7
 uint32_t genesys_sizeof(int which);
 
 /* Failure detection on the host (a watchdog's probe): *stalled_mask gets bit r

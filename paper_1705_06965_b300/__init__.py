@@ -36,6 +36,7 @@ FORM_PLAIN, FORM_BATCHED, FORM_WARP, FORM_HBM = 0, 1, 2, 3
 ST_FIRST_ERROR, ST_TIMEOUTS, ST_FAILED_CALLS, ST_BAD_ARGS, ST_WORDS = 0, 1, 2, 3, 8
 
 EINVAL, ENOMEM, ETIMEDOUT, ENODEV, EDEVICE, ECUDA = -22, -12, -110, -19, -1001, -1000
+SIZEOF_DEV = 7  # GENESYS_SIZEOF_DEV
 
 # every entry point declared in include/genesys.h
 EXPORTS = [
@@ -270,6 +271,14 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def device_view(self) -> ctypes.Array:
+        """The context's device view (genesys_device_view) as raw bytes, for
+        kernels of one's own: pass it by value, or bind it for the
+        handle-less genesys_syscall (genesys_syscall_bind)."""
+        buf = ctypes.create_string_buffer(int(lib().genesys_sizeof(SIZEOF_DEV)))
+        _check(lib().genesys_device_view(self.handle, buf), "genesys_device_view")
+        return buf
 
     # -- staging arena (pinned, host-mapped: one address valid on both sides)
     def staging(self, nbytes: int) -> int:

@@ -916,6 +916,7 @@ uint32_t genesys_sizeof(int which) {
     case GENESYS_SIZEOF_TRACE_DEV: return sizeof(genesys_trace_dev);
     case GENESYS_SIZEOF_TRACE_HOST: return sizeof(genesys_trace_host);
     case GENESYS_SIZEOF_C5_REQUEST: return sizeof(genesys_c5_request);
+    case GENESYS_SIZEOF_DEV: return sizeof(genesys_dev);
     default: return 0;
   }
 }

@@ -98,3 +98,46 @@ def test_call_trace_joins_and_adds_up(gran, bt, tmp_path):
     # the host stages lie inside the call: pickup after publish, completion
     # before the result is seen (up to the calibration error)
     assert b["service"]["p99_ns"] <= b["total"]["p99_ns"] + slack, b
+
+
+def test_handle_less_genesys_syscall_from_a_kernel_of_ones_own(G, ctx, tmp_path):
+    """include/genesys_syscall.cuh: a kernel built apart from the library binds
+    the context's device view and calls genesys_syscall(nr, ...) - one
+    work-item pwrite per thread (the plain form), then a work-group getpid.
+    The file holds every thread's record and every call returned its own
+    result."""
+    import ctypes
+    import subprocess
+    from paper_1705_06965_b300 import build
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    so = str(tmp_path / "syscall_demo.so")
+    r = subprocess.run([build.nvcc(), *build.ARCH, "-std=c++17", "-O3", "-Xcompiler", "-fPIC", "-shared", "-cudart",
+                        "shared", "-I", os.path.join(root, "include"),
+                        os.path.join(root, "tests", "c_abi", "syscall_demo.cu"), "-o", so],
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    demo = ctypes.CDLL(so)
+    demo.syscall_demo.restype = ctypes.c_int
+    demo.syscall_demo.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32,
+                                  ctypes.c_void_p, ctypes.c_void_p]
+    blocks, threads = 8, 128
+    n = blocks * threads
+    ctx.staging_reset()
+    rec = ctx.staging(n * 64)
+    want = np.random.default_rng(1705).integers(0, 256, n * 64, dtype=np.uint8)
+    ctx.host_view(rec, n * 64)[:] = want
+    item = torch.full((n,), -1, dtype=torch.int64, device="cuda:0")
+    group = torch.zeros(blocks, dtype=torch.int64, device="cuda:0")
+    path = str(tmp_path / "records.bin")
+    fd = os.open(path, os.O_CREAT | os.O_TRUNC | os.O_WRONLY, 0o644)
+    try:
+        view = ctx.device_view()
+        rc = demo.syscall_demo(ctypes.addressof(view), fd, rec, blocks, threads, item.data_ptr(), group.data_ptr())
+        ctx.drain()
+    finally:
+        os.close(fd)
+    assert rc == 0
+    assert bool((item.cpu() == 64).all())
+    assert bool((group.cpu() == os.getpid()).all())
+    assert np.array_equal(np.fromfile(path, np.uint8), want)
+    assert not any(ctx.status())

@@ -483,6 +483,11 @@ def test_binding_and_library_agree_on_struct_sizes():
     assert int(L.genesys_sizeof(4)) == G.TRACE_DEV_DTYPE.itemsize == 40
     assert int(L.genesys_sizeof(5)) == G.TRACE_HOST_DTYPE.itemsize == 24
     assert int(L.genesys_sizeof(99)) == 0
+    # the device view as raw bytes (for kernels of one's own), filled in
+    with _ctx(n_slots=4096) as c:
+        view = c.device_view()
+        assert len(view) == int(L.genesys_sizeof(G.SIZEOF_DEV)) > 0
+        assert any(view.raw)
 
 
 def test_checked_build_host_protocol_checker(tmp_path):
@@ -600,9 +605,11 @@ def test_service_health_sees_a_paused_thread():
         assert c.service_health(50_000_000) == ([], 0)
 
 
-def test_a_user_kernel_compiles_against_the_headers(tmp_path):
-    """The device header is usable from a user's own kernel: the README's
-    example compiles for sm_103a with nothing but include/ (not run here)."""
+@pytest.mark.parametrize("src", ["user_kernel.cu", "syscall_demo.cu"])
+def test_a_user_kernel_compiles_against_the_headers(tmp_path, src):
+    """The device headers are usable from a user's own kernel: the README's
+    example (genesys::call) and a kernel of the handle-less genesys_syscall
+    compile for sm_103a with nothing but include/ (not run here)."""
     import shutil
     import subprocess
     from paper_1705_06965_b300 import build
@@ -611,7 +618,7 @@ def test_a_user_kernel_compiles_against_the_headers(tmp_path):
         pytest.skip("no nvcc")
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     r = subprocess.run([nvcc, *build.ARCH, "-std=c++17", "-c", "-I", os.path.join(root, "include"),
-                        os.path.join(root, "tests", "c_abi", "user_kernel.cu"), "-o", str(tmp_path / "u.o")],
+                        os.path.join(root, "tests", "c_abi", src), "-o", str(tmp_path / "u.o")],
                        capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
 
