@@ -500,6 +500,9 @@ def kv_client(reqs: bytes, req_off, arrival_ns, port_base: int, n_sockets: int, 
     n = len(arrival_ns)
     off = np.ascontiguousarray(np.asarray(req_off, np.uint64))
     arr = np.ascontiguousarray(np.asarray(arrival_ns, np.uint64))
+    # the library reads request j at reqs[req_off[j]:req_off[j + 1]], 24 bytes at least
+    if len(off) != n + 1 or (n and (int(off[-1]) > len(reqs) or bool(np.any(np.diff(off) < 24)))):
+        raise ValueError("req_off must hold n + 1 increasing offsets into reqs, 24 bytes or more apart")
     rb = ctypes.create_string_buffer(reqs, max(len(reqs), 1))
     out = np.zeros(max(n, 1) * KV_REPLY_STRIDE, np.uint8)
     rlen = np.zeros(max(n, 1), np.uint32)

@@ -89,3 +89,17 @@ def test_values0_table_matches_stream():
     for i in range(300):
         v = tr.value0(i)
         assert T[i, :len(v)].tobytes() == v and not T[i, len(v):].any()
+
+
+def test_kv_client_refuses_offsets_that_do_not_describe_the_requests():
+    """The load generator reads request j at reqs[req_off[j]:req_off[j + 1]]:
+    offsets that do not cover n requests of at least a header each are
+    refused before anything is sent."""
+    import paper_1705_06965_b300 as G
+    reqs = bytes(48)
+    with pytest.raises(ValueError):
+        G.kv_client(reqs, [0, 24], [0, 0], 47999, 1)          # n + 1 offsets needed
+    with pytest.raises(ValueError):
+        G.kv_client(reqs, [0, 24, 72], [0, 0], 47999, 1)      # runs past the bytes
+    with pytest.raises(ValueError):
+        G.kv_client(reqs, [0, 8, 48], [0, 0], 47999, 1)       # shorter than a header
