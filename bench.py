@@ -519,6 +519,11 @@ def profile_extras(args, rig, local, rank, link):
                     "frac_of_hbm_peak": round(gbs / hbm_peak(), 5),
                     "ms": round(ms, 2), "counts_equal_ground_truth": ok}
             out["wordcount_c3"] = {"autotuned": best, "corpus_bytes": c.total_bytes, **res}
+            if rank == 0:
+                try:
+                    out["wordcount_c3"]["cpu_baseline_oracle"] = cpu_baseline_c3(c)
+                except Exception as e:  # reported in the line, never hidden
+                    out["wordcount_c3"]["cpu_baseline_oracle"] = {"error": f"{type(e).__name__}: {e}"}
     finally:
         for fd in fds:
             os.close(fd)
@@ -749,11 +754,56 @@ def serve_c5(G, local, rank):
             slow = tr.subset(np.arange(2000))
             slow.arrival_ns = (slow.arrival_ns.astype(np.float64) * (tr.params["rate_per_s"] / 4000.0)).astype(np.uint64)
             _, out["served_first2000_at_4k_per_s"] = run(slow, max_inflight=64, **tuned)
+        if rank == 0:
+            try:
+                out["cpu_baseline_oracle_replay_first1000"] = cpu_baseline_c5(first, in_fds, d, r_served)
+            except Exception as e:  # reported in the line, never hidden
+                out["cpu_baseline_oracle_replay_first1000"] = {"error": f"{type(e).__name__}: {e}"}
     finally:
         for fd in in_fds:
             os.close(fd)
     out["trace"] = {"requests": len(tr), "rate_per_s": tr.params["rate_per_s"]}
     return out
+
+
+def cpu_baseline_c3(c, sample_bytes=512 << 20):
+    """The oracle's wordcount on the host cores (Sec. 7.1's CPU baseline):
+    one thread, and the files-to-cores OpenMP form on every core, over the
+    corpus's first files up to sample_bytes; the two must count the same."""
+    import numpy as np
+    import oracle
+    sizes = np.asarray(c.sizes, np.int64)
+    k = min(len(sizes), int(np.searchsorted(np.cumsum(sizes), sample_bytes)) + 1)
+    paths, nb = c.paths[:k], int(sizes[:k].sum())
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    one, _ = oracle.c3_wordcount(paths, c.queries)
+    d1 = time.perf_counter() - t
+    t = time.perf_counter()
+    omp, _ = oracle.c3_wordcount(paths, c.queries, threads=cores)
+    d2 = time.perf_counter() - t
+    return {"kind": "oracle", "sample": f"first {k} of {len(sizes)} files, {nb} bytes",
+            "one_thread_GB_per_s": round(nb / d1 / 1e9, 3), "files_to_cores_GB_per_s": round(nb / d2 / 1e9, 3),
+            "cores": cores, "counts_agree": bool(np.array_equal(one, omp))}
+
+
+def cpu_baseline_c5(sub, in_fds, d, served):
+    """The oracle's sequential replay (one thread; requests in arrival order,
+    each operation a plain host call) of the requests `sub`, whose served
+    results are `served`: requests/s, and whether the results agree."""
+    import numpy as np
+    import oracle
+    ofd = os.open(os.path.join(d, "oracle_out.bin"), os.O_CREAT | os.O_RDWR, 0o644)
+    try:
+        t = time.perf_counter()
+        want = oracle.c5_trace(sub, ofd, in_fds)
+        dt = time.perf_counter() - t
+    finally:
+        os.close(ofd)
+    m = np.arange(want.shape[1])[None, :] < sub.n_ops[:, None]
+    return {"kind": "oracle", "requests": len(sub), "cores": 1, "seconds": round(dt, 3),
+            "requests_per_s": round(len(sub) / dt, 1),
+            "served_results_equal_oracle": bool(np.array_equal(want[m], np.asarray(served)[m]))}
 
 
 def _kv_requests_at(rate, n_max):
