@@ -183,7 +183,12 @@ int genesys_reclaim(genesys_ctx *ctx);
  * kernels start keeps registration off the path. */
 int genesys_mmap_reserve(genesys_ctx *ctx, const uint64_t *sizes, uint32_t n);
 
+/* Copy the service counters (genesys_stats: requests, Linux calls, batches,
+ * bytes, failures, per-call-type time, the service threads' CPU time) into
+ * *out (host memory, caller-owned).  GENESYS_EINVAL for NULL arguments. */
 int genesys_stats_get(genesys_ctx *ctx, genesys_stats *out);
+/* Zero the service counters; the service threads' CPU time counts from
+ * here on.  Call between measurements, with no calls in flight. */
 int genesys_stats_reset(genesys_ctx *ctx);
 
 /* Copy the device status words (GENESYS_ST_*) into out; clear them if `clear`. */
@@ -198,6 +203,8 @@ int genesys_latency(genesys_ctx *ctx, uint64_t *out, uint32_t cap, uint32_t *n_o
  * host-mapped memory whose address is valid on the host and on the GPU, so
  * GPU code can pass it to pread/pwrite/sendto/recvfrom.  NULL if exhausted. */
 void *genesys_staging(genesys_ctx *ctx, size_t bytes);
+/* Give the whole staging arena back (every earlier genesys_staging address
+ * becomes free for reuse).  Only when no kernel or server uses staging. */
 int genesys_staging_reset(genesys_ctx *ctx);
 
 /* Message of the calling thread's last failure. */
@@ -404,6 +411,10 @@ typedef struct genesys_serve_stats {
   uint64_t requests, syscalls, makespan_ns, max_inflight, admission_wait_ns, graph_launches;
 } genesys_serve_stats;
 
+/* Fill *cfg with the defaults: 64 launch slots on 64 streams; budgets of
+ * 64 MiB staging, 64 MiB HBM and 16,384 syscall slots; 256-thread blocks;
+ * min_part 16 KiB; graphs on; pread data scanned where it lands; arrivals
+ * honoured; mmaps reserved; 120 s timeout. */
 int genesys_serve_config_default(genesys_serve_config *cfg);
 int genesys_c5_serve(genesys_ctx *ctx, const genesys_c5_request *reqs, uint32_t n_req, const int32_t *in_fds,
                      uint32_t n_in, int32_t out_fd, const genesys_serve_config *cfg, uint64_t *results,
