@@ -60,6 +60,8 @@ def build(force: bool = False, verbose: bool = False, device_checks: bool = Fals
             raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
         if verbose:
             print(r.stdout + r.stderr)
+        elif "warning" in r.stderr:
+            print(r.stderr, file=sys.stderr)
     return lib
 
 

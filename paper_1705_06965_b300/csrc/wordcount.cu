@@ -56,8 +56,6 @@ int set_err(int code, const char *msg) { return genesys_internal_error(code, msg
 // within the 48 KiB a launch gets without opting in.
 inline uint32_t c3_tile_bytes(uint32_t threads) { return threads * 16 * (threads > 512 ? 2 : 4); }
 
-__device__ __forceinline__ bool is_sep(uint8_t c) { return c == ' ' || c == '\n'; }
-
 __device__ __forceinline__ uint32_t qhash(uint64_t w0, uint64_t w1, uint32_t len) {
   uint64_t z = w0 * 0x9E3779B97F4A7C15ull ^ (w1 + len) * 0xC2B2AE3D27D4EB4Full;
   z ^= z >> 29;
