@@ -358,7 +358,7 @@ int64_t execute_one(genesys_ctx *c, Request &r, Counters &k) {
 // call.  Contiguous buffers become one pread/pwrite, others one
 // preadv/pwritev.  Each request then receives the part of the merged result
 // that covers its own range - the value its own call would have returned.
-size_t merge_run(genesys_ctx *c, Request *const *reqs, size_t i, size_t n, Counters &k) {
+size_t merge_run(Request *const *reqs, size_t i, size_t n, Counters &k) {
   const uint32_t nr = reqs[i]->nr;
   const int fd = (int)reqs[i]->a[0];
   size_t j = i + 1;
@@ -485,7 +485,7 @@ void process_batch(genesys_ctx *c, uint32_t ri, Batch &b, size_t n, Counters &k)
   for (size_t i = 0; i < n;) {
     Request &r = *p[i];
     if (c->cfg.merge && (r.nr == SYS_pread64 || r.nr == SYS_pwrite64)) {
-      i = merge_run(c, p, i, n, k);
+      i = merge_run(p, i, n, k);
       continue;
     }
     const uint64_t e0 = genesys_mono_ns();
