@@ -251,6 +251,20 @@ def host_link_peak(torch, sizes=(4 << 10, 64 << 10, 1 << 20, 16 << 20, 64 << 20,
     return out
 
 
+def service_phases(before: dict, after: dict) -> dict:
+    """Service-thread time per request between two genesys stats snapshots,
+    by phase: taking the batch (slot reads), ordering it for merging, the
+    Linux calls, writing results back; and the mean batch size."""
+    req = max(after["requests"] - before["requests"], 1)
+    os_ns = sum(after["op_ns"][o] - before["op_ns"][o] for o in after["op_ns"])
+
+    def per(key):
+        return round((after[key] - before[key]) / req, 2)
+    return {"pickup": per("pickup_ns"), "order": per("order_ns"), "os_call": round(os_ns / req, 2),
+            "complete": per("complete_ns"), "busy": per("busy_ns"),
+            "requests_per_batch": round(req / max(after["batches"] - before["batches"], 1), 1)}
+
+
 def pctl(a, q):
     import numpy as np
     return float(np.percentile(a, q)) if len(a) else None
@@ -450,6 +464,7 @@ def run_only(args):
         after = rig.ctx.stats()
         d = {k: after[k] - before[k] for k in ("requests", "os_calls", "batches", "busy_ns")}
         d["syscall_ns"] = sum(after["op_ns"][o] - before["op_ns"][o] for o in after["op_ns"])
+        d["ns_per_request"] = service_phases(before, after)
         out.update({"ms": round(ms, 3), "calls": calls, "calls_per_s": round(calls / (ms * 1e-3), 1),
                     "kernel_ms": round(rig.ctx.last_launch_ms(), 3),
                     "service": {**d, "requests_per_os_call": round(d["requests"] / max(d["os_calls"], 1), 2),
@@ -1010,9 +1025,13 @@ def run_genesys(args):
     # pread+scan GB/s at 1 GiB and over the C3 corpus
     sweep = {}
     n = max(SIZES)
+    plain_phases = None
     for name, g, bt, relaxed, nb in COMBOS:
         ctx.latency(clear=True)
+        st0 = ctx.stats() if combo_key(name, relaxed, nb) == combo_key("work-item", False, False) else None
         ms = rig.timed(lambda: rig.c2(n, g, bt, relaxed, nb))
+        if st0 is not None:
+            plain_phases = service_phases(st0, ctx.stats())
         lat = ctx.latency(clear=True)
         calls = calls_for(g, bt, n)
         sweep[combo_key(name, relaxed, nb)] = {
@@ -1035,12 +1054,19 @@ def run_genesys(args):
     # by a host thread (no GPU in the loop; same threads and batch size).
     torch.cuda.synchronize()
     n_probe = SIZES[-1]
-    ceiling = max(ctx.service_probe(rig.fds[n_probe], rig.c2_stage, 64, n_probe) for _ in range(3))
+    probes_run = []
+    for _ in range(3):
+        st0 = ctx.stats()
+        rate = ctx.service_probe(rig.fds[n_probe], rig.c2_stage, 64, n_probe)
+        probes_run.append((rate, service_phases(st0, ctx.stats())))
+    ceiling, probe_phases = max(probes_run, key=lambda t: t[0])
     service_roofline = {"bound": "host_service", "kernel": "c2_pwrite_kernel<work-item,strong,blocking>",
                         "threads": n_probe, "achieved": plain["syscalls_per_s"], "peak": round(ceiling, 1),
                         "unit": "calls/s", "frac": round(plain["syscalls_per_s"] / ceiling, 4),
                         "peak_source": "genesys_service_probe: the same 2^20 64-byte pwrites published by a host "
-                                       "thread, same service threads and batch size, best of 3 (measured)"}
+                                       "thread, same service threads and batch size, best of 3 (measured)",
+                        # where each request's service time goes, GPU in the loop against the probe
+                        "service_ns_per_request": {"gpu_path": plain_phases, "host_probe": probe_phases}}
     # Coarse-grain pwrites move 64 bytes per thread through one merged Linux
     # call per group: their bound is the host's write bandwidth into the file
     # (one tmpfs inode, writers serialised), measured here with the same
@@ -1109,7 +1135,8 @@ def run_genesys(args):
         "autotuned_step": {"best": step_cfg, "table": step_table},
         "host_link_GB_per_s": link,
         "probes": probes,
-        "service": {k: stats[k] for k in ("requests", "os_calls", "batches", "bytes", "failed", "busy_ns")},
+        "service": {k: stats[k] for k in ("requests", "os_calls", "batches", "bytes", "failed", "busy_ns",
+                                          "pickup_ns", "order_ns", "complete_ns")},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": round(job_value(world, calls_step * args.steps, e2e_tot), 1), "unit": "syscalls/s",

@@ -103,6 +103,11 @@ typedef struct genesys_stats {
                                   sequence number was not the slot's previous one + 1,
                                   or whose ring entry named a slot out of range; always
                                   0 in other builds                                    */
+  uint64_t pickup_ns;          /* service-thread time taking batches: reading the slots
+                                  of the ready ring entries (and any coalescing window) */
+  uint64_t order_ns;           /* ... ordering a batch so that file neighbours merge   */
+  uint64_t complete_ns;        /* ... writing results, completion words and the rings'
+                                  finished counts (the Linux calls are op_ns)           */
 } genesys_stats;
 
 typedef struct genesys_ctx genesys_ctx;

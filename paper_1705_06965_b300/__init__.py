@@ -93,7 +93,8 @@ class Stats(ctypes.Structure):
                 ("requests", "os_calls", "failed", "nonblocking_failed", "bytes", "batches", "busy_ns")] + [
         ("by_op", ctypes.c_uint64 * 8), ("op_ns", ctypes.c_uint64 * 8), ("op_max_ns", ctypes.c_uint64 * 8),
         ("mmap_new", ctypes.c_uint64), ("mmap_reused", ctypes.c_uint64), ("service_cpu_ns", ctypes.c_uint64),
-        ("protocol_errors", ctypes.c_uint64)]
+        ("protocol_errors", ctypes.c_uint64), ("pickup_ns", ctypes.c_uint64), ("order_ns", ctypes.c_uint64),
+        ("complete_ns", ctypes.c_uint64)]
 
     OPS = ("pread", "pwrite", "sendto", "recvfrom", "mmap", "munmap", "internal", "other")
 

@@ -95,6 +95,10 @@ struct alignas(64) Counters {
   std::atomic<uint64_t> by_op[8] = {};
   std::atomic<uint64_t> op_ns[8] = {}, op_max_ns[8] = {};
   std::atomic<uint64_t> last_batch_ns{0};  // when the ring's last batch was finished
+  // where a batch's time goes: taking it (slot reads, any coalescing window),
+  // ordering it for merging, and writing its results back; the Linux calls
+  // themselves are op_ns
+  std::atomic<uint64_t> pickup_ns{0}, order_ns{0}, complete_ns{0};
 };
 
 struct Request {
@@ -406,7 +410,8 @@ size_t merge_run(Request *const *reqs, size_t i, size_t n, Counters &k) {
 
 inline bool is_rw(uint32_t nr) { return nr == SYS_pread64 || nr == SYS_pwrite64; }
 
-void process_batch(genesys_ctx *c, uint32_t ri, Batch &b, size_t n, Counters &k) {
+// Returns the time it finished (genesys_mono_ns).
+uint64_t process_batch(genesys_ctx *c, uint32_t ri, Batch &b, size_t n, Counters &k) {
   const uint64_t t0 = genesys_mono_ns();
   Request *const req = b.req.data();
   Request **p = b.ptr.data();
@@ -482,6 +487,7 @@ void process_batch(genesys_ctx *c, uint32_t ri, Batch &b, size_t n, Counters &k)
         for (size_t i = 0; i < n; ++i) p[i] = req + i;
     }
   }
+  bump(k.order_ns, genesys_mono_ns() - t0);
   for (size_t i = 0; i < n;) {
     Request &r = *p[i];
     if (c->cfg.merge && (r.nr == SYS_pread64 || r.nr == SYS_pwrite64)) {
@@ -499,6 +505,7 @@ void process_batch(genesys_ctx *c, uint32_t ri, Batch &b, size_t n, Counters &k)
       bump(k.bytes, (uint64_t)r.ret);
     ++i;
   }
+  const uint64_t t_cpl = genesys_mono_ns();
   uint64_t per_op[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (size_t i = 0; i < n; ++i) {
     complete(c, req[i], k);
@@ -516,8 +523,11 @@ void process_batch(genesys_ctx *c, uint32_t ri, Batch &b, size_t n, Counters &k)
     if (per_op[o]) bump(k.by_op[o], per_op[o]);
   bump(k.requests, n);
   bump(k.batches, 1);
-  k.last_batch_ns.store(genesys_mono_ns(), std::memory_order_relaxed);
-  bump(k.busy_ns, genesys_mono_ns() - t0);
+  const uint64_t t_end = genesys_mono_ns();
+  bump(k.complete_ns, t_end - t_cpl);
+  k.last_batch_ns.store(t_end, std::memory_order_relaxed);
+  bump(k.busy_ns, t_end - t0);
+  return t_end;
 }
 
 inline bool entry_ready(const uint64_t *ring, uint32_t mask, uint64_t pos, uint32_t *slot) {
@@ -569,8 +579,10 @@ size_t poll_ring(genesys_ctx *c, uint32_t ri, Batch &b) {
     __builtin_prefetch(&c->slots[s], 0, 0);
     ++n;
   }
-  for (size_t i = 0; i < n; ++i) read_request(c, slots[i], &batch[i]);
   if (n == 0) return 0;
+  Counters &k = c->counters[ri];
+  const uint64_t t_pick = genesys_mono_ns();
+  for (size_t i = 0; i < n; ++i) read_request(c, slots[i], &batch[i]);
   if (n < maxb && c->cfg.coalesce_window_ns) {
     const uint64_t until = genesys_mono_ns() + c->cfg.coalesce_window_ns;
     while (n < maxb && genesys_mono_ns() < until) {
@@ -582,11 +594,13 @@ size_t poll_ring(genesys_ctx *c, uint32_t ri, Batch &b) {
       }
     }
   }
-  process_batch(c, ri, b, n, c->counters[ri]);
+  bump(k.pickup_ns, genesys_mono_ns() - t_pick);
+  const uint64_t t_done = process_batch(c, ri, b, n, k);
   c->head[ri] = h + n;
   c->retired[ri].store(h + n, std::memory_order_release);
-  for (uint32_t k = 0; k < GENESYS_RING_DONE_COPIES; ++k)
-    __atomic_store_n(&c->ring_done[((size_t)ri * GENESYS_RING_DONE_COPIES + k) * 8], h + n, __ATOMIC_RELEASE);
+  for (uint32_t q = 0; q < GENESYS_RING_DONE_COPIES; ++q)
+    __atomic_store_n(&c->ring_done[((size_t)ri * GENESYS_RING_DONE_COPIES + q) * 8], h + n, __ATOMIC_RELEASE);
+  bump(k.complete_ns, genesys_mono_ns() - t_done);
   return n;
 }
 
@@ -1128,6 +1142,9 @@ int genesys_stats_get(genesys_ctx *c, genesys_stats *o) {
       o->bytes += k.bytes.load();
       o->batches += k.batches.load();
       o->busy_ns += k.busy_ns.load();
+      o->pickup_ns += k.pickup_ns.load();
+      o->order_ns += k.order_ns.load();
+      o->complete_ns += k.complete_ns.load();
       for (int i = 0; i < 8; ++i) {
         o->by_op[i] += k.by_op[i].load();
         o->op_ns[i] += k.op_ns[i].load();
@@ -1151,6 +1168,7 @@ int genesys_stats_reset(genesys_ctx *c) {
   for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) {
     Counters &k = c->counters[r];
     k.requests = 0; k.os_calls = 0; k.failed = 0; k.nb_failed = 0; k.bytes = 0; k.batches = 0; k.busy_ns = 0;
+    k.pickup_ns = 0; k.order_ns = 0; k.complete_ns = 0;
     for (int i = 0; i < 8; ++i) k.by_op[i] = 0, k.op_ns[i] = 0, k.op_max_ns[i] = 0;
   }
   std::lock_guard<std::mutex> g(c->restart_mu);

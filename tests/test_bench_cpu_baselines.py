@@ -38,3 +38,23 @@ def test_c5_baseline_replay_checks_the_served_results():
     finally:
         for fd in in_fds:
             os.close(fd)
+
+
+def test_service_phases_from_a_host_only_context(tmp_path):
+    """The per-request service breakdown the bench reports: with emulated
+    callers on a host-only context every phase is filled in, and ordering,
+    Linux calls and completion together fit in the batch-processing time."""
+    import paper_1705_06965_b300 as G
+    n = 4096
+    fd = os.open(str(tmp_path / "p.bin"), os.O_CREAT | os.O_TRUNC | os.O_RDWR, 0o600)
+    try:
+        with G.Context(host_only=True, service_threads=2, coalesce_max=256, staging_bytes=n * 64 + 4096) as c:
+            buf = c.staging(n * 64)
+            before = c.stats()
+            assert c.service_probe(fd, buf, 64, n) > 0
+            ph = bench.service_phases(before, c.stats())
+    finally:
+        os.close(fd)
+    assert set(ph) == {"pickup", "order", "os_call", "complete", "busy", "requests_per_batch"}
+    assert all(v >= 0 for v in ph.values()) and ph["os_call"] > 0 and ph["requests_per_batch"] >= 1
+    assert ph["order"] + ph["os_call"] <= ph["busy"] + 1e-6
