@@ -471,7 +471,9 @@ def run_only(args):
                                 "requests_per_batch": round(d["requests"] / max(d["batches"], 1), 2),
                                 "busy_frac": round(d["busy_ns"] / (ms * 1e6 * args.service_threads), 4)}})
         if kind == "c2" and g == 0:
+            st0 = rig.ctx.stats()
             out["service_probe_calls_per_s"] = round(rig.ctx.service_probe(rig.fds[n], rig.c2_stage, 64, n), 1)
+            out["service_probe_ns_per_request"] = service_phases(st0, rig.ctx.stats())
         print(json.dumps(out), flush=True)
     finally:
         rig.close()
