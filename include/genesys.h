@@ -112,9 +112,11 @@ typedef struct genesys_stats {
 
 typedef struct genesys_ctx genesys_ctx;
 
-/* Fill *cfg with defaults: slots = SMs x 2048 (or 65536 without a GPU), 4
- * service threads, 256 MiB staging, no coalescing window, coalesce_max 64,
- * merge on, 2 s device deadline, 1 M latency samples, polls 256 ns .. 2 us. */
+/* Fill *cfg with defaults (Sec. 5 sizes the syscall area by the hardware
+ * threads that can be active at once): slots = SMs x 2048 (or 65536 without a
+ * GPU), 4 service threads, 256 MiB staging, no coalescing window, coalesce_max
+ * 64, merge on, 2 s device deadline, 1 M latency samples, polls 256 ns .. 2
+ * us. */
 int genesys_config_default(genesys_config *cfg);
 
 /* Create a context on CUDA device `device`: allocates the syscall area, the
@@ -123,15 +125,16 @@ int genesys_config_default(genesys_config *cfg);
  * service threads.  *out receives the context.  Sec. 5. */
 int genesys_init(const genesys_config *cfg, int device, genesys_ctx **out);
 
-/* Wait for the device's work in flight (kernels that still make calls keep
- * being served; every device-side wait is bounded), stop the service threads
- * after draining for up to 1 s, and free everything the context owns.  Returns
- * GENESYS_EINVAL and leaves the context untouched while a key-value or echo
- * server started on it still runs (stop it first); on any other return the
- * context is gone.  Idempotent for a NULL context. */
+/* Tear the context down (no counterpart in the paper).  Wait for the device's work in flight (kernels that still
+ * make calls keep being served; every device-side wait is bounded), stop the
+ * service threads after draining for up to 1 s, and free everything the
+ * context owns.  Returns GENESYS_EINVAL and leaves the context untouched while
+ * a key-value or echo server started on it still runs (stop it first); on any
+ * other return the context is gone.  Idempotent for a NULL context. */
 int genesys_shutdown(genesys_ctx *ctx);
 
-/* The device view of the context (plain struct, pass it to kernels by value;
+/* The device view of the context: the syscall area and its rings (Sec. 5,
+ * Fig. 3) as a plain struct, pass it to kernels by value;
  * genesys_device.cuh reads it; genesys_syscall.cuh binds it for the
  * handle-less genesys_syscall). */
 int genesys_device_view(genesys_ctx *ctx, genesys_dev *out);
@@ -155,16 +158,18 @@ int genesys_device_view(genesys_ctx *ctx, genesys_dev *out);
 int genesys_launch(genesys_ctx *ctx, const void *kernel, const uint32_t grid[3], const uint32_t block[3],
                    size_t smem_bytes, void **args, uint32_t flags, void *stream);
 
-/* Device time (ms) of the kernel of the most recent genesys_launch, from CUDA
- * events recorded immediately before and after it on its stream.  For
- * non-blocking calls the kernel can end before the CPU has processed them;
- * genesys_drain covers the rest. */
+/* Measurement only (no counterpart in the paper).  Device time (ms) of the
+ * kernel of the most recent genesys_launch, from CUDA events recorded
+ * immediately before and after it on its stream.  For non-blocking calls the
+ * kernel can end before the CPU has processed them; genesys_drain covers the
+ * rest. */
 int genesys_last_launch_ms(genesys_ctx *ctx, float *ms);
 
-/* With GENESYS_INIT_NO_THREADS: process ready requests on the calling thread
- * for up to timeout_ns; returns the number of requests processed.  With
- * service threads: waits up to timeout_ns for all published requests to be
- * processed; returns 0 or GENESYS_ETIMEDOUT. */
+/* CPU-side system call processing (Sec. 5) on the caller's thread.  With
+ * GENESYS_INIT_NO_THREADS: process ready requests on the calling thread for up
+ * to timeout_ns; returns the number of requests processed.  With service
+ * threads: waits up to timeout_ns for all published requests to be processed;
+ * returns 0 or GENESYS_ETIMEDOUT. */
 int genesys_service(genesys_ctx *ctx, uint64_t timeout_ns);
 
 /* Sec. 8.3: wait until every request published so far (non-blocking ones
@@ -172,47 +177,53 @@ int genesys_service(genesys_ctx *ctx, uint64_t timeout_ns);
  * have finished (e.g. after a stream synchronize).  0 or GENESYS_ETIMEDOUT. */
 int genesys_drain(genesys_ctx *ctx, uint64_t timeout_ns);
 
-/* Unregister and unmap the regions GPU code released with munmap.  A GPU
- * munmap cannot do this itself: cudaHostUnregister waits until no kernel is
- * running, and the calling kernel is running.  Released regions stay pinned
- * until this call (or genesys_shutdown) and are reused by later GPU mmaps of
- * a size they fit.  Call it when no kernel that makes calls on this context is
- * running. */
+/* GPU mmap/munmap support (Sec. 5, Table 1's memory calls).  Unregister and
+ * unmap the regions GPU code released with munmap.  A GPU munmap cannot do
+ * this itself: cudaHostUnregister waits until no kernel is running, and the
+ * calling kernel is running.  Released regions stay pinned until this call (or
+ * genesys_shutdown) and are reused by later GPU mmaps of a size they fit.
+ * Call it when no kernel that makes calls on this context is running. */
 int genesys_reclaim(genesys_ctx *ctx);
 
-/* Map (mmap(2), anonymous) and register n regions of the given sizes (rounded
- * up to pages) ahead of time, into the pool GPU mmaps are served from.
- * cudaHostRegister can stall while the GPU is busy with other kernels (on a
- * B300 a registration waited tens of seconds behind a stream of kernels), and
- * a kernel waiting for its mmap keeps the GPU busy: reserving before the
- * kernels start keeps registration off the path. */
+/* GPU mmap support (Sec. 5).  Map (mmap(2), anonymous) and register n regions
+ * of the given sizes (rounded up to pages) ahead of time, into the pool GPU
+ * mmaps are served from. cudaHostRegister can stall while the GPU is busy with
+ * other kernels (on a B300 a registration waited tens of seconds behind a
+ * stream of kernels), and a kernel waiting for its mmap keeps the GPU busy:
+ * reserving before the kernels start keeps registration off the path. */
 int genesys_mmap_reserve(genesys_ctx *ctx, const uint64_t *sizes, uint32_t n);
 
-/* Copy the service counters (genesys_stats: requests, Linux calls, batches,
- * bytes, failures, per-call-type time, the service threads' CPU time) into
- * *out (host memory, caller-owned).  GENESYS_EINVAL for NULL arguments. */
+/* Measurement of the service side (Sec. 4.2 coalescing, Sec. 7).  Copy the
+ * service counters (genesys_stats: requests, Linux calls, batches, bytes,
+ * failures, per-call-type time, the service threads' CPU time) into *out (host
+ * memory, caller-owned).  GENESYS_EINVAL for NULL arguments. */
 int genesys_stats_get(genesys_ctx *ctx, genesys_stats *out);
 /* Zero the service counters; the service threads' CPU time counts from
  * here on.  Call between measurements, with no calls in flight. */
 int genesys_stats_reset(genesys_ctx *ctx);
 
-/* Copy the device status words (GENESYS_ST_*) into out; clear them if `clear`. */
+/* Copy the device status words (GENESYS_ST_*: timeouts and the first error,
+ * including those of non-blocking calls nobody waits for, Sec. 4.1) into out;
+ * clear them if `clear`. */
 int genesys_status(genesys_ctx *ctx, int32_t out[GENESYS_ST_WORDS], int clear);
 
-/* Copy up to `cap` per-call latency samples (ns, caller-side invocation
- * latency) into out (host memory); *n_out = samples recorded (may exceed
- * cap); clears the buffer if `clear`. */
+/* Invocation latency as Sec. 7 measures it.  Copy up to `cap` per-call latency
+ * samples (ns, caller-side invocation latency) into out (host memory); *n_out
+ * = samples recorded (may exceed cap); clears the buffer if `clear`. */
 int genesys_latency(genesys_ctx *ctx, uint64_t *out, uint32_t cap, uint32_t *n_out, int clear);
 
-/* Bump-allocate `bytes` (256-byte aligned) from the staging arena: pinned,
- * host-mapped memory whose address is valid on the host and on the GPU, so
- * GPU code can pass it to pread/pwrite/sendto/recvfrom.  NULL if exhausted. */
+/* Buffers GPU calls can name (Sec. 5 relies on shared virtual memory; here
+ * pinned host-mapped memory stands in).  Bump-allocate `bytes` (256-byte
+ * aligned) from the staging arena: pinned, host-mapped memory whose address is
+ * valid on the host and on the GPU, so GPU code can pass it to
+ * pread/pwrite/sendto/recvfrom.  NULL if exhausted. */
 void *genesys_staging(genesys_ctx *ctx, size_t bytes);
 /* Give the whole staging arena back (every earlier genesys_staging address
  * becomes free for reuse).  Only when no kernel or server uses staging. */
 int genesys_staging_reset(genesys_ctx *ctx);
 
-/* Message of the calling thread's last failure. */
+/* Message of the calling thread's last failure (interface plumbing, no
+ * counterpart in the paper). */
 const char *genesys_last_error(void);
 
 /* Per-call trace (the timeline of a call, Sec. 5: publish, CPU pickup, CPU
@@ -221,17 +232,20 @@ const char *genesys_last_error(void);
  * host records by the service thread (CLOCK_MONOTONIC, ns).  A record pair
  * is joined by (slot, seq). */
 /* (genesys_trace_dev and genesys_trace_host are defined in genesys_layout.h) */
-/* Copy out and clear the trace (call it with no kernel running on the
+/* Measurement only (where a call's time goes; no counterpart in the paper).
+ * Copy out and clear the trace (call it with no kernel running on the
  * context): up to dev_cap / host_cap records (the rest is dropped and counted
- * in *n_dev / *n_host, which return the totals recorded).  *host_minus_device_ns
- * (if non-NULL) = host clock - device clock, from a round-trip calibration
- * (the sample with the shortest round trip; error <= half of it). */
+ * in *n_dev / *n_host, which return the totals recorded).
+ * *host_minus_device_ns (if non-NULL) = host clock - device clock, from a
+ * round-trip calibration (the sample with the shortest round trip; error <=
+ * half of it). */
 int genesys_trace_read(genesys_ctx *ctx, genesys_trace_dev *dev, uint32_t dev_cap, uint32_t *n_dev,
                        genesys_trace_host *host, uint32_t host_cap, uint32_t *n_host, int64_t *host_minus_device_ns);
 
-/* Size in bytes of a structure of this interface, so that a binding built
- * against another version of this header can refuse to run instead of
- * misreading memory: which = GENESYS_SIZEOF_*; 0 for an unknown value. */
+/* Interface check (no counterpart in the paper).  Size in bytes of a structure
+ * of this interface, so that a binding built against another version of this
+ * header can refuse to run instead of misreading memory: which =
+ * GENESYS_SIZEOF_*; 0 for an unknown value. */
 #define GENESYS_SIZEOF_CONFIG       0
 #define GENESYS_SIZEOF_STATS        1
 #define GENESYS_SIZEOF_SERVE_CONFIG 2
@@ -242,7 +256,8 @@ int genesys_trace_read(genesys_ctx *ctx, genesys_trace_dev *dev, uint32_t dev_ca
 #define GENESYS_SIZEOF_DEV          7
 uint32_t genesys_sizeof(int which);
 
-/* Failure detection on the host (a watchdog's probe): *stalled_mask gets bit r
+/* Failure detection on the host (no counterpart in the paper; a watchdog's
+ * probe): *stalled_mask gets bit r
  * set for every doorbell ring r (r < 64) that has requests waiting but whose
  * service has finished no batch for stall_ns (a stopped, paused or stuck
  * service thread, or a NO_THREADS context nobody services); *pending (if
@@ -250,19 +265,20 @@ uint32_t genesys_sizeof(int which);
  * enough to call periodically while kernels run. */
 int genesys_service_health(genesys_ctx *ctx, uint64_t stall_ns, uint64_t *stalled_mask, uint64_t *pending);
 
-/* Failure handling on the host: stop the service thread of doorbell ring
- * `ring` (it finishes the batch it holds), leave the ring unserved for
- * pause_ns, then start a new thread that continues from the same ring
- * position.  Requests published meanwhile wait in the ring; a caller whose
- * wait passes device_deadline_ns gives up with -ETIMEDOUT, and its request is
- * still carried out later.  GENESYS_EINVAL without service threads or for a
- * bad ring.  Blocks for pause_ns. */
+/* Failure handling on the host (no counterpart in the paper): stop the service
+ * thread of doorbell ring `ring` (it finishes the batch it holds), leave the
+ * ring unserved for pause_ns, then start a new thread that continues from the
+ * same ring position.  Requests published meanwhile wait in the ring; a caller
+ * whose wait passes device_deadline_ns gives up with -ETIMEDOUT, and its
+ * request is still carried out later.  GENESYS_EINVAL without service threads
+ * or for a bad ring.  Blocks for pause_ns. */
 int genesys_service_restart(genesys_ctx *ctx, uint32_t ring, uint64_t pause_ns);
 
-/* GENESYS_INIT_HOST_ONLY contexts: make one call through the full protocol
- * from a CPU thread standing in for a GPU lane (claim a slot, marshal,
- * publish, ring the doorbell, wait if GENESYS_REQ_BLOCKING is in flags).
- * Safe to call from many threads at once.  *ret receives the result. */
+/* Protocol testing without a GPU (no counterpart in the paper; the steps are
+ * Sec. 5's).  GENESYS_INIT_HOST_ONLY contexts: make one call through the full
+ * protocol from a CPU thread standing in for a GPU lane (claim a slot,
+ * marshal, publish, ring the doorbell, wait if GENESYS_REQ_BLOCKING is in
+ * flags). Safe to call from many threads at once.  *ret receives the result. */
 int genesys_emulate_call(genesys_ctx *ctx, uint32_t nr, const uint64_t args[6], uint32_t flags, int64_t *ret);
 
 /* ------------------------------------------------------------ workloads
@@ -454,18 +470,20 @@ int genesys_kv_start(genesys_ctx *ctx, const uint8_t *keys, const uint16_t *vlen
  * has not left, or its calls did not drain) the server is kept and the call
  * can be repeated; the context cannot be shut down until one succeeds. */
 int genesys_kv_stop(genesys_kv_server *srv, uint64_t timeout_ns, uint64_t *served);
-/* Current value of key k (copied to out, GENESYS_KV_VALUE_MAX bytes room);
- * returns its length. */
+/* C4 (Sec. 7.3).  Current value of key k (copied to out, GENESYS_KV_VALUE_MAX
+ * bytes room); returns its length. */
 int genesys_kv_value(genesys_kv_server *srv, uint32_t k, uint8_t *out);
-/* Open-loop UDP load generator on up to 4 host threads, each with its own
- * socket: request j (reqs + req_off[j], req_off[n] = end) is sent
+/* C4's load generator (Sec. 7.3 measures its network workloads with a client
+ * on the host).  Open-loop UDP load generator on up to 4 host threads, each
+ * with its own socket: request j (reqs + req_off[j], req_off[n] = end) is sent
  * arrival_ns[j] after start to the socket its key maps to, by the thread that
  * owns that socket (so one key's requests leave in order), and its reply comes
- * back to that thread; replies are matched by seq into replies[seq * (8 + VALUE_MAX)],
- * reply_len[seq], latency_ns[seq] (send to receive).  Then sends STOP to every
- * socket.  stats[6]: received, duplicates, malformed, send errors, largest
- * send lateness (ns), first send to last reply (ns).  GENESYS_ETIMEDOUT if
- * replies are still missing timeout_ns after the last arrival. */
+ * back to that thread; replies are matched by seq into replies[seq * (8 +
+ * VALUE_MAX)], reply_len[seq], latency_ns[seq] (send to receive).  Then sends
+ * STOP to every socket.  stats[6]: received, duplicates, malformed, send
+ * errors, largest send lateness (ns), first send to last reply (ns).
+ * GENESYS_ETIMEDOUT if replies are still missing timeout_ns after the last
+ * arrival. */
 int genesys_kv_client(const uint8_t *reqs, const uint64_t *req_off, uint64_t n, const uint64_t *arrival_ns,
                       uint16_t port_base, uint32_t n_sockets, uint64_t timeout_ns, uint8_t *replies,
                       uint32_t *reply_len, uint64_t *latency_ns, uint64_t *stats);
@@ -495,16 +513,17 @@ int genesys_echo_start(genesys_ctx *ctx, uint32_t n_sockets, uint32_t max_packet
  * stats[2] (if non-NULL): datagrams echoed, bytes echoed.  On an error the
  * server is kept and the call can be repeated, as for genesys_kv_stop. */
 int genesys_echo_stop(genesys_echo_server *srv, uint64_t timeout_ns, uint64_t *stats);
-/* Closed-loop UDP echo load generator on n_threads host threads (each with
- * its own socket and the server sockets s = t, t + n_threads, ...): `window`
- * datagrams of packet_bytes (8..GENESYS_ECHO_PACKET_MAX) in flight per server
- * socket (fewer if the replies would not fit in half of the thread's receive
- * buffer), n_packets in total.  A datagram is lane u32, generation u32, then
- * seeded bytes; a reply counts as echoed when it equals the datagram byte for
- * byte.  Ends when every datagram is answered or no reply came for stall_ns
- * (0 = 200 ms); then, if send_stop, sends a GENESYS_ECHO_STOP_BYTES datagram
- * to every server socket.  stats[7]: sent, echoed, bad replies, lost (no
- * reply), first send to last reply (ns), echoed bytes, send errors. */
+/* Fig. 10's client side.  Closed-loop UDP echo load generator on n_threads
+ * host threads (each with its own socket and the server sockets s = t, t +
+ * n_threads, ...): `window` datagrams of packet_bytes
+ * (8..GENESYS_ECHO_PACKET_MAX) in flight per server socket (fewer if the
+ * replies would not fit in half of the thread's receive buffer), n_packets in
+ * total.  A datagram is lane u32, generation u32, then seeded bytes; a reply
+ * counts as echoed when it equals the datagram byte for byte.  Ends when every
+ * datagram is answered or no reply came for stall_ns (0 = 200 ms); then, if
+ * send_stop, sends a GENESYS_ECHO_STOP_BYTES datagram to every server socket.
+ * stats[7]: sent, echoed, bad replies, lost (no reply), first send to last
+ * reply (ns), echoed bytes, send errors. */
 int genesys_echo_client(uint16_t port_base, uint32_t n_sockets, uint32_t packet_bytes, uint64_t n_packets,
                         uint32_t window, uint32_t n_threads, uint64_t seed, uint64_t stall_ns, uint32_t send_stop,
                         uint64_t *stats);
