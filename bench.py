@@ -409,7 +409,7 @@ def tune_step(args, local, rank):
         finally:
             rig.close()
 
-    best, table = tuner.tune(key, autotune.grid(service_threads=(1, 2, 4), coalesce_max=(64, 256),
+    best, table = tuner.tune(key, autotune.grid(service_threads=(1, 2, 4), coalesce_max=(64, 256, 1024),
                                                 poll_max_ns=(2048,), n_slots=(0, 32768)), run, repeats=2)
     return best, table
 
