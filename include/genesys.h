@@ -541,6 +541,15 @@ int genesys_echo_client(uint16_t port_base, uint32_t n_sockets, uint32_t packet_
  * wrote fewer bytes than asked makes it return GENESYS_EINVAL. */
 int genesys_service_probe(genesys_ctx *ctx, int fd, const void *payload, uint32_t bytes_per_call, uint64_t n_calls,
                           uint64_t *elapsed_ns);
+/* The same probe with the doorbells rung out of file order, as GPU
+ * work-items ring them: the calls are cut into runs of `run` consecutive ones
+ * (32: a warp's), and run k is rung in pass k % stride of each round, so
+ * neighbouring runs land a 1/stride of the round apart and rarely meet in one
+ * batch (stride 8: the eight warps of a 256-thread block).  run = stride = 1
+ * is genesys_service_probe.  GENESYS_EINVAL for run or stride 0, otherwise
+ * as genesys_service_probe. */
+int genesys_service_probe_order(genesys_ctx *ctx, int fd, const void *payload, uint32_t bytes_per_call,
+                                uint64_t n_calls, uint32_t run, uint32_t stride, uint64_t *elapsed_ns);
 
 /* C6, block permutation (Sec. 6, Fig. 6): n_blocks thread blocks of 1024
  * threads each take one 8 KiB block of input_dev (device), permute it `iters`

@@ -48,7 +48,7 @@ EXPORTS = [
     "genesys_reclaim", "genesys_mmap_reserve", "genesys_kv_start", "genesys_kv_stop", "genesys_kv_value",
     "genesys_kv_client", "genesys_c6_permute", "genesys_gpu_call", "genesys_echo_start", "genesys_echo_stop",
     "genesys_echo_client", "genesys_service_probe", "genesys_link_pingpong", "genesys_service_restart",
-    "genesys_trace_read", "genesys_sizeof", "genesys_service_health",
+    "genesys_trace_read", "genesys_sizeof", "genesys_service_health", "genesys_service_probe_order",
 ]
 
 
@@ -162,6 +162,8 @@ def lib() -> ctypes.CDLL:
                                               ctypes.POINTER(i64)]),
         "genesys_link_pingpong": (ctypes.c_int, [ctypes.c_int, u32, u64, ctypes.POINTER(u64)]),
         "genesys_service_probe": (ctypes.c_int, [vp, ctypes.c_int, vp, u32, u64, ctypes.POINTER(u64)]),
+        "genesys_service_probe_order": (ctypes.c_int, [vp, ctypes.c_int, vp, u32, u64, u32, u32,
+                                                       ctypes.POINTER(u64)]),
         "genesys_echo_start": (ctypes.c_int, [vp, u32, u32, u32, u32, u32, ctypes.c_uint16, u64, ctypes.POINTER(vp)]),
         "genesys_echo_stop": (ctypes.c_int, [vp, u64, vp]),
         "genesys_echo_client": (ctypes.c_int, [ctypes.c_uint16, u32, u32, u64, u32, u32, u64, u64, u32, vp]),
@@ -347,12 +349,15 @@ class Context:
         pause_ns, start a new one (genesys_service_restart)."""
         _check(lib().genesys_service_restart(self.handle, ring, pause_ns), "genesys_service_restart")
 
-    def service_probe(self, fd: int, payload: int, bytes_per_call: int, n_calls: int) -> float:
+    def service_probe(self, fd: int, payload: int, bytes_per_call: int, n_calls: int, run: int = 1,
+                      stride: int = 1) -> float:
         """Service-thread ceiling for work-item pwrites (genesys_service_probe):
-        the host publishes the requests itself; returns calls per second."""
+        the host publishes the requests itself; returns calls per second.
+        run/stride > 1 ring the doorbells out of file order, as GPU warps do
+        (genesys_service_probe_order)."""
         ns = ctypes.c_uint64()
-        _check(lib().genesys_service_probe(self.handle, fd, payload, bytes_per_call, n_calls, ctypes.byref(ns)),
-               "genesys_service_probe")
+        _check(lib().genesys_service_probe_order(self.handle, fd, payload, bytes_per_call, n_calls, run, stride,
+                                                 ctypes.byref(ns)), "genesys_service_probe")
         return n_calls / (ns.value * 1e-9) if ns.value else float("inf")
 
     def status(self, clear: bool = True) -> list:

@@ -1280,8 +1280,14 @@ int genesys_staging_reset(genesys_ctx *c) {
 // usable by kernels.  No kernel may be running on the context meanwhile.
 int genesys_service_probe(genesys_ctx *c, int fd, const void *payload, uint32_t bytes_per_call, uint64_t n_calls,
                           uint64_t *elapsed_ns) {
+  return genesys_service_probe_order(c, fd, payload, bytes_per_call, n_calls, 1, 1, elapsed_ns);
+}
+
+int genesys_service_probe_order(genesys_ctx *c, int fd, const void *payload, uint32_t bytes_per_call,
+                                uint64_t n_calls, uint32_t run, uint32_t stride, uint64_t *elapsed_ns) {
   return genesys_guard("genesys_service_probe", [&]() -> int {
     if (!c || !payload || !elapsed_ns || bytes_per_call == 0) return fail(GENESYS_EINVAL, "NULL argument");
+    if (run == 0 || stride == 0) return fail(GENESYS_EINVAL, "service probe: run and stride must be >= 1");
     if (c->threads.empty()) return fail(GENESYS_EINVAL, "genesys_service_probe needs service threads");
     const uint32_t S = c->cfg.n_slots, R = c->cfg.n_service_threads;
     std::vector<uint32_t> seq(S), kd(S), owner(S), tails_raw((size_t)R * 32);
@@ -1319,12 +1325,17 @@ int genesys_service_probe(genesys_ctx *c, int fd, const void *payload, uint32_t 
                          __ATOMIC_RELEASE);
       }
       const uint64_t t0 = genesys_mono_ns();
-      for (uint32_t s = 0; s < m; ++s) {
-        const uint32_t r = genesys_ring_of(s, R);
-        const uint32_t pos = tails_raw[(size_t)r * 32]++;
-        __atomic_store_n(&c->rings[(size_t)r * c->ring_cap + (pos & (c->ring_cap - 1))], GENESYS_RING_ENTRY(pos, s),
-                         __ATOMIC_RELEASE);
-      }
+      // doorbells: runs of `run` consecutive slots; run k is rung in pass
+      // k % stride, so neighbouring runs are a 1/stride of the round apart
+      const uint32_t n_runs = (m + run - 1) / run;
+      for (uint32_t pass = 0; pass < stride; ++pass)
+        for (uint32_t k = pass; k < n_runs; k += stride)
+          for (uint32_t s = k * run; s < m && s < (k + 1) * run; ++s) {
+            const uint32_t r = genesys_ring_of(s, R);
+            const uint32_t pos = tails_raw[(size_t)r * 32]++;
+            __atomic_store_n(&c->rings[(size_t)r * c->ring_cap + (pos & (c->ring_cap - 1))],
+                             GENESYS_RING_ENTRY(pos, s), __ATOMIC_RELEASE);
+          }
       for (uint32_t s = 0; s < m; ++s) {
         uint64_t d;
         while ((uint32_t)((d = __atomic_load_n(&c->done[s], __ATOMIC_ACQUIRE)) >> 32) != seq[s]) {

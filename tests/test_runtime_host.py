@@ -681,3 +681,28 @@ def test_service_threads_that_cannot_start_are_an_error_not_an_abort():
         pytest.skip("the address-space limit did not stop the threads here")
     assert f"code {G.ENOMEM}" in out, r.stdout
     assert any(ln.startswith("after ") and int(ln.split()[1]) > 0 for ln in out), r.stdout
+
+
+def test_service_probe_in_warp_interleaved_order(tmp_path):
+    """genesys_service_probe_order: with the doorbells of 32-call runs rung
+    eight runs apart, every call still lands (the file is the payload), and a
+    batch no longer holds a run's neighbours, so the merged calls cover one
+    run each - as with GPU work-items, whose batches merge about a warp."""
+    n = 1 << 16
+    fd = os.open(str(tmp_path / "o.bin"), os.O_CREAT | os.O_TRUNC | os.O_RDWR, 0o600)
+    try:
+        with _ctx(service_threads=2, coalesce_max=64, n_slots=65536, staging_bytes=n * 64 + 4096) as c:
+            p = c.staging(n * 64)
+            want = np.random.default_rng(11).integers(0, 256, n * 64, dtype=np.uint8)
+            c.host_view(p, n * 64)[:] = want
+            c.stats_reset()
+            assert c.service_probe(fd, p, 64, n, run=32, stride=8) > 0
+            st = c.stats()
+            with pytest.raises(G.GenesysError):
+                c.service_probe(fd, p, 64, n, run=0, stride=8)
+        got = np.fromfile(str(tmp_path / "o.bin"), np.uint8)
+    finally:
+        os.close(fd)
+    assert np.array_equal(got, want)
+    assert st["requests"] == n and st["failed"] == 0
+    assert st["requests"] / st["os_calls"] <= 32.0
