@@ -53,3 +53,28 @@ def test_clock_record_reasons_and_median(tmp_path):
     assert bench.ClockSampler.summary(s)["reasons"] == ["hw_slowdown"]
     s.p = None
     assert bench.ClockSampler.summary(s)["sm_mhz"] is None
+
+
+def test_traffic_figure_is_scaled_and_dropped_when_the_source_changes(tmp_path, monkeypatch):
+    """The roofline's traffic: the committed per-thread figure times the
+    threads of a launch, and no figure at all once the kernel's source (the
+    device protocol headers or its section of workloads.cu) differs from the
+    one the capture was taken on."""
+    import shutil
+    root = bench.ROOT
+    for rel in ("include/genesys_device.cuh", "include/genesys_layout.h",
+                "paper_1705_06965_b300/csrc/workloads.cu"):
+        os.makedirs(tmp_path / os.path.dirname(rel), exist_ok=True)
+        shutil.copy(os.path.join(root, rel), tmp_path / rel)
+    kern = "c2_pwrite_kernel<work-item,strong,blocking>"
+    h = bench.kernel_src_hash(kern)
+    os.makedirs(tmp_path / "profiles")
+    (tmp_path / "profiles" / "traffic.txt").write_text(f"# comment\n{kern} {h} 243.5 thread x\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.kernel_src_hash(kern) == h
+    assert bench.load_traffic(kern, 1 << 20) == round(243.5 * (1 << 20))
+    assert bench.load_traffic("c2_pwrite_kernel<warp,strong,blocking>", 1 << 20) is None
+    with open(tmp_path / "include" / "genesys_device.cuh", "a") as f:
+        f.write("\n// changed\n")
+    assert bench.kernel_src_hash(kern) != h
+    assert bench.load_traffic(kern, 1 << 20) is None
