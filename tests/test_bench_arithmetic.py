@@ -78,3 +78,18 @@ def test_traffic_figure_is_scaled_and_dropped_when_the_source_changes(tmp_path, 
         f.write("\n// changed\n")
     assert bench.kernel_src_hash(kern) != h
     assert bench.load_traffic(kern, 1 << 20) is None
+
+
+def test_cpu_baseline_leg_compares_the_gpu_histogram_with_the_oracle():
+    """The GPU arm hands its C1 histogram to the CPU-baseline leg, which
+    reports whether it equals the oracle's for the same seeded file; the
+    arm's own check (forms agree, every byte counted) holds for the oracle's
+    histogram too."""
+    import numpy as np
+    want = oracle.c1_histogram(workloads.c1_file(None, bench.C1_BYTES, seed=workloads.SEED_C1), bench.C1_CHUNK)
+    assert int(want.sum(dtype=np.uint64)) == bench.C1_BYTES
+    out = bench.cpu_baseline_sample(budget_s=0.5, c1_hist=want.copy())
+    assert out["kind"] == "oracle" and out["c1_histogram_equals_oracle"] is True
+    bad = want.copy()
+    bad[7] += 1
+    assert bench.cpu_baseline_sample(budget_s=0.5, c1_hist=bad)["c1_histogram_equals_oracle"] is False
