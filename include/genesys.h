@@ -83,7 +83,7 @@ typedef struct genesys_config {
   uint32_t reserved0;
 } genesys_config;
 
-typedef struct genesys_stats {
+typedef struct genesys_stats {  /* genesys_stats_t */
   uint64_t requests;           /* GPU requests retired by the service threads          */
   uint64_t os_calls;           /* Linux calls made for them (fewer when merged)        */
   uint64_t failed;             /* requests whose result was negative                   */
@@ -108,7 +108,7 @@ typedef struct genesys_stats {
   uint64_t order_ns;           /* ... ordering a batch so that file neighbours merge   */
   uint64_t complete_ns;        /* ... writing results, completion words and the rings'
                                   finished counts (the Linux calls are op_ns)           */
-} genesys_stats;
+} genesys_stats_t;
 
 typedef struct genesys_ctx genesys_ctx;
 
@@ -145,6 +145,8 @@ int genesys_device_view(genesys_ctx *ctx, genesys_dev *out);
 #define GENESYS_LAUNCH_NONBLOCKING 0x20u  /* the kernel's calls are non-blocking       */
 #define GENESYS_LAUNCH_COOPERATIVE 0x100u /* force a cooperative launch                */
 #define GENESYS_LAUNCH_SYNC        0x200u /* wait for the kernel, then drain its calls */
+#define GENESYS_LAUNCH_GRAPH       0x400u /* launch through a CUDA graph built once per
+                                             launch shape and relaunched               */
 
 /* Launch a kernel that makes GPU system calls.  `kernel` is the kernel's host
  * stub (a __global__ function pointer from a library linked against the shared
@@ -154,7 +156,18 @@ int genesys_device_view(genesys_ctx *ctx, genesys_dev *out);
  *   - work-item grain with relaxed ordering -> GENESYS_EINVAL (always strong);
  *   - kernel grain with strong ordering -> cooperative launch; a grid larger
  *     than the resident set -> GENESYS_EINVAL (this is the deadlock of Sec. 4.1).
- * The per-launch kernel-grain state is reset on `stream` before the kernel. */
+ * The kernel-grain call sites are reset on `stream` before every kernel
+ * (whatever grain `flags` declares): a relaxed kernel-grain site serves one
+ * call per block per launch (genesys_device.cuh, call_at).
+ * GENESYS_LAUNCH_GRAPH (no counterpart in the paper, which launches kernels
+ * directly; it cuts the launch cost of kernels relaunched with new
+ * arguments): the first launch of a (kernel, grid, block, smem_bytes,
+ * cooperative) shape builds a graph of that one kernel node and instantiates
+ * it; later launches of the shape set the node's arguments to `args` on the
+ * instantiated graph and launch it (cudaGraphExecKernelNodeSetParams +
+ * cudaGraphLaunch), so the kernel is not set up again.  The graphs belong to
+ * the context (freed by genesys_shutdown); queued launches keep the arguments
+ * they were given.  Set-up or launch failures are GENESYS_ECUDA. */
 int genesys_launch(genesys_ctx *ctx, const void *kernel, const uint32_t grid[3], const uint32_t block[3],
                    size_t smem_bytes, void **args, uint32_t flags, void *stream);
 
@@ -197,7 +210,13 @@ int genesys_mmap_reserve(genesys_ctx *ctx, const uint64_t *sizes, uint32_t n);
  * service counters (genesys_stats: requests, Linux calls, batches, bytes,
  * failures, per-call-type time, the service threads' CPU time) into *out (host
  * memory, caller-owned).  GENESYS_EINVAL for NULL arguments. */
-int genesys_stats_get(genesys_ctx *ctx, genesys_stats *out);
+int genesys_stats_get(genesys_ctx *ctx, genesys_stats_t *out);
+/* The same as genesys_stats_get, under the boundary's own name (Sec. 4.2,
+ * Sec. 7: the service counters). */
+int genesys_stats(genesys_ctx *ctx, genesys_stats_t *out);
+/* Measurement only (no counterpart in the paper): launches made through
+ * GENESYS_LAUNCH_GRAPH on this context so far, into *out. */
+int genesys_graph_launches(genesys_ctx *ctx, uint64_t *out);
 /* Zero the service counters; the service threads' CPU time counts from
  * here on.  Call between measurements, with no calls in flight. */
 int genesys_stats_reset(genesys_ctx *ctx);
@@ -273,6 +292,15 @@ int genesys_service_health(genesys_ctx *ctx, uint64_t stall_ns, uint64_t *stalle
  * request is still carried out later.  GENESYS_EINVAL without service threads
  * or for a bad ring.  Blocks for pause_ns. */
 int genesys_service_restart(genesys_ctx *ctx, uint32_t ring, uint64_t pause_ns);
+
+/* Failure injection on the host for tests (no counterpart in the paper).
+ * Checked builds only (GENESYS_DEVICE_CHECKS, libgenesys_checked.so): from now
+ * on every pread the service threads make for GPU requests asks for at most
+ * cap_bytes (0 = no cap), merged or not, so that GPU callers receive short
+ * reads in the middle of a file, which Linux allows at any time (Sec. 5: the
+ * CPU carries out the call and returns its result).  Callers that need whole
+ * chunks go on reading (genesys::pread_full).  Other builds: GENESYS_EINVAL. */
+int genesys_check_pread_cap(genesys_ctx *ctx, uint64_t cap_bytes);
 
 /* Protocol testing without a GPU (no counterpart in the paper; the steps are
  * Sec. 5's).  GENESYS_INIT_HOST_ONLY contexts: make one call through the full
@@ -357,8 +385,9 @@ int genesys_c3_wordcount(genesys_ctx *ctx, const int32_t *fds, const uint64_t *f
  *     n bytes takes ceil(n / chunk) of them; more returns GENESYS_EINVAL with
  *     a message saying so.
  *   - Set-up: the first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current, and keeps it; make that
- *     first call before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current, keeps it, and makes the
+ *     caller's current device current again; make that first call before any
+ *     stream capture.
  *   - Sharing: every call uses the same array, which keeps the last call's
  *     contents (each call rewrites the part it reads, queue head included).
  *     Calls are serialised on the host and each waits for its kernel, but

@@ -185,9 +185,9 @@ __device__ __forceinline__ uint32_t ring_of(const genesys_dev &g, uint32_t slot)
  * One thread.  Try to claim a slot (device-side lock in HBM, never an RMW on
  * host memory): up to 32 slots from `hint` on.  A claimed slot whose previous
  * request the CPU has not finished yet (a non-blocking call may still be in
- * flight: Fig. 4, "if the slot is not free, system call invocation is
- * delayed") is waited for, bounded.  Returns 1 with *slot_out set, 0 if every
- * slot tried is taken, or -ETIMEDOUT. */
+ * flight) is waited for, bounded: a slot still held by an unfinished request
+ * delays the new call (Sec. 5, Fig. 4).  Returns 1 with *slot_out set, 0 if
+ * every slot tried is taken, or -ETIMEDOUT. */
 __device__ __forceinline__ int64_t slot_try_claim(const genesys_dev &g, uint32_t hint, uint32_t *slot_out,
                                                   uint64_t t0) {
   uint32_t s = hint % g.n_slots;
@@ -236,8 +236,12 @@ __device__ __forceinline__ int64_t slot_claim(const genesys_dev &g, uint32_t hin
   }
 }
 
-/* Marshal the request into the slot with 16-byte stores; returns its sequence.
- * The caller fences (system scope) and rings the doorbell afterwards. */
+/* Marshal the request into the slot with four 16-byte stores that cover its
+ * whole 64-byte line (the arguments, then the request word beside a zeroed
+ * result word), so the line crosses the host link as full writes rather than
+ * a partial one; returns its sequence.  The result word is the CPU's only
+ * while it serves the slot's previous request, which the claim has waited
+ * for.  The caller fences (system scope) and rings the doorbell afterwards. */
 __device__ __forceinline__ uint32_t slot_fill(const genesys_dev &g, uint32_t s, uint32_t nr, uint32_t flags,
                                               uint64_t a0, uint64_t a1, uint64_t a2, uint64_t a3, uint64_t a4,
                                               uint64_t a5) {
@@ -248,45 +252,47 @@ __device__ __forceinline__ uint32_t slot_fill(const genesys_dev &g, uint32_t s, 
   st_v2(&sl->args[2], a2, a3);
   st_v2(&sl->args[4], a4, a5);
   const uint64_t req = ((uint64_t)sq << 32) | ((uint64_t)(nr & 0xFFFFu) << 16) | (flags & 0xFFFFu);
-  asm volatile("st.global.u64 [%0], %1;" ::"l"(&sl->req), "l"(req) : "memory");
+  st_v2(&sl->req, req, 0);
   return sq;
 }
+
+/* Doorbells.  The service thread takes a ring's entries in position order
+ * and stops at the first one not yet written, so the time between taking a
+ * position and writing its entry holds up every later entry of the ring.  The
+ * system-scope fence that orders the slot stores before the entry (it waits
+ * until the host link has acknowledged them, microseconds) therefore comes
+ * first; the position is taken after it and the entry written at once.  A
+ * fence followed by a relaxed system-scope store is a release pattern. */
 
 /* Doorbell for one published slot (one thread); returns its ring position. */
 __device__ __forceinline__ uint32_t ring_one(const genesys_dev &g, uint32_t s) {
   const uint32_t r = ring_of(g, s);
   if (!dcheck(g, r < g.n_rings && s < g.n_slots)) return 0;
+  fence_acq_rel_sys();
   const uint32_t pos = atomicAdd(&g.ring_tail[r * 32u], 1u);
-  st_release_sys(g.rings + (size_t)r * (g.ring_mask + 1u) + (pos & g.ring_mask), GENESYS_RING_ENTRY(pos, s));
+  st_relaxed_sys(g.rings + (size_t)r * (g.ring_mask + 1u) + (pos & g.ring_mask), GENESYS_RING_ENTRY(pos, s));
   return pos;
 }
 
-/* Doorbell for the lanes of `mask` that each filled slot `s`.  Lanes going to
- * the same ring (grouped with __match_any_sync) take consecutive positions with
- * one atomic; after a warp barrier the group's first lane makes one system-scope
- * release fence and writes all of the group's entries, so every lane's slot
- * stores happen before its entry becomes visible, at one fence per group
- * instead of one per lane.  Returns the calling lane's ring position. */
+/* Doorbell for the lanes of `mask` that each filled slot `s`.  Every lane
+ * fences its own slot stores (one warp-wide instruction); the lanes going to
+ * the same ring (grouped with __match_any_sync) then take consecutive
+ * positions with one atomic, and each lane writes its own entry, so a warp's
+ * entries leave as one contiguous store instead of one store per lane.
+ * Returns the calling lane's ring position (lane order within the group). */
 __device__ __forceinline__ uint32_t ring_warp(const genesys_dev &g, uint32_t mask, uint32_t s) {
   const uint32_t r = ring_of(g, s);
   dcheck(g, r < g.n_rings && s < g.n_slots);
+  fence_acq_rel_sys();
   const uint32_t peers = __match_any_sync(mask, r);
   const uint32_t lane = lane_id();
   const uint32_t leader = __ffs(peers) - 1;
   uint32_t base = 0;
   if (lane == leader) base = atomicAdd(&g.ring_tail[r * 32u], (uint32_t)__popc(peers));
   base = __shfl_sync(peers, base, leader);
-  __syncwarp(peers);
-  if (lane == leader) fence_acq_rel_sys();
-  uint64_t *ring = g.rings + (size_t)r * (g.ring_mask + 1u);
-  uint32_t rem = peers;
-  for (uint32_t k = 0; rem; ++k) {
-    const uint32_t j = __ffs(rem) - 1;
-    rem &= rem - 1;
-    const uint32_t sj = __shfl_sync(peers, s, j);
-    if (lane == leader) st_relaxed_sys(ring + ((base + k) & g.ring_mask), GENESYS_RING_ENTRY(base + k, sj));
-  }
-  return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));  // entries are written in lane order
+  const uint32_t pos = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+  st_relaxed_sys(g.rings + (size_t)r * (g.ring_mask + 1u) + (pos & g.ring_mask), GENESYS_RING_ENTRY(pos, s));
+  return pos;
 }
 
 /* Wait until the CPU finished request `sq` of slot `s`; returns its result.
@@ -467,6 +473,14 @@ __device__ __forceinline__ bool is_block_leader() {
   return threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0;
 }
 
+/* A relaxed kernel-grain site reached more often than the grid has blocks
+ * in one launch (see call_at): recorded as a bad argument, -EINVAL. */
+__device__ __forceinline__ int64_t site_reused(const genesys_dev &g) {
+  atomicAdd(reinterpret_cast<int *>(&g.status[GENESYS_ST_BAD_ARGS]), 1);
+  atomicCAS(reinterpret_cast<int *>(&g.status[GENESYS_ST_FIRST_ERROR]), 0, -22);
+  return -22;
+}
+
 /* ------------------------------------------------------------- the call */
 
 template <int G, int O, int B, int R = ROLE_AUTO>
@@ -539,7 +553,15 @@ __device__ __forceinline__ int64_t call_at(const genesys_dev &g, uint32_t site, 
     return ret;
   }
 
-  /* KERNEL grain: one caller for the whole grid. */
+  /* KERNEL grain: one caller for the whole grid.  Strongly ordered calls
+   * may be made at one site any number of times (grid barriers separate
+   * them).  A relaxed call site serves one call per block per launch: its
+   * arrival counters are reset before each launch (genesys_launch), and
+   * nothing tells a block's second call at a site from another block's
+   * first.  A site reached more often than the grid has blocks has been
+   * reused: the extra arrivals make no call, return -EINVAL and record it
+   * (status word GENESYS_ST_BAD_ARGS), so the launch reports the misuse;
+   * give each relaxed kernel-grain call of a kernel its own site (call_at). */
   genesys_ksite *ks = g.ksite + (site % GENESYS_KSITES);
   const uint32_t nblocks = gridDim.x * gridDim.y * gridDim.z;
   __shared__ int64_t kret_s;
@@ -564,6 +586,8 @@ __device__ __forceinline__ int64_t call_at(const genesys_dev &g, uint32_t site, 
       if (arrived == nblocks - 1) {
         __threadfence_system();
         r = single_call(g, nr, flags, B == BLOCKING, a0, a1, a2, a3, a4, a5);
+      } else if (arrived >= nblocks) {
+        r = site_reused(g);
       }
     }
     return r;
@@ -572,11 +596,14 @@ __device__ __forceinline__ int64_t call_at(const genesys_dev &g, uint32_t site, 
    * result (the caller is resident by construction, so they cannot deadlock) */
   if (is_block_leader()) {
     int64_t r;
-    if (atomicAdd(&ks->ticket, 1u) == 0u) {
+    const uint32_t ticket = atomicAdd(&ks->ticket, 1u);
+    if (ticket == 0u) {
       r = single_call(g, nr, flags, B == BLOCKING, a0, a1, a2, a3, a4, a5);
       ks->ret = r;
       __threadfence();
       st_release_gpu(&ks->flag, 1u);
+    } else if (ticket >= nblocks) {
+      r = site_reused(g);
     } else {
       const uint64_t t0 = now_ns();
       uint32_t ns = 64;
@@ -650,6 +677,28 @@ template <int G, int O, int B, int R = ROLE_AUTO>
 __device__ __forceinline__ int64_t call(const genesys_dev &g, uint32_t nr, uint64_t a0 = 0, uint64_t a1 = 0,
                                         uint64_t a2 = 0, uint64_t a3 = 0, uint64_t a4 = 0, uint64_t a5 = 0) {
   return call_at<G, O, B, R>(g, 0u, nr, a0, a1, a2, a3, a4, a5);
+}
+
+/* pread of `len` bytes at `off` into `buf` that goes on after a short read,
+ * as a reader's loop does: a pread may return fewer bytes than asked before
+ * the end of the file (Linux allows it; the file system, a signal or the
+ * host's service can cause it), so the group calls again for the rest until
+ * it has `len` bytes or a read returns 0 (end of file).  Blocking; the group
+ * and ordering of call<G, O, BLOCKING>, whose result every thread of the
+ * group receives, so the loop is uniform across the group.  Returns the bytes
+ * read, or the first -errno. */
+template <int G, int O, int R = ROLE_AUTO>
+__device__ __forceinline__ int64_t pread_full(const genesys_dev &g, uint64_t fd, uint8_t *buf, uint64_t len,
+                                              uint64_t off) {
+  static_assert(G == WARP || G == GROUP, "pread_full: warp or work-group grain (the result is broadcast)");
+  uint64_t got = 0;
+  while (got < len) {
+    const int64_t r = call<G, O, BLOCKING, R>(g, SYS_pread64, fd, (uint64_t)(buf + got), len - got, off + got);
+    if (r < 0) return r;
+    if (r == 0) break;
+    got += (uint64_t)r < len - got ? (uint64_t)r : len - got;
+  }
+  return (int64_t)got;
 }
 
 }  // namespace genesys

@@ -10,9 +10,12 @@
  * Differences from the paper's layout, forced by a discrete GPU behind PCIe
  * without host-native atomics (device RMW on host memory is not atomic with
  * respect to the CPU):
- *   - every word has exactly one writer.  The request word and arguments are
- *     written only by the GPU, the completion word only by the CPU, so no
- *     read-modify-write on host memory is ever needed;
+ *   - every word has one writer at a time.  The request word and arguments
+ *     are written only by the GPU, the completion word only by the CPU; the
+ *     slot's result word is the CPU's while it serves a request and the GPU's
+ *     (it zeroes it with the rest of the line) once the request has completed
+ *     and the slot is claimed again.  No read-modify-write on host memory is
+ *     ever needed;
  *   - the slot state of Fig. 4 is carried by sequence numbers instead of an
  *     atomically updated state field: a slot is FREE when its completion
  *     sequence equals its request sequence, READY/PROCESSING while the request
@@ -37,7 +40,9 @@ extern "C" {
 
 #define GENESYS_SLOT_BYTES 64u
 
-/* One request slot, written by the GPU only (Sec. 5, Fig. 3). */
+/* One request slot (Sec. 5, Fig. 3), one 64-byte line.  The GPU writes the
+ * whole line when it fills the slot (the result word as 0), so the line
+ * crosses the host link as full writes. */
 typedef struct genesys_slot {
   uint64_t args[6];   /* Linux passes at most six arguments; 16-byte aligned
                          so the GPU writes them with three vector stores    */
@@ -48,6 +53,9 @@ typedef struct genesys_slot {
   uint64_t ret;       /* full 64-bit return value, written by the CPU when it
                          does not fit in the completion word (see below)     */
 } genesys_slot;
+#ifdef __cplusplus
+static_assert(sizeof(genesys_slot) == GENESYS_SLOT_BYTES, "a slot is one 64-byte line");
+#endif
 
 /* Completion word, written by the CPU only:
  *   bits 63..32: sequence number of the last finished request of the slot

@@ -39,4 +39,19 @@ __device__ __forceinline__ int64_t genesys_syscall(uint32_t nr, uint64_t a0 = 0,
   return genesys::call<G, O, B>(genesys_bound_dev, nr, a0, a1, a2, a3, a4, a5);
 }
 
+/* The same call at kernel-grain site `site` (0 .. GENESYS_KSITES - 1; the
+ * form above uses site 0).  A relaxed kernel-grain site serves one call per
+ * block per launch (genesys_launch resets the sites before each launch): a
+ * kernel that makes several relaxed kernel-grain calls gives each its own
+ * site.  A site reused within a launch makes no further calls: the extra
+ * arrivals return -EINVAL and the launch's status words record it.  Strongly
+ * ordered kernel-grain calls may share a site. */
+template <int G, int O, int B>
+__device__ __forceinline__ int64_t genesys_syscall_at(uint32_t site, uint32_t nr, uint64_t a0 = 0, uint64_t a1 = 0,
+                                                      uint64_t a2 = 0, uint64_t a3 = 0, uint64_t a4 = 0,
+                                                      uint64_t a5 = 0) {
+  static_assert(!(G == genesys::ITEM && O == genesys::RELAXED), "work-item calls are strongly ordered (Sec. 4.1)");
+  return genesys::call_at<G, O, B>(genesys_bound_dev, site, nr, a0, a1, a2, a3, a4, a5);
+}
+
 #endif

@@ -49,6 +49,7 @@ EXPORTS = [
     "genesys_kv_client", "genesys_c6_permute", "genesys_gpu_call", "genesys_echo_start", "genesys_echo_stop",
     "genesys_echo_client", "genesys_service_probe", "genesys_link_pingpong", "genesys_service_restart",
     "genesys_trace_read", "genesys_sizeof", "genesys_service_health", "genesys_service_probe_order",
+    "genesys_stats", "genesys_graph_launches", "genesys_check_pread_cap",
 ]
 
 
@@ -129,6 +130,9 @@ def lib() -> ctypes.CDLL:
         "genesys_service": (ctypes.c_int, [vp, u64]),
         "genesys_drain": (ctypes.c_int, [vp, u64]),
         "genesys_stats_get": (ctypes.c_int, [vp, ctypes.POINTER(Stats)]),
+        "genesys_stats": (ctypes.c_int, [vp, ctypes.POINTER(Stats)]),
+        "genesys_graph_launches": (ctypes.c_int, [vp, ctypes.POINTER(u64)]),
+        "genesys_check_pread_cap": (ctypes.c_int, [vp, u64]),
         "genesys_stats_reset": (ctypes.c_int, [vp]),
         "genesys_status": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.c_int]),
         "genesys_latency": (ctypes.c_int, [vp, ctypes.POINTER(u64), u32, ctypes.POINTER(u32), ctypes.c_int]),
@@ -312,8 +316,20 @@ class Context:
 
     def stats(self) -> dict:
         s = Stats()
-        _check(lib().genesys_stats_get(self.handle, ctypes.byref(s)), "genesys_stats_get")
+        _check(lib().genesys_stats(self.handle, ctypes.byref(s)), "genesys_stats")
         return s.as_dict()
+
+    def graph_launches(self) -> int:
+        """Launches made through GENESYS_LAUNCH_GRAPH on this context."""
+        n = ctypes.c_uint64()
+        _check(lib().genesys_graph_launches(self.handle, ctypes.byref(n)), "genesys_graph_launches")
+        return int(n.value)
+
+    def pread_cap(self, cap_bytes: int) -> None:
+        """Checked library only (GENESYS_LIBRARY=checked): every pread the
+        service threads make asks for at most cap_bytes (0 = no cap), so GPU
+        callers meet short reads mid-file (genesys_check_pread_cap)."""
+        _check(lib().genesys_check_pread_cap(self.handle, int(cap_bytes)), "genesys_check_pread_cap")
 
     def reclaim(self) -> None:
         """Unpin and unmap regions GPU code released with munmap (call when no

@@ -36,6 +36,7 @@
 #include <string>
 #include <thread>
 #include <map>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -201,6 +202,30 @@ struct genesys_ctx {
   std::vector<uint32_t> last_seq;
   std::atomic<uint64_t> protocol_errors{0};
   uint64_t created_ns = 0;
+  // checked builds: every pread made for GPU requests asks for at most this
+  // many bytes (0 = no cap), so that callers meet short reads mid-file
+  uint64_t pread_cap = 0;
+
+  // GENESYS_LAUNCH_GRAPH: one single-kernel graph per launch shape, relaunched
+  // with each call's arguments
+  struct GraphKey {
+    const void *kernel;
+    uint32_t grid[3], block[3];
+    size_t smem;
+    bool coop;
+    bool operator<(const GraphKey &o) const {
+      return std::tie(kernel, grid[0], grid[1], grid[2], block[0], block[1], block[2], smem, coop) <
+             std::tie(o.kernel, o.grid[0], o.grid[1], o.grid[2], o.block[0], o.block[1], o.block[2], o.smem, o.coop);
+    }
+  };
+  struct GraphExec {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t node = nullptr;
+  };
+  std::mutex graph_mu;
+  std::map<GraphKey, GraphExec> graphs;
+  std::atomic<uint64_t> graph_launches{0};
 };
 
 namespace {
@@ -333,6 +358,18 @@ void reclaim(genesys_ctx *c, bool all) {
   }
 }
 
+// One positional read or write for one request, as its own Linux call would
+// be made (pread asks for at most pread_cap bytes when a cap is set).
+int64_t rw_one(const genesys_ctx *c, const Request &r) {
+  void *buf = (void *)r.a[1];
+  uint64_t len = r.a[2];
+  if (r.nr == SYS_pread64) {
+    if (c->pread_cap && len > c->pread_cap) len = c->pread_cap;
+    return sys_ret(pread((int)r.a[0], buf, len, (off_t)r.a[3]));
+  }
+  return sys_ret(pwrite((int)r.a[0], buf, len, (off_t)r.a[3]));
+}
+
 int64_t execute_one(genesys_ctx *c, Request &r, Counters &k) {
   const uint64_t *a = r.a;
   bump(k.os_calls, 1);
@@ -351,6 +388,9 @@ int64_t execute_one(genesys_ctx *c, Request &r, Counters &k) {
       return do_mmap(c, a);
     case SYS_munmap:
       return do_munmap(c, a);
+    case SYS_pread64:
+    case SYS_pwrite64:
+      return rw_one(c, r);
     default:
       if (!allowed(c, r.nr)) return -ENOSYS;
       return sys_ret(syscall((long)r.nr, a[0], a[1], a[2], a[3], a[4], a[5]));
@@ -362,7 +402,14 @@ int64_t execute_one(genesys_ctx *c, Request &r, Counters &k) {
 // call.  Contiguous buffers become one pread/pwrite, others one
 // preadv/pwritev.  Each request then receives the part of the merged result
 // that covers its own range - the value its own call would have returned.
-size_t merge_run(Request *const *reqs, size_t i, size_t n, Counters &k) {
+// A merged call can come back short of the run's total (a short read or
+// write, or a fault in one request's buffer after earlier bytes were moved)
+// or fail: the requests it covered in full keep their share, the one it
+// covered in part keeps that part (a short count its own call could have
+// returned), and every later request is made again as a call of its own, so
+// that no request receives 0 or another's error for bytes its own call would
+// have moved.
+size_t merge_run(const genesys_ctx *c, Request *const *reqs, size_t i, size_t n, Counters &k) {
   const uint32_t nr = reqs[i]->nr;
   const int fd = (int)reqs[i]->a[0];
   size_t j = i + 1;
@@ -379,32 +426,56 @@ size_t merge_run(Request *const *reqs, size_t i, size_t n, Counters &k) {
   int64_t res;
   bump(k.os_calls, 1);
   const uint64_t e0 = genesys_mono_ns();
-  if (m == 1 || contiguous_buf) {
+  if (m == 1) {
+    res = rw_one(c, *reqs[i]);
+  } else if (contiguous_buf) {
     void *buf = (void *)reqs[i]->a[1];
-    long r = nr == SYS_pread64 ? pread(fd, buf, total, (off_t)off) : pwrite(fd, buf, total, (off_t)off);
+    const uint64_t ask = nr == SYS_pread64 && c->pread_cap ? std::min<uint64_t>(total, c->pread_cap) : total;
+    long r = nr == SYS_pread64 ? pread(fd, buf, ask, (off_t)off) : pwrite(fd, buf, ask, (off_t)off);
     res = sys_ret(r);
   } else {
     iovec iov[IOV_MAX];
+    size_t niov = m;
     for (size_t t = 0; t < m; ++t) iov[t] = {(void *)reqs[i + t]->a[1], (size_t)reqs[i + t]->a[2]};
-    long r = nr == SYS_pread64 ? preadv(fd, iov, (int)m, (off_t)off) : pwritev(fd, iov, (int)m, (off_t)off);
+    if (nr == SYS_pread64 && c->pread_cap && total > c->pread_cap) {  // ask for at most the cap
+      uint64_t left = c->pread_cap;
+      for (niov = 0; niov < m && left; ++niov) {
+        if (iov[niov].iov_len > left) iov[niov].iov_len = (size_t)left;
+        left -= iov[niov].iov_len;
+      }
+    }
+    long r = nr == SYS_pread64 ? preadv(fd, iov, (int)niov, (off_t)off) : pwritev(fd, iov, (int)niov, (off_t)off);
     res = sys_ret(r);
+  }
+  uint64_t moved = res > 0 ? (uint64_t)res : 0;
+  // requests the merged call covered (in full, or the one it covered in part)
+  size_t t = i;
+  uint64_t prefix = 0;
+  if (m == 1) {
+    reqs[t++]->ret = res;
+  } else if (res >= 0) {
+    for (; t < j; ++t) {
+      const uint64_t len = reqs[t]->a[2];
+      if ((uint64_t)res < prefix + len) break;
+      reqs[t]->ret = (int64_t)len;
+      prefix += len;
+    }
+    if (t < j && (uint64_t)res > prefix) {
+      reqs[t]->ret = (int64_t)((uint64_t)res - prefix);
+      ++t;
+    }
+  }
+  // the rest: each as its own call
+  for (; t < j; ++t) {
+    bump(k.os_calls, 1);
+    reqs[t]->ret = rw_one(c, *reqs[t]);
+    if (reqs[t]->ret > 0) moved += (uint64_t)reqs[t]->ret;
   }
   const uint64_t dt = genesys_mono_ns() - e0;
   const int oi = nr == SYS_pread64 ? OP_PREAD : OP_PWRITE;
   bump(k.op_ns[oi], dt);
   if (dt > k.op_max_ns[oi].load(std::memory_order_relaxed)) k.op_max_ns[oi].store(dt, std::memory_order_relaxed);
-  uint64_t prefix = 0;
-  for (size_t t = i; t < j; ++t) {
-    const uint64_t len = reqs[t]->a[2];
-    if (res < 0) {
-      reqs[t]->ret = res;
-    } else {
-      const uint64_t got = (uint64_t)res > prefix ? (uint64_t)res - prefix : 0;
-      reqs[t]->ret = (int64_t)std::min<uint64_t>(got, len);
-    }
-    prefix += len;
-  }
-  if (res > 0) bump(k.bytes, (uint64_t)res);
+  if (moved) bump(k.bytes, moved);
   return j;
 }
 
@@ -491,7 +562,7 @@ uint64_t process_batch(genesys_ctx *c, uint32_t ri, Batch &b, size_t n, Counters
   for (size_t i = 0; i < n;) {
     Request &r = *p[i];
     if (c->cfg.merge && (r.nr == SYS_pread64 || r.nr == SYS_pwrite64)) {
-      i = merge_run(p, i, n, k);
+      i = merge_run(c, p, i, n, k);
       continue;
     }
     const uint64_t e0 = genesys_mono_ns();
@@ -691,6 +762,11 @@ void free_all(genesys_ctx *c) {
   dev_free(c, c->trace);
   dev_free(c, c->trace_count);
   if (c->scratch && !c->host_only) cudaFree(c->scratch);
+  for (auto &kv : c->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  c->graphs.clear();
   if (c->aux) cudaStreamDestroy(c->aux);
   if (c->ev_start) cudaEventDestroy(c->ev_start);
   if (c->ev_end) cudaEventDestroy(c->ev_end);
@@ -709,6 +785,47 @@ int read_tails(genesys_ctx *c, std::vector<uint32_t> &tails) {
   CUDA_TRY(cudaMemcpyAsync(raw.data(), c->ring_tail, raw.size() * 4, cudaMemcpyDeviceToHost, c->aux));
   CUDA_TRY(cudaStreamSynchronize(c->aux));
   for (uint32_t r = 0; r < n; ++r) tails[r] = raw[(size_t)r * 32];
+  return 0;
+}
+
+// GENESYS_LAUNCH_GRAPH: the first launch of a (kernel, grid, block, shared
+// memory, cooperative) shape builds and instantiates a graph holding that one
+// kernel node; later launches of the shape set the node's arguments on the
+// instantiated graph and launch it, without rebuilding it.  Launches already
+// queued keep the arguments they were given.
+int launch_graph(genesys_ctx *c, const void *kernel, const uint32_t grid[3], const uint32_t block[3], size_t smem,
+                 void **args, bool coop, cudaStream_t s) {
+  cudaKernelNodeParams kp{};
+  kp.func = const_cast<void *>(kernel);
+  kp.gridDim = dim3(grid[0], grid[1], grid[2]);
+  kp.blockDim = dim3(block[0], block[1], block[2]);
+  kp.sharedMemBytes = (unsigned)smem;
+  kp.kernelParams = args;
+  genesys_ctx::GraphKey key{kernel, {grid[0], grid[1], grid[2]}, {block[0], block[1], block[2]}, smem, coop};
+  std::lock_guard<std::mutex> lock(c->graph_mu);
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end()) {
+    genesys_ctx::GraphExec ge;
+    cudaError_t e = cudaGraphCreate(&ge.graph, 0);
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&ge.node, ge.graph, nullptr, 0, &kp);
+    if (e == cudaSuccess && coop) {
+      cudaKernelNodeAttrValue v{};
+      v.cooperative = 1;
+      e = cudaGraphKernelNodeSetAttribute(ge.node, cudaKernelNodeAttributeCooperative, &v);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge.exec, ge.graph, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (ge.exec) cudaGraphExecDestroy(ge.exec);
+      if (ge.graph) cudaGraphDestroy(ge.graph);
+      return fail(GENESYS_ECUDA, "graph launch set-up: %s", cudaGetErrorString(e));
+    }
+    it = c->graphs.emplace(key, ge).first;
+  } else {
+    CUDA_TRY(cudaGraphExecKernelNodeSetParams(it->second.exec, it->second.node, &kp));
+  }
+  CUDA_TRY(cudaGraphLaunch(it->second.exec, s));
+  c->graph_launches.fetch_add(1, std::memory_order_relaxed);
   return 0;
 }
 
@@ -924,7 +1041,7 @@ static uint64_t service_cpu_total(genesys_ctx *c) {
 uint32_t genesys_sizeof(int which) {
   switch (which) {
     case GENESYS_SIZEOF_CONFIG: return sizeof(genesys_config);
-    case GENESYS_SIZEOF_STATS: return sizeof(genesys_stats);
+    case GENESYS_SIZEOF_STATS: return sizeof(genesys_stats_t);
     case GENESYS_SIZEOF_SERVE_CONFIG: return sizeof(genesys_serve_config);
     case GENESYS_SIZEOF_SERVE_STATS: return sizeof(genesys_serve_stats);
     case GENESYS_SIZEOF_TRACE_DEV: return sizeof(genesys_trace_dev);
@@ -1053,12 +1170,18 @@ int genesys_launch(genesys_ctx *c, const void *kernel, const uint32_t grid[3], c
                   "kernel-grain strong ordering needs every block resident: grid %llu > %d x %u (Sec. 4.1)",
                   (unsigned long long)nblocks, per_sm, c->n_sms);
   }
-  if (gran == GENESYS_GRAN_KERNEL) CUDA_TRY(cudaMemsetAsync(c->ksite, 0, GENESYS_KSITES * sizeof(genesys_ksite), s));
+  // kernel-grain call sites start every launch reset, whatever grain the
+  // flags declare (a kernel may mix grains)
+  CUDA_TRY(cudaMemsetAsync(c->ksite, 0, GENESYS_KSITES * sizeof(genesys_ksite), s));
   CUDA_TRY(cudaEventRecord(c->ev_start, s));
-  if (coop)
+  if (flags & GENESYS_LAUNCH_GRAPH) {
+    int rc = launch_graph(c, kernel, grid, block, smem, args, coop, s);
+    if (rc) return rc;
+  } else if (coop) {
     CUDA_TRY(cudaLaunchCooperativeKernel(kernel, g, b, args, smem, s));
-  else
+  } else {
     CUDA_TRY(cudaLaunchKernel(kernel, g, b, args, smem, s));
+  }
   CUDA_TRY(cudaEventRecord(c->ev_end, s));
   if (flags & GENESYS_LAUNCH_SYNC) {
     CUDA_TRY(cudaStreamSynchronize(s));
@@ -1129,7 +1252,7 @@ int genesys_reclaim(genesys_ctx *c) {
   return 0;
 }
 
-int genesys_stats_get(genesys_ctx *c, genesys_stats *o) {
+int genesys_stats_get(genesys_ctx *c, genesys_stats_t *o) {
   return genesys_guard("genesys_stats_get", [&]() -> int {
     if (!c || !o) return fail(GENESYS_EINVAL, "NULL argument");
     memset(o, 0, sizeof *o);
@@ -1174,6 +1297,25 @@ int genesys_stats_reset(genesys_ctx *c) {
   std::lock_guard<std::mutex> g(c->restart_mu);
   c->cpu_reset_ns = service_cpu_total(c);
   return 0;
+}
+
+int genesys_stats(genesys_ctx *c, genesys_stats_t *out) { return genesys_stats_get(c, out); }
+
+int genesys_graph_launches(genesys_ctx *c, uint64_t *out) {
+  if (!c || !out) return fail(GENESYS_EINVAL, "NULL argument");
+  *out = c->graph_launches.load();
+  return 0;
+}
+
+int genesys_check_pread_cap(genesys_ctx *c, uint64_t cap_bytes) {
+  if (!c) return fail(GENESYS_EINVAL, "ctx is NULL");
+#ifdef GENESYS_DEVICE_CHECKS
+  c->pread_cap = cap_bytes;
+  return 0;
+#else
+  (void)cap_bytes;
+  return fail(GENESYS_EINVAL, "genesys_check_pread_cap: only the checked build (GENESYS_DEVICE_CHECKS) caps preads");
+#endif
 }
 
 int genesys_trace_read(genesys_ctx *c, genesys_trace_dev *dev, uint32_t dev_cap, uint32_t *n_dev,

@@ -108,9 +108,8 @@ __global__ void __launch_bounds__(1024) c5_request_kernel(genesys_dev g, const g
         // (the SMs copy it: a copy-engine transfer ordered on a stream could
         // queue behind this very kernel) and scans it there
         uint8_t *st_part = staging + st_off + p0;
-        int64_t r = call<GROUP, RELAXED, BLOCKING, ROLE_CONSUMER>(g, SYS_pread64, fd, (uint64_t)st_part, plen,
-                                                                   op.off + p0);
-        if (r > (int64_t)plen) r = (int64_t)plen;
+        // a short read is continued until the part is whole or the file ends
+        const int64_t r = pread_full<GROUP, RELAXED, ROLE_CONSUMER>(g, fd, st_part, plen, op.off + p0);
         uint8_t *dst = region + p0;
         // 16-byte loads, eight in flight per thread: the bytes cross the host
         // link, so a thread's loads must overlap to cover its latency

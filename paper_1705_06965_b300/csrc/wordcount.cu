@@ -222,7 +222,8 @@ __global__ void __launch_bounds__(1024, 1) c3_plain_kernel(genesys_dev g, const 
     const C3Item it = items[idx];
     uint64_t dst, n, foff;
     c3_read_args(it, buf, &dst, &n, &foff);
-    const int64_t r = call<GROUP, STRONG, BLOCKING>(g, SYS_pread64, (uint64_t)it.fd, dst, n, foff);
+    // a short read is continued until the item and its halo are whole or the file ends
+    const int64_t r = pread_full<GROUP, STRONG>(g, (uint64_t)it.fd, (uint8_t *)dst, n, foff);
     if (r < 0) break;
     c3_scan(g, S, tile, tile_bytes, buf, buf_bytes, it.off, it.len, c3_avail(it, r));
     __syncthreads();  // S.item is rewritten by the next pop
@@ -249,6 +250,21 @@ __global__ void __launch_bounds__(1024, 1) c3_batched_kernel(genesys_dev g, cons
     c3_read_args(it, buf, &dst, &n, &foff);
     issue(g, t, SYS_pread64, (uint64_t)it.fd, dst, n, foff);
   };
+  // the prefetched read came back short of what it asked for: read the rest
+  // (blocking) until the item and its halo are whole or the file ends
+  auto finish_item = [&](int64_t r, uint32_t idx, uint8_t *buf) -> int64_t {
+    const C3Item it = items[idx];
+    uint64_t dst, n, foff;
+    c3_read_args(it, buf, &dst, &n, &foff);
+    uint64_t got = r > 0 ? ((uint64_t)r < n ? (uint64_t)r : n) : 0;
+    while (r > 0 && got < n) {
+      Ticket more;
+      issue(g, &more, SYS_pread64, (uint64_t)it.fd, dst + got, n - got, foff + got);
+      r = wait(g, more);
+      if (r > 0) got += (uint64_t)r < n - got ? (uint64_t)r : n - got;
+    }
+    return r < 0 ? r : (int64_t)got;
+  };
   if (leader) {
     cur_idx = atomicAdd(head, 1u);
     if (cur_idx < n_items) issue_item(&cur, cur_idx, bufs[0]);
@@ -259,7 +275,7 @@ __global__ void __launch_bounds__(1024, 1) c3_batched_kernel(genesys_dev g, cons
       if (cur_idx < n_items) {
         nxt_idx = atomicAdd(head, 1u);
         if (nxt_idx < n_items) issue_item(&nxt, nxt_idx, bufs[(k + 1) & 1]);
-        r = wait(g, cur);
+        r = finish_item(wait(g, cur), cur_idx, bufs[k & 1]);
         if (r < 0 && nxt_idx < n_items) {  // stop: collect the prefetch, release its slot
           wait(g, nxt);
           nxt_idx = 0xFFFFFFFFu;
@@ -405,48 +421,25 @@ static void *g_c3_noalloc_dev_addr[kStaticMaxDevices];
 
 }  // namespace
 
-extern "C" int genesys_c3_wordcount_noalloc(genesys_ctx *c, const int32_t *fds, const uint64_t *file_bytes,
-                                            uint32_t n_files, const uint8_t *queries16, const uint8_t *qlen,
-                                            uint32_t nq, uint64_t chunk, uint32_t ctas, uint32_t threads,
-                                            uint32_t form, void *staging, uint64_t staging_bytes,
-                                            unsigned long long *counts_dev, void *stream) {
-  if (!c || !fds || !file_bytes || !queries16 || !qlen || !staging || !counts_dev)
-    return set_err(GENESYS_EINVAL, "NULL argument");
-  if (nq == 0 || nq > (uint32_t)kMaxQ) return set_err(GENESYS_EINVAL, "1..64 queries");
-  for (uint32_t q = 0; q < nq; ++q)
-    if (qlen[q] == 0 || qlen[q] > kHalo) return set_err(GENESYS_EINVAL, "query length must be 1..16");
-  if (chunk < 64 || chunk % 16 || chunk > (1u << 30)) return set_err(GENESYS_EINVAL, "chunk: multiple of 16, >= 64");
-  if (ctas == 0 || threads < 32 || threads > 1024 || threads % 32) return set_err(GENESYS_EINVAL, "bad launch shape");
-  if ((uintptr_t)staging % 16) return set_err(GENESYS_EINVAL, "staging must be 16-byte aligned");
-  const uint64_t buf_bytes = chunk + 64;
-  const uint64_t need = (uint64_t)ctas * buf_bytes * (form == GENESYS_FORM_BATCHED ? 2 : 1);
-  if (staging_bytes < need) return set_err(GENESYS_EINVAL, "staging too small: ctas * (chunk + 64) per buffer");
-  uint64_t n_items = 0;
-  for (uint32_t f = 0; f < n_files; ++f) {
-    if (fds[f] < 0) return set_err(GENESYS_EINVAL, "bad fd");
-    n_items += (file_bytes[f] + chunk - 1) / chunk;
-  }
-  if (n_items > kStaticMaxItems) {
-    char msg[200];
-    snprintf(msg, sizeof msg,
-             "the files need %llu work items of %llu bytes; the allocation-free wordcount holds at most %u "
-             "(use a larger chunk or genesys_c3_wordcount)",
-             (unsigned long long)n_items, (unsigned long long)chunk, kStaticMaxItems);
-    return set_err(GENESYS_EINVAL, msg);
-  }
-  if (n_items == 0) return 0;
-  const int dev = genesys_internal_device(c);
-  if (dev < 0 || dev >= kStaticMaxDevices) return set_err(GENESYS_EINVAL, "device ordinal out of range");
-
-  std::lock_guard<std::mutex> lock(g_c3_noalloc_mu);
+// The device address of the array on device `dev`, looked up once per device
+// with that device current; the caller's current device is restored.
+static int c3_noalloc_scratch_address(int dev, unsigned char **out) {
   if (!g_c3_noalloc_dev_addr[dev]) {
-    // one-time set-up on this device: the device address of the array
-    if (cudaSetDevice(dev) != cudaSuccess) {
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(GENESYS_ECUDA, "cudaGetDevice failed");
+    }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) {
       cudaGetLastError();
       return set_err(GENESYS_ECUDA, "cudaSetDevice failed");
     }
     void *p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_c3_noalloc_scratch);
+    if (prev != dev && cudaSetDevice(prev) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(GENESYS_ECUDA, "cudaSetDevice (restoring the caller's device) failed");
+    }
     if (e != cudaSuccess || !p) {
       cudaGetLastError();
       char msg[160];
@@ -455,63 +448,104 @@ extern "C" int genesys_c3_wordcount_noalloc(genesys_ctx *c, const int32_t *fds, 
     }
     g_c3_noalloc_dev_addr[dev] = p;
   }
-  unsigned char *h = g_c3_noalloc_host;
-  memset(h, 0, kStaticItemsOff);  // queue head starts at 0; unused query entries are 0
-  C3Queries *q = reinterpret_cast<C3Queries *>(h + kStaticQOff);
-  q->nq = nq;
-  for (uint32_t i = 0; i < nq; ++i) {
-    uint8_t tmp[16] = {0};
-    memcpy(tmp, queries16 + 16 * i, qlen[i]);
-    memcpy(&q->w[i][0], tmp, 8);
-    memcpy(&q->w[i][1], tmp + 8, 8);
-    q->len[i] = qlen[i];
-  }
-  C3Item *hi = reinterpret_cast<C3Item *>(h + kStaticItemsOff);
-  uint32_t n = 0;
-  for (uint32_t f = 0; f < n_files; ++f) {
-    for (uint64_t off = 0; off < file_bytes[f]; off += chunk) {
-      C3Item it{};
-      it.fd = fds[f];
-      it.len = (uint32_t)(file_bytes[f] - off < chunk ? file_bytes[f] - off : chunk);
-      it.off = off;
-      it.fsize = file_bytes[f];
-      hi[n++] = it;
-    }
-  }
-  unsigned char *scratch = (unsigned char *)g_c3_noalloc_dev_addr[dev];
-  cudaStream_t s = (cudaStream_t)stream;
-  if (cudaMemcpyAsync(scratch, h, kStaticItemsOff + (size_t)n * sizeof(C3Item), cudaMemcpyHostToDevice, s) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    return set_err(GENESYS_ECUDA, "upload of work items failed");
-  }
-  genesys_dev g;
-  genesys_device_view(c, &g);
-  if (form == GENESYS_FORM_BATCHED && g.n_slots < 2ull * ctas)
-    return set_err(GENESYS_EINVAL, "the batched form holds two slots per block: n_slots must be >= 2 * ctas");
-  const C3Item *d_items = (const C3Item *)(scratch + kStaticItemsOff);
-  uint32_t *head = (uint32_t *)scratch;
-  const C3Queries *d_q = (const C3Queries *)(scratch + kStaticQOff);
-  uint8_t *st = (uint8_t *)staging;
-  uint64_t bb = buf_bytes;
-  uint32_t tile_bytes = c3_tile_bytes(threads);
-  void *args[] = {&g, &d_items, &n, &head, &d_q, &st, &bb, &tile_bytes, &counts_dev};
-  const size_t smem = tile_bytes + 48;
-  const void *k = form == GENESYS_FORM_BATCHED ? (const void *)&c3_batched_kernel : (const void *)&c3_plain_kernel;
-  const uint32_t flags = form == GENESYS_FORM_BATCHED
-                             ? (GENESYS_GRAN_GROUP | GENESYS_LAUNCH_RELAXED | GENESYS_LAUNCH_NONBLOCKING)
-                             : GENESYS_GRAN_GROUP;
-  const uint32_t g3[3] = {ctas, 1, 1}, b3[3] = {threads, 1, 1};
-  int rc = genesys_launch(c, k, g3, b3, smem, args, flags | GENESYS_LAUNCH_SYNC, stream);
-  if (rc) return rc;
-  int32_t stw[GENESYS_ST_WORDS];
-  rc = genesys_status(c, stw, 1);
-  if (rc) return rc;
-  if (stw[GENESYS_ST_TIMEOUTS] || stw[GENESYS_ST_FAILED_CALLS] || stw[GENESYS_ST_FIRST_ERROR]) {
-    char msg[160];
-    snprintf(msg, sizeof msg, "device-side calls failed: first error %d, %d timeouts, %d failed calls",
-             stw[GENESYS_ST_FIRST_ERROR], stw[GENESYS_ST_TIMEOUTS], stw[GENESYS_ST_FAILED_CALLS]);
-    return set_err(GENESYS_EDEVICE, msg);
-  }
+  *out = (unsigned char *)g_c3_noalloc_dev_addr[dev];
   return 0;
+}
+
+extern "C" int genesys_c3_wordcount_noalloc(genesys_ctx *c, const int32_t *fds, const uint64_t *file_bytes,
+                                            uint32_t n_files, const uint8_t *queries16, const uint8_t *qlen,
+                                            uint32_t nq, uint64_t chunk, uint32_t ctas, uint32_t threads,
+                                            uint32_t form, void *staging, uint64_t staging_bytes,
+                                            unsigned long long *counts_dev, void *stream) {
+  return genesys_guard("genesys_c3_wordcount_noalloc", [&]() -> int {
+    if (!c || !fds || !file_bytes || !queries16 || !qlen || !staging || !counts_dev)
+      return set_err(GENESYS_EINVAL, "NULL argument");
+    if (nq == 0 || nq > (uint32_t)kMaxQ) return set_err(GENESYS_EINVAL, "1..64 queries");
+    for (uint32_t q = 0; q < nq; ++q)
+      if (qlen[q] == 0 || qlen[q] > kHalo) return set_err(GENESYS_EINVAL, "query length must be 1..16");
+    if (chunk < 64 || chunk % 16 || chunk > (1u << 30)) return set_err(GENESYS_EINVAL, "chunk: multiple of 16, >= 64");
+    if (ctas == 0 || threads < 32 || threads > 1024 || threads % 32) return set_err(GENESYS_EINVAL, "bad launch shape");
+    if ((uintptr_t)staging % 16) return set_err(GENESYS_EINVAL, "staging must be 16-byte aligned");
+    const uint64_t buf_bytes = chunk + 64;
+    const uint64_t need = (uint64_t)ctas * buf_bytes * (form == GENESYS_FORM_BATCHED ? 2 : 1);
+    if (staging_bytes < need) return set_err(GENESYS_EINVAL, "staging too small: ctas * (chunk + 64) per buffer");
+    uint64_t n_items = 0;
+    for (uint32_t f = 0; f < n_files; ++f) {
+      if (fds[f] < 0) return set_err(GENESYS_EINVAL, "bad fd");
+      n_items += (file_bytes[f] + chunk - 1) / chunk;
+    }
+    if (n_items > kStaticMaxItems) {
+      char msg[200];
+      snprintf(msg, sizeof msg,
+               "the files need %llu work items of %llu bytes; the allocation-free wordcount holds at most %u "
+               "(use a larger chunk or genesys_c3_wordcount)",
+               (unsigned long long)n_items, (unsigned long long)chunk, kStaticMaxItems);
+      return set_err(GENESYS_EINVAL, msg);
+    }
+    if (n_items == 0) return 0;
+    const int dev = genesys_internal_device(c);
+    if (dev < 0 || dev >= kStaticMaxDevices) return set_err(GENESYS_EINVAL, "device ordinal out of range");
+
+    std::lock_guard<std::mutex> lock(g_c3_noalloc_mu);
+    unsigned char *scratch = nullptr;
+    if (int rc0 = c3_noalloc_scratch_address(dev, &scratch)) return rc0;  // first call on the device only
+    unsigned char *h = g_c3_noalloc_host;
+    memset(h, 0, kStaticItemsOff);  // queue head starts at 0; unused query entries are 0
+    C3Queries *q = reinterpret_cast<C3Queries *>(h + kStaticQOff);
+    q->nq = nq;
+    for (uint32_t i = 0; i < nq; ++i) {
+      uint8_t tmp[16] = {0};
+      memcpy(tmp, queries16 + 16 * i, qlen[i]);
+      memcpy(&q->w[i][0], tmp, 8);
+      memcpy(&q->w[i][1], tmp + 8, 8);
+      q->len[i] = qlen[i];
+    }
+    C3Item *hi = reinterpret_cast<C3Item *>(h + kStaticItemsOff);
+    uint32_t n = 0;
+    for (uint32_t f = 0; f < n_files; ++f) {
+      for (uint64_t off = 0; off < file_bytes[f]; off += chunk) {
+        C3Item it{};
+        it.fd = fds[f];
+        it.len = (uint32_t)(file_bytes[f] - off < chunk ? file_bytes[f] - off : chunk);
+        it.off = off;
+        it.fsize = file_bytes[f];
+        hi[n++] = it;
+      }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(scratch, h, kStaticItemsOff + (size_t)n * sizeof(C3Item), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return set_err(GENESYS_ECUDA, "upload of work items failed");
+    }
+    genesys_dev g;
+    genesys_device_view(c, &g);
+    if (form == GENESYS_FORM_BATCHED && g.n_slots < 2ull * ctas)
+      return set_err(GENESYS_EINVAL, "the batched form holds two slots per block: n_slots must be >= 2 * ctas");
+    const C3Item *d_items = (const C3Item *)(scratch + kStaticItemsOff);
+    uint32_t *head = (uint32_t *)scratch;
+    const C3Queries *d_q = (const C3Queries *)(scratch + kStaticQOff);
+    uint8_t *st = (uint8_t *)staging;
+    uint64_t bb = buf_bytes;
+    uint32_t tile_bytes = c3_tile_bytes(threads);
+    void *args[] = {&g, &d_items, &n, &head, &d_q, &st, &bb, &tile_bytes, &counts_dev};
+    const size_t smem = tile_bytes + 48;
+    const void *k = form == GENESYS_FORM_BATCHED ? (const void *)&c3_batched_kernel : (const void *)&c3_plain_kernel;
+    const uint32_t flags = form == GENESYS_FORM_BATCHED
+                               ? (GENESYS_GRAN_GROUP | GENESYS_LAUNCH_RELAXED | GENESYS_LAUNCH_NONBLOCKING)
+                               : GENESYS_GRAN_GROUP;
+    const uint32_t g3[3] = {ctas, 1, 1}, b3[3] = {threads, 1, 1};
+    int rc = genesys_launch(c, k, g3, b3, smem, args, flags | GENESYS_LAUNCH_SYNC, stream);
+    if (rc) return rc;
+    int32_t stw[GENESYS_ST_WORDS];
+    rc = genesys_status(c, stw, 1);
+    if (rc) return rc;
+    if (stw[GENESYS_ST_TIMEOUTS] || stw[GENESYS_ST_FAILED_CALLS] || stw[GENESYS_ST_FIRST_ERROR]) {
+      char msg[160];
+      snprintf(msg, sizeof msg, "device-side calls failed: first error %d, %d timeouts, %d failed calls",
+               stw[GENESYS_ST_FIRST_ERROR], stw[GENESYS_ST_TIMEOUTS], stw[GENESYS_ST_FAILED_CALLS]);
+      return set_err(GENESYS_EDEVICE, msg);
+    }
+    return 0;
+  });
 }

@@ -116,9 +116,10 @@ __global__ void __launch_bounds__(1024, 1) c1_plain_kernel(genesys_dev g, int fd
   for (uint64_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
     const uint64_t off = c * chunk;
     const uint64_t len = file_bytes - off < chunk ? file_bytes - off : chunk;
-    const int64_t r = call<GROUP, STRONG, BLOCKING>(g, SYS_pread64, (uint64_t)fd, (uint64_t)buf, len, off);
+    // a short read is continued until the chunk is whole or the file ends
+    const int64_t r = pread_full<GROUP, STRONG>(g, (uint64_t)fd, buf, len, off);
     if (r <= 0) break;  // r is the same in every thread (broadcast after the call)
-    hist_bytes(buf, (uint64_t)r < len ? (uint64_t)r : len, my);
+    hist_bytes(buf, (uint64_t)r, my);
   }
   hist_flush(sh, hist_out);
 }
@@ -138,9 +139,9 @@ __global__ void __launch_bounds__(1024, 1) c1_hbm_kernel(genesys_dev g, int fd, 
   for (uint64_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
     const uint64_t off = c * chunk;
     const uint64_t len = file_bytes - off < chunk ? file_bytes - off : chunk;
-    const int64_t r = call<GROUP, STRONG, BLOCKING>(g, SYS_pread64, (uint64_t)fd, (uint64_t)buf, len, off);
+    const int64_t r = pread_full<GROUP, STRONG>(g, (uint64_t)fd, buf, len, off);
     if (r <= 0) break;  // r is the same in every thread (broadcast after the call)
-    const uint64_t n = (uint64_t)r < len ? (uint64_t)r : len;
+    const uint64_t n = (uint64_t)r;
     const uint4 *src = reinterpret_cast<const uint4 *>(buf);
     uint4 *dst = reinterpret_cast<uint4 *>(land);
 #pragma unroll 4
@@ -170,9 +171,9 @@ __global__ void __launch_bounds__(1024, 1) c1_warp_kernel(genesys_dev g, int fd,
   for (uint64_t c = gw; c < n_chunks; c += n_warps) {  // warp-uniform loop
     const uint64_t off = c * chunk;
     const uint64_t len = file_bytes - off < chunk ? file_bytes - off : chunk;
-    const int64_t r = call<WARP, STRONG, BLOCKING>(g, SYS_pread64, (uint64_t)fd, (uint64_t)buf, len, off);
+    const int64_t r = pread_full<WARP, STRONG>(g, (uint64_t)fd, buf, len, off);
     if (r <= 0) break;  // r is the same in every lane (broadcast after the call)
-    hist_bytes_warp(buf, (uint64_t)r < len ? (uint64_t)r : len, my, lane);
+    hist_bytes_warp(buf, (uint64_t)r, my, lane);
   }
   hist_flush(sh, hist_out);
 }
@@ -192,10 +193,11 @@ __global__ void __launch_bounds__(1024, 1) c1_batched_kernel(genesys_dev g, int 
   const uint64_t n_mine = blockIdx.x < n_chunks ? (n_chunks - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   const bool leader = threadIdx.x == 0;
   Ticket t[D];  // the k-th chunk of this block uses ticket and buffer k % D
+  auto chunk_off = [&](uint64_t k) { return (blockIdx.x + k * gridDim.x) * (uint64_t)chunk; };
+  auto chunk_len = [&](uint64_t off) { return file_bytes - off < chunk ? file_bytes - off : (uint64_t)chunk; };
   auto issue_chunk = [&](uint64_t k) {
-    const uint64_t off = (blockIdx.x + k * gridDim.x) * (uint64_t)chunk;
-    const uint64_t len = file_bytes - off < chunk ? file_bytes - off : chunk;
-    issue(g, &t[k % D], SYS_pread64, (uint64_t)fd, (uint64_t)(base + (k % D) * (uint64_t)chunk), len, off);
+    const uint64_t off = chunk_off(k);
+    issue(g, &t[k % D], SYS_pread64, (uint64_t)fd, (uint64_t)(base + (k % D) * (uint64_t)chunk), chunk_len(off), off);
   };
   uint64_t issued = 0;
   if (leader)
@@ -203,7 +205,18 @@ __global__ void __launch_bounds__(1024, 1) c1_batched_kernel(genesys_dev g, int 
   __syncthreads();
   for (uint64_t k = 0; k < n_mine; ++k) {
     if (leader) {
-      const int64_t r = wait(g, t[k % D]);
+      int64_t r = wait(g, t[k % D]);
+      // a short read is continued (blocking) until the chunk is whole or the file ends
+      const uint64_t off = chunk_off(k), len = chunk_len(off);
+      uint8_t *buf = base + (k % D) * (uint64_t)chunk;
+      uint64_t got = r > 0 ? ((uint64_t)r < len ? (uint64_t)r : len) : 0;
+      while (r > 0 && got < len) {
+        Ticket more;
+        issue(g, &more, SYS_pread64, (uint64_t)fd, (uint64_t)(buf + got), len - got, off + got);
+        r = wait(g, more);
+        if (r > 0) got += (uint64_t)r < len - got ? (uint64_t)r : len - got;
+      }
+      if (r >= 0) r = (int64_t)got;
       if (r <= 0)  // stop early: collect the reads still in flight so that their slots are released
         for (uint64_t j = k + 1; j < issued; ++j) wait(g, t[j % D]);
       r_s = r;
@@ -211,7 +224,7 @@ __global__ void __launch_bounds__(1024, 1) c1_batched_kernel(genesys_dev g, int 
     __syncthreads();  // consumer: barrier after the read completes
     const int64_t r = r_s;
     if (r <= 0) break;
-    hist_bytes(base + (k % D) * (uint64_t)chunk, (uint64_t)r < chunk ? (uint64_t)r : chunk, my);
+    hist_bytes(base + (k % D) * (uint64_t)chunk, (uint64_t)r, my);
     __syncthreads();  // buffer k % D is free again
     if (leader && issued < n_mine) issue_chunk(issued++);
   }

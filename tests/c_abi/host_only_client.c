@@ -64,7 +64,7 @@ int main(int argc, char **argv) {
   CHECK(memcmp(buf, buf + 4096, 4096) == 0, "bytes read back differ");
   close(fd);
 
-  genesys_stats st;
+  genesys_stats_t st;
   CHECK(genesys_stats_get(ctx, &st) == 0, "stats");
   CHECK(st.requests == 66 && st.failed == 0, "requests %llu failed %llu", (unsigned long long)st.requests,
         (unsigned long long)st.failed);

@@ -1,6 +1,10 @@
 """The checked build (device-side index checks compiled in, failures counted
 in a status word instead of faulting): C1 in every form, C2 at every grain
-and the C3 wordcount give the oracle's results with all status words zero."""
+and the C3 wordcount give the oracle's results with all status words zero.
+Then, with every pread the service makes capped at 1,000 bytes (a host-side
+knob of the checked build: short reads in the middle of files, which Linux
+allows), C1 in every form, C3 in both forms and C5's preads still equal the
+oracle, whose reader loops until it has what it asked for or the file ends."""
 import os
 import subprocess
 import sys

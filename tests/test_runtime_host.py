@@ -413,7 +413,9 @@ def test_merged_preads_split_a_short_read_correctly(tmp_path):
     """Coalescing must not change any call's result (Sec. 4.2): eight 64-byte
     preads that continue each other merge into one Linux call; the file ends
     inside the fifth, so the results are 64, 64, 64, 64, 16, 0, 0, 0 - what
-    each call alone would have returned - and the bytes land where each asked."""
+    each call alone would have returned - and the bytes land where each asked.
+    The merged call came back short, so the three requests past its end are
+    made again as calls of their own (each then returns 0 at end of file)."""
     p = str(tmp_path / "short.bin")
     data = workloads.stream_bytes(21, 4 * 64 + 16)
     open(p, "wb").write(data)
@@ -444,9 +446,112 @@ def test_merged_preads_split_a_short_read_correctly(tmp_path):
         finally:
             os.close(fd)
     assert results == [64, 64, 64, 64, 16, 0, 0, 0], results
-    assert st["os_calls"] == 1, st
+    assert st["os_calls"] == 1 + 3, st
     assert got[:4 * 64 + 16] == data
     assert got[4 * 64 + 16:] == b"\xaa" * (8 * 64 - 4 * 64 - 16)
+
+
+def _serve_concurrent(c, n, call):
+    """Publish n emulated calls from n threads, then serve them as one pass of
+    a NO_THREADS context; returns the results."""
+    threads, results = [], [None] * n
+
+    def run(i):
+        results[i] = call(i)
+
+    for i in range(n):
+        t = threading.Thread(target=run, args=(i,))
+        t.start()
+        threads.append(t)
+    time.sleep(0.2)        # all published before the one service pass
+    served = 0
+    for _ in range(200):
+        served += c.service(1_000_000)
+        if served >= n:
+            break
+    [t.join() for t in threads]
+    return results
+
+
+def test_merged_pwritev_with_a_bad_middle_buffer_gives_each_its_own_result(tmp_path):
+    """Eight 64-byte pwrites that continue each other in the file, from
+    scattered buffers, merge into one pwritev; the fourth request's buffer is
+    not mapped.  Linux stops the merged call at that buffer and returns the
+    bytes written before it: the first three requests keep 64, the fourth
+    (made again alone) gets -EFAULT and the last four, made again alone, write
+    their bytes and get 64 - what separate calls would have done."""
+    p = str(tmp_path / "bad.bin")
+    n, bad = 8, 3
+    pieces = [workloads.stream_bytes(200 + i, 64) for i in range(n)]
+    with _ctx(no_threads=True, service_threads=1, n_slots=64, coalesce_max=64) as c:
+        buf = c.staging(n * 64)
+        view = c.host_view(buf, n * 64)
+        for i in range(n):  # piece i sits in buffer slot n-1-i (not neighbours: a vector call)
+            view[(n - 1 - i) * 64:(n - i) * 64] = np.frombuffer(pieces[i], np.uint8)
+        fd = os.open(p, os.O_CREAT | os.O_TRUNC | os.O_RDWR, 0o644)
+        try:
+            def call(i):
+                addr = 0x1000 if i == bad else buf + (n - 1 - i) * 64   # page 1: never mapped
+                return c.emulate_call(G.SYS_pwrite64, [fd, addr, 64, 64 * i])
+            results = _serve_concurrent(c, n, call)
+            st = c.stats()
+        finally:
+            os.close(fd)
+    assert results == [64, 64, 64, -errno.EFAULT, 64, 64, 64, 64], results
+    assert st["os_calls"] == 1 + (n - bad), st
+    data = open(p, "rb").read()
+    assert data == b"".join(pieces[:bad]) + b"\0" * 64 + b"".join(pieces[bad + 1:])
+
+
+def test_pread_cap_is_a_checked_build_knob():
+    """genesys_check_pread_cap exists in every build but caps preads only in
+    the checked one; elsewhere it is refused."""
+    with _ctx() as c:
+        with pytest.raises(G.GenesysError) as e:
+            c.pread_cap(1000)
+        assert e.value.code == G.EINVAL
+
+
+def test_pread_cap_makes_short_reads_in_the_checked_build(tmp_path):
+    """Checked build, preads capped at 100 bytes: a lone 1,000-byte pread
+    returns 100; eight 64-byte preads that continue each other merge into one
+    capped call of 100 bytes, so the first gets 64, the second the 36 that
+    call covered (a short read), and the other six, made again alone, 64
+    each; every byte lands where its request asked."""
+    import subprocess
+    import sys
+    from paper_1705_06965_b300 import build
+    build.build(device_checks=True)
+    path = str(tmp_path / "cap.bin")
+    open(path, "wb").write(workloads.stream_bytes(31, 4096))
+    code = (
+        "import os, threading, time, sys\n"
+        "sys.path.insert(0, 'tests')\n"
+        "import paper_1705_06965_b300 as G\n"
+        "from test_runtime_host import _ctx, _serve_concurrent\n"
+        "assert G.LIB_PATH.endswith('libgenesys_checked.so')\n"
+        f"path = {path!r}\n"
+        "data = open(path, 'rb').read()\n"
+        "fd = os.open(path, os.O_RDONLY)\n"
+        "with _ctx(service_threads=1) as c:\n"
+        "    c.pread_cap(100)\n"
+        "    b = c.staging(1000)\n"
+        "    assert c.emulate_call(G.SYS_pread64, [fd, b, 1000, 5]) == 100\n"
+        "    assert bytes(c.host_view(b, 100)) == data[5:105]\n"
+        "with _ctx(no_threads=True, service_threads=1, n_slots=64, coalesce_max=64) as c:\n"
+        "    c.pread_cap(100)\n"
+        "    b = c.staging(512)\n"
+        "    r = _serve_concurrent(c, 8, lambda i: c.emulate_call(G.SYS_pread64, [fd, b + 64 * i, 64, 64 * i]))\n"
+        "    assert r == [64, 36] + [64] * 6, r\n"
+        "    got = bytes(c.host_view(b, 512))\n"
+        "    assert got[:100] == data[:100] and got[128:512] == data[128:512]\n"
+        "    assert c.stats()['os_calls'] == 7\n"
+        "os.close(fd)\n"
+        "print('ok')\n")
+    env = dict(os.environ, GENESYS_LIBRARY="checked")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
 
 
 def test_merged_pwrites_with_scattered_buffers_use_one_vector_call(tmp_path):
@@ -566,6 +671,9 @@ def test_every_entry_point_rejects_null_arguments():
     t("genesys_service_restart", None, 0, 0)
     t("genesys_trace_read", None, None, 0, None, None, 0, None, None)
     t("genesys_c5_serve", None, None, 0, None, 0, 0, None, None, None, None)
+    t("genesys_stats", None, None)
+    t("genesys_graph_launches", None, None)
+    t("genesys_check_pread_cap", None, 0)
     assert res.pop("genesys_shutdown") == 0
     assert all(v == G.EINVAL for v in res.values()), res
     assert len(res) >= 35
@@ -605,11 +713,12 @@ def test_service_health_sees_a_paused_thread():
         assert c.service_health(50_000_000) == ([], 0)
 
 
-@pytest.mark.parametrize("src", ["user_kernel.cu", "syscall_demo.cu"])
+@pytest.mark.parametrize("src", ["user_kernel.cu", "syscall_demo.cu", "launch_demo.cu"])
 def test_a_user_kernel_compiles_against_the_headers(tmp_path, src):
-    """The device headers are usable from a user's own kernel: the README's
-    example (genesys::call) and a kernel of the handle-less genesys_syscall
-    compile for sm_103a with nothing but include/ (not run here)."""
+    """The device headers are usable from a user's own kernel: a pread kernel
+    through genesys::call, a kernel of the handle-less genesys_syscall and the
+    launch demo (graph relaunch, kernel-grain sites) compile for sm_103a with
+    nothing but include/ (not run here)."""
     import shutil
     import subprocess
     from paper_1705_06965_b300 import build

@@ -8,8 +8,11 @@ collected last so that a run stopping at the first failure has run every other
 test first; it also passes alone in a fresh process.
 
 The test calls the new entry point through the C ABI twice in a row and checks
-each result against genesys_c3_wordcount on the same inputs (integer counts:
-the tolerance is exact equality, as in every wordcount test).
+each result against genesys_c3_wordcount on the same inputs and against the
+generator's recorded per-query counts, the ground truth the oracle is pinned
+to (integer counts: the tolerance is exact equality, as in every wordcount
+test).  The caller's current CUDA device is the same after the first call,
+which sets up the array's address, as before it.
 """
 import ctypes
 import os
@@ -55,13 +58,17 @@ def test_noalloc_wordcount_matches_allocating_entry_point():
             assert rc == 0, G.last_error()
             want = ref.cpu().numpy()
             assert want.sum() > 0
+            assert np.array_equal(want.astype(np.uint64), corpus.truth_total())
+            device_before = torch.cuda.current_device()
             for call in range(2):
                 got = torch.zeros(nq, dtype=torch.int64, device="cuda")
                 rc = L.genesys_c3_wordcount_noalloc(ctx.handle, fds.ctypes.data, sizes.ctypes.data, len(fds),
                                                     q.ctypes.data, ql.ctypes.data, nq, chunk, ctas, threads,
                                                     G.FORM_BATCHED, st, need, got.data_ptr(), None)
                 assert rc == 0, (call, G.last_error())
+                assert torch.cuda.current_device() == device_before, call
                 assert np.array_equal(got.cpu().numpy(), want), call
+                assert np.array_equal(got.cpu().numpy().astype(np.uint64), corpus.truth_total()), call
             # inputs needing more work items than the fixed array holds are refused
             too_small_chunk = 64
             n_items = int(sum(-(-int(s) // too_small_chunk) for s in sizes))
