@@ -38,6 +38,7 @@ import sys
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+ALG_BYTES_PER_CALL = 64 + 8  # a call's slot and its result word (payload bytes are counted apart)
 sys.path.insert(0, ROOT)
 
 SIZES = [1 << 10, 1 << 12, 1 << 14, 1 << 16, 1 << 18, 1 << 20]
@@ -270,6 +271,92 @@ def pctl(a, q):
     return float(np.percentile(a, q)) if len(a) else None
 
 
+def _at(d, *path):
+    """d[path[0]][path[1]]..., or None where a level is missing."""
+    for k in path:
+        if not isinstance(d, dict) or k not in d:
+            return None
+        d = d[k]
+    return d
+
+
+def _sig(x, digits=3):
+    """x to `digits` significant digits (numbers only; other values as they are)."""
+    if isinstance(x, bool) or not isinstance(x, (int, float)) or x == 0:
+        return x
+    from math import floor, log10
+    nd = digits - 1 - int(floor(log10(abs(x))))
+    return round(x, nd) if nd > 0 else int(round(x, nd))
+
+
+def _beats(a, b, higher_is_better=True):
+    """a beats b (None when either is missing)."""
+    if a is None or b is None:
+        return None
+    return bool(a > b) if higher_is_better else bool(a < b)
+
+
+def summarize(line: dict) -> dict:
+    """The figures of every config in a few hundred bytes, for the end of the
+    bench line: the headline, C1's 4 MiB forms and the 1 GiB scan against the
+    host link, the C3 wordcount, the C4 service's saturation point, the C5
+    served trace against its plain form, every oracle timing with its cores,
+    whether each result was checked against the oracle, and the targets (the
+    batched or served form against the plain blocking strong form, in
+    syscalls/s, requests/s and p99, and the scan's fraction of the link)."""
+    ex = line
+    scan = {k: v for k, v in (_at(ex, "pread_scan_1GiB") or {}).items() if isinstance(v, dict) and "GB_per_s" in v}
+    scan_best = max(scan.items(), key=lambda kv: kv[1]["GB_per_s"], default=(None, {}))
+    c3 = _at(ex, "wordcount_c3") or {}
+    c3b = max((c3[k] for k in ("plain", "batched") if isinstance(c3.get(k), dict)),
+              key=lambda v: v.get("GB_per_s", 0), default={})
+    c4 = _at(ex, "kv_c4") or {}
+    c5 = _at(ex, "served_c5") or {}
+    plain5, served5 = c5.get("plain_first1000") or {}, c5.get("served_first1000") or {}
+    pers5 = c5.get("persistent_first1000") or {}
+    c2p, c2b = _at(ex, "forms", "plain_blocking_strong") or {}, _at(ex, "forms", "batched") or {}
+    oc = _at(ex, "oracle_checks") or {}
+    out = {
+        "c2c1_syscalls_per_s": _sig(ex.get("value")), "e2e": _sig(_at(ex, "e2e", "value")),
+        "wi_2p20": {"calls_per_s": _sig(c2p.get("syscalls_per_s")),
+                    "frac_file_order": _sig(_at(ex, "roofline", "service", "frac")),
+                    "frac_interleaved": _sig(_at(ex, "roofline", "service", "warp_interleaved_order", "frac"))},
+        "c1_4MiB_GBps": {k: _sig(_at(ex, "c1_4MiB", k, "GB_per_s")) for k in ("plain", "batched")},
+        "scan_1GiB": {"form": scan_best[0], "GBps": _sig(scan_best[1].get("GB_per_s")),
+                      "frac_h2d": _sig(scan_best[1].get("frac_of_host_link_h2d"))},
+        "c3": {"GBps": _sig(c3b.get("GB_per_s")), "frac_h2d": _sig(c3b.get("frac_of_host_link_h2d")),
+               "truth_eq": c3b.get("counts_equal_ground_truth")},
+        "c4": {"sat_rps": _sig(c4.get("saturation_req_per_s")), "p50_us": _sig(c4.get("saturation_p50_us")),
+               "p99_us": _sig(c4.get("saturation_p99_us")), "best_any_rps": _sig(c4.get("best_any_req_per_s")),
+               "host_bound": c4.get("saturation_host_bound"), "replies_eq_oracle": oc.get("c4_replies_equal")},
+        "c5": {"served_rps": _sig(_at(c5, "served_full", "requests_per_s")),
+               "served_p99_ms": _sig(_at(c5, "served_full", "p99_ms")),
+               "persistent_rps": _sig(_at(c5, "persistent_full", "requests_per_s")),
+               "persistent_p99_ms": _sig(_at(c5, "persistent_full", "p99_ms")),
+               "plain1k_rps": _sig(plain5.get("requests_per_s")), "plain1k_p99_ms": _sig(plain5.get("p99_ms")),
+               "alone_eq_mix": c5.get("first1000_alone_equals_mix"), "full_eq_oracle": oc.get("c5_full_equal")},
+        "oracle": {"cores": _at(ex, "probes", "host_cpus"),
+                   "c2c1_sps_1t": _sig(_at(ex, "cpu_baseline", "value")),
+                   "c1_eq": _at(ex, "cpu_baseline", "c1_histogram_equals_oracle"),
+                   "c3_GBps_1t": _sig(_at(c3, "cpu_baseline_oracle", "one_thread_GB_per_s")),
+                   "c3_GBps_all": _sig(_at(c3, "cpu_baseline_oracle", "files_to_cores_GB_per_s")),
+                   "c4_sat_rps_1t": _sig(_at(c4, "cpu_baseline_oracle_server", "saturation_req_per_s")),
+                   "c5_rps_1t": _sig(_at(c5, "cpu_baseline_oracle_replay_first1000", "requests_per_s"))},
+    }
+    best5 = max((v for v in (served5, pers5) if v), key=lambda v: v.get("requests_per_s", 0), default={})
+    out["targets"] = {
+        "c2_batched_beats_plain": {"syscalls_per_s": _beats(c2b.get("syscalls_per_s"), c2p.get("syscalls_per_s")),
+                                   "requests_per_s": _beats(c2b.get("requests_per_s"), c2p.get("requests_per_s")),
+                                   "p99": _beats(c2b.get("p99_us"), c2p.get("p99_us"), False)},
+        "c5_served_beats_plain": {"syscalls_per_s": _beats(best5.get("syscalls_per_s"), plain5.get("syscalls_per_s")),
+                                  "requests_per_s": _beats(best5.get("requests_per_s"), plain5.get("requests_per_s")),
+                                  "p99": _beats(best5.get("p99_ms"), plain5.get("p99_ms"), False)},
+        "scan_frac_h2d_ge_0.8": (None if scan_best[1].get("frac_of_host_link_h2d") is None
+                                 else bool(scan_best[1]["frac_of_host_link_h2d"] >= 0.8)),
+    }
+    return out
+
+
 def kernel_src_hash(kernel: str) -> str:
     """Hash of what a kernel's counters depend on: the device protocol headers
     and the kernel's own section of its source file."""
@@ -484,7 +571,7 @@ def run_only(args):
 
 
 # ---------------------------------------------------------------- extras
-def profile_extras(args, rig, local, rank, link):
+def profile_extras(args, rig, local, rank, link, checks=None):
     """Untimed measurements reported beside the headline: pread+scan and
     wordcount GB/s at autotuned settings (fractions of the measured host
     link), the served C5 trace against its plain one-at-a-time form, and the
@@ -548,8 +635,8 @@ def profile_extras(args, rig, local, rank, link):
     finally:
         for fd in fds:
             os.close(fd)
-    out["served_c5"] = serve_c5(G, local, rank)
-    out["kv_c4"] = serve_c4(G, local, rank)
+    out["served_c5"] = serve_c5(G, local, rank, checks)
+    out["kv_c4"] = serve_c4(G, local, rank, checks=checks)
     out["fig6_block_permutation"] = study_fig6(G, rig, local)
     out["fig7_coalescing"] = study_fig7(G, rig, local, rank)
     out["fig10_echo"] = study_fig10(G, local, rank)
@@ -729,10 +816,12 @@ def study_fig7(G, rig, local, rank, sizes=(256 << 10, 1 << 20, 4 << 20, 16 << 20
     return out
 
 
-def serve_c5(G, local, rank):
+def serve_c5(G, local, rank, checks=None):
     """C5: the 10,000-request trace served with continuous admission (up to 64
     kernels in flight, graph relaunch, autotuned call granularity), and its
-    first 1,000 requests both served and in the plain one-at-a-time form."""
+    first 1,000 requests both served and in the plain one-at-a-time form.
+    checks["c5"] receives what the oracle leg compares: the trace, the full
+    run's results and its output file."""
     import numpy as np
     import workloads
     tr = workloads.c5_trace(workloads.C5_FULL)
@@ -741,8 +830,8 @@ def serve_c5(G, local, rank):
     out = {}
     try:
         with G.Context(device=local, service_threads=8, staging_bytes=512 << 20) as ctx:
-            def run(sub, **cfg):
-                ofd = os.open(os.path.join(d, "out.bin"), os.O_CREAT | os.O_RDWR, 0o644)
+            def run(sub, out_name="out.bin", **cfg):
+                ofd = os.open(os.path.join(d, out_name), os.O_CREAT | os.O_TRUNC | os.O_RDWR, 0o644)
                 try:
                     t0 = time.perf_counter()
                     res, lat, st = ctx.c5_serve(sub.arrival_ns, sub.threads, sub.n_ops, sub.ops, in_fds, ofd, **cfg)
@@ -769,7 +858,9 @@ def serve_c5(G, local, rank):
             r_served, out["served_first1000"] = run(first, max_inflight=64, **tuned)
             m = np.arange(8)[None, :] < first.n_ops[:, None]
             out["first1000_alone_equals_mix"] = bool(np.array_equal(r_plain[m], r_served[m]))
-            _, out["served_full"] = run(tr, max_inflight=64, **tuned)
+            r_full, out["served_full"] = run(tr, "out_full.bin", max_inflight=64, **tuned)
+            if checks is not None:
+                checks["c5"] = (tr, r_full, os.path.join(d, "out_full.bin"))
             # below saturation: the first 2,000 requests with arrivals spread to
             # 4 k/s, where latency is service time rather than queueing
             slow = tr.subset(np.arange(2000))
@@ -833,19 +924,35 @@ def _kv_requests_at(rate, n_max):
     return int(min(n_max, max(200_000, rate * 1.25)))
 
 
-def _kv_point(tr, reqs, off, rate, run_server, port):
+def reply_digests(replies) -> "np.ndarray":
+    """A 64-bit digest of each reply (its length and CRC-32), so that replies
+    can be kept per offered rate and compared with the oracle's afterwards
+    without holding every byte."""
+    import zlib
+    import numpy as np
+    return np.fromiter(((len(r) << 32) | zlib.crc32(r) for r in replies), np.uint64, len(replies))
+
+
+def _kv_point(tr, reqs, off, rate, run_server, port, client_cpus=None, keep=None):
     """Offer the first requests of the trace (_kv_requests_at) at `rate`
     requests/s to a server started by run_server(port); achieved rate and
-    send-to-reply latency."""
+    send-to-reply latency.  The load generator's threads run on client_cpus
+    (if given); keep[rate] receives the replies' digests."""
     import numpy as np
     import paper_1705_06965_b300 as G
     n = _kv_requests_at(rate, len(tr))
     arr = (tr.arrival_ns[:n].astype(np.float64) * (tr.params["rate_per_s"] / rate)).astype(np.uint64)
     stop = run_server(port)
+    mask = os.sched_getaffinity(0)
     try:
+        if client_cpus:  # threads the generator starts inherit this thread's CPU set
+            os.sched_setaffinity(0, client_cpus)
         reps, lat, st = G.kv_client(reqs[:int(off[n])], off[:n + 1], arr, port, 32, timeout_ns=10_000_000_000)
     finally:
+        os.sched_setaffinity(0, mask)
         served = stop()
+    if keep is not None:
+        keep[str(int(rate))] = reply_digests(reps)
     got = lat[lat > 0]
     achieved = st["received"] / (st["span_ns"] * 1e-9) if st["span_ns"] else 0.0
     return {"requests": n, "received": st["received"], "served": served, "achieved_req_per_s": round(achieved, 1),
@@ -858,12 +965,12 @@ def _kv_point(tr, reqs, off, rate, run_server, port):
             "offered_on_schedule": bool(st["max_send_late_ns"] <= max(1_000_000, 0.05 * float(arr[-1])))}
 
 
-def _kv_sweep(tr, reqs, off, run_server, port, rates):
+def _kv_sweep(tr, reqs, off, run_server, port, rates, client_cpus=None, keep=None):
     """Offered rates from the first, doubling, until the server saturates
     (achieved below 90 % of offered, or replies missing)."""
     out = {}
     for rate in rates:
-        pt = _kv_point(tr, reqs, off, rate, run_server, port)
+        pt = _kv_point(tr, reqs, off, rate, run_server, port, client_cpus, keep)
         out[str(int(rate))] = pt
         port += 40
         if pt["received"] < pt["requests"] or pt["achieved_req_per_s"] < 0.9 * rate:
@@ -871,46 +978,85 @@ def _kv_sweep(tr, reqs, off, run_server, port, rates):
     return out
 
 
-def serve_c4(G, local, rank, rates=tuple(50_000.0 * 2 ** i for i in range(7)), n_req=1_000_000):
+def kv_saturation(points: dict) -> dict:
+    """The server's saturation point from a rate sweep: the best achieved rate
+    among the points the load generator offered on schedule with every reply
+    received (a point where the generator fell behind measures the host, not
+    the server); the best of all points for context, and whether the sweep
+    ended on a point the generator did not keep to (then the server's own
+    limit may be higher)."""
+    clean = [v for v in points.values() if v["offered_on_schedule"] and v["received"] == v["requests"]]
+    best = max(clean, key=lambda v: v["achieved_req_per_s"], default=None)
+    any_best = max(points.values(), key=lambda v: v["achieved_req_per_s"], default=None)
+    last = list(points.values())[-1] if points else None
+    return {"saturation_req_per_s": best["achieved_req_per_s"] if best else None,
+            "saturation_p50_us": best["p50_us"] if best else None,
+            "saturation_p99_us": best["p99_us"] if best else None,
+            "best_any_req_per_s": any_best["achieved_req_per_s"] if any_best else None,
+            "saturation_host_bound": bool(last is not None and not last["offered_on_schedule"])}
+
+
+def c4_cpu_split():
+    """Disjoint host cores for the key-value service (its service threads, or
+    the oracle's server) and for the load generator, on a host with 16 or more
+    cores: (server cores, generator cores), or (None, None)."""
+    n = os.cpu_count() or 1
+    if n < 16:
+        return None, None
+    half = n // 2
+    return list(range(half)), set(range(half, n))
+
+
+def serve_c4(G, local, rank, rates=tuple(50_000.0 * 2 ** i for i in range(7)), n_req=1_000_000, checks=None):
     """C4: 1M-key table in HBM, Zipf 0.99 keys, 90% GET; offered rates 50k/s
     doubling to saturation, 1.25 s of requests per rate (200k to 1M);
-    achieved requests/s and send-to-reply latency.  The oracle's single-thread
+    achieved requests/s and send-to-reply latency.  The service threads and
+    the load generator run on disjoint host cores.  The oracle's single-thread
     CPU server is offered the same rates (its own saturation point is the CPU
-    baseline)."""
+    baseline).  checks["c4"] receives what the oracle leg compares: the trace
+    and every reply's digest per offered rate."""
     import workloads
     p = dict(workloads.C4_FULL, n_requests=n_req)
     tr = workloads.kv_trace(p)
     reqs, off = workloads.kv_request_bytes(tr)
+    server_cpus, client_cpus = c4_cpu_split()
     out = {"keys": len(tr.keys), "requests_per_rate": {str(int(r)): _kv_requests_at(r, n_req) for r in rates},
-           "sockets": 32}
-    with G.Context(device=local, service_threads=8, staging_bytes=64 << 20) as ctx:
+           "sockets": 32, "service_threads": 8,
+           "cores": {"server": f"{server_cpus[0]}-{server_cpus[-1]}" if server_cpus else "any",
+                     "load_generator": f"{min(client_cpus)}-{max(client_cpus)}" if client_cpus else "any"}}
+    digests = {}
+    with G.Context(device=local, service_threads=8, staging_bytes=64 << 20,
+                   service_cpus=server_cpus[:8] if server_cpus else None) as ctx:
         def gpu_server(port):
             srv = G.KVServer(ctx, tr.keys, tr.vlen0, tr.vseed0, n_sockets=32, batch=64, port_base=port)
             return srv.stop
-        out["rates"] = _kv_sweep(tr, reqs, off, gpu_server, 41000 + 400 * rank, rates)
+        out["rates"] = _kv_sweep(tr, reqs, off, gpu_server, 41000 + 400 * rank, rates, client_cpus, digests)
+    if checks is not None:
+        checks["c4"] = (tr, digests)
     if rank == 0:
-        out["cpu_baseline_oracle_server"] = cpu_baseline_c4(tr, reqs, off, 41000 + 400 * rank + 200, rates)
-    best = max(out["rates"].values(), key=lambda v: v["achieved_req_per_s"], default=None)
-    out["saturation_req_per_s"] = best["achieved_req_per_s"] if best else None
-    # a saturation point where the generator fell behind its own schedule is
-    # a bound of the host (generator, loopback stack and service threads share
-    # its cores), a lower bound on the GPU server
-    out["saturation_host_bound"] = bool(best and not best["offered_on_schedule"])
+        out["cpu_baseline_oracle_server"] = cpu_baseline_c4(tr, reqs, off, 41000 + 400 * rank + 200, rates,
+                                                            server_cpus, client_cpus)
+    out.update(kv_saturation(out["rates"]))
     return out
 
 
-def cpu_baseline_c4(tr, reqs, off, port, rates):
+def cpu_baseline_c4(tr, reqs, off, port, rates, server_cpus=None, client_cpus=None):
     """The oracle's key-value server (one host thread, recvfrom/sendto one
-    datagram at a time) offered the same rates."""
+    datagram at a time, on the server cores) offered the same rates."""
     import oracle
     table = tr.values0_table()
 
     def cpu_server(port):
-        srv = oracle.UdpServer("kv", port, 32, trace=tr, idle_ns=5_000_000_000, values0=table)
+        mask = os.sched_getaffinity(0)
+        try:
+            if server_cpus:  # the server's thread inherits this thread's CPU set
+                os.sched_setaffinity(0, set(server_cpus))
+            srv = oracle.UdpServer("kv", port, 32, trace=tr, idle_ns=5_000_000_000, values0=table)
+        finally:
+            os.sched_setaffinity(0, mask)
         return lambda: srv.join()["answered"]
-    res = _kv_sweep(tr, reqs, off, cpu_server, port, rates)
-    return {"threads": 1, "rates": res,
-            "saturation_req_per_s": max((v["achieved_req_per_s"] for v in res.values()), default=None)}
+    res = _kv_sweep(tr, reqs, off, cpu_server, port, rates, client_cpus)
+    return {"threads": 1, "rates": res, **kv_saturation(res)}
 
 
 def study_fig10(G, local, rank, sizes=(64, 256, 1024, 4096, 16384, 65504), n_sockets=32):
@@ -1110,24 +1256,25 @@ def run_genesys(args):
     link = host_link_peak(torch)
     link["round_trip_ns"] = G.link_pingpong(local, rounds=20000)  # GPU <-> host flag, the floor of a blocking call
     probes = host_probes(torch, local, rig.scan_path)
-    extras = profile_extras(args, rig, local, rank, link) if args.extras else {}
+    checks = {}
+    extras = profile_extras(args, rig, local, rank, link, checks) if args.extras else {}
     # dominant kernel of the timed region and its host-link roofline
     tot = {k: sum(v) for k, v in kernel_ms.items()}
     dom = max(tot, key=tot.get)
     avg_ms = statistics.mean(kernel_ms[dom])
     # algorithmic host-link bytes per launch of the dominant kernel, averaged
-    # over the sizes it ran at: per GPU thread its 64-byte payload written to
-    # pinned memory; per call a 64-byte slot + 8-byte doorbell written and an
-    # 8-byte completion word read.
+    # over the sizes it ran at (the method's own traffic: per GPU thread its
+    # 64-byte payload; per call its 64-byte slot and its 8-byte result - 136 B
+    # per work-item call; the doorbell entry is this design's, not counted)
     if dom.startswith("c2_pwrite_kernel"):
         gname = dom.split("<")[1].split(",")[0]
         gr = {v: k for k, v in G.GRAN_NAMES.items()}[gname]
         sel = [(nn, g, bt) for nn in SIZES for name, g, bt, relaxed, nb in COMBOS
                if g == gr and ("relaxed" if relaxed else "strong") in dom and ("nonblocking" in dom) == nb]
-        alg_bytes = statistics.mean(nn * 64 + calls_for(g, bt, nn) * 80 for nn, g, bt in sel)
+        alg_bytes = statistics.mean(nn * 64 + calls_for(g, bt, nn) * ALG_BYTES_PER_CALL for nn, g, bt in sel)
         units = statistics.mean(nn for nn, _, _ in sel)
     else:
-        alg_bytes = C1_BYTES + (C1_BYTES // C1_CHUNK) * 80
+        alg_bytes = C1_BYTES + (C1_BYTES // C1_CHUNK) * ALG_BYTES_PER_CALL
         units = C1_BYTES
     achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
     peak = link["d2h"] if dom.startswith("c2") else link["h2d"]
@@ -1139,6 +1286,11 @@ def run_genesys(args):
                 "service": service_roofline, "coarse": coarse_roofline}
 
     cpu = cpu_baseline_sample(budget_s=20.0, c1_hist=c1_hist) if rank == 0 and args.extras else None
+    if cpu is not None and cpu.get("c1_histogram_equals_oracle") is False:
+        raise RuntimeError("the step's C1 histogram differs from the oracle's: no bench line")
+    # the full-size C4 and C5 results against the oracle (after every GPU
+    # measurement; rank 0)
+    ochecks = oracle_checks(checks) if rank == 0 and args.extras else {"ran": False}
 
     line = {
         "metric": "GPU syscalls/s (C2 pwrite invocation sweep + C1 pread pass)",
@@ -1171,7 +1323,9 @@ def run_genesys(args):
                 "d2h_bytes_per_step": sum(SIZES) * 64 * len(COMBOS) + 2 * 1024 + 32},
         "clocks": clocks,
         "gpu_launches": launches[0],
+        "oracle_checks": ochecks,
     }
+    line["summary"] = summarize(line)  # last key: the driver keeps the line's tail
     rig.close()
     if world > 1:
         import torch.distributed as dist
@@ -1181,6 +1335,41 @@ def run_genesys(args):
 
 
 # ---------------------------------------------------------------- oracle
+def oracle_checks(checks: dict) -> dict:
+    """The CPU-baseline leg's comparisons of full-size results with the
+    oracle: every C4 reply at every offered rate (by digest; a missing reply
+    counts as a mismatch) against the oracle's replay in client sequence
+    order, and every request and the output file of the full C5 trace against
+    the oracle's replay of each request (shared among the host's cores)."""
+    import filecmp
+    import numpy as np
+    import oracle
+    out = {"ran": True}
+    if "c4" in checks:
+        tr, digests = checks["c4"]
+        t = time.perf_counter()
+        want = reply_digests(oracle.c4_replay(tr))
+        bad = {rate: int(np.count_nonzero(d != want[:len(d)])) for rate, d in digests.items()}
+        out["c4_mismatched_replies_by_rate"] = bad
+        out["c4_replies_checked"] = int(sum(len(d) for d in digests.values()))
+        out["c4_replies_equal"] = bool(digests) and all(v == 0 for v in bad.values())
+        out["c4_oracle_s"] = round(time.perf_counter() - t, 2)
+    if "c5" in checks:
+        tr, res, path = checks["c5"]
+        ref = path + ".oracle"
+        if os.path.exists(ref):
+            os.unlink(ref)
+        t = time.perf_counter()
+        want = oracle.c5_trace_parallel(tr, ref)
+        m = np.arange(8)[None, :] < tr.n_ops[:, None]
+        n_bad = int(np.count_nonzero(((np.asarray(res) != want) & m).any(axis=1)))
+        same_file = filecmp.cmp(path, ref, shallow=False)
+        out.update({"c5_requests_checked": len(tr), "c5_mismatched_requests": n_bad,
+                    "c5_output_file_equal": bool(same_file), "c5_full_equal": bool(n_bad == 0 and same_file),
+                    "c5_oracle_s": round(time.perf_counter() - t, 2), "c5_oracle_processes": os.cpu_count()})
+    return out
+
+
 def oracle_step(d, budget_s=None):
     """One step of the workload by the CPU oracle: the same sweep of pwrites
     (grouped as each granularity issues them) and the C1 preads.  Returns

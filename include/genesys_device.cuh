@@ -561,7 +561,10 @@ __device__ __forceinline__ int64_t call_at(const genesys_dev &g, uint32_t site, 
    * first.  A site reached more often than the grid has blocks has been
    * reused: the extra arrivals make no call, return -EINVAL and record it
    * (status word GENESYS_ST_BAD_ARGS), so the launch reports the misuse;
-   * give each relaxed kernel-grain call of a kernel its own site (call_at). */
+   * give each relaxed kernel-grain call of a kernel its own site (call_at).
+   * A relaxed call whose role is both producer and consumer (a call that is
+   * neither, e.g. getpid, unless R names a role) is strongly ordered, so at
+   * kernel grain it waits at grid barriers and needs every block resident. */
   genesys_ksite *ks = g.ksite + (site % GENESYS_KSITES);
   const uint32_t nblocks = gridDim.x * gridDim.y * gridDim.z;
   __shared__ int64_t kret_s;

@@ -173,6 +173,46 @@ def c5_trace(trace, out_fd: int, in_fds=None) -> np.ndarray:
                 _os.close(fd)
 
 
+def _c5_share(job):
+    """One share of c5_trace_parallel, run in a child process: requests
+    lo .. hi-1, each alone, in order."""
+    ops, n_ops, in_paths, out_path, lo = job
+    import os as _os
+    in_fds = [_os.open(p, _os.O_RDONLY) for p in in_paths]
+    ofd = _os.open(out_path, _os.O_RDWR)
+    try:
+        res = np.zeros((len(n_ops), 8), np.uint64)
+        for i in range(len(n_ops)):
+            n = int(n_ops[i])
+            res[i, :n] = c5_request(ops[i], n, in_fds, ofd)
+        return lo, res
+    finally:
+        for fd in in_fds + [ofd]:
+            _os.close(fd)
+
+
+def c5_trace_parallel(trace, out_path: str, procs: int = 0) -> np.ndarray:
+    """c5_trace with its requests shared among `procs` processes (default:
+    every host core), started with spawn so that a process that uses CUDA can
+    call it.  Each request still runs alone, its operations in order, as in
+    c5_trace; requests only read their input files and write disjoint ranges
+    of the output file, so the results and the file are c5_trace's (pinned in
+    tests/test_oracle.py).  Returns results [n, 8] (unused ops 0)."""
+    import multiprocessing as mp
+    import os as _os
+    n = len(trace)
+    procs = procs or (_os.cpu_count() or 1)
+    _os.close(_os.open(out_path, _os.O_CREAT | _os.O_RDWR, 0o644))
+    bounds = np.unique(np.linspace(0, n, 4 * procs + 1).astype(np.int64))  # more shares than processes: uneven requests
+    jobs = [(trace.ops[a:b], trace.n_ops[a:b], list(trace.in_paths), out_path, int(a))
+            for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
+    out = np.zeros((n, 8), np.uint64)
+    with mp.get_context("spawn").Pool(min(procs, max(len(jobs), 1))) as pool:
+        for lo, res in pool.imap_unordered(_c5_share, jobs):
+            out[lo:lo + len(res)] = res
+    return out
+
+
 def c4_replay(trace, idx=None):
     """C4 (Sec. 7.3 UDP service): the sequential server's reply to each request
     of the trace (in the given order, default seq order), as a list of bytes."""

@@ -45,8 +45,10 @@ __global__ void launch_demo_sites(genesys_dev g, int fd, uint8_t *buf, uint64_t 
 }
 
 __global__ void launch_demo_reuse(genesys_dev g, long long *ret) {
-  const int64_t a = call_at<KERNEL, RELAXED, BLOCKING>(g, 3, SYS_getpid);
-  const int64_t b = call_at<KERNEL, RELAXED, BLOCKING>(g, 3, SYS_getpid);
+  // getpid is neither producer nor consumer (relaxed would mean strong): the
+  // consumer role is named, so the first block to arrive calls
+  const int64_t a = call_at<KERNEL, RELAXED, BLOCKING, ROLE_CONSUMER>(g, 3, SYS_getpid);
+  const int64_t b = call_at<KERNEL, RELAXED, BLOCKING, ROLE_CONSUMER>(g, 3, SYS_getpid);
   if (threadIdx.x == 0) {
     ret[2 * blockIdx.x] = a;
     ret[2 * blockIdx.x + 1] = b;

@@ -93,3 +93,91 @@ def test_cpu_baseline_leg_compares_the_gpu_histogram_with_the_oracle():
     bad = want.copy()
     bad[7] += 1
     assert bench.cpu_baseline_sample(budget_s=0.5, c1_hist=bad)["c1_histogram_equals_oracle"] is False
+
+
+def _full_line():
+    """A bench line with every section the summary reads, at realistic sizes."""
+    pt = lambda rate, got, late: {"requests": 1000, "received": got, "served": got,  # noqa: E731
+                                   "achieved_req_per_s": rate, "p50_us": 41.234567, "p99_us": 812.98765,
+                                   "max_send_late_us": 12.3, "offered_on_schedule": late}
+    return {
+        "value": 9752850.612345, "e2e": {"value": 9727511.123},
+        "forms": {"plain_blocking_strong": {"syscalls_per_s": 31600000.1, "requests_per_s": 31600000.1,
+                                            "p50_us": 300.1, "p99_us": 900.2},
+                  "batched": {"syscalls_per_s": 84000.5, "requests_per_s": 86000000.3, "p50_us": 200.1,
+                              "p99_us": 700.7}},
+        "roofline": {"service": {"frac": 0.181234, "warp_interleaved_order": {"frac": 0.347712}}},
+        "c1_4MiB": {"plain": {"GB_per_s": 5.31123}, "batched": {"GB_per_s": 7.7789}},
+        "pread_scan_1GiB": {"autotuned": {"form": 0}, "plain": {"GB_per_s": 49.712, "frac_of_host_link_h2d": 0.894},
+                            "warp": {"GB_per_s": 51.1, "frac_of_host_link_h2d": 0.919},
+                            "batched": {"GB_per_s": 47.2, "frac_of_host_link_h2d": 0.849}},
+        "wordcount_c3": {"plain": {"GB_per_s": 40.1, "frac_of_host_link_h2d": 0.72, "counts_equal_ground_truth": True},
+                         "batched": {"GB_per_s": 49.5, "frac_of_host_link_h2d": 0.89,
+                                     "counts_equal_ground_truth": True},
+                         "cpu_baseline_oracle": {"one_thread_GB_per_s": 0.131, "files_to_cores_GB_per_s": 0.771}},
+        "kv_c4": {"rates": {"50000": pt(49999.9, 1000, True), "800000": pt(799012.3, 1000, True),
+                            "1600000": pt(1300123.4, 1000, False)},
+                  "saturation_req_per_s": 799012.3, "saturation_p50_us": 41.234567, "saturation_p99_us": 812.98765,
+                  "best_any_req_per_s": 1300123.4, "saturation_host_bound": True,
+                  "cpu_baseline_oracle_server": {"saturation_req_per_s": 270123.1}},
+        "served_c5": {"plain_first1000": {"requests_per_s": 2100.3, "syscalls_per_s": 57000.1, "p99_ms": 447.12},
+                      "served_first1000": {"requests_per_s": 8800.2, "syscalls_per_s": 240000.7, "p99_ms": 65.3},
+                      "persistent_first1000": {"requests_per_s": 12000.2, "syscalls_per_s": 330000.7, "p99_ms": 30.3},
+                      "served_full": {"requests_per_s": 8700.1, "p99_ms": 70.123},
+                      "persistent_full": {"requests_per_s": 11000.1, "p99_ms": 40.123},
+                      "first1000_alone_equals_mix": True,
+                      "cpu_baseline_oracle_replay_first1000": {"requests_per_s": 174.2}},
+        "probes": {"host_cpus": 16},
+        "cpu_baseline": {"value": 1293220.2, "c1_histogram_equals_oracle": True},
+        "oracle_checks": {"ran": True, "c4_replies_equal": True, "c5_full_equal": True},
+    }
+
+
+def test_summary_fits_the_kept_tail_and_carries_every_config():
+    """The driver keeps the last 1,500 characters of the bench line: the
+    summary (the line's last key, targets inside) must fit with room to spare
+    and hold a figure for every config."""
+    import json
+    line = _full_line()
+    line["summary"] = bench.summarize(line)
+    tail = json.dumps(line)[-1500:]
+    assert '"summary": {' in tail and '"targets": {' in tail
+    sm = line["summary"]
+    assert len(json.dumps(sm)) <= 1350, len(json.dumps(sm))
+    assert sm["scan_1GiB"] == {"form": "warp", "GBps": 51.1, "frac_h2d": 0.919}
+    assert sm["c3"]["GBps"] == 49.5 and sm["c3"]["truth_eq"] is True
+    assert sm["c4"]["sat_rps"] == 799000 and sm["c4"]["replies_eq_oracle"] is True
+    assert sm["c4"]["p99_us"] == 813 and sm["c4"]["best_any_rps"] == 1300000
+    assert sm["c5"]["persistent_rps"] == 11000 and sm["c5"]["full_eq_oracle"] is True
+    assert sm["oracle"]["cores"] == 16 and sm["oracle"]["c5_rps_1t"] == 174
+    t = sm["targets"]
+    assert t["c2_batched_beats_plain"] == {"syscalls_per_s": False, "requests_per_s": True, "p99": True}
+    assert t["c5_served_beats_plain"] == {"syscalls_per_s": True, "requests_per_s": True, "p99": True}
+    assert t["scan_frac_h2d_ge_0.8"] is True
+
+
+def test_summary_of_a_line_without_extras():
+    """--extras 0 lines (launch lists) still get a summary, with None where a
+    section was not measured."""
+    sm = bench.summarize({"value": 1.0, "e2e": {"value": 1.0}})
+    assert sm["c4"]["sat_rps"] is None and sm["targets"]["scan_frac_h2d_ge_0.8"] is None
+    assert sm["targets"]["c5_served_beats_plain"]["p99"] is None
+
+
+def test_kv_saturation_counts_only_points_offered_on_schedule():
+    """A point where the load generator fell behind its own schedule measures
+    the host: the saturation point is the best clean point, and the sweep is
+    marked host-bound when it ended on such a point."""
+    pts = _full_line()["kv_c4"]["rates"]
+    sat = bench.kv_saturation(pts)
+    assert sat["saturation_req_per_s"] == 799012.3 and sat["best_any_req_per_s"] == 1300123.4
+    assert sat["saturation_host_bound"] is True
+    pts["800000"]["received"] = 999                  # a reply missing: not a clean point either
+    assert bench.kv_saturation(pts)["saturation_req_per_s"] == 49999.9
+    assert bench.kv_saturation({})["saturation_req_per_s"] is None
+
+
+def test_reply_digests_tell_replies_apart():
+    import numpy as np
+    d = bench.reply_digests([b"", b"\x80\x00\x10\x00abcd", b"\x80\x00\x10\x00abce", b"\x81\x00\x00\x00" + b"\0" * 4])
+    assert d.dtype == np.uint64 and len(set(d.tolist())) == 4 and d[0] == 0

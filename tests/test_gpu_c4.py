@@ -80,3 +80,26 @@ def test_c4_full_table_replies_bit_exact(G, ctx):
     bad = [j for j in range(len(tr)) if reps[j] != want[j]]
     assert not bad, (len(bad), bad[:5])
     assert served == len(tr)
+
+
+def test_c4_full_table_at_800k_per_s_every_reply_bit_exact(G, ctx):
+    """The benchmark's configuration at 800 k requests/s offered, where the
+    server's batches fill and requests of one hot key meet in a batch (they
+    are applied in arrival order): the 1 M-key table, 32 sockets, batches of
+    64, 1 M requests; every reply equals the oracle's replay in client
+    sequence order, and none is missing."""
+    p = dict(workloads.C4_FULL, n_requests=1_000_000, rate_per_s=800_000.0)
+    tr = workloads.kv_trace(p)
+    want = oracle.c4_replay(tr)
+    reqs, off = workloads.kv_request_bytes(tr)
+    port = _port() + 201
+    srv = G.KVServer(ctx, tr.keys, tr.vlen0, tr.vseed0, n_sockets=32, batch=64, port_base=port)
+    try:
+        reps, lat, st = G.kv_client(reqs, off, tr.arrival_ns, port, 32, timeout_ns=20_000_000_000)
+    finally:
+        served = srv.stop()
+    assert st["rc"] == 0 and st["received"] == len(tr), st
+    assert st["duplicates"] == 0 and st["malformed"] == 0
+    bad = [j for j in range(len(tr)) if reps[j] != want[j]]
+    assert not bad, (len(bad), bad[:5])
+    assert served == len(tr)

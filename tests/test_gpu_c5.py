@@ -112,32 +112,17 @@ def test_c5_rejects_oversized_request(ctx, G, trace, tmp_path):
     assert e.value.code == G.EINVAL
 
 
-def test_c5_full_trace_sampled(ctx, tmp_path):
+def test_c5_full_trace_equals_oracle(ctx, tmp_path):
     """The full 10,000-request trace, served the way the benchmark serves it
-    (64 in flight, graph relaunch, arrivals honoured): 150 requests drawn with
-    a fixed seed are replayed one by one by the oracle, and their results and
-    the output bytes of their pwrites must match.  Requests write disjoint
-    ranges, so each sampled one is checked on its own."""
+    (64 in flight, graph relaunch, arrivals honoured): every request's results
+    and the whole output file equal the oracle's replay of every request, one
+    at a time (shared among host processes: requests are independent)."""
     tr = workloads.c5_trace(workloads.C5_FULL)
     res, lat, st, out = serve(ctx, tr, str(tmp_path / "full.bin"), max_inflight=64)
     assert st["requests"] == len(tr) and np.all(lat > 0)
-    pick = np.sort(np.random.default_rng(0x5EED0C5).choice(len(tr), 150, replace=False))
-    in_fds = [os.open(p, os.O_RDONLY) for p in tr.in_paths]
     ref_path = str(tmp_path / "ref.bin")
-    ref_fd = os.open(ref_path, os.O_CREAT | os.O_TRUNC | os.O_RDWR, 0o644)
-    try:
-        for r in pick:
-            n = int(tr.n_ops[r])
-            want = oracle.c5_request(tr.ops[r], n, in_fds, ref_fd)
-            assert np.array_equal(res[r, :n], want), r
-    finally:
-        for fd in in_fds:
-            os.close(fd)
-        os.close(ref_fd)
-    ref = open(ref_path, "rb").read()
-    for r in pick:
-        for k in range(int(tr.n_ops[r])):
-            op = tr.ops[r][k]
-            if int(op["kind"]) == 1:
-                a, b = int(op["out_off"]), int(op["out_off"]) + int(op["len"])
-                assert out[a:b] == ref[a:b], (r, k)
+    want = oracle.c5_trace_parallel(tr, ref_path)
+    m = _mask(tr)
+    bad = np.where((res != want) & m)[0]
+    assert len(bad) == 0, (len(np.unique(bad)), np.unique(bad)[:5])
+    assert out == open(ref_path, "rb").read()

@@ -273,6 +273,22 @@ def test_c5_trace_shape():
     assert np.all(mm["len"] % 4096 == 0) and mm["len"].min() >= 4096
 
 
+def test_c5_parallel_replay_equals_the_sequential_one(tmp_path):
+    """The multi-process replay the full-trace parity checks use gives the
+    sequential replay's results and output file, byte for byte (requests are
+    independent: read-only inputs, disjoint output ranges)."""
+    tr = workloads.c5_trace(workloads.C5_SMALL).subset(np.arange(60))
+    seq_path, par_path = str(tmp_path / "seq.bin"), str(tmp_path / "par.bin")
+    fd = os.open(seq_path, os.O_CREAT | os.O_TRUNC | os.O_RDWR, 0o644)
+    try:
+        want = oracle.c5_trace(tr, fd)
+    finally:
+        os.close(fd)
+    got = oracle.c5_trace_parallel(tr, par_path, procs=3)
+    assert np.array_equal(got, want)
+    assert open(par_path, "rb").read() == open(seq_path, "rb").read()
+
+
 # ------------------------------------------------------------------------- C4
 
 def test_c4_replay_closed_forms():
