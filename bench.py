@@ -853,19 +853,31 @@ def serve_c5(G, local, rank, checks=None):
             finally:
                 os.close(ofd)
             out["autotuned"] = tuned
+            # the persistent executor form: one kernel serves every request
+            ofd = os.open(os.path.join(d, "tune_p.bin"), os.O_CREAT | os.O_RDWR, 0o644)
+            try:
+                tuned_p = autotune.tune_serve(local, ctx, tr, in_fds, ofd, extra={"persistent": 1})
+            finally:
+                os.close(ofd)
+            out["autotuned_persistent"] = tuned_p
             first = tr.subset(np.arange(1000))
             r_plain, out["plain_first1000"] = run(first, max_inflight=1, use_graphs=0)
             r_served, out["served_first1000"] = run(first, max_inflight=64, **tuned)
+            r_pers, out["persistent_first1000"] = run(first, max_inflight=64, persistent=1, **tuned_p)
             m = np.arange(8)[None, :] < first.n_ops[:, None]
-            out["first1000_alone_equals_mix"] = bool(np.array_equal(r_plain[m], r_served[m]))
+            out["first1000_alone_equals_mix"] = bool(np.array_equal(r_plain[m], r_served[m]) and
+                                                     np.array_equal(r_plain[m], r_pers[m]))
             r_full, out["served_full"] = run(tr, "out_full.bin", max_inflight=64, **tuned)
+            r_pfull, out["persistent_full"] = run(tr, "out_pfull.bin", max_inflight=64, persistent=1, **tuned_p)
             if checks is not None:
-                checks["c5"] = (tr, r_full, os.path.join(d, "out_full.bin"))
+                checks["c5"] = (tr, {"served_full": (r_full, os.path.join(d, "out_full.bin")),
+                                     "persistent_full": (r_pfull, os.path.join(d, "out_pfull.bin"))})
             # below saturation: the first 2,000 requests with arrivals spread to
             # 4 k/s, where latency is service time rather than queueing
             slow = tr.subset(np.arange(2000))
             slow.arrival_ns = (slow.arrival_ns.astype(np.float64) * (tr.params["rate_per_s"] / 4000.0)).astype(np.uint64)
             _, out["served_first2000_at_4k_per_s"] = run(slow, max_inflight=64, **tuned)
+            _, out["persistent_first2000_at_4k_per_s"] = run(slow, max_inflight=64, persistent=1, **tuned_p)
         if rank == 0:
             try:
                 out["cpu_baseline_oracle_replay_first1000"] = cpu_baseline_c5(first, in_fds, d, r_served)
@@ -1355,17 +1367,19 @@ def oracle_checks(checks: dict) -> dict:
         out["c4_replies_equal"] = bool(digests) and all(v == 0 for v in bad.values())
         out["c4_oracle_s"] = round(time.perf_counter() - t, 2)
     if "c5" in checks:
-        tr, res, path = checks["c5"]
-        ref = path + ".oracle"
+        tr, runs = checks["c5"]
+        ref = os.path.join(os.path.dirname(next(iter(runs.values()))[1]), "out_full.oracle")
         if os.path.exists(ref):
             os.unlink(ref)
         t = time.perf_counter()
         want = oracle.c5_trace_parallel(tr, ref)
         m = np.arange(8)[None, :] < tr.n_ops[:, None]
-        n_bad = int(np.count_nonzero(((np.asarray(res) != want) & m).any(axis=1)))
-        same_file = filecmp.cmp(path, ref, shallow=False)
-        out.update({"c5_requests_checked": len(tr), "c5_mismatched_requests": n_bad,
-                    "c5_output_file_equal": bool(same_file), "c5_full_equal": bool(n_bad == 0 and same_file),
+        per = {}
+        for name, (res, path) in runs.items():
+            n_bad = int(np.count_nonzero(((np.asarray(res) != want) & m).any(axis=1)))
+            per[name] = {"mismatched_requests": n_bad, "output_file_equal": bool(filecmp.cmp(path, ref, shallow=False))}
+        out.update({"c5_requests_checked": len(tr), "c5_by_form": per,
+                    "c5_full_equal": all(v["mismatched_requests"] == 0 and v["output_file_equal"] for v in per.values()),
                     "c5_oracle_s": round(time.perf_counter() - t, 2), "c5_oracle_processes": os.cpu_count()})
     return out
 

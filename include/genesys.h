@@ -420,9 +420,16 @@ int genesys_c3_wordcount_noalloc(genesys_ctx *ctx, const int32_t *fds, const uin
  * syscall slots, staging bytes and HBM bytes are free; launches them on
  * n_streams streams (launch slot i on stream i mod n_streams; as relaunched
  * single-kernel CUDA graphs if use_graphs);
- * retires them when their completion event fires.  Outputs (host arrays):
- * results[n_req * 8] (negative errno on failure), latency_ns[n_req]
- * (retirement - arrival); *stats if non-NULL. */
+ * retires them when their completion event fires.  With cfg.persistent, one
+ * executor kernel of persistent_blocks blocks (block_threads each) runs for
+ * the whole trace instead: admitting a request appends its blocks as work
+ * units (request, block) to a ring in pinned host memory, the executor's
+ * blocks take units in ring order and run them, the request's last block
+ * writes its results to pinned memory, and the loop retires the request when
+ * it sees them; uneven requests share the one launch and no launch is made
+ * per request (max_inflight <= 65534; n_streams and use_graphs do not apply).
+ * Outputs (host arrays): results[n_req * 8] (negative errno on failure),
+ * latency_ns[n_req] (retirement - arrival); *stats if non-NULL. */
 #define GENESYS_C5_MAX_OPS 8u
 #define GENESYS_C5_MAX_PARTS 256u
 #define GENESYS_C5_PREAD 0u
@@ -455,6 +462,9 @@ typedef struct genesys_serve_config {
   uint32_t reserve_mmaps;   /* 1: map and register the trace's mmap regions before
                                the first request (genesys_mmap_reserve)            */
   uint64_t timeout_ns;      /* give up (GENESYS_ETIMEDOUT) after this long         */
+  uint32_t persistent;      /* 1: one persistent executor kernel serves the whole
+                               trace (below); 0: one kernel launch per request     */
+  uint32_t persistent_blocks; /* executor blocks (0: as many as can be resident)   */
 } genesys_serve_config;
 
 typedef struct genesys_serve_stats {

@@ -481,6 +481,61 @@ __device__ __forceinline__ int64_t site_reused(const genesys_dev &g) {
   return -22;
 }
 
+/* Relaxed kernel-grain call over `nblocks` blocks at site record `ks` (every
+ * thread of each block takes part).  producer: every block arrives and the
+ * last one to arrive calls, so no block ever waits for another (no deadlock
+ * whatever the number of blocks); only its caller receives the result.
+ * consumer: the first block to arrive calls and the others wait for its
+ * result (the caller is running by construction, so they cannot deadlock);
+ * every thread receives it. */
+__device__ __forceinline__ int64_t kernel_relaxed(const genesys_dev &g, genesys_ksite *ks, uint32_t nblocks,
+                                                  bool producer, uint32_t nr, uint32_t flags, bool wait, uint64_t a0,
+                                                  uint64_t a1, uint64_t a2, uint64_t a3, uint64_t a4, uint64_t a5) {
+  __shared__ int64_t kret_s;
+  if (producer) {
+    __syncthreads();
+    int64_t r = 0;
+    if (is_block_leader()) {
+      __threadfence_system();
+      const uint32_t arrived = atomicAdd(&ks->arrive, 1u);
+      if (arrived == nblocks - 1) {
+        __threadfence_system();
+        r = single_call(g, nr, flags, wait, a0, a1, a2, a3, a4, a5);
+      } else if (arrived >= nblocks) {
+        r = site_reused(g);
+      }
+    }
+    return r;
+  }
+  if (is_block_leader()) {
+    int64_t r;
+    const uint32_t ticket = atomicAdd(&ks->ticket, 1u);
+    if (ticket == 0u) {
+      r = single_call(g, nr, flags, wait, a0, a1, a2, a3, a4, a5);
+      ks->ret = r;
+      __threadfence();
+      st_release_gpu(&ks->flag, 1u);
+    } else if (ticket >= nblocks) {
+      r = site_reused(g);
+    } else {
+      const uint64_t t0 = now_ns();
+      uint32_t ns = 64;
+      r = 0;
+      while (ld_acquire_gpu(&ks->flag) == 0u) {
+        if (expired(g, t0)) { note_error(g, -kETIMEDOUT); r = -kETIMEDOUT; break; }
+        __nanosleep(ns);
+        ns = ns < 2048 ? ns * 2 : ns;
+      }
+      if (r == 0) r = *(volatile int64_t *)&ks->ret;
+    }
+    kret_s = r;
+  }
+  __syncthreads();
+  const int64_t r = kret_s;
+  __syncthreads();
+  return r;
+}
+
 /* ------------------------------------------------------------- the call */
 
 template <int G, int O, int B, int R = ROLE_AUTO>
@@ -567,7 +622,6 @@ __device__ __forceinline__ int64_t call_at(const genesys_dev &g, uint32_t site, 
    * kernel grain it waits at grid barriers and needs every block resident. */
   genesys_ksite *ks = g.ksite + (site % GENESYS_KSITES);
   const uint32_t nblocks = gridDim.x * gridDim.y * gridDim.z;
-  __shared__ int64_t kret_s;
   if (pre && post) {
     /* strong: grid barriers before and after (cooperative launch only) */
     if (!grid_sync(g)) return -kETIMEDOUT;
@@ -578,52 +632,28 @@ __device__ __forceinline__ int64_t call_at(const genesys_dev &g, uint32_t site, 
     if (!grid_sync(g)) return -kETIMEDOUT;
     return *(volatile int64_t *)&ks->ret;
   }
-  if (pre) {
-    /* relaxed producer: every CTA arrives; the last one to arrive calls, so no
-     * CTA ever waits for another (no deadlock whatever the grid size) */
-    __syncthreads();
-    int64_t r = 0;
-    if (is_block_leader()) {
-      __threadfence_system();
-      const uint32_t arrived = atomicAdd(&ks->arrive, 1u);
-      if (arrived == nblocks - 1) {
-        __threadfence_system();
-        r = single_call(g, nr, flags, B == BLOCKING, a0, a1, a2, a3, a4, a5);
-      } else if (arrived >= nblocks) {
-        r = site_reused(g);
-      }
-    }
-    return r;
-  }
-  /* relaxed consumer: the first CTA to arrive calls; the others wait for its
-   * result (the caller is resident by construction, so they cannot deadlock) */
-  if (is_block_leader()) {
-    int64_t r;
-    const uint32_t ticket = atomicAdd(&ks->ticket, 1u);
-    if (ticket == 0u) {
-      r = single_call(g, nr, flags, B == BLOCKING, a0, a1, a2, a3, a4, a5);
-      ks->ret = r;
-      __threadfence();
-      st_release_gpu(&ks->flag, 1u);
-    } else if (ticket >= nblocks) {
-      r = site_reused(g);
-    } else {
-      const uint64_t t0 = now_ns();
-      uint32_t ns = 64;
-      r = 0;
-      while (ld_acquire_gpu(&ks->flag) == 0u) {
-        if (expired(g, t0)) { note_error(g, -kETIMEDOUT); r = -kETIMEDOUT; break; }
-        __nanosleep(ns);
-        ns = ns < 2048 ? ns * 2 : ns;
-      }
-      if (r == 0) r = *(volatile int64_t *)&ks->ret;
-    }
-    kret_s = r;
-  }
-  __syncthreads();
-  const int64_t r = kret_s;
-  __syncthreads();
-  return r;
+  return kernel_relaxed(g, ks, nblocks, pre, nr, flags, B == BLOCKING, a0, a1, a2, a3, a4, a5);
+}
+
+/* A relaxed kernel-grain call over a group of `nblocks` thread blocks that
+ * need not be the launch's grid - the virtual grid of a request that a
+ * persistent kernel runs on whichever of its blocks pick it up - with its own
+ * call-site record `ks` (zeroed before the group's first block arrives, and
+ * by the group before it is used for another).  Every block of the group
+ * makes the call once, with all its threads; the rules are call_at's relaxed
+ * kernel grain: a producer (R = ROLE_PRODUCER) is issued by the last block to
+ * arrive and only its caller waits, a consumer (ROLE_CONSUMER) by the first
+ * block to arrive and every block receives the result.  Neither waits for a
+ * block that has not started, so the group may be larger than what is
+ * resident.  Arrivals beyond nblocks are a reused site: -EINVAL. */
+template <int B, int R>
+__device__ __forceinline__ int64_t call_vgrid(const genesys_dev &g, genesys_ksite *ks, uint32_t nblocks, uint32_t nr,
+                                              uint64_t a0 = 0, uint64_t a1 = 0, uint64_t a2 = 0, uint64_t a3 = 0,
+                                              uint64_t a4 = 0, uint64_t a5 = 0) {
+  static_assert(R == ROLE_PRODUCER || R == ROLE_CONSUMER, "call_vgrid: a producer or a consumer call");
+  const uint32_t flags = (B == BLOCKING ? GENESYS_REQ_BLOCKING : 0u) | (GENESYS_GRAN_KERNEL << GENESYS_REQ_GRAN_SHIFT) |
+                         GENESYS_REQ_RELAXED;
+  return kernel_relaxed(g, ks, nblocks, R == ROLE_PRODUCER, nr, flags, B == BLOCKING, a0, a1, a2, a3, a4, a5);
 }
 
 /* Warp grain with request coalescing.  Every active lane brings its own

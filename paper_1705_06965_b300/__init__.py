@@ -76,7 +76,8 @@ class ServeConfig(ctypes.Structure):
                 ("slot_budget", ctypes.c_uint32), ("block_threads", ctypes.c_uint32), ("min_part", ctypes.c_uint32),
                 ("use_graphs", ctypes.c_uint32), ("pread_to_hbm", ctypes.c_uint32),
                 ("honor_arrivals", ctypes.c_uint32), ("reserve_mmaps", ctypes.c_uint32),
-                ("timeout_ns", ctypes.c_uint64)]
+                ("timeout_ns", ctypes.c_uint64), ("persistent", ctypes.c_uint32),
+                ("persistent_blocks", ctypes.c_uint32)]
 
 
 class ServeStats(ctypes.Structure):

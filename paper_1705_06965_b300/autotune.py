@@ -205,13 +205,18 @@ def tune_context(device: int, step: Callable, tuner: Autotuner | None = None, fo
 
 
 def tune_serve(device: int, ctx, trace, in_fds, out_fd: int, tuner: Autotuner | None = None, force: bool = False,
-               min_parts=(4096, 16384, 65536), block_threads=(256, 1024), n_requests: int = 300):
+               min_parts=(4096, 16384, 65536), block_threads=(256, 1024), n_requests: int = 300,
+               extra: dict | None = None):
     """C5 serving: the granularity of the request kernels' pread/pwrite calls
     (min_part: bytes per work-group call) x threads per block, measured as the
-    makespan of the trace's first n_requests served back to back."""
+    makespan of the trace's first n_requests served back to back.  extra:
+    serve settings every candidate shares (e.g. persistent=1 tunes the
+    executor form on its own)."""
     import numpy as np
     tuner = tuner or Autotuner()
-    key = tuner.key("serve", requests=n_requests, min_parts=len(min_parts), block_threads=len(block_threads))
+    extra = dict(extra or {})
+    key = tuner.key("serve", requests=n_requests, min_parts=len(min_parts), block_threads=len(block_threads),
+                    **{k: int(v) for k, v in sorted(extra.items())})
     hit = None if force else tuner.lookup(key)
     if hit:
         return hit
@@ -219,7 +224,7 @@ def tune_serve(device: int, ctx, trace, in_fds, out_fd: int, tuner: Autotuner | 
 
     def run(cfg):
         _, _, st = ctx.c5_serve(sub.arrival_ns, sub.threads, sub.n_ops, sub.ops, in_fds, out_fd, honor_arrivals=0,
-                                **cfg)
+                                **cfg, **extra)
         return st["makespan_ns"] * 1e-9
 
     best, _ = tuner.tune(key, grid(min_part=min_parts, block_threads=block_threads), run, repeats=1, force=True)

@@ -82,14 +82,14 @@ __host__ __device__ __forceinline__ uint64_t region_bytes(uint32_t parts, uint64
   return ((uint64_t)parts * share + 16 + 255) & ~uint64_t(255);
 }
 
-// One request.  Block b handles part b of each pread/pwrite; mmap'd regions
-// are filled and checksummed by all threads of the kernel.
-__global__ void __launch_bounds__(1024) c5_request_kernel(genesys_dev g, const genesys_c5_op *ops, uint32_t n_ops,
-                                                          const int32_t *in_fds, int32_t out_fd, uint8_t *staging,
-                                                          uint8_t *landing, unsigned long long *results,
-                                                          uint32_t min_part, uint32_t pread_to_hbm) {
-  const uint32_t nb = gridDim.x;
-  const uint32_t b = blockIdx.x;
+// Block b of the nb blocks that run one request: it handles part b of each
+// pread/pwrite; mmap'd regions are filled and checksummed by all threads of
+// the nb blocks.  ks: the request's kernel-grain call sites (2 per op).  The
+// blocks are the launch's grid (one kernel per request) or a virtual grid run
+// by the persistent executor's blocks.
+__device__ void c5_run_block(const genesys_dev &g, const genesys_c5_op *ops, uint32_t n_ops, const int32_t *in_fds,
+                             int32_t out_fd, uint8_t *staging, uint8_t *landing, unsigned long long *results,
+                             uint32_t min_part, uint32_t pread_to_hbm, uint32_t b, uint32_t nb, genesys_ksite *ks) {
   uint64_t st_off = 0, land_off = 0;  // this operation's region
   for (uint32_t k = 0; k < n_ops; ++k) {
     const genesys_c5_op op = ops[k];
@@ -168,9 +168,9 @@ __global__ void __launch_bounds__(1024) c5_request_kernel(genesys_dev g, const g
       // mmap at kernel grain (consumer: the first block to arrive calls, the
       // others wait for its result), fill + checksum by every thread, munmap at
       // kernel grain (producer: the last block to arrive calls)
-      const int64_t p = call_at<KERNEL, RELAXED, BLOCKING, ROLE_CONSUMER>(
-          g, 2 * k, SYS_mmap, 0, op.len, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS | kMapUninitialized,
-          (uint64_t)-1, 0);
+      const int64_t p = call_vgrid<BLOCKING, ROLE_CONSUMER>(
+          g, ks + 2 * k, nb, SYS_mmap, 0, op.len, PROT_READ | PROT_WRITE,
+          MAP_PRIVATE | MAP_ANONYMOUS | kMapUninitialized, (uint64_t)-1, 0);
       if (p < 0 || p == 0) {
         if (b == 0 && threadIdx.x == 0) atomicExch(&results[GENESYS_C5_MAX_OPS + k], (unsigned long long)p);
         continue;
@@ -190,10 +190,129 @@ __global__ void __launch_bounds__(1024) c5_request_kernel(genesys_dev g, const g
       }
       s = block_sum(s);
       if (threadIdx.x == 0) atomicAdd(&results[k], (unsigned long long)s);
-      const int64_t u = call_at<KERNEL, RELAXED, BLOCKING, ROLE_PRODUCER>(g, 2 * k + 1, SYS_munmap, (uint64_t)p,
-                                                                          op.len);
+      const int64_t u = call_vgrid<BLOCKING, ROLE_PRODUCER>(g, ks + 2 * k + 1, nb, SYS_munmap, (uint64_t)p, op.len);
       if (u < 0 && threadIdx.x == 0) atomicExch(&results[GENESYS_C5_MAX_OPS + k], (unsigned long long)u);
     }
+  }
+}
+
+// One request as its own kernel: block b of the grid is block b of the request.
+__global__ void __launch_bounds__(1024) c5_request_kernel(genesys_dev g, const genesys_c5_op *ops, uint32_t n_ops,
+                                                          const int32_t *in_fds, int32_t out_fd, uint8_t *staging,
+                                                          uint8_t *landing, unsigned long long *results,
+                                                          uint32_t min_part, uint32_t pread_to_hbm) {
+  c5_run_block(g, ops, n_ops, in_fds, out_fd, staging, landing, results, min_part, pread_to_hbm, blockIdx.x, gridDim.x,
+               g.ksite);
+}
+
+// ------------------------------------------------------ persistent executor
+// One kernel serves the whole trace: its blocks pop work units - block b of
+// the request in launch slot si - from a ring the serve loop appends to as it
+// admits requests, and run c5_run_block for them.  Requests of every size
+// share the launch; a request's blocks run on whichever executor blocks take
+// its units, so blocks of many requests are on the device at once.
+//
+// Host-written, pinned: the slot records (a request's operations and
+// regions, written before its units are published) and the unit ring (entry
+// = (position + 1):32 | slot:16 | block:16, release-stored by the host; the
+// device acquires it).  Device memory: the ring's consumer position, each
+// slot's results, call sites and count of finished blocks.  Device-written,
+// pinned: each slot's results and the sequence number of its finished request
+// (release-stored last), which the serve loop polls to retire requests.
+constexpr uint32_t kExecStop = 0xFFFFu;  // unit slot field: the block leaves
+
+struct alignas(64) ExecSlot {  // written by the host before the slot's units
+  uint32_t n_ops, nb;
+  uint64_t st_off, hbm_off;
+  uint64_t seq;
+  genesys_c5_op ops[GENESYS_C5_MAX_OPS];
+};
+
+struct alignas(64) ExecDone {  // written by the request's last block
+  unsigned long long results[2 * GENESYS_C5_MAX_OPS];
+  uint64_t seq;
+};
+
+// Wait (one thread) for ring entry `u`; returns it, or 0 if `deadline_ns`
+// passed first (then the executor records -ETIMEDOUT in *err).
+__device__ uint64_t exec_wait_unit(const uint64_t *units, uint32_t mask, uint32_t u, uint64_t deadline_ns,
+                                   int32_t *err) {
+  const uint64_t t0 = now_ns();
+  uint32_t ns = 256;
+  for (;;) {
+    const uint64_t e = ld_acquire_sys(units + (u & mask));
+    if ((uint32_t)(e >> 32) == u + 1u) return e;
+    if (now_ns() - t0 > deadline_ns) {
+      atomicCAS(err, 0, -(int32_t)kETIMEDOUT);
+      return 0;
+    }
+    __nanosleep(ns);
+    ns = ns < 32768 ? ns * 2 : ns;  // idle executor blocks poll the host rarely
+  }
+}
+
+__global__ void __launch_bounds__(1024) c5_executor_kernel(
+    genesys_dev g, const ExecSlot *slots, ExecDone *done, const uint64_t *units, uint32_t unit_mask, uint32_t *head,
+    unsigned long long *results, genesys_ksite *ksites, uint32_t *finished, const int32_t *in_fds, int32_t out_fd,
+    uint8_t *staging, uint8_t *landing, uint32_t min_part, uint32_t pread_to_hbm, uint64_t idle_deadline_ns,
+    int32_t *err) {
+  __shared__ genesys_c5_op ops_s[GENESYS_C5_MAX_OPS];
+  __shared__ uint32_t si_s, b_s, nb_s, nops_s;
+  __shared__ uint64_t st_off_s, hbm_off_s, seq_s;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const uint32_t u = atomicAdd(head, 1u);
+      const uint64_t e = exec_wait_unit(units, unit_mask, u, idle_deadline_ns, err);
+      const uint32_t si = e ? (uint32_t)(e >> 16) & 0xFFFFu : kExecStop;
+      si_s = si;
+      if (si != kExecStop) {
+        // the slot record was written before the entry was released
+        const volatile ExecSlot *r = slots + si;
+        b_s = (uint32_t)e & 0xFFFFu;
+        nb_s = r->nb;
+        nops_s = r->n_ops;
+        st_off_s = r->st_off;
+        hbm_off_s = r->hbm_off;
+        seq_s = r->seq;
+        for (uint32_t k = 0; k < GENESYS_C5_MAX_OPS; ++k) {
+          ops_s[k].kind = r->ops[k].kind;
+          ops_s[k].file = r->ops[k].file;
+          ops_s[k].off = r->ops[k].off;
+          ops_s[k].len = r->ops[k].len;
+          ops_s[k].seed = r->ops[k].seed;
+          ops_s[k].out_off = r->ops[k].out_off;
+        }
+      }
+    }
+    __syncthreads();
+    const uint32_t si = si_s;
+    if (si == kExecStop) break;
+    const uint32_t nb = nb_s;
+    unsigned long long *res = results + (size_t)si * 2 * GENESYS_C5_MAX_OPS;
+    genesys_ksite *ks = ksites + (size_t)si * kSitesPerReq;
+    c5_run_block(g, ops_s, nops_s, in_fds, out_fd, staging + st_off_s, landing + hbm_off_s, res, min_part,
+                 pread_to_hbm, b_s, nb, ks);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (atomicAdd(&finished[si], 1u) == nb - 1u) {
+        // the request's last block: hand its results to the host and make
+        // the slot's device state ready for the next request
+        __threadfence();
+        volatile ExecDone *d = done + si;
+        for (uint32_t k = 0; k < 2 * GENESYS_C5_MAX_OPS; ++k) d->results[k] = atomicExch(res + k, 0ull);
+        for (uint32_t k = 0; k < kSitesPerReq; ++k) {
+          ks[k].arrive = 0;
+          ks[k].ticket = 0;
+          ks[k].flag = 0;
+          ks[k].ret = 0;
+        }
+        finished[si] = 0;
+        fence_acq_rel_sys();
+        st_relaxed_sys((uint64_t *)&d->seq, seq_s);
+      }
+    }
+    __syncthreads();  // the shared request state is rewritten by the next unit
   }
 }
 
@@ -273,6 +392,241 @@ struct Launch {
   cudaGraphNode_t node = nullptr;
 };
 
+// GPU mmaps are served from regions mapped and registered before the first
+// request, while no request kernel runs: per power-of-two size class, as many
+// regions as the trace has mmaps of that class, at most two per request
+// slot (blocks of a request can be one operation apart).
+int reserve_trace_mmaps(genesys_ctx *c, const genesys_c5_request *reqs, uint32_t n_req, uint32_t K) {
+  std::map<uint64_t, uint64_t> per_class;
+  for (uint32_t r = 0; r < n_req; ++r)
+    for (uint32_t k = 0; k < reqs[r].n_ops; ++k)
+      if (reqs[r].ops[k].kind == GENESYS_C5_MMAP) {
+        uint64_t cls = 4096;
+        while (cls < reqs[r].ops[k].len) cls <<= 1;
+        per_class[cls] += 1;
+      }
+  std::vector<uint64_t> sizes;
+  for (auto &kv : per_class)
+    for (uint64_t i = 0; i < std::min<uint64_t>(kv.second, 2ull * K); ++i) sizes.push_back(kv.first);
+  return sizes.empty() ? 0 : genesys_mmap_reserve(c, sizes.data(), (uint32_t)sizes.size());
+}
+
+// System calls a request makes (each pread/pwrite part, mmap and munmap).
+uint64_t calls_of(const genesys_c5_request &q, uint32_t blocks, uint32_t min_part) {
+  uint64_t calls = 0;
+  for (uint32_t k = 0; k < q.n_ops; ++k) {
+    const genesys_c5_op &op = q.ops[k];
+    if (op.kind == GENESYS_C5_MMAP) { calls += 2; continue; }
+    uint64_t p = (op.len + min_part - 1) / min_part;
+    p = std::min<uint64_t>(std::min<uint64_t>(p ? p : 1, blocks), GENESYS_C5_MAX_PARTS);
+    const uint64_t sh = ((op.len + p - 1) / p + 15) & ~uint64_t(15);
+    calls += (op.len + sh - 1) / sh;
+  }
+  return calls;
+}
+
+// genesys_c5_serve with cfg.persistent: the serve loop feeds one executor
+// kernel (c5_executor_kernel) instead of launching a kernel per request.
+int serve_persistent(genesys_ctx *c, const genesys_c5_request *reqs, uint32_t n_req, const int32_t *in_fds,
+                     uint32_t n_in, int32_t out_fd, const genesys_serve_config &cfg, const genesys_dev &g0,
+                     uint64_t *results, uint64_t *latency_ns, genesys_serve_stats *stats) {
+  const uint32_t K = cfg.max_inflight, bt = cfg.block_threads;
+  if (K >= kExecStop) return set_err(GENESYS_EINVAL, "persistent executor: max_inflight must be below 65535");
+  uint32_t P = cfg.persistent_blocks;
+  if (P == 0) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c5_executor_kernel, (int)bt, 0) != cudaSuccess ||
+        per_sm <= 0)
+      return set_err(GENESYS_ECUDA, "occupancy query failed");
+    P = (uint32_t)per_sm * g0.n_sms;
+  }
+  if (g0.n_slots < 2ull * P + 2ull * K)
+    return set_err(GENESYS_EINVAL, "persistent executor: the slot area needs 2 slots per executor block and request");
+  uint32_t max_nb = 1;
+  for (uint32_t r = 0; r < n_req; ++r) max_nb = std::max(max_nb, (reqs[r].threads + bt - 1) / bt);
+  if (max_nb > 0xFFFFu) return set_err(GENESYS_EINVAL, "persistent executor: at most 65535 blocks per request");
+  uint32_t cap = 1;
+  while (cap < (uint64_t)K * max_nb + P + 1) cap <<= 1;  // units of the requests in flight + the stops
+
+  // device memory (the context's scratch): ring consumer position, per slot
+  // results / call sites / finished blocks, the fd table, the HBM landing
+  const size_t res_off = 256;
+  const size_t ks_off = res_off + (size_t)K * 2 * GENESYS_C5_MAX_OPS * 8;
+  const size_t fin_off = ks_off + (size_t)K * kSitesPerReq * sizeof(genesys_ksite);
+  const size_t fds_off = (fin_off + (size_t)K * 4 + 255) & ~size_t(255);
+  const size_t land_off = (fds_off + (size_t)n_in * 4 + 4095) & ~size_t(4095);
+  void *scratch = nullptr;
+  int rc = genesys_internal_scratch(c, land_off + cfg.hbm_budget + 4096, &scratch);
+  if (rc) return rc;
+  uint8_t *dbase = (uint8_t *)scratch;
+  // pinned, host-mapped: slot records, results handed back, the unit ring, the error word
+  const size_t h_slots = (size_t)K * sizeof(ExecSlot), h_done = (size_t)K * sizeof(ExecDone);
+  const size_t h_units = (size_t)cap * 8, h_bytes = h_slots + h_done + h_units + 64;
+  uint8_t *hp = nullptr;
+  if (cudaHostAlloc((void **)&hp, h_bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(GENESYS_ECUDA, "persistent executor: pinned memory");
+  }
+  memset(hp, 0, h_bytes);
+  ExecSlot *hslots = (ExecSlot *)hp;
+  ExecDone *hdone = (ExecDone *)(hp + h_slots);
+  uint64_t *units = (uint64_t *)(hp + h_slots + h_done);
+  int32_t *herr = (int32_t *)(hp + h_slots + h_done + h_units);
+  const uint64_t staging_mark = genesys_internal_staging_mark(c);
+  uint8_t *staging = (uint8_t *)genesys_staging(c, cfg.staging_budget + 4096);
+  cudaStream_t stream = nullptr;
+  auto give_back = [&]() {
+    if (stream) cudaStreamDestroy(stream);
+    cudaFreeHost(hp);
+    genesys_internal_staging_release(c, staging_mark);
+  };
+  if (!staging) {
+    give_back();
+    return set_err(GENESYS_ENOMEM, "staging arena too small for staging_budget");
+  }
+  staging = (uint8_t *)(((uintptr_t)staging + 255) & ~uintptr_t(255));
+  if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMemsetAsync(dbase, 0, land_off, stream) != cudaSuccess ||
+      cudaMemcpyAsync(dbase + fds_off, in_fds, (size_t)n_in * 4, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess) {
+    cudaGetLastError();
+    give_back();
+    return set_err(GENESYS_ECUDA, "persistent executor: set-up");
+  }
+  if (cfg.reserve_mmaps && (rc = reserve_trace_mmaps(c, reqs, n_req, K))) {
+    give_back();
+    return rc;
+  }
+
+  // the executor runs until it takes a stop unit (one per block), or its
+  // blocks have waited cfg.timeout_ns for a unit
+  {
+    genesys_dev g = g0;
+    uint32_t *head = (uint32_t *)dbase;
+    unsigned long long *d_res = (unsigned long long *)(dbase + res_off);
+    genesys_ksite *d_ks = (genesys_ksite *)(dbase + ks_off);
+    uint32_t *d_fin = (uint32_t *)(dbase + fin_off);
+    const int32_t *d_fds = (const int32_t *)(dbase + fds_off);
+    uint8_t *land = dbase + land_off;
+    const ExecSlot *slots_p = hslots;
+    ExecDone *done_p = hdone;
+    const uint64_t *units_p = units;
+    uint32_t mask = cap - 1, mp = cfg.min_part, p2h = cfg.pread_to_hbm;
+    int32_t ofd = out_fd;
+    uint64_t idle = cfg.timeout_ns;
+    int32_t *err_p = herr;
+    void *args[] = {&g, &slots_p, &done_p, &units_p, &mask, &head, &d_res, &d_ks, &d_fin, &d_fds, &ofd,
+                    &staging, &land, &mp, &p2h, &idle, &err_p};
+    if (cudaLaunchKernel((const void *)&c5_executor_kernel, dim3(P), dim3(bt), args, 0, stream) != cudaSuccess) {
+      cudaGetLastError();
+      give_back();
+      return set_err(GENESYS_ECUDA, "persistent executor: launch");
+    }
+  }
+
+  struct Busy {
+    bool busy = false;
+    uint32_t req = 0;
+    uint64_t seq = 0;
+    Needs need{};
+    uint64_t st_off = 0, hbm_off = 0;
+  };
+  std::vector<Busy> bs(K);
+  RangeAlloc st_alloc(cfg.staging_budget), hbm_alloc(cfg.hbm_budget);
+  uint64_t next = 0, retired = 0, calls = 0, admitted_wait_ns = 0, inflight = 0, max_inflight_seen = 0;
+  uint32_t tail = 0;  // ring positions published
+  int err = 0;
+  const uint64_t t0 = genesys_mono_ns();
+  std::vector<uint64_t> arrival_abs(n_req);
+  for (uint32_t r = 0; r < n_req; ++r) arrival_abs[r] = cfg.honor_arrivals ? t0 + reqs[r].arrival_ns : t0;
+  const uint64_t deadline = t0 + cfg.timeout_ns;
+  auto publish = [&](uint32_t si, uint32_t b) {
+    __atomic_store_n(&units[tail & (cap - 1)],
+                     ((uint64_t)(tail + 1u) << 32) | ((uint64_t)si << 16) | (uint64_t)b, __ATOMIC_RELEASE);
+    ++tail;
+  };
+  while (retired < n_req && !err) {
+    bool progress = false;
+    for (uint32_t si = 0; si < K; ++si) {  // retire finished requests
+      Busy &B = bs[si];
+      if (!B.busy || __atomic_load_n(&hdone[si].seq, __ATOMIC_ACQUIRE) != B.seq) continue;
+      latency_ns[B.req] = genesys_mono_ns() - arrival_abs[B.req];
+      const volatile unsigned long long *hr = hdone[si].results;
+      for (uint32_t k = 0; k < GENESYS_C5_MAX_OPS; ++k)
+        results[(size_t)B.req * GENESYS_C5_MAX_OPS + k] = hr[GENESYS_C5_MAX_OPS + k] ? hr[GENESYS_C5_MAX_OPS + k] : hr[k];
+      st_alloc.release(B.st_off, B.need.staging);
+      hbm_alloc.release(B.hbm_off, B.need.hbm);
+      B.busy = false;
+      --inflight;
+      ++retired;
+      progress = true;
+    }
+    while (next < n_req) {  // admit arrived requests, in arrival order, while budgets allow
+      const uint64_t now = genesys_mono_ns();
+      if (arrival_abs[next] > now) break;
+      uint32_t si = 0;
+      while (si < K && bs[si].busy) ++si;
+      if (si == K) break;
+      const Needs nd = needs_of(reqs[next], bt, cfg.min_part, cfg.pread_to_hbm);
+      uint64_t so = 0, ho = 0;
+      if (!st_alloc.alloc(nd.staging, &so)) break;
+      if (!hbm_alloc.alloc(nd.hbm, &ho)) { st_alloc.release(so, nd.staging); break; }
+      Busy &B = bs[si];
+      B = Busy{true, (uint32_t)next, next + 1, nd, so, ho};
+      ExecSlot &rec = hslots[si];
+      rec.n_ops = reqs[next].n_ops;
+      rec.nb = nd.blocks;
+      rec.st_off = so;
+      rec.hbm_off = ho;
+      rec.seq = B.seq;
+      memcpy(rec.ops, reqs[next].ops, sizeof rec.ops);
+      for (uint32_t b = 0; b < nd.blocks; ++b) publish(si, b);  // each release-stored after the record
+      admitted_wait_ns += now - arrival_abs[next];
+      calls += calls_of(reqs[next], nd.blocks, cfg.min_part);
+      ++inflight;
+      max_inflight_seen = std::max(max_inflight_seen, inflight);
+      ++next;
+      progress = true;
+    }
+    if (!progress) {
+      if (genesys_mono_ns() > deadline) { err = GENESYS_ETIMEDOUT; break; }
+      if (cudaStreamQuery(stream) != cudaErrorNotReady) { err = GENESYS_EDEVICE; break; }  // executor left early
+      timespec ts{0, 2000};
+      nanosleep(&ts, nullptr);
+    }
+  }
+  const uint64_t t_end = genesys_mono_ns();
+  for (uint32_t b = 0; b < P; ++b) publish(kExecStop, 0);  // every executor block leaves
+  const cudaError_t se = cudaStreamSynchronize(stream);
+  if (se != cudaSuccess && !err) err = GENESYS_ECUDA;
+  const int drc = genesys_drain(c, 10ull * g0.deadline_ns);
+  genesys_reclaim(c);
+  const int32_t exec_err = *(volatile int32_t *)herr;
+  give_back();
+  if (stats) {
+    memset(stats, 0, sizeof *stats);
+    stats->requests = retired;
+    stats->syscalls = calls;
+    stats->makespan_ns = t_end - t0;
+    stats->max_inflight = max_inflight_seen;
+    stats->admission_wait_ns = admitted_wait_ns;
+  }
+  if (err == GENESYS_ETIMEDOUT) return set_err(err, "serve: trace did not finish within timeout_ns");
+  if (err == GENESYS_EDEVICE || exec_err) return set_err(GENESYS_EDEVICE, "serve: the executor kernel left early");
+  if (err) return set_err(err, "serve: a CUDA call failed");
+  if (drc) return drc;
+  int32_t stw[GENESYS_ST_WORDS];
+  rc = genesys_status(c, stw, 1);
+  if (rc) return rc;
+  if (stw[GENESYS_ST_TIMEOUTS] || stw[GENESYS_ST_FIRST_ERROR]) {
+    char msg[160];
+    snprintf(msg, sizeof msg, "serve: device-side calls failed: first error %d, %d timeouts",
+             stw[GENESYS_ST_FIRST_ERROR], stw[GENESYS_ST_TIMEOUTS]);
+    return set_err(GENESYS_EDEVICE, msg);
+  }
+  return 0;
+}
+
 }  // namespace
 
 extern "C" int genesys_serve_config_default(genesys_serve_config *cfg) {
@@ -326,6 +680,8 @@ extern "C" int genesys_c5_serve(genesys_ctx *c, const genesys_c5_request *reqs, 
     if (cfg.slot_budget > g0.n_slots) cfg.slot_budget = g0.n_slots;
     const int dev = genesys_internal_device(c);
     if (cudaSetDevice(dev) != cudaSuccess) return set_err(GENESYS_ECUDA, "cudaSetDevice");
+    if (cfg.persistent)
+      return serve_persistent(c, reqs, n_req, in_fds, n_in, out_fd, cfg, g0, results, latency_ns, stats);
 
     // device state: per launch slot its ops, results (+ error words) and
     // kernel-grain call records; the input fd table; the HBM landing arena
@@ -374,32 +730,12 @@ extern "C" int genesys_c5_serve(genesys_ctx *c, const genesys_c5_request *reqs, 
     }
     cudaMemcpy(dbase + fds_off, in_fds, n_in * sizeof(int32_t), cudaMemcpyHostToDevice);
 
-    // GPU mmaps are served from regions mapped and registered now, while no
-    // request kernel runs: per power-of-two size class, as many regions as the
-    // trace has mmaps of that class, at most two per launch slot (blocks of a
-    // request can be one operation apart)
-    {
-      std::map<uint64_t, uint64_t> per_class;
-      for (uint32_t r = 0; r < n_req; ++r)
-        for (uint32_t k = 0; k < reqs[r].n_ops; ++k)
-          if (reqs[r].ops[k].kind == GENESYS_C5_MMAP) {
-            uint64_t cls = 4096;
-            while (cls < reqs[r].ops[k].len) cls <<= 1;
-            per_class[cls] += 1;
-          }
-      std::vector<uint64_t> sizes;
-      for (auto &kv : per_class)
-        for (uint64_t i = 0; i < std::min<uint64_t>(kv.second, 2ull * K); ++i) sizes.push_back(kv.first);
-      if (cfg.reserve_mmaps && !sizes.empty()) {
-        rc = genesys_mmap_reserve(c, sizes.data(), (uint32_t)sizes.size());
-        if (rc) {
-          for (auto &L : slots) cudaEventDestroy(L.done);
-          for (auto s : streams) cudaStreamDestroy(s);
-          cudaFreeHost(hmirror);
-          genesys_internal_staging_release(c, staging_mark);
-          return rc;
-        }
-      }
+    if (cfg.reserve_mmaps && (rc = reserve_trace_mmaps(c, reqs, n_req, K))) {
+      for (auto &L : slots) cudaEventDestroy(L.done);
+      for (auto s : streams) cudaStreamDestroy(s);
+      cudaFreeHost(hmirror);
+      genesys_internal_staging_release(c, staging_mark);
+      return rc;
     }
 
     RangeAlloc st_alloc(cfg.staging_budget), hbm_alloc(cfg.hbm_budget);
@@ -511,14 +847,7 @@ extern "C" int genesys_c5_serve(genesys_ctx *c, const genesys_c5_request *reqs, 
         ++launched;
         ++inflight;
         max_inflight_seen = std::max(max_inflight_seen, inflight);
-        for (uint32_t k = 0; k < reqs[next].n_ops; ++k) {
-          const genesys_c5_op &op = reqs[next].ops[k];
-          if (op.kind == GENESYS_C5_MMAP) { calls += 2; continue; }
-          uint64_t p = (op.len + cfg.min_part - 1) / cfg.min_part;
-          p = std::min<uint64_t>(std::min<uint64_t>(p ? p : 1, nd.blocks), GENESYS_C5_MAX_PARTS);
-          const uint64_t sh = ((op.len + p - 1) / p + 15) & ~uint64_t(15);
-          calls += (op.len + sh - 1) / sh;
-        }
+        calls += calls_of(reqs[next], nd.blocks, cfg.min_part);
         ++next;
         progress = true;
       }

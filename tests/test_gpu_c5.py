@@ -3,7 +3,9 @@ request's results (pread checksums, pwrite byte counts, mmap-fill checksums)
 and the output file equal the CPU oracle's, bit-exact; each request's result
 is the same when it runs alone (one request on the GPU at a time) and in the
 mix (up to 32 overlapping, admitted as budgets free up), with and without
-CUDA-graph relaunch, with preads landing in pinned staging or in HBM."""
+CUDA-graph relaunch, with preads landing in pinned staging or in HBM, and
+with one persistent executor kernel serving every request instead of a
+kernel per request; the full 10,000-request trace in both serving forms."""
 import os
 
 import numpy as np
@@ -112,17 +114,48 @@ def test_c5_rejects_oversized_request(ctx, G, trace, tmp_path):
     assert e.value.code == G.EINVAL
 
 
-def test_c5_full_trace_equals_oracle(ctx, tmp_path):
-    """The full 10,000-request trace, served the way the benchmark serves it
-    (64 in flight, graph relaunch, arrivals honoured): every request's results
-    and the whole output file equal the oracle's replay of every request, one
-    at a time (shared among host processes: requests are independent)."""
+@pytest.mark.parametrize("max_inflight", [1, 32])
+def test_c5_persistent_executor_matches_oracle(ctx, trace, want, tmp_path, max_inflight):
+    """One executor kernel serves the whole trace (requests admitted as
+    budgets free up, their blocks taken from a ring by the executor's
+    blocks): the same results and file as the oracle, alone and in the mix."""
+    res, lat, st, out = serve(ctx, trace, str(tmp_path / "p.bin"), persistent=1, max_inflight=max_inflight,
+                              honor_arrivals=0)
+    m = _mask(trace)
+    assert np.array_equal(res[m], want[0][m])
+    assert out == want[1]
+    assert st["requests"] == len(trace) and st["graph_launches"] == 0 and np.all(lat > 0)
+    assert st["max_inflight"] == max_inflight
+
+
+def test_c5_persistent_executor_with_few_blocks_and_hbm_landing(ctx, trace, want, tmp_path):
+    """Fewer executor blocks than a large request has blocks (a request's
+    blocks then run one after another on the same executor blocks, and its
+    kernel-grain mmap and munmap still meet), preads landing in HBM."""
+    sub = trace.subset(np.arange(60))
+    res, _, st, _ = serve(ctx, sub, str(tmp_path / "pf.bin"), persistent=1, persistent_blocks=3, max_inflight=8,
+                          pread_to_hbm=1, honor_arrivals=0)
+    m = _mask(sub)
+    assert np.array_equal(res[m], want[0][:60][m])
+
+
+@pytest.fixture(scope="module")
+def full(tmp_path_factory):
+    """The full 10,000-request trace and the oracle's replay of every request,
+    one at a time (shared among host processes: requests are independent)."""
     tr = workloads.c5_trace(workloads.C5_FULL)
-    res, lat, st, out = serve(ctx, tr, str(tmp_path / "full.bin"), max_inflight=64)
+    ref_path = str(tmp_path_factory.mktemp("c5full") / "ref.bin")
+    return tr, oracle.c5_trace_parallel(tr, ref_path), open(ref_path, "rb").read()
+
+
+@pytest.mark.parametrize("form", [{}, {"persistent": 1}], ids=["kernel_per_request", "persistent_executor"])
+def test_c5_full_trace_equals_oracle(ctx, full, tmp_path, form):
+    """The full trace served the way the benchmark serves it (64 in flight,
+    arrivals honoured; graph relaunch or the persistent executor): every
+    request's results and the whole output file equal the oracle's."""
+    tr, want, ref = full
+    res, lat, st, out = serve(ctx, tr, str(tmp_path / "full.bin"), max_inflight=64, **form)
     assert st["requests"] == len(tr) and np.all(lat > 0)
-    ref_path = str(tmp_path / "ref.bin")
-    want = oracle.c5_trace_parallel(tr, ref_path)
-    m = _mask(tr)
-    bad = np.where((res != want) & m)[0]
-    assert len(bad) == 0, (len(np.unique(bad)), np.unique(bad)[:5])
-    assert out == open(ref_path, "rb").read()
+    bad = np.where(((res != want) & _mask(tr)).any(axis=1))[0]
+    assert len(bad) == 0, (len(bad), bad[:5])
+    assert out == ref
