@@ -263,7 +263,8 @@ def service_phases(before: dict, after: dict) -> dict:
         return round((after[key] - before[key]) / req, 2)
     return {"pickup": per("pickup_ns"), "order": per("order_ns"), "os_call": round(os_ns / req, 2),
             "complete": per("complete_ns"), "busy": per("busy_ns"),
-            "requests_per_batch": round(req / max(after["batches"] - before["batches"], 1), 1)}
+            "requests_per_batch": round(req / max(after["batches"] - before["batches"], 1), 1),
+            "requests_per_os_call": round(req / max(after["os_calls"] - before["os_calls"], 1), 1)}
 
 
 def pctl(a, q):
@@ -485,7 +486,7 @@ def tune_step(args, local, rank):
     machine."""
     from paper_1705_06965_b300 import autotune
     tuner = autotune.Autotuner()
-    key = tuner.key("bench-step", sizes=len(SIZES), combos=len(COMBOS))
+    key = tuner.key("bench-step", sizes=len(SIZES), combos=len(COMBOS), batches="256-4096")
 
     def run(cfg):
         rig = Rig(args, local, rank, need_scan=False, need_c3=False, service_threads=cfg["service_threads"],
@@ -496,8 +497,12 @@ def tune_step(args, local, rank):
         finally:
             rig.close()
 
-    best, table = tuner.tune(key, autotune.grid(service_threads=(1, 2, 4), coalesce_max=(64, 256, 1024),
-                                                poll_max_ns=(2048,), n_slots=(0, 32768)), run, repeats=2)
+    # slot areas smaller than the default (one slot per resident thread) made
+    # work-item callers wait for slots and doubled the step in every run, so
+    # the slot area is not searched; batches up to 4096 (with the doorbells
+    # written without holes, batches fill to the cap)
+    best, table = tuner.tune(key, autotune.grid(service_threads=(1, 2, 4), coalesce_max=(256, 1024, 4096),
+                                                poll_max_ns=(2048,), n_slots=(0,)), run, repeats=2)
     return best, table
 
 

@@ -513,8 +513,9 @@ int genesys_kv_stop(genesys_kv_server *srv, uint64_t timeout_ns, uint64_t *serve
  * bytes room); returns its length. */
 int genesys_kv_value(genesys_kv_server *srv, uint32_t k, uint8_t *out);
 /* C4's load generator (Sec. 7.3 measures its network workloads with a client
- * on the host).  Open-loop UDP load generator on up to 4 host threads, each
- * with its own socket: request j (reqs + req_off[j], req_off[n] = end) is sent
+ * on the host).  Open-loop UDP load generator on up to 8 host threads (no
+ * more than the CPUs the calling thread may run on: restricting the caller's
+ * CPU set gives the generator its own cores), each with its own socket: request j (reqs + req_off[j], req_off[n] = end) is sent
  * arrival_ns[j] after start to the socket its key maps to, by the thread that
  * owns that socket (so one key's requests leave in order), and its reply comes
  * back to that thread; replies are matched by seq into replies[seq * (8 +

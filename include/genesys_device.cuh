@@ -256,6 +256,37 @@ __device__ __forceinline__ uint32_t slot_fill(const genesys_dev &g, uint32_t s, 
   return sq;
 }
 
+/* The same marshalling for a whole warp whose 32 lanes claimed the 32
+ * consecutive slots s0 .. s0 + 31 (s0 a multiple of 32): the warp's slots are
+ * 2 KiB of contiguous lines, written with four lane-interleaved 16-byte
+ * stores per lane, each store instruction covering 512 contiguous bytes
+ * (eight whole slots), so the lines leave for the host as full writes instead
+ * of 16-byte pieces at a 64-byte stride.  Store j, lane l writes quarter l % 4
+ * of slot 8j + l / 4; the quarter's words come from the lane that owns the
+ * slot, by shuffles.  Every lane of the warp calls it; returns the calling
+ * lane's sequence. */
+__device__ __forceinline__ uint32_t slot_fill_warp(const genesys_dev &g, uint32_t s, uint32_t nr, uint32_t flags,
+                                                   uint64_t a0, uint64_t a1, uint64_t a2, uint64_t a3,
+                                                   uint64_t a4, uint64_t a5) {
+  const uint32_t sq = ld_relaxed_gpu(&g.seq[s]) + 1u;
+  st_relaxed_gpu(&g.seq[s], sq);
+  const uint64_t req = ((uint64_t)sq << 32) | ((uint64_t)(nr & 0xFFFFu) << 16) | (flags & 0xFFFFu);
+  const uint32_t lane = lane_id(), q = lane & 3u;
+  uint64_t *base = reinterpret_cast<uint64_t *>(g.slots + (s - lane));
+#pragma unroll
+  for (uint32_t j = 0; j < 4; ++j) {
+    const uint32_t src = 8u * j + (lane >> 2);
+    const uint64_t x0 = __shfl_sync(0xFFFFFFFFu, a0, src), y0 = __shfl_sync(0xFFFFFFFFu, a1, src);
+    const uint64_t x1 = __shfl_sync(0xFFFFFFFFu, a2, src), y1 = __shfl_sync(0xFFFFFFFFu, a3, src);
+    const uint64_t x2 = __shfl_sync(0xFFFFFFFFu, a4, src), y2 = __shfl_sync(0xFFFFFFFFu, a5, src);
+    const uint64_t x3 = __shfl_sync(0xFFFFFFFFu, req, src);
+    const uint64_t x = q == 0 ? x0 : q == 1 ? x1 : q == 2 ? x2 : x3;
+    const uint64_t y = q == 0 ? y0 : q == 1 ? y1 : q == 2 ? y2 : 0ull;
+    st_v2(base + 64u * j + 2u * lane, x, y);
+  }
+  return sq;
+}
+
 /* Doorbells.  The service thread takes a ring's entries in position order
  * and stops at the first one not yet written, so the time between taking a
  * position and writing its entry holds up every later entry of the ring.  The
@@ -571,8 +602,14 @@ __device__ __forceinline__ int64_t call_at(const genesys_dev &g, uint32_t site, 
         ok = t > 0;
       }
       const uint32_t okmask = __ballot_sync(active, ok);
+      // a full warp on 32 consecutive slots (the usual case: each lane got the
+      // slot of its hardware id) writes them as whole lines
+      const uint32_t s0 = __shfl_sync(active, s, __ffs(active) - 1);
+      const bool lines = okmask == 0xFFFFFFFFu && (s0 & 31u) == 0 &&
+                         __all_sync(0xFFFFFFFFu, s == s0 + lane_id()) && dcheck(g, s0 + 32u <= g.n_slots);
       if (ok) {
-        const uint32_t sq = slot_fill(g, s, nr, flags, a0, a1, a2, a3, a4, a5);
+        const uint32_t sq = lines ? slot_fill_warp(g, s, nr, flags, a0, a1, a2, a3, a4, a5)
+                                  : slot_fill(g, s, nr, flags, a0, a1, a2, a3, a4, a5);
         const uint32_t pos = ring_warp(g, okmask, s);
         const uint64_t t_pub = g.trace_cap ? now_ns() : 0;
         rc = B == BLOCKING ? slot_wait_ring(g, s, sq, ring_of(g, s), pos, t0) : 0;

@@ -17,6 +17,7 @@
 // (0 ok, 1 no such key), vlen u16, seq u32, value[vlen] (GET of a present key).
 #include <arpa/inet.h>
 #include <cuda_runtime.h>
+#include <sched.h>
 #include <errno.h>
 #include <netinet/in.h>
 #include <pthread.h>
@@ -512,7 +513,12 @@ extern "C" int genesys_kv_client(const uint8_t *reqs, const uint64_t *req_off, u
   return genesys_guard("genesys_kv_client", [&]() -> int {
     if (!reqs || !req_off || !arrival_ns || !replies || !reply_len || !latency_ns || n_sockets == 0)
       return set_err(GENESYS_EINVAL, "NULL argument");
-    const uint32_t n_threads = std::min<uint32_t>(n_sockets, 4);
+    // one thread per CPU the caller may run on (it restricts the generator to
+    // its share of the host's cores that way), at most 8, at most one per socket
+    cpu_set_t allowed;
+    uint32_t cpus = 1;
+    if (sched_getaffinity(0, sizeof allowed, &allowed) == 0) cpus = std::max(1, CPU_COUNT(&allowed));
+    const uint32_t n_threads = std::min<uint32_t>(std::min<uint32_t>(n_sockets, 8), cpus);
     std::vector<uint64_t> t_send(n, 0);  // before any socket is opened: this may throw
     std::vector<int> fds;
     for (uint32_t w = 0; w < n_threads; ++w) {
