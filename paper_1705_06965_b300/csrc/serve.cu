@@ -251,47 +251,44 @@ __device__ uint64_t exec_wait_unit(const uint64_t *units, uint32_t mask, uint32_
   }
 }
 
+constexpr uint32_t kExecSlotWords = sizeof(ExecSlot) / 16;  // 16-byte pieces of a slot record
+static_assert(sizeof(ExecSlot) % 16 == 0 && kExecSlotWords <= 32, "a slot record is read by one warp");
+
 __global__ void __launch_bounds__(1024) c5_executor_kernel(
     genesys_dev g, const ExecSlot *slots, ExecDone *done, const uint64_t *units, uint32_t unit_mask, uint32_t *head,
     unsigned long long *results, genesys_ksite *ksites, uint32_t *finished, const int32_t *in_fds, int32_t out_fd,
     uint8_t *staging, uint8_t *landing, uint32_t min_part, uint32_t pread_to_hbm, uint64_t idle_deadline_ns,
     int32_t *err) {
-  __shared__ genesys_c5_op ops_s[GENESYS_C5_MAX_OPS];
-  __shared__ uint32_t si_s, b_s, nb_s, nops_s;
-  __shared__ uint64_t st_off_s, hbm_off_s, seq_s;
+  __shared__ ExecSlot rec_s;
+  __shared__ uint32_t si_s, b_s;
   for (;;) {
     if (threadIdx.x == 0) {
       const uint32_t u = atomicAdd(head, 1u);
       const uint64_t e = exec_wait_unit(units, unit_mask, u, idle_deadline_ns, err);
-      const uint32_t si = e ? (uint32_t)(e >> 16) & 0xFFFFu : kExecStop;
-      si_s = si;
-      if (si != kExecStop) {
-        // the slot record was written before the entry was released
-        const volatile ExecSlot *r = slots + si;
-        b_s = (uint32_t)e & 0xFFFFu;
-        nb_s = r->nb;
-        nops_s = r->n_ops;
-        st_off_s = r->st_off;
-        hbm_off_s = r->hbm_off;
-        seq_s = r->seq;
-        for (uint32_t k = 0; k < GENESYS_C5_MAX_OPS; ++k) {
-          ops_s[k].kind = r->ops[k].kind;
-          ops_s[k].file = r->ops[k].file;
-          ops_s[k].off = r->ops[k].off;
-          ops_s[k].len = r->ops[k].len;
-          ops_s[k].seed = r->ops[k].seed;
-          ops_s[k].out_off = r->ops[k].out_off;
-        }
-      }
+      si_s = e ? (uint32_t)(e >> 16) & 0xFFFFu : kExecStop;
+      b_s = (uint32_t)e & 0xFFFFu;
     }
     __syncthreads();
     const uint32_t si = si_s;
     if (si == kExecStop) break;
-    const uint32_t nb = nb_s;
+    // the slot record (written by the host before it released the entry that
+    // thread 0 acquired), one 16-byte piece per thread of the first warp: a
+    // single round trip over the host link, not one per field
+    if (threadIdx.x < kExecSlotWords) {
+      uint64_t lo, hi;
+      asm volatile("ld.relaxed.sys.global.v2.u64 {%0, %1}, [%2];"
+                   : "=l"(lo), "=l"(hi)
+                   : "l"(reinterpret_cast<const uint64_t *>(slots + si) + 2 * threadIdx.x)
+                   : "memory");
+      reinterpret_cast<uint64_t *>(&rec_s)[2 * threadIdx.x] = lo;
+      reinterpret_cast<uint64_t *>(&rec_s)[2 * threadIdx.x + 1] = hi;
+    }
+    __syncthreads();
+    const uint32_t nb = rec_s.nb;
     unsigned long long *res = results + (size_t)si * 2 * GENESYS_C5_MAX_OPS;
     genesys_ksite *ks = ksites + (size_t)si * kSitesPerReq;
-    c5_run_block(g, ops_s, nops_s, in_fds, out_fd, staging + st_off_s, landing + hbm_off_s, res, min_part,
-                 pread_to_hbm, b_s, nb, ks);
+    c5_run_block(g, rec_s.ops, rec_s.n_ops, in_fds, out_fd, staging + rec_s.st_off, landing + rec_s.hbm_off, res,
+                 min_part, pread_to_hbm, b_s, nb, ks);
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
@@ -309,7 +306,7 @@ __global__ void __launch_bounds__(1024) c5_executor_kernel(
         }
         finished[si] = 0;
         fence_acq_rel_sys();
-        st_relaxed_sys((uint64_t *)&d->seq, seq_s);
+        st_relaxed_sys((uint64_t *)&d->seq, rec_s.seq);
       }
     }
     __syncthreads();  // the shared request state is rewritten by the next unit
