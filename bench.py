@@ -264,7 +264,11 @@ def service_phases(before: dict, after: dict) -> dict:
     return {"pickup": per("pickup_ns"), "order": per("order_ns"), "os_call": round(os_ns / req, 2),
             "complete": per("complete_ns"), "busy": per("busy_ns"),
             "requests_per_batch": round(req / max(after["batches"] - before["batches"], 1), 1),
-            "requests_per_os_call": round(req / max(after["os_calls"] - before["os_calls"], 1), 1)}
+            "requests_per_os_call": round(req / max(after["os_calls"] - before["os_calls"], 1), 1),
+            "empty_polls_per_batch": round((after["empty_polls"] - before["empty_polls"]) /
+                                           max(after["batches"] - before["batches"], 1), 2),
+            "hole_polls_per_batch": round((after["hole_polls"] - before["hole_polls"]) /
+                                          max(after["batches"] - before["batches"], 1), 2)}
 
 
 def pctl(a, q):
@@ -959,17 +963,20 @@ def _kv_point(tr, reqs, off, rate, run_server, port, client_cpus=None, keep=None
     import paper_1705_06965_b300 as G
     n = _kv_requests_at(rate, len(tr))
     arr = (tr.arrival_ns[:n].astype(np.float64) * (tr.params["rate_per_s"] / rate)).astype(np.uint64)
-    stop = run_server(port)
+    srv = run_server(port)
     mask = os.sched_getaffinity(0)
+    seen = None
     try:
         if client_cpus:  # threads the generator starts inherit this thread's CPU set
             os.sched_setaffinity(0, client_cpus)
         reps, lat, st = G.kv_client(reqs[:int(off[n])], off[:n + 1], arr, port, 32, timeout_ns=10_000_000_000)
+        if hasattr(srv, "received"):  # the GPU server logs the requests that reached it
+            seen = srv.received(n)
     finally:
         os.sched_setaffinity(0, mask)
-        served = stop()
+        served = srv.stop()
     if keep is not None:
-        keep[str(int(rate))] = reply_digests(reps)
+        keep[str(int(rate))] = (reply_digests(reps), seen)
     got = lat[lat > 0]
     achieved = st["received"] / (st["span_ns"] * 1e-9) if st["span_ns"] else 0.0
     return {"requests": n, "received": st["received"], "served": served, "achieved_req_per_s": round(achieved, 1),
@@ -1045,8 +1052,7 @@ def serve_c4(G, local, rank, rates=tuple(50_000.0 * 2 ** i for i in range(7)), n
     with G.Context(device=local, service_threads=8, staging_bytes=64 << 20,
                    service_cpus=server_cpus[:8] if server_cpus else None) as ctx:
         def gpu_server(port):
-            srv = G.KVServer(ctx, tr.keys, tr.vlen0, tr.vseed0, n_sockets=32, batch=64, port_base=port)
-            return srv.stop
+            return G.KVServer(ctx, tr.keys, tr.vlen0, tr.vseed0, n_sockets=32, batch=64, port_base=port)
         out["rates"] = _kv_sweep(tr, reqs, off, gpu_server, 41000 + 400 * rank, rates, client_cpus, digests)
     if checks is not None:
         checks["c4"] = (tr, digests)
@@ -1063,15 +1069,19 @@ def cpu_baseline_c4(tr, reqs, off, port, rates, server_cpus=None, client_cpus=No
     import oracle
     table = tr.values0_table()
 
-    def cpu_server(port):
-        mask = os.sched_getaffinity(0)
-        try:
-            if server_cpus:  # the server's thread inherits this thread's CPU set
-                os.sched_setaffinity(0, set(server_cpus))
-            srv = oracle.UdpServer("kv", port, 32, trace=tr, idle_ns=5_000_000_000, values0=table)
-        finally:
-            os.sched_setaffinity(0, mask)
-        return lambda: srv.join()["answered"]
+    class CpuServer:
+        def __init__(self, port):
+            mask = os.sched_getaffinity(0)
+            try:
+                if server_cpus:  # the server's thread inherits this thread's CPU set
+                    os.sched_setaffinity(0, set(server_cpus))
+                self.srv = oracle.UdpServer("kv", port, 32, trace=tr, idle_ns=5_000_000_000, values0=table)
+            finally:
+                os.sched_setaffinity(0, mask)
+
+        def stop(self):
+            return self.srv.join()["answered"]
+    cpu_server = CpuServer
     res = _kv_sweep(tr, reqs, off, cpu_server, port, rates, client_cpus)
     return {"threads": 1, "rates": res, **kv_saturation(res)}
 
@@ -1363,13 +1373,29 @@ def oracle_checks(checks: dict) -> dict:
     import oracle
     out = {"ran": True}
     if "c4" in checks:
-        tr, digests = checks["c4"]
+        # every reply that came back, against the oracle's replay in client
+        # sequence order of the requests that reached the server (all of them
+        # unless datagrams were lost: then exactly the server's received log)
+        tr, per_rate = checks["c4"]
         t = time.perf_counter()
         want = reply_digests(oracle.c4_replay(tr))
-        bad = {rate: int(np.count_nonzero(d != want[:len(d)])) for rate, d in digests.items()}
-        out["c4_mismatched_replies_by_rate"] = bad
-        out["c4_replies_checked"] = int(sum(len(d) for d in digests.values()))
-        out["c4_replies_equal"] = bool(digests) and all(v == 0 for v in bad.values())
+        by_rate, checked = {}, 0
+        for rate, (d, seen) in per_rate.items():
+            n = len(d)
+            replied = d != 0  # a missing reply has digest 0, a real one never does
+            if seen is None or seen.all():
+                w, idx = want[:n], np.arange(n)
+            else:
+                idx = np.nonzero(seen)[0]
+                w = reply_digests(oracle.c4_replay(tr, idx))
+            cmp = replied[idx]
+            bad = int(np.count_nonzero(d[idx][cmp] != w[cmp]))
+            checked += int(cmp.sum())
+            by_rate[rate] = {"mismatched": bad, "requests_lost": int(n - len(idx)),
+                             "replies_lost": int(np.count_nonzero(~replied[idx]))}
+        out["c4_by_rate"] = by_rate
+        out["c4_replies_checked"] = checked
+        out["c4_replies_equal"] = bool(per_rate) and all(v["mismatched"] == 0 for v in by_rate.values())
         out["c4_oracle_s"] = round(time.perf_counter() - t, 2)
     if "c5" in checks:
         tr, runs = checks["c5"]

@@ -108,6 +108,10 @@ typedef struct genesys_stats {  /* genesys_stats_t */
   uint64_t order_ns;           /* ... ordering a batch so that file neighbours merge   */
   uint64_t complete_ns;        /* ... writing results, completion words and the rings'
                                   finished counts (the Linux calls are op_ns)           */
+  uint64_t empty_polls;        /* ring polls that found no new request at the head     */
+  uint64_t hole_polls;         /* of those, polls where a later entry was already
+                                  written: a position taken whose entry had not yet
+                                  arrived held the ring up                            */
 } genesys_stats_t;
 
 typedef struct genesys_ctx genesys_ctx;
@@ -509,6 +513,15 @@ int genesys_kv_start(genesys_ctx *ctx, const uint8_t *keys, const uint16_t *vlen
  * has not left, or its calls did not drain) the server is kept and the call
  * can be repeated; the context cannot be shut down until one succeeds. */
 int genesys_kv_stop(genesys_kv_server *srv, uint64_t timeout_ns, uint64_t *served);
+/* C4 (Sec. 7.3; the survey's reading for lost datagrams: the server logs the
+ * requests it received and the oracle replays exactly those).  Bit j of
+ * out[j / 32] (host array of (n_seqs + 31) / 32 words) is set when the
+ * request whose seq field is j reached the server, for j < n_seqs <=
+ * GENESYS_KV_SEQ_LOG (requests with larger seq are not logged).  Call it
+ * after the load has ended, before genesys_kv_stop.  GENESYS_EINVAL for NULL
+ * arguments or n_seqs too large. */
+#define GENESYS_KV_SEQ_LOG (1u << 24)
+int genesys_kv_received(genesys_kv_server *srv, uint32_t *out, uint64_t n_seqs);
 /* C4 (Sec. 7.3).  Current value of key k (copied to out, GENESYS_KV_VALUE_MAX
  * bytes room); returns its length. */
 int genesys_kv_value(genesys_kv_server *srv, uint32_t k, uint8_t *out);

@@ -49,7 +49,7 @@ EXPORTS = [
     "genesys_kv_client", "genesys_c6_permute", "genesys_gpu_call", "genesys_echo_start", "genesys_echo_stop",
     "genesys_echo_client", "genesys_service_probe", "genesys_link_pingpong", "genesys_service_restart",
     "genesys_trace_read", "genesys_sizeof", "genesys_service_health", "genesys_service_probe_order",
-    "genesys_stats", "genesys_graph_launches", "genesys_check_pread_cap",
+    "genesys_stats", "genesys_graph_launches", "genesys_check_pread_cap", "genesys_kv_received",
 ]
 
 
@@ -96,7 +96,7 @@ class Stats(ctypes.Structure):
         ("by_op", ctypes.c_uint64 * 8), ("op_ns", ctypes.c_uint64 * 8), ("op_max_ns", ctypes.c_uint64 * 8),
         ("mmap_new", ctypes.c_uint64), ("mmap_reused", ctypes.c_uint64), ("service_cpu_ns", ctypes.c_uint64),
         ("protocol_errors", ctypes.c_uint64), ("pickup_ns", ctypes.c_uint64), ("order_ns", ctypes.c_uint64),
-        ("complete_ns", ctypes.c_uint64)]
+        ("complete_ns", ctypes.c_uint64), ("empty_polls", ctypes.c_uint64), ("hole_polls", ctypes.c_uint64)]
 
     OPS = ("pread", "pwrite", "sendto", "recvfrom", "mmap", "munmap", "internal", "other")
 
@@ -155,6 +155,7 @@ def lib() -> ctypes.CDLL:
                                             ctypes.POINTER(vp)]),
         "genesys_kv_stop": (ctypes.c_int, [vp, u64, ctypes.POINTER(u64)]),
         "genesys_kv_value": (ctypes.c_int, [vp, u32, vp]),
+        "genesys_kv_received": (ctypes.c_int, [vp, vp, u64]),
         "genesys_c6_permute": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, u64, u32, u32, u32, vp, u64, vp]),
         "genesys_gpu_call": (ctypes.c_int, [vp, u32, ctypes.POINTER(u64), u32, u32, vp, vp]),
         "genesys_kv_client": (ctypes.c_int, [vp, vp, u64, vp, ctypes.c_uint16, u32, u64, vp, vp, vp, vp]),
@@ -501,6 +502,13 @@ class KVServer:
         buf = ctypes.create_string_buffer(1024)
         n = _check(lib().genesys_kv_value(self._h, k, buf), "genesys_kv_value")
         return buf.raw[:n]
+
+    def received(self, n: int) -> np.ndarray:
+        """Which of the requests with seq 0 .. n-1 reached the server (bool
+        array; genesys_kv_received): call after the load, before stop."""
+        words = np.zeros(max((n + 31) // 32, 1), np.uint32)
+        _check(lib().genesys_kv_received(self._h, words.ctypes.data, n), "genesys_kv_received")
+        return np.unpackbits(words.view(np.uint8), bitorder="little")[:n].astype(bool)
 
     def stop(self, timeout_ns: int = 30_000_000_000) -> int:
         """Stop the server; returns the replies it sent.  On an error the

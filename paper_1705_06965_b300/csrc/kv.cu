@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(1024) kv_server_kernel(genesys_dev g, const in
                                                          uint32_t batch, const uint8_t *keys, const uint32_t *index,
                                                          uint32_t index_mask, uint8_t *vals, uint16_t *vlens,
                                                          volatile int32_t *stop_flag, uint64_t idle_timeout_ns,
-                                                         unsigned long long *served) {
+                                                         unsigned long long *served, uint32_t *seen) {
   __shared__ KvShared S;
   KvBlockArea *A = areas + blockIdx.x;
   const int fd = fds[blockIdx.x];
@@ -173,6 +173,9 @@ __global__ void __launch_bounds__(1024) kv_server_kernel(genesys_dev g, const in
         S.stop = 1;
       } else {
         S.ki[i] = kv_lookup(keys, index, index_mask, k[0], k[1]);
+        // the log of received requests (genesys_kv_received)
+        const uint32_t seq = (uint32_t)q[4] | ((uint32_t)q[5] << 8) | ((uint32_t)q[6] << 16) | ((uint32_t)q[7] << 24);
+        if (seq < GENESYS_KV_SEQ_LOG) atomicOr(&seen[seq >> 5], 1u << (seq & 31));
       }
     }
     __syncthreads();
@@ -265,6 +268,7 @@ struct genesys_kv_server {
   void *dmem = nullptr;          // device: fds, index, keys, vals, vlens, stop flag, served
   int32_t *d_stop = nullptr;
   unsigned long long *d_served = nullptr;
+  uint32_t *d_seen = nullptr;    // received-request log, GENESYS_KV_SEQ_LOG bits
   uint8_t *d_vals = nullptr;
   uint16_t *d_vlens = nullptr;
   uint64_t staging_mark = 0;
@@ -316,7 +320,8 @@ extern "C" int genesys_kv_start(genesys_ctx *c, const uint8_t *keys, const uint1
     // device memory: fds | stop | served | index | keys | vals | vlens | vlen0 | vseed0
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) & ~size_t(255); return o; };
-    const size_t o_fds = take(4 * n_sockets), o_stop = take(4), o_served = take(8), o_index = take(4ull * index_size),
+    const size_t o_fds = take(4 * n_sockets), o_stop = take(4), o_served = take(8),
+                 o_seen = take(GENESYS_KV_SEQ_LOG / 8), o_index = take(4ull * index_size),
                  o_keys = take(16ull * n_keys), o_vals = take((size_t)kVal * n_keys), o_vlens = take(2ull * n_keys),
                  o_vlen0 = take(2ull * n_keys), o_vseed0 = take(8ull * n_keys);
     if (cudaMalloc(&s->dmem, off) != cudaSuccess) return fail_cleanup(GENESYS_ENOMEM, "device memory for the table");
@@ -330,6 +335,7 @@ extern "C" int genesys_kv_start(genesys_ctx *c, const uint8_t *keys, const uint1
       return fail_cleanup(GENESYS_ECUDA, "upload of the table");
     s->d_stop = (int32_t *)(d + o_stop);
     s->d_served = (unsigned long long *)(d + o_served);
+    s->d_seen = (uint32_t *)(d + o_seen);  // zeroed with the rest of [0, o_keys) above
     s->d_vals = d + o_vals;
     s->d_vlens = (uint16_t *)(d + o_vlens);
     kv_build_kernel<<<n_keys, 128>>>(d + o_keys, (const uint16_t *)(d + o_vlen0), (const uint64_t *)(d + o_vseed0),
@@ -353,7 +359,8 @@ extern "C" int genesys_kv_start(genesys_ctx *c, const uint8_t *keys, const uint1
     volatile int32_t *stop = s->d_stop;
     uint64_t idle = idle_timeout_ns ? idle_timeout_ns : 10000000000ull;
     unsigned long long *served = s->d_served;
-    void *args[] = {&g, &d_fds, &areas, &bt, &d_keys, &d_index, &imask, &vals, &vl, &stop, &idle, &served};
+    uint32_t *seen = s->d_seen;
+    void *args[] = {&g, &d_fds, &areas, &bt, &d_keys, &d_index, &imask, &vals, &vl, &stop, &idle, &served, &seen};
     const uint32_t g3[3] = {n_sockets, 1, 1}, b3[3] = {threads, 1, 1};
     int rc = genesys_launch(c, (const void *)&kv_server_kernel, g3, b3, 0, args,
                             GENESYS_GRAN_GROUP | GENESYS_LAUNCH_RELAXED, s->stream);
@@ -398,6 +405,22 @@ extern "C" int genesys_kv_stop(genesys_kv_server *s, uint64_t timeout_ns, uint64
     cudaStreamDestroy(s->ctl);
     genesys_internal_staging_release(s->ctx, s->staging_mark);
     delete s;
+    return 0;
+  });
+}
+
+// The received-request log (for checks): bit j of out[j / 32] is set when
+// the request with sequence number j has reached the server.
+extern "C" int genesys_kv_received(genesys_kv_server *s, uint32_t *out, uint64_t n_seqs) {
+  return genesys_guard("genesys_kv_received", [&]() -> int {
+    if (!s || !out) return set_err(GENESYS_EINVAL, "NULL argument");
+    if (n_seqs > GENESYS_KV_SEQ_LOG) return set_err(GENESYS_EINVAL, "the log holds GENESYS_KV_SEQ_LOG requests");
+    const size_t words = (size_t)(n_seqs + 31) / 32;
+    if (words && (cudaMemcpyAsync(out, s->d_seen, words * 4, cudaMemcpyDeviceToHost, s->ctl) != cudaSuccess ||
+                  cudaStreamSynchronize(s->ctl) != cudaSuccess)) {
+      cudaGetLastError();
+      return set_err(GENESYS_ECUDA, "copy of the received-request log");
+    }
     return 0;
   });
 }

@@ -100,6 +100,10 @@ struct alignas(64) Counters {
   // ordering it for merging, and writing its results back; the Linux calls
   // themselves are op_ns
   std::atomic<uint64_t> pickup_ns{0}, order_ns{0}, complete_ns{0};
+  // polls that found the entry at the ring's head not yet written; of those,
+  // the ones where a later entry was already written (a position taken on
+  // the GPU whose entry had not arrived: a hole that holds up the ring)
+  std::atomic<uint64_t> empty_polls{0}, hole_polls{0};
 };
 
 struct Request {
@@ -650,8 +654,17 @@ size_t poll_ring(genesys_ctx *c, uint32_t ri, Batch &b) {
     __builtin_prefetch(&c->slots[s], 0, 0);
     ++n;
   }
-  if (n == 0) return 0;
   Counters &k = c->counters[ri];
+  if (n == 0) {
+    bump(k.empty_polls, 1);
+    uint32_t t;
+    for (uint32_t ahead : {1u, 8u, 32u, 64u})
+      if (entry_ready(ring, mask, h + ahead, &t)) {
+        bump(k.hole_polls, 1);
+        break;
+      }
+    return 0;
+  }
   const uint64_t t_pick = genesys_mono_ns();
   for (size_t i = 0; i < n; ++i) read_request(c, slots[i], &batch[i]);
   if (n < maxb && c->cfg.coalesce_window_ns) {
@@ -1268,6 +1281,8 @@ int genesys_stats_get(genesys_ctx *c, genesys_stats_t *o) {
       o->pickup_ns += k.pickup_ns.load();
       o->order_ns += k.order_ns.load();
       o->complete_ns += k.complete_ns.load();
+      o->empty_polls += k.empty_polls.load();
+      o->hole_polls += k.hole_polls.load();
       for (int i = 0; i < 8; ++i) {
         o->by_op[i] += k.by_op[i].load();
         o->op_ns[i] += k.op_ns[i].load();
@@ -1291,7 +1306,7 @@ int genesys_stats_reset(genesys_ctx *c) {
   for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) {
     Counters &k = c->counters[r];
     k.requests = 0; k.os_calls = 0; k.failed = 0; k.nb_failed = 0; k.bytes = 0; k.batches = 0; k.busy_ns = 0;
-    k.pickup_ns = 0; k.order_ns = 0; k.complete_ns = 0;
+    k.pickup_ns = 0; k.order_ns = 0; k.complete_ns = 0; k.empty_polls = 0; k.hole_polls = 0;
     for (int i = 0; i < 8; ++i) k.by_op[i] = 0, k.op_ns[i] = 0, k.op_max_ns[i] = 0;
   }
   std::lock_guard<std::mutex> g(c->restart_mu);

@@ -55,6 +55,7 @@ def test_service_phases_from_a_host_only_context(tmp_path):
             ph = bench.service_phases(before, c.stats())
     finally:
         os.close(fd)
-    assert set(ph) == {"pickup", "order", "os_call", "complete", "busy", "requests_per_batch", "requests_per_os_call"}
+    assert set(ph) == {"pickup", "order", "os_call", "complete", "busy", "requests_per_batch", "requests_per_os_call",
+                       "empty_polls_per_batch", "hole_polls_per_batch"}
     assert all(v >= 0 for v in ph.values()) and ph["os_call"] > 0 and ph["requests_per_batch"] >= 1
     assert ph["order"] + ph["os_call"] <= ph["busy"] + 1e-6

@@ -96,10 +96,51 @@ def test_c4_full_table_at_800k_per_s_every_reply_bit_exact(G, ctx):
     srv = G.KVServer(ctx, tr.keys, tr.vlen0, tr.vseed0, n_sockets=32, batch=64, port_base=port)
     try:
         reps, lat, st = G.kv_client(reqs, off, tr.arrival_ns, port, 32, timeout_ns=20_000_000_000)
+        seen = srv.received(len(tr))
     finally:
         served = srv.stop()
     assert st["rc"] == 0 and st["received"] == len(tr), st
     assert st["duplicates"] == 0 and st["malformed"] == 0
+    assert seen.all()  # the server's log of received requests
     bad = [j for j in range(len(tr)) if reps[j] != want[j]]
     assert not bad, (len(bad), bad[:5])
     assert served == len(tr)
+
+
+def test_c4_lost_requests_are_left_out_of_the_replay(G, ctx):
+    """The server logs the requests that reached it; the oracle replays
+    exactly those (a lost SET must not change the expected replies of later
+    GETs of its key).  The loss is made on the client side: a plain UDP
+    client sends the trace in sequence order but skips every 7th request, and
+    the received log must say exactly which arrived."""
+    import socket
+    import time
+    p = dict(workloads.C4_SMALL, n_requests=3000)
+    tr = workloads.kv_trace(p)
+    keep = np.arange(len(tr)) % 7 != 3
+    n_sockets = 8
+    port = _port() + 301
+    srv = G.KVServer(ctx, tr.keys, tr.vlen0, tr.vseed0, n_sockets=n_sockets, batch=32, port_base=port)
+    so = socket.socket(socket.AF_INET, socket.SOCK_DGRAM)
+    so.setsockopt(socket.SOL_SOCKET, socket.SO_RCVBUF, 16 << 20)
+    so.settimeout(5.0)
+    reps = {}
+    try:
+        for j in np.nonzero(keep)[0]:
+            d, _ = workloads.kv_request_bytes(tr, [j])
+            k0 = int.from_bytes(d[8:12], "little")
+            so.sendto(d, ("127.0.0.1", port + k0 % n_sockets))
+            if j % 64 == 0:
+                time.sleep(0.001)      # a gentle rate: nothing is lost on the way
+        while len(reps) < int(keep.sum()):
+            r = so.recv(2048)
+            reps[int.from_bytes(r[4:8], "little")] = r
+        seen = srv.received(len(tr))
+    finally:
+        so.close()
+        srv.stop()
+    assert np.array_equal(seen, keep)
+    idx = np.nonzero(seen)[0]
+    want = oracle.c4_replay(tr, idx)
+    bad = [int(j) for i, j in enumerate(idx) if reps[int(j)] != want[i]]
+    assert not bad, (len(bad), bad[:5])

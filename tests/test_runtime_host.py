@@ -674,6 +674,7 @@ def test_every_entry_point_rejects_null_arguments():
     t("genesys_stats", None, None)
     t("genesys_graph_launches", None, None)
     t("genesys_check_pread_cap", None, 0)
+    t("genesys_kv_received", None, None, 0)
     assert res.pop("genesys_shutdown") == 0
     assert all(v == G.EINVAL for v in res.values()), res
     assert len(res) >= 35
