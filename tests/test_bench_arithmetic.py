@@ -153,14 +153,14 @@ def test_summary_fits_the_kept_tail_and_carries_every_config():
     t = sm["targets"]
     assert t["c2_batched_beats_plain"] == {"syscalls_per_s": False, "requests_per_s": True, "p99": True}
     assert t["c5_served_beats_plain"] == {"syscalls_per_s": True, "requests_per_s": True, "p99": True}
-    assert t["scan_frac_h2d_ge_0.8"] is True
+    assert t["pread_scan_frac_h2d_ge_0.75"] == {"scan_1GiB": True, "c3": True}
 
 
 def test_summary_of_a_line_without_extras():
     """--extras 0 lines (launch lists) still get a summary, with None where a
     section was not measured."""
     sm = bench.summarize({"value": 1.0, "e2e": {"value": 1.0}})
-    assert sm["c4"]["sat_rps"] is None and sm["targets"]["scan_frac_h2d_ge_0.8"] is None
+    assert sm["c4"]["sat_rps"] is None and sm["targets"]["pread_scan_frac_h2d_ge_0.75"]["scan_1GiB"] is None
     assert sm["targets"]["c5_served_beats_plain"]["p99"] is None
 
 
