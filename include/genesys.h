@@ -59,14 +59,16 @@ extern "C" {
 typedef struct genesys_config {
   uint32_t n_slots;            /* syscall-area slots; 0 = one per resident GPU thread
                                   (SMs x 2048), the paper's one-slot-per-active-
-                                  work-item sizing (Sec. 5)                            */
+                                  work-item sizing (Sec. 5); at most 2^24              */
   uint32_t n_service_threads;  /* CPU service threads, one doorbell ring each (>= 1)   */
   const int32_t *service_cpus; /* CPU to pin each service thread to, or NULL           */
   uint64_t staging_bytes;      /* pinned host-mapped staging arena                      */
   uint64_t coalesce_window_ns; /* Sec. 4.2: how long a service thread waits after the
                                   first request of a batch for more to arrive (0 = take
                                   what is ready)                                       */
-  uint32_t coalesce_max;       /* Sec. 4.2: most requests processed as one batch (>= 1) */
+  uint32_t coalesce_max;       /* Sec. 4.2: requests processed as one batch (>= 1); the
+                                  requests of one doorbell entry (up to a warp's 32)
+                                  are never split, so a batch may hold up to 31 more  */
   uint32_t merge;              /* 1: a batch's pread/pwrite requests that are
                                   contiguous in the file are merged into one Linux call
                                   (pread/pwrite or preadv/pwritev)                    */
@@ -585,7 +587,9 @@ int genesys_echo_client(uint16_t port_base, uint32_t n_sockets, uint32_t packet_
  * processing): the calling host thread publishes n_calls requests
  * pwrite(fd, payload + i * bytes_per_call, bytes_per_call, i * bytes_per_call)
  * into the slot area, one slot each, as a work-item-grain blocking launch
- * would (slots filled first, in rounds of n_slots), and *elapsed_ns is the
+ * would (slots filled first, in rounds of n_slots; one doorbell entry for 32
+ * consecutive slots that start at a multiple of 32, as a full warp rings),
+ * and *elapsed_ns is the
  * time from the first doorbell entry to the last completion, summed over the
  * rounds: the service threads' time alone, with no GPU in the loop.  payload
  * is a host address.  The context must be idle (no kernel running, no slot

@@ -181,6 +181,14 @@ __device__ __forceinline__ uint32_t ring_of(const genesys_dev &g, uint32_t slot)
   return genesys_ring_of(slot, g.n_rings);
 }
 
+/* The doorbell ring of a request: by file region for pread/pwrite (file
+ * neighbours from different blocks meet in one ring and merge), by slot
+ * group for other calls. */
+__device__ __forceinline__ uint32_t ring_for(const genesys_dev &g, uint32_t slot, uint32_t nr, uint64_t a0,
+                                             uint64_t a3) {
+  return (nr == SYS_pread64 || nr == SYS_pwrite64) ? genesys_ring_of_file(a0, a3, g.n_rings) : ring_of(g, slot);
+}
+
 /* ------------------------------------------------------ slot protocol
  * One thread.  Try to claim a slot (device-side lock in HBM, never an RMW on
  * host memory): up to 32 slots from `hint` on.  A claimed slot whose previous
@@ -295,9 +303,9 @@ __device__ __forceinline__ uint32_t slot_fill_warp(const genesys_dev &g, uint32_
  * first; the position is taken after it and the entry written at once.  A
  * fence followed by a relaxed system-scope store is a release pattern. */
 
-/* Doorbell for one published slot (one thread); returns its ring position. */
-__device__ __forceinline__ uint32_t ring_one(const genesys_dev &g, uint32_t s) {
-  const uint32_t r = ring_of(g, s);
+/* Doorbell for one published slot on ring r (one thread); returns its ring
+ * position. */
+__device__ __forceinline__ uint32_t ring_one(const genesys_dev &g, uint32_t s, uint32_t r) {
   if (!dcheck(g, r < g.n_rings && s < g.n_slots)) return 0;
   fence_acq_rel_sys();
   const uint32_t pos = atomicAdd(&g.ring_tail[r * 32u], 1u);
@@ -305,15 +313,17 @@ __device__ __forceinline__ uint32_t ring_one(const genesys_dev &g, uint32_t s) {
   return pos;
 }
 
-/* Doorbell for the lanes of `mask` that each filled slot `s`.  Every lane
- * fences its own slot stores (one warp-wide instruction); the lanes going to
- * the same ring (grouped with __match_any_sync) then take consecutive
- * positions with one atomic, and each lane writes its own entry, so a warp's
- * entries leave as one contiguous store instead of one store per lane.
- * Returns the calling lane's ring position (lane order within the group). */
-__device__ __forceinline__ uint32_t ring_warp(const genesys_dev &g, uint32_t mask, uint32_t s) {
-  const uint32_t r = ring_of(g, s);
+/* Doorbell for the lanes of `mask` that each filled slot `s`.  After a warp
+ * barrier (so that the fences below cover the slot stores of every lane, in
+ * case lanes wrote parts of each other's slots) every lane fences (one
+ * warp-wide instruction); the lanes going to the same ring (grouped with
+ * __match_any_sync) then take consecutive positions with one atomic, and each
+ * lane writes its own entry, so a warp's entries leave as one contiguous
+ * store instead of one store per lane.  Returns the calling lane's ring
+ * position (lane order within the group). */
+__device__ __forceinline__ uint32_t ring_warp(const genesys_dev &g, uint32_t mask, uint32_t s, uint32_t r) {
   dcheck(g, r < g.n_rings && s < g.n_slots);
+  __syncwarp(mask);
   fence_acq_rel_sys();
   const uint32_t peers = __match_any_sync(mask, r);
   const uint32_t lane = lane_id();
@@ -324,6 +334,25 @@ __device__ __forceinline__ uint32_t ring_warp(const genesys_dev &g, uint32_t mas
   const uint32_t pos = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
   st_relaxed_sys(g.rings + (size_t)r * (g.ring_mask + 1u) + (pos & g.ring_mask), GENESYS_RING_ENTRY(pos, s));
   return pos;
+}
+
+/* Doorbell for a full warp whose lanes filled the 32 consecutive slots
+ * s0 .. s0 + 31 (s0 a multiple of 32) with requests of ring r: one entry at
+ * one ring position announces the 32 requests.  The warp barrier orders
+ * every lane's slot stores before lane 0's system-scope fence, which orders
+ * them before the entry (a release on behalf of the warp).  Every lane of
+ * the warp calls; returns the ring position (the same for every lane). */
+__device__ __forceinline__ uint32_t ring_run(const genesys_dev &g, uint32_t s0, uint32_t r) {
+  dcheck(g, r < g.n_rings && s0 + GENESYS_RING_MAX_RUN <= g.n_slots);
+  __syncwarp();
+  uint32_t pos = 0;
+  if (lane_id() == 0) {
+    fence_acq_rel_sys();
+    pos = atomicAdd(&g.ring_tail[r * 32u], 1u);
+    st_relaxed_sys(g.rings + (size_t)r * (g.ring_mask + 1u) + (pos & g.ring_mask),
+                   GENESYS_RING_ENTRY_RUN(pos, s0, GENESYS_RING_MAX_RUN));
+  }
+  return __shfl_sync(0xFFFFFFFFu, pos, 0);
 }
 
 /* Wait until the CPU finished request `sq` of slot `s`; returns its result.
@@ -410,12 +439,13 @@ __device__ __forceinline__ int64_t single_call(const genesys_dev &g, uint32_t nr
   int64_t rc = slot_claim(g, hw_lane_id(), &s, t0);
   if (rc < 0) return rc;
   const uint32_t sq = slot_fill(g, s, nr, flags, a0, a1, a2, a3, a4, a5);
-  const uint32_t pos = ring_one(g, s);  // st.release.sys: the slot stores (and, through
-                                        // the group's barrier, its earlier stores) first
+  const uint32_t r = ring_for(g, s, nr, a0, a3);
+  const uint32_t pos = ring_one(g, s, r);  // fence first: the slot stores (and, through
+                                           // the group's barrier, its earlier stores)
   const uint64_t t_pub = g.trace_cap ? now_ns() : 0;
   int64_t ret = 0;
   if (wait) {
-    ret = slot_wait_ring(g, s, sq, ring_of(g, s), pos, t0);
+    ret = slot_wait_ring(g, s, sq, r, pos, t0);
     trace_call(g, s, sq, nr, (flags >> GENESYS_REQ_GRAN_SHIFT) & 3u, t0, t_pub, ret == -kETIMEDOUT ? 0 : now_ns());
     if (ret == -kETIMEDOUT) {  /* the CPU may still finish it: keep the slot's
                                   sequence so the next claimer waits for it */
@@ -438,8 +468,8 @@ struct Ticket {
   uint32_t slot;
   uint32_t seq;
   uint64_t t0;
-  uint32_t pos;  // ring position
-  uint32_t pad;
+  uint32_t pos;   // ring position
+  uint32_t ring;  // doorbell ring
 };
 
 __device__ __forceinline__ int64_t issue(const genesys_dev &g, Ticket *t, uint32_t nr, uint64_t a0 = 0,
@@ -449,13 +479,14 @@ __device__ __forceinline__ int64_t issue(const genesys_dev &g, Ticket *t, uint32
   int64_t rc = slot_claim(g, hw_lane_id(), &t->slot, t->t0);
   if (rc < 0) { t->slot = 0xFFFFFFFFu; return rc; }
   t->seq = slot_fill(g, t->slot, nr, GENESYS_REQ_TICKET | GENESYS_REQ_RELAXED, a0, a1, a2, a3, a4, a5);
-  t->pos = ring_one(g, t->slot);
+  t->ring = ring_for(g, t->slot, nr, a0, a3);
+  t->pos = ring_one(g, t->slot, t->ring);
   return 0;
 }
 
 __device__ __forceinline__ int64_t wait(const genesys_dev &g, const Ticket &t) {
   if (t.slot == 0xFFFFFFFFu) return -kETIMEDOUT;
-  const int64_t ret = slot_wait_ring(g, t.slot, t.seq, ring_of(g, t.slot), t.pos, now_ns());
+  const int64_t ret = slot_wait_ring(g, t.slot, t.seq, t.ring, t.pos, now_ns());
   trace_call(g, t.slot, t.seq, 0, GENESYS_GRAN_GROUP, t.t0, 0, ret == -kETIMEDOUT ? 0 : now_ns());
   slot_release(g, t.slot);
   if (ret != -kETIMEDOUT) note_latency(g, t.t0);
@@ -605,14 +636,16 @@ __device__ __forceinline__ int64_t call_at(const genesys_dev &g, uint32_t site, 
       // a full warp on 32 consecutive slots (the usual case: each lane got the
       // slot of its hardware id) writes them as whole lines
       const uint32_t s0 = __shfl_sync(active, s, __ffs(active) - 1);
+      const uint32_t r = ring_for(g, s, nr, a0, a3);
+      const uint32_t r0 = __shfl_sync(active, r, __ffs(active) - 1);
       const bool lines = okmask == 0xFFFFFFFFu && (s0 & 31u) == 0 &&
-                         __all_sync(0xFFFFFFFFu, s == s0 + lane_id()) && dcheck(g, s0 + 32u <= g.n_slots);
+                         __all_sync(0xFFFFFFFFu, s == s0 + lane_id() && r == r0) && dcheck(g, s0 + 32u <= g.n_slots);
       if (ok) {
         const uint32_t sq = lines ? slot_fill_warp(g, s, nr, flags, a0, a1, a2, a3, a4, a5)
                                   : slot_fill(g, s, nr, flags, a0, a1, a2, a3, a4, a5);
-        const uint32_t pos = ring_warp(g, okmask, s);
+        const uint32_t pos = lines ? ring_run(g, s0, r) : ring_warp(g, okmask, s, r);
         const uint64_t t_pub = g.trace_cap ? now_ns() : 0;
-        rc = B == BLOCKING ? slot_wait_ring(g, s, sq, ring_of(g, s), pos, t0) : 0;
+        rc = B == BLOCKING ? slot_wait_ring(g, s, sq, r, pos, t0) : 0;
         trace_call(g, s, sq, nr, GENESYS_GRAN_ITEM, t0, t_pub,
                    (B == BLOCKING && rc != -kETIMEDOUT) ? now_ns() : 0);
         slot_release(g, s);

@@ -90,11 +90,11 @@ static_assert(sizeof(genesys_slot) == GENESYS_SLOT_BYTES, "a slot is one 64-byte
 #define GENESYS_HD
 #endif
 
-/* Doorbell ring of a slot.  Slots are taken in groups of 256 (eight warps of
- * one SM: the slot a lane tries first is its hardware id), so the requests of
- * one thread block - usually neighbours in a file - meet in one ring, where
- * the service thread can merge them; the group number is hashed so that the
- * callers of different SMs and warp slots spread over all rings. */
+/* Doorbell ring of a slot, for calls other than positional file calls.
+ * Slots are taken in groups of 256 (eight warps of one SM: the slot a lane
+ * tries first is its hardware id), so the requests of one thread block meet
+ * in one ring; the group number is hashed so that the callers of different
+ * SMs and warp slots spread over all rings. */
 #define GENESYS_RING_GROUP_SHIFT 8u
 static inline GENESYS_HD uint32_t genesys_ring_of(uint32_t slot, uint32_t n_rings) {
   uint32_t g = slot >> GENESYS_RING_GROUP_SHIFT;
@@ -104,8 +104,32 @@ static inline GENESYS_HD uint32_t genesys_ring_of(uint32_t slot, uint32_t n_ring
   return g % n_rings;
 }
 
-/* Doorbell ring entry: bits 63..32 = ring position + 1, bits 31..0 = slot. */
-#define GENESYS_RING_ENTRY(pos, slot) ((((uint64_t)(uint32_t)((pos) + 1u)) << 32) | (uint64_t)(uint32_t)(slot))
+/* Doorbell ring of a positional file call (pread/pwrite): calls on the same
+ * 256 KiB region of one file meet in one ring, whichever GPU threads make
+ * them, so the ring's service thread finds file neighbours in its batches
+ * and merges them into one Linux call; the regions of a file spread over all
+ * rings.  Any slot may therefore reach any ring (each ring holds an entry
+ * for every slot). */
+#define GENESYS_RING_REGION_SHIFT 18u
+static inline GENESYS_HD uint32_t genesys_ring_of_file(uint64_t fd, uint64_t off, uint32_t n_rings) {
+  uint64_t z = (off >> GENESYS_RING_REGION_SHIFT) * 0x9E3779B97F4A7C15ull ^ (fd + 1) * 0xC2B2AE3D27D4EB4Full;
+  z ^= z >> 29;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 32;
+  return (uint32_t)(z % n_rings);
+}
+
+/* Doorbell ring entry: bits 63..32 = ring position + 1; bits 31..24 = the
+ * number of requests it announces, minus 1; bits 23..0 = the slot of the
+ * first.  An entry announces the requests of `count` consecutive slots: one
+ * (a single caller), or a whole warp's 32 when its lanes filled 32 consecutive
+ * slots (one ring position for the warp).  Slot numbers are below 2^24. */
+#define GENESYS_RING_SLOT_BITS 24u
+#define GENESYS_RING_MAX_RUN 32u
+#define GENESYS_RING_ENTRY_RUN(pos, slot, count)                                             \
+  ((((uint64_t)(uint32_t)((pos) + 1u)) << 32) | ((uint64_t)(((count) - 1u) & 0xFFu) << 24) | \
+   (uint64_t)((slot) & 0xFFFFFFu))
+#define GENESYS_RING_ENTRY(pos, slot) GENESYS_RING_ENTRY_RUN(pos, slot, 1u)
 
 /* Copies of each ring's finished-entries count (callers poll the copy of
  * their warp, so that no single host-memory word takes every poll). */

@@ -304,9 +304,14 @@ extern "C" int genesys_kv_start(genesys_ctx *c, const uint8_t *keys, const uint1
       int fd = socket(AF_INET, SOCK_DGRAM, 0);
       if (fd < 0) return fail_cleanup(GENESYS_EINVAL, "socket failed");
       s->socks.push_back(fd);
+      // SO_RCVBUFFORCE / SO_SNDBUFFORCE pass the system cap (net.core.rmem_max,
+      // often a few hundred KiB) when permitted: bursts of requests then wait in
+      // the socket instead of being dropped
       int buf = 64 << 20;
-      setsockopt(fd, SOL_SOCKET, SO_RCVBUF, &buf, sizeof buf);
-      setsockopt(fd, SOL_SOCKET, SO_SNDBUF, &buf, sizeof buf);
+      if (setsockopt(fd, SOL_SOCKET, SO_RCVBUFFORCE, &buf, sizeof buf) != 0)
+        setsockopt(fd, SOL_SOCKET, SO_RCVBUF, &buf, sizeof buf);
+      if (setsockopt(fd, SOL_SOCKET, SO_SNDBUFFORCE, &buf, sizeof buf) != 0)
+        setsockopt(fd, SOL_SOCKET, SO_SNDBUF, &buf, sizeof buf);
       sockaddr_in a{};
       a.sin_family = AF_INET;
       a.sin_port = htons((uint16_t)(port_base + w));

@@ -123,9 +123,13 @@ struct Batch {
   std::vector<uint32_t> hidx, hgen;  // open-addressing table: (call, fd, offset) -> run
   std::vector<uint32_t> slot_ids;    // slots of the ready ring entries
   uint32_t gen = 0;
-  explicit Batch(size_t n) : req(n), ptr(n), run(n + 1), next(n), has_pred(n), slot_ids(n) {
+  size_t target;                     // requests a batch takes (coalesce_max)
+  // room for the target and one more ring entry's requests (entries are taken whole)
+  explicit Batch(size_t want)
+      : req(want + GENESYS_RING_MAX_RUN - 1), ptr(req.size()), run(req.size() + 1), next(req.size()),
+        has_pred(req.size()), slot_ids(req.size()), target(want) {
     size_t cap = 16;
-    while (cap < 2 * n) cap <<= 1;
+    while (cap < 2 * req.size()) cap <<= 1;
     hidx.assign(cap, 0);
     hgen.assign(cap, 0);
   }
@@ -605,10 +609,13 @@ uint64_t process_batch(genesys_ctx *c, uint32_t ri, Batch &b, size_t n, Counters
   return t_end;
 }
 
-inline bool entry_ready(const uint64_t *ring, uint32_t mask, uint64_t pos, uint32_t *slot) {
+// Ring entry `pos` if written: the first slot and the number of requests it
+// announces (consecutive slots; see GENESYS_RING_ENTRY_RUN).
+inline bool entry_ready(const uint64_t *ring, uint32_t mask, uint64_t pos, uint32_t *slot, uint32_t *count) {
   const uint64_t e = __atomic_load_n(&ring[pos & mask], __ATOMIC_ACQUIRE);
   if ((uint32_t)(e >> 32) != (uint32_t)(pos + 1)) return false;
-  *slot = (uint32_t)e;
+  *slot = (uint32_t)e & ((1u << GENESYS_RING_SLOT_BITS) - 1u);
+  *count = (((uint32_t)e >> GENESYS_RING_SLOT_BITS) & 0xFFu) + 1u;
   return true;
 }
 
@@ -635,31 +642,35 @@ inline void read_request(genesys_ctx *c, uint32_t s, Request *r) {
   r->ret = 0;
 }
 
-// Take up to coalesce_max ready requests from ring `ri` and process them as one
-// batch (Sec. 4.2).  Returns the number processed.
+// Take ready entries from ring `ri` until the batch holds coalesce_max
+// requests (an entry's requests are taken whole, so a batch may hold up to
+// GENESYS_RING_MAX_RUN - 1 more) and process them as one batch (Sec. 4.2).
+// Returns the number of requests processed.
 size_t poll_ring(genesys_ctx *c, uint32_t ri, Batch &b) {
   const uint64_t *ring = c->rings + (size_t)ri * c->ring_cap;
   const uint32_t mask = c->ring_cap - 1;
-  uint64_t h = c->head[ri];
+  const uint64_t h = c->head[ri];
   std::vector<Request> &batch = b.req;
-  const size_t maxb = batch.size();
-  size_t n = 0;
-  uint32_t s;
+  const size_t target = b.target;
+  size_t n = 0, e = 0;  // requests, entries
+  uint32_t s, cnt;
   // take the ready entries first and prefetch their slots (written by the GPU,
   // so their lines are not in the CPU's caches), then read the slots
   uint32_t *slots = b.slot_ids.data();
-  const size_t cap_n = maxb;
-  while (n < cap_n && entry_ready(ring, mask, h + n, &s)) {
-    slots[n] = s;
-    __builtin_prefetch(&c->slots[s], 0, 0);
-    ++n;
+  while (n < target && entry_ready(ring, mask, h + e, &s, &cnt)) {
+    for (uint32_t q = 0; q < cnt; ++q) {
+      slots[n + q] = s + q;
+      __builtin_prefetch(&c->slots[s + q], 0, 0);
+    }
+    n += cnt;
+    ++e;
   }
   Counters &k = c->counters[ri];
   if (n == 0) {
     bump(k.empty_polls, 1);
-    uint32_t t;
+    uint32_t t, tc;
     for (uint32_t ahead : {1u, 8u, 32u, 64u})
-      if (entry_ready(ring, mask, h + ahead, &t)) {
+      if (entry_ready(ring, mask, h + ahead, &t, &tc)) {
         bump(k.hole_polls, 1);
         break;
       }
@@ -667,12 +678,13 @@ size_t poll_ring(genesys_ctx *c, uint32_t ri, Batch &b) {
   }
   const uint64_t t_pick = genesys_mono_ns();
   for (size_t i = 0; i < n; ++i) read_request(c, slots[i], &batch[i]);
-  if (n < maxb && c->cfg.coalesce_window_ns) {
+  if (n < target && c->cfg.coalesce_window_ns) {
     const uint64_t until = genesys_mono_ns() + c->cfg.coalesce_window_ns;
-    while (n < maxb && genesys_mono_ns() < until) {
-      if (entry_ready(ring, mask, h + n, &s)) {
-        read_request(c, s, &batch[n]);
-        ++n;
+    while (n < target && genesys_mono_ns() < until) {
+      if (entry_ready(ring, mask, h + e, &s, &cnt)) {
+        for (uint32_t q = 0; q < cnt; ++q) read_request(c, s + q, &batch[n + q]);
+        n += cnt;
+        ++e;
       } else {
         cpu_relax();
       }
@@ -680,10 +692,10 @@ size_t poll_ring(genesys_ctx *c, uint32_t ri, Batch &b) {
   }
   bump(k.pickup_ns, genesys_mono_ns() - t_pick);
   const uint64_t t_done = process_batch(c, ri, b, n, k);
-  c->head[ri] = h + n;
-  c->retired[ri].store(h + n, std::memory_order_release);
+  c->head[ri] = h + e;
+  c->retired[ri].store(h + e, std::memory_order_release);
   for (uint32_t q = 0; q < GENESYS_RING_DONE_COPIES; ++q)
-    __atomic_store_n(&c->ring_done[((size_t)ri * GENESYS_RING_DONE_COPIES + q) * 8], h + n, __ATOMIC_RELEASE);
+    __atomic_store_n(&c->ring_done[((size_t)ri * GENESYS_RING_DONE_COPIES + q) * 8], h + e, __ATOMIC_RELEASE);
   bump(k.complete_ns, genesys_mono_ns() - t_done);
   return n;
 }
@@ -944,19 +956,14 @@ int genesys_init(const genesys_config *cfg_in, int device, genesys_ctx **out) {
     }
     if (cfg.n_slots == 0) cfg.n_slots = c->host_only ? 65536u : c->n_sms * 2048u;
     if (cfg.n_slots < 32) cfg.n_slots = 32;
+    if (cfg.n_slots > (1u << GENESYS_RING_SLOT_BITS))
+      return fail(GENESYS_EINVAL, "n_slots above 2^24 (doorbell entries name slots in 24 bits)");
     c->cfg = cfg;
 
-    // doorbell rings: ring r receives the slots s with genesys_ring_of(s) == r,
-    // each with at most one request outstanding - so a ring whose capacity is
-    // the largest number of slots that map to one ring can never overflow.
-    {
-      std::vector<uint64_t> per(cfg.n_service_threads, 0);
-      const uint32_t gsz = 1u << GENESYS_RING_GROUP_SHIFT;
-      for (uint64_t s0 = 0; s0 < cfg.n_slots; s0 += gsz)
-        per[genesys_ring_of((uint32_t)s0, cfg.n_service_threads)] += std::min<uint64_t>(gsz, cfg.n_slots - s0);
-      const uint64_t most = *std::max_element(per.begin(), per.end());
-      c->ring_cap = (uint32_t)next_pow2(std::max<uint64_t>(most, 64));
-    }
+    // doorbell rings: a slot has at most one request outstanding, announced by
+    // one entry in one ring (any ring: positional file calls go by file
+    // region), so a ring with an entry for every slot can never overflow
+    c->ring_cap = (uint32_t)next_pow2(std::max<uint64_t>(cfg.n_slots, 64));
 
     int rc;
     if ((rc = host_alloc(c.get(), &c->slots, (size_t)cfg.n_slots * sizeof(genesys_slot)))) return rc;
@@ -1483,16 +1490,33 @@ int genesys_service_probe_order(genesys_ctx *c, int fd, const void *payload, uin
       }
       const uint64_t t0 = genesys_mono_ns();
       // doorbells: runs of `run` consecutive slots; run k is rung in pass
-      // k % stride, so neighbouring runs are a 1/stride of the round apart
+      // k % stride, so neighbouring runs are a 1/stride of the round apart.
+      // As a GPU warp does, 32 consecutive slots starting at a multiple of 32
+      // (always one ring) are announced by one entry, other slots one by one.
       const uint32_t n_runs = (m + run - 1) / run;
+      auto ring_at = [&](uint32_t s) {
+        return genesys_ring_of_file((uint64_t)(int64_t)fd, (i0 + s) * (uint64_t)bytes_per_call, R);
+      };
+      auto ring_entry = [&](uint32_t s, uint32_t count) {
+        const uint32_t r = ring_at(s);  // the ring a GPU pwrite of this request rings: by file region
+        const uint32_t pos = tails_raw[(size_t)r * 32]++;
+        __atomic_store_n(&c->rings[(size_t)r * c->ring_cap + (pos & (c->ring_cap - 1))],
+                         GENESYS_RING_ENTRY_RUN(pos, s, count), __ATOMIC_RELEASE);
+      };
       for (uint32_t pass = 0; pass < stride; ++pass)
-        for (uint32_t k = pass; k < n_runs; k += stride)
-          for (uint32_t s = k * run; s < m && s < (k + 1) * run; ++s) {
-            const uint32_t r = genesys_ring_of(s, R);
-            const uint32_t pos = tails_raw[(size_t)r * 32]++;
-            __atomic_store_n(&c->rings[(size_t)r * c->ring_cap + (pos & (c->ring_cap - 1))],
-                             GENESYS_RING_ENTRY(pos, s), __ATOMIC_RELEASE);
+        for (uint32_t k = pass; k < n_runs; k += stride) {
+          const uint32_t end = std::min(m, (k + 1) * run);
+          for (uint32_t s = k * run; s < end;) {
+            if (s % GENESYS_RING_MAX_RUN == 0 && s + GENESYS_RING_MAX_RUN <= end &&
+                ring_at(s) == ring_at(s + GENESYS_RING_MAX_RUN - 1)) {
+              ring_entry(s, GENESYS_RING_MAX_RUN);
+              s += GENESYS_RING_MAX_RUN;
+            } else {
+              ring_entry(s, 1);
+              ++s;
+            }
           }
+        }
       for (uint32_t s = 0; s < m; ++s) {
         uint64_t d;
         while ((uint32_t)((d = __atomic_load_n(&c->done[s], __ATOMIC_ACQUIRE)) >> 32) != seq[s]) {
@@ -1563,7 +1587,10 @@ int genesys_emulate_call(genesys_ctx *c, uint32_t nr, const uint64_t args[6], ui
     for (int i = 0; i < 6; ++i) __atomic_store_n(&sl->args[i], args[i], __ATOMIC_RELAXED);
     __atomic_store_n(&sl->req, ((uint64_t)nsq << 32) | ((uint64_t)(nr & 0xFFFFu) << 16) | (flags & 0xFFFFu),
                      __ATOMIC_RELEASE);
-    const uint32_t r = genesys_ring_of(s, c->cfg.n_service_threads);
+    // the ring the device would choose: by file region for pread/pwrite
+    const uint32_t r = (nr == SYS_pread64 || nr == SYS_pwrite64)
+                           ? genesys_ring_of_file(args[0], args[3], c->cfg.n_service_threads)
+                           : genesys_ring_of(s, c->cfg.n_service_threads);
     const uint32_t pos = __atomic_fetch_add(&c->ring_tail[r * 32], 1u, __ATOMIC_ACQ_REL);
     __atomic_store_n(&c->rings[(size_t)r * c->ring_cap + (pos & (c->ring_cap - 1))], GENESYS_RING_ENTRY(pos, s),
                      __ATOMIC_RELEASE);
