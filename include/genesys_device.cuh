@@ -322,7 +322,7 @@ __device__ __forceinline__ uint32_t ring_one(const genesys_dev &g, uint32_t s, u
  * store instead of one store per lane.  Returns the calling lane's ring
  * position (lane order within the group). */
 __device__ __forceinline__ uint32_t ring_warp(const genesys_dev &g, uint32_t mask, uint32_t s, uint32_t r) {
-  dcheck(g, r < g.n_rings && s < g.n_slots);
+  if (!dcheck(g, r < g.n_rings && s < g.n_slots)) r = 0;  // checked builds: counted, and kept in bounds
   __syncwarp(mask);
   fence_acq_rel_sys();
   const uint32_t peers = __match_any_sync(mask, r);
@@ -343,7 +343,7 @@ __device__ __forceinline__ uint32_t ring_warp(const genesys_dev &g, uint32_t mas
  * them before the entry (a release on behalf of the warp).  Every lane of
  * the warp calls; returns the ring position (the same for every lane). */
 __device__ __forceinline__ uint32_t ring_run(const genesys_dev &g, uint32_t s0, uint32_t r) {
-  dcheck(g, r < g.n_rings && s0 + GENESYS_RING_MAX_RUN <= g.n_slots);
+  if (!dcheck(g, r < g.n_rings && s0 + GENESYS_RING_MAX_RUN <= g.n_slots)) r = 0;  // counted, kept in bounds
   __syncwarp();
   uint32_t pos = 0;
   if (lane_id() == 0) {
