@@ -320,6 +320,7 @@ def summarize(line: dict) -> dict:
     plain5, served5 = c5.get("plain_first1000") or {}, c5.get("served_first1000") or {}
     pers5 = c5.get("persistent_first1000") or {}
     c2p, c2b = _at(ex, "forms", "plain_blocking_strong") or {}, _at(ex, "forms", "batched") or {}
+    c2pc = _at(ex, "forms", "plain_per_call_service") or {}
     oc = _at(ex, "oracle_checks") or {}
     out = {
         "c2c1_syscalls_per_s": _sig(ex.get("value")), "e2e": _sig(_at(ex, "e2e", "value")),
@@ -356,6 +357,12 @@ def summarize(line: dict) -> dict:
         "c5_served_beats_plain": {"syscalls_per_s": _beats(best5.get("syscalls_per_s"), plain5.get("syscalls_per_s")),
                                   "requests_per_s": _beats(best5.get("requests_per_s"), plain5.get("requests_per_s")),
                                   "p99": _beats(best5.get("p99_ms"), plain5.get("p99_ms"), False)},
+        # the same work-item calls, batched and merged by the service (Sec. 4.2) against call by call
+        "c2_batched_service_beats_per_call": {
+            "syscalls_per_s": _beats(c2p.get("syscalls_per_s"), c2pc.get("syscalls_per_s")),
+            "p99": _beats(c2p.get("p99_us"), c2pc.get("p99_us"), False)},
+        "c1_batched_beats_plain": _beats(_at(ex, "c1_4MiB", "batched", "GB_per_s"), _at(ex, "c1_4MiB", "plain", "GB_per_s")),
+        "c3_batched_beats_plain": _beats(_at(c3, "batched", "GB_per_s"), _at(c3, "plain", "GB_per_s")),
         # pread + scan against the host link: the 1 GiB scan and the C3 wordcount, each
         # against the stated fraction (0.75 of the measured H2D copy rate)
         "pread_scan_frac_h2d_ge_0.75": {
@@ -453,23 +460,46 @@ class Rig:
         self.ctx.close()
 
 
-def c3_run(rig, form):
-    """Wordcount over the full corpus; returns (ms, bytes, counts ok)."""
+def per_call_service(G, rig, local, service_threads, n):
+    """The work-item strong blocking pwrites of n GPU threads served call by
+    call: every request its own Linux call (no merging), each batch one
+    doorbell entry (coalesce_max 1), on a context of its own with the same
+    service threads; rate and per-call latency."""
+    with G.Context(device=local, service_threads=service_threads, coalesce_max=1, merge=False,
+                   staging_bytes=1 << 20, deadline_ns=10_000_000_000) as ctx:
+        fn = lambda: ctx.c2_pwrite(rig.fds[n], n, 0, 256, False, False, SEED_C2, rig.c2_stage, n * 64)  # noqa
+        fn()
+        ctx.latency(clear=True)
+        st0 = ctx.stats()
+        ms = rig.timed(fn)
+        lat = ctx.latency(clear=True)
+        ph = service_phases(st0, ctx.stats())
+    return {"combo": "work-item/strong/blocking", "service": "coalesce_max 1, no merging", "ms": round(ms, 3),
+            "syscalls_per_s": round(n / (ms * 1e-3), 1), "requests_per_s": round(n / (ms * 1e-3), 1),
+            "p50_us": round(pctl(lat, 50) / 1e3, 2) if len(lat) else None,
+            "p99_us": round(pctl(lat, 99) / 1e3, 2) if len(lat) else None, "service_ns_per_request": ph}
+
+
+def c3_run(rig, form, n_files=None):
+    """Wordcount over the full corpus (or its first n_files files, a small
+    case for profiling); returns (ms, bytes, counts ok)."""
     import numpy as np
     import workloads
     torch = rig.torch
     c = workloads.corpus(workloads.C3_FULL)
-    fds = [os.open(p, os.O_RDONLY) for p in c.paths]
+    k = len(c.paths) if n_files is None else min(int(n_files), len(c.paths))
+    paths, sizes = c.paths[:k], c.sizes[:k]
+    fds = [os.open(p, os.O_RDONLY) for p in paths]
     try:
         counts = torch.zeros(len(c.queries), dtype=torch.int64, device=rig.dev)
-        ms = rig.timed(lambda: rig.ctx.c3_wordcount(fds, c.sizes, c.queries, counts.data_ptr(), rig.c3_stage,
+        ms = rig.timed(lambda: rig.ctx.c3_wordcount(fds, sizes, c.queries, counts.data_ptr(), rig.c3_stage,
                                                      rig.c3_stage_bytes, chunk=C3_CHUNK, ctas=C3_CTAS,
                                                      threads=C3_THREADS, form=form))
-        ok = np.array_equal(counts.cpu().numpy().astype(np.uint64), c.truth_total())
+        ok = np.array_equal(counts.cpu().numpy().astype(np.uint64), c.truth[:k].sum(axis=0, dtype=np.uint64))
     finally:
         for fd in fds:
             os.close(fd)
-    return ms, c.total_bytes, ok
+    return ms, int(np.asarray(sizes, np.uint64).sum()), ok
 
 
 def sweep_step(rig, note=None):
@@ -550,9 +580,11 @@ def run_only(args):
             fn = (lambda: rig.c1(form)) if nbytes == C1_BYTES else (lambda: rig.scan(form, nbytes))  # noqa: E731
             calls = nbytes // (C1_CHUNK if nbytes == C1_BYTES else SCAN_CHUNK)
         elif kind == "c3":
-            form = G.FORM_BATCHED if rest == "batched" else G.FORM_PLAIN
-            c3_run(rig, form)
-            ms, nbytes, ok = c3_run(rig, form)
+            form_s, _, nf = rest.partition(":")
+            form = G.FORM_BATCHED if form_s == "batched" else G.FORM_PLAIN
+            nf = int(nf) if nf else None
+            c3_run(rig, form, nf)
+            ms, nbytes, ok = c3_run(rig, form, nf)
             out.update({"ms": round(ms, 3), "GB_per_s": round(nbytes / (ms * 1e-3) / 1e9, 2), "counts_ok": ok})
             print(json.dumps(out), flush=True)
             return
@@ -1234,6 +1266,10 @@ def run_genesys(args):
     plain = sweep[combo_key("work-item", False, False)]
     batched_key = max((k for k in sweep if "relaxed" in k), key=lambda k: sweep[k]["requests_per_s"])
     batched = sweep[batched_key]
+    # the same 2^20 work-item pwrites served call by call (Sec. 4.2 without
+    # coalescing: no merging, batches of one doorbell entry) beside the
+    # batched and merged service of the timed step
+    per_call = per_call_service(G, rig, local, step_cfg["service_threads"], n)
 
     # The work-item kernels are bound by the service threads' rate, not by the
     # link: their calls/s against the ceiling of the same requests published
@@ -1337,7 +1373,8 @@ def run_genesys(args):
                    "parallelism": f"replicas x{world}"},
         "requests_per_s": round(job_value(world, (sum(SIZES) * len(COMBOS) + c1_calls) * args.steps, tot_ms * 1e-3), 1),
         "forms": {"plain_blocking_strong": {"combo": "work-item/strong/blocking", **plain},
-                  "batched": {"combo": batched_key, **batched}},
+                  "batched": {"combo": batched_key, **batched},
+                  "plain_per_call_service": per_call},
         "plain_latency_by_threads": lat_by_size,
         "c1_4MiB": c1_forms,
         "sweep_2p20": sweep,
@@ -1503,7 +1540,7 @@ def main():
     ap.add_argument("--coalesce-max", type=int, default=64, help="--only: service batch size")
     ap.add_argument("--poll-max-ns", type=int, default=2048, help="--only: largest completion-poll back-off")
     ap.add_argument("--only", default=None, help="run one case: c2:<grain>/<order>/<block>:<threads>, "
-                                                 "c1:<plain|batched>:<bytes>, c3:<plain|batched>, c4, c5, fig10, f4")
+                                                 "c1:<plain|batched>:<bytes>, c3:<plain|batched>[:<first n files>], c4, c5, fig10, f4")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

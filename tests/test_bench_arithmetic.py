@@ -105,7 +105,9 @@ def _full_line():
         "forms": {"plain_blocking_strong": {"syscalls_per_s": 31600000.1, "requests_per_s": 31600000.1,
                                             "p50_us": 300.1, "p99_us": 900.2},
                   "batched": {"syscalls_per_s": 84000.5, "requests_per_s": 86000000.3, "p50_us": 200.1,
-                              "p99_us": 700.7}},
+                              "p99_us": 700.7},
+                  "plain_per_call_service": {"syscalls_per_s": 9000000.2, "requests_per_s": 9000000.2,
+                                             "p50_us": 9000.1, "p99_us": 20000.2}},
         "roofline": {"service": {"frac": 0.181234, "warp_interleaved_order": {"frac": 0.347712}}},
         "c1_4MiB": {"plain": {"GB_per_s": 5.31123}, "batched": {"GB_per_s": 7.7789}},
         "pread_scan_1GiB": {"autotuned": {"form": 0}, "plain": {"GB_per_s": 49.712, "frac_of_host_link_h2d": 0.894},
@@ -154,6 +156,8 @@ def test_summary_fits_the_kept_tail_and_carries_every_config():
     assert t["c2_batched_beats_plain"] == {"syscalls_per_s": False, "requests_per_s": True, "p99": True}
     assert t["c5_served_beats_plain"] == {"syscalls_per_s": True, "requests_per_s": True, "p99": True}
     assert t["pread_scan_frac_h2d_ge_0.75"] == {"scan_1GiB": True, "c3": True}
+    assert t["c2_batched_service_beats_per_call"] == {"syscalls_per_s": True, "p99": True}
+    assert t["c1_batched_beats_plain"] is True and t["c3_batched_beats_plain"] is True
 
 
 def test_summary_of_a_line_without_extras():
