@@ -388,6 +388,12 @@ __device__ __forceinline__ int64_t slot_wait(const genesys_dev &g, uint32_t s, u
  * has passed its position, one acquire fence and one read of its completion
  * word give the result. */
 constexpr uint32_t kMaxNapNs = 100000;
+/* Before a caller has seen its ring's count advance it does not know the
+ * rate the entries ahead of it are served at: its first nap assumes this many
+ * ns per entry (a lone request costs the service about that; a warp's entry
+ * of 32 more), so a caller deep in a queue does not poll the host while the
+ * entries ahead of it are still being served. */
+constexpr uint32_t kPriorNsPerEntry = 64;
 
 __device__ __forceinline__ int64_t slot_wait_ring(const genesys_dev &g, uint32_t s, uint32_t sq, uint32_t r,
                                                   uint32_t pos, uint64_t t0) {
@@ -408,6 +414,8 @@ __device__ __forceinline__ int64_t slot_wait_ring(const genesys_dev &g, uint32_t
     if (when0 == 0) {
       when0 = now;
       fin0 = fin;
+      const uint64_t prior = (uint64_t)ahead * kPriorNsPerEntry;
+      nap = prior > nap ? prior : nap;
     } else if (fin != fin0) {
       const uint64_t est = (now - when0) / (uint32_t)(fin - fin0) * (uint64_t)ahead;  // ns per entry x ahead
       nap = est > nap ? est : nap;
