@@ -344,6 +344,7 @@ def summarize(line: dict) -> dict:
         "oracle": {"cores": _at(ex, "probes", "host_cpus"),
                    "c2c1_sps_1t": _sig(_at(ex, "cpu_baseline", "value")),
                    "c1_eq": _at(ex, "cpu_baseline", "c1_histogram_equals_oracle"),
+                   "c2_files_eq": oc.get("c2_files_equal"), "scan_eq": oc.get("scan_1GiB_histogram_equal"),
                    "c3_GBps_1t": _sig(_at(c3, "cpu_baseline_oracle", "one_thread_GB_per_s")),
                    "c3_GBps_all": _sig(_at(c3, "cpu_baseline_oracle", "files_to_cores_GB_per_s")),
                    "c4_sat_rps_1t": _sig(_at(c4, "cpu_baseline_oracle_server", "saturation_req_per_s")),
@@ -535,13 +536,19 @@ def tune_step(args, local, rank):
         finally:
             rig.close()
 
-    # slot areas smaller than the default (one slot per resident thread) made
-    # work-item callers wait for slots and doubled the step in every run, so
-    # the slot area is not searched; batches up to 4096 (with the doorbells
-    # written without holes, batches fill to the cap)
+    # service threads x batch size (batches up to 4096: with the doorbells
+    # written without holes, batches fill to the cap) on the default slot
+    # area, one slot per resident thread; then the slot-area size for the best
+    # pair (smaller areas make work-item callers wait for slots: a 32 K-slot
+    # area doubled the step in every run)
     best, table = tuner.tune(key, autotune.grid(service_threads=(1, 2, 4), coalesce_max=(256, 1024, 4096),
                                                 poll_max_ns=(2048,), n_slots=(0,)), run, repeats=2)
-    return best, table
+    import torch
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    key2 = tuner.key("bench-step-slots", sizes=len(SIZES), combos=len(COMBOS),
+                     base=f"{best['service_threads']}x{best['coalesce_max']}")
+    best2, table2 = tuner.tune(key2, [dict(best, n_slots=v) for v in (0, 1024 * sms, 512 * sms)], run, repeats=2)
+    return best2, table + table2
 
 
 # ---------------------------------------------------------------- one case
@@ -633,7 +640,7 @@ def profile_extras(args, rig, local, rank, link, checks=None):
     best = autotune.tune_scan(local, rig.fd_scan, SCAN_BYTES)
     per_form = best.get("by_form") or {str(best["form"]): best}
     sb = max(c["groups"] * c["chunk"] * (32 if c["form"] == G.FORM_WARP else 2) for c in per_form.values())
-    res = {}
+    res, hists = {}, {}
     names = {G.FORM_PLAIN: "plain", G.FORM_BATCHED: "batched", G.FORM_WARP: "warp", G.FORM_HBM: "hbm_landing"}
     for f, cfg in sorted(per_form.items()):
         with G.Context(device=local, service_threads=cfg["service_threads"], staging_bytes=sb + (1 << 20)) as ctx:
@@ -642,12 +649,21 @@ def profile_extras(args, rig, local, rank, link, checks=None):
                                           chunk=cfg["chunk"], groups=cfg["groups"], threads=1024, form=cfg["form"])
             fn()
             ms = min(rig.timed(fn) for _ in range(3))
+            rig.hist[0].zero_()
+            fn()  # once more from zero: the histogram this form computes
+            hists[names[cfg["form"]]] = rig.hist[0].cpu().numpy().view(np.uint32).copy()
             gbs = SCAN_BYTES / (ms * 1e-3) / 1e9
             res[names[cfg["form"]]] = {"GB_per_s": round(gbs, 2), "frac_of_host_link_h2d": round(gbs / link["h2d"], 4),
                                        "frac_of_hbm_peak": round(gbs / hbm_peak(), 5),
                                        "ms": round(ms, 2), "chunk": cfg["chunk"], "groups": cfg["groups"],
                                        "service_threads": cfg["service_threads"]}
-    out["pread_scan_1GiB"] = {"autotuned": {k: v for k, v in best.items() if k != "by_form"}, **res}
+    first = next(iter(hists.values()))
+    out["pread_scan_1GiB"] = {"autotuned": {k: v for k, v in best.items() if k != "by_form"}, **res,
+                              # what holds at any size: the forms agree, every byte is counted once
+                              "histograms_checked": bool(all(np.array_equal(h, first) for h in hists.values()) and
+                                                         int(first.sum(dtype=np.uint64)) == SCAN_BYTES)}
+    if checks is not None:
+        checks["scan"] = (rig.scan_path, first)
     # C3 wordcount over the full corpus
     c = workloads.corpus(workloads.C3_FULL)
     fds = [os.open(p, os.O_RDONLY) for p in c.paths]
@@ -1323,7 +1339,7 @@ def run_genesys(args):
     link = host_link_peak(torch)
     link["round_trip_ns"] = G.link_pingpong(local, rounds=20000)  # GPU <-> host flag, the floor of a blocking call
     probes = host_probes(torch, local, rig.scan_path)
-    checks = {}
+    checks = {"c2_files": [(nn, os.path.join(rig.d, f"c2_{nn}.bin")) for nn in SIZES]}
     extras = profile_extras(args, rig, local, rank, link, checks) if args.extras else {}
     # dominant kernel of the timed region and its host-link roofline
     tot = {k: sum(v) for k, v in kernel_ms.items()}
@@ -1413,6 +1429,20 @@ def oracle_checks(checks: dict) -> dict:
     import numpy as np
     import oracle
     out = {"ran": True}
+    if "c2_files" in checks:
+        # the files the sweep wrote (every combination writes the same bytes)
+        # against the oracle's pwrites of the same threads
+        same = {}
+        for n, path in checks["c2_files"]:
+            ref = path + ".oracle"
+            oracle.c2_pwrite(ref, n, 1, SEED_C2)
+            same[str(n)] = bool(filecmp.cmp(path, ref, shallow=False))
+            os.unlink(ref)
+        out["c2_files_equal"] = all(same.values())
+        out["c2_files_by_threads"] = same
+    if "scan" in checks:
+        path, hist = checks["scan"]
+        out["scan_1GiB_histogram_equal"] = bool(np.array_equal(hist, oracle.c1_histogram(path, SCAN_CHUNK)))
     if "c4" in checks:
         # every reply that came back, against the oracle's replay in client
         # sequence order of the requests that reached the server (all of them

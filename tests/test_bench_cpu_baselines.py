@@ -59,3 +59,29 @@ def test_service_phases_from_a_host_only_context(tmp_path):
                        "empty_polls_per_batch", "hole_polls_per_batch"}
     assert all(v >= 0 for v in ph.values()) and ph["os_call"] > 0 and ph["requests_per_batch"] >= 1
     assert ph["order"] + ph["os_call"] <= ph["busy"] + 1e-6
+
+
+def test_oracle_checks_of_the_c2_files_and_the_scan(tmp_path):
+    """The bench's oracle leg compares the files the sweep wrote and the scan's
+    histogram with the oracle's, and a one-byte difference in either shows."""
+    import numpy as np
+    import oracle
+    import workloads
+    n = 1000
+    c2 = tmp_path / "c2.bin"
+    want = tmp_path / "want.bin"
+    oracle.c2_pwrite(str(want), n, 32, bench.SEED_C2)      # written another way: a warp's calls
+    c2.write_bytes(want.read_bytes())
+    scan = workloads.c1_file(str(tmp_path / "scan.bin"), 100_000, seed=7)
+    hist = oracle.c1_histogram(scan, 4096)
+    out = bench.oracle_checks({"c2_files": [(n, str(c2))], "scan": (scan, hist.copy())})
+    assert out["c2_files_equal"] is True and out["scan_1GiB_histogram_equal"] is True
+    data = bytearray(c2.read_bytes())
+    data[12345] ^= 1
+    c2.write_bytes(bytes(data))
+    bad = hist.copy()
+    bad[3] += 1
+    bad[4] -= 1
+    out = bench.oracle_checks({"c2_files": [(n, str(c2))], "scan": (scan, bad)})
+    assert out["c2_files_equal"] is False and out["scan_1GiB_histogram_equal"] is False
+    assert not (tmp_path / "c2.bin.oracle").exists()
