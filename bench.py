@@ -52,6 +52,7 @@ C1_BYTES, C1_CHUNK, C1_GROUPS, C1_THREADS = 4 << 20, 4096, 64, 256
 SCAN_BYTES, SCAN_CHUNK, SCAN_GROUPS, SCAN_THREADS = 1 << 30, 1 << 20, 148, 1024
 C3_CHUNK, C3_CTAS, C3_THREADS = 1 << 20, 296, 512
 GRAN_BY_NAME = {name: (g, bt) for name, g, bt in GRAINS}
+PROFILE_REPEATS = 3  # runs of each combination in the untimed profile pass
 
 
 def combo_key(name, relaxed, nb):
@@ -324,7 +325,7 @@ def summarize(line: dict) -> dict:
     oc = _at(ex, "oracle_checks") or {}
     out = {
         "c2c1_syscalls_per_s": _sig(ex.get("value")), "e2e": _sig(_at(ex, "e2e", "value")),
-        "wi_2p20": {"calls_per_s": _sig(c2p.get("syscalls_per_s")),
+        "wi_2p20": {"calls_per_s": _sig(_at(ex, "roofline", "service", "achieved")),
                     "frac_file_order": _sig(_at(ex, "roofline", "service", "frac")),
                     "frac_interleaved": _sig(_at(ex, "roofline", "service", "warp_interleaved_order", "frac"))},
         "c1_4MiB_GBps": {k: _sig(_at(ex, "c1_4MiB", k, "GB_per_s")) for k in ("plain", "batched")},
@@ -1257,19 +1258,28 @@ def run_genesys(args):
     # ---- profile pass (untimed): per-combination rate and latency at 2^20,
     # latency of the plain form at every size, plain vs batched forms,
     # pread+scan GB/s at 1 GiB and over the C3 corpus
+    # Each combination runs PROFILE_REPEATS times: rate and latency are the
+    # median run's, `ms_best` the fastest (host cores are shared, and one
+    # run can land on a slow stretch); the work-item phases are the best run's,
+    # like the host-only probe it is compared with (best of 3).
     sweep = {}
     n = max(SIZES)
     plain_phases = None
     for name, g, bt, relaxed, nb in COMBOS:
-        ctx.latency(clear=True)
-        st0 = ctx.stats() if combo_key(name, relaxed, nb) == combo_key("work-item", False, False) else None
-        ms = rig.timed(lambda: rig.c2(n, g, bt, relaxed, nb))
-        if st0 is not None:
-            plain_phases = service_phases(st0, ctx.stats())
-        lat = ctx.latency(clear=True)
+        is_plain = combo_key(name, relaxed, nb) == combo_key("work-item", False, False)
+        runs = []
+        for _ in range(PROFILE_REPEATS):
+            ctx.latency(clear=True)
+            st0 = ctx.stats() if is_plain else None
+            ms = rig.timed(lambda: rig.c2(n, g, bt, relaxed, nb))
+            runs.append((ms, ctx.latency(clear=True), service_phases(st0, ctx.stats()) if is_plain else None))
+        runs.sort(key=lambda t: t[0])
+        ms, lat, _ = runs[len(runs) // 2]
+        if is_plain:
+            plain_phases = runs[0][2]
         calls = calls_for(g, bt, n)
         sweep[combo_key(name, relaxed, nb)] = {
-            "ms": round(ms, 3), "syscalls_per_s": round(calls / (ms * 1e-3), 1),
+            "ms": round(ms, 3), "ms_best": round(runs[0][0], 3), "syscalls_per_s": round(calls / (ms * 1e-3), 1),
             "requests_per_s": round(n / (ms * 1e-3), 1),
             "p50_us": round(pctl(lat, 50) / 1e3, 2) if len(lat) else None,
             "p99_us": round(pctl(lat, 99) / 1e3, 2) if len(lat) else None}
@@ -1298,9 +1308,13 @@ def run_genesys(args):
         rate = ctx.service_probe(rig.fds[n_probe], rig.c2_stage, 64, n_probe)
         probes_run.append((rate, service_phases(st0, ctx.stats())))
     ceiling, probe_phases = max(probes_run, key=lambda t: t[0])
+    # best of the GPU path's runs against the probe's best; the median beside it
+    plain_best = round(n / (plain["ms_best"] * 1e-3), 1)
     service_roofline = {"bound": "host_service", "kernel": "c2_pwrite_kernel<work-item,strong,blocking>",
-                        "threads": n_probe, "achieved": plain["syscalls_per_s"], "peak": round(ceiling, 1),
-                        "unit": "calls/s", "frac": round(plain["syscalls_per_s"] / ceiling, 4),
+                        "threads": n_probe, "achieved": plain_best, "achieved_median": plain["syscalls_per_s"],
+                        "peak": round(ceiling, 1), "unit": "calls/s", "frac": round(plain_best / ceiling, 4),
+                        "frac_median": round(plain["syscalls_per_s"] / ceiling, 4),
+                        "achieved_source": f"best of {PROFILE_REPEATS} runs of the 2^20-thread kernel",
                         "peak_source": "genesys_service_probe: the same 2^20 64-byte pwrites published by a host "
                                        "thread, same service threads and batch size, best of 3 (measured)",
                         # where each request's service time goes, GPU in the loop against the probe
@@ -1317,7 +1331,8 @@ def run_genesys(args):
             runs.append((r_il, service_phases(st0, ctx.stats())))
         il_peak, il_phases = max(runs, key=lambda t: t[0])
         service_roofline["warp_interleaved_order"] = {
-            "peak": round(il_peak, 1), "frac": round(plain["syscalls_per_s"] / il_peak, 4),
+            "peak": round(il_peak, 1), "frac": round(plain_best / il_peak, 4),
+            "frac_median": round(plain["syscalls_per_s"] / il_peak, 4),
             "order": "doorbells in runs of 32 calls (a warp), neighbouring runs 1/8 of a round apart (the 8 warps "
                      "of a 256-thread block), best of 2 (measured)",
             "service_ns_per_request": il_phases}
@@ -1329,10 +1344,13 @@ def run_genesys(args):
     # buffer and file by one host thread.
     host_write, host_chunk = host_pwrite_peak(rig.fds[n_probe], rig.c2_stage, n_probe * 64)
     coarse = sweep[combo_key("wg1024", True, False)]
-    coarse_gbs = n_probe * 64 / (coarse["ms"] * 1e-3) / 1e9
+    coarse_gbs = n_probe * 64 / (coarse["ms_best"] * 1e-3) / 1e9
+    coarse_median = n_probe * 64 / (coarse["ms"] * 1e-3) / 1e9
     coarse_roofline = {"bound": "host_file_write", "kernel": "c2_pwrite_kernel<work-group,relaxed,blocking>",
                        "threads": n_probe, "group": 1024, "achieved": round(coarse_gbs, 3),
-                       "peak": round(host_write, 3), "unit": "GB/s", "frac": round(coarse_gbs / host_write, 4),
+                       "achieved_median": round(coarse_median, 3), "peak": round(host_write, 3), "unit": "GB/s",
+                       "frac": round(coarse_gbs / host_write, 4), "frac_median": round(coarse_median / host_write, 4),
+                       "achieved_source": f"best of {PROFILE_REPEATS} runs",
                        "peak_source": f"one host thread writing the same 64 MiB from the same pinned buffer to the "
                                       f"same tmpfs file with pwrite calls of 256 KiB-64 MiB, best of 3 each (best: "
                                       f"{host_chunk >> 10} KiB calls; measured)"}
@@ -1378,7 +1396,10 @@ def run_genesys(args):
     line = {
         "metric": "GPU syscalls/s (C2 pwrite invocation sweep + C1 pread pass)",
         "value": round(value, 1), "unit": "syscalls/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(tot_ms / args.steps, 3), "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": round(tot_ms / args.steps, 3),
+        # the step's kernels alone (device time); the rest of ms_per_step is
+        # launching, synchronising and draining between them
+        "kernel_ms_per_step": round(sum(tot.values()) / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": WORKLOAD,
                    "threads": SIZES, "combinations": len(COMBOS), "kernels_per_step": len(SIZES) * len(COMBOS) + 2,

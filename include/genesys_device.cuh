@@ -189,40 +189,83 @@ __device__ __forceinline__ uint32_t ring_for(const genesys_dev &g, uint32_t slot
   return (nr == SYS_pread64 || nr == SYS_pwrite64) ? genesys_ring_of_file(a0, a3, g.n_rings) : ring_of(g, slot);
 }
 
+/* Give up the claim lock of a slot this thread owns without using it. */
+__device__ __forceinline__ void slot_release_lock(const genesys_dev &g, uint32_t s) {
+  __threadfence();
+  atomicExch(&g.owner[s], 0u);
+}
+
 /* ------------------------------------------------------ slot protocol
- * One thread.  Try to claim a slot (device-side lock in HBM, never an RMW on
- * host memory): up to 32 slots from `hint` on.  A claimed slot whose previous
- * request the CPU has not finished yet (a non-blocking call may still be in
- * flight) is waited for, bounded: a slot still held by an unfinished request
- * delays the new call (Sec. 5, Fig. 4).  Returns 1 with *slot_out set, 0 if
- * every slot tried is taken, or -ETIMEDOUT. */
+ * Wait (bounded) until the CPU has finished the previous request of slot `s`,
+ * which the caller owns: sequence `sq` is the slot's last.  Returns 0, or
+ * -ETIMEDOUT with the slot released. */
+__device__ __forceinline__ int64_t slot_wait_previous(const genesys_dev &g, uint32_t s, uint32_t sq, uint64_t t0) {
+  uint32_t ns = 128;
+  while ((uint32_t)(ld_relaxed_sys(&g.done[s]) >> 32) != sq) {
+    if (expired(g, t0)) {
+      __threadfence();
+      atomicExch(&g.owner[s], 0u);
+      note_error(g, -kETIMEDOUT);
+      return -kETIMEDOUT;
+    }
+    __nanosleep(ns);
+    ns = ns < 2048 ? ns * 2 : ns;
+  }
+  fence_acq_rel_sys();
+  st_relaxed_gpu(&g.known_done[s], sq);
+  return 0;
+}
+
+/* One thread.  Try to claim a slot (device-side lock in HBM, never an RMW on
+ * host memory): up to 32 slots from `hint` on.  A slot's previous request may
+ * still be in flight (a non-blocking call releases its slot once published).
+ * Without `skip_busy` the first free slot is taken and its previous request
+ * waited for, bounded: a slot still held by an unfinished request delays the
+ * new call (Sec. 5, Fig. 4).  With `skip_busy` (one caller claiming one slot)
+ * a slot whose previous request is unfinished is passed over for a later one
+ * of the 32 that is ready, one look at its completion word each; only when
+ * none is does the caller wait, for the first it passed over (kept owned
+ * meanwhile: the CPU finishes it whatever the GPU holds, so no hold-and-wait).
+ * Returns 1 with *slot_out set, 0 if every slot tried is taken, or
+ * -ETIMEDOUT. */
 __device__ __forceinline__ int64_t slot_try_claim(const genesys_dev &g, uint32_t hint, uint32_t *slot_out,
-                                                  uint64_t t0) {
+                                                  uint64_t t0, bool skip_busy = false) {
   uint32_t s = hint % g.n_slots;
+  uint32_t busy = 0xFFFFFFFFu, busy_sq = 0;  // the first owned slot with an unfinished request
   for (uint32_t probe = 0; probe < 32; ++probe) {
     if (!dcheck(g, s < g.n_slots)) return -kETIMEDOUT;
     if (atomicCAS(&g.owner[s], 0u, 1u) == 0u) {
       __threadfence();
       const uint32_t sq = ld_relaxed_gpu(&g.seq[s]);
-      if (ld_relaxed_gpu(&g.known_done[s]) != sq) {
-        uint32_t ns = 128;
-        while ((uint32_t)(ld_relaxed_sys(&g.done[s]) >> 32) != sq) {
-          if (expired(g, t0)) {
-            __threadfence();
-            atomicExch(&g.owner[s], 0u);
-            note_error(g, -kETIMEDOUT);
-            return -kETIMEDOUT;
-          }
-          __nanosleep(ns);
-          ns = ns < 2048 ? ns * 2 : ns;
-        }
+      bool ready = ld_relaxed_gpu(&g.known_done[s]) == sq;
+      if (!ready && skip_busy && (uint32_t)(ld_relaxed_sys(&g.done[s]) >> 32) == sq) {
         fence_acq_rel_sys();
         st_relaxed_gpu(&g.known_done[s], sq);
+        ready = true;
       }
-      *slot_out = s;
-      return 1;
+      if (ready || !skip_busy) {
+        if (busy != 0xFFFFFFFFu) slot_release_lock(g, busy);
+        if (!ready) {
+          const int64_t w = slot_wait_previous(g, s, sq, t0);
+          if (w < 0) return w;
+        }
+        *slot_out = s;
+        return 1;
+      }
+      if (busy == 0xFFFFFFFFu) {
+        busy = s;
+        busy_sq = sq;
+      } else {
+        slot_release_lock(g, s);
+      }
     }
     s = (s + 1 == g.n_slots) ? 0 : s + 1;
+  }
+  if (busy != 0xFFFFFFFFu) {
+    const int64_t w = slot_wait_previous(g, busy, busy_sq, t0);
+    if (w < 0) return w;
+    *slot_out = busy;
+    return 1;
   }
   if (expired(g, t0)) {
     note_error(g, -kETIMEDOUT);
@@ -234,10 +277,10 @@ __device__ __forceinline__ int64_t slot_try_claim(const genesys_dev &g, uint32_t
 /* One thread: claim a slot, waiting (bounded, with back-off) while all are
  * taken.  The caller must not hold anything other callers need meanwhile. */
 __device__ __forceinline__ int64_t slot_claim(const genesys_dev &g, uint32_t hint, uint32_t *slot_out,
-                                              uint64_t t0) {
+                                              uint64_t t0, bool skip_busy = false) {
   uint32_t ns = 32;
   for (uint32_t round = 0;; ++round) {
-    const int64_t r = slot_try_claim(g, hint + round * 32u, slot_out, t0);
+    const int64_t r = slot_try_claim(g, hint + round * 32u, slot_out, t0, skip_busy);
     if (r != 0) return r < 0 ? r : 0;
     __nanosleep(ns);
     ns = ns < 4096 ? ns * 2 : ns;
@@ -444,7 +487,7 @@ __device__ __forceinline__ int64_t single_call(const genesys_dev &g, uint32_t nr
                                                uint64_t a5) {
   const uint64_t t0 = now_ns();
   uint32_t s;
-  int64_t rc = slot_claim(g, hw_lane_id(), &s, t0);
+  int64_t rc = slot_claim(g, hw_lane_id(), &s, t0, true);
   if (rc < 0) return rc;
   const uint32_t sq = slot_fill(g, s, nr, flags, a0, a1, a2, a3, a4, a5);
   const uint32_t r = ring_for(g, s, nr, a0, a3);
@@ -484,7 +527,7 @@ __device__ __forceinline__ int64_t issue(const genesys_dev &g, Ticket *t, uint32
                                          uint64_t a1 = 0, uint64_t a2 = 0, uint64_t a3 = 0, uint64_t a4 = 0,
                                          uint64_t a5 = 0) {
   t->t0 = now_ns();
-  int64_t rc = slot_claim(g, hw_lane_id(), &t->slot, t->t0);
+  int64_t rc = slot_claim(g, hw_lane_id(), &t->slot, t->t0, true);
   if (rc < 0) { t->slot = 0xFFFFFFFFu; return rc; }
   t->seq = slot_fill(g, t->slot, nr, GENESYS_REQ_TICKET | GENESYS_REQ_RELAXED, a0, a1, a2, a3, a4, a5);
   t->ring = ring_for(g, t->slot, nr, a0, a3);

@@ -1016,6 +1016,9 @@ int genesys_init(const genesys_config *cfg_in, int device, genesys_ctx **out) {
   });
 }
 
+// How long genesys_drain spins before it sleeps between looks.
+constexpr uint64_t kDrainSpinNs = 50000;
+
 int genesys_drain(genesys_ctx *c, uint64_t timeout_ns) {
   return genesys_guard("genesys_drain", [&]() -> int {
     if (!c) return fail(GENESYS_EINVAL, "ctx is NULL");
@@ -1023,7 +1026,13 @@ int genesys_drain(genesys_ctx *c, uint64_t timeout_ns) {
     int rc = read_tails(c, tails);
     if (rc) return rc;
     std::unique_ptr<Batch> batch;  // NO_THREADS mode: the caller services the rings
-    const uint64_t until = genesys_mono_ns() + timeout_ns;
+    const uint64_t start = genesys_mono_ns(), until = start + timeout_ns;
+    // After a blocking launch its last requests retire within microseconds of
+    // its end: spin briefly before sleeping, since a sleep costs tens of
+    // microseconds of timer slack (once per launch when a step runs many).  The
+    // spin stays short so that a long drain (non-blocking calls still being
+    // served) does not take a core from the service threads.
+    const uint64_t spin_until = start + kDrainSpinNs;
     for (uint32_t r = 0; r < c->cfg.n_service_threads; ++r) {
       for (;;) {
         // positions are 32-bit on the device: compare modulo 2^32
@@ -1033,6 +1042,8 @@ int genesys_drain(genesys_ctx *c, uint64_t timeout_ns) {
           std::lock_guard<std::mutex> g(c->svc_mu);
           if (!batch) batch.reset(new Batch(std::max<uint32_t>(1, c->cfg.coalesce_max)));
           poll_ring(c, r, *batch);
+        } else if (genesys_mono_ns() < spin_until) {
+          for (int i = 0; i < 32; ++i) cpu_relax();
         } else {
           std::this_thread::sleep_for(std::chrono::microseconds(5));
         }

@@ -108,7 +108,8 @@ def _full_line():
                               "p99_us": 700.7},
                   "plain_per_call_service": {"syscalls_per_s": 9000000.2, "requests_per_s": 9000000.2,
                                              "p50_us": 9000.1, "p99_us": 20000.2}},
-        "roofline": {"service": {"frac": 0.181234, "warp_interleaved_order": {"frac": 0.347712}}},
+        "roofline": {"service": {"achieved": 33400000.2, "frac": 0.181234,
+                                 "warp_interleaved_order": {"frac": 0.347712}}},
         "c1_4MiB": {"plain": {"GB_per_s": 5.31123}, "batched": {"GB_per_s": 7.7789}},
         "pread_scan_1GiB": {"autotuned": {"form": 0}, "plain": {"GB_per_s": 49.712, "frac_of_host_link_h2d": 0.894},
                             "warp": {"GB_per_s": 51.1, "frac_of_host_link_h2d": 0.919},
@@ -147,6 +148,7 @@ def test_summary_fits_the_kept_tail_and_carries_every_config():
     sm = line["summary"]
     assert len(json.dumps(sm)) <= 1350, len(json.dumps(sm))
     assert sm["scan_1GiB"] == {"form": "warp", "GBps": 51.1, "frac_h2d": 0.919}
+    assert sm["wi_2p20"] == {"calls_per_s": 33400000, "frac_file_order": 0.181, "frac_interleaved": 0.348}
     assert sm["c3"]["GBps"] == 49.5 and sm["c3"]["truth_eq"] is True
     assert sm["c4"]["sat_rps"] == 799000 and sm["c4"]["replies_eq_oracle"] is True
     assert sm["c4"]["p99_us"] == 813 and sm["c4"]["best_any_rps"] == 1300000

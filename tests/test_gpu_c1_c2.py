@@ -194,6 +194,28 @@ def test_c2_small_slot_area_and_coalescing_window(G, tmp_path, n_slots, threads,
         assert st["failed"] == 0
 
 
+@pytest.mark.parametrize("gran,bt", [(1, 256), (2, 64)])
+def test_nonblocking_callers_pass_over_slots_still_in_flight(G, tmp_path, gran, bt):
+    """Non-blocking warp and work-group pwrites of 2^20 threads on a context
+    whose rings nobody serves until the kernel has ended (no service threads;
+    the drain serves them afterwards).  Later blocks on an SM start from the
+    slots of their hardware ids, whose previous requests are still unserved:
+    they take other ready slots instead of waiting, so the kernel ends on its
+    own (a caller that waited would run into the 2 s deadline), and the file
+    is the oracle's."""
+    n = 1 << 20
+    group = {1: 32, 2: bt}[gran]
+    want_path = str(tmp_path / "want.bin")
+    oracle.c2_pwrite(want_path, n, group)
+    with G.Context(device=0, no_threads=True, service_threads=2, staging_bytes=n * 64 + (1 << 20),
+                   deadline_ns=2_000_000_000) as c:
+        for relaxed in (False, True):
+            got = _c2(c, G, str(tmp_path / "got.bin"), n, gran, bt, relaxed, True)
+            assert got == open(want_path, "rb").read(), relaxed
+            assert c.status() == [0] * G.ST_WORDS
+        assert c.stats()["requests"] == 2 * n // group
+
+
 def test_service_probe_leaves_the_context_usable(G, tmp_path):
     """genesys_service_probe publishes work-item pwrites from the host into
     the same slot area and rewrites the device-side claim state: kernels on
