@@ -340,6 +340,9 @@ def summarize(line: dict) -> dict:
                "served_p99_ms": _sig(_at(c5, "served_full", "p99_ms")),
                "persistent_rps": _sig(_at(c5, "persistent_full", "requests_per_s")),
                "persistent_p99_ms": _sig(_at(c5, "persistent_full", "p99_ms")),
+               # the executor's full-trace host-link rate, fraction of measured H2D / D2H
+               "persistent_link_frac": [_sig(_at(c5, "persistent_full", "link", "frac_h2d")),
+                                        _sig(_at(c5, "persistent_full", "link", "frac_d2h"))],
                "plain1k_rps": _sig(plain5.get("requests_per_s")), "plain1k_p99_ms": _sig(plain5.get("p99_ms")),
                "alone_eq_mix": c5.get("first1000_alone_equals_mix"), "full_eq_oracle": oc.get("c5_full_equal")},
         "oracle": {"cores": _at(ex, "probes", "host_cpus"),
@@ -565,7 +568,10 @@ def run_only(args):
         if kind == "f4":
             res = study_f4(G, local)
         else:
-            res = {"c4": serve_c4, "c5": serve_c5, "fig10": study_fig10}[kind](G, local, rank)
+            if kind == "c5":
+                res = serve_c5(G, local, rank, link=host_link_peak(torch))
+            else:
+                res = {"c4": serve_c4, "fig10": study_fig10}[kind](G, local, rank)
         print(json.dumps({"only": args.only, kind: res}), flush=True)
         return
     rig = Rig(args, local, rank, need_scan=kind == "c1" and rest.split(":")[-1] != str(C1_BYTES),
@@ -697,7 +703,7 @@ def profile_extras(args, rig, local, rank, link, checks=None):
     finally:
         for fd in fds:
             os.close(fd)
-    out["served_c5"] = serve_c5(G, local, rank, checks)
+    out["served_c5"] = serve_c5(G, local, rank, checks, link)
     out["kv_c4"] = serve_c4(G, local, rank, checks=checks)
     out["fig6_block_permutation"] = study_fig6(G, rig, local)
     out["fig7_coalescing"] = study_fig7(G, rig, local, rank)
@@ -878,12 +884,28 @@ def study_fig7(G, rig, local, rank, sizes=(256 << 10, 1 << 20, 4 << 20, 16 << 20
     return out
 
 
-def serve_c5(G, local, rank, checks=None):
+def c5_link_bytes(tr):
+    """Host-link bytes of a C5 trace, each direction: pread data in (H2D);
+    pwrite data out (D2H); each mmap'd region filled by the GPU (D2H) and read
+    back for its checksum (H2D)."""
+    import numpy as np
+    import workloads
+    live = np.arange(tr.ops.shape[1])[None, :] < tr.n_ops[:, None]
+    kind, ln = tr.ops["kind"][live], tr.ops["len"][live].astype(np.int64)
+    rd = int(ln[kind == workloads.OP_PREAD].sum())
+    wr = int(ln[kind == workloads.OP_PWRITE].sum())
+    mm = int(ln[kind == workloads.OP_MMAP].sum())
+    return rd + mm, wr + mm
+
+
+def serve_c5(G, local, rank, checks=None, link=None):
     """C5: the 10,000-request trace served with continuous admission (up to 64
     kernels in flight, graph relaunch, autotuned call granularity), and its
     first 1,000 requests both served and in the plain one-at-a-time form.
     checks["c5"] receives what the oracle leg compares: the trace, the full
-    run's results and its output file."""
+    run's results and its output file.  With `link` (the measured pinned copy
+    rates) each run also reports its host-link rate in both directions and
+    the fractions of the measured rates."""
     import numpy as np
     import workloads
     tr = workloads.c5_trace(workloads.C5_FULL)
@@ -901,13 +923,21 @@ def serve_c5(G, local, rank, checks=None):
                 finally:
                     os.close(ofd)
                 span = st["makespan_ns"] * 1e-9
-                return res, {"requests": st["requests"], "syscalls": st["syscalls"],
-                             "syscalls_per_s": round(st["syscalls"] / span, 1),
-                             "requests_per_s": round(st["requests"] / span, 1),
-                             "p50_ms": round(float(np.percentile(lat, 50)) / 1e6, 3),
-                             "p99_ms": round(float(np.percentile(lat, 99)) / 1e6, 3),
-                             "makespan_s": round(span, 3), "wall_s": round(wall, 3),
-                             "max_inflight": st["max_inflight"], "graph_launches": st["graph_launches"]}
+                row = {"requests": st["requests"], "syscalls": st["syscalls"],
+                       "syscalls_per_s": round(st["syscalls"] / span, 1),
+                       "requests_per_s": round(st["requests"] / span, 1),
+                       "p50_ms": round(float(np.percentile(lat, 50)) / 1e6, 3),
+                       "p99_ms": round(float(np.percentile(lat, 99)) / 1e6, 3),
+                       "makespan_s": round(span, 3), "wall_s": round(wall, 3),
+                       "max_inflight": st["max_inflight"], "graph_launches": st["graph_launches"]}
+                if link:
+                    h2d, d2h = c5_link_bytes(sub)
+                    row["link"] = {"h2d_GB": round(h2d / 1e9, 3), "d2h_GB": round(d2h / 1e9, 3),
+                                   "h2d_GB_per_s": round(h2d / span / 1e9, 2),
+                                   "d2h_GB_per_s": round(d2h / span / 1e9, 2),
+                                   "frac_h2d": round(h2d / span / 1e9 / link["h2d"], 4),
+                                   "frac_d2h": round(d2h / span / 1e9 / link["d2h"], 4)}
+                return res, row
             from paper_1705_06965_b300 import autotune
             ofd = os.open(os.path.join(d, "tune.bin"), os.O_CREAT | os.O_RDWR, 0o644)
             try:

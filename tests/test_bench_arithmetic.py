@@ -127,7 +127,8 @@ def _full_line():
                       "served_first1000": {"requests_per_s": 8800.2, "syscalls_per_s": 240000.7, "p99_ms": 65.3},
                       "persistent_first1000": {"requests_per_s": 12000.2, "syscalls_per_s": 330000.7, "p99_ms": 30.3},
                       "served_full": {"requests_per_s": 8700.1, "p99_ms": 70.123},
-                      "persistent_full": {"requests_per_s": 11000.1, "p99_ms": 40.123},
+                      "persistent_full": {"requests_per_s": 11000.1, "p99_ms": 40.123,
+                                          "link": {"frac_h2d": 0.63456, "frac_d2h": 0.59123}},
                       "first1000_alone_equals_mix": True,
                       "cpu_baseline_oracle_replay_first1000": {"requests_per_s": 174.2}},
         "probes": {"host_cpus": 16},
@@ -153,6 +154,7 @@ def test_summary_fits_the_kept_tail_and_carries_every_config():
     assert sm["c4"]["sat_rps"] == 799000 and sm["c4"]["replies_eq_oracle"] is True
     assert sm["c4"]["p99_us"] == 813 and sm["c4"]["best_any_rps"] == 1300000
     assert sm["c5"]["persistent_rps"] == 11000 and sm["c5"]["full_eq_oracle"] is True
+    assert sm["c5"]["persistent_link_frac"] == [0.635, 0.591]
     assert sm["oracle"]["cores"] == 16 and sm["oracle"]["c5_rps_1t"] == 174
     t = sm["targets"]
     assert t["c2_batched_beats_plain"] == {"syscalls_per_s": False, "requests_per_s": True, "p99": True}
@@ -187,3 +189,19 @@ def test_reply_digests_tell_replies_apart():
     import numpy as np
     d = bench.reply_digests([b"", b"\x80\x00\x10\x00abcd", b"\x80\x00\x10\x00abce", b"\x81\x00\x00\x00" + b"\0" * 4])
     assert d.dtype == np.uint64 and len(set(d.tolist())) == 4 and d[0] == 0
+
+
+def test_c5_link_bytes_counts_each_direction():
+    """pread bytes come in, pwrite bytes go out, an mmap'd region goes out
+    (the fill) and comes back (the checksum's read); operations past a
+    request's count are not counted."""
+    import numpy as np
+    import workloads
+    ops = np.zeros((2, workloads.C5_MAX_OPS), workloads.C5_OP)
+    ops[0, 0] = (workloads.OP_PREAD, 0, 0, 1000, 0, 0)
+    ops[0, 1] = (workloads.OP_MMAP, 0, 0, 8192, 0, 0)
+    ops[0, 2] = (workloads.OP_PWRITE, 0, 0, 999999, 0, 0)       # past n_ops: not run
+    ops[1, 0] = (workloads.OP_PWRITE, 0, 0, 300, 0, 0)
+    tr = workloads.Trace(np.zeros(2, np.uint64), np.array([64, 64], np.uint32), np.array([2, 1], np.uint32), ops,
+                         [], 300)
+    assert bench.c5_link_bytes(tr) == (1000 + 8192, 300 + 8192)
