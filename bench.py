@@ -884,6 +884,14 @@ def study_fig7(G, rig, local, rank, sizes=(256 << 10, 1 << 20, 4 << 20, 16 << 20
     return out
 
 
+# C5 serving: 128 requests on the GPU at once (one stream each), 256 MiB
+# staging and HBM budgets, 12 service threads (a sweep on the B300 machine:
+# 9.6-9.7 k requests/s against 9.2-9.4 k with 64 requests, 64 MiB budgets and
+# 8 threads, in both forms)
+C5_SERVE = dict(max_inflight=128, n_streams=128, staging_budget=256 << 20, hbm_budget=256 << 20)
+C5_SERVICE_THREADS = 12
+
+
 def c5_link_bytes(tr):
     """Host-link bytes of a C5 trace, each direction: pread data in (H2D);
     pwrite data out (D2H); each mmap'd region filled by the GPU (D2H) and read
@@ -899,8 +907,8 @@ def c5_link_bytes(tr):
 
 
 def serve_c5(G, local, rank, checks=None, link=None):
-    """C5: the 10,000-request trace served with continuous admission (up to 64
-    kernels in flight, graph relaunch, autotuned call granularity), and its
+    """C5: the 10,000-request trace served with continuous admission (up to 128
+    requests in flight, graph relaunch, autotuned call granularity), and its
     first 1,000 requests both served and in the plain one-at-a-time form.
     checks["c5"] receives what the oracle leg compares: the trace, the full
     run's results and its output file.  With `link` (the measured pinned copy
@@ -913,7 +921,7 @@ def serve_c5(G, local, rank, checks=None, link=None):
     in_fds = [os.open(p, os.O_RDONLY) for p in tr.in_paths]
     out = {}
     try:
-        with G.Context(device=local, service_threads=8, staging_bytes=512 << 20) as ctx:
+        with G.Context(device=local, service_threads=C5_SERVICE_THREADS, staging_bytes=512 << 20) as ctx:
             def run(sub, out_name="out.bin", **cfg):
                 ofd = os.open(os.path.join(d, out_name), os.O_CREAT | os.O_TRUNC | os.O_RDWR, 0o644)
                 try:
@@ -941,26 +949,26 @@ def serve_c5(G, local, rank, checks=None, link=None):
             from paper_1705_06965_b300 import autotune
             ofd = os.open(os.path.join(d, "tune.bin"), os.O_CREAT | os.O_RDWR, 0o644)
             try:
-                tuned = autotune.tune_serve(local, ctx, tr, in_fds, ofd)
+                tuned = autotune.tune_serve(local, ctx, tr, in_fds, ofd, extra=C5_SERVE)
             finally:
                 os.close(ofd)
             out["autotuned"] = tuned
             # the persistent executor form: one kernel serves every request
             ofd = os.open(os.path.join(d, "tune_p.bin"), os.O_CREAT | os.O_RDWR, 0o644)
             try:
-                tuned_p = autotune.tune_serve(local, ctx, tr, in_fds, ofd, extra={"persistent": 1})
+                tuned_p = autotune.tune_serve(local, ctx, tr, in_fds, ofd, extra={**C5_SERVE, "persistent": 1})
             finally:
                 os.close(ofd)
             out["autotuned_persistent"] = tuned_p
             first = tr.subset(np.arange(1000))
             r_plain, out["plain_first1000"] = run(first, max_inflight=1, use_graphs=0)
-            r_served, out["served_first1000"] = run(first, max_inflight=64, **tuned)
-            r_pers, out["persistent_first1000"] = run(first, max_inflight=64, persistent=1, **tuned_p)
+            r_served, out["served_first1000"] = run(first, **C5_SERVE, **tuned)
+            r_pers, out["persistent_first1000"] = run(first, **C5_SERVE, persistent=1, **tuned_p)
             m = np.arange(8)[None, :] < first.n_ops[:, None]
             out["first1000_alone_equals_mix"] = bool(np.array_equal(r_plain[m], r_served[m]) and
                                                      np.array_equal(r_plain[m], r_pers[m]))
-            r_full, out["served_full"] = run(tr, "out_full.bin", max_inflight=64, **tuned)
-            r_pfull, out["persistent_full"] = run(tr, "out_pfull.bin", max_inflight=64, persistent=1, **tuned_p)
+            r_full, out["served_full"] = run(tr, "out_full.bin", **C5_SERVE, **tuned)
+            r_pfull, out["persistent_full"] = run(tr, "out_pfull.bin", **C5_SERVE, persistent=1, **tuned_p)
             if checks is not None:
                 checks["c5"] = (tr, {"served_full": (r_full, os.path.join(d, "out_full.bin")),
                                      "persistent_full": (r_pfull, os.path.join(d, "out_pfull.bin"))})
@@ -968,8 +976,8 @@ def serve_c5(G, local, rank, checks=None, link=None):
             # 4 k/s, where latency is service time rather than queueing
             slow = tr.subset(np.arange(2000))
             slow.arrival_ns = (slow.arrival_ns.astype(np.float64) * (tr.params["rate_per_s"] / 4000.0)).astype(np.uint64)
-            _, out["served_first2000_at_4k_per_s"] = run(slow, max_inflight=64, **tuned)
-            _, out["persistent_first2000_at_4k_per_s"] = run(slow, max_inflight=64, persistent=1, **tuned_p)
+            _, out["served_first2000_at_4k_per_s"] = run(slow, **C5_SERVE, **tuned)
+            _, out["persistent_first2000_at_4k_per_s"] = run(slow, **C5_SERVE, persistent=1, **tuned_p)
         if rank == 0:
             try:
                 out["cpu_baseline_oracle_replay_first1000"] = cpu_baseline_c5(first, in_fds, d, r_served)
@@ -1114,9 +1122,14 @@ def c4_cpu_split():
     return list(range(half)), set(range(half, n))
 
 
-def serve_c4(G, local, rank, rates=tuple(50_000.0 * 2 ** i for i in range(7)), n_req=1_000_000, checks=None):
+C4_RATES = (50_000.0, 100_000.0, 200_000.0, 400_000.0, 800_000.0, 1_200_000.0, 1_600_000.0, 3_200_000.0)
+
+
+def serve_c4(G, local, rank, rates=C4_RATES, n_req=1_000_000, checks=None):
     """C4: 1M-key table in HBM, Zipf 0.99 keys, 90% GET; offered rates 50k/s
-    doubling to saturation, 1.25 s of requests per rate (200k to 1M);
+    doubling to saturation (with 1.2M/s between 800k and 1.6M, where the
+    load generator stops keeping its schedule), 1.25 s of requests per rate
+    (200k to 1M);
     achieved requests/s and send-to-reply latency.  The service threads and
     the load generator run on disjoint host cores.  The oracle's single-thread
     CPU server is offered the same rates (its own saturation point is the CPU
