@@ -110,7 +110,8 @@ def _full_line():
                                              "p50_us": 9000.1, "p99_us": 20000.2}},
         "roofline": {"service": {"achieved": 33400000.2, "frac": 0.181234,
                                  "warp_interleaved_order": {"frac": 0.347712}}},
-        "c1_4MiB": {"plain": {"GB_per_s": 5.31123}, "batched": {"GB_per_s": 7.7789}},
+        "c1_4MiB": {"plain": {"GB_per_s": 5.31123, "preads_per_s": 1296000.3, "p99_us": 612.34},
+                    "batched": {"GB_per_s": 7.7789, "preads_per_s": 1899000.1, "p99_us": 701.2}},
         "pread_scan_1GiB": {"autotuned": {"form": 0}, "plain": {"GB_per_s": 49.712, "frac_of_host_link_h2d": 0.894},
                             "warp": {"GB_per_s": 51.1, "frac_of_host_link_h2d": 0.919},
                             "batched": {"GB_per_s": 47.2, "frac_of_host_link_h2d": 0.849}},
@@ -157,11 +158,12 @@ def test_summary_fits_the_kept_tail_and_carries_every_config():
     assert sm["c5"]["persistent_link_frac"] == [0.635, 0.591]
     assert sm["oracle"]["cores"] == 16 and sm["oracle"]["c5_rps_1t"] == 174
     t = sm["targets"]
-    assert t["c2_batched_beats_plain"] == {"syscalls_per_s": False, "requests_per_s": True, "p99": True}
+    assert t["c2_batched_beats_plain"] == {"syscalls_per_s": True, "p99": True}
+    assert t["c2_coarse_grain_beats_work_item"] == {"syscalls_per_s": False, "requests_per_s": True, "p99": True}
+    assert t["c1_batched_beats_plain"] == {"syscalls_per_s": True, "p99": False}
     assert t["c5_served_beats_plain"] == {"syscalls_per_s": True, "requests_per_s": True, "p99": True}
     assert t["pread_scan_frac_h2d_ge_0.75"] == {"scan_1GiB": True, "c3": True}
-    assert t["c2_batched_service_beats_per_call"] == {"syscalls_per_s": True, "p99": True}
-    assert t["c1_batched_beats_plain"] is True and t["c3_batched_beats_plain"] is True
+    assert t["c3_batched_beats_plain"] is True
 
 
 def test_summary_of_a_line_without_extras():
