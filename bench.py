@@ -19,6 +19,7 @@ step's calls are all complete inside the timed region).
     python bench.py --only c3:batched
     python bench.py --only c4          # key-value service rate sweep (+ oracle server)
     python bench.py --only c5          # the served mixed trace
+    python bench.py --only c5:persistent:1000   # one serving form, first n requests
     python bench.py --only fig10       # echo bandwidth versus packet size
     python bench.py --only f4          # open/write/lseek/read/close/madvise from GPU code
 
@@ -574,11 +575,12 @@ def run_only(args):
         import paper_1705_06965_b300 as G
         if kind == "f4":
             res = study_f4(G, local)
+        elif kind == "c5" and rest:
+            res = serve_c5_part(G, local, rest)
+        elif kind == "c5":
+            res = serve_c5(G, local, rank, link=host_link_peak(torch))
         else:
-            if kind == "c5":
-                res = serve_c5(G, local, rank, link=host_link_peak(torch))
-            else:
-                res = {"c4": serve_c4, "fig10": study_fig10}[kind](G, local, rank)
+            res = {"c4": serve_c4, "fig10": study_fig10}[kind](G, local, rank)
         print(json.dumps({"only": args.only, kind: res}), flush=True)
         return
     rig = Rig(args, local, rank, need_scan=kind == "c1" and rest.split(":")[-1] != str(C1_BYTES),
@@ -995,6 +997,41 @@ def serve_c5(G, local, rank, checks=None, link=None):
             os.close(fd)
     out["trace"] = {"requests": len(tr), "rate_per_s": tr.params["rate_per_s"]}
     return out
+
+
+def serve_c5_part(G, local, spec):
+    """One serving form on the trace's first n requests, all present at the
+    start, with the bench's serving settings and fixed call granularity
+    (64 KiB parts, 1024-thread blocks): `spec` = "served:n" or
+    "persistent:n".  A small, bounded case for profiling the executor."""
+    import numpy as np
+    import torch
+    import workloads
+    form, _, n = spec.partition(":")
+    tr = workloads.c5_trace(workloads.C5_FULL)
+    sub = tr.subset(np.arange(min(int(n or 1000), len(tr))))
+    d = workloads.scratch_dir("bench_c5_part")
+    in_fds = [os.open(p, os.O_RDONLY) for p in tr.in_paths]
+    link = host_link_peak(torch)
+    try:
+        with G.Context(device=local, service_threads=C5_SERVICE_THREADS, staging_bytes=512 << 20) as ctx:
+            ofd = os.open(os.path.join(d, "out.bin"), os.O_CREAT | os.O_TRUNC | os.O_RDWR, 0o644)
+            try:
+                cfg = dict(C5_SERVE, min_part=65536, block_threads=1024, honor_arrivals=0,
+                           persistent=1 if form == "persistent" else 0)
+                _, lat, st = ctx.c5_serve(sub.arrival_ns, sub.threads, sub.n_ops, sub.ops, in_fds, ofd, **cfg)
+            finally:
+                os.close(ofd)
+    finally:
+        for fd in in_fds:
+            os.close(fd)
+    span = st["makespan_ns"] * 1e-9
+    h2d, d2h = c5_link_bytes(sub)
+    return {"form": form, "requests": st["requests"], "requests_per_s": round(st["requests"] / span, 1),
+            "p99_ms": round(float(np.percentile(lat, 99)) / 1e6, 3), "makespan_s": round(span, 4),
+            "link": {"h2d_GB": round(h2d / 1e9, 3), "d2h_GB": round(d2h / 1e9, 3),
+                     "frac_h2d": round(h2d / span / 1e9 / link["h2d"], 4),
+                     "frac_d2h": round(d2h / span / 1e9 / link["d2h"], 4)}}
 
 
 def cpu_baseline_c3(c, sample_bytes=512 << 20):
