@@ -188,6 +188,12 @@ struct genesys_ctx {
   std::atomic<uint64_t> mmap_new{0}, mmap_reused{0};
 
   cudaStream_t aux = nullptr;  // private stream for small copies
+  // pinned landing buffers of the small device-to-host reads made after every
+  // launch (ring positions, status words): a copy into pageable memory is
+  // staged by the driver and takes about twice as long
+  uint32_t *tails_host = nullptr;
+  int32_t *status_host = nullptr;
+  std::mutex small_mu;  // one such read at a time
   cudaEvent_t ev_start = nullptr, ev_end = nullptr;  // around the last launched kernel
 
   void *scratch = nullptr;  // device scratch arena for workload entry points
@@ -775,6 +781,8 @@ void free_all(genesys_ctx *c) {
   host_free(c, c->rings);
   host_free(c, c->ring_done);
   host_free(c, c->staging);
+  host_free(c, c->tails_host);
+  host_free(c, c->status_host);
   dev_free(c, c->owner);
   dev_free(c, c->seq);
   dev_free(c, c->known_done);
@@ -802,14 +810,14 @@ void free_all(genesys_ctx *c) {
 // kernels have finished.
 int read_tails(genesys_ctx *c, std::vector<uint32_t> &tails) {
   const uint32_t n = c->cfg.n_service_threads;
-  std::vector<uint32_t> raw((size_t)n * 32);
   if (c->host_only) {
     for (uint32_t r = 0; r < n; ++r) tails[r] = __atomic_load_n(&c->ring_tail[r * 32], __ATOMIC_ACQUIRE);
     return 0;
   }
-  CUDA_TRY(cudaMemcpyAsync(raw.data(), c->ring_tail, raw.size() * 4, cudaMemcpyDeviceToHost, c->aux));
+  std::lock_guard<std::mutex> g(c->small_mu);
+  CUDA_TRY(cudaMemcpyAsync(c->tails_host, c->ring_tail, (size_t)n * 32 * 4, cudaMemcpyDeviceToHost, c->aux));
   CUDA_TRY(cudaStreamSynchronize(c->aux));
-  for (uint32_t r = 0; r < n; ++r) tails[r] = raw[(size_t)r * 32];
+  for (uint32_t r = 0; r < n; ++r) tails[r] = c->tails_host[(size_t)r * 32];
   return 0;
 }
 
@@ -979,6 +987,10 @@ int genesys_init(const genesys_config *cfg_in, int device, genesys_ctx **out) {
     if ((rc = dev_alloc(c.get(), &c->ksite, GENESYS_KSITES))) return rc;
     if ((rc = dev_alloc(c.get(), &c->grid_bar, 64))) return rc;
     if ((rc = dev_alloc(c.get(), &c->status, GENESYS_ST_WORDS))) return rc;
+    if (!c->host_only) {
+      if ((rc = host_alloc(c.get(), &c->tails_host, (size_t)cfg.n_service_threads * 32 * 4))) return rc;
+      if ((rc = host_alloc(c.get(), &c->status_host, GENESYS_ST_WORDS * 4))) return rc;
+    }
     if ((rc = dev_alloc(c.get(), &c->lat, std::max<uint32_t>(cfg.lat_samples, 1)))) return rc;
     if ((rc = dev_alloc(c.get(), &c->lat_count, 1))) return rc;
     if (cfg.trace_capacity) {
@@ -1392,9 +1404,11 @@ int genesys_status(genesys_ctx *c, int32_t out[GENESYS_ST_WORDS], int clear) {
     if (clear) memset(c->status, 0, GENESYS_ST_WORDS * 4);
     return 0;
   }
-  CUDA_TRY(cudaMemcpyAsync(out, c->status, GENESYS_ST_WORDS * 4, cudaMemcpyDeviceToHost, c->aux));
+  std::lock_guard<std::mutex> g(c->small_mu);
+  CUDA_TRY(cudaMemcpyAsync(c->status_host, c->status, GENESYS_ST_WORDS * 4, cudaMemcpyDeviceToHost, c->aux));
   if (clear) CUDA_TRY(cudaMemsetAsync(c->status, 0, GENESYS_ST_WORDS * 4, c->aux));
   CUDA_TRY(cudaStreamSynchronize(c->aux));
+  memcpy(out, c->status_host, GENESYS_ST_WORDS * 4);
   return 0;
 }
 
