@@ -420,7 +420,7 @@ class Rig:
     """Context, files and buffers of the GPU arm."""
 
     def __init__(self, args, local, rank, need_scan=True, service_threads=None, coalesce_max=64, need_c3=True,
-                 poll_max_ns=2048, n_slots=0):
+                 poll_max_ns=2048, n_slots=0, coalesce_window_ns=0):
         import torch
         import paper_1705_06965_b300 as G
         import workloads
@@ -434,7 +434,7 @@ class Rig:
         self.c1_stage_bytes = max(2 * C1_GROUPS * C1_CHUNK, 2 * SCAN_GROUPS * SCAN_CHUNK if need_scan else 0)
         self.c3_stage_bytes = C3_CTAS * (C3_CHUNK + 64) * 2 if need_c3 else 0
         self.ctx = G.Context(device=local, service_threads=st_threads, coalesce_max=coalesce_max, poll_max_ns=poll_max_ns,
-                             n_slots=n_slots,
+                             n_slots=n_slots, coalesce_window_ns=coalesce_window_ns,
                              staging_bytes=max(SIZES) * 64 + self.c1_stage_bytes + self.c3_stage_bytes + (4 << 20),
                              deadline_ns=10_000_000_000)
         self.c2_stage = self.ctx.staging(max(SIZES) * 64)
@@ -585,7 +585,7 @@ def run_only(args):
         return
     rig = Rig(args, local, rank, need_scan=kind == "c1" and rest.split(":")[-1] != str(C1_BYTES),
               need_c3=kind == "c3", service_threads=args.service_threads, coalesce_max=args.coalesce_max,
-              poll_max_ns=args.poll_max_ns)
+              poll_max_ns=args.poll_max_ns, coalesce_window_ns=args.coalesce_window_ns)
     G = rig.G
     out = {"only": args.only}
     try:
@@ -1692,6 +1692,8 @@ def main():
     ap.add_argument("--extras", type=int, default=1, help="0: only the timed step (for launch lists)")
     ap.add_argument("--coalesce-max", type=int, default=64, help="--only: service batch size")
     ap.add_argument("--poll-max-ns", type=int, default=2048, help="--only: largest completion-poll back-off")
+    ap.add_argument("--coalesce-window-ns", type=int, default=0,
+                    help="--only: how long a service thread waits for more requests after a batch's first")
     ap.add_argument("--only", default=None, help="run one case: c2:<grain>/<order>/<block>:<threads>, "
                                                  "c1:<plain|batched>:<bytes>, c3:<plain|batched>[:<first n files>], c4, c5, fig10, f4")
     args = ap.parse_args()
