@@ -228,10 +228,12 @@ def hbm_peak() -> float:
         return 7700.0
 
 
-def host_link_peak(torch, sizes=(4 << 10, 64 << 10, 1 << 20, 16 << 20, 64 << 20, 256 << 20, 1 << 30)):
+def host_link_peak(torch, sizes=(4 << 10, 64 << 10, 1 << 20, 16 << 20, 64 << 20, 256 << 20, 1 << 30), sm=False):
     """Pinned cudaMemcpy sweep, H2D and D2H, best of 6 per size (GB/s); the
     ceiling is the best at >= 64 MiB.  Returns {"h2d": .., "d2h": .., "sweep":
-    {direction: {bytes: GB/s}}}."""
+    {direction: {bytes: GB/s}}}; with `sm`, also the SMs' own zero-copy
+    streaming over the same 1 GiB of pinned memory (genesys_link_stream, best
+    of 3): "sm_read" (what a scan of pinned staging can reach) and "sm_write"."""
     n = max(sizes)
     h = torch.empty(n, dtype=torch.uint8, pin_memory=True)
     d = torch.empty(n, dtype=torch.uint8, device="cuda")
@@ -250,6 +252,11 @@ def host_link_peak(torch, sizes=(4 << 10, 64 << 10, 1 << 20, 16 << 20, 64 << 20,
             row[str(size)] = round(best, 2)
         out["sweep"][name] = row
         out[name] = max(v for k, v in row.items() if int(k) >= 64 << 20)
+    if sm:
+        import paper_1705_06965_b300 as G
+        dev = torch.cuda.current_device()
+        out["sm_read"] = round(G.link_stream(h.data_ptr(), n, write=False, device=dev), 2)
+        out["sm_write"] = round(G.link_stream(h.data_ptr(), n, write=True, device=dev), 2)
     del h, d
     return out
 
@@ -303,6 +310,11 @@ def _beats(a, b, higher_is_better=True):
     return bool(a > b) if higher_is_better else bool(a < b)
 
 
+def _frac(a, b, nd=4):
+    """a / b rounded, or None without b."""
+    return round(a / b, nd) if a is not None and b else None
+
+
 def summarize(line: dict) -> dict:
     """The figures of every config in a few hundred bytes, for the end of the
     bench line: the headline, C1's 4 MiB forms and the 1 GiB scan against the
@@ -331,8 +343,10 @@ def summarize(line: dict) -> dict:
                     "frac_interleaved": _sig(_at(ex, "roofline", "service", "warp_interleaved_order", "frac"))},
         "c1_4MiB_GBps": {k: _sig(_at(ex, "c1_4MiB", k, "GB_per_s")) for k in ("plain", "batched")},
         "scan_1GiB": {"form": scan_best[0], "GBps": _sig(scan_best[1].get("GB_per_s")),
-                      "frac_h2d": _sig(scan_best[1].get("frac_of_host_link_h2d"))},
+                      "frac_h2d": _sig(scan_best[1].get("frac_of_host_link_h2d")),
+                      "frac_sm_read": _sig(scan_best[1].get("frac_of_sm_zero_copy_read"))},
         "c3": {"GBps": _sig(c3b.get("GB_per_s")), "frac_h2d": _sig(c3b.get("frac_of_host_link_h2d")),
+               "frac_sm_read": _sig(c3b.get("frac_of_sm_zero_copy_read")),
                "truth_eq": c3b.get("counts_equal_ground_truth")},
         "c4": {"sat_rps": _sig(c4.get("saturation_req_per_s")), "p50_us": _sig(c4.get("saturation_p50_us")),
                "p99_us": _sig(c4.get("saturation_p99_us")), "best_any_rps": _sig(c4.get("best_any_req_per_s")),
@@ -670,6 +684,7 @@ def profile_extras(args, rig, local, rank, link, checks=None):
             hists[names[cfg["form"]]] = rig.hist[0].cpu().numpy().view(np.uint32).copy()
             gbs = SCAN_BYTES / (ms * 1e-3) / 1e9
             res[names[cfg["form"]]] = {"GB_per_s": round(gbs, 2), "frac_of_host_link_h2d": round(gbs / link["h2d"], 4),
+                                       "frac_of_sm_zero_copy_read": _frac(gbs, link.get("sm_read")),
                                        "frac_of_hbm_peak": round(gbs / hbm_peak(), 5),
                                        "ms": round(ms, 2), "chunk": cfg["chunk"], "groups": cfg["groups"],
                                        "service_threads": cfg["service_threads"]}
@@ -701,6 +716,7 @@ def profile_extras(args, rig, local, rank, link, checks=None):
                 gbs = c.total_bytes / (ms * 1e-3) / 1e9
                 res["plain" if form == G.FORM_PLAIN else "batched"] = {
                     "GB_per_s": round(gbs, 2), "frac_of_host_link_h2d": round(gbs / link["h2d"], 4),
+                    "frac_of_sm_zero_copy_read": _frac(gbs, link.get("sm_read")),
                     "frac_of_hbm_peak": round(gbs / hbm_peak(), 5),
                     "ms": round(ms, 2), "counts_equal_ground_truth": ok}
             out["wordcount_c3"] = {"autotuned": best, "corpus_bytes": c.total_bytes, **res}
@@ -1456,7 +1472,7 @@ def run_genesys(args):
                        "peak_source": f"one host thread writing the same 64 MiB from the same pinned buffer to the "
                                       f"same tmpfs file with pwrite calls of 256 KiB-64 MiB, best of 3 each (best: "
                                       f"{host_chunk >> 10} KiB calls; measured)"}
-    link = host_link_peak(torch)
+    link = host_link_peak(torch, sm=True)
     link["round_trip_ns"] = G.link_pingpong(local, rounds=20000)  # GPU <-> host flag, the floor of a blocking call
     probes = host_probes(torch, local, rig.scan_path)
     checks = {"c2_files": [(nn, os.path.join(rig.d, f"c2_{nn}.bin")) for nn in SIZES]}

@@ -47,7 +47,8 @@ EXPORTS = [
     "genesys_c3_wordcount", "genesys_c3_wordcount_noalloc", "genesys_serve_config_default", "genesys_c5_serve",
     "genesys_reclaim", "genesys_mmap_reserve", "genesys_kv_start", "genesys_kv_stop", "genesys_kv_value",
     "genesys_kv_client", "genesys_c6_permute", "genesys_gpu_call", "genesys_echo_start", "genesys_echo_stop",
-    "genesys_echo_client", "genesys_service_probe", "genesys_link_pingpong", "genesys_service_restart",
+    "genesys_echo_client", "genesys_service_probe", "genesys_link_pingpong", "genesys_link_stream",
+    "genesys_service_restart",
     "genesys_trace_read", "genesys_sizeof", "genesys_service_health", "genesys_service_probe_order",
     "genesys_stats", "genesys_graph_launches", "genesys_check_pread_cap", "genesys_kv_received",
 ]
@@ -167,6 +168,8 @@ def lib() -> ctypes.CDLL:
         "genesys_trace_read": (ctypes.c_int, [vp, vp, u32, ctypes.POINTER(u32), vp, u32, ctypes.POINTER(u32),
                                               ctypes.POINTER(i64)]),
         "genesys_link_pingpong": (ctypes.c_int, [ctypes.c_int, u32, u64, ctypes.POINTER(u64)]),
+        "genesys_link_stream": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, u64, ctypes.c_int, u32, u32, u32,
+                                               ctypes.POINTER(ctypes.c_double)]),
         "genesys_service_probe": (ctypes.c_int, [vp, ctypes.c_int, vp, u32, u64, ctypes.POINTER(u64)]),
         "genesys_service_probe_order": (ctypes.c_int, [vp, ctypes.c_int, vp, u32, u64, u32, u32,
                                                        ctypes.POINTER(u64)]),
@@ -638,6 +641,20 @@ def link_pingpong(device: int = 0, rounds: int = 2000, timeout_ns: int = 2_000_0
     ns = ctypes.c_uint64()
     _check(lib().genesys_link_pingpong(device, rounds, timeout_ns, ctypes.byref(ns)), "genesys_link_pingpong")
     return float(ns.value)
+
+
+def link_stream(host_ptr: int, nbytes: int, write: bool = False, device: int = 0, blocks: int = 0,
+                threads: int = 512, reps: int = 3) -> float:
+    """Zero-copy host-link GB/s of the SMs reading (or writing) nbytes of
+    pinned, host-mapped memory at host_ptr (genesys_link_stream); blocks 0 =
+    4 per SM."""
+    import torch
+    if blocks == 0:
+        blocks = 4 * torch.cuda.get_device_properties(device).multi_processor_count
+    gbs = ctypes.c_double()
+    _check(lib().genesys_link_stream(device, host_ptr, nbytes, 1 if write else 0, blocks, threads, reps,
+                                     ctypes.byref(gbs)), "genesys_link_stream")
+    return float(gbs.value)
 
 
 def echo_client(port_base: int, n_sockets: int, packet_bytes: int, n_packets: int, window: int = 4,

@@ -407,6 +407,31 @@ __global__ void pingpong_kernel(uint64_t *ping, const uint64_t *pong, uint32_t r
   out[2] = late ? 1ull : 0ull;
 }
 
+// Zero-copy streaming over the host link: every thread of the grid reads
+// (or writes) 16-byte words of pinned host memory, four independent accesses
+// in flight per thread.  The reads fold into one word that is compared with a
+// value it practically never takes, so they cannot be dropped.
+__global__ void link_read_kernel(const uint4 *__restrict__ p, uint64_t n16, unsigned long long *sink) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t x = 0;
+  for (; i + 3 * stride < n16; i += 4 * stride) {
+    const uint4 a = p[i], b = p[i + stride], c = p[i + 2 * stride], d = p[i + 3 * stride];
+    x ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w ^ c.x ^ c.y ^ c.z ^ c.w ^ d.x ^ d.y ^ d.z ^ d.w;
+  }
+  for (; i < n16; i += stride) {
+    const uint4 a = p[i];
+    x ^= a.x ^ a.y ^ a.z ^ a.w;
+  }
+  if (x == 0x9E3779B9u) atomicAdd(sink, 1ull);
+}
+
+__global__ void link_write_kernel(uint4 *__restrict__ p, uint64_t n16) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride)
+    p[i] = make_uint4((uint32_t)i, (uint32_t)(i >> 32), ~(uint32_t)i, 0x5EEDu);
+}
+
 // Clock alignment: round r, one GPU thread reads its clock, stores r to
 // `ping`, waits for the host to answer r on `pong` and reads its clock again;
 // t[2r], t[2r + 1] = the two readings.  Bounded by deadline_ns.
@@ -683,6 +708,56 @@ int genesys_link_pingpong(int device, uint32_t rounds, uint64_t timeout_ns, uint
     if (st) cudaStreamDestroy(st);
     if (d_out) cudaFree(d_out);
     cudaFreeHost(flags);
+    return rc;
+  });
+}
+
+// Zero-copy bandwidth of the SMs over the host link: the ceiling of a kernel
+// that reads what the service copied into pinned staging (or writes what a
+// pwrite will send).  Best of `reps` timed launches after one warm-up.
+int genesys_link_stream(int device, void *host_buf, uint64_t bytes, int write, uint32_t blocks, uint32_t threads,
+                        uint32_t reps, double *gb_per_s) {
+  return genesys_guard("genesys_link_stream", [&]() -> int {
+    if (!host_buf || !gb_per_s || bytes < 16 || bytes % 16 || (uintptr_t)host_buf % 16 || reps == 0)
+      return set_err(GENESYS_EINVAL, "a 16-byte aligned buffer of a positive multiple of 16 bytes, reps >= 1");
+    if (blocks == 0 || blocks > 65535 || threads == 0 || threads > 1024 || threads % 32)
+      return set_err(GENESYS_EINVAL, "blocks 1..65535, threads a multiple of 32 up to 1024");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(device) != cudaSuccess) return set_err(GENESYS_ECUDA, "cudaSetDevice");
+    uint4 *d_buf = nullptr;
+    unsigned long long *d_sink = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = 0;
+    if (cudaHostGetDevicePointer((void **)&d_buf, host_buf, 0) != cudaSuccess) {
+      cudaGetLastError();
+      rc = set_err(GENESYS_EINVAL, "host_buf is not pinned, host-mapped memory");
+    } else if (cudaMalloc((void **)&d_sink, sizeof(unsigned long long)) != cudaSuccess ||
+               cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+               cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+      rc = set_err(GENESYS_ECUDA, "link stream set-up");
+    }
+    const uint64_t n16 = bytes / 16;
+    float best = 0.0f;
+    for (uint32_t r = 0; rc == 0 && r <= reps; ++r) {
+      cudaEventRecord(e0, st);
+      if (write) link_write_kernel<<<blocks, threads, 0, st>>>(d_buf, n16);
+      else link_read_kernel<<<blocks, threads, 0, st>>>(d_buf, n16, d_sink);
+      cudaEventRecord(e1, st);
+      float ms = 0.0f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        rc = set_err(GENESYS_ECUDA, "link stream kernel");
+      } else if (r > 0 && ms > 0.0f && (best == 0.0f || ms < best)) {
+        best = ms;  // launch 0 is the warm-up
+      }
+    }
+    if (rc == 0) *gb_per_s = (double)bytes / (best * 1e-3) / 1e9;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    if (d_sink) cudaFree(d_sink);
+    if (prev >= 0) cudaSetDevice(prev);
     return rc;
   });
 }

@@ -113,7 +113,8 @@ def _full_line():
         "c1_4MiB": {"plain": {"GB_per_s": 5.31123, "preads_per_s": 1296000.3, "p99_us": 612.34},
                     "batched": {"GB_per_s": 7.7789, "preads_per_s": 1899000.1, "p99_us": 701.2}},
         "pread_scan_1GiB": {"autotuned": {"form": 0}, "plain": {"GB_per_s": 49.712, "frac_of_host_link_h2d": 0.894},
-                            "warp": {"GB_per_s": 51.1, "frac_of_host_link_h2d": 0.919},
+                            "warp": {"GB_per_s": 51.1, "frac_of_host_link_h2d": 0.919,
+                                     "frac_of_sm_zero_copy_read": 0.98765},
                             "batched": {"GB_per_s": 47.2, "frac_of_host_link_h2d": 0.849}},
         "wordcount_c3": {"plain": {"GB_per_s": 40.1, "frac_of_host_link_h2d": 0.72, "counts_equal_ground_truth": True},
                          "batched": {"GB_per_s": 49.5, "frac_of_host_link_h2d": 0.89,
@@ -149,7 +150,7 @@ def test_summary_fits_the_kept_tail_and_carries_every_config():
     assert '"summary": {' in tail and '"targets": {' in tail
     sm = line["summary"]
     assert len(json.dumps(sm)) <= 1350, len(json.dumps(sm))
-    assert sm["scan_1GiB"] == {"form": "warp", "GBps": 51.1, "frac_h2d": 0.919}
+    assert sm["scan_1GiB"] == {"form": "warp", "GBps": 51.1, "frac_h2d": 0.919, "frac_sm_read": 0.988}
     assert sm["wi_2p20"] == {"calls_per_s": 33400000, "frac_file_order": 0.181, "frac_interleaved": 0.348}
     assert sm["c3"]["GBps"] == 49.5 and sm["c3"]["truth_eq"] is True
     assert sm["c4"]["sat_rps"] == 799000 and sm["c4"]["replies_eq_oracle"] is True

@@ -668,6 +668,7 @@ def test_every_entry_point_rejects_null_arguments():
     t("genesys_echo_client", 0, 0, 0, 0, 0, 0, 0, 0, 0, None)
     t("genesys_service_probe", None, 0, None, 0, 0, None)
     t("genesys_link_pingpong", 0, 0, 0, None)
+    t("genesys_link_stream", 0, None, 0, 0, 0, 0, 0, None)
     t("genesys_service_restart", None, 0, 0)
     t("genesys_trace_read", None, None, 0, None, None, 0, None, None)
     t("genesys_c5_serve", None, None, 0, None, 0, 0, None, None, None, None)
