@@ -969,7 +969,11 @@ def serve_c5(G, local, rank, checks=None, link=None):
                                    "h2d_GB_per_s": round(h2d / span / 1e9, 2),
                                    "d2h_GB_per_s": round(d2h / span / 1e9, 2),
                                    "frac_h2d": round(h2d / span / 1e9 / link["h2d"], 4),
-                                   "frac_d2h": round(d2h / span / 1e9 / link["d2h"], 4)}
+                                   "frac_d2h": round(d2h / span / 1e9 / link["d2h"], 4),
+                                   # against what the SMs alone stream over the link (the fills
+                                   # are SM stores, the read-backs and scans SM loads)
+                                   "frac_sm_read": _frac(h2d / span / 1e9, link.get("sm_read")),
+                                   "frac_sm_write": _frac(d2h / span / 1e9, link.get("sm_write"))}
                 return res, row
             from paper_1705_06965_b300 import autotune
             ofd = os.open(os.path.join(d, "tune.bin"), os.O_CREAT | os.O_RDWR, 0o644)
@@ -1028,7 +1032,7 @@ def serve_c5_part(G, local, spec):
     sub = tr.subset(np.arange(min(int(n or 1000), len(tr))))
     d = workloads.scratch_dir("bench_c5_part")
     in_fds = [os.open(p, os.O_RDONLY) for p in tr.in_paths]
-    link = host_link_peak(torch)
+    link = host_link_peak(torch, sm=True)
     try:
         with G.Context(device=local, service_threads=C5_SERVICE_THREADS, staging_bytes=512 << 20) as ctx:
             ofd = os.open(os.path.join(d, "out.bin"), os.O_CREAT | os.O_TRUNC | os.O_RDWR, 0o644)
@@ -1047,7 +1051,9 @@ def serve_c5_part(G, local, spec):
             "p99_ms": round(float(np.percentile(lat, 99)) / 1e6, 3), "makespan_s": round(span, 4),
             "link": {"h2d_GB": round(h2d / 1e9, 3), "d2h_GB": round(d2h / 1e9, 3),
                      "frac_h2d": round(h2d / span / 1e9 / link["h2d"], 4),
-                     "frac_d2h": round(d2h / span / 1e9 / link["d2h"], 4)}}
+                     "frac_d2h": round(d2h / span / 1e9 / link["d2h"], 4),
+                     "frac_sm_read": _frac(h2d / span / 1e9, link.get("sm_read")),
+                     "frac_sm_write": _frac(d2h / span / 1e9, link.get("sm_write"))}}
 
 
 def cpu_baseline_c3(c, sample_bytes=512 << 20):
