@@ -592,7 +592,7 @@ def run_only(args):
         elif kind == "c5" and rest:
             res = serve_c5_part(G, local, rest)
         elif kind == "c5":
-            res = serve_c5(G, local, rank, link=host_link_peak(torch))
+            res = serve_c5(G, local, rank, link=host_link_peak(torch, sm=True))
         else:
             res = {"c4": serve_c4, "fig10": study_fig10}[kind](G, local, rank)
         print(json.dumps({"only": args.only, kind: res}), flush=True)
