@@ -257,6 +257,8 @@ def host_link_peak(torch, sizes=(4 << 10, 64 << 10, 1 << 20, 16 << 20, 64 << 20,
         dev = torch.cuda.current_device()
         out["sm_read"] = round(G.link_stream(h.data_ptr(), n, write=False, device=dev), 2)
         out["sm_write"] = round(G.link_stream(h.data_ptr(), n, write=True, device=dev), 2)
+        # both directions at once (half the blocks each way): the sum of the two
+        out["sm_both"] = round(G.link_stream(h.data_ptr(), n, write=2, device=dev), 2)
     del h, d
     return out
 
@@ -355,9 +357,10 @@ def summarize(line: dict) -> dict:
                "served_p99_ms": _sig(_at(c5, "served_full", "p99_ms")),
                "persistent_rps": _sig(_at(c5, "persistent_full", "requests_per_s")),
                "persistent_p99_ms": _sig(_at(c5, "persistent_full", "p99_ms")),
-               # the executor's full-trace host-link rate, fraction of measured H2D / D2H
-               "persistent_link_frac": [_sig(_at(c5, "persistent_full", "link", "frac_h2d")),
-                                        _sig(_at(c5, "persistent_full", "link", "frac_d2h"))],
+               # the executor's full-trace host-link rate: fractions of the measured H2D and
+               # D2H copy rates, and of the SMs' own rate streaming both ways at once
+               "persistent_link_frac": [_sig(_at(c5, "persistent_full", "link", k))
+                                        for k in ("frac_h2d", "frac_d2h", "frac_sm_both")],
                "plain1k_rps": _sig(plain5.get("requests_per_s")), "plain1k_p99_ms": _sig(plain5.get("p99_ms")),
                "alone_eq_mix": c5.get("first1000_alone_equals_mix"), "full_eq_oracle": oc.get("c5_full_equal")},
         "oracle": {"cores": _at(ex, "probes", "host_cpus"),
@@ -973,7 +976,9 @@ def serve_c5(G, local, rank, checks=None, link=None):
                                    # against what the SMs alone stream over the link (the fills
                                    # are SM stores, the read-backs and scans SM loads)
                                    "frac_sm_read": _frac(h2d / span / 1e9, link.get("sm_read")),
-                                   "frac_sm_write": _frac(d2h / span / 1e9, link.get("sm_write"))}
+                                   "frac_sm_write": _frac(d2h / span / 1e9, link.get("sm_write")),
+                                   # both directions against the SMs streaming both at once
+                                   "frac_sm_both": _frac((h2d + d2h) / span / 1e9, link.get("sm_both"))}
                 return res, row
             from paper_1705_06965_b300 import autotune
             ofd = os.open(os.path.join(d, "tune.bin"), os.O_CREAT | os.O_RDWR, 0o644)
@@ -1053,7 +1058,8 @@ def serve_c5_part(G, local, spec):
                      "frac_h2d": round(h2d / span / 1e9 / link["h2d"], 4),
                      "frac_d2h": round(d2h / span / 1e9 / link["d2h"], 4),
                      "frac_sm_read": _frac(h2d / span / 1e9, link.get("sm_read")),
-                     "frac_sm_write": _frac(d2h / span / 1e9, link.get("sm_write"))}}
+                     "frac_sm_write": _frac(d2h / span / 1e9, link.get("sm_write")),
+                     "frac_sm_both": _frac((h2d + d2h) / span / 1e9, link.get("sm_both"))}}
 
 
 def cpu_baseline_c3(c, sample_bytes=512 << 20):

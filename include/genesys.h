@@ -652,11 +652,14 @@ int genesys_link_pingpong(int device, uint32_t rounds, uint64_t timeout_ns, uint
  * `host_buf` (the caller's; for example a context's staging, or any memory
  * pinned by cudaHostAlloc or cudaHostRegister with mapping) with 16-byte
  * loads (write = 0) or 16-byte stores (write = 1) that cover every word
- * once.  *gb_per_s = bytes / the fastest of `reps` launches (CUDA events)
- * after one warm-up.  Use more bytes than the GPU's L2 holds, or reads may be
+ * once, or both at once (write = 2: the even blocks read the first half of
+ * the buffer while the odd blocks write the second half).  *gb_per_s = bytes
+ * (both directions together for write = 2) / the fastest of `reps` launches
+ * (CUDA events) after one warm-up.  Use more bytes than the GPU's L2 holds, or reads may be
  * served from it.  GENESYS_EINVAL: NULL pointers, a buffer not 16-byte aligned
  * or not a positive multiple of 16 bytes, reps 0, blocks outside 1..65535,
- * threads not a multiple of 32 up to 1024, or memory that is not pinned and
+ * threads not a multiple of 32 up to 1024, write outside 0..2 (2: fewer than
+ * 2 blocks or bytes not a multiple of 32), or memory that is not pinned and
  * mapped.  The caller's current device is unchanged. */
 int genesys_link_stream(int device, void *host_buf, uint64_t bytes, int write, uint32_t blocks, uint32_t threads,
                         uint32_t reps, double *gb_per_s);

@@ -643,16 +643,17 @@ def link_pingpong(device: int = 0, rounds: int = 2000, timeout_ns: int = 2_000_0
     return float(ns.value)
 
 
-def link_stream(host_ptr: int, nbytes: int, write: bool = False, device: int = 0, blocks: int = 0,
+def link_stream(host_ptr: int, nbytes: int, write=False, device: int = 0, blocks: int = 0,
                 threads: int = 512, reps: int = 3) -> float:
-    """Zero-copy host-link GB/s of the SMs reading (or writing) nbytes of
-    pinned, host-mapped memory at host_ptr (genesys_link_stream); blocks 0 =
-    4 per SM."""
+    """Zero-copy host-link GB/s of the SMs reading (write False/0), writing
+    (True/1) or both at once (2: half the blocks each way, the two directions'
+    bytes summed) nbytes of pinned, host-mapped memory at host_ptr
+    (genesys_link_stream); blocks 0 = 4 per SM."""
     import torch
     if blocks == 0:
         blocks = 4 * torch.cuda.get_device_properties(device).multi_processor_count
     gbs = ctypes.c_double()
-    _check(lib().genesys_link_stream(device, host_ptr, nbytes, 1 if write else 0, blocks, threads, reps,
+    _check(lib().genesys_link_stream(device, host_ptr, nbytes, int(write), blocks, threads, reps,
                                      ctypes.byref(gbs)), "genesys_link_stream")
     return float(gbs.value)
 

@@ -432,6 +432,32 @@ __global__ void link_write_kernel(uint4 *__restrict__ p, uint64_t n16) {
     p[i] = make_uint4((uint32_t)i, (uint32_t)(i >> 32), ~(uint32_t)i, 0x5EEDu);
 }
 
+// Both directions at once: the even blocks read the first n16_half words,
+// the odd blocks write the next n16_half (as the two kernels above do).
+__global__ void link_both_kernel(uint4 *__restrict__ p, uint64_t n16_half, unsigned long long *sink) {
+  const uint64_t half_blocks = gridDim.x / 2;
+  const uint64_t stride = half_blocks * blockDim.x;
+  const uint64_t first = (uint64_t)(blockIdx.x / 2) * blockDim.x + threadIdx.x;
+  if (blockIdx.x / 2 >= half_blocks) return;  // an odd grid's last block
+  if (blockIdx.x % 2 == 0) {
+    uint32_t x = 0;
+    uint64_t i = first;
+    for (; i + 3 * stride < n16_half; i += 4 * stride) {
+      const uint4 a = p[i], b = p[i + stride], c = p[i + 2 * stride], d = p[i + 3 * stride];
+      x ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w ^ c.x ^ c.y ^ c.z ^ c.w ^ d.x ^ d.y ^ d.z ^ d.w;
+    }
+    for (; i < n16_half; i += stride) {
+      const uint4 a = p[i];
+      x ^= a.x ^ a.y ^ a.z ^ a.w;
+    }
+    if (x == 0x9E3779B9u) atomicAdd(sink, 1ull);
+  } else {
+    uint4 *q = p + n16_half;
+    for (uint64_t i = first; i < n16_half; i += stride)
+      q[i] = make_uint4((uint32_t)i, (uint32_t)(i >> 32), ~(uint32_t)i, 0x5EEDu);
+  }
+}
+
 // Clock alignment: round r, one GPU thread reads its clock, stores r to
 // `ping`, waits for the host to answer r on `pong` and reads its clock again;
 // t[2r], t[2r + 1] = the two readings.  Bounded by deadline_ns.
@@ -722,6 +748,8 @@ int genesys_link_stream(int device, void *host_buf, uint64_t bytes, int write, u
       return set_err(GENESYS_EINVAL, "a 16-byte aligned buffer of a positive multiple of 16 bytes, reps >= 1");
     if (blocks == 0 || blocks > 65535 || threads == 0 || threads > 1024 || threads % 32)
       return set_err(GENESYS_EINVAL, "blocks 1..65535, threads a multiple of 32 up to 1024");
+    if (write < 0 || write > 2 || (write == 2 && (blocks < 2 || bytes % 32)))
+      return set_err(GENESYS_EINVAL, "write 0, 1 or 2 (both: at least 2 blocks and a multiple of 32 bytes)");
     int prev = -1;
     cudaGetDevice(&prev);
     if (cudaSetDevice(device) != cudaSuccess) return set_err(GENESYS_ECUDA, "cudaSetDevice");
@@ -742,7 +770,8 @@ int genesys_link_stream(int device, void *host_buf, uint64_t bytes, int write, u
     float best = 0.0f;
     for (uint32_t r = 0; rc == 0 && r <= reps; ++r) {
       cudaEventRecord(e0, st);
-      if (write) link_write_kernel<<<blocks, threads, 0, st>>>(d_buf, n16);
+      if (write == 2) link_both_kernel<<<blocks, threads, 0, st>>>(d_buf, n16 / 2, d_sink);
+      else if (write) link_write_kernel<<<blocks, threads, 0, st>>>(d_buf, n16);
       else link_read_kernel<<<blocks, threads, 0, st>>>(d_buf, n16, d_sink);
       cudaEventRecord(e1, st);
       float ms = 0.0f;

@@ -130,7 +130,8 @@ def _full_line():
                       "persistent_first1000": {"requests_per_s": 12000.2, "syscalls_per_s": 330000.7, "p99_ms": 30.3},
                       "served_full": {"requests_per_s": 8700.1, "p99_ms": 70.123},
                       "persistent_full": {"requests_per_s": 11000.1, "p99_ms": 40.123,
-                                          "link": {"frac_h2d": 0.63456, "frac_d2h": 0.59123}},
+                                          "link": {"frac_h2d": 0.63456, "frac_d2h": 0.59123,
+                                                   "frac_sm_both": 0.90111}},
                       "first1000_alone_equals_mix": True,
                       "cpu_baseline_oracle_replay_first1000": {"requests_per_s": 174.2}},
         "probes": {"host_cpus": 16},
@@ -156,7 +157,7 @@ def test_summary_fits_the_kept_tail_and_carries_every_config():
     assert sm["c4"]["sat_rps"] == 799000 and sm["c4"]["replies_eq_oracle"] is True
     assert sm["c4"]["p99_us"] == 813 and sm["c4"]["best_any_rps"] == 1300000
     assert sm["c5"]["persistent_rps"] == 11000 and sm["c5"]["full_eq_oracle"] is True
-    assert sm["c5"]["persistent_link_frac"] == [0.635, 0.591]
+    assert sm["c5"]["persistent_link_frac"] == [0.635, 0.591, 0.901]
     assert sm["oracle"]["cores"] == 16 and sm["oracle"]["c5_rps_1t"] == 174
     t = sm["targets"]
     assert t["c2_batched_beats_plain"] == {"syscalls_per_s": True, "p99": True}

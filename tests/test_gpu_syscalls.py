@@ -89,6 +89,16 @@ def test_link_stream_reads_and_writes_pinned_memory():
     assert (words[:, 3] == 0x5EED).all()
     r = G.link_stream(buf.data_ptr(), n, write=False, reps=2)
     assert r > 5.0 and w > 5.0, (r, w)
+    # both directions at once: the odd blocks write the second half (the same
+    # pattern, counted from its start); the even blocks only read the first
+    buf.zero_()
+    b = G.link_stream(buf.data_ptr(), n, write=2, reps=1)
+    half = len(words) // 2
+    assert (words[:half] == 0).all()
+    j = np.arange(half, dtype=np.uint64)
+    assert np.array_equal(words[half:, 0], (j & 0xFFFFFFFF).astype(np.uint32))
+    assert np.array_equal(words[half:, 2], (~j & 0xFFFFFFFF).astype(np.uint32))
+    assert b > 5.0, b
     with pytest.raises(G.GenesysError) as e:
         G.link_stream(buf.data_ptr() + 8, 4096)                    # not 16-byte aligned
     assert e.value.code == G.EINVAL
