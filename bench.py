@@ -1508,10 +1508,18 @@ def run_genesys(args):
         alg_bytes = C1_BYTES + (C1_BYTES // C1_CHUNK) * ALG_BYTES_PER_CALL
         units = C1_BYTES
     achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
-    peak = link["d2h"] if dom.startswith("c2") else link["h2d"]
+    # the kernel moves its bytes with its own SM stores (pwrite payloads and
+    # slots) or loads (preads): the SMs' zero-copy rate over the link is its
+    # ceiling; the copy engines' rate is reported beside it
+    c2 = dom.startswith("c2")
+    copy_peak = link["d2h"] if c2 else link["h2d"]
+    peak = link.get("sm_write" if c2 else "sm_read") or copy_peak
     roofline = {"bound": "host_link", "kernel": dom, "achieved": round(achieved, 3), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 5), "traffic": load_traffic(dom, units),
-                "peak_source": "pinned cudaMemcpy sweep in this run, best at >= 64 MiB (of measured)",
+                "peak_source": ("the SMs' zero-copy " + ("stores" if c2 else "loads") + " over 1 GiB of pinned memory "
+                                "(genesys_link_stream) in this run (of measured)")
+                if peak != copy_peak else "pinned cudaMemcpy sweep in this run, best at >= 64 MiB (of measured)",
+                "peak_copy_engine": copy_peak, "frac_copy_engine": round(achieved / copy_peak, 5),
                 "alg_bytes_per_launch": int(alg_bytes), "avg_launch_ms": round(avg_ms, 4),
                 "share_of_timed_device_time": round(tot[dom] / sum(tot.values()), 4),
                 "service": service_roofline, "coarse": coarse_roofline}
