@@ -186,7 +186,8 @@ __device__ __forceinline__ uint32_t ring_of(const genesys_dev &g, uint32_t slot)
  * group for other calls. */
 __device__ __forceinline__ uint32_t ring_for(const genesys_dev &g, uint32_t slot, uint32_t nr, uint64_t a0,
                                              uint64_t a3) {
-  return (nr == SYS_pread64 || nr == SYS_pwrite64) ? genesys_ring_of_file(a0, a3, g.n_rings) : ring_of(g, slot);
+  return (nr == SYS_pread64 || nr == SYS_pwrite64) ? genesys_ring_of_file(a0, a3, g.n_rings, nr == SYS_pread64)
+                                                    : ring_of(g, slot);
 }
 
 /* Give up the claim lock of a slot this thread owns without using it. */

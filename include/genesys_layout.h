@@ -105,14 +105,20 @@ static inline GENESYS_HD uint32_t genesys_ring_of(uint32_t slot, uint32_t n_ring
 }
 
 /* Doorbell ring of a positional file call (pread/pwrite): calls on the same
- * 256 KiB region of one file meet in one ring, whichever GPU threads make
- * them, so the ring's service thread finds file neighbours in its batches
- * and merges them into one Linux call; the regions of a file spread over all
- * rings.  Any slot may therefore reach any ring (each ring holds an entry
- * for every slot). */
-#define GENESYS_RING_REGION_SHIFT 18u
-static inline GENESYS_HD uint32_t genesys_ring_of_file(uint64_t fd, uint64_t off, uint32_t n_rings) {
-  uint64_t z = (off >> GENESYS_RING_REGION_SHIFT) * 0x9E3779B97F4A7C15ull ^ (fd + 1) * 0xC2B2AE3D27D4EB4Full;
+ * region of one file meet in one ring, whichever GPU threads make them, and
+ * the regions of a file spread over all rings.  Any slot may therefore reach
+ * any ring (each ring holds an entry for every slot).  Writes to one file
+ * serialise on its inode lock whichever thread makes them, so for writes the
+ * region is 256 KiB: the ring's service thread finds file neighbours in its
+ * batches and merges them into fewer Linux calls.  Reads of one file take no
+ * such lock and copy in parallel on several threads, so for reads the region
+ * is 16 KiB: neighbouring small reads (4 KiB chunks of many blocks) spread
+ * over the service threads instead of queueing on one. */
+#define GENESYS_RING_REGION_SHIFT_WRITE 18u
+#define GENESYS_RING_REGION_SHIFT_READ 14u
+static inline GENESYS_HD uint32_t genesys_ring_of_file(uint64_t fd, uint64_t off, uint32_t n_rings, int is_read) {
+  const uint32_t shift = is_read ? GENESYS_RING_REGION_SHIFT_READ : GENESYS_RING_REGION_SHIFT_WRITE;
+  uint64_t z = (off >> shift) * 0x9E3779B97F4A7C15ull ^ (fd + 1) * 0xC2B2AE3D27D4EB4Full;
   z ^= z >> 29;
   z *= 0xBF58476D1CE4E5B9ull;
   z ^= z >> 32;

@@ -1520,7 +1520,7 @@ int genesys_service_probe_order(genesys_ctx *c, int fd, const void *payload, uin
       // (always one ring) are announced by one entry, other slots one by one.
       const uint32_t n_runs = (m + run - 1) / run;
       auto ring_at = [&](uint32_t s) {
-        return genesys_ring_of_file((uint64_t)(int64_t)fd, (i0 + s) * (uint64_t)bytes_per_call, R);
+        return genesys_ring_of_file((uint64_t)(int64_t)fd, (i0 + s) * (uint64_t)bytes_per_call, R, 0);
       };
       auto ring_entry = [&](uint32_t s, uint32_t count) {
         const uint32_t r = ring_at(s);  // the ring a GPU pwrite of this request rings: by file region
@@ -1614,7 +1614,7 @@ int genesys_emulate_call(genesys_ctx *c, uint32_t nr, const uint64_t args[6], ui
                      __ATOMIC_RELEASE);
     // the ring the device would choose: by file region for pread/pwrite
     const uint32_t r = (nr == SYS_pread64 || nr == SYS_pwrite64)
-                           ? genesys_ring_of_file(args[0], args[3], c->cfg.n_service_threads)
+                           ? genesys_ring_of_file(args[0], args[3], c->cfg.n_service_threads, nr == SYS_pread64)
                            : genesys_ring_of(s, c->cfg.n_service_threads);
     const uint32_t pos = __atomic_fetch_add(&c->ring_tail[r * 32], 1u, __ATOMIC_ACQ_REL);
     __atomic_store_n(&c->rings[(size_t)r * c->ring_cap + (pos & (c->ring_cap - 1))], GENESYS_RING_ENTRY(pos, s),
