@@ -305,6 +305,28 @@ def test_c_abi_from_plain_c(tmp_path):
     assert out.stdout.startswith("ok requests=66")
 
 
+def test_ring_choice_spreads_reads_and_groups_writes(tmp_path):
+    """Doorbell rings of positional file calls (genesys_ring_of_file, compiled
+    from the layout header by a plain C program): a round of 64 neighbouring
+    4 KiB preads reaches at least 3 of 4 rings, so the service threads copy in
+    parallel, while neighbouring pwrites of one 16 KiB block (64-byte calls)
+    and of one 256 KiB region (64 KiB calls) stay in one ring, where they
+    merge."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    exe = str(tmp_path / "ring_regions")
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-I", os.path.join(root, "include"),
+                           os.path.join(root, "tests", "c_abi", "ring_regions.c"), "-o", exe])
+    out = subprocess.run([exe, "4"], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    got = dict(kv.split("=") for kv in out.stdout.split())
+    assert int(got["reads_min_rings"]) >= 3, got
+    assert int(got["writes_max_rings"]) == 1 and int(got["big_writes_max_rings"]) == 1, got
+
+
 def test_service_thread_restart_loses_no_request():
     """A service thread is stopped and restarted while emulated callers keep
     calling: requests published meanwhile wait in the ring and are carried out
