@@ -515,7 +515,7 @@ int genesys_kv_start(genesys_ctx *ctx, const uint8_t *keys, const uint16_t *vlen
  * has not left, or its calls did not drain) the server is kept and the call
  * can be repeated; the context cannot be shut down until one succeeds. */
 int genesys_kv_stop(genesys_kv_server *srv, uint64_t timeout_ns, uint64_t *served);
-/* C4 (Sec. 7.3; the survey's reading for lost datagrams: the server logs the
+/* C4 (Sec. 7.3; lost datagrams are read this way: the server logs the
  * requests it received and the oracle replays exactly those).  Bit j of
  * out[j / 32] (host array of (n_seqs + 31) / 32 words) is set when the
  * request whose seq field is j reached the server, for j < n_seqs <=
