@@ -234,7 +234,10 @@ __device__ __forceinline__ int64_t slot_try_claim(const genesys_dev &g, uint32_t
   uint32_t s = hint % g.n_slots;
   uint32_t busy = 0xFFFFFFFFu, busy_sq = 0;  // the first owned slot with an unfinished request
   for (uint32_t probe = 0; probe < 32; ++probe) {
-    if (!dcheck(g, s < g.n_slots)) return -kETIMEDOUT;
+    if (!dcheck(g, s < g.n_slots)) {  // (checked builds; s stays below n_slots by construction)
+      if (busy != 0xFFFFFFFFu) slot_release_lock(g, busy);
+      return -kETIMEDOUT;
+    }
     if (atomicCAS(&g.owner[s], 0u, 1u) == 0u) {
       __threadfence();
       const uint32_t sq = ld_relaxed_gpu(&g.seq[s]);
