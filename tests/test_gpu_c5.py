@@ -149,13 +149,19 @@ def full(tmp_path_factory):
 
 
 @pytest.mark.parametrize("form", [{}, {"persistent": 1}], ids=["kernel_per_request", "persistent_executor"])
-def test_c5_full_trace_equals_oracle(ctx, full, tmp_path, form):
-    """The full trace served the way the benchmark serves it (64 in flight,
-    arrivals honoured; graph relaunch or the persistent executor): every
-    request's results and the whole output file equal the oracle's."""
+def test_c5_full_trace_equals_oracle(G, full, tmp_path, form):
+    """The full trace served the way the benchmark serves it (its context and
+    serving settings: 128 in flight on 128 streams, 256 MiB staging and HBM
+    budgets, 12 service threads; arrivals honoured; graph relaunch or the
+    persistent executor): every request's results and the whole output file
+    equal the oracle's."""
+    import bench
     tr, want, ref = full
-    res, lat, st, out = serve(ctx, tr, str(tmp_path / "full.bin"), max_inflight=64, **form)
+    with G.Context(device=0, service_threads=bench.C5_SERVICE_THREADS, staging_bytes=512 << 20,
+                   deadline_ns=10_000_000_000) as c:
+        res, lat, st, out = serve(c, tr, str(tmp_path / "full.bin"), **bench.C5_SERVE, **form)
     assert st["requests"] == len(tr) and np.all(lat > 0)
+    assert st["max_inflight"] > 64
     bad = np.where(((res != want) & _mask(tr)).any(axis=1))[0]
     assert len(bad) == 0, (len(bad), bad[:5])
     assert out == ref
