@@ -781,6 +781,7 @@ int genesys_link_stream(int device, void *host_buf, uint64_t bytes, int write, u
         best = ms;  // launch 0 is the warm-up
       }
     }
+    if (rc == 0 && best <= 0.0f) rc = set_err(GENESYS_ECUDA, "link stream: no timed launch");
     if (rc == 0) *gb_per_s = (double)bytes / (best * 1e-3) / 1e9;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
