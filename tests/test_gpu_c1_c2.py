@@ -194,6 +194,23 @@ def test_c2_small_slot_area_and_coalescing_window(G, tmp_path, n_slots, threads,
         assert st["failed"] == 0
 
 
+def test_c2_every_combination_on_a_64_slot_area(G, tmp_path):
+    """Every legal grain x ordering x blocking combination with 4,133 threads
+    on a 64-slot area: callers outnumber slots 65 to 1, so work-item lanes wait
+    for slots and lone callers find all 32 they try busy and wait for one; the
+    files equal the oracle's and no wait runs out."""
+    n = 4096 + 37
+    with G.Context(device=0, n_slots=64, service_threads=2, staging_bytes=n * 64 + (1 << 20),
+                   deadline_ns=10_000_000_000) as c:
+        for gran, relaxed, nb in COMBOS:
+            for bt in ((64, 256) if gran == 2 else (256,)):
+                want_path = str(tmp_path / "want.bin")
+                oracle.c2_pwrite(want_path, n, {0: 1, 1: 32, 2: bt, 3: n}[gran])
+                got = _c2(c, G, str(tmp_path / "got.bin"), n, gran, bt, relaxed, nb)
+                assert got == open(want_path, "rb").read(), (gran, bt, relaxed, nb)
+                assert c.status() == [0] * G.ST_WORDS, (gran, bt, relaxed, nb)
+
+
 @pytest.mark.parametrize("gran,bt", [(1, 256), (2, 64)])
 def test_nonblocking_callers_pass_over_slots_still_in_flight(G, tmp_path, gran, bt):
     """Non-blocking warp and work-group pwrites of 2^20 threads on a context
