@@ -181,10 +181,10 @@ typedef struct genesys_dev {
   genesys_slot *slots;        /* host-mapped, n_slots entries                       */
   uint64_t *done;             /* host-mapped, n_slots completion words              */
   uint64_t *rings;            /* host-mapped, n_rings * ring_cap doorbell entries   */
-  uint64_t *ring_done;        /* host-mapped: entries of ring r the CPU has finished,
-                                 GENESYS_RING_DONE_COPIES copies on separate 64-byte
-                                 lines (word 8 * (r * COPIES + c)), stored with
-                                 release after each batch's completion words       */
+  uint64_t *ring_done;        /* host-mapped: leading entries of ring r the CPU has
+                                 finished, GENESYS_RING_DONE_COPIES copies on separate
+                                 64-byte lines (word 8 * (r * COPIES + c)), stored with
+                                 release after the completion words they cover      */
   uint32_t *owner;            /* device memory: slot claim locks                    */
   uint32_t *seq;              /* device memory: last published sequence per slot    */
   uint32_t *known_done;       /* device memory: last sequence seen finished         */

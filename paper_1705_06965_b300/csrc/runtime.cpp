@@ -110,6 +110,7 @@ struct Request {
   uint32_t slot, seq, nr, flags;
   uint64_t a[6];
   int64_t ret;
+  uint32_t entry;  // index, within its batch, of the ring entry that announced it
 };
 
 // One service batch and the scratch its processing needs (owned by one
@@ -122,12 +123,18 @@ struct Batch {
   std::vector<uint8_t> has_pred;
   std::vector<uint32_t> hidx, hgen;  // open-addressing table: (call, fd, offset) -> run
   std::vector<uint32_t> slot_ids;    // slots of the ready ring entries
+  std::vector<uint32_t> entry_of;    // ring entry (index within the batch) of each request
+  std::vector<uint32_t> left;        // per ring entry: its requests not yet completed
+  std::vector<uint64_t> done_ns;     // per request: when its completion word was written
+  uint32_t n_entries = 0, prefix = 0;  // entries taken; leading entries wholly completed
+  uint64_t head = 0;                 // ring position of the batch's first entry
   uint32_t gen = 0;
   size_t target;                     // requests a batch takes (coalesce_max)
   // room for the target and one more ring entry's requests (entries are taken whole)
   explicit Batch(size_t want)
       : req(want + GENESYS_RING_MAX_RUN - 1), ptr(req.size()), run(req.size() + 1), next(req.size()),
-        has_pred(req.size()), slot_ids(req.size()), target(want) {
+        has_pred(req.size()), slot_ids(req.size()), entry_of(req.size()), left(req.size()),
+        done_ns(req.size()), target(want) {
     size_t cap = 16;
     while (cap < 2 * req.size()) cap <<= 1;
     hidx.assign(cap, 0);
@@ -495,6 +502,27 @@ size_t merge_run(const genesys_ctx *c, Request *const *reqs, size_t i, size_t n,
 
 inline bool is_rw(uint32_t nr) { return nr == SYS_pread64 || nr == SYS_pwrite64; }
 
+// Requests p[0..m) of the batch are carried out: write their completion
+// words now, and advance the ring's finished count past every leading entry
+// whose requests are all complete.  A caller waits for the count to pass its
+// entry, so completing call by call (instead of once the whole batch is done)
+// lets the first requests of a batch go on while the service still works on
+// the rest.
+void finish(genesys_ctx *c, uint32_t ri, Batch &b, Request *const *p, size_t m, Counters &k) {
+  const uint64_t now = c->cfg.trace_capacity ? genesys_mono_ns() : 0;
+  for (size_t i = 0; i < m; ++i) {
+    complete(c, *p[i], k);
+    --b.left[p[i]->entry];
+    b.done_ns[(size_t)(p[i] - b.req.data())] = now;
+  }
+  const uint32_t before = b.prefix;
+  while (b.prefix < b.n_entries && b.left[b.prefix] == 0) ++b.prefix;
+  if (b.prefix != before)
+    for (uint32_t q = 0; q < GENESYS_RING_DONE_COPIES; ++q)
+      __atomic_store_n(&c->ring_done[((size_t)ri * GENESYS_RING_DONE_COPIES + q) * 8], b.head + b.prefix,
+                       __ATOMIC_RELEASE);
+}
+
 // Returns the time it finished (genesys_mono_ns).
 uint64_t process_batch(genesys_ctx *c, uint32_t ri, Batch &b, size_t n, Counters &k) {
   const uint64_t t0 = genesys_mono_ns();
@@ -573,35 +601,39 @@ uint64_t process_batch(genesys_ctx *c, uint32_t ri, Batch &b, size_t n, Counters
     }
   }
   bump(k.order_ns, genesys_mono_ns() - t0);
+  uint64_t cpl_ns = 0;  // time spent completing (writing completion words and the count)
   for (size_t i = 0; i < n;) {
     Request &r = *p[i];
     if (c->cfg.merge && (r.nr == SYS_pread64 || r.nr == SYS_pwrite64)) {
-      i = merge_run(c, p, i, n, k);
+      const size_t j = merge_run(c, p, i, n, k);
+      const uint64_t f0 = genesys_mono_ns();
+      finish(c, ri, b, p + i, j - i, k);
+      cpl_ns += genesys_mono_ns() - f0;
+      i = j;
       continue;
     }
     const uint64_t e0 = genesys_mono_ns();
     r.ret = execute_one(c, r, k);
-    const uint64_t dt = genesys_mono_ns() - e0;
+    const uint64_t e1 = genesys_mono_ns();
+    const uint64_t dt = e1 - e0;
     const int oi = op_index(r.nr);
     bump(k.op_ns[oi], dt);
     if (dt > k.op_max_ns[oi].load(std::memory_order_relaxed)) k.op_max_ns[oi].store(dt, std::memory_order_relaxed);
     if (r.ret > 0 && (r.nr == SYS_pread64 || r.nr == SYS_pwrite64 || r.nr == SYS_read || r.nr == SYS_write ||
                       r.nr == SYS_sendto || r.nr == SYS_recvfrom))
       bump(k.bytes, (uint64_t)r.ret);
+    finish(c, ri, b, p + i, 1, k);
+    cpl_ns += genesys_mono_ns() - e1;
     ++i;
   }
   const uint64_t t_cpl = genesys_mono_ns();
   uint64_t per_op[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (size_t i = 0; i < n; ++i) {
-    complete(c, req[i], k);
-    ++per_op[op_index(req[i].nr)];
-  }
+  for (size_t i = 0; i < n; ++i) ++per_op[op_index(req[i].nr)];
   if (c->cfg.trace_capacity) {
     std::vector<genesys_trace_host> &tr = c->trace_host[ri];
     const uint32_t at = c->trace_n[ri].load(std::memory_order_relaxed);
-    const uint64_t t_done = genesys_mono_ns();
     for (size_t i = 0; i < n; ++i)
-      if (at + i < tr.size()) tr[at + i] = genesys_trace_host{req[i].slot, req[i].seq, t0, t_done};
+      if (at + i < tr.size()) tr[at + i] = genesys_trace_host{req[i].slot, req[i].seq, t0, b.done_ns[i]};
     c->trace_n[ri].store(at + (uint32_t)n, std::memory_order_release);
   }
   for (int o = 0; o < 8; ++o)
@@ -609,7 +641,7 @@ uint64_t process_batch(genesys_ctx *c, uint32_t ri, Batch &b, size_t n, Counters
   bump(k.requests, n);
   bump(k.batches, 1);
   const uint64_t t_end = genesys_mono_ns();
-  bump(k.complete_ns, t_end - t_cpl);
+  bump(k.complete_ns, cpl_ns + (t_end - t_cpl));
   k.last_batch_ns.store(t_end, std::memory_order_relaxed);
   bump(k.busy_ns, t_end - t0);
   return t_end;
@@ -663,11 +695,14 @@ size_t poll_ring(genesys_ctx *c, uint32_t ri, Batch &b) {
   // take the ready entries first and prefetch their slots (written by the GPU,
   // so their lines are not in the CPU's caches), then read the slots
   uint32_t *slots = b.slot_ids.data();
+  uint32_t *ent = b.entry_of.data();
   while (n < target && entry_ready(ring, mask, h + e, &s, &cnt)) {
     for (uint32_t q = 0; q < cnt; ++q) {
       slots[n + q] = s + q;
+      ent[n + q] = (uint32_t)e;
       __builtin_prefetch(&c->slots[s + q], 0, 0);
     }
+    b.left[e] = cnt;
     n += cnt;
     ++e;
   }
@@ -683,12 +718,19 @@ size_t poll_ring(genesys_ctx *c, uint32_t ri, Batch &b) {
     return 0;
   }
   const uint64_t t_pick = genesys_mono_ns();
-  for (size_t i = 0; i < n; ++i) read_request(c, slots[i], &batch[i]);
+  for (size_t i = 0; i < n; ++i) {
+    read_request(c, slots[i], &batch[i]);
+    batch[i].entry = ent[i];
+  }
   if (n < target && c->cfg.coalesce_window_ns) {
     const uint64_t until = genesys_mono_ns() + c->cfg.coalesce_window_ns;
     while (n < target && genesys_mono_ns() < until) {
       if (entry_ready(ring, mask, h + e, &s, &cnt)) {
-        for (uint32_t q = 0; q < cnt; ++q) read_request(c, s + q, &batch[n + q]);
+        for (uint32_t q = 0; q < cnt; ++q) {
+          read_request(c, s + q, &batch[n + q]);
+          batch[n + q].entry = (uint32_t)e;
+        }
+        b.left[e] = cnt;
         n += cnt;
         ++e;
       } else {
@@ -696,6 +738,9 @@ size_t poll_ring(genesys_ctx *c, uint32_t ri, Batch &b) {
       }
     }
   }
+  b.head = h;
+  b.n_entries = (uint32_t)e;
+  b.prefix = 0;
   bump(k.pickup_ns, genesys_mono_ns() - t_pick);
   const uint64_t t_done = process_batch(c, ri, b, n, k);
   c->head[ri] = h + e;
